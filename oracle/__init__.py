@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the B-spline registration objective (arXiv 1806.09907).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+of the benchmark may import this module; the library itself never does. The
+arithmetic lives in ``airgb_oracle.c`` (plain C, double precision); this
+module builds it with gcc and wraps it with ctypes. It shares no code with the
+CUDA path.
+
+Every array argument is widened to float64 (exact for the fp32 arrays the GPU
+path consumes). Shapes follow the library's layout: scalar volumes are
+``(Z, Y, X)`` (``(Y, X)`` in 2D), vector fields and control coefficients are
+component planes ``(d, Z, Y, X)`` / ``(d, nz, ny, nx)`` with component 0 = x.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "airgb_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+MSE, NCC, LCC = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` with gcc (portable C11)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    ci, cd = ctypes.c_int, ctypes.c_double
+    lib.alref_kernel_b3.argtypes = [cd]
+    lib.alref_kernel_b3.restype = cd
+    lib.alref_lattice_size.argtypes = [ci, i64p, ci, i64p]
+    lib.alref_displacement.argtypes = [ci, i64p, ci, dp, dp]
+    lib.alref_displacement_adjoint.argtypes = [ci, i64p, ci, dp, dp]
+    lib.alref_warp.argtypes = [ci, i64p, dp, dp, dp, u8p, dp]
+    lib.alref_mse.argtypes = [i64p, dp, dp, u8p, dp, dp]
+    lib.alref_ncc.argtypes = [i64p, dp, dp, u8p, cd, dp, dp]
+    lib.alref_lcc.argtypes = [ci, i64p, dp, dp, u8p, ci, cd, dp, dp]
+    lib.alref_diffusion.argtypes = [ci, i64p, dp, dp, dp]
+    lib.alref_objective_grad.argtypes = [ci, i64p, ci, ci, ci, cd, cd, dp, dp, dp, dp, dp]
+    for name in ("alref_lattice_size", "alref_displacement", "alref_displacement_adjoint",
+                 "alref_warp", "alref_mse", "alref_ncc", "alref_lcc", "alref_diffusion",
+                 "alref_objective_grad"):
+        getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a, t=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _grid(shape):
+    """Volume shape (Z,Y,X) or (Y,X) -> (ndim, int64[3] sizes X,Y,Z)."""
+    if len(shape) == 3:
+        return 3, np.array([shape[2], shape[1], shape[0]], dtype=np.int64)
+    if len(shape) == 2:
+        return 2, np.array([shape[1], shape[0], 1], dtype=np.int64)
+    raise ValueError(f"bad volume shape {shape}")
+
+
+def _check(st, what):
+    if st != 0:
+        raise ValueError(f"oracle {what} rejected its arguments (status {st})")
+
+
+def kernel_b3(r: float) -> float:
+    """k_B1D(r) of the cubic B-spline kernel (Sec. III-C)."""
+    return _load().alref_kernel_b3(float(r))
+
+
+def lattice_shape(shape, delta: int):
+    """Control-lattice shape in volume order ((nz,ny,nx) or (ny,nx))."""
+    nd, N = _grid(shape)
+    n = np.zeros(3, dtype=np.int64)
+    _check(_load().alref_lattice_size(nd, _p(N, ctypes.c_int64), int(delta), _p(n, ctypes.c_int64)),
+           "lattice_size")
+    return (int(n[2]), int(n[1]), int(n[0])) if nd == 3 else (int(n[1]), int(n[0]))
+
+
+def displacement(shape, delta, ctrl):
+    """u = sum_j c_j k(x_j, x), Eq. (kernel_basis) with the B-spline basis."""
+    nd, N = _grid(shape)
+    c = _d(ctrl)
+    assert c.shape == (nd,) + lattice_shape(shape, delta), c.shape
+    u = np.zeros((nd,) + tuple(shape), dtype=np.float64)
+    _check(_load().alref_displacement(nd, _p(N, ctypes.c_int64), int(delta), _p(c), _p(u)),
+           "displacement")
+    return u
+
+
+def displacement_adjoint(shape, delta, g_disp):
+    """g_c = B^T g_u, the transpose of :func:`displacement`."""
+    nd, N = _grid(shape)
+    g = _d(g_disp)
+    assert g.shape == (nd,) + tuple(shape)
+    gc = np.zeros((nd,) + lattice_shape(shape, delta), dtype=np.float64)
+    _check(_load().alref_displacement_adjoint(nd, _p(N, ctypes.c_int64), int(delta), _p(g), _p(gc)),
+           "displacement_adjoint")
+    return gc
+
+
+def warp(moving, disp, with_grad=False):
+    """Backward warp with mask and linear interpolation (Sec. III-C, Image Warping).
+
+    Returns (W, mask[, dM~/dy]) with W = 0 and grad = 0 outside the mask."""
+    m = _d(moving)
+    nd, N = _grid(m.shape)
+    u = _d(disp)
+    assert u.shape == (nd,) + m.shape
+    w = np.zeros(m.shape, dtype=np.float64)
+    mask = np.zeros(m.shape, dtype=np.uint8)
+    gy = np.zeros((nd,) + m.shape, dtype=np.float64) if with_grad else None
+    _check(_load().alref_warp(nd, _p(N, ctypes.c_int64), _p(m), _p(u), _p(w),
+                              _p(mask, ctypes.c_uint8), _p(gy) if with_grad else None), "warp")
+    return (w, mask, gy) if with_grad else (w, mask)
+
+
+def similarity(kind, fixed, warped, mask, eps=1e-5, window=7):
+    """S and dS/dW for MSE / NCC / LCC (Sec. III-B)."""
+    f, w = _d(fixed), _d(warped)
+    mk = np.ascontiguousarray(mask, dtype=np.uint8)
+    nd, N = _grid(f.shape)
+    S = np.zeros(1, dtype=np.float64)
+    g = np.zeros(f.shape, dtype=np.float64)
+    lib = _load()
+    if kind == MSE:
+        st = lib.alref_mse(_p(N, ctypes.c_int64), _p(f), _p(w), _p(mk, ctypes.c_uint8), _p(S), _p(g))
+    elif kind == NCC:
+        st = lib.alref_ncc(_p(N, ctypes.c_int64), _p(f), _p(w), _p(mk, ctypes.c_uint8), float(eps),
+                           _p(S), _p(g))
+    elif kind == LCC:
+        st = lib.alref_lcc(nd, _p(N, ctypes.c_int64), _p(f), _p(w), _p(mk, ctypes.c_uint8),
+                           int(window), float(eps), _p(S), _p(g))
+    else:
+        raise ValueError(kind)
+    _check(st, "similarity")
+    return float(S[0]), g
+
+
+def diffusion(disp):
+    """R_diff and dR/du, Eq. (diffusion_regularizer)."""
+    u = _d(disp)
+    nd = u.shape[0]
+    _, N = _grid(u.shape[1:])
+    R = np.zeros(1, dtype=np.float64)
+    g = np.zeros_like(u)
+    _check(_load().alref_diffusion(nd, _p(N, ctypes.c_int64), _p(u), _p(R), _p(g)), "diffusion")
+    return float(R[0]), g
+
+
+def objective_grad(kind, fixed, moving, ctrl, delta, lam, eps=1e-5, window=7, grad=True):
+    """J = S + lam*R, Eq. (objective), and dJ/dc.
+
+    Returns ({"J","S","R","n_mask"}, g_ctrl or None)."""
+    f, m, c = _d(fixed), _d(moving), _d(ctrl)
+    nd, N = _grid(f.shape)
+    assert c.shape == (nd,) + lattice_shape(f.shape, delta), c.shape
+    out = np.zeros(4, dtype=np.float64)
+    gc = np.zeros_like(c) if grad else None
+    _check(_load().alref_objective_grad(nd, _p(N, ctypes.c_int64), int(delta), int(kind),
+                                        int(window), float(eps), float(lam), _p(f), _p(m), _p(c),
+                                        _p(out), _p(gc) if grad else None), "objective_grad")
+    vals = {"J": float(out[0]), "S": float(out[1]), "R": float(out[2]), "n_mask": float(out[3])}
+    return vals, gc

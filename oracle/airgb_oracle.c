@@ -1,0 +1,533 @@
+/*
+ * FP64 CPU oracle for the regularised B-spline registration objective of
+ * AIRLab (arXiv 1806.09907) and its gradient with respect to the control
+ * points.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference that the
+ * CUDA library is checked against. Only the test suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may load it. It shares no code with
+ * the CUDA path: no headers, helpers, tables or constants.
+ *
+ * Every routine computes in double precision, from double inputs (the
+ * Python wrapper widens the fp32 arrays the GPU path consumes, which is
+ * exact). Each routine states the passage of the paper it follows and the
+ * reading taken where the paper is silent.
+ *
+ * Conventions (readings of the paper, stated once):
+ *  - Grid: d in {2,3}; sizes N = (X, Y, Z), Z = 1 in 2D; voxel spacing 1;
+ *    linear index (z*Y + y)*X + x, x fastest.
+ *  - Vector fields are component planes: u[i][z][y][x], i < d, voxel units.
+ *  - Control lattice (Sec. III-C, the B-spline kernel; placement is not
+ *    given in the paper): spacing delta (integer); per active axis
+ *    n_k = floor((N_k - 1)/delta) + 4 control points, point j at voxel
+ *    coordinate p_j = (j - 1)*delta. In 2D n_z = 1. Coefficients are planes
+ *    c[i][jz][jy][jx], voxel units.
+ *  - The kernel argument is scaled by delta: k(x_j, x) = prod_k
+ *    k_B1D((x_k - p_{j,k})/delta) (the spacing defines the kernel's extent,
+ *    Sec. III-C).
+ *  - Warp (Sec. III-C, Image Warping): y = x + u(x); a point is outside if
+ *    any y_k < 0 or y_k > N_k - 1 (the strict test of the masking snippet,
+ *    mapped from [-1,1] to voxel units with -1 -> 0 and +1 -> N_k - 1).
+ *    A non-finite y_k counts as outside. Linear interpolation uses the floor
+ *    cell clamped to [0, N_k - 2].
+ *
+ * "Parity pins": each routine is pinned by tests against closed forms,
+ * invariants, library routines on special cases and central differences;
+ * none is unpinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ALREF_OK 0
+#define ALREF_ERR_ARG 1
+
+/* ------------------------------------------------------------------------ */
+/* The cubic B-spline kernel k_B1D of Sec. III-C (B-spline item):           */
+/*   2/3 - |r|^2 + |r|^3/2   for 0 <= |r| < 1                               */
+/*   (2 - |r|)^3 / 6         for 1 <= |r| < 2                               */
+/*   0                       for 2 <= |r|                                   */
+/* ------------------------------------------------------------------------ */
+double alref_kernel_b3(double r)
+{
+    double a = fabs(r);
+    if (a < 1.0)
+        return 2.0 / 3.0 - a * a + a * a * a / 2.0;
+    if (a < 2.0) {
+        double t = 2.0 - a;
+        return t * t * t / 6.0;
+    }
+    return 0.0;
+}
+
+/* Control-lattice size per axis (reading: n = floor((N-1)/delta) + 4). */
+int alref_lattice_size(int ndim, const int64_t *N, int delta, int64_t *n)
+{
+    if ((ndim != 2 && ndim != 3) || delta < 1)
+        return ALREF_ERR_ARG;
+    for (int k = 0; k < 3; ++k) {
+        if (k < ndim) {
+            if (N[k] < 2)
+                return ALREF_ERR_ARG;
+            n[k] = (N[k] - 1) / delta + 4;
+        } else {
+            if (N[k] != 1)
+                return ALREF_ERR_ARG;
+            n[k] = 1;
+        }
+    }
+    return ALREF_OK;
+}
+
+static int64_t nvox(const int64_t *N) { return N[0] * N[1] * N[2]; }
+
+/* Kernel weight of control index j for voxel coordinate xk along an axis.
+ * For an inactive axis (2D, z) the single plane has weight 1. */
+static double axis_weight(int active, int64_t xk, int64_t j, int delta)
+{
+    if (!active)
+        return 1.0;
+    double pj = (double)(j - 1) * (double)delta;
+    return alref_kernel_b3(((double)xk - pj) / (double)delta);
+}
+
+/* Range of control indices that can have a non-zero weight at xk: the kernel
+ * vanishes for |r| >= 2, i.e. outside j in (xk/delta - 1, xk/delta + 3).
+ * A generous window is used; the weight itself decides. */
+static void axis_range(int active, int64_t xk, int delta, int64_t nk, int64_t *j0, int64_t *j1)
+{
+    if (!active) {
+        *j0 = 0;
+        *j1 = 0;
+        return;
+    }
+    int64_t q = xk / delta;
+    int64_t a = q - 2, b = q + 5;
+    if (a < 0)
+        a = 0;
+    if (b > nk - 1)
+        b = nk - 1;
+    *j0 = a;
+    *j1 = b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (kernel_basis) with the B-spline basis: u_i(x) = sum_j c_{i,j} k(x_j,x). */
+/* The sum runs over every control point whose kernel can be non-zero.      */
+/* ------------------------------------------------------------------------ */
+int alref_displacement(int ndim, const int64_t *N, int delta, const double *ctrl, double *disp)
+{
+    int64_t n[3];
+    if (alref_lattice_size(ndim, N, delta, n))
+        return ALREF_ERR_ARG;
+    const int64_t X = N[0], Y = N[1], Z = N[2];
+    const int64_t nc = n[0] * n[1] * n[2], nv = nvox(N);
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                int64_t jx0, jx1, jy0, jy1, jz0, jz1;
+                axis_range(1, x, delta, n[0], &jx0, &jx1);
+                axis_range(1, y, delta, n[1], &jy0, &jy1);
+                axis_range(ndim == 3, z, delta, n[2], &jz0, &jz1);
+                for (int i = 0; i < ndim; ++i) {
+                    double acc = 0.0;
+                    for (int64_t jz = jz0; jz <= jz1; ++jz)
+                        for (int64_t jy = jy0; jy <= jy1; ++jy)
+                            for (int64_t jx = jx0; jx <= jx1; ++jx) {
+                                double k = axis_weight(1, x, jx, delta) *
+                                           axis_weight(1, y, jy, delta) *
+                                           axis_weight(ndim == 3, z, jz, delta);
+                                acc += ctrl[i * nc + (jz * n[1] + jy) * n[0] + jx] * k;
+                            }
+                    disp[i * nv + (z * Y + y) * X + x] = acc;
+                }
+            }
+    return ALREF_OK;
+}
+
+/* Transpose of the expansion above (the adjoint of the up-sampling by
+ * transposed convolution, Sec. III-C): g_c[i,j] = sum_x k(x_j,x) g_u[i](x). */
+int alref_displacement_adjoint(int ndim, const int64_t *N, int delta, const double *g_disp,
+                               double *g_ctrl)
+{
+    int64_t n[3];
+    if (alref_lattice_size(ndim, N, delta, n))
+        return ALREF_ERR_ARG;
+    const int64_t X = N[0], Y = N[1], Z = N[2];
+    const int64_t nc = n[0] * n[1] * n[2], nv = nvox(N);
+    for (int64_t i = 0; i < ndim * nc; ++i)
+        g_ctrl[i] = 0.0;
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                int64_t jx0, jx1, jy0, jy1, jz0, jz1;
+                axis_range(1, x, delta, n[0], &jx0, &jx1);
+                axis_range(1, y, delta, n[1], &jy0, &jy1);
+                axis_range(ndim == 3, z, delta, n[2], &jz0, &jz1);
+                for (int64_t jz = jz0; jz <= jz1; ++jz)
+                    for (int64_t jy = jy0; jy <= jy1; ++jy)
+                        for (int64_t jx = jx0; jx <= jx1; ++jx) {
+                            double k = axis_weight(1, x, jx, delta) *
+                                       axis_weight(1, y, jy, delta) *
+                                       axis_weight(ndim == 3, z, jz, delta);
+                            if (k == 0.0)
+                                continue;
+                            for (int i = 0; i < ndim; ++i)
+                                g_ctrl[i * nc + (jz * n[1] + jy) * n[0] + jx] +=
+                                    k * g_disp[i * nv + (z * Y + y) * X + x];
+                        }
+            }
+    return ALREF_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward warp with the out-of-domain mask and linear interpolation       */
+/* (Sec. III-C, Image Warping). Also returns the derivative of the          */
+/* interpolant with respect to the sample position, needed by the exact     */
+/* gradient (Sec. III-A): zero where the point is outside.                   */
+/*   warped[v] = m(v) * M~(y(v)), mask[v] = m(v), grad_y[k][v] = dM~/dy_k.   */
+/* grad_y may be NULL.                                                       */
+/* ------------------------------------------------------------------------ */
+int alref_warp(int ndim, const int64_t *N, const double *moving, const double *disp,
+               double *warped, uint8_t *mask, double *grad_y)
+{
+    if ((ndim != 2 && ndim != 3) || N[0] < 2 || N[1] < 2 || (ndim == 3 && N[2] < 2) ||
+        (ndim == 2 && N[2] != 1))
+        return ALREF_ERR_ARG;
+    const int64_t X = N[0], Y = N[1], Z = N[2], nv = nvox(N);
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                const int64_t v = (z * Y + y) * X + x;
+                double p[3] = {(double)x, (double)y, (double)z};
+                int inside = 1;
+                for (int k = 0; k < ndim; ++k) {
+                    p[k] += disp[k * nv + v];
+                    /* outside iff p > N-1 or p < 0; NaN fails both tests below */
+                    if (!(p[k] >= 0.0 && p[k] <= (double)(N[k] - 1)))
+                        inside = 0;
+                }
+                mask[v] = (uint8_t)inside;
+                if (!inside) {
+                    warped[v] = 0.0;
+                    if (grad_y)
+                        for (int k = 0; k < ndim; ++k)
+                            grad_y[k * nv + v] = 0.0;
+                    continue;
+                }
+                int64_t c[3] = {0, 0, 0};
+                double f[3] = {0.0, 0.0, 0.0};
+                for (int k = 0; k < ndim; ++k) {
+                    int64_t i0 = (int64_t)floor(p[k]);
+                    if (i0 > N[k] - 2)
+                        i0 = N[k] - 2;
+                    if (i0 < 0)
+                        i0 = 0;
+                    c[k] = i0;
+                    f[k] = p[k] - (double)i0;
+                }
+                double val = 0.0, g[3] = {0.0, 0.0, 0.0};
+                const int ncorner = ndim == 3 ? 8 : 4;
+                for (int corner = 0; corner < ncorner; ++corner) {
+                    int b[3] = {corner & 1, (corner >> 1) & 1, (corner >> 2) & 1};
+                    double wk[3], dk[3];
+                    for (int k = 0; k < 3; ++k) {
+                        if (k < ndim) {
+                            wk[k] = b[k] ? f[k] : 1.0 - f[k];
+                            dk[k] = b[k] ? 1.0 : -1.0;
+                        } else {
+                            wk[k] = 1.0;
+                            dk[k] = 0.0;
+                        }
+                    }
+                    int64_t zz = c[2] + (ndim == 3 ? b[2] : 0);
+                    double m = moving[(zz * Y + (c[1] + b[1])) * X + (c[0] + b[0])];
+                    val += wk[0] * wk[1] * wk[2] * m;
+                    g[0] += dk[0] * wk[1] * wk[2] * m;
+                    g[1] += wk[0] * dk[1] * wk[2] * m;
+                    g[2] += wk[0] * wk[1] * dk[2] * m;
+                }
+                warped[v] = val;
+                if (grad_y)
+                    for (int k = 0; k < ndim; ++k)
+                        grad_y[k * nv + v] = g[k];
+            }
+    return ALREF_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Similarity measures (Sec. III-B). Each returns S and dS/dW per voxel.     */
+/* g_w may be NULL (value only).                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (mse): mean of squared differences, taken over the points inside the
+ * mask (reading: the mask of the warping snippet drops outside points, so
+ * the mean runs over |X_m|). */
+int alref_mse(const int64_t *N, const double *fixed, const double *warped, const uint8_t *mask,
+              double *S, double *g_w)
+{
+    const int64_t nv = nvox(N);
+    double cnt = 0.0, sum = 0.0;
+    for (int64_t v = 0; v < nv; ++v)
+        if (mask[v]) {
+            double d = warped[v] - fixed[v];
+            sum += d * d;
+            cnt += 1.0;
+        }
+    *S = cnt > 0.0 ? sum / cnt : 0.0;
+    if (g_w)
+        for (int64_t v = 0; v < nv; ++v)
+            g_w[v] = (mask[v] && cnt > 0.0) ? 2.0 * (warped[v] - fixed[v]) / cnt : 0.0;
+    return ALREF_OK;
+}
+
+/* NCC (Sec. III-B). The printed formula is garbled; reading: the Pearson
+ * correlation over the masked points,
+ *   rho = sum (F-muF)(W-muW) / sqrt(sum (F-muF)^2 * sum (W-muW)^2 + eps),
+ * and S = 1 - rho (zero for identical images). */
+int alref_ncc(const int64_t *N, const double *fixed, const double *warped, const uint8_t *mask,
+              double eps, double *S, double *g_w)
+{
+    const int64_t nv = nvox(N);
+    double cnt = 0.0, sf = 0.0, sw = 0.0;
+    for (int64_t v = 0; v < nv; ++v)
+        if (mask[v]) {
+            cnt += 1.0;
+            sf += fixed[v];
+            sw += warped[v];
+        }
+    if (cnt == 0.0) {
+        *S = 0.0;
+        if (g_w)
+            for (int64_t v = 0; v < nv; ++v)
+                g_w[v] = 0.0;
+        return ALREF_OK;
+    }
+    double muf = sf / cnt, muw = sw / cnt;
+    double cov = 0.0, vf = 0.0, vw = 0.0;
+    for (int64_t v = 0; v < nv; ++v)
+        if (mask[v]) {
+            double a = fixed[v] - muf, b = warped[v] - muw;
+            cov += a * b;
+            vf += a * a;
+            vw += b * b;
+        }
+    double D = vf * vw + eps;
+    double rho = cov / sqrt(D);
+    *S = 1.0 - rho;
+    if (g_w)
+        for (int64_t v = 0; v < nv; ++v) {
+            if (!mask[v]) {
+                g_w[v] = 0.0;
+                continue;
+            }
+            /* d rho / d W(v): the mean terms drop out because the centred
+             * values sum to zero over the mask. */
+            double drho = (fixed[v] - muf) / sqrt(D) - cov * vf * (warped[v] - muw) / (D * sqrt(D));
+            g_w[v] = -drho;
+        }
+    return ALREF_OK;
+}
+
+/* LCC (Sec. III-B): NCC with mean and variance taken in a local window.
+ * Readings: a centred box window of odd width w (w^d voxels), zero padding
+ * outside the grid, n = w^d constant (plain convolution with a box of ones);
+ * W is zero where the mask is off (it enters the sums as zero);
+ *   cov = S_FW - S_F S_W / n, var_F = S_FF - S_F^2/n, var_W likewise,
+ *   rho(x) = cov / sqrt(var_F var_W + eps),
+ *   S = 1 - (1/|X_m|) sum_{x in mask} rho(x).
+ * The gradient is exact (Sec. III-B: no approximation): with
+ *   a(x) = dS/dS_W(x), b(x) = dS/dS_WW(x), c(x) = dS/dS_FW(x) (zero off mask),
+ *   dS/dW(y) = sum_{x: y in window(x)} [a(x) + 2 W(y) b(x) + F(y) c(x)],
+ * and the window is symmetric, so the sum runs over the window of y. */
+static double box_sum(int ndim, const int64_t *N, const double *f, int64_t x, int64_t y, int64_t z,
+                      int r)
+{
+    const int64_t X = N[0], Y = N[1], Z = N[2];
+    double s = 0.0;
+    int rz = ndim == 3 ? r : 0;
+    for (int64_t dz = -rz; dz <= rz; ++dz)
+        for (int64_t dy = -r; dy <= r; ++dy)
+            for (int64_t dx = -r; dx <= r; ++dx) {
+                int64_t xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx < 0 || xx >= X || yy < 0 || yy >= Y || zz < 0 || zz >= Z)
+                    continue; /* zero padding */
+                s += f[(zz * Y + yy) * X + xx];
+            }
+    return s;
+}
+
+int alref_lcc(int ndim, const int64_t *N, const double *fixed, const double *warped,
+              const uint8_t *mask, int window, double eps, double *S, double *g_w)
+{
+    if (window < 1 || (window % 2) == 0 || (ndim != 2 && ndim != 3))
+        return ALREF_ERR_ARG;
+    const int64_t X = N[0], Y = N[1], Z = N[2], nv = nvox(N);
+    const int r = window / 2;
+    const double n = ndim == 3 ? (double)window * window * window : (double)window * window;
+    double *w = (double *)malloc(sizeof(double) * nv);
+    double *ff = (double *)malloc(sizeof(double) * nv);
+    double *ww = (double *)malloc(sizeof(double) * nv);
+    double *fw = (double *)malloc(sizeof(double) * nv);
+    double *ca = (double *)malloc(sizeof(double) * nv);
+    double *cb = (double *)malloc(sizeof(double) * nv);
+    double *cc = (double *)malloc(sizeof(double) * nv);
+    if (!w || !ff || !ww || !fw || !ca || !cb || !cc) {
+        free(w), free(ff), free(ww), free(fw), free(ca), free(cb), free(cc);
+        return ALREF_ERR_ARG;
+    }
+    double cnt = 0.0;
+    for (int64_t v = 0; v < nv; ++v) {
+        w[v] = mask[v] ? warped[v] : 0.0;
+        ff[v] = fixed[v] * fixed[v];
+        ww[v] = w[v] * w[v];
+        fw[v] = fixed[v] * w[v];
+        if (mask[v])
+            cnt += 1.0;
+    }
+    double rho_sum = 0.0;
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                const int64_t v = (z * Y + y) * X + x;
+                ca[v] = cb[v] = cc[v] = 0.0;
+                if (!mask[v])
+                    continue;
+                double SF = box_sum(ndim, N, fixed, x, y, z, r);
+                double SW = box_sum(ndim, N, w, x, y, z, r);
+                double SFF = box_sum(ndim, N, ff, x, y, z, r);
+                double SWW = box_sum(ndim, N, ww, x, y, z, r);
+                double SFW = box_sum(ndim, N, fw, x, y, z, r);
+                double cov = SFW - SF * SW / n;
+                double vf = SFF - SF * SF / n;
+                double vw = SWW - SW * SW / n;
+                double D = vf * vw + eps;
+                double sD = sqrt(D);
+                double rho = cov / sD;
+                rho_sum += rho;
+                /* partial derivatives of rho with respect to the three local
+                 * sums that depend on W */
+                double d_sfw = 1.0 / sD;
+                double d_sww = -cov * vf / (2.0 * D * sD);
+                double d_sw = -SF / (n * sD) + cov * vf * SW / (n * D * sD);
+                /* S = 1 - rho_sum / cnt */
+                ca[v] = -d_sw / cnt;
+                cb[v] = -d_sww / cnt;
+                cc[v] = -d_sfw / cnt;
+            }
+    *S = cnt > 0.0 ? 1.0 - rho_sum / cnt : 0.0;
+    if (g_w) {
+        for (int64_t z = 0; z < Z; ++z)
+            for (int64_t y = 0; y < Y; ++y)
+                for (int64_t x = 0; x < X; ++x) {
+                    const int64_t v = (z * Y + y) * X + x;
+                    if (!mask[v] || cnt == 0.0) {
+                        g_w[v] = 0.0;
+                        continue;
+                    }
+                    double A = box_sum(ndim, N, ca, x, y, z, r);
+                    double B = box_sum(ndim, N, cb, x, y, z, r);
+                    double C = box_sum(ndim, N, cc, x, y, z, r);
+                    g_w[v] = A + 2.0 * w[v] * B + fixed[v] * C;
+                }
+    }
+    free(w), free(ff), free(ww), free(fw), free(ca), free(cb), free(cc);
+    return ALREF_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (diffusion_regularizer): R = (1/|X|) sum_x sum_i ||grad u_i(x)||^2.  */
+/* Reading: forward differences with unit spacing; the difference that      */
+/* would leave the grid is dropped (Neumann). g_disp = dR/du, may be NULL.   */
+/* ------------------------------------------------------------------------ */
+int alref_diffusion(int ndim, const int64_t *N, const double *disp, double *R, double *g_disp)
+{
+    const int64_t X = N[0], Y = N[1], Z = N[2], nv = nvox(N);
+    const int64_t stride[3] = {1, X, X * Y};
+    double sum = 0.0;
+    if (g_disp)
+        for (int64_t v = 0; v < ndim * nv; ++v)
+            g_disp[v] = 0.0;
+    for (int i = 0; i < ndim; ++i) {
+        const double *u = disp + i * nv;
+        for (int64_t z = 0; z < Z; ++z)
+            for (int64_t y = 0; y < Y; ++y)
+                for (int64_t x = 0; x < X; ++x) {
+                    const int64_t v = (z * Y + y) * X + x;
+                    const int64_t pos[3] = {x, y, z};
+                    for (int k = 0; k < ndim; ++k) {
+                        if (pos[k] + 1 >= N[k])
+                            continue;
+                        double d = u[v + stride[k]] - u[v];
+                        sum += d * d;
+                        if (g_disp) {
+                            g_disp[i * nv + v + stride[k]] += 2.0 * d / (double)nv;
+                            g_disp[i * nv + v] -= 2.0 * d / (double)nv;
+                        }
+                    }
+                }
+    }
+    *R = sum / (double)nv;
+    return ALREF_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (objective) for one control-point vector, with its exact gradient    */
+/* by the chain rule (Sec. III-A):                                           */
+/*   u = B c; (W, m) = warp(M, u); S = S(W, F); R = R_diff(u); J = S + lam R */
+/*   g_u = m * dS/dW * dM~/dy + lam * dR/du;  dJ/dc = B^T g_u               */
+/* kind: 0 = MSE, 1 = NCC, 2 = LCC. out = {J, S, R, |X_m|}. g_ctrl NULL =    */
+/* value only.                                                               */
+/* ------------------------------------------------------------------------ */
+int alref_objective_grad(int ndim, const int64_t *N, int delta, int kind, int window, double eps,
+                         double lambda, const double *fixed, const double *moving,
+                         const double *ctrl, double *out, double *g_ctrl)
+{
+    int64_t n[3];
+    if (alref_lattice_size(ndim, N, delta, n))
+        return ALREF_ERR_ARG;
+    const int64_t nv = nvox(N);
+    double *u = (double *)malloc(sizeof(double) * ndim * nv);
+    double *w = (double *)malloc(sizeof(double) * nv);
+    double *gy = (double *)malloc(sizeof(double) * ndim * nv);
+    double *gw = (double *)malloc(sizeof(double) * nv);
+    double *gu = (double *)malloc(sizeof(double) * ndim * nv);
+    uint8_t *m = (uint8_t *)malloc(nv);
+    int st = ALREF_ERR_ARG;
+    if (!u || !w || !gy || !gw || !gu || !m)
+        goto done;
+    if ((st = alref_displacement(ndim, N, delta, ctrl, u)))
+        goto done;
+    if ((st = alref_warp(ndim, N, moving, u, w, m, gy)))
+        goto done;
+    double S = 0.0, R = 0.0;
+    if (kind == 0)
+        st = alref_mse(N, fixed, w, m, &S, gw);
+    else if (kind == 1)
+        st = alref_ncc(N, fixed, w, m, eps, &S, gw);
+    else if (kind == 2)
+        st = alref_lcc(ndim, N, fixed, w, m, window, eps, &S, gw);
+    else
+        st = ALREF_ERR_ARG;
+    if (st)
+        goto done;
+    if ((st = alref_diffusion(ndim, N, u, &R, gu)))
+        goto done;
+    double cnt = 0.0;
+    for (int64_t v = 0; v < nv; ++v)
+        cnt += m[v];
+    out[0] = S + lambda * R;
+    out[1] = S;
+    out[2] = R;
+    out[3] = cnt;
+    if (g_ctrl) {
+        for (int i = 0; i < ndim; ++i)
+            for (int64_t v = 0; v < nv; ++v)
+                gu[i * nv + v] = (m[v] ? gw[v] * gy[i * nv + v] : 0.0) + lambda * gu[i * nv + v];
+        st = alref_displacement_adjoint(ndim, N, delta, gu, g_ctrl);
+    }
+done:
+    free(u), free(w), free(gy), free(gw), free(gu), free(m);
+    return st;
+}
