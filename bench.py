@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the fused forward+adjoint objective on GB300.
+
+One step = one evaluation of J = S_LCC + lambda*R_diff and dJ/dc
+(al_objective_grad) on the 256x256x160 CT-like pair: local NCC with a 7^3
+window, cubic B-spline spacing 6 (46x46x30 control points), lambda = 0.1,
+control coefficients ~ N(0, 3^2) voxels. Inputs are seeded synthetic volumes
+(the paper's CT data is not available) already resident in HBM; the L2 cache
+is flushed by a 256 MiB write before every timed step.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint objective evals/s at 256×256×160; HBM GB/s vs peak; time-to-MSE"
+UNIT = "evals/s"
+SHAPE = (160, 256, 256)
+SPACING = 6
+LAMBDA = 0.1
+WINDOW = 7
+CTRL_SIGMA = 3.0
+WORKLOAD = ("3D 256x256x160 fp32 CT-like pair (ellipsoids in [-1000,1500] HU + N(0,20^2) noise), "
+            "LCC 7^3 + 0.1 diffusion, cubic B-spline spacing 6 (46x46x30 points), "
+            "c ~ N(0, 3^2) voxels; one fused forward+adjoint evaluation per step")
+FLUSH_BYTES = 256 << 20
+
+# Algorithmic HBM bytes per voxel of each kernel of the fused LCC path (the
+# minimum each must move): k_fused_fwd reads M and writes W + mask; k_lcc_tiles
+# reads F, W, mask and writes dS/dW; k_fused_gw reads M and dS/dW; the
+# point-wise fused kernels read F and M. Per-launch control-point traffic is
+# added separately (coefficients in, partial sums out).
+KERNEL_BYTES_PER_VOXEL = {
+    "k_fused_fwd": 9.0, "k_lcc_tiles": 13.0, "k_fused_gw": 8.0,
+    "k_fused_mse": 8.0, "k_fused_ncc": 8.0,
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--sim", choices=["lcc", "mse", "ncc"], default="lcc")
+    p.add_argument("--shape", type=str, default=None, help="Z,Y,X (default 160,256,256)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-budget", type=float, default=20.0,
+                   help="seconds of oracle work for the cpu_baseline sample")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload(shape):
+    from paper_1806_09907_gb300 import synth
+    F, M = synth.ct_pair(shape)
+    nd = len(shape)
+    lat = tuple((s - 1) // SPACING + 4 for s in shape)
+    c = synth.random_ctrl(lat, nd, CTRL_SIGMA, synth.FIELD_SEED)
+    return F, M, c
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(F, M, c, sim, budget_s):
+    """Time the oracle (single-threaded, as it stands) on a z-slab of the
+    workload whose depth is chosen so one evaluation takes about budget_s.
+    Returns (evals/s of the full workload scaled by voxel count, seconds,
+    slab depth)."""
+    import oracle
+    kind = {"mse": oracle.MSE, "ncc": oracle.NCC, "lcc": oracle.LCC}[sim]
+    Z = F.shape[0]
+
+    def run(depth):
+        sh = (depth,) + F.shape[1:]
+        nz = (depth - 1) // SPACING + 4
+        t0 = time.perf_counter()
+        oracle.objective_grad(kind, F[:depth], M[:depth], c[:, :nz], SPACING, LAMBDA, 1e-5, WINDOW)
+        return time.perf_counter() - t0
+
+    probe = min(4, Z)
+    t_probe = run(probe)
+    depth = int(max(2, min(Z, budget_s / max(t_probe / probe, 1e-9))))
+    t = run(depth) if depth != probe else t_probe
+    return (depth / Z) / t, t, depth
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            return d, "measured"
+        except (OSError, ValueError):
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_reference(args, shape):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    F, M, c = workload(shape)
+    steps, warmup = max(1, args.steps), max(0, args.warmup)
+    budget = max(1.0, 150.0 / (steps + warmup))  # whole run within a few minutes
+    vals, times, depth = [], [], None
+    for i in range(warmup + steps):
+        v, t, depth = oracle_sample(F, M, c, args.sim, budget)
+        if i >= warmup:
+            vals.append(v)
+            times.append(t * shape[0] / depth)  # seconds per full-workload evaluation
+    total = sum(times)
+    value = steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": 1000.0 * total / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape_zyx": list(shape), "spacing": SPACING,
+                   "similarity": f"{args.sim}{WINDOW if args.sim == 'lcc' else ''}",
+                   "lambda": LAMBDA, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "cpu": cpu_model(),
+                         "sample": f"one FP64 oracle forward+adjoint per step on a "
+                                   f"{shape[2]}x{shape[1]}x{depth} z-slab, time scaled by "
+                                   f"voxel count to the full volume"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    shape = tuple(int(s) for s in args.shape.split(",")) if args.shape else SHAPE
+    if args.impl == "reference":
+        return run_reference(args, shape)
+
+    import torch
+    from paper_1806_09907_gb300 import airgb
+    from paper_1806_09907_gb300 import build as airgb_build
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    if rank == 0:
+        airgb_build.build()
+    if pg:
+        pg.barrier()
+    airgb.load()
+
+    F, M, c = workload(shape)
+    Fd, Md, cd = (torch.from_numpy(a).to(dev) for a in (F, M, c))
+    obj = airgb.Objective(shape, SPACING, args.sim, LAMBDA, 1e-5, WINDOW, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    warmup = max(3, args.warmup)
+    steps = max(1, args.steps)
+    for _ in range(warmup):
+        flush.zero_()
+        obj(Fd, Md, cd)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    clocks = ClockSampler(torch.cuda.get_device_properties(dev).index
+                          if hasattr(torch.cuda.get_device_properties(dev), "index") else local_rank)
+    airgb.profile_reset()
+    airgb.profile_enable(True)
+    clocks.start()
+    barrier()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        obj(Fd, Md, cd)
+        ends[k].record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    airgb.profile_enable(False)
+    kernels = airgb.profile_collect()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * steps / (total_ms / 1000.0)
+
+    # ---- end to end through the public API with host buffers
+    Fh, Mh, ch = (torch.from_numpy(a).pin_memory() for a in (F, M, c))
+    vh = torch.empty(4, dtype=torch.float64).pin_memory()
+    gh = torch.empty(tuple(cd.shape), dtype=torch.float32).pin_memory()
+    Fe, Me, ce = torch.empty_like(Fd), torch.empty_like(Md), torch.empty_like(cd)
+    e2e_steps = max(3, min(steps, 20))
+    for _ in range(2):
+        Fe.copy_(Fh, non_blocking=True)
+        Me.copy_(Mh, non_blocking=True)
+        ce.copy_(ch, non_blocking=True)
+        obj(Fe, Me, ce)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Fe.copy_(Fh, non_blocking=True)
+        Me.copy_(Mh, non_blocking=True)
+        ce.copy_(ch, non_blocking=True)
+        v, g = obj(Fe, Me, ce)
+        vh.copy_(v, non_blocking=True)
+        gh.copy_(g, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * e2e_steps / (e2e_ms / 1000.0)
+    h2d = F.nbytes + M.nbytes + c.nbytes
+    d2h = vh.numel() * 8 + gh.numel() * 4
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel
+    nv = int(np.prod(shape))
+    dom = max(kernels.items(), key=lambda kv: kv[1][0]) if kernels else None
+    peaks, peak_src = measured_peaks()
+    roof = None
+    if dom:
+        name, (ms_tot, launches) = dom
+        per_launch_ms = ms_tot / max(launches, 1)
+        bpv = KERNEL_BYTES_PER_VOXEL.get(name)
+        if bpv is not None:
+            algo_bytes = bpv * nv + (c.nbytes if name.startswith("k_fused") else 0)
+            achieved = algo_bytes / (per_launch_ms / 1000.0) / 1e9
+            peak = float(peaks.get("hbm_gbs", 6800.0))
+            roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": peak_src, "algorithmic_bytes": algo_bytes,
+                    "launch_ms": per_launch_ms}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, t, depth = oracle_sample(F, M, c, args.sim, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
+               "sample": f"one FP64 oracle forward+adjoint on a {shape[2]}x{shape[1]}x{depth} "
+                         f"z-slab of the workload ({t:.1f} s), scaled by voxel count"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape_zyx": list(shape), "spacing": SPACING,
+                   "similarity": f"{args.sim}{WINDOW if args.sim == 'lcc' else ''}",
+                   "lambda": LAMBDA, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed by a 256 MiB write before every timed step",
+                   "timing": "per-step CUDA events on the launching stream"},
+        "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
+                    "max": max(step_ms)},
+        "kernels": {k: {"total_ms": v[0], "launches": v[1], "avg_us": 1000.0 * v[0] / max(v[1], 1)}
+                    for k, v in kernels.items()},
+        "gpu_launches": int(sum(v[1] for v in kernels.values())),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+        "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

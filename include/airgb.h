@@ -1,0 +1,214 @@
+/*
+ * airgb.h - C ABI of libairgb.so: the regularised B-spline registration
+ * objective of AIRLab (arXiv 1806.09907) and its exact gradient with respect
+ * to the control points, as hand-written CUDA kernels for sm_103a (GB300).
+ *
+ * The objective (Sec. II-A, Eq. objective):
+ *     J(c) = S(I_M o (x + u_c), I_F) + lambda * R_diff(u_c)
+ * with u_c the cubic B-spline expansion of the control coefficients c
+ * (Eq. kernel_basis, Sec. III-C), the backward warp with linear
+ * interpolation and the out-of-domain mask (Sec. III-C, Image Warping), the
+ * MSE / NCC / LCC similarity (Eq. mse, Sec. III-B) and the diffusion
+ * regulariser (Eq. diffusion_regularizer, Sec. III-F).
+ *
+ * Conventions shared by every call
+ *  - Grid: ndim 2 or 3, sizes X, Y, Z (Z = 1 in 2D, every active size >= 2).
+ *    Volumes are fp32, x fastest: element (x,y,z) at (z*Y + y)*X + x.
+ *  - Vector fields (displacements and their gradients) are ndim component
+ *    planes, component 0 = x: u[i*X*Y*Z + voxel]. Voxel units.
+ *  - Control lattice with integer spacing delta: n_k = (N_k - 1)/delta + 4
+ *    points per active axis (n_z = 1 in 2D), point j at voxel coordinate
+ *    (j - 1)*delta; coefficients are ndim planes c[i][jz][jy][jx], voxel units.
+ *    The kernel is k_B1D(r/delta) per axis (tensor product).
+ *  - Warp: y = x + u(x); a voxel is outside the mask when some y_k < 0 or
+ *    y_k > N_k - 1 (or y_k is not finite); outside voxels have W = 0.
+ *    Linear interpolation uses the floor cell clamped to [0, N_k - 2].
+ *  - Similarities run over the masked voxels: MSE is the mean over them, NCC
+ *    is 1 - Pearson correlation over them, LCC is 1 - the mean over them of
+ *    the correlation in a centred box window (zero padding, fixed count
+ *    window^ndim). eps is added to var_F*var_W under the square root.
+ *  - R_diff uses forward differences with the out-of-grid difference dropped,
+ *    divided by the number of voxels.
+ *
+ * Memory and streams
+ *  - Every array pointer is DEVICE memory owned by the caller, contiguous,
+ *    16-byte aligned (AL_ERR_ALIGN otherwise). Results are written to device
+ *    memory; nothing is copied to the host and no call synchronises, except
+ *    al_get_device_error. Calls are asynchronous on `stream` (a cudaStream_t;
+ *    NULL = the legacy default stream).
+ *  - The library allocates no device memory. Calls that need scratch take a
+ *    caller-owned workspace of at least the size the matching
+ *    *_workspace_bytes function returns (AL_ERR_WORKSPACE otherwise); its
+ *    contents on entry do not matter. Two calls that share a workspace or an
+ *    output must be ordered on the GPU by the caller.
+ *  - Gradients are overwritten, not accumulated, unless a call says so. A NULL
+ *    gradient pointer means value only, where allowed.
+ *  - Results are deterministic: sums use fixed-order reductions, no atomics.
+ *
+ * Errors
+ *  - Argument, shape, alignment and workspace errors are detected on the host
+ *    before anything is launched; the call returns that status and leaves
+ *    every output untouched.
+ *  - A failed kernel launch returns AL_ERR_CUDA (the CUDA error is left for
+ *    the caller to read with cudaGetLastError).
+ *  - Errors found by the kernels themselves are recorded in a per-device
+ *    error word that al_get_device_error reads and clears.
+ *  - No call aborts, traps or throws.
+ */
+#ifndef AIRGB_H
+#define AIRGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AL_OK = 0,
+    AL_ERR_INVALID_ARG = 1, /* NULL pointer, bad enum, bad spacing/window/eps */
+    AL_ERR_SHAPE = 2,       /* grid or lattice sizes inconsistent or unsupported */
+    AL_ERR_ALIGN = 3,       /* a pointer is not 16-byte aligned */
+    AL_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
+    AL_ERR_BOUNDS = 5,      /* a kernel saw an index out of range (checked builds) */
+    AL_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+    AL_ERR_UNSUPPORTED = 7, /* valid but not supported by this build */
+    AL_ERR_WORKSPACE = 8    /* workspace missing or too small */
+} al_status;
+
+typedef enum { AL_SIM_MSE = 0, AL_SIM_NCC = 1, AL_SIM_LCC = 2 } al_sim_kind;
+
+/* cudaStream_t, passed as an opaque pointer so this header needs no CUDA. */
+typedef void *al_stream;
+
+/* Image grid (Sec. II-A: the regular point set X). */
+typedef struct {
+    int32_t ndim;    /* 2 or 3 */
+    int32_t reserved;
+    int64_t size[3]; /* X, Y, Z; Z = 1 when ndim = 2 */
+} al_grid;
+
+/* Cubic B-spline transformation on a control lattice (Sec. III-C). */
+typedef struct {
+    al_grid grid;
+    int32_t spacing; /* delta, control spacing in voxels, 1..32 */
+    int32_t reserved;
+    int64_t n[3];    /* lattice size nx, ny, nz; filled by al_bspline_init */
+} al_bspline;
+
+/* Similarity measure (Sec. III-B). */
+typedef struct {
+    int32_t kind;       /* al_sim_kind */
+    int32_t lcc_window; /* odd window width for LCC, 1..15 (default 7) */
+    double eps;         /* added to var_F*var_W, >= 0 (default 1e-5) */
+} al_sim_params;
+
+/* One registration objective (Eq. objective): transformation, similarity
+ * and the weight lambda of the diffusion regulariser. */
+typedef struct {
+    al_bspline bs;
+    al_sim_params sim;
+    double lambda;
+} al_problem;
+
+/* Text for a status code (static storage). */
+const char *al_status_string(al_status status);
+
+/* Fill *bs for grid *g and spacing delta: checks the grid (ndim 2/3, sizes
+ * >= 2 on active axes, Z = 1 in 2D, at most 2^31 voxels) and sets
+ * bs->n = (N - 1)/delta + 4 per active axis (Sec. III-C; lattice placement
+ * is a reading, the paper gives none). Host only, launches nothing. */
+al_status al_bspline_init(al_bspline *bs, const al_grid *g, int32_t spacing);
+
+/* A1. Displacement u = sum_j c_j k(x_j, x) (Eq. kernel_basis, Sec. III-C:
+ * the control points are up-sampled with the B-spline as interpolation
+ * kernel). ctrl: ndim * nz*ny*nx floats; disp: ndim * Z*Y*X floats
+ * (overwritten). */
+al_status al_displacement(const al_bspline *bs, const float *ctrl, float *disp, al_stream stream);
+
+/* A6. Adjoint of al_displacement (the transposed up-sampling):
+ * grad_ctrl[i,j] = sum_x k(x_j, x) grad_disp[i](x), computed as a gather per
+ * control point (fixed order, no atomics). grad_ctrl is overwritten.
+ * Workspace: al_displacement_adjoint_workspace_bytes(bs). */
+al_status al_displacement_adjoint(const al_bspline *bs, const float *grad_disp, float *grad_ctrl,
+                                  void *workspace, size_t workspace_bytes, al_stream stream);
+size_t al_displacement_adjoint_workspace_bytes(const al_bspline *bs);
+
+/* A2. Backward warp (Sec. III-C, Image Warping): warped = m * M~(x + u),
+ * mask = m (1 inside, 0 outside), both overwritten. moving, warped: Z*Y*X
+ * floats; disp: ndim planes; mask: Z*Y*X bytes. */
+al_status al_warp(const al_grid *g, const float *moving, const float *disp, float *warped,
+                  uint8_t *mask, al_stream stream);
+
+/* A5. Adjoint of the warp with respect to the displacement (the exact
+ * gradient, Sec. III-A): grad_disp[k](x) = mask(x) * grad_warped(x) *
+ * dM~/dy_k(x + u(x)), the derivative of the linear interpolant inside its
+ * (clamped) floor cell. accumulate = 0 overwrites grad_disp, 1 adds to it. */
+al_status al_warp_adjoint(const al_grid *g, const float *moving, const float *disp,
+                          const uint8_t *mask, const float *grad_warped, float *grad_disp,
+                          int32_t accumulate, al_stream stream);
+
+/* A3. Similarity S(W, F) over the mask (Eq. mse; NCC and LCC of Sec. III-B)
+ * and its gradient dS/dW (grad_warped, nullable, overwritten; zero off the
+ * mask). value_dev: 2 doubles on the device, {S, number of masked voxels}.
+ * Workspace: al_similarity_workspace_bytes(g, p). */
+al_status al_similarity(const al_grid *g, const al_sim_params *p, const float *fixed,
+                        const float *warped, const uint8_t *mask, double *value_dev,
+                        float *grad_warped, void *workspace, size_t workspace_bytes,
+                        al_stream stream);
+size_t al_similarity_workspace_bytes(const al_grid *g, const al_sim_params *p);
+
+/* A4. Diffusion regulariser R (Eq. diffusion_regularizer) of a displacement
+ * field and weight * dR/du (grad_disp, nullable, overwritten).
+ * value_dev: 1 double on the device, R (unweighted).
+ * Workspace: al_regulariser_workspace_bytes(g). */
+al_status al_regulariser(const al_grid *g, const float *disp, double weight, double *value_dev,
+                         float *grad_disp, void *workspace, size_t workspace_bytes,
+                         al_stream stream);
+size_t al_regulariser_workspace_bytes(const al_grid *g);
+
+/* A7. One evaluation of J = S + lambda R (Eq. objective) and dJ/dc, fused:
+ * the displacement, warped image and per-voxel gradients stay on chip (LCC
+ * keeps the warped image and its gradient in the workspace); R and dR/dc are
+ * evaluated on the control lattice in Gram form, which equals the voxel sum.
+ * value_dev: 4 doubles on the device, {J, S, R, number of masked voxels}.
+ * grad_ctrl: ndim * nz*ny*nx floats, nullable (value only), overwritten.
+ * Workspace: al_objective_workspace_bytes(pr). */
+al_status al_objective_grad(const al_problem *pr, const float *fixed, const float *moving,
+                            const float *ctrl, double *value_dev, float *grad_ctrl,
+                            void *workspace, size_t workspace_bytes, al_stream stream);
+size_t al_objective_workspace_bytes(const al_problem *pr);
+
+/* The same evaluation as the composition of the step calls above
+ * (A1 -> A2 -> A3, A4 -> A5 -> A6), with every intermediate field in the
+ * workspace. Same arguments and results as al_objective_grad.
+ * Workspace: al_objective_unfused_workspace_bytes(pr). */
+al_status al_objective_grad_unfused(const al_problem *pr, const float *fixed, const float *moving,
+                                    const float *ctrl, double *value_dev, float *grad_ctrl,
+                                    void *workspace, size_t workspace_bytes, al_stream stream);
+size_t al_objective_unfused_workspace_bytes(const al_problem *pr);
+
+/* Synchronise `stream`, then read and clear the current device's kernel
+ * error word: AL_OK, AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the
+ * synchronisation itself failed). */
+al_status al_get_device_error(al_stream stream);
+
+/* Instrumentation (not part of the method). When enabled, every kernel the
+ * library launches is bracketed by two CUDA events recorded on the
+ * launching stream. al_profile_collect synchronises on the recorded events,
+ * adds their elapsed times to per-kernel totals and reports up to
+ * max_kernels totals: total_ms[i], launches[i], and the kernel names as
+ * newline-separated text in `names` (truncated to names_bytes). Returns the
+ * number of distinct kernels seen. Host only; not thread-safe against
+ * concurrent launches on other threads while enabled. */
+al_status al_profile_enable(int32_t on);
+int32_t al_profile_collect(char *names, size_t names_bytes, double *total_ms, int64_t *launches,
+                           int32_t max_kernels);
+al_status al_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIRGB_H */

@@ -103,7 +103,7 @@ static void axis_range(int active, int64_t xk, int delta, int64_t nk, int64_t *j
         return;
     }
     int64_t q = xk / delta;
-    int64_t a = q - 2, b = q + 5;
+    int64_t a = q - 1, b = q + 4;
     if (a < 0)
         a = 0;
     if (b > nk - 1)
@@ -130,14 +130,20 @@ int alref_displacement(int ndim, const int64_t *N, int delta, const double *ctrl
                 axis_range(1, x, delta, n[0], &jx0, &jx1);
                 axis_range(1, y, delta, n[1], &jy0, &jy1);
                 axis_range(ndim == 3, z, delta, n[2], &jz0, &jz1);
+                /* the kernel is a tensor product: k = kx(jx) * ky(jy) * kz(jz) */
+                double kx[8], ky[8], kz[8];
+                for (int64_t j = jx0; j <= jx1; ++j)
+                    kx[j - jx0] = axis_weight(1, x, j, delta);
+                for (int64_t j = jy0; j <= jy1; ++j)
+                    ky[j - jy0] = axis_weight(1, y, j, delta);
+                for (int64_t j = jz0; j <= jz1; ++j)
+                    kz[j - jz0] = axis_weight(ndim == 3, z, j, delta);
                 for (int i = 0; i < ndim; ++i) {
                     double acc = 0.0;
                     for (int64_t jz = jz0; jz <= jz1; ++jz)
                         for (int64_t jy = jy0; jy <= jy1; ++jy)
                             for (int64_t jx = jx0; jx <= jx1; ++jx) {
-                                double k = axis_weight(1, x, jx, delta) *
-                                           axis_weight(1, y, jy, delta) *
-                                           axis_weight(ndim == 3, z, jz, delta);
+                                double k = kx[jx - jx0] * ky[jy - jy0] * kz[jz - jz0];
                                 acc += ctrl[i * nc + (jz * n[1] + jy) * n[0] + jx] * k;
                             }
                     disp[i * nv + (z * Y + y) * X + x] = acc;
@@ -165,12 +171,17 @@ int alref_displacement_adjoint(int ndim, const int64_t *N, int delta, const doub
                 axis_range(1, x, delta, n[0], &jx0, &jx1);
                 axis_range(1, y, delta, n[1], &jy0, &jy1);
                 axis_range(ndim == 3, z, delta, n[2], &jz0, &jz1);
+                double kx[8], ky[8], kz[8];
+                for (int64_t j = jx0; j <= jx1; ++j)
+                    kx[j - jx0] = axis_weight(1, x, j, delta);
+                for (int64_t j = jy0; j <= jy1; ++j)
+                    ky[j - jy0] = axis_weight(1, y, j, delta);
+                for (int64_t j = jz0; j <= jz1; ++j)
+                    kz[j - jz0] = axis_weight(ndim == 3, z, j, delta);
                 for (int64_t jz = jz0; jz <= jz1; ++jz)
                     for (int64_t jy = jy0; jy <= jy1; ++jy)
                         for (int64_t jx = jx0; jx <= jx1; ++jx) {
-                            double k = axis_weight(1, x, jx, delta) *
-                                       axis_weight(1, y, jy, delta) *
-                                       axis_weight(ndim == 3, z, jz, delta);
+                            double k = kx[jx - jx0] * ky[jy - jy0] * kz[jz - jz0];
                             if (k == 0.0)
                                 continue;
                             for (int i = 0; i < ndim; ++i)

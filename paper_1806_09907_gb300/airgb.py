@@ -1,0 +1,349 @@
+"""ctypes binding of libairgb.so (include/airgb.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library. PyTorch supplies device memory (tensors) and the
+current CUDA stream. The library must have been built (``build()`` in
+``__graft_entry__`` or ``python -m paper_1806_09907_gb300.build``); loading
+fails loudly otherwise, and every call raises ``AirgbError`` on a non-zero
+status.
+
+Layouts (see the header): volumes are float32 tensors shaped (Z, Y, X) or
+(Y, X); vector fields and control coefficients are (d, Z, Y, X) /
+(d, nz, ny, nx) with component 0 = x.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libairgb.so")
+
+AL_SIM_MSE, AL_SIM_NCC, AL_SIM_LCC = 0, 1, 2
+SIM_KINDS = {"mse": AL_SIM_MSE, "ncc": AL_SIM_NCC, "lcc": AL_SIM_LCC}
+
+# Entry points declared in include/airgb.h.
+EXPORTS = (
+    "al_status_string", "al_bspline_init", "al_displacement", "al_displacement_adjoint",
+    "al_displacement_adjoint_workspace_bytes", "al_warp", "al_warp_adjoint", "al_similarity",
+    "al_similarity_workspace_bytes", "al_regulariser", "al_regulariser_workspace_bytes",
+    "al_objective_grad", "al_objective_workspace_bytes", "al_objective_grad_unfused",
+    "al_objective_unfused_workspace_bytes", "al_get_device_error", "al_profile_enable",
+    "al_profile_collect", "al_profile_reset",
+)
+
+
+class AirgbError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} failed: status {status} ({status_string(status)})")
+
+
+class al_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("size", ctypes.c_int64 * 3)]
+
+
+class al_bspline(ctypes.Structure):
+    _fields_ = [("grid", al_grid), ("spacing", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 3)]
+
+
+class al_sim_params(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("lcc_window", ctypes.c_int32),
+                ("eps", ctypes.c_double)]
+
+
+class al_problem(ctypes.Structure):
+    _fields_ = [("bs", al_bspline), ("sim", al_sim_params), ("lam", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libairgb.so (once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libairgb.so not found at {LIB_PATH}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, SZ, VP = ctypes.POINTER, ctypes.c_int32, ctypes.c_size_t, ctypes.c_void_p
+    D = ctypes.c_double
+    sig = {
+        "al_status_string": ([I32], ctypes.c_char_p),
+        "al_bspline_init": ([P(al_bspline), P(al_grid), I32], I32),
+        "al_displacement": ([P(al_bspline), VP, VP, VP], I32),
+        "al_displacement_adjoint": ([P(al_bspline), VP, VP, VP, SZ, VP], I32),
+        "al_displacement_adjoint_workspace_bytes": ([P(al_bspline)], SZ),
+        "al_warp": ([P(al_grid), VP, VP, VP, VP, VP], I32),
+        "al_warp_adjoint": ([P(al_grid), VP, VP, VP, VP, VP, I32, VP], I32),
+        "al_similarity": ([P(al_grid), P(al_sim_params), VP, VP, VP, VP, VP, VP, SZ, VP], I32),
+        "al_similarity_workspace_bytes": ([P(al_grid), P(al_sim_params)], SZ),
+        "al_regulariser": ([P(al_grid), VP, D, VP, VP, VP, SZ, VP], I32),
+        "al_regulariser_workspace_bytes": ([P(al_grid)], SZ),
+        "al_objective_grad": ([P(al_problem), VP, VP, VP, VP, VP, VP, SZ, VP], I32),
+        "al_objective_workspace_bytes": ([P(al_problem)], SZ),
+        "al_objective_grad_unfused": ([P(al_problem), VP, VP, VP, VP, VP, VP, SZ, VP], I32),
+        "al_objective_unfused_workspace_bytes": ([P(al_problem)], SZ),
+        "al_get_device_error": ([VP], I32),
+        "al_profile_enable": ([I32], I32),
+        "al_profile_collect": ([ctypes.c_char_p, SZ, P(D), P(ctypes.c_int64), I32], I32),
+        "al_profile_reset": ([], I32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().al_status_string(int(status)).decode()
+
+
+def _call(name, *args):
+    st = getattr(load(), name)(*args)
+    if st != 0:
+        raise AirgbError(name, st)
+
+
+# ---------------------------------------------------------------- helpers --
+
+def make_grid(shape) -> al_grid:
+    g = al_grid()
+    if len(shape) == 3:
+        g.ndim, g.size[0], g.size[1], g.size[2] = 3, shape[2], shape[1], shape[0]
+    elif len(shape) == 2:
+        g.ndim, g.size[0], g.size[1], g.size[2] = 2, shape[1], shape[0], 1
+    else:
+        raise ValueError(f"volume shape must be (Z,Y,X) or (Y,X), got {tuple(shape)}")
+    return g
+
+
+def bspline_init(shape, spacing: int) -> al_bspline:
+    bs = al_bspline()
+    _call("al_bspline_init", ctypes.byref(bs), ctypes.byref(make_grid(shape)), int(spacing))
+    return bs
+
+
+def lattice_shape(shape, spacing: int):
+    """Control-lattice shape in volume order: (nz, ny, nx) or (ny, nx)."""
+    bs = bspline_init(shape, spacing)
+    return (bs.n[2], bs.n[1], bs.n[0]) if len(shape) == 3 else (bs.n[1], bs.n[0])
+
+
+def make_problem(shape, spacing: int, sim: str = "mse", lam: float = 0.1, eps: float = 1e-5,
+                 window: int = 7) -> al_problem:
+    pr = al_problem()
+    pr.bs = bspline_init(shape, spacing)
+    pr.sim.kind = SIM_KINDS[sim] if isinstance(sim, str) else int(sim)
+    pr.sim.lcc_window = int(window)
+    pr.sim.eps = float(eps)
+    pr.lam = float(lam)
+    return pr
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensors must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, shape, what):
+    if t.dtype != torch.float32 or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: expected float32 {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes, device, ws=None):
+    if ws is not None:
+        if ws.numel() * ws.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return ws
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _ndim_of(shape):
+    return len(shape)
+
+
+# ------------------------------------------------------------ entry points --
+
+def al_displacement(shape, spacing, ctrl, disp=None, stream=None):
+    """A1: B-spline expansion u = sum_j c_j k(x_j, x)."""
+    bs = bspline_init(shape, spacing)
+    d = _ndim_of(shape)
+    _f32(ctrl, (d,) + lattice_shape(shape, spacing), "ctrl")
+    if disp is None:
+        disp = torch.empty((d,) + tuple(shape), dtype=torch.float32, device=ctrl.device)
+    _f32(disp, (d,) + tuple(shape), "disp")
+    _call("al_displacement", ctypes.byref(bs), _ptr(ctrl), _ptr(disp), _stream(stream))
+    return disp
+
+
+def al_displacement_adjoint(shape, spacing, grad_disp, grad_ctrl=None, workspace=None,
+                            stream=None):
+    """A6: transpose of the expansion, g_c = B^T g_u."""
+    bs = bspline_init(shape, spacing)
+    d = _ndim_of(shape)
+    _f32(grad_disp, (d,) + tuple(shape), "grad_disp")
+    if grad_ctrl is None:
+        grad_ctrl = torch.empty((d,) + lattice_shape(shape, spacing), dtype=torch.float32,
+                                device=grad_disp.device)
+    nb = load().al_displacement_adjoint_workspace_bytes(ctypes.byref(bs))
+    ws = _workspace(nb, grad_disp.device, workspace)
+    _call("al_displacement_adjoint", ctypes.byref(bs), _ptr(grad_disp), _ptr(grad_ctrl),
+          _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    return grad_ctrl
+
+
+def al_warp(moving, disp, warped=None, mask=None, stream=None):
+    """A2: backward warp with mask. Returns (warped, mask uint8)."""
+    shape = tuple(moving.shape)
+    g = make_grid(shape)
+    _f32(moving, shape, "moving")
+    _f32(disp, (len(shape),) + shape, "disp")
+    if warped is None:
+        warped = torch.empty(shape, dtype=torch.float32, device=moving.device)
+    if mask is None:
+        mask = torch.empty(shape, dtype=torch.uint8, device=moving.device)
+    _call("al_warp", ctypes.byref(g), _ptr(moving), _ptr(disp), _ptr(warped), _ptr(mask),
+          _stream(stream))
+    return warped, mask
+
+
+def al_warp_adjoint(moving, disp, mask, grad_warped, grad_disp=None, accumulate=False,
+                    stream=None):
+    """A5: grad_disp = mask * grad_warped * dM~/dy (optionally accumulated)."""
+    shape = tuple(moving.shape)
+    g = make_grid(shape)
+    if grad_disp is None:
+        if accumulate:
+            raise ValueError("accumulate needs grad_disp")
+        grad_disp = torch.empty((len(shape),) + shape, dtype=torch.float32, device=moving.device)
+    _call("al_warp_adjoint", ctypes.byref(g), _ptr(moving), _ptr(disp), _ptr(mask),
+          _ptr(grad_warped), _ptr(grad_disp), int(bool(accumulate)), _stream(stream))
+    return grad_disp
+
+
+def al_similarity(sim, fixed, warped, mask, eps=1e-5, window=7, grad=True, workspace=None,
+                  stream=None):
+    """A3: similarity value {S, n_mask} (float64 device tensor) and dS/dW."""
+    shape = tuple(fixed.shape)
+    g = make_grid(shape)
+    p = al_sim_params()
+    p.kind = SIM_KINDS[sim] if isinstance(sim, str) else int(sim)
+    p.lcc_window = int(window)
+    p.eps = float(eps)
+    value = torch.empty(2, dtype=torch.float64, device=fixed.device)
+    gw = torch.empty(shape, dtype=torch.float32, device=fixed.device) if grad else None
+    nb = load().al_similarity_workspace_bytes(ctypes.byref(g), ctypes.byref(p))
+    if nb == 0:
+        raise AirgbError("al_similarity_workspace_bytes", 1)
+    ws = _workspace(nb, fixed.device, workspace)
+    _call("al_similarity", ctypes.byref(g), ctypes.byref(p), _ptr(fixed), _ptr(warped),
+          _ptr(mask), _ptr(value), _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+          _stream(stream))
+    return value, gw
+
+
+def al_regulariser(disp, weight=1.0, grad=True, workspace=None, stream=None):
+    """A4: R_diff (float64 device tensor of 1) and weight * dR/du."""
+    shape = tuple(disp.shape[1:])
+    g = make_grid(shape)
+    value = torch.empty(1, dtype=torch.float64, device=disp.device)
+    gu = torch.empty_like(disp) if grad else None
+    nb = load().al_regulariser_workspace_bytes(ctypes.byref(g))
+    ws = _workspace(nb, disp.device, workspace)
+    _call("al_regulariser", ctypes.byref(g), _ptr(disp), ctypes.c_double(weight), _ptr(value),
+          _ptr(gu), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    return value, gu
+
+
+def objective_workspace_bytes(problem: al_problem, fused=True) -> int:
+    fn = "al_objective_workspace_bytes" if fused else "al_objective_unfused_workspace_bytes"
+    n = getattr(load(), fn)(ctypes.byref(problem))
+    if n == 0:
+        raise AirgbError(fn, 1)
+    return int(n)
+
+
+def al_objective_grad(problem: al_problem, fixed, moving, ctrl, value=None, grad_ctrl=None,
+                      workspace=None, want_grad=True, fused=True, stream=None):
+    """A7: value {J, S, R, n_mask} (float64 device tensor) and dJ/dc."""
+    shape = tuple(fixed.shape)
+    d = len(shape)
+    _f32(fixed, shape, "fixed")
+    _f32(moving, shape, "moving")
+    lat = (problem.bs.n[2], problem.bs.n[1], problem.bs.n[0]) if d == 3 else \
+        (problem.bs.n[1], problem.bs.n[0])
+    _f32(ctrl, (d,) + lat, "ctrl")
+    if value is None:
+        value = torch.empty(4, dtype=torch.float64, device=fixed.device)
+    if want_grad and grad_ctrl is None:
+        grad_ctrl = torch.empty_like(ctrl)
+    ws = _workspace(objective_workspace_bytes(problem, fused), fixed.device, workspace)
+    fn = "al_objective_grad" if fused else "al_objective_grad_unfused"
+    _call(fn, ctypes.byref(problem), _ptr(fixed), _ptr(moving), _ptr(ctrl), _ptr(value),
+          _ptr(grad_ctrl if want_grad else None), _ptr(ws), ctypes.c_size_t(ws.numel()),
+          _stream(stream))
+    return value, (grad_ctrl if want_grad else None)
+
+
+def al_get_device_error(stream=None) -> int:
+    return int(load().al_get_device_error(_stream(stream)))
+
+
+def profile_enable(on: bool = True):
+    _call("al_profile_enable", int(bool(on)))
+
+
+def profile_reset():
+    _call("al_profile_reset")
+
+
+def profile_collect(max_kernels: int = 64):
+    """Per-kernel totals since the last reset: {name: (total_ms, launches)}."""
+    buf = ctypes.create_string_buffer(8192)
+    ms = (ctypes.c_double * max_kernels)()
+    cnt = (ctypes.c_int64 * max_kernels)()
+    n = load().al_profile_collect(buf, ctypes.c_size_t(8192), ms, cnt, max_kernels)
+    names = buf.value.decode().split("\n")[:min(n, max_kernels)]
+    return {names[i]: (ms[i], int(cnt[i])) for i in range(len(names))}
+
+
+class Objective:
+    """Preallocated evaluator of J and dJ/dc for one problem: holds the
+    workspace and output buffers so repeated calls allocate nothing."""
+
+    def __init__(self, shape, spacing, sim="mse", lam=0.1, eps=1e-5, window=7, device="cuda",
+                 fused=True):
+        self.shape = tuple(shape)
+        self.problem = make_problem(shape, spacing, sim, lam, eps, window)
+        self.fused = fused
+        d = len(shape)
+        self.lattice = lattice_shape(shape, spacing)
+        self.value = torch.empty(4, dtype=torch.float64, device=device)
+        self.grad = torch.empty((d,) + self.lattice, dtype=torch.float32, device=device)
+        self.workspace = torch.empty(objective_workspace_bytes(self.problem, fused),
+                                     dtype=torch.uint8, device=device)
+
+    def __call__(self, fixed, moving, ctrl, want_grad=True, stream=None):
+        return al_objective_grad(self.problem, fixed, moving, ctrl, self.value,
+                                 self.grad if want_grad else None, self.workspace,
+                                 want_grad=want_grad, fused=self.fused, stream=stream)

@@ -1,0 +1,180 @@
+// Shared device-side descriptors and helpers of libairgb (CUDA, sm_103a).
+// Nothing here is shared with the FP64 oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace airgb {
+
+constexpr int kMaxDelta = 32;
+
+// Image grid. 2D grids have Z = 1. nv = X*Y*Z < 2^31 (checked on the host).
+struct Grid {
+    int ndim;
+    int X, Y, Z;
+    int nv;
+};
+
+// Control lattice of the cubic B-spline transformation (Sec. III-C):
+// point j at voxel coordinate (j - 1)*delta, n = (N - 1)/delta + 4 points
+// per active axis; w[p][a] is the weight of control index q + a for a voxel
+// at x = q*delta + p, i.e. k_B1D(p/delta + 1 - a).
+struct Lattice {
+    int delta;
+    int nx, ny, nz;
+    int nc;  // nx*ny*nz
+    float w[kMaxDelta][4];
+};
+
+// Compile-time cubic B-spline weights for phase p of spacing DELTA
+// (t = p/DELTA): (1-t)^3/6, (3t^3 - 6t^2 + 4)/6, (-3t^3 + 3t^2 + 3t + 1)/6,
+// t^3/6, evaluated in double and rounded once.
+template <int DELTA>
+__host__ __device__ constexpr float bsw(int p, int a)
+{
+    return (float)(a == 0   ? (1.0 - (double)p / DELTA) * (1.0 - (double)p / DELTA) *
+                                (1.0 - (double)p / DELTA) / 6.0
+                   : a == 1 ? (3.0 * ((double)p / DELTA) * ((double)p / DELTA) * ((double)p / DELTA) -
+                               6.0 * ((double)p / DELTA) * ((double)p / DELTA) + 4.0) /
+                                  6.0
+                   : a == 2 ? (-3.0 * ((double)p / DELTA) * ((double)p / DELTA) * ((double)p / DELTA) +
+                               3.0 * ((double)p / DELTA) * ((double)p / DELTA) +
+                               3.0 * ((double)p / DELTA) + 1.0) /
+                                  6.0
+                            : ((double)p / DELTA) * ((double)p / DELTA) * ((double)p / DELTA) / 6.0);
+}
+
+// The weights of every phase of DELTA as a constexpr table.
+template <int DELTA>
+struct WTab {
+    float w[DELTA][4];
+    __host__ __device__ constexpr WTab() : w{}
+    {
+        for (int p = 0; p < DELTA; ++p)
+            for (int a = 0; a < 4; ++a)
+                w[p][a] = bsw<DELTA>(p, a);
+    }
+};
+
+// Same weights at run time, in double (used by the Gram-form regulariser).
+__host__ __device__ inline double bsw_d(int p, int a, int delta)
+{
+    const double t = (double)p / (double)delta;
+    switch (a) {
+    case 0: return (1.0 - t) * (1.0 - t) * (1.0 - t) / 6.0;
+    case 1: return (3.0 * t * t * t - 6.0 * t * t + 4.0) / 6.0;
+    case 2: return (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) / 6.0;
+    default: return t * t * t / 6.0;
+    }
+}
+
+// Sample position of a voxel displaced by u along one axis of size n:
+// y = x + u split exactly as integer part + fraction, so no rounding happens
+// in forming y (x + u in fp32 would lose bits for large x). Sets `inside` to
+// false when y < 0, y > n - 1 or u is not finite. On return (inside) `cell` is
+// the floor cell clamped to [0, n-2] and `f` in [0, 1] the offset in it.
+struct AxisSample {
+    int cell;
+    float f;
+};
+
+__device__ __forceinline__ bool axis_sample(int x, float u, int n, AxisSample &s)
+{
+    const float fl = floorf(u);
+    if (!(fabsf(fl) < 1.0e9f))  // not finite, or absurdly far outside
+        return false;
+    const int iy = x + (int)fl;
+    const float f = u - fl;  // exact for u >= 0; correctly rounded otherwise
+    if (iy < 0 || iy > n - 1 || (iy == n - 1 && f > 0.0f))
+        return false;
+    if (iy == n - 1) {  // on the last face: clamp the cell, weight 1 on the last voxel
+        s.cell = n - 2;
+        s.f = 1.0f;
+    } else {
+        s.cell = iy;
+        s.f = f;
+    }
+    return true;
+}
+
+// Linear interpolation value and gradient in a 3D cell: corners m[z][y][x].
+struct Interp {
+    float v, gx, gy, gz;
+};
+
+__device__ __forceinline__ Interp trilinear(const float *__restrict__ M, int X, int Y,
+                                            const AxisSample &sx, const AxisSample &sy,
+                                            const AxisSample &sz)
+{
+    const int64_t base = ((int64_t)sz.cell * Y + sy.cell) * X + sx.cell;
+    const int64_t sY = X, sZ = (int64_t)X * Y;
+    const float m000 = __ldg(M + base), m001 = __ldg(M + base + 1);
+    const float m010 = __ldg(M + base + sY), m011 = __ldg(M + base + sY + 1);
+    const float m100 = __ldg(M + base + sZ), m101 = __ldg(M + base + sZ + 1);
+    const float m110 = __ldg(M + base + sZ + sY), m111 = __ldg(M + base + sZ + sY + 1);
+    const float fx = sx.f, fy = sy.f, fz = sz.f;
+    // along x
+    const float d00 = m001 - m000, d01 = m011 - m010, d10 = m101 - m100, d11 = m111 - m110;
+    const float a00 = fmaf(fx, d00, m000), a01 = fmaf(fx, d01, m010);
+    const float a10 = fmaf(fx, d10, m100), a11 = fmaf(fx, d11, m110);
+    // along y
+    const float e0 = a01 - a00, e1 = a11 - a10;
+    const float b0 = fmaf(fy, e0, a00), b1 = fmaf(fy, e1, a10);
+    Interp r;
+    r.v = fmaf(fz, b1 - b0, b0);
+    r.gz = b1 - b0;
+    r.gy = fmaf(fz, e1 - e0, e0);
+    const float gx0 = fmaf(fy, d01 - d00, d00), gx1 = fmaf(fy, d11 - d10, d10);
+    r.gx = fmaf(fz, gx1 - gx0, gx0);
+    return r;
+}
+
+__device__ __forceinline__ Interp bilinear(const float *__restrict__ M, int X,
+                                           const AxisSample &sx, const AxisSample &sy)
+{
+    const int64_t base = (int64_t)sy.cell * X + sx.cell;
+    const float m00 = __ldg(M + base), m01 = __ldg(M + base + 1);
+    const float m10 = __ldg(M + base + X), m11 = __ldg(M + base + X + 1);
+    const float fx = sx.f, fy = sy.f;
+    const float d0 = m01 - m00, d1 = m11 - m10;
+    const float a0 = fmaf(fx, d0, m00), a1 = fmaf(fx, d1, m10);
+    Interp r;
+    r.v = fmaf(fy, a1 - a0, a0);
+    r.gy = a1 - a0;
+    r.gx = fmaf(fy, d1 - d0, d0);
+    r.gz = 0.0f;
+    return r;
+}
+
+// Deterministic block reduction of K doubles per thread (fixed tree).
+// `scratch` holds at least K * (blockDim.x / 32) doubles. Result valid in
+// thread 0 (written back into v).
+template <int K>
+__device__ __forceinline__ void block_reduce_d(double (&v)[K], double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    }
+    __syncthreads();  // scratch may still be in use by a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            scratch[k * nwarp + warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w)
+                s += scratch[k * nwarp + w];
+            v[k] = s;
+        }
+}
+
+}  // namespace airgb

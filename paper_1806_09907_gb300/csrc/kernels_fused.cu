@@ -1,0 +1,784 @@
+// A7: fused evaluation of J = S + lambda*R and dJ/dc.
+//
+// k_fused streams a brick of control cells slice by slice: the B-spline
+// expansion (A1), the masked warp (A2), the point-wise similarity terms (A3),
+// the warp adjoint (A5) and the transposed expansion (A6) all happen on
+// chip; only the brick's partial sums on its (cells+3)^D control points and
+// its moment sums leave it. k_ctrl then sums, for every control point, the
+// partials of the (at most 2 per axis) bricks that touch it in a fixed
+// order, so the result is deterministic without atomics. The regulariser is
+// evaluated on the control lattice in Gram form (k_gram):
+//   R = (1/|X|) sum_i c_i^T (Gz(x)Gy(x)Hx + Gz(x)Hy(x)Gx + Hz(x)Gy(x)Gx) c_i,
+// G = B^T B and H = (DB)^T (DB) per axis (B the sampled 1D B-spline matrix,
+// D the forward difference), which equals the voxel-grid definition exactly.
+//
+// LCC needs W in a neighbourhood, so it runs as: k_fused<FWD> writes W and
+// the mask, k_lcc_tiles turns them into dS/dW, k_fused<GW> projects that.
+#include "launch.h"
+#include "profile.h"
+
+namespace airgb {
+
+namespace {
+
+enum { MODE_MSE = 0, MODE_NCC = 1, MODE_FWD = 2, MODE_GW = 3 };
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <int D, int DELTA, int MODE>
+struct FCfg {
+    static constexpr int BCX = 8, BCY = 4, BCZ = (D == 3) ? 4 : 1;
+    static constexpr int BY = BCY * DELTA;
+    static constexpr int BZ = (D == 3) ? BCZ * DELTA : 1;
+    static constexpr int THREADS = BY * BCX;  // one thread per (row, x cell)
+    static constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
+    static constexpr int CH = (MODE == MODE_NCC) ? 3 * D : (MODE == MODE_FWD ? 0 : D);
+    static constexpr int CHS = CH > 0 ? CH : 1;  // storage size
+    static constexpr int NMOM = (MODE == MODE_MSE) ? 2 : (MODE == MODE_NCC ? 6 : 0);
+    static constexpr int NPART = CH * JZ * JY * JX;  // floats of one brick's partials
+    // dynamic shared memory (floats): per-thread x partials Q[BY][BCX][4][CHS],
+    // row sums Xs[BY][JX][CHS], brick sums acc[JZ][JY][JX][CHS]
+    static constexpr int nQ = (MODE == MODE_FWD) ? 0 : BY * BCX * 4 * CHS;
+    static constexpr int nXs = (MODE == MODE_FWD) ? 0 : BY * JX * CHS;
+    static constexpr int nAcc = (MODE == MODE_FWD) ? 0 : JZ * JY * JX * CHS;
+    static constexpr size_t dyn_smem = (size_t)(nQ + nXs + nAcc) * sizeof(float);
+};
+
+template <int D, int DELTA, int MODE>
+__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS)
+    k_fused(Grid g, Lattice L, const float *__restrict__ F,
+            const float *__restrict__ M, const float *__restrict__ c,
+            const float *__restrict__ gw_in, float *__restrict__ W_out,
+            uint8_t *__restrict__ m_out, float *__restrict__ bpart, double *__restrict__ mpart)
+{
+    using C = FCfg<D, DELTA, MODE>;
+    constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS;
+    constexpr int BCX = C::BCX, BY = C::BY;
+    __shared__ float cb[D][JZ][JY][JX];
+    __shared__ float tz[D][JY][JX];
+    extern __shared__ float dsm[];
+    float(*Q)[BCX][4][CHS] = reinterpret_cast<float(*)[BCX][4][CHS]>(dsm);
+    float(*Xs)[JX][CHS] = reinterpret_cast<float(*)[JX][CHS]>(dsm + C::nQ);
+    float(*acc)[JY][JX][CHS] = reinterpret_cast<float(*)[JY][JX][CHS]>(dsm + C::nQ + C::nXs);
+    __shared__ double red[(C::NMOM > 0 ? C::NMOM : 1) * C::THREADS / 32];
+    __shared__ float wt[DELTA][4];
+    constexpr WTab<DELTA> kW{};  // compile-time weights for the unrolled x phases
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+
+    const int tid = threadIdx.x;
+    if (tid < DELTA * 4)
+        wt[tid / 4][tid % 4] = L.w[tid / 4][tid % 4];
+    const int cx0 = blockIdx.x * BCX, cy0 = blockIdx.y * C::BCY, cz0 = blockIdx.z * C::BCZ;
+    const int y0 = cy0 * DELTA, z0 = (D == 3) ? cz0 * DELTA : 0;
+
+    // control block of the brick (zero beyond the lattice)
+    for (int e = tid; e < D * JZ * JY * JX; e += C::THREADS) {
+        const int i = e / (JZ * JY * JX);
+        int r = e - i * JZ * JY * JX;
+        const int lz = r / (JY * JX);
+        r -= lz * JY * JX;
+        const int ly = r / JX, lx = r - ly * JX;
+        const int jx = cx0 + lx, jy = cy0 + ly, jz = cz0 + lz;
+        float v = 0.0f;
+        if (jx < nx && jy < ny && jz < nz)
+            v = __ldg(c + (((int64_t)i * nz + jz) * ny + jy) * nx + jx);
+        cb[i][lz][ly][lx] = v;
+    }
+    if (MODE != MODE_FWD)
+        for (int e = tid; e < C::nAcc; e += C::THREADS)
+            (&acc[0][0][0][0])[e] = 0.0f;
+
+    const int cxl = tid % BCX, yl = tid / BCX;
+    const int y = y0 + yl, xc = (cx0 + cxl) * DELTA;
+    const int qyl = yl / DELTA, py = yl - qyl * DELTA;
+    float mom[C::NMOM > 0 ? C::NMOM : 1];
+#pragma unroll
+    for (int k = 0; k < (C::NMOM > 0 ? C::NMOM : 1); ++k)
+        mom[k] = 0.0f;
+    __syncthreads();
+    float wy[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        wy[b] = wt[py][b];
+
+    const int nslices = (D == 3) ? min(C::BZ, g.Z - z0) : 1;
+    for (int zl = 0; zl < nslices; ++zl) {
+        const int z = z0 + zl;
+        const int qzl = zl / DELTA, pz = zl - qzl * DELTA;
+        // ---- phase 1: z contraction of the control block for this slice
+        for (int e = tid; e < D * JY * JX; e += C::THREADS) {
+            const int i = e / (JY * JX), r = e - i * JY * JX;
+            const int ly = r / JX, lx = r - ly * JX;
+            float v;
+            if (D == 3) {
+                v = wt[pz][0] * cb[i][qzl][ly][lx];
+                v = fmaf(wt[pz][1], cb[i][qzl + 1][ly][lx], v);
+                v = fmaf(wt[pz][2], cb[i][qzl + 2][ly][lx], v);
+                v = fmaf(wt[pz][3], cb[i][qzl + 3][ly][lx], v);
+            } else {
+                v = cb[i][0][ly][lx];
+            }
+            tz[i][ly][lx] = v;
+        }
+        __syncthreads();
+        // ---- phase 2: voxels of this thread's row segment (one x cell)
+        float tzy[4][D];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float v = wy[0] * tz[i][qyl][cxl + e];
+                v = fmaf(wy[1], tz[i][qyl + 1][cxl + e], v);
+                v = fmaf(wy[2], tz[i][qyl + 2][cxl + e], v);
+                v = fmaf(wy[3], tz[i][qyl + 3][cxl + e], v);
+                tzy[e][i] = v;
+            }
+        float q[4][CHS];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int k = 0; k < CHS; ++k)
+                q[e][k] = 0.0f;
+        if (y < g.Y) {
+            const int64_t rowbase = ((int64_t)z * g.Y + y) * g.X;
+#pragma unroll
+            for (int px = 0; px < DELTA; ++px) {
+                const int x = xc + px;
+                if (x < g.X) {
+                    float uu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float v = kW.w[px][0] * tzy[0][i];
+                        v = fmaf(kW.w[px][1], tzy[1][i], v);
+                        v = fmaf(kW.w[px][2], tzy[2][i], v);
+                        v = fmaf(kW.w[px][3], tzy[3][i], v);
+                        uu[i] = v;
+                    }
+                    AxisSample sx, sy, sz;
+                    bool in = axis_sample(x, uu[0], g.X, sx);
+                    in &= axis_sample(y, uu[1], g.Y, sy);
+                    if (D == 3)
+                        in &= axis_sample(z, uu[2], g.Z, sz);
+                    const int64_t v = rowbase + x;
+                    if (MODE == MODE_FWD) {
+                        float wv = 0.0f;
+                        if (in)
+                            wv = (D == 3) ? trilinear(M, g.X, g.Y, sx, sy, sz).v
+                                          : bilinear(M, g.X, sx, sy).v;
+                        W_out[v] = wv;
+                        m_out[v] = in ? 1 : 0;
+                    } else {
+                        float gwv = 0.0f;
+                        if (MODE == MODE_GW) {
+                            gwv = __ldg(gw_in + v);
+                            in &= (gwv != 0.0f);
+                        }
+                        if (in) {
+                            const Interp ip = (D == 3) ? trilinear(M, g.X, g.Y, sx, sy, sz)
+                                                       : bilinear(M, g.X, sx, sy);
+                            const float gr[3] = {ip.gx, ip.gy, ip.gz};
+                            float vch[CHS];
+                            if (MODE == MODE_MSE) {
+                                const float d = ip.v - __ldg(F + v);
+                                mom[0] = fmaf(d, d, mom[0]);
+                                mom[1] += 1.0f;
+#pragma unroll
+                                for (int i = 0; i < D; ++i)
+                                    vch[i] = d * gr[i];
+                            } else if (MODE == MODE_NCC) {
+                                const float f = __ldg(F + v), w = ip.v;
+                                mom[0] += 1.0f;
+                                mom[1] += f;
+                                mom[2] += w;
+                                mom[3] = fmaf(f, f, mom[3]);
+                                mom[4] = fmaf(w, w, mom[4]);
+                                mom[5] = fmaf(f, w, mom[5]);
+#pragma unroll
+                                for (int i = 0; i < D; ++i) {
+                                    vch[i] = f * gr[i];
+                                    vch[D + i] = w * gr[i];
+                                    vch[2 * D + i] = gr[i];
+                                }
+                            } else {  // MODE_GW
+#pragma unroll
+                                for (int i = 0; i < D; ++i)
+                                    vch[i] = gwv * gr[i];
+                            }
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                                for (int k = 0; k < CHS; ++k)
+                                    q[e][k] = fmaf(kW.w[px][e], vch[k], q[e][k]);
+                        }
+                    }
+                }
+            }
+        }
+        if (MODE != MODE_FWD) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int k = 0; k < CHS; ++k)
+                    Q[yl][cxl][e][k] = q[e][k];
+        }
+        __syncthreads();
+        if (MODE != MODE_FWD) {
+            // ---- phase 3a: combine the x partials of neighbouring cells per row
+            for (int e = tid; e < BY * JX * CHS; e += C::THREADS) {
+                const int r = e / (JX * CHS), t = e - r * JX * CHS;
+                const int jxl = t / CHS, k = t - jxl * CHS;
+                float s = 0.0f;
+#pragma unroll
+                for (int a = 3; a >= 0; --a) {
+                    const int cl = jxl - a;
+                    if (cl >= 0 && cl < BCX)
+                        s += Q[r][cl][a][k];
+                }
+                Xs[r][jxl][k] = s;
+            }
+            __syncthreads();
+            // ---- phase 3b: y contraction, then z weights into the brick sums
+            for (int e = tid; e < JY * JX * CHS; e += C::THREADS) {
+                const int jyl = e / (JX * CHS), t = e - jyl * JX * CHS;
+                const int jxl = t / CHS, k = t - jxl * CHS;
+                float s = 0.0f;
+                const int r0 = max(0, (jyl - 3) * DELTA), r1 = min(BY, (jyl + 1) * DELTA);
+                for (int r = r0; r < r1; ++r) {
+                    const int qr = r / DELTA, pr = r - qr * DELTA;
+                    s = fmaf(wt[pr][jyl - qr], Xs[r][jxl][k], s);
+                }
+                if (D == 3) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        acc[qzl + a][jyl][jxl][k] =
+                            fmaf(wt[pz][a], s, acc[qzl + a][jyl][jxl][k]);
+                } else {
+                    acc[0][jyl][jxl][k] += s;
+                }
+            }
+        }
+    }
+    const int brick = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (MODE != MODE_FWD) {
+        __syncthreads();
+        float *dst = bpart + (int64_t)brick * C::NPART;
+        for (int e = tid; e < C::NPART; e += C::THREADS) {
+            // dst layout [k][lz][ly][lx]
+            const int k = e / (JZ * JY * JX), r = e - k * JZ * JY * JX;
+            const int lz = r / (JY * JX), r2 = r - lz * JY * JX;
+            const int ly = r2 / JX, lx = r2 - ly * JX;
+            dst[e] = acc[lz][ly][lx][k];
+        }
+    }
+    if (C::NMOM > 0) {
+        double m[C::NMOM > 0 ? C::NMOM : 1];
+#pragma unroll
+        for (int k = 0; k < (C::NMOM > 0 ? C::NMOM : 1); ++k)
+            m[k] = mom[k];
+        block_reduce_d<(C::NMOM > 0 ? C::NMOM : 1)>(m, red);
+        if (tid == 0)
+            for (int k = 0; k < C::NMOM; ++k)
+                mpart[(int64_t)brick * C::NMOM + k] = m[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gram-form diffusion regulariser on the control lattice.
+// Band entries of G = B^T B and H = (DB)^T (DB) along one axis of size N:
+//   G[j][j+o] = sum_{x=0}^{N-1} b_j(x) b_{j+o}(x),
+//   H[j][j+o] = sum_{x=0}^{N-2} (b_j(x+1)-b_j(x)) (b_{j+o}(x+1)-b_{j+o}(x)),
+// b_j(x) = w[x mod delta][j - x/delta] when that index is in 0..3, else 0.
+__device__ __forceinline__ float bvalue(const Lattice &L, int j, int x)
+{
+    const int q = x / L.delta, a = j - q;
+    return (a >= 0 && a <= 3) ? L.w[x - q * L.delta][a] : 0.0f;
+}
+
+__device__ void band_entry(const Lattice &L, int N, int n, int j, int o, float &G, float &H)
+{
+    const int j2 = j + o;
+    G = 0.0f;
+    H = 0.0f;
+    if (j < 0 || j >= n || j2 < 0 || j2 >= n)
+        return;
+    const int lo = max(0, (max(j, j2) - 3) * L.delta - 1);
+    const int hi = min(N, (min(j, j2) + 1) * L.delta + 1);
+    for (int x = lo; x < hi; ++x) {
+        const float a = bvalue(L, j, x), b = bvalue(L, j2, x);
+        G = fmaf(a, b, G);
+        if (x + 1 < N) {
+            const float da = bvalue(L, j, x + 1) - a, db = bvalue(L, j2, x + 1) - b;
+            H = fmaf(da, db, H);
+        }
+    }
+}
+
+constexpr int kGramT3 = 8, kGramT2 = 16, kGramThreads = 256;
+
+__global__ void __launch_bounds__(kGramThreads)
+    k_gram3(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
+            double *__restrict__ rpart)
+{
+    constexpr int T = kGramT3, H3 = T + 6;
+    __shared__ float cs[H3][H3][H3];
+    __shared__ float A[H3][H3][T], B[H3][H3][T];
+    __shared__ float GA[H3][T][T], HB[H3][T][T], GB[H3][T][T];
+    __shared__ float tG[3][T][7], tH[3][T][7];
+    __shared__ double red[kGramThreads / 32];
+    const int j0[3] = {(int)blockIdx.x * T, (int)blockIdx.y * T, (int)blockIdx.z * T};
+    const int nn[3] = {L.nx, L.ny, L.nz};
+    const int NN[3] = {g.X, g.Y, g.Z};
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 3 * T * 7; e += kGramThreads) {
+        const int k = e / (T * 7), r = e - k * T * 7, l = r / 7, o = r - l * 7 - 3;
+        band_entry(L, NN[k], nn[k], j0[k] + l, o, tG[k][l][o + 3], tH[k][l][o + 3]);
+    }
+    float rsum = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        __syncthreads();
+        for (int e = tid; e < H3 * H3 * H3; e += kGramThreads) {
+            const int lz = e / (H3 * H3), r = e - lz * H3 * H3, ly = r / H3, lx = r - ly * H3;
+            const int jx = j0[0] + lx - 3, jy = j0[1] + ly - 3, jz = j0[2] + lz - 3;
+            float v = 0.0f;
+            if (jx >= 0 && jx < L.nx && jy >= 0 && jy < L.ny && jz >= 0 && jz < L.nz)
+                v = __ldg(c + (((int64_t)i * L.nz + jz) * L.ny + jy) * L.nx + jx);
+            (&cs[0][0][0])[e] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < H3 * H3 * T; e += kGramThreads) {
+            const int lz = e / (H3 * T), r = e - lz * H3 * T, ly = r / T, lx = r - ly * T;
+            float a = 0.f, b = 0.f;
+#pragma unroll
+            for (int o = 0; o < 7; ++o) {
+                const float v = cs[lz][ly][lx + o];
+                a = fmaf(tH[0][lx][o], v, a);
+                b = fmaf(tG[0][lx][o], v, b);
+            }
+            A[lz][ly][lx] = a;
+            B[lz][ly][lx] = b;
+        }
+        __syncthreads();
+        for (int e = tid; e < H3 * T * T; e += kGramThreads) {
+            const int lz = e / (T * T), r = e - lz * T * T, ly = r / T, lx = r - ly * T;
+            float ga = 0.f, hb = 0.f, gb = 0.f;
+#pragma unroll
+            for (int o = 0; o < 7; ++o) {
+                const float a = A[lz][ly + o][lx], b = B[lz][ly + o][lx];
+                ga = fmaf(tG[1][ly][o], a, ga);
+                hb = fmaf(tH[1][ly][o], b, hb);
+                gb = fmaf(tG[1][ly][o], b, gb);
+            }
+            GA[lz][ly][lx] = ga;
+            HB[lz][ly][lx] = hb;
+            GB[lz][ly][lx] = gb;
+        }
+        __syncthreads();
+        for (int e = tid; e < T * T * T; e += kGramThreads) {
+            const int lz = e / (T * T), r = e - lz * T * T, ly = r / T, lx = r - ly * T;
+            const int jx = j0[0] + lx, jy = j0[1] + ly, jz = j0[2] + lz;
+            if (jx >= L.nx || jy >= L.ny || jz >= L.nz)
+                continue;
+            float s = 0.f;
+#pragma unroll
+            for (int o = 0; o < 7; ++o) {
+                s = fmaf(tG[2][lz][o], GA[lz + o][ly][lx] + HB[lz + o][ly][lx], s);
+                s = fmaf(tH[2][lz][o], GB[lz + o][ly][lx], s);
+            }
+            rsum = fmaf(cs[lz + 3][ly + 3][lx + 3], s, rsum);
+            gR[(((int64_t)i * L.nz + jz) * L.ny + jy) * L.nx + jx] = gscale * s;
+        }
+    }
+    double acc[1] = {rsum};
+    block_reduce_d<1>(acc, red);
+    if (tid == 0)
+        rpart[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+}
+
+__global__ void __launch_bounds__(kGramThreads)
+    k_gram2(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
+            double *__restrict__ rpart)
+{
+    constexpr int T = kGramT2, H2 = T + 6;
+    __shared__ float cs[H2][H2];
+    __shared__ float A[H2][T], B[H2][T];
+    __shared__ float tG[2][T][7], tH[2][T][7];
+    __shared__ double red[kGramThreads / 32];
+    const int j0[2] = {(int)blockIdx.x * T, (int)blockIdx.y * T};
+    const int nn[2] = {L.nx, L.ny};
+    const int NN[2] = {g.X, g.Y};
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 2 * T * 7; e += kGramThreads) {
+        const int k = e / (T * 7), r = e - k * T * 7, l = r / 7, o = r - l * 7 - 3;
+        band_entry(L, NN[k], nn[k], j0[k] + l, o, tG[k][l][o + 3], tH[k][l][o + 3]);
+    }
+    float rsum = 0.0f;
+    for (int i = 0; i < 2; ++i) {
+        __syncthreads();
+        for (int e = tid; e < H2 * H2; e += kGramThreads) {
+            const int ly = e / H2, lx = e - ly * H2;
+            const int jx = j0[0] + lx - 3, jy = j0[1] + ly - 3;
+            float v = 0.0f;
+            if (jx >= 0 && jx < L.nx && jy >= 0 && jy < L.ny)
+                v = __ldg(c + ((int64_t)i * L.ny + jy) * L.nx + jx);
+            cs[ly][lx] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < H2 * T; e += kGramThreads) {
+            const int ly = e / T, lx = e - ly * T;
+            float a = 0.f, b = 0.f;
+#pragma unroll
+            for (int o = 0; o < 7; ++o) {
+                const float v = cs[ly][lx + o];
+                a = fmaf(tH[0][lx][o], v, a);
+                b = fmaf(tG[0][lx][o], v, b);
+            }
+            A[ly][lx] = a;
+            B[ly][lx] = b;
+        }
+        __syncthreads();
+        for (int e = tid; e < T * T; e += kGramThreads) {
+            const int ly = e / T, lx = e - ly * T;
+            const int jx = j0[0] + lx, jy = j0[1] + ly;
+            if (jx >= L.nx || jy >= L.ny)
+                continue;
+            float s = 0.f;
+#pragma unroll
+            for (int o = 0; o < 7; ++o) {
+                s = fmaf(tG[1][ly][o], A[ly + o][lx], s);
+                s = fmaf(tH[1][ly][o], B[ly + o][lx], s);
+            }
+            rsum = fmaf(cs[ly + 3][lx + 3], s, rsum);
+            gR[((int64_t)i * L.ny + jy) * L.nx + jx] = gscale * s;
+        }
+    }
+    double acc[1] = {rsum};
+    block_reduce_d<1>(acc, red);
+    if (tid == 0)
+        rpart[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
+}
+
+// ---------------------------------------------------------------------------
+// Scalars: value = {J, S, R, n_mask}; scal = per-mode coefficients of the
+// projected channels in dS/dc.
+template <int K>
+__device__ void sum_parts(const double *__restrict__ p, int nb, double (&t)[K], double *red)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        t[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            t[k] += p[(int64_t)b * K + k];
+    block_reduce_d<K>(t, red);
+}
+
+__global__ void k_finalize(int mode, int64_t nv, double lambda, double eps,
+                           const double *__restrict__ mpart, int nbricks,
+                           const double *__restrict__ rpart, int ngram,
+                           const double *__restrict__ lpart, int nlcc, double *__restrict__ value,
+                           double *__restrict__ scal)
+{
+    __shared__ double red[6 * 32];
+    double r[1];
+    sum_parts<1>(rpart, ngram, r, red);
+    const double R = r[0] / (double)nv;
+    double S = 0.0, n = 0.0;
+    if (mode == MODE_MSE) {
+        double t[2];
+        sum_parts<2>(mpart, nbricks, t, red);
+        if (threadIdx.x == 0) {
+            n = t[1];
+            S = n > 0.0 ? t[0] / n : 0.0;
+            scal[0] = n > 0.0 ? 2.0 / n : 0.0;
+        }
+    } else if (mode == MODE_NCC) {
+        double t[6];
+        sum_parts<6>(mpart, nbricks, t, red);
+        if (threadIdx.x == 0) {
+            n = t[0];
+            if (n > 0.0) {
+                const double muf = t[1] / n, muw = t[2] / n;
+                const double cov = t[5] - n * muf * muw;
+                const double vf = t[3] - n * muf * muf;
+                const double vw = t[4] - n * muw * muw;
+                const double Dd = vf * vw + eps;
+                const double sD = sqrt(Dd);
+                S = 1.0 - cov / sD;
+                const double al = -1.0 / sD, be = cov * vf / (Dd * sD);
+                scal[0] = al;
+                scal[1] = be;
+                scal[2] = -al * muf - be * muw;
+            } else {
+                scal[0] = scal[1] = scal[2] = 0.0;
+            }
+        }
+    } else {  // LCC
+        double t[2];
+        sum_parts<2>(lpart, nlcc, t, red);
+        if (threadIdx.x == 0) {
+            n = t[1];
+            S = n > 0.0 ? 1.0 - t[0] / n : 0.0;
+            scal[0] = n > 0.0 ? 1.0 / n : 0.0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        value[0] = S + lambda * R;
+        value[1] = S;
+        value[2] = R;
+        value[3] = n;
+    }
+}
+
+// Per control point: fixed-order sum of the partials of the bricks that
+// touch it, channel combination, plus lambda * dR/dc.
+template <int D, int CH, int BCX, int BCY, int BCZ>
+__global__ void k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, double lambda,
+                       const float *__restrict__ bpart, const double *__restrict__ scal,
+                       const float *__restrict__ gR, float *__restrict__ gc)
+{
+    constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
+    constexpr int NPART = CH * JZ * JY * JX;
+    const int64_t total = (int64_t)L.nc;
+    float k0 = (float)scal[0], k1 = 0.f, k2 = 0.f;
+    if (CH == 3 * D) {
+        k1 = (float)scal[1];
+        k2 = (float)scal[2];
+    }
+    const float lam = (float)lambda;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int jx = (int)(e % L.nx);
+        const int64_t r = e / L.nx;
+        const int jy = (int)(r % L.ny), jz = (int)(r / L.ny);
+        float p[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+            p[k] = 0.0f;
+        const int bz_hi = (D == 3) ? min(jz / BCZ, gbz - 1) : 0;
+        const int bz_lo = (D == 3) ? max(0, jz / BCZ - 1) : 0;
+        for (int bz = bz_lo; bz <= bz_hi; ++bz) {
+            const int lz = (D == 3) ? jz - bz * BCZ : 0;
+            if (lz >= JZ)
+                continue;
+            for (int by = max(0, jy / BCY - 1); by <= min(jy / BCY, gby - 1); ++by) {
+                const int ly = jy - by * BCY;
+                if (ly >= JY)
+                    continue;
+                for (int bx = max(0, jx / BCX - 1); bx <= min(jx / BCX, gbx - 1); ++bx) {
+                    const int lx = jx - bx * BCX;
+                    if (lx >= JX)
+                        continue;
+                    const int brick = (bz * gby + by) * gbx + bx;
+                    const float *src = bpart + (int64_t)brick * NPART + (lz * JY + ly) * JX + lx;
+#pragma unroll
+                    for (int k = 0; k < CH; ++k)
+                        p[k] += __ldg(src + k * (JZ * JY * JX));
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            float v;
+            if (CH == 3 * D)
+                v = fmaf(k0, p[i], fmaf(k1, p[D + i], k2 * p[2 * D + i]));
+            else
+                v = k0 * p[i];
+            gc[(int64_t)i * total + e] = fmaf(lam, __ldg(gR + (int64_t)i * total + e), v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct Layout {
+    size_t scal, rpart, gR, bpart, mpart, Wb, mb, gb, lpart, total;
+    int nbricks, gbx, gby, gbz, ngram, nlcc;
+};
+
+template <int D, int DELTA, int MODE>
+void brick_grid(const Grid &g, int &gbx, int &gby, int &gbz)
+{
+    using C = FCfg<D, DELTA, MODE>;
+    const int cx = (g.X + DELTA - 1) / DELTA, cy = (g.Y + DELTA - 1) / DELTA;
+    const int cz = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
+    gbx = (cx + C::BCX - 1) / C::BCX;
+    gby = (cy + C::BCY - 1) / C::BCY;
+    gbz = (cz + C::BCZ - 1) / C::BCZ;
+}
+
+Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
+{
+    Layout o{};
+    const int D = g.ndim;
+    const int BCX = 8, BCY = 4, BCZ = (D == 3) ? 4 : 1;
+    const int cx = (g.X + L.delta - 1) / L.delta, cy = (g.Y + L.delta - 1) / L.delta;
+    const int cz = (D == 3) ? (g.Z + L.delta - 1) / L.delta : 1;
+    o.gbx = (cx + BCX - 1) / BCX;
+    o.gby = (cy + BCY - 1) / BCY;
+    o.gbz = (cz + BCZ - 1) / BCZ;
+    o.nbricks = o.gbx * o.gby * o.gbz;
+    const int CH = (kind == 1) ? 3 * D : D;
+    const int npart = CH * ((D == 3) ? BCZ + 3 : 1) * (BCY + 3) * (BCX + 3);
+    if (D == 3)
+        o.ngram = ((L.nx + kGramT3 - 1) / kGramT3) * ((L.ny + kGramT3 - 1) / kGramT3) *
+                  ((L.nz + kGramT3 - 1) / kGramT3);
+    else
+        o.ngram = ((L.nx + kGramT2 - 1) / kGramT2) * ((L.ny + kGramT2 - 1) / kGramT2);
+    o.nlcc = (kind == 2) ? lcc_num_blocks(g, window) : 0;
+    size_t off = 0;
+    o.scal = off;
+    off += 256;
+    o.rpart = off;
+    off += align256((size_t)o.ngram * 8);
+    o.gR = off;
+    off += align256((size_t)D * L.nc * 4);
+    o.bpart = off;
+    off += align256((size_t)o.nbricks * npart * 4);
+    o.mpart = off;
+    off += align256((size_t)o.nbricks * 6 * 8);
+    if (kind == 2) {
+        o.Wb = off;
+        off += align256((size_t)g.nv * 4);
+        o.mb = off;
+        off += align256((size_t)g.nv);
+        o.gb = off;
+        off += align256((size_t)g.nv * 4);
+        o.lpart = off;
+        off += align256((size_t)o.nlcc * 2 * 8);
+    }
+    o.total = off;
+    return o;
+}
+
+template <int D, int DELTA, int MODE>
+cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay, char *ws,
+                             const float *F, const float *M, const float *c, const float *gw,
+                             float *Wo, uint8_t *mo, cudaStream_t s)
+{
+    using C = FCfg<D, DELTA, MODE>;
+    dim3 grid(lay.gbx, lay.gby, lay.gbz);
+    ProfScope ps(s, MODE == MODE_MSE   ? "k_fused_mse"
+                    : MODE == MODE_NCC ? "k_fused_ncc"
+                    : MODE == MODE_FWD ? "k_fused_fwd"
+                                       : "k_fused_gw");
+    if (C::dyn_smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<D, DELTA, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::dyn_smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_fused<D, DELTA, MODE><<<grid, C::THREADS, C::dyn_smem, s>>>(
+        g, L, F, M, c, gw, Wo, mo, (float *)(ws + lay.bpart),
+        (double *)(ws + lay.mpart));
+    return cudaGetLastError();
+}
+
+template <int D, int DELTA>
+cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, double eps,
+                    double lambda, const float *F, const float *M, const float *c, double *value,
+                    float *gc, char *ws, cudaStream_t s)
+{
+    const Layout lay = make_layout(g, L, kind, window);
+    double *scal = (double *)(ws + lay.scal);
+    double *rpart = (double *)(ws + lay.rpart);
+    float *gR = (float *)(ws + lay.gR);
+    const float gscale = (float)(2.0 / (double)g.nv);
+    cudaError_t e;
+    prof_begin(s, "k_gram");
+    if (D == 3) {
+        dim3 gg((L.nx + kGramT3 - 1) / kGramT3, (L.ny + kGramT3 - 1) / kGramT3,
+                (L.nz + kGramT3 - 1) / kGramT3);
+        k_gram3<<<gg, kGramThreads, 0, s>>>(g, L, c, gscale, gR, rpart);
+    } else {
+        dim3 gg((L.nx + kGramT2 - 1) / kGramT2, (L.ny + kGramT2 - 1) / kGramT2);
+        k_gram2<<<gg, kGramThreads, 0, s>>>(g, L, c, gscale, gR, rpart);
+    }
+    prof_end(s);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    int mode;
+    if (kind == 0) {
+        mode = MODE_MSE;
+        e = run_fused_kernel<D, DELTA, MODE_MSE>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr, s);
+    } else if (kind == 1) {
+        mode = MODE_NCC;
+        e = run_fused_kernel<D, DELTA, MODE_NCC>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr, s);
+    } else {
+        mode = 2;
+        float *Wb = (float *)(ws + lay.Wb), *gb = (float *)(ws + lay.gb);
+        uint8_t *mb = (uint8_t *)(ws + lay.mb);
+        e = run_fused_kernel<D, DELTA, MODE_FWD>(g, L, lay, ws, F, M, c, nullptr, Wb, mb, s);
+        if (e != cudaSuccess)
+            return e;
+        e = launch_lcc_tiles(g, window, eps, F, Wb, mb, gc ? gb : nullptr,
+                             (double *)(ws + lay.lpart), s);
+        if (e != cudaSuccess)
+            return e;
+        if (gc)
+            e = run_fused_kernel<D, DELTA, MODE_GW>(g, L, lay, ws, F, M, c, gb, nullptr, nullptr, s);
+    }
+    if (e != cudaSuccess)
+        return e;
+    prof_begin(s, "k_finalize");
+    k_finalize<<<1, 1024, 0, s>>>(mode, g.nv, lambda, eps, (double *)(ws + lay.mpart),
+                                  lay.nbricks, rpart, lay.ngram, (double *)(ws + lay.lpart),
+                                  lay.nlcc, value, scal);
+    prof_end(s);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if (gc) {
+        const int th = 256;
+        int64_t nb = ((int64_t)L.nc + th - 1) / th;
+        if (nb > 152 * 16)
+            nb = 152 * 16;
+        const float *bp = (const float *)(ws + lay.bpart);
+        ProfScope ps(s, "k_ctrl");
+        if (kind == 1)
+            k_ctrl<D, 3 * D, 8, 4, (D == 3 ? 4 : 1)><<<(int)nb, th, 0, s>>>(
+                L, lay.gbx, lay.gby, lay.gbz, mode, lambda, bp, scal, gR, gc);
+        else
+            k_ctrl<D, D, 8, 4, (D == 3 ? 4 : 1)><<<(int)nb, th, 0, s>>>(
+                L, lay.gbx, lay.gby, lay.gbz, mode, lambda, bp, scal, gR, gc);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace
+
+bool fused_supported(const Grid &g, const Lattice &L, int kind, int window)
+{
+    (void)g;
+    (void)kind;
+    (void)window;
+    return L.delta == 4 || L.delta == 6 || L.delta == 8;
+}
+
+size_t fused_ws(const Grid &g, const Lattice &L, int kind, int window)
+{
+    return make_layout(g, L, kind, window).total;
+}
+
+cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, double eps,
+                         double lambda, const float *F, const float *M, const float *c,
+                         double *value, float *gc, void *ws, cudaStream_t s)
+{
+    char *w = (char *)ws;
+    if (g.ndim == 3) {
+        switch (L.delta) {
+        case 4: return run_all<3, 4>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        case 6: return run_all<3, 6>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        case 8: return run_all<3, 8>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        }
+    } else {
+        switch (L.delta) {
+        case 4: return run_all<2, 4>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        case 6: return run_all<2, 6>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        case 8: return run_all<2, 8>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace airgb

@@ -1,0 +1,57 @@
+// Host-side launchers shared between the translation units of libairgb.
+// Each returns cudaSuccess or the launch error; none synchronises.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace airgb {
+
+// ---- A1 / A6: B-spline expansion and its adjoint (unfused) ----------------
+cudaError_t launch_displacement(const Grid &g, const Lattice &L, const float *ctrl, float *disp,
+                                cudaStream_t s);
+size_t displacement_adjoint_ws(const Grid &g, const Lattice &L);
+cudaError_t launch_displacement_adjoint(const Grid &g, const Lattice &L, const float *grad_disp,
+                                        float *grad_ctrl, void *ws, cudaStream_t s);
+
+// ---- A2 / A5: warp and its adjoint -----------------------------------------
+cudaError_t launch_warp(const Grid &g, const float *moving, const float *disp, float *warped,
+                        uint8_t *mask, cudaStream_t s);
+cudaError_t launch_warp_adjoint(const Grid &g, const float *moving, const float *disp,
+                                const uint8_t *mask, const float *grad_warped, float *grad_disp,
+                                int accumulate, cudaStream_t s);
+
+// ---- A4: diffusion regulariser on the voxel grid ----------------------------
+size_t regulariser_ws(const Grid &g);
+cudaError_t launch_regulariser(const Grid &g, const float *disp, double weight, double *value_dev,
+                               float *grad_disp, void *ws, cudaStream_t s);
+
+// ---- A3: similarity (unfused) ------------------------------------------------
+size_t similarity_ws(const Grid &g, int kind, int window);
+cudaError_t launch_similarity(const Grid &g, int kind, int window, double eps, const float *fixed,
+                              const float *warped, const uint8_t *mask, double *value_dev,
+                              float *grad_warped, void *ws, cudaStream_t s);
+
+// LCC local-correlation kernel used by both the unfused similarity and the
+// fused objective: grad_unscaled = dS/dW * |X_m| (nullable), per-block
+// {sum of rho over masked core voxels, masked core voxel count}.
+int lcc_num_blocks(const Grid &g, int window);
+cudaError_t launch_lcc_tiles(const Grid &g, int window, double eps, const float *fixed,
+                             const float *warped, const uint8_t *mask, float *grad_unscaled,
+                             double *block_partials, cudaStream_t s);
+
+// ---- A7: fused objective -----------------------------------------------------
+bool fused_supported(const Grid &g, const Lattice &L, int kind, int window);
+size_t fused_ws(const Grid &g, const Lattice &L, int kind, int window);
+cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, double eps,
+                         double lambda, const float *fixed, const float *moving, const float *ctrl,
+                         double *value_dev, float *grad_ctrl, void *ws, cudaStream_t s);
+
+// J = S + lambda * R from the unfused pieces: out[0..3] = {J, S, R, n_mask}.
+cudaError_t launch_combine(const double *sim_value /*S, n_mask*/, const double *reg_value /*R*/,
+                           double lambda, double *out, cudaStream_t s);
+
+}  // namespace airgb

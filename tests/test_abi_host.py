@@ -1,0 +1,109 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point the header declares, and rejects bad arguments before it
+launches anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1806_09907_gb300 import airgb
+from paper_1806_09907_gb300 import build as airgb_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "airgb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    airgb_build.build()
+    return airgb.load()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(al_[a-z0-9_]+)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_binding_exports():
+    assert header_functions() == sorted(airgb.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    assert airgb.status_string(0) == "ok"
+    assert "aligned" in airgb.status_string(3)
+    assert airgb.status_string(99) == "unknown status"
+
+
+def test_bspline_init_lattice_sizes(lib):
+    # n = (N - 1)/delta + 4 per active axis, 1 for the inactive z of 2D
+    bs = airgb.bspline_init((160, 256, 256), 6)
+    assert (bs.n[0], bs.n[1], bs.n[2]) == (46, 46, 30)
+    bs = airgb.bspline_init((128, 128), 8)
+    assert (bs.n[0], bs.n[1], bs.n[2]) == (19, 19, 1)
+    assert airgb.lattice_shape((9, 10, 11), 4) == (6, 6, 6)
+
+
+@pytest.mark.parametrize("ndim,size,spacing,status", [
+    (4, (8, 8, 8), 4, 2),    # ndim
+    (3, (1, 8, 8), 4, 2),    # axis of one voxel
+    (2, (8, 8, 2), 4, 2),    # 2D with Z != 1
+    (3, (8, 8, 8), 0, 1),    # spacing
+    (3, (8, 8, 8), 33, 1),   # spacing above the table
+    (3, (1 << 21, 2, 2), 4, 2),  # axis too long
+])
+def test_bspline_init_rejects(lib, ndim, size, spacing, status):
+    g = airgb.al_grid()
+    g.ndim = ndim
+    for k in range(3):
+        g.size[k] = size[k]
+    bs = airgb.al_bspline()
+    assert lib.al_bspline_init(ctypes.byref(bs), ctypes.byref(g), spacing) == status
+
+
+def test_calls_reject_bad_pointers_before_launching(lib):
+    bs = airgb.bspline_init((16, 16, 16), 4)
+    # NULL arrays
+    assert lib.al_displacement(ctypes.byref(bs), None, None, None) == 1
+    # misaligned (never dereferenced: checked on the host)
+    a, b = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10004)
+    assert lib.al_displacement(ctypes.byref(bs), a, b, None) == 3
+    # lattice that does not match the grid
+    bad = airgb.bspline_init((16, 16, 16), 4)
+    bad.n[0] += 1
+    assert lib.al_displacement(ctypes.byref(bad), a, a, None) == 2
+
+
+def test_workspace_checks(lib):
+    pr = airgb.make_problem((24, 20, 18), 4, "lcc", 0.1)
+    need = lib.al_objective_workspace_bytes(ctypes.byref(pr))
+    assert need > 0
+    p = ctypes.c_void_p(0x10000)
+    st = lib.al_objective_grad(ctypes.byref(pr), p, p, p, p, p, p, ctypes.c_size_t(need - 1), None)
+    assert st == 8
+    st = lib.al_objective_grad(ctypes.byref(pr), p, p, p, p, p, None, ctypes.c_size_t(need), None)
+    assert st == 8  # NULL workspace
+    # unsupported LCC window and invalid eps are caught on the host
+    pr.sim.lcc_window = 9
+    assert lib.al_objective_workspace_bytes(ctypes.byref(pr)) == 0
+    pr.sim.lcc_window = 7
+    pr.sim.eps = -1.0
+    st = lib.al_objective_grad(ctypes.byref(pr), p, p, p, p, p, p, ctypes.c_size_t(need), None)
+    assert st == 1
+
+
+def test_fused_workspace_scales_with_volume(lib):
+    small = airgb.make_problem((40, 64, 64), 6, "mse")
+    big = airgb.make_problem((160, 256, 256), 6, "lcc")
+    a = lib.al_objective_workspace_bytes(ctypes.byref(small))
+    b = lib.al_objective_workspace_bytes(ctypes.byref(big))
+    # LCC keeps W, the mask and dS/dW: 9 bytes per voxel plus the partials
+    assert b > 9 * 160 * 256 * 256 > a > 0

@@ -1,0 +1,262 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (from the accuracy targets of the method's hot path):
+  warped image   max |W_gpu - W_ref| <= 1e-5 * (max M - min M)
+  objective      |J_gpu - J_ref| <= 1e-5 * |J_ref|
+  gradient       ||g_gpu - g_ref||_2 <= 1e-4 * ||g_ref||_2
+Steps without a stated tolerance use one derived from fp32 arithmetic
+(a few ulps of the largest term, stated per test). Integer results (the
+mask) must match bit for bit when both sides see the same fp32 input."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1806_09907_gb300 import airgb, synth
+from paper_1806_09907_gb300 import build as airgb_build
+
+pytestmark = pytest.mark.gpu
+
+W_TOL, J_TOL, G_TOL = 1e-5, 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    airgb_build.build()
+    return airgb.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def blob_case(shape, delta, sigma_c, seed, field_rms=1.5):
+    nd = len(shape)
+    blobs = synth.blob_scene(shape, max(4, int(np.prod(shape) ** (1 / nd) / 3)), (2.0, 6.0), seed)
+    F = synth.render_blobs(shape, blobs).astype(np.float32)
+    field = synth.smooth_field(shape, field_rms, seed + 1, min_wavelength=4.0 * delta)
+    M = synth.render_blobs(shape, blobs, field).astype(np.float32)
+    c = synth.random_ctrl(oracle.lattice_shape(shape, delta), nd, sigma_c, seed + 2)
+    return F, M, c
+
+
+def ct_case(shape, delta, sigma_c, seed):
+    nd = len(shape)
+    F, M = synth.ct_pair(shape, seed=seed, field_seed=seed + 1, n_inner=12)
+    c = synth.random_ctrl(oracle.lattice_shape(shape, delta), nd, sigma_c, seed + 2)
+    return F, M, c
+
+
+SMALL = [((37, 45), 4), ((50, 41), 6), ((33, 70), 8), ((29, 31), 5),
+         ((19, 23, 29), 4), ((21, 26, 40), 6), ((17, 40, 37), 8), ((13, 15, 18), 3)]
+
+
+# ------------------------------------------------------------------ A1 / A6 --
+
+@pytest.mark.parametrize("shape,delta", SMALL + [((9, 10, 11), 1), ((7, 300), 2)])
+def test_displacement(shape, delta):
+    nd = len(shape)
+    c = synth.random_ctrl(oracle.lattice_shape(shape, delta), nd, 2.0, 11)
+    u = host(airgb.al_displacement(shape, delta, dev(c)))
+    ref = oracle.displacement(shape, delta, c)
+    # fp32: 4^d products summed, each term <= |c|max * weight
+    assert np.abs(u - ref).max() <= 4e-6 * np.abs(c).max()
+
+
+@pytest.mark.parametrize("shape,delta", SMALL)
+def test_displacement_adjoint(shape, delta):
+    nd = len(shape)
+    g = np.random.default_rng(12).normal(size=(nd,) + shape).astype(np.float32)
+    gc = host(airgb.al_displacement_adjoint(shape, delta, dev(g)))
+    ref = oracle.displacement_adjoint(shape, delta, g)
+    assert rel_l2(gc, ref) <= 1e-6
+    assert np.abs(gc - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ A2 / A5 --
+
+@pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (64, 5, 7), (2, 2, 2), (2, 3)])
+def test_warp_and_adjoint(shape):
+    nd = len(shape)
+    rng = np.random.default_rng(13)
+    M = rng.normal(size=shape).astype(np.float32) * 100.0 - 40.0
+    u = rng.uniform(-3.0, 3.0, size=(nd,) + shape).astype(np.float32)
+    # exact integer displacements, points exactly on the faces, non-finite u
+    u.reshape(nd, -1)[:, :7] = np.round(u.reshape(nd, -1)[:, :7])
+    flat = u.reshape(nd, -1)
+    flat[0, 7] = np.nan
+    flat[1, 8] = np.inf
+    W, m = airgb.al_warp(dev(M), dev(u))
+    W, m = host(W), host(m)
+    Wr, mr, gy = oracle.warp(M, u, with_grad=True)
+    assert np.array_equal(m, mr)
+    assert m.reshape(-1)[7] == 0 and m.reshape(-1)[8] == 0
+    assert np.abs(W - Wr).max() <= W_TOL * (M.max() - M.min())
+    gw = rng.normal(size=shape).astype(np.float32)
+    gu = host(airgb.al_warp_adjoint(dev(M), dev(u), dev(m), dev(gw)))
+    ref = gy * (gw * mr)[None]
+    assert np.abs(gu - ref).max() <= 1e-5 * np.abs(ref).max()
+    # accumulate
+    base = rng.normal(size=(nd,) + shape).astype(np.float32)
+    acc = dev(base.copy())
+    airgb.al_warp_adjoint(dev(M), dev(u), dev(m), dev(gw), grad_disp=acc, accumulate=True)
+    assert np.abs(host(acc) - (base + ref)).max() <= 1e-5 * np.abs(base + ref).max()
+
+
+def test_warp_face_tie_and_shift():
+    shape = (6, 7, 8)
+    M = np.arange(np.prod(shape), dtype=np.float32).reshape(shape)
+    u = np.zeros((3,) + shape, dtype=np.float32)
+    u[0], u[1], u[2] = 2.0, -1.0, 3.0
+    W, m = airgb.al_warp(dev(M), dev(u))
+    Wr, mr = oracle.warp(M, u)
+    assert np.array_equal(host(m), mr) and np.array_equal(host(W), Wr.astype(np.float32))
+
+
+# ----------------------------------------------------------------------- A3 --
+
+@pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (40, 64, 33)])
+@pytest.mark.parametrize("sim,window", [("mse", 7), ("ncc", 7), ("lcc", 3), ("lcc", 5), ("lcc", 7)])
+def test_similarity(shape, sim, window):
+    rng = np.random.default_rng(14)
+    F = (rng.normal(size=shape) * 30.0 - 700.0).astype(np.float32)
+    Wv = (0.8 * F + rng.normal(size=shape) * 20.0 - 100.0).astype(np.float32)
+    m = (rng.uniform(size=shape) > 0.15).astype(np.uint8)
+    Wv = Wv * m
+    kind = airgb.SIM_KINDS[sim]
+    val, gw = airgb.al_similarity(sim, dev(F), dev(Wv), dev(m), eps=1e-5, window=window)
+    val, gw = host(val), host(gw)
+    S, gr = oracle.similarity(kind, F, Wv, m, eps=1e-5, window=window)
+    assert val[1] == m.sum()
+    assert abs(val[0] - S) <= J_TOL * abs(S)
+    assert rel_l2(gw, gr) <= G_TOL
+
+
+# ----------------------------------------------------------------------- A4 --
+
+@pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (2, 2, 2)])
+def test_regulariser(shape):
+    nd = len(shape)
+    u = np.random.default_rng(15).normal(size=(nd,) + shape).astype(np.float32) * 3.0
+    val, gu = airgb.al_regulariser(dev(u), weight=0.1)
+    R, gr = oracle.diffusion(u)
+    assert abs(host(val)[0] - R) <= J_TOL * abs(R)
+    assert rel_l2(host(gu), 0.1 * gr) <= 1e-5
+
+
+# ----------------------------------------------------------------------- A7 --
+
+def check_objective(F, M, c, delta, sim, window=7, lam=0.1, fused=True):
+    shape = F.shape
+    pr = airgb.make_problem(shape, delta, sim, lam, 1e-5, window)
+    val, g = airgb.al_objective_grad(pr, dev(F), dev(M), dev(c), fused=fused)
+    val, g = host(val), host(g)
+    ref, gref = oracle.objective_grad(airgb.SIM_KINDS[sim], F, M, c, delta, lam, 1e-5, window)
+    assert abs(val[3] - ref["n_mask"]) <= 1e-6 * F.size  # mask flips only within rounding
+    assert abs(val[2] - ref["R"]) <= J_TOL * abs(ref["R"]) + 1e-12
+    assert abs(val[1] - ref["S"]) <= J_TOL * abs(ref["J"])
+    assert abs(val[0] - ref["J"]) <= J_TOL * abs(ref["J"])
+    assert rel_l2(g, gref) <= G_TOL
+    return val, g
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("sim", ["mse", "ncc", "lcc"])
+@pytest.mark.parametrize("shape,delta", SMALL)
+def test_objective_small(shape, delta, sim, fused):
+    F, M, c = blob_case(shape, delta, 1.2, 20 + delta)
+    check_objective(F, M, c, delta, sim, window=5 if len(shape) == 3 else 7, fused=fused)
+
+
+@pytest.mark.parametrize("sim", ["mse", "ncc", "lcc"])
+def test_objective_ct_several_bricks(sim):
+    """CT-like values (-1000..1500 HU) on a grid spanning several bricks in
+    every axis with ragged tails (delta = 6)."""
+    shape = (45, 70, 101)
+    F, M, c = ct_case(shape, 6, 2.0, 31)
+    check_objective(F, M, c, 6, sim, window=7)
+
+
+def test_objective_identity_identical_images():
+    shape, delta = (21, 26, 40), 6
+    F, _, _ = blob_case(shape, delta, 1.0, 41)
+    c = np.zeros((3,) + oracle.lattice_shape(shape, delta), dtype=np.float32)
+    pr = airgb.make_problem(shape, delta, "mse", 0.1)
+    val, g = airgb.al_objective_grad(pr, dev(F), dev(F), dev(c))
+    val, g = host(val), host(g)
+    assert val[0] == 0.0 and val[3] == F.size
+    assert np.all(g == 0.0)
+
+
+def test_objective_everything_outside():
+    """A field that moves every voxel out of the domain: S = 0, J = lambda R."""
+    shape, delta = (19, 23, 29), 4
+    F, M, _ = blob_case(shape, delta, 1.0, 42)
+    c = np.full((3,) + oracle.lattice_shape(shape, delta), 1000.0, dtype=np.float32)
+    for sim in ("mse", "ncc", "lcc"):
+        val, g = airgb.al_objective_grad(airgb.make_problem(shape, delta, sim, 0.1), dev(F),
+                                         dev(M), dev(c))
+        val = host(val)
+        assert val[3] == 0 and val[1] == 0.0
+        assert val[0] == pytest.approx(0.1 * val[2], abs=1e-12)
+
+
+def test_objective_deterministic():
+    shape, delta = (45, 70, 101), 6
+    F, M, c = ct_case(shape, delta, 2.0, 43)
+    obj = airgb.Objective(shape, delta, "lcc", 0.1, window=7)
+    v1, g1 = (t.clone() for t in obj(dev(F), dev(M), dev(c)))
+    v2, g2 = obj(dev(F), dev(M), dev(c))
+    assert torch.equal(v1, v2) and torch.equal(g1, g2)
+    assert airgb.al_get_device_error() == 0
+
+
+def test_value_only_matches():
+    shape, delta = (21, 26, 40), 6
+    F, M, c = blob_case(shape, delta, 1.0, 44)
+    for sim in ("mse", "ncc", "lcc"):
+        pr = airgb.make_problem(shape, delta, sim, 0.1, window=5)
+        v_full, _ = airgb.al_objective_grad(pr, dev(F), dev(M), dev(c))
+        v_only, g = airgb.al_objective_grad(pr, dev(F), dev(M), dev(c), want_grad=False)
+        assert g is None
+        assert torch.equal(v_full, v_only)
+
+
+# ------------------------------------------------------- full-size workloads --
+
+def test_full_2d_128_mse():
+    """2D 128x128 blob pair, spacing 8, MSE + 0.1 diffusion, at c = 0 and at
+    a random c ~ N(0, 1)."""
+    F, M = synth.blobs_2d_128()
+    shape = F.shape
+    for sigma in (0.0, 1.0):
+        c = synth.random_ctrl(oracle.lattice_shape(shape, 8), 2, sigma, 9907)
+        check_objective(F, M, c, 8, "mse")
+
+
+def test_full_3d_128_mse():
+    """3D 128^3 blob pair, spacing 8, MSE + 0.1 diffusion."""
+    F, M = synth.blobs_3d_128()
+    c = synth.random_ctrl(oracle.lattice_shape(F.shape, 8), 3, 1.0, 9907)
+    check_objective(F, M, c, 8, "mse")
+
+
+@pytest.mark.parametrize("sim", ["lcc", "mse"])
+def test_full_ct_256x256x160(sim):
+    """The benchmark workload: 256x256x160 CT-like pair, spacing 6, LCC 7^3
+    (and MSE) + 0.1 diffusion, c ~ N(0, 3^2) voxels, in the launch
+    configuration the benchmark times."""
+    F, M = synth.ct_pair()
+    c = synth.random_ctrl(oracle.lattice_shape(F.shape, 6), 3, 3.0, 9907)
+    check_objective(F, M, c, 6, sim, window=7)
