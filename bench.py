@@ -40,12 +40,13 @@ WORKLOAD = ("3D 256x256x160 fp32 CT-like pair (ellipsoids in [-1000,1500] HU + N
 FLUSH_BYTES = 256 << 20
 
 # Algorithmic HBM bytes per voxel of each kernel of the fused LCC path (the
-# minimum each must move): k_fused_fwd reads M and writes W + mask; k_lcc_tiles
-# reads F, W, mask and writes dS/dW; k_fused_gw reads M and dS/dW; the
-# point-wise fused kernels read F and M. Per-launch control-point traffic is
-# added separately (coefficients in, partial sums out).
+# minimum each must move): k_fused_fwd reads M and writes W + mask;
+# k_lcc_stats reads F, W, mask and writes the three LCC coefficients;
+# k_lcc_grad reads them with F, W, mask and writes dS/dW; k_fused_gw reads M
+# and dS/dW; the point-wise fused kernels read F and M. Per-launch
+# control-point traffic is added separately (coefficients in).
 KERNEL_BYTES_PER_VOXEL = {
-    "k_fused_fwd": 9.0, "k_lcc_tiles": 13.0, "k_fused_gw": 8.0,
+    "k_fused_fwd": 9.0, "k_lcc_stats": 21.0, "k_lcc_grad": 25.0, "k_fused_gw": 8.0,
     "k_fused_mse": 8.0, "k_fused_ncc": 8.0,
 }
 

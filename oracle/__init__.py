@@ -57,9 +57,11 @@ def _load():
     lib.alref_lcc.argtypes = [ci, i64p, dp, dp, u8p, ci, cd, dp, dp]
     lib.alref_diffusion.argtypes = [ci, i64p, dp, dp, dp]
     lib.alref_objective_grad.argtypes = [ci, i64p, ci, ci, ci, cd, cd, dp, dp, dp, dp, dp]
+    lib.alref_objective_grad_ex.argtypes = [ci, i64p, ci, ci, ci, cd, cd, dp, dp, dp, dp, dp, dp,
+                                            dp]
     for name in ("alref_lattice_size", "alref_displacement", "alref_displacement_adjoint",
                  "alref_warp", "alref_mse", "alref_ncc", "alref_lcc", "alref_diffusion",
-                 "alref_objective_grad"):
+                 "alref_objective_grad", "alref_objective_grad_ex"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -172,17 +174,25 @@ def diffusion(disp):
     return float(R[0]), g
 
 
-def objective_grad(kind, fixed, moving, ctrl, delta, lam, eps=1e-5, window=7, grad=True):
+def objective_grad(kind, fixed, moving, ctrl, delta, lam, eps=1e-5, window=7, grad=True,
+                   intermediates=False):
     """J = S + lam*R, Eq. (objective), and dJ/dc.
 
-    Returns ({"J","S","R","n_mask"}, g_ctrl or None)."""
+    Returns ({"J","S","R","n_mask"}, g_ctrl or None); with intermediates=True
+    the dict also holds the displacement "u" and the per-voxel "dS_dW"."""
     f, m, c = _d(fixed), _d(moving), _d(ctrl)
     nd, N = _grid(f.shape)
     assert c.shape == (nd,) + lattice_shape(f.shape, delta), c.shape
     out = np.zeros(4, dtype=np.float64)
     gc = np.zeros_like(c) if grad else None
-    _check(_load().alref_objective_grad(nd, _p(N, ctypes.c_int64), int(delta), int(kind),
-                                        int(window), float(eps), float(lam), _p(f), _p(m), _p(c),
-                                        _p(out), _p(gc) if grad else None), "objective_grad")
+    u = np.zeros((nd,) + f.shape) if intermediates else None
+    gw = np.zeros(f.shape) if intermediates else None
+    _check(_load().alref_objective_grad_ex(nd, _p(N, ctypes.c_int64), int(delta), int(kind),
+                                           int(window), float(eps), float(lam), _p(f), _p(m),
+                                           _p(c), _p(out), _p(gc) if grad else None,
+                                           _p(u) if intermediates else None,
+                                           _p(gw) if intermediates else None), "objective_grad")
     vals = {"J": float(out[0]), "S": float(out[1]), "R": float(out[2]), "n_mask": float(out[3])}
+    if intermediates:
+        vals["u"], vals["dS_dW"] = u, gw
     return vals, gc

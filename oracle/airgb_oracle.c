@@ -491,9 +491,25 @@ int alref_diffusion(int ndim, const int64_t *N, const double *disp, double *R, d
 /* kind: 0 = MSE, 1 = NCC, 2 = LCC. out = {J, S, R, |X_m|}. g_ctrl NULL =    */
 /* value only.                                                               */
 /* ------------------------------------------------------------------------ */
+int alref_objective_grad_ex(int ndim, const int64_t *N, int delta, int kind, int window,
+                            double eps, double lambda, const double *fixed, const double *moving,
+                            const double *ctrl, double *out, double *g_ctrl, double *u_out,
+                            double *gw_out);
+
 int alref_objective_grad(int ndim, const int64_t *N, int delta, int kind, int window, double eps,
                          double lambda, const double *fixed, const double *moving,
                          const double *ctrl, double *out, double *g_ctrl)
+{
+    return alref_objective_grad_ex(ndim, N, delta, kind, window, eps, lambda, fixed, moving, ctrl,
+                                   out, g_ctrl, NULL, NULL);
+}
+
+/* Same, also returning the displacement u (ndim planes) and dS/dW per voxel
+ * when u_out / gw_out are not NULL (test diagnostics). */
+int alref_objective_grad_ex(int ndim, const int64_t *N, int delta, int kind, int window,
+                            double eps, double lambda, const double *fixed, const double *moving,
+                            const double *ctrl, double *out, double *g_ctrl, double *u_out,
+                            double *gw_out)
 {
     int64_t n[3];
     if (alref_lattice_size(ndim, N, delta, n))
@@ -532,6 +548,10 @@ int alref_objective_grad(int ndim, const int64_t *N, int delta, int kind, int wi
     out[1] = S;
     out[2] = R;
     out[3] = cnt;
+    if (u_out)
+        memcpy(u_out, u, sizeof(double) * ndim * nv);
+    if (gw_out)
+        memcpy(gw_out, gw, sizeof(double) * nv);
     if (g_ctrl) {
         for (int i = 0; i < ndim; ++i)
             for (int64_t v = 0; v < nv; ++v)

@@ -114,15 +114,17 @@ __device__ __forceinline__ Interp trilinear(const float *__restrict__ M, int X, 
     const float m100 = __ldg(M + base + sZ), m101 = __ldg(M + base + sZ + 1);
     const float m110 = __ldg(M + base + sZ + sY), m111 = __ldg(M + base + sZ + sY + 1);
     const float fx = sx.f, fy = sy.f, fz = sz.f;
-    // along x
+    const float gx_ = 1.0f - fx, gy_ = 1.0f - fy, gz_ = 1.0f - fz;
+    // along x; (1-f) m0 + f m1 is exact at f = 0 and f = 1, so samples on
+    // grid points (including the clamped last face) return the voxel value
     const float d00 = m001 - m000, d01 = m011 - m010, d10 = m101 - m100, d11 = m111 - m110;
-    const float a00 = fmaf(fx, d00, m000), a01 = fmaf(fx, d01, m010);
-    const float a10 = fmaf(fx, d10, m100), a11 = fmaf(fx, d11, m110);
+    const float a00 = fmaf(fx, m001, gx_ * m000), a01 = fmaf(fx, m011, gx_ * m010);
+    const float a10 = fmaf(fx, m101, gx_ * m100), a11 = fmaf(fx, m111, gx_ * m110);
     // along y
     const float e0 = a01 - a00, e1 = a11 - a10;
-    const float b0 = fmaf(fy, e0, a00), b1 = fmaf(fy, e1, a10);
+    const float b0 = fmaf(fy, a01, gy_ * a00), b1 = fmaf(fy, a11, gy_ * a10);
     Interp r;
-    r.v = fmaf(fz, b1 - b0, b0);
+    r.v = fmaf(fz, b1, gz_ * b0);
     r.gz = b1 - b0;
     r.gy = fmaf(fz, e1 - e0, e0);
     const float gx0 = fmaf(fy, d01 - d00, d00), gx1 = fmaf(fy, d11 - d10, d10);
@@ -137,10 +139,11 @@ __device__ __forceinline__ Interp bilinear(const float *__restrict__ M, int X,
     const float m00 = __ldg(M + base), m01 = __ldg(M + base + 1);
     const float m10 = __ldg(M + base + X), m11 = __ldg(M + base + X + 1);
     const float fx = sx.f, fy = sy.f;
+    const float gx_ = 1.0f - fx;
     const float d0 = m01 - m00, d1 = m11 - m10;
-    const float a0 = fmaf(fx, d0, m00), a1 = fmaf(fx, d1, m10);
+    const float a0 = fmaf(fx, m01, gx_ * m00), a1 = fmaf(fx, m11, gx_ * m10);
     Interp r;
-    r.v = fmaf(fy, a1 - a0, a0);
+    r.v = fmaf(fy, a1, (1.0f - fy) * a0);
     r.gy = a1 - a0;
     r.gx = fmaf(fy, d1 - d0, d0);
     r.gz = 0.0f;

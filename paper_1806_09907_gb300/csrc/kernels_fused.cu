@@ -13,7 +13,8 @@
 // D the forward difference), which equals the voxel-grid definition exactly.
 //
 // LCC needs W in a neighbourhood, so it runs as: k_fused<FWD> writes W and
-// the mask, k_lcc_tiles turns them into dS/dW, k_fused<GW> projects that.
+// the mask, k_lcc_stats and k_lcc_grad turn them into dS/dW, k_fused<GW>
+// projects that.
 #include "launch.h"
 #include "profile.h"
 
@@ -591,7 +592,7 @@ __global__ void k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, double la
 
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t scal, rpart, gR, bpart, mpart, Wb, mb, gb, lpart, total;
+    size_t scal, rpart, gR, bpart, mpart, Wb, mb, gb, lpart, coef, total;
     int nbricks, gbx, gby, gbz, ngram, nlcc;
 };
 
@@ -645,6 +646,8 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
         off += align256((size_t)g.nv * 4);
         o.lpart = off;
         off += align256((size_t)o.nlcc * 2 * 8);
+        o.coef = off;
+        off += lcc_coef_bytes(g);
     }
     o.total = off;
     return o;
@@ -661,7 +664,7 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
                     : MODE == MODE_NCC ? "k_fused_ncc"
                     : MODE == MODE_FWD ? "k_fused_fwd"
                                        : "k_fused_gw");
-    if (C::dyn_smem > 48 * 1024) {
+    if (C::dyn_smem > 0) {  // static + dynamic may pass 48 KB: always opt in
         cudaError_t e = cudaFuncSetAttribute(k_fused<D, DELTA, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::dyn_smem);
@@ -711,8 +714,8 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
         e = run_fused_kernel<D, DELTA, MODE_FWD>(g, L, lay, ws, F, M, c, nullptr, Wb, mb, s);
         if (e != cudaSuccess)
             return e;
-        e = launch_lcc_tiles(g, window, eps, F, Wb, mb, gc ? gb : nullptr,
-                             (double *)(ws + lay.lpart), s);
+        e = launch_lcc(g, window, eps, F, Wb, mb, gc ? gb : nullptr, (double *)(ws + lay.lpart),
+                       (float *)(ws + lay.coef), s);
         if (e != cudaSuccess)
             return e;
         if (gc)

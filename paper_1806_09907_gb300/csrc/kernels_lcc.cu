@@ -1,0 +1,469 @@
+// LCC (local NCC, Sec. III-B) statistics and exact gradient.
+//
+// S = 1 - (1/|X_m|) sum_{x in mask} rho(x), rho the correlation of F and W
+// in the (2R+1)^D box around x (zero padding, fixed count n). With
+// a, b, c = -drho/dS_W, -drho/dS_WW, -drho/dS_FW (zero off the mask),
+//   dS/dW(y) * |X_m| = sum_{x: y in box(x)} [a + 2 W(y) b + F(y) c](x)
+// on the mask (the box is symmetric, so the sum runs over box(y)).
+//
+// Numerics. fp32 local sums S_FF - S_F^2/n cancel catastrophically when the
+// intensities are large compared with their local spread (CT: -1000 HU with
+// 20 HU noise). Every partial sum here is therefore taken relative to the
+// value at the centre of its own window, and merging windows converts the
+// partial sums to the new centre exactly:
+//   sum (v - b)   = sum (v - a) + n (a - b)
+//   sum (v - b)^2 = sum (v - a)^2 + 2 (a - b) sum (v - a) + n (a - b)^2
+// (and the cross term likewise), so every quantity stays of the size of the
+// local spread. The statistics are shift invariant, so the derivatives with
+// respect to the shifted sums are the derivatives with respect to the plain
+// ones, and the shift re-enters the gradient as
+//   a'(x) = a(x) - 2 W(x) b(x) - F(x) c(x),   dS/dW(y) ~ A' + 2 W B + F C.
+//
+// k_lcc_stats: z-streaming tiles. Per input slice the tile (with an R halo)
+// enters a ring of 2R+1 slices in shared memory; the z sums of every column
+// are taken directly from the ring (relative to the column's centre value),
+// then merged along x and along y with the conversion above. It writes
+// (a', b, c) per voxel and per-block {sum rho, count} partials.
+// k_lcc_grad: plain box sums of (a', b, c) (z through a ring of x/y sums)
+// and dS/dW * |X_m| on the mask.
+#include "launch.h"
+#include "profile.h"
+
+namespace airgb {
+
+namespace {
+
+template <int D, int R>
+struct LccA {
+    static constexpr int TX = 32, TY = 16;
+    static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
+    static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
+    static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
+    static constexpr int ZC = (D == 3) ? 32 : 1;
+    static constexpr int THREADS = 512;
+    static constexpr int KL = (NL + THREADS - 1) / THREADS;  // load elements per thread
+    // shared memory: raw F / masked W ring, z sums (5 + 2 centre values),
+    // x-merged sums, mask ring (bytes, at the end)
+    static constexpr int oRF = 0, oRW = oRF + NR * NL, oZ = oRW + NR * NL, oX = oZ + 7 * NL;
+    static constexpr int oM = oX + 5 * NX;  // in floats; mask bytes start here
+    static constexpr size_t smem = (size_t)oM * 4 + (size_t)NR * NL;
+};
+
+template <int D, int R>
+struct LccB {
+    static constexpr int TX = 32, TY = 16;
+    static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
+    static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
+    static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
+    static constexpr int ZC = (D == 3) ? 32 : 1;
+    static constexpr int THREADS = 512;
+    static constexpr int KL = (NL + THREADS - 1) / THREADS;
+    static constexpr int KC = (NC + THREADS - 1) / THREADS;
+    static constexpr int oL = 0, oX = oL + 3 * NL, oQ = oX + 3 * NX;
+    static constexpr int total = oQ + NR * 3 * NC;
+    static constexpr size_t smem = (size_t)total * 4;
+};
+
+// Merge of a partial window (sums t1f,t1w,t2f,t2w,tfw relative to its centre
+// (af, aw), n points) into sums relative to (bf, bw).
+struct Sums {
+    float s1f, s1w, s2f, s2w, sfw;
+};
+
+__device__ __forceinline__ void merge(Sums &S, float t1f, float t1w, float t2f, float t2w,
+                                      float tfw, float af, float aw, float bf, float bw, float n)
+{
+    const float d = af - bf, e = aw - bw;
+    S.s1f += fmaf(n, d, t1f);
+    S.s1w += fmaf(n, e, t1w);
+    S.s2f += fmaf(d, fmaf(n, d, 2.0f * t1f), t2f);
+    S.s2w += fmaf(e, fmaf(n, e, 2.0f * t1w), t2w);
+    S.sfw += fmaf(d, fmaf(n, e, t1w), fmaf(e, t1f, tfw));
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
+    k_lcc_stats(Grid g, float eps, const float *__restrict__ F, const float *__restrict__ W,
+                const uint8_t *__restrict__ m, float *__restrict__ coef, double *__restrict__ part)
+{
+    using C = LccA<D, R>;
+    constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
+    constexpr int W1 = C::W1;
+    extern __shared__ float sm[];
+    float *rF = sm + C::oRF, *rW = sm + C::oRW, *Zs = sm + C::oZ, *Xs = sm + C::oX;
+    uint8_t *rM = reinterpret_cast<uint8_t *>(sm + C::oM);
+    __shared__ double red[2 * C::THREADS / 32];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+    const int zc0 = blockIdx.z * C::ZC, zc1 = min(zc0 + C::ZC, g.Z);
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+    const float n1 = (float)NR, n2 = (float)(NR * W1), n3 = (float)(NR * W1 * W1);
+    const float inv_n = 1.0f / n3;
+    float rho_sum = 0.0f, cnt = 0.0f;
+
+    // register prefetch of one slice of the load region (F, masked W, mask)
+    float pf[C::KL], pw[C::KL];
+    uint8_t pm[C::KL];
+    auto prefetch = [&](int zi) {
+        const bool zin = zi >= 0 && zi < g.Z;
+#pragma unroll
+        for (int k = 0; k < C::KL; ++k) {
+            const int e = tid + k * C::THREADS;
+            pf[k] = 0.0f;
+            pw[k] = 0.0f;
+            pm[k] = 0;
+            if (e < NL) {
+                const int ly = e / LX, lx = e - ly * LX;
+                const int x = x0 - R + lx, y = y0 - R + ly;
+                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
+                    const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
+                    pm[k] = __ldg(m + v);
+                    pf[k] = __ldg(F + v);
+                    pw[k] = pm[k] ? __ldg(W + v) : 0.0f;
+                }
+            }
+        }
+    };
+
+    int slot = 0;  // ring slot of the newest slice
+    const int zi_end = zc1 + C::RZ;
+    prefetch(zc0 - C::RZ);
+    for (int zi = zc0 - C::RZ; zi < zi_end; ++zi) {
+#pragma unroll
+        for (int k = 0; k < C::KL; ++k) {
+            const int e = tid + k * C::THREADS;
+            if (e < NL) {
+                rF[slot * NL + e] = pf[k];
+                rW[slot * NL + e] = pw[k];
+                rM[slot * NL + e] = pm[k];
+            }
+        }
+        if (zi + 1 < zi_end)
+            prefetch(zi + 1);  // in flight while this slice is processed
+        __syncthreads();
+        const int zc = zi - C::RZ;
+        if (zc >= zc0) {
+            const int oldest = (slot + 1 == NR) ? 0 : slot + 1;
+            int cs = oldest + C::RZ;
+            if (cs >= NR)
+                cs -= NR;
+            // ---- z sums of every column, relative to the column's centre value
+            for (int e = tid; e < NL; e += C::THREADS) {
+                const float af = rF[cs * NL + e], aw = rW[cs * NL + e];
+                float s1f = 0.f, s1w = 0.f, s2f = 0.f, s2w = 0.f, sfw = 0.f;
+                int sl = oldest;
+#pragma unroll
+                for (int t = 0; t < NR; ++t) {
+                    const float f = rF[sl * NL + e] - af, w = rW[sl * NL + e] - aw;
+                    s1f += f;
+                    s1w += w;
+                    s2f = fmaf(f, f, s2f);
+                    s2w = fmaf(w, w, s2w);
+                    sfw = fmaf(f, w, sfw);
+                    sl = (sl + 1 == NR) ? 0 : sl + 1;
+                }
+                Zs[0 * NL + e] = s1f;
+                Zs[1 * NL + e] = s1w;
+                Zs[2 * NL + e] = s2f;
+                Zs[3 * NL + e] = s2w;
+                Zs[4 * NL + e] = sfw;
+                Zs[5 * NL + e] = af;
+                Zs[6 * NL + e] = aw;
+            }
+            __syncthreads();
+            // ---- merge along x, two neighbouring outputs per thread sharing
+            //      W1 - 1 of their columns: outputs (ly, tx) and (ly, tx + 1)
+            for (int e = tid; e < NX / 2; e += C::THREADS) {
+                const int ly = e / (TX / 2), tx = 2 * (e - ly * (TX / 2));
+                const int base = ly * LX + tx;
+                const float bf0 = Zs[5 * NL + base + R], bw0 = Zs[6 * NL + base + R];
+                const float bf1 = Zs[5 * NL + base + R + 1], bw1 = Zs[6 * NL + base + R + 1];
+                Sums S0{0.f, 0.f, 0.f, 0.f, 0.f}, S1{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int d = 0; d <= W1; ++d) {
+                    const int c = base + d;
+                    const float t1f = Zs[c], t1w = Zs[NL + c], t2f = Zs[2 * NL + c];
+                    const float t2w = Zs[3 * NL + c], tfw = Zs[4 * NL + c];
+                    const float af = Zs[5 * NL + c], aw = Zs[6 * NL + c];
+                    if (d < W1)
+                        merge(S0, t1f, t1w, t2f, t2w, tfw, af, aw, bf0, bw0, n1);
+                    if (d > 0)
+                        merge(S1, t1f, t1w, t2f, t2w, tfw, af, aw, bf1, bw1, n1);
+                }
+                const int o = ly * TX + tx;
+                Xs[0 * NX + o] = S0.s1f;
+                Xs[1 * NX + o] = S0.s1w;
+                Xs[2 * NX + o] = S0.s2f;
+                Xs[3 * NX + o] = S0.s2w;
+                Xs[4 * NX + o] = S0.sfw;
+                Xs[0 * NX + o + 1] = S1.s1f;
+                Xs[1 * NX + o + 1] = S1.s1w;
+                Xs[2 * NX + o + 1] = S1.s2f;
+                Xs[3 * NX + o + 1] = S1.s2w;
+                Xs[4 * NX + o + 1] = S1.sfw;
+            }
+            __syncthreads();
+            // ---- merge along y (two outputs per thread, rows ty and ty + 1)
+            //      and evaluate the statistics of the core voxels
+            for (int e = tid; e < NC / 2; e += C::THREADS) {
+                const int tp = e / TX, tx = e - tp * TX;
+                const int ty0 = 2 * tp;
+                float bfv[2], bwv[2];
+                bool on[2];
+                int64_t vv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ty = ty0 + h, x = x0 + tx, y = y0 + ty;
+                    const int zcol = (ty + R) * LX + tx + R;
+                    on[h] = x < g.X && y < g.Y && rM[cs * NL + zcol];
+                    vv[h] = (int64_t)zc * sZ + (int64_t)y * sY + x;
+                    bfv[h] = Zs[5 * NL + zcol];
+                    bwv[h] = Zs[6 * NL + zcol];
+                }
+                Sums S[2] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+                for (int d = 0; d <= W1; ++d) {
+                    const int r = (ty0 + d) * TX + tx;
+                    const int zrow = (ty0 + d) * LX + tx + R;
+                    const float t1f = Xs[r], t1w = Xs[NX + r], t2f = Xs[2 * NX + r];
+                    const float t2w = Xs[3 * NX + r], tfw = Xs[4 * NX + r];
+                    const float af = Zs[5 * NL + zrow], aw = Zs[6 * NL + zrow];
+                    if (d < W1)
+                        merge(S[0], t1f, t1w, t2f, t2w, tfw, af, aw, bfv[0], bwv[0], n2);
+                    if (d > 0)
+                        merge(S[1], t1f, t1w, t2f, t2w, tfw, af, aw, bfv[1], bwv[1], n2);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int x = x0 + tx, y = y0 + ty0 + h;
+                    if (x >= g.X || y >= g.Y)
+                        continue;
+                    float ca = 0.f, cb = 0.f, cc = 0.f;
+                    if (on[h]) {
+                        const Sums &T = S[h];
+                        const float cov = fmaf(-T.s1f * T.s1w, inv_n, T.sfw);
+                        const float vf = fmaf(-T.s1f * T.s1f, inv_n, T.s2f);
+                        const float vw = fmaf(-T.s1w * T.s1w, inv_n, T.s2w);
+                        const float Dd = fmaf(vf, vw, eps);
+                        const float rs = rsqrtf(Dd);
+                        const float rs3 = rs * rs * rs;
+                        const float rho = cov * rs;
+                        cb = 0.5f * cov * vf * rs3;  // -drho/dS_WW
+                        cc = -rs;                    // -drho/dS_FW
+                        const float a = (T.s1f * rs - cov * vf * T.s1w * rs3) * inv_n;  // -drho/dS_W
+                        ca = a - 2.0f * bwv[h] * cb - bfv[h] * cc;
+                        rho_sum += rho;
+                        cnt += 1.0f;
+                    }
+                    if (coef) {
+                        coef[vv[h]] = ca;
+                        coef[g.nv + vv[h]] = cb;
+                        coef[2 * (int64_t)g.nv + vv[h]] = cc;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        slot = (slot + 1 == NR) ? 0 : slot + 1;
+    }
+    double acc[2] = {rho_sum, cnt};
+    block_reduce_d<2>(acc, red);
+    if (tid == 0) {
+        const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        part[2 * b] = acc[0];
+        part[2 * b + 1] = acc[1];
+    }
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(LccB<D, R>::THREADS)
+    k_lcc_grad(Grid g, const float *__restrict__ F, const float *__restrict__ W,
+               const uint8_t *__restrict__ m, const float *__restrict__ coef,
+               float *__restrict__ gout)
+{
+    using C = LccB<D, R>;
+    constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
+    extern __shared__ float sm[];
+    float *Lq = sm + C::oL, *Xq = sm + C::oX, *Q = sm + C::oQ;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+    const int zc0 = blockIdx.z * C::ZC, zc1 = min(zc0 + C::ZC, g.Z);
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+
+    float pq[C::KL][3];
+    auto prefetch = [&](int zi) {
+        const bool zin = zi >= 0 && zi < g.Z;
+#pragma unroll
+        for (int k = 0; k < C::KL; ++k) {
+            const int e = tid + k * C::THREADS;
+            pq[k][0] = pq[k][1] = pq[k][2] = 0.0f;
+            if (e < NL) {
+                const int ly = e / LX, lx = e - ly * LX;
+                const int x = x0 - R + lx, y = y0 - R + ly;
+                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
+                    const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
+                    pq[k][0] = __ldg(coef + v);
+                    pq[k][1] = __ldg(coef + g.nv + v);
+                    pq[k][2] = __ldg(coef + 2 * (int64_t)g.nv + v);
+                }
+            }
+        }
+    };
+    // core voxel values of the output slice, fetched one slice ahead
+    float cf[C::KC], cw[C::KC];
+    uint8_t cm[C::KC];
+    auto prefetch_core = [&](int zo) {
+#pragma unroll
+        for (int k = 0; k < C::KC; ++k) {
+            const int e = tid + k * C::THREADS;
+            cf[k] = cw[k] = 0.0f;
+            cm[k] = 0;
+            const int ty = e / TX, tx = e - ty * TX;
+            const int x = x0 + tx, y = y0 + ty;
+            if (e < NC && zo >= 0 && zo < g.Z && x < g.X && y < g.Y) {
+                const int64_t v = (int64_t)zo * sZ + (int64_t)y * sY + x;
+                cm[k] = __ldg(m + v);
+                if (cm[k]) {
+                    cf[k] = __ldg(F + v);
+                    cw[k] = __ldg(W + v);
+                }
+            }
+        }
+    };
+
+    int slot = 0;
+    const int zi_end = zc1 + C::RZ;
+    prefetch(zc0 - C::RZ);
+    for (int zi = zc0 - C::RZ; zi < zi_end; ++zi) {
+#pragma unroll
+        for (int k = 0; k < C::KL; ++k) {
+            const int e = tid + k * C::THREADS;
+            if (e < NL) {
+                Lq[e] = pq[k][0];
+                Lq[NL + e] = pq[k][1];
+                Lq[2 * NL + e] = pq[k][2];
+            }
+        }
+        const int zo = zi - C::RZ;
+        if (zi + 1 < zi_end)
+            prefetch(zi + 1);
+        if (zo >= zc0)
+            prefetch_core(zo);
+        __syncthreads();
+        for (int e = tid; e < 3 * NX; e += C::THREADS) {
+            const int q = e / NX, r = e - q * NX;
+            const int ly = r / TX, tx = r - ly * TX;
+            const float *src = Lq + q * NL + ly * LX + tx;
+            float s = 0.f;
+#pragma unroll
+            for (int d = 0; d < C::W1; ++d)
+                s += src[d];
+            Xq[e] = s;
+        }
+        __syncthreads();
+        for (int e = tid; e < 3 * NC; e += C::THREADS) {
+            const int q = e / NC, r = e - q * NC;
+            const int ty = r / TX, tx = r - ty * TX;
+            const float *src = Xq + q * NX + ty * TX + tx;
+            float s = 0.f;
+#pragma unroll
+            for (int d = 0; d < C::W1; ++d)
+                s += src[d * TX];
+            Q[(slot * 3 + q) * NC + r] = s;
+        }
+        __syncthreads();
+        if (zo >= zc0) {
+            const int oldest = (slot + 1 == NR) ? 0 : slot + 1;
+#pragma unroll
+            for (int k = 0; k < C::KC; ++k) {
+                const int e = tid + k * C::THREADS;
+                const int ty = e / TX, tx = e - ty * TX;
+                const int x = x0 + tx, y = y0 + ty;
+                if (e >= NC || x >= g.X || y >= g.Y)
+                    continue;
+                float gv = 0.0f;
+                if (cm[k]) {
+                    float A = 0.f, B = 0.f, Cc = 0.f;
+                    int sl = oldest;
+#pragma unroll
+                    for (int t = 0; t < NR; ++t) {
+                        A += Q[(sl * 3 + 0) * NC + e];
+                        B += Q[(sl * 3 + 1) * NC + e];
+                        Cc += Q[(sl * 3 + 2) * NC + e];
+                        sl = (sl + 1 == NR) ? 0 : sl + 1;
+                    }
+                    gv = fmaf(2.0f * cw[k], B, fmaf(cf[k], Cc, A));
+                }
+                gout[(int64_t)zo * sZ + (int64_t)y * sY + x] = gv;
+            }
+        }
+        __syncthreads();
+        slot = (slot + 1 == NR) ? 0 : slot + 1;
+    }
+}
+
+template <int D, int R>
+cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, const uint8_t *m,
+                    float *gout, double *part, float *coef, cudaStream_t s)
+{
+    using A = LccA<D, R>;
+    using B = LccB<D, R>;
+    static_assert(A::smem <= 227 * 1024 && B::smem <= 227 * 1024, "LCC tile too large");
+    cudaError_t e = cudaFuncSetAttribute(k_lcc_stats<D, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A::smem);
+    if (e != cudaSuccess)
+        return e;
+    {
+        dim3 grid((g.X + A::TX - 1) / A::TX, (g.Y + A::TY - 1) / A::TY, (g.Z + A::ZC - 1) / A::ZC);
+        ProfScope ps(s, "k_lcc_stats");
+        k_lcc_stats<D, R><<<grid, A::THREADS, A::smem, s>>>(g, (float)eps, F, W, m,
+                                                            gout ? coef : nullptr, part);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess || !gout)
+        return e;
+    e = cudaFuncSetAttribute(k_lcc_grad<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)B::smem);
+    if (e != cudaSuccess)
+        return e;
+    {
+        dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + B::ZC - 1) / B::ZC);
+        ProfScope ps(s, "k_lcc_grad");
+        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, F, W, m, coef, gout);
+    }
+    return cudaGetLastError();
+}
+
+template <int D, int R>
+int lcc_blocks(const Grid &g)
+{
+    using A = LccA<D, R>;
+    return ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY) * ((g.Z + A::ZC - 1) / A::ZC);
+}
+
+}  // namespace
+
+int lcc_num_blocks(const Grid &g, int window)
+{
+    const int R = window / 2;
+    if (g.ndim == 3)
+        return R == 1 ? lcc_blocks<3, 1>(g) : R == 2 ? lcc_blocks<3, 2>(g) : lcc_blocks<3, 3>(g);
+    return R == 1 ? lcc_blocks<2, 1>(g) : R == 2 ? lcc_blocks<2, 2>(g) : lcc_blocks<2, 3>(g);
+}
+
+size_t lcc_coef_bytes(const Grid &g) { return ((size_t)g.nv * 3 * 4 + 255) / 256 * 256; }
+
+cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,
+                       const uint8_t *m, float *gout, double *part, float *coef, cudaStream_t s)
+{
+    const int R = window / 2;
+    if (g.ndim == 3) {
+        if (R == 1) return lcc_run<3, 1>(g, eps, F, W, m, gout, part, coef, s);
+        if (R == 2) return lcc_run<3, 2>(g, eps, F, W, m, gout, part, coef, s);
+        return lcc_run<3, 3>(g, eps, F, W, m, gout, part, coef, s);
+    }
+    if (R == 1) return lcc_run<2, 1>(g, eps, F, W, m, gout, part, coef, s);
+    if (R == 2) return lcc_run<2, 2>(g, eps, F, W, m, gout, part, coef, s);
+    return lcc_run<2, 3>(g, eps, F, W, m, gout, part, coef, s);
+}
+
+}  // namespace airgb

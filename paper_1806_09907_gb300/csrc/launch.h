@@ -35,13 +35,15 @@ cudaError_t launch_similarity(const Grid &g, int kind, int window, double eps, c
                               const float *warped, const uint8_t *mask, double *value_dev,
                               float *grad_warped, void *ws, cudaStream_t s);
 
-// LCC local-correlation kernel used by both the unfused similarity and the
-// fused objective: grad_unscaled = dS/dW * |X_m| (nullable), per-block
-// {sum of rho over masked core voxels, masked core voxel count}.
+// LCC statistics + exact gradient, shared by the unfused similarity and the
+// fused objective: grad_unscaled = dS/dW * |X_m| (nullable; needs `coef`,
+// 3*nv floats of scratch), per-block {sum of rho over masked voxels, masked
+// voxel count} partials (lcc_num_blocks(g, window) blocks).
 int lcc_num_blocks(const Grid &g, int window);
-cudaError_t launch_lcc_tiles(const Grid &g, int window, double eps, const float *fixed,
-                             const float *warped, const uint8_t *mask, float *grad_unscaled,
-                             double *block_partials, cudaStream_t s);
+size_t lcc_coef_bytes(const Grid &g);
+cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *fixed,
+                       const float *warped, const uint8_t *mask, float *grad_unscaled,
+                       double *block_partials, float *coef, cudaStream_t s);
 
 // ---- A7: fused objective -----------------------------------------------------
 bool fused_supported(const Grid &g, const Lattice &L, int kind, int window);
