@@ -3,7 +3,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "../../include/airgb.h"
+#include "airgb.h"
 #include "launch.h"
 
 using namespace airgb;

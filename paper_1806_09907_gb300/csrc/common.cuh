@@ -150,6 +150,39 @@ __device__ __forceinline__ Interp bilinear(const float *__restrict__ M, int X,
     return r;
 }
 
+// Interpolation from corner values already loaded: c[0..7] = m000, m001,
+// m010, m011, m100, m101, m110, m111 (z, y, x bits), same arithmetic as
+// trilinear() / bilinear().
+__device__ __forceinline__ Interp interp8(const float (&c)[8], float fx, float fy, float fz)
+{
+    const float gx_ = 1.0f - fx, gy_ = 1.0f - fy, gz_ = 1.0f - fz;
+    const float d00 = c[1] - c[0], d01 = c[3] - c[2], d10 = c[5] - c[4], d11 = c[7] - c[6];
+    const float a00 = fmaf(fx, c[1], gx_ * c[0]), a01 = fmaf(fx, c[3], gx_ * c[2]);
+    const float a10 = fmaf(fx, c[5], gx_ * c[4]), a11 = fmaf(fx, c[7], gx_ * c[6]);
+    const float e0 = a01 - a00, e1 = a11 - a10;
+    const float b0 = fmaf(fy, a01, gy_ * a00), b1 = fmaf(fy, a11, gy_ * a10);
+    Interp r;
+    r.v = fmaf(fz, b1, gz_ * b0);
+    r.gz = b1 - b0;
+    r.gy = fmaf(fz, e1 - e0, e0);
+    const float gx0 = fmaf(fy, d01 - d00, d00), gx1 = fmaf(fy, d11 - d10, d10);
+    r.gx = fmaf(fz, gx1 - gx0, gx0);
+    return r;
+}
+
+__device__ __forceinline__ Interp interp4(const float (&c)[4], float fx, float fy)
+{
+    const float gx_ = 1.0f - fx;
+    const float d0 = c[1] - c[0], d1 = c[3] - c[2];
+    const float a0 = fmaf(fx, c[1], gx_ * c[0]), a1 = fmaf(fx, c[3], gx_ * c[2]);
+    Interp r;
+    r.v = fmaf(fy, a1, (1.0f - fy) * a0);
+    r.gy = a1 - a0;
+    r.gx = fmaf(fy, d1 - d0, d0);
+    r.gz = 0.0f;
+    return r;
+}
+
 // Deterministic block reduction of K doubles per thread (fixed tree).
 // `scratch` holds at least K * (blockDim.x / 32) doubles. Result valid in
 // thread 0 (written back into v).

@@ -12,9 +12,9 @@
 // G = B^T B and H = (DB)^T (DB) per axis (B the sampled 1D B-spline matrix,
 // D the forward difference), which equals the voxel-grid definition exactly.
 //
-// LCC needs W in a neighbourhood, so it runs as: k_fused<FWD> writes W and
-// the mask, k_lcc_stats and k_lcc_grad turn them into dS/dW, k_fused<GW>
-// projects that.
+// LCC needs W in a neighbourhood, so it runs as: k_fused<FWD> writes W, the
+// mask and dM~/dy, k_lcc_stats and k_lcc_grad turn W into dS/dW, and
+// k_fused<GW> projects dS/dW * dM~/dy onto the control points.
 #include "launch.h"
 #include "profile.h"
 
@@ -26,53 +26,83 @@ enum { MODE_MSE = 0, MODE_NCC = 1, MODE_FWD = 2, MODE_GW = 3 };
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Brick of control cells handled by one CTA: BCX x BCY cells in x/y (one
+// thread per voxel column, lanes consecutive in x) and BCZ cell layers in z
+// streamed slice by slice. Every axis spans >= 3 cells, so a control point
+// is touched by at most two bricks per axis (k_ctrl relies on it).
+__host__ __device__ constexpr int brick_bcx(int delta) { return delta <= 4 ? 8 : 4; }
+__host__ __device__ constexpr int brick_bcy(int delta) { return delta <= 4 ? 4 : 3; }
+__host__ __device__ constexpr int brick_bcz(int ndim) { return ndim == 3 ? 4 : 1; }
+
 template <int D, int DELTA, int MODE>
 struct FCfg {
-    static constexpr int BCX = 8, BCY = 4, BCZ = (D == 3) ? 4 : 1;
-    static constexpr int BY = BCY * DELTA;
-    static constexpr int BZ = (D == 3) ? BCZ * DELTA : 1;
-    static constexpr int THREADS = BY * BCX;  // one thread per (row, x cell)
+    static constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
+    static constexpr int BX = BCX * DELTA, BY = BCY * DELTA;
+    static constexpr int THREADS = BX * BY;
     static constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
     static constexpr int CH = (MODE == MODE_NCC) ? 3 * D : (MODE == MODE_FWD ? 0 : D);
     static constexpr int CHS = CH > 0 ? CH : 1;  // storage size
     static constexpr int NMOM = (MODE == MODE_MSE) ? 2 : (MODE == MODE_NCC ? 6 : 0);
     static constexpr int NPART = CH * JZ * JY * JX;  // floats of one brick's partials
-    // dynamic shared memory (floats): per-thread x partials Q[BY][BCX][4][CHS],
-    // row sums Xs[BY][JX][CHS], brick sums acc[JZ][JY][JX][CHS]
-    static constexpr int nQ = (MODE == MODE_FWD) ? 0 : BY * BCX * 4 * CHS;
-    static constexpr int nXs = (MODE == MODE_FWD) ? 0 : BY * JX * CHS;
-    static constexpr int nAcc = (MODE == MODE_FWD) ? 0 : JZ * JY * JX * CHS;
-    static constexpr size_t dyn_smem = (size_t)(nQ + nXs + nAcc) * sizeof(float);
+    static constexpr int VC = (MODE == MODE_FWD) ? 2 : 1;  // slices whose loads are in flight
+    // dynamic shared memory: one plane of column partials P[BY][BX][CHS] and
+    // its x contraction X[BY][JX][CHS]
+    static constexpr int nP = (MODE == MODE_FWD) ? 0 : BY * BX * CHS;
+    static constexpr int nX = (MODE == MODE_FWD) ? 0 : BY * JX * CHS;
+    static constexpr size_t dyn_smem = (size_t)(nP + nX) * sizeof(float);
 };
 
-template <int D, int DELTA, int MODE>
-__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS)
-    k_fused(Grid g, Lattice L, const float *__restrict__ F,
-            const float *__restrict__ M, const float *__restrict__ c,
-            const float *__restrict__ gw_in, float *__restrict__ W_out,
-            uint8_t *__restrict__ m_out, float *__restrict__ bpart, double *__restrict__ mpart)
+// xy contraction of control plane jz for the column (qx + px/DELTA, ...):
+// sum_b wy[b] sum_e wx[e] cb[i][jz][qy + b][qx + e].
+template <int D, int JZ, int JY, int JX>
+__device__ __forceinline__ void plane_xy(const float (&cb)[D][JZ][JY][JX], int jz, int qy, int qx,
+                                         const float (&wx)[4], const float (&wy)[4], float (&out)[D])
 {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float acc = 0.0f;
+        if (jz < JZ) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float r = wx[0] * cb[i][jz][qy + b][qx];
+                r = fmaf(wx[1], cb[i][jz][qy + b][qx + 1], r);
+                r = fmaf(wx[2], cb[i][jz][qy + b][qx + 2], r);
+                r = fmaf(wx[3], cb[i][jz][qy + b][qx + 3], r);
+                acc = fmaf(wy[b], r, acc);
+            }
+        }
+        out[i] = acc;
+    }
+}
+
+template <int D, int DELTA, int MODE>
+__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
+                                  (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
+                                                                                            : 1)
+    k_fused(Grid g, Lattice L, const float *__restrict__ F, const float *__restrict__ M,
+            const float *__restrict__ c, const float *__restrict__ gw_in,
+            float *__restrict__ W_out, uint8_t *__restrict__ m_out, float *__restrict__ G_io,
+            float *__restrict__ bpart, double *__restrict__ mpart)
+{
+    // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
+    // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
     using C = FCfg<D, DELTA, MODE>;
-    constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS;
-    constexpr int BCX = C::BCX, BY = C::BY;
+    constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS, BX = C::BX, BY = C::BY;
+    constexpr WTab<DELTA> kW{};  // weights of the compile-time z phases
     __shared__ float cb[D][JZ][JY][JX];
-    __shared__ float tz[D][JY][JX];
-    extern __shared__ float dsm[];
-    float(*Q)[BCX][4][CHS] = reinterpret_cast<float(*)[BCX][4][CHS]>(dsm);
-    float(*Xs)[JX][CHS] = reinterpret_cast<float(*)[JX][CHS]>(dsm + C::nQ);
-    float(*acc)[JY][JX][CHS] = reinterpret_cast<float(*)[JY][JX][CHS]>(dsm + C::nQ + C::nXs);
-    __shared__ double red[(C::NMOM > 0 ? C::NMOM : 1) * C::THREADS / 32];
     __shared__ float wt[DELTA][4];
-    constexpr WTab<DELTA> kW{};  // compile-time weights for the unrolled x phases
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    __shared__ double red[(C::NMOM > 0 ? C::NMOM : 1) * ((C::THREADS + 31) / 32)];
+    extern __shared__ float dsm[];
+    float *P = dsm, *Xc = dsm + C::nP;
 
     const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int cx0 = blockIdx.x * C::BCX, cy0 = blockIdx.y * C::BCY, cz0 = blockIdx.z * C::BCZ;
+    const int x = cx0 * DELTA + tx, y = cy0 * DELTA + ty, z0 = (D == 3) ? cz0 * DELTA : 0;
+    const int brick = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+
     if (tid < DELTA * 4)
         wt[tid / 4][tid % 4] = L.w[tid / 4][tid % 4];
-    const int cx0 = blockIdx.x * BCX, cy0 = blockIdx.y * C::BCY, cz0 = blockIdx.z * C::BCZ;
-    const int y0 = cy0 * DELTA, z0 = (D == 3) ? cz0 * DELTA : 0;
-
-    // control block of the brick (zero beyond the lattice)
     for (int e = tid; e < D * JZ * JY * JX; e += C::THREADS) {
         const int i = e / (JZ * JY * JX);
         int r = e - i * JZ * JY * JX;
@@ -81,205 +111,254 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS)
         const int ly = r / JX, lx = r - ly * JX;
         const int jx = cx0 + lx, jy = cy0 + ly, jz = cz0 + lz;
         float v = 0.0f;
-        if (jx < nx && jy < ny && jz < nz)
-            v = __ldg(c + (((int64_t)i * nz + jz) * ny + jy) * nx + jx);
+        if (jx < L.nx && jy < L.ny && jz < L.nz)
+            v = __ldg(c + (((int64_t)i * L.nz + jz) * L.ny + jy) * L.nx + jx);
         cb[i][lz][ly][lx] = v;
     }
-    if (MODE != MODE_FWD)
-        for (int e = tid; e < C::nAcc; e += C::THREADS)
-            (&acc[0][0][0][0])[e] = 0.0f;
+    __syncthreads();
 
-    const int cxl = tid % BCX, yl = tid / BCX;
-    const int y = y0 + yl, xc = (cx0 + cxl) * DELTA;
-    const int qyl = yl / DELTA, py = yl - qyl * DELTA;
+    const int qxl = tx / DELTA, px = tx - qxl * DELTA;
+    const int qyl = ty / DELTA, py = ty - qyl * DELTA;
+    float wx[4], wy[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        wx[e] = wt[px][e];
+        wy[e] = wt[py][e];
+    }
+    const bool colvalid = x < g.X && y < g.Y;
+    float cxy[4][D];  // xy-contracted control values of the four active planes
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        if (MODE != MODE_GW)
+            plane_xy<D, JZ, JY, JX>(cb, a, qyl, qxl, wx, wy, cxy[a]);
+    float qz[4][CHS];  // column partial sums of the four active planes
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < CHS; ++k)
+            qz[a][k] = 0.0f;
     float mom[C::NMOM > 0 ? C::NMOM : 1];
 #pragma unroll
     for (int k = 0; k < (C::NMOM > 0 ? C::NMOM : 1); ++k)
         mom[k] = 0.0f;
-    __syncthreads();
-    float wy[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        wy[b] = wt[py][b];
 
-    const int nslices = (D == 3) ? min(C::BZ, g.Z - z0) : 1;
-    for (int zl = 0; zl < nslices; ++zl) {
-        const int z = z0 + zl;
-        const int qzl = zl / DELTA, pz = zl - qzl * DELTA;
-        // ---- phase 1: z contraction of the control block for this slice
-        for (int e = tid; e < D * JY * JX; e += C::THREADS) {
-            const int i = e / (JY * JX), r = e - i * JY * JX;
-            const int ly = r / JX, lx = r - ly * JX;
-            float v;
-            if (D == 3) {
-                v = wt[pz][0] * cb[i][qzl][ly][lx];
-                v = fmaf(wt[pz][1], cb[i][qzl + 1][ly][lx], v);
-                v = fmaf(wt[pz][2], cb[i][qzl + 2][ly][lx], v);
-                v = fmaf(wt[pz][3], cb[i][qzl + 3][ly][lx], v);
-            } else {
-                v = cb[i][0][ly][lx];
-            }
-            tz[i][ly][lx] = v;
-        }
+    // one plane of column partials -> x then y contraction -> global partials
+    auto flush = [&](int lp, const float (&vals)[CHS]) {
+#pragma unroll
+        for (int k = 0; k < CHS; ++k)
+            P[(ty * BX + tx) * CHS + k] = colvalid ? vals[k] : 0.0f;
         __syncthreads();
-        // ---- phase 2: voxels of this thread's row segment (one x cell)
-        float tzy[4][D];
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                float v = wy[0] * tz[i][qyl][cxl + e];
-                v = fmaf(wy[1], tz[i][qyl + 1][cxl + e], v);
-                v = fmaf(wy[2], tz[i][qyl + 2][cxl + e], v);
-                v = fmaf(wy[3], tz[i][qyl + 3][cxl + e], v);
-                tzy[e][i] = v;
+        for (int e = tid; e < BY * JX * CHS; e += C::THREADS) {
+            const int yy = e / (JX * CHS), r = e - yy * JX * CHS;
+            const int jxl = r / CHS, k = r - jxl * CHS;
+            const int x_lo = max(0, (jxl - 3) * DELTA), x_hi = min(BX, (jxl + 1) * DELTA);
+            float s = 0.0f;
+            for (int xx = x_lo; xx < x_hi; ++xx) {
+                const int q = xx / DELTA;
+                s = fmaf(wt[xx - q * DELTA][jxl - q], P[(yy * BX + xx) * CHS + k], s);
             }
-        float q[4][CHS];
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-            for (int k = 0; k < CHS; ++k)
-                q[e][k] = 0.0f;
-        if (y < g.Y) {
-            const int64_t rowbase = ((int64_t)z * g.Y + y) * g.X;
-#pragma unroll
-            for (int px = 0; px < DELTA; ++px) {
-                const int x = xc + px;
-                if (x < g.X) {
-                    float uu[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        float v = kW.w[px][0] * tzy[0][i];
-                        v = fmaf(kW.w[px][1], tzy[1][i], v);
-                        v = fmaf(kW.w[px][2], tzy[2][i], v);
-                        v = fmaf(kW.w[px][3], tzy[3][i], v);
-                        uu[i] = v;
-                    }
-                    AxisSample sx, sy, sz;
-                    bool in = axis_sample(x, uu[0], g.X, sx);
-                    in &= axis_sample(y, uu[1], g.Y, sy);
-                    if (D == 3)
-                        in &= axis_sample(z, uu[2], g.Z, sz);
-                    const int64_t v = rowbase + x;
-                    if (MODE == MODE_FWD) {
-                        float wv = 0.0f;
-                        if (in)
-                            wv = (D == 3) ? trilinear(M, g.X, g.Y, sx, sy, sz).v
-                                          : bilinear(M, g.X, sx, sy).v;
-                        W_out[v] = wv;
-                        m_out[v] = in ? 1 : 0;
-                    } else {
-                        float gwv = 0.0f;
-                        if (MODE == MODE_GW) {
-                            gwv = __ldg(gw_in + v);
-                            in &= (gwv != 0.0f);
-                        }
-                        if (in) {
-                            const Interp ip = (D == 3) ? trilinear(M, g.X, g.Y, sx, sy, sz)
-                                                       : bilinear(M, g.X, sx, sy);
-                            const float gr[3] = {ip.gx, ip.gy, ip.gz};
-                            float vch[CHS];
-                            if (MODE == MODE_MSE) {
-                                const float d = ip.v - __ldg(F + v);
-                                mom[0] = fmaf(d, d, mom[0]);
-                                mom[1] += 1.0f;
-#pragma unroll
-                                for (int i = 0; i < D; ++i)
-                                    vch[i] = d * gr[i];
-                            } else if (MODE == MODE_NCC) {
-                                const float f = __ldg(F + v), w = ip.v;
-                                mom[0] += 1.0f;
-                                mom[1] += f;
-                                mom[2] += w;
-                                mom[3] = fmaf(f, f, mom[3]);
-                                mom[4] = fmaf(w, w, mom[4]);
-                                mom[5] = fmaf(f, w, mom[5]);
-#pragma unroll
-                                for (int i = 0; i < D; ++i) {
-                                    vch[i] = f * gr[i];
-                                    vch[D + i] = w * gr[i];
-                                    vch[2 * D + i] = gr[i];
-                                }
-                            } else {  // MODE_GW
-#pragma unroll
-                                for (int i = 0; i < D; ++i)
-                                    vch[i] = gwv * gr[i];
-                            }
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-#pragma unroll
-                                for (int k = 0; k < CHS; ++k)
-                                    q[e][k] = fmaf(kW.w[px][e], vch[k], q[e][k]);
-                        }
-                    }
-                }
-            }
+            Xc[(yy * JX + jxl) * CHS + k] = s;
         }
-        if (MODE != MODE_FWD) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-#pragma unroll
-                for (int k = 0; k < CHS; ++k)
-                    Q[yl][cxl][e][k] = q[e][k];
-        }
-        __syncthreads();
-        if (MODE != MODE_FWD) {
-            // ---- phase 3a: combine the x partials of neighbouring cells per row
-            for (int e = tid; e < BY * JX * CHS; e += C::THREADS) {
-                const int r = e / (JX * CHS), t = e - r * JX * CHS;
-                const int jxl = t / CHS, k = t - jxl * CHS;
-                float s = 0.0f;
-#pragma unroll
-                for (int a = 3; a >= 0; --a) {
-                    const int cl = jxl - a;
-                    if (cl >= 0 && cl < BCX)
-                        s += Q[r][cl][a][k];
-                }
-                Xs[r][jxl][k] = s;
-            }
-            __syncthreads();
-            // ---- phase 3b: y contraction, then z weights into the brick sums
-            for (int e = tid; e < JY * JX * CHS; e += C::THREADS) {
-                const int jyl = e / (JX * CHS), t = e - jyl * JX * CHS;
-                const int jxl = t / CHS, k = t - jxl * CHS;
-                float s = 0.0f;
-                const int r0 = max(0, (jyl - 3) * DELTA), r1 = min(BY, (jyl + 1) * DELTA);
-                for (int r = r0; r < r1; ++r) {
-                    const int qr = r / DELTA, pr = r - qr * DELTA;
-                    s = fmaf(wt[pr][jyl - qr], Xs[r][jxl][k], s);
-                }
-                if (D == 3) {
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        acc[qzl + a][jyl][jxl][k] =
-                            fmaf(wt[pz][a], s, acc[qzl + a][jyl][jxl][k]);
-                } else {
-                    acc[0][jyl][jxl][k] += s;
-                }
-            }
-        }
-    }
-    const int brick = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    if (MODE != MODE_FWD) {
         __syncthreads();
         float *dst = bpart + (int64_t)brick * C::NPART;
-        for (int e = tid; e < C::NPART; e += C::THREADS) {
-            // dst layout [k][lz][ly][lx]
-            const int k = e / (JZ * JY * JX), r = e - k * JZ * JY * JX;
-            const int lz = r / (JY * JX), r2 = r - lz * JY * JX;
-            const int ly = r2 / JX, lx = r2 - ly * JX;
-            dst[e] = acc[lz][ly][lx][k];
+        for (int e = tid; e < JY * JX * CHS; e += C::THREADS) {
+            const int k = e / (JY * JX), r = e - k * JY * JX;
+            const int jyl = r / JX, jxl = r - jyl * JX;
+            const int y_lo = max(0, (jyl - 3) * DELTA), y_hi = min(BY, (jyl + 1) * DELTA);
+            float s = 0.0f;
+            for (int yy = y_lo; yy < y_hi; ++yy) {
+                const int q = yy / DELTA;
+                s = fmaf(wt[yy - q * DELTA][jyl - q], Xc[(yy * JX + jxl) * CHS + k], s);
+            }
+            dst[(k * JZ + lp) * JY * JX + jyl * JX + jxl] = s;
         }
+    };
+
+    const int cells_z = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
+    const int nlayers = (D == 3) ? min(C::BCZ, cells_z - cz0) : 1;
+    const int64_t sYm = g.X, sZm = (int64_t)g.X * g.Y;
+    constexpr int NCOR = (D == 3) ? 8 : 4;
+    for (int cz = 0; cz < C::BCZ; ++cz) {
+        if (cz > 0) {
+            // plane cz - 1 has all its contributions: write it out, roll
+            if (MODE != MODE_FWD)
+                flush(cz - 1, qz[0]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                for (int k = 0; k < CHS; ++k)
+                    qz[a][k] = qz[a + 1][k];
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    cxy[a][i] = cxy[a + 1][i];
+            }
+#pragma unroll
+            for (int k = 0; k < CHS; ++k)
+                qz[3][k] = 0.0f;
+            if (MODE != MODE_GW)
+                plane_xy<D, JZ, JY, JX>(cb, cz + 3, qyl, qxl, wx, wy, cxy[3]);
+        }
+        if (cz >= nlayers || !colvalid)
+            continue;
+        const int zl0 = z0 + cz * DELTA;
+        if constexpr (MODE == MODE_GW) {
+            // dS/dW * dM~/dy from memory, all loads of the layer issued first
+            float gv[DELTA], gr[DELTA][D];
+#pragma unroll
+            for (int pz = 0; pz < DELTA; ++pz) {
+                const int z = min(zl0 + pz, g.Z - 1);
+                const int64_t v = (int64_t)z * sZm + (int64_t)y * sYm + x;
+                gv[pz] = __ldg(gw_in + v);
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    gr[pz][i] = __ldg(G_io + (int64_t)i * g.nv + v);
+            }
+#pragma unroll
+            for (int pz = 0; pz < DELTA; ++pz) {
+                if (zl0 + pz >= g.Z)
+                    break;
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float vch = gv[pz] * gr[pz][i];
+                    if (D == 3) {
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            qz[a][i] = fmaf(kW.w[pz][a], vch, qz[a][i]);
+                    } else {
+                        qz[0][i] += vch;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+        for (int p0 = 0; p0 < DELTA; p0 += C::VC) {
+            // issue every load of VC slices, then use them
+            float mcor[C::VC][NCOR], aux[C::VC], fx[C::VC], fy[C::VC], fz[C::VC];
+            bool inb[C::VC];
+#pragma unroll
+            for (int j = 0; j < C::VC; ++j) {
+                const int pz = p0 + j;
+                if (pz >= DELTA)
+                    break;
+                const int z = zl0 + pz;
+                float uu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    float v = kW.w[pz][0] * cxy[0][i];
+                    v = fmaf(kW.w[pz][1], cxy[1][i], v);
+                    v = fmaf(kW.w[pz][2], cxy[2][i], v);
+                    v = fmaf(kW.w[pz][3], cxy[3][i], v);
+                    uu[i] = (D == 3) ? v : cxy[0][i];
+                }
+                AxisSample sx{0, 0.f}, sy{0, 0.f}, sz{0, 0.f};
+                bool in = axis_sample(x, uu[0], g.X, sx);
+                in &= axis_sample(y, uu[1], g.Y, sy);
+                if (D == 3)
+                    in &= axis_sample(z, uu[2], g.Z, sz);
+                in &= (z < g.Z);
+                if (!in)  // any in-volume cell; its values are not used
+                    sx.cell = sy.cell = sz.cell = 0;
+                inb[j] = in;
+                fx[j] = sx.f;
+                fy[j] = sy.f;
+                fz[j] = sz.f;
+                const int64_t base = (D == 3 ? (int64_t)sz.cell * sZm : 0) +
+                                     (int64_t)sy.cell * sYm + sx.cell;
+                mcor[j][0] = __ldg(M + base);
+                mcor[j][1] = __ldg(M + base + 1);
+                mcor[j][2] = __ldg(M + base + sYm);
+                mcor[j][3] = __ldg(M + base + sYm + 1);
+                if constexpr (D == 3) {
+                    mcor[j][4] = __ldg(M + base + sZm);
+                    mcor[j][5] = __ldg(M + base + sZm + 1);
+                    mcor[j][6] = __ldg(M + base + sZm + sYm);
+                    mcor[j][7] = __ldg(M + base + sZm + sYm + 1);
+                }
+                const int64_t v = (int64_t)min(z, g.Z - 1) * sZm + (int64_t)y * sYm + x;
+                aux[j] = 0.0f;
+                if (MODE == MODE_MSE || MODE == MODE_NCC)
+                    aux[j] = __ldg(F + v);
+
+            }
+#pragma unroll
+            for (int j = 0; j < C::VC; ++j) {
+                const int pz = p0 + j;
+                if (pz >= DELTA)
+                    break;
+                const int z = zl0 + pz;
+                if (z >= g.Z)
+                    break;
+                Interp ip;
+                if constexpr (D == 3)
+                    ip = interp8(mcor[j], fx[j], fy[j], fz[j]);
+                else
+                    ip = interp4(mcor[j], fx[j], fy[j]);
+                const int64_t v = (int64_t)z * sZm + (int64_t)y * sYm + x;
+                if (MODE == MODE_FWD) {
+                    W_out[v] = inb[j] ? ip.v : 0.0f;
+                    m_out[v] = inb[j] ? 1 : 0;
+                    if (G_io) {
+                        G_io[v] = inb[j] ? ip.gx : 0.0f;
+                        G_io[g.nv + v] = inb[j] ? ip.gy : 0.0f;
+                        if (D == 3)
+                            G_io[2 * (int64_t)g.nv + v] = inb[j] ? ip.gz : 0.0f;
+                    }
+                } else if (inb[j]) {
+                    const float gr[3] = {ip.gx, ip.gy, ip.gz};
+                    float vch[CHS];
+                    if (MODE == MODE_MSE) {
+                        const float d = ip.v - aux[j];
+                        mom[0] = fmaf(d, d, mom[0]);
+                        mom[1] += 1.0f;
+#pragma unroll
+                        for (int i = 0; i < D; ++i)
+                            vch[i] = d * gr[i];
+                    } else if (MODE == MODE_NCC) {
+                        const float f = aux[j], w = ip.v;
+                        mom[0] += 1.0f;
+                        mom[1] += f;
+                        mom[2] += w;
+                        mom[3] = fmaf(f, f, mom[3]);
+                        mom[4] = fmaf(w, w, mom[4]);
+                        mom[5] = fmaf(f, w, mom[5]);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            vch[i] = f * gr[i];
+                            vch[D + i] = w * gr[i];
+                            vch[2 * D + i] = gr[i];
+                        }
+                    }
+                    if (D == 3) {
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int k = 0; k < CHS; ++k)
+                                qz[a][k] = fmaf(kW.w[pz][a], vch[k], qz[a][k]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < CHS; ++k)
+                            qz[0][k] += vch[k];
+                    }
+                }
+            }
+        }
+        }  // MODE != MODE_GW
+    }
+    if (MODE != MODE_FWD) {
+        // the last four planes (a single plane in 2D)
+#pragma unroll
+        for (int a = 0; a < (D == 3 ? 4 : 1); ++a)
+            flush((D == 3 ? C::BCZ - 1 : 0) + a, qz[a]);
     }
     if (C::NMOM > 0) {
-        double m[C::NMOM > 0 ? C::NMOM : 1];
+        double mm[C::NMOM > 0 ? C::NMOM : 1];
 #pragma unroll
         for (int k = 0; k < (C::NMOM > 0 ? C::NMOM : 1); ++k)
-            m[k] = mom[k];
-        block_reduce_d<(C::NMOM > 0 ? C::NMOM : 1)>(m, red);
+            mm[k] = mom[k];
+        block_reduce_d<(C::NMOM > 0 ? C::NMOM : 1)>(mm, red);
         if (tid == 0)
             for (int k = 0; k < C::NMOM; ++k)
-                mpart[(int64_t)brick * C::NMOM + k] = m[k];
+                mpart[(int64_t)brick * C::NMOM + k] = mm[k];
     }
 }
 
@@ -592,26 +671,15 @@ __global__ void k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, double la
 
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t scal, rpart, gR, bpart, mpart, Wb, mb, gb, lpart, coef, total;
+    size_t scal, rpart, gR, bpart, mpart, Wb, mb, gb, lpart, coef, Gb, total;
     int nbricks, gbx, gby, gbz, ngram, nlcc;
 };
-
-template <int D, int DELTA, int MODE>
-void brick_grid(const Grid &g, int &gbx, int &gby, int &gbz)
-{
-    using C = FCfg<D, DELTA, MODE>;
-    const int cx = (g.X + DELTA - 1) / DELTA, cy = (g.Y + DELTA - 1) / DELTA;
-    const int cz = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
-    gbx = (cx + C::BCX - 1) / C::BCX;
-    gby = (cy + C::BCY - 1) / C::BCY;
-    gbz = (cz + C::BCZ - 1) / C::BCZ;
-}
 
 Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
 {
     Layout o{};
     const int D = g.ndim;
-    const int BCX = 8, BCY = 4, BCZ = (D == 3) ? 4 : 1;
+    const int BCX = brick_bcx(L.delta), BCY = brick_bcy(L.delta), BCZ = brick_bcz(D);
     const int cx = (g.X + L.delta - 1) / L.delta, cy = (g.Y + L.delta - 1) / L.delta;
     const int cz = (D == 3) ? (g.Z + L.delta - 1) / L.delta : 1;
     o.gbx = (cx + BCX - 1) / BCX;
@@ -648,6 +716,8 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
         off += align256((size_t)o.nlcc * 2 * 8);
         o.coef = off;
         off += lcc_coef_bytes(g);
+        o.Gb = off;
+        off += align256((size_t)g.nv * D * 4);
     }
     o.total = off;
     return o;
@@ -656,7 +726,7 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
 template <int D, int DELTA, int MODE>
 cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay, char *ws,
                              const float *F, const float *M, const float *c, const float *gw,
-                             float *Wo, uint8_t *mo, cudaStream_t s)
+                             float *Wo, uint8_t *mo, float *G, cudaStream_t s)
 {
     using C = FCfg<D, DELTA, MODE>;
     dim3 grid(lay.gbx, lay.gby, lay.gbz);
@@ -672,7 +742,7 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
             return e;
     }
     k_fused<D, DELTA, MODE><<<grid, C::THREADS, C::dyn_smem, s>>>(
-        g, L, F, M, c, gw, Wo, mo, (float *)(ws + lay.bpart),
+        g, L, F, M, c, gw, Wo, mo, G, (float *)(ws + lay.bpart),
         (double *)(ws + lay.mpart));
     return cudaGetLastError();
 }
@@ -703,15 +773,18 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     int mode;
     if (kind == 0) {
         mode = MODE_MSE;
-        e = run_fused_kernel<D, DELTA, MODE_MSE>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr, s);
+        e = run_fused_kernel<D, DELTA, MODE_MSE>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr,
+                                                 nullptr, s);
     } else if (kind == 1) {
         mode = MODE_NCC;
-        e = run_fused_kernel<D, DELTA, MODE_NCC>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr, s);
+        e = run_fused_kernel<D, DELTA, MODE_NCC>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr,
+                                                 nullptr, s);
     } else {
         mode = 2;
         float *Wb = (float *)(ws + lay.Wb), *gb = (float *)(ws + lay.gb);
         uint8_t *mb = (uint8_t *)(ws + lay.mb);
-        e = run_fused_kernel<D, DELTA, MODE_FWD>(g, L, lay, ws, F, M, c, nullptr, Wb, mb, s);
+        float *Gb = gc ? (float *)(ws + lay.Gb) : nullptr;
+        e = run_fused_kernel<D, DELTA, MODE_FWD>(g, L, lay, ws, F, M, c, nullptr, Wb, mb, Gb, s);
         if (e != cudaSuccess)
             return e;
         e = launch_lcc(g, window, eps, F, Wb, mb, gc ? gb : nullptr, (double *)(ws + lay.lpart),
@@ -719,7 +792,8 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
         if (e != cudaSuccess)
             return e;
         if (gc)
-            e = run_fused_kernel<D, DELTA, MODE_GW>(g, L, lay, ws, F, M, c, gb, nullptr, nullptr, s);
+            e = run_fused_kernel<D, DELTA, MODE_GW>(g, L, lay, ws, F, M, c, gb, nullptr, nullptr,
+                                                    Gb, s);
     }
     if (e != cudaSuccess)
         return e;
@@ -737,12 +811,13 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
             nb = 152 * 16;
         const float *bp = (const float *)(ws + lay.bpart);
         ProfScope ps(s, "k_ctrl");
+        constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
         if (kind == 1)
-            k_ctrl<D, 3 * D, 8, 4, (D == 3 ? 4 : 1)><<<(int)nb, th, 0, s>>>(
-                L, lay.gbx, lay.gby, lay.gbz, mode, lambda, bp, scal, gR, gc);
+            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz,
+                                                                  mode, lambda, bp, scal, gR, gc);
         else
-            k_ctrl<D, D, 8, 4, (D == 3 ? 4 : 1)><<<(int)nb, th, 0, s>>>(
-                L, lay.gbx, lay.gby, lay.gbz, mode, lambda, bp, scal, gR, gc);
+            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz, mode,
+                                                              lambda, bp, scal, gR, gc);
         e = cudaGetLastError();
     }
     return e;

@@ -24,8 +24,8 @@
 // are taken directly from the ring (relative to the column's centre value),
 // then merged along x and along y with the conversion above. It writes
 // (a', b, c) per voxel and per-block {sum rho, count} partials.
-// k_lcc_grad: plain box sums of (a', b, c) (z through a ring of x/y sums)
-// and dS/dW * |X_m| on the mask.
+// k_lcc_grad: plain box sums of (a', b, c) (stored as float4 per voxel; z
+// through a register ring of x/y sums) and dS/dW * |X_m| on the mask.
 #include "launch.h"
 #include "profile.h"
 
@@ -51,17 +51,14 @@ struct LccA {
 
 template <int D, int R>
 struct LccB {
-    static constexpr int TX = 32, TY = 16;
+    static constexpr int TX = 32, TY = 16;  // one thread per core column
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
     static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
     static constexpr int ZC = (D == 3) ? 32 : 1;
-    static constexpr int THREADS = 512;
+    static constexpr int THREADS = NC;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;
-    static constexpr int KC = (NC + THREADS - 1) / THREADS;
-    static constexpr int oL = 0, oX = oL + 3 * NL, oQ = oX + 3 * NX;
-    static constexpr int total = oQ + NR * 3 * NC;
-    static constexpr size_t smem = (size_t)total * 4;
+    static constexpr size_t smem = (size_t)(NL + NX) * sizeof(float4);
 };
 
 // Merge of a partial window (sums t1f,t1w,t2f,t2w,tfw relative to its centre
@@ -119,7 +116,7 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
                     const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
                     pm[k] = __ldg(m + v);
                     pf[k] = __ldg(F + v);
-                    pw[k] = pm[k] ? __ldg(W + v) : 0.0f;
+                    pw[k] = __ldg(W + v);  // masked when staged (no dependent load)
                 }
             }
         }
@@ -134,7 +131,7 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
             const int e = tid + k * C::THREADS;
             if (e < NL) {
                 rF[slot * NL + e] = pf[k];
-                rW[slot * NL + e] = pw[k];
+                rW[slot * NL + e] = pm[k] ? pw[k] : 0.0f;
                 rM[slot * NL + e] = pm[k];
             }
         }
@@ -255,11 +252,8 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
                         rho_sum += rho;
                         cnt += 1.0f;
                     }
-                    if (coef) {
-                        coef[vv[h]] = ca;
-                        coef[g.nv + vv[h]] = cb;
-                        coef[2 * (int64_t)g.nv + vv[h]] = cc;
-                    }
+                    if (coef)
+                        reinterpret_cast<float4 *>(coef)[vv[h]] = make_float4(ca, cb, cc, 0.0f);
                 }
             }
         }
@@ -275,131 +269,183 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
     }
 }
 
+// Mask, F and W of the thread's core voxel in the next output slice.
+struct CoreVox {
+    uint8_t m;
+    float f, w;
+};
+
+// One slice step of k_lcc_grad. The thread owns core column (tx, ty); P is
+// the ring slot of slice zi (compile time, so the ring stays in registers).
+template <int D, int R, int P>
+__device__ __forceinline__ void lcc_grad_step(const Grid &g, int zi, int zc0, int x0, int y0,
+                                              const float4 *__restrict__ coef,
+                                              const float *__restrict__ F,
+                                              const float *__restrict__ W,
+                                              const uint8_t *__restrict__ m,
+                                              float *__restrict__ gout, float4 *L4, float4 *X4,
+                                              float4 (&pq)[LccB<D, R>::KL], float3 (&ring)[LccB<D, R>::NR],
+                                              CoreVox &core, int zi_end)
+{
+    using C = LccB<D, R>;
+    constexpr int NL = C::NL, LX = C::LX, TX = C::TX, NR = C::NR, W1 = C::W1;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+    // stage slice zi (prefetched), then start fetching zi + 1
+#pragma unroll
+    for (int k = 0; k < C::KL; ++k) {
+        const int e = tid + k * C::THREADS;
+        if (e < NL)
+            L4[e] = pq[k];
+    }
+    if (zi + 1 < zi_end) {
+        const int zn = zi + 1;
+        const bool zin = zn >= 0 && zn < g.Z;
+#pragma unroll
+        for (int k = 0; k < C::KL; ++k) {
+            const int e = tid + k * C::THREADS;
+            pq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < NL) {
+                const int ly = e / LX, lx = e - ly * LX;
+                const int x = x0 - R + lx, y = y0 - R + ly;
+                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y)
+                    pq[k] = __ldg(coef + (int64_t)zn * sZ + (int64_t)y * sY + x);
+            }
+        }
+    }
+    // the core voxel of the output slice zo = zi - RZ (fetched one step ago);
+    // start fetching the core voxel of the next output slice
+    const int zo = zi - C::RZ;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool out = zo >= zc0 && x < g.X && y < g.Y;
+    const int64_t vo = (int64_t)zo * sZ + (int64_t)y * sY + x;
+    const uint8_t mo = core.m;
+    const float fo = core.f, wo = core.w;
+    if (zo + 1 >= zc0 && zo + 1 < zi_end - C::RZ && x < g.X && y < g.Y) {
+        const int64_t vn = vo + sZ;
+        core.m = __ldg(m + vn);
+        core.f = __ldg(F + vn);
+        core.w = __ldg(W + vn);
+    }
+    __syncthreads();
+    // x box sums: rows ty and ty + TY (halo rows) of the load region
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int ly = ty + h * C::TY;
+        if (ly < C::LY) {
+            const float4 *src = L4 + ly * LX + tx;
+            float a = 0.f, b = 0.f, c = 0.f;
+#pragma unroll
+            for (int d = 0; d < W1; ++d) {
+                const float4 q = src[d];
+                a += q.x;
+                b += q.y;
+                c += q.z;
+            }
+            X4[ly * TX + tx] = make_float4(a, b, c, 0.f);
+        }
+    }
+    __syncthreads();
+    // y box sum of this column: this slice's entry of the z ring
+    {
+        float a = 0.f, b = 0.f, c = 0.f;
+#pragma unroll
+        for (int d = 0; d < W1; ++d) {
+            const float4 q = X4[(ty + d) * TX + tx];
+            a += q.x;
+            b += q.y;
+            c += q.z;
+        }
+        ring[P] = make_float3(a, b, c);
+    }
+    if (out) {
+        float gv = 0.0f;
+        if (mo) {
+            float A = 0.f, B = 0.f, Cc = 0.f;
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                A += ring[t].x;
+                B += ring[t].y;
+                Cc += ring[t].z;
+            }
+            gv = fmaf(2.0f * wo, B, fmaf(fo, Cc, A));
+        }
+        gout[vo] = gv;
+    }
+    __syncthreads();  // L4 / X4 are rewritten by the next step
+}
+
+template <int D, int R, int P>
+__device__ __forceinline__ void lcc_grad_steps(const Grid &g, int zb, int zc0, int x0, int y0,
+                                               const float4 *__restrict__ coef,
+                                               const float *__restrict__ F,
+                                               const float *__restrict__ W,
+                                               const uint8_t *__restrict__ m,
+                                               float *__restrict__ gout, float4 *L4, float4 *X4,
+                                               float4 (&pq)[LccB<D, R>::KL],
+                                               float3 (&ring)[LccB<D, R>::NR], CoreVox &core,
+                                               int zi_end)
+{
+    if constexpr (P < LccB<D, R>::NR) {
+        if (zb + P < zi_end) {
+            lcc_grad_step<D, R, P>(g, zb + P, zc0, x0, y0, coef, F, W, m, gout, L4, X4, pq, ring,
+                                   core, zi_end);
+            lcc_grad_steps<D, R, P + 1>(g, zb, zc0, x0, y0, coef, F, W, m, gout, L4, X4, pq, ring,
+                                        core, zi_end);
+        }
+    }
+}
+
+// dS/dW * |X_m| = A' + 2 W B + F C on the mask, with (A', B, C) the box sums
+// of the coefficients. One thread per core column; x and y box sums through
+// shared memory, the z box sum from a register ring of the last 2R+1 x/y
+// sums (summed directly, no running sums).
 template <int D, int R>
-__global__ void __launch_bounds__(LccB<D, R>::THREADS)
+__global__ void __launch_bounds__(LccB<D, R>::THREADS, 1)
     k_lcc_grad(Grid g, const float *__restrict__ F, const float *__restrict__ W,
-               const uint8_t *__restrict__ m, const float *__restrict__ coef,
+               const uint8_t *__restrict__ m, const float4 *__restrict__ coef,
                float *__restrict__ gout)
 {
     using C = LccB<D, R>;
-    constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
-    extern __shared__ float sm[];
-    float *Lq = sm + C::oL, *Xq = sm + C::oX, *Q = sm + C::oQ;
+    extern __shared__ float4 sm4[];
+    float4 *L4 = sm4, *X4 = sm4 + C::NL;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
     const int zc0 = blockIdx.z * C::ZC, zc1 = min(zc0 + C::ZC, g.Z);
     const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
-
-    float pq[C::KL][3];
-    auto prefetch = [&](int zi) {
-        const bool zin = zi >= 0 && zi < g.Z;
+    float4 pq[C::KL];
+    float3 ring[C::NR];
+#pragma unroll
+    for (int t = 0; t < C::NR; ++t)
+        ring[t] = make_float3(0.f, 0.f, 0.f);
+    const int zs = zc0 - C::RZ, zi_end = zc1 + C::RZ;
+    {
+        const bool zin = zs >= 0 && zs < g.Z;
 #pragma unroll
         for (int k = 0; k < C::KL; ++k) {
             const int e = tid + k * C::THREADS;
-            pq[k][0] = pq[k][1] = pq[k][2] = 0.0f;
-            if (e < NL) {
-                const int ly = e / LX, lx = e - ly * LX;
+            pq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < C::NL) {
+                const int ly = e / C::LX, lx = e - ly * C::LX;
                 const int x = x0 - R + lx, y = y0 - R + ly;
-                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
-                    const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
-                    pq[k][0] = __ldg(coef + v);
-                    pq[k][1] = __ldg(coef + g.nv + v);
-                    pq[k][2] = __ldg(coef + 2 * (int64_t)g.nv + v);
-                }
+                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y)
+                    pq[k] = __ldg(coef + (int64_t)zs * sZ + (int64_t)y * sY + x);
             }
         }
-    };
-    // core voxel values of the output slice, fetched one slice ahead
-    float cf[C::KC], cw[C::KC];
-    uint8_t cm[C::KC];
-    auto prefetch_core = [&](int zo) {
-#pragma unroll
-        for (int k = 0; k < C::KC; ++k) {
-            const int e = tid + k * C::THREADS;
-            cf[k] = cw[k] = 0.0f;
-            cm[k] = 0;
-            const int ty = e / TX, tx = e - ty * TX;
-            const int x = x0 + tx, y = y0 + ty;
-            if (e < NC && zo >= 0 && zo < g.Z && x < g.X && y < g.Y) {
-                const int64_t v = (int64_t)zo * sZ + (int64_t)y * sY + x;
-                cm[k] = __ldg(m + v);
-                if (cm[k]) {
-                    cf[k] = __ldg(F + v);
-                    cw[k] = __ldg(W + v);
-                }
-            }
-        }
-    };
-
-    int slot = 0;
-    const int zi_end = zc1 + C::RZ;
-    prefetch(zc0 - C::RZ);
-    for (int zi = zc0 - C::RZ; zi < zi_end; ++zi) {
-#pragma unroll
-        for (int k = 0; k < C::KL; ++k) {
-            const int e = tid + k * C::THREADS;
-            if (e < NL) {
-                Lq[e] = pq[k][0];
-                Lq[NL + e] = pq[k][1];
-                Lq[2 * NL + e] = pq[k][2];
-            }
-        }
-        const int zo = zi - C::RZ;
-        if (zi + 1 < zi_end)
-            prefetch(zi + 1);
-        if (zo >= zc0)
-            prefetch_core(zo);
-        __syncthreads();
-        for (int e = tid; e < 3 * NX; e += C::THREADS) {
-            const int q = e / NX, r = e - q * NX;
-            const int ly = r / TX, tx = r - ly * TX;
-            const float *src = Lq + q * NL + ly * LX + tx;
-            float s = 0.f;
-#pragma unroll
-            for (int d = 0; d < C::W1; ++d)
-                s += src[d];
-            Xq[e] = s;
-        }
-        __syncthreads();
-        for (int e = tid; e < 3 * NC; e += C::THREADS) {
-            const int q = e / NC, r = e - q * NC;
-            const int ty = r / TX, tx = r - ty * TX;
-            const float *src = Xq + q * NX + ty * TX + tx;
-            float s = 0.f;
-#pragma unroll
-            for (int d = 0; d < C::W1; ++d)
-                s += src[d * TX];
-            Q[(slot * 3 + q) * NC + r] = s;
-        }
-        __syncthreads();
-        if (zo >= zc0) {
-            const int oldest = (slot + 1 == NR) ? 0 : slot + 1;
-#pragma unroll
-            for (int k = 0; k < C::KC; ++k) {
-                const int e = tid + k * C::THREADS;
-                const int ty = e / TX, tx = e - ty * TX;
-                const int x = x0 + tx, y = y0 + ty;
-                if (e >= NC || x >= g.X || y >= g.Y)
-                    continue;
-                float gv = 0.0f;
-                if (cm[k]) {
-                    float A = 0.f, B = 0.f, Cc = 0.f;
-                    int sl = oldest;
-#pragma unroll
-                    for (int t = 0; t < NR; ++t) {
-                        A += Q[(sl * 3 + 0) * NC + e];
-                        B += Q[(sl * 3 + 1) * NC + e];
-                        Cc += Q[(sl * 3 + 2) * NC + e];
-                        sl = (sl + 1 == NR) ? 0 : sl + 1;
-                    }
-                    gv = fmaf(2.0f * cw[k], B, fmaf(cf[k], Cc, A));
-                }
-                gout[(int64_t)zo * sZ + (int64_t)y * sY + x] = gv;
-            }
-        }
-        __syncthreads();
-        slot = (slot + 1 == NR) ? 0 : slot + 1;
     }
+    CoreVox core{0, 0.f, 0.f};
+    {
+        const int x = x0 + tid % C::TX, y = y0 + tid / C::TX;
+        if (x < g.X && y < g.Y) {  // first output slice is zc0
+            const int64_t v = (int64_t)zc0 * sZ + (int64_t)y * sY + x;
+            core.m = __ldg(m + v);
+            core.f = __ldg(F + v);
+            core.w = __ldg(W + v);
+        }
+    }
+    for (int zb = zs; zb < zi_end; zb += C::NR)
+        lcc_grad_steps<D, R, 0>(g, zb, zc0, x0, y0, coef, F, W, m, gout, L4, X4, pq, ring, core,
+                                zi_end);
 }
 
 template <int D, int R>
@@ -428,7 +474,9 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     {
         dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + B::ZC - 1) / B::ZC);
         ProfScope ps(s, "k_lcc_grad");
-        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, F, W, m, coef, gout);
+        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, F, W, m,
+                                                           reinterpret_cast<const float4 *>(coef),
+                                                           gout);
     }
     return cudaGetLastError();
 }
@@ -450,7 +498,7 @@ int lcc_num_blocks(const Grid &g, int window)
     return R == 1 ? lcc_blocks<2, 1>(g) : R == 2 ? lcc_blocks<2, 2>(g) : lcc_blocks<2, 3>(g);
 }
 
-size_t lcc_coef_bytes(const Grid &g) { return ((size_t)g.nv * 3 * 4 + 255) / 256 * 256; }
+size_t lcc_coef_bytes(const Grid &g) { return ((size_t)g.nv * 16 + 255) / 256 * 256; }
 
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,
                        const uint8_t *m, float *gout, double *part, float *coef, cudaStream_t s)

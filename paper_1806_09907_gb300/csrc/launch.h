@@ -37,7 +37,7 @@ cudaError_t launch_similarity(const Grid &g, int kind, int window, double eps, c
 
 // LCC statistics + exact gradient, shared by the unfused similarity and the
 // fused objective: grad_unscaled = dS/dW * |X_m| (nullable; needs `coef`,
-// 3*nv floats of scratch), per-block {sum of rho over masked voxels, masked
+// lcc_coef_bytes(g) of scratch), per-block {sum of rho over masked voxels, masked
 // voxel count} partials (lcc_num_blocks(g, window) blocks).
 int lcc_num_blocks(const Grid &g, int window);
 size_t lcc_coef_bytes(const Grid &g);

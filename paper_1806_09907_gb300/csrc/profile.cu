@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/airgb.h"
+#include "airgb.h"
 #include "profile.h"
 
 namespace airgb {
