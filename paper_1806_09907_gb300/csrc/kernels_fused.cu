@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
             continue;
         const int zl0 = z0 + cz * DELTA;
         if constexpr (MODE == MODE_GW) {
+            static_assert(C::VC >= 1, "the GW layer loads all DELTA slices at once");
             // dS/dW * dM~/dy from memory, all loads of the layer issued first
             float gv[DELTA], gr[DELTA][D];
 #pragma unroll
