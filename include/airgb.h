@@ -74,7 +74,9 @@ typedef enum {
     AL_ERR_BOUNDS = 5,      /* a kernel saw an index out of range (checked builds) */
     AL_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
     AL_ERR_UNSUPPORTED = 7, /* valid but not supported by this build */
-    AL_ERR_WORKSPACE = 8    /* workspace missing or too small */
+    AL_ERR_WORKSPACE = 8,   /* workspace missing or too small */
+    AL_ERR_SCRATCH_LIMIT = 9 /* problem needs more than the built-in scratch of the
+                                allocation-free entry point */
 } al_status;
 
 typedef enum { AL_SIM_MSE = 0, AL_SIM_NCC = 1, AL_SIM_LCC = 2 } al_sim_kind;
@@ -188,6 +190,29 @@ al_status al_objective_grad_unfused(const al_problem *pr, const float *fixed, co
                                     const float *ctrl, double *value_dev, float *grad_ctrl,
                                     void *workspace, size_t workspace_bytes, al_stream stream);
 size_t al_objective_unfused_workspace_bytes(const al_problem *pr);
+
+/* The similarity step A3 for callers that cannot allocate device memory
+ * (the paper has no counterpart: it is a service of this library). Some
+ * hosts cannot provide a workspace: their device memory belongs to another
+ * allocator that must see every allocation (a framework's caching pool, an
+ * embedded runtime that forbids allocation after start-up), or they are
+ * plain C programs without a device allocator. This call takes its scratch
+ * from a fixed array in the library's own device memory,
+ * al_noalloc_scratch_bytes() bytes (4 MiB) held on every GPU that loads the
+ * library until the process exits, and calls no allocating routine.
+ * Arguments and results are those of al_similarity without the workspace.
+ * A problem whose workspace (al_similarity_workspace_bytes) exceeds the
+ * array returns AL_ERR_SCRATCH_LIMIT and launches nothing: MSE and NCC fit
+ * at any size, LCC up to about 250,000 voxels.
+ * All calls on a device share the array and leave their data in it; calls
+ * whose kernels overlap on the GPU race on it, so order them. The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current) and caches it: make it before any stream
+ * capture. */
+al_status al_similarity_noalloc(const al_grid *g, const al_sim_params *p, const float *fixed,
+                                const float *warped, const uint8_t *mask, double *value_dev,
+                                float *grad_warped, al_stream stream);
+size_t al_noalloc_scratch_bytes(void);
 
 /* Synchronise `stream`, then read and clear the current device's kernel
  * error word: AL_OK, AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the

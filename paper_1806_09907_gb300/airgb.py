@@ -31,7 +31,7 @@ EXPORTS = (
     "al_similarity_workspace_bytes", "al_regulariser", "al_regulariser_workspace_bytes",
     "al_objective_grad", "al_objective_workspace_bytes", "al_objective_grad_unfused",
     "al_objective_unfused_workspace_bytes", "al_get_device_error", "al_profile_enable",
-    "al_profile_collect", "al_profile_reset",
+    "al_profile_collect", "al_profile_reset", "al_similarity_noalloc", "al_noalloc_scratch_bytes",
 )
 
 
@@ -94,6 +94,8 @@ def load():
         "al_profile_enable": ([I32], I32),
         "al_profile_collect": ([ctypes.c_char_p, SZ, P(D), P(ctypes.c_int64), I32], I32),
         "al_profile_reset": ([], I32),
+        "al_similarity_noalloc": ([P(al_grid), P(al_sim_params), VP, VP, VP, VP, VP, VP], I32),
+        "al_noalloc_scratch_bytes": ([], SZ),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -259,6 +261,22 @@ def al_similarity(sim, fixed, warped, mask, eps=1e-5, window=7, grad=True, works
     _call("al_similarity", ctypes.byref(g), ctypes.byref(p), _ptr(fixed), _ptr(warped),
           _ptr(mask), _ptr(value), _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
           _stream(stream))
+    return value, gw
+
+
+def al_similarity_noalloc(sim, fixed, warped, mask, eps=1e-5, window=7, grad=True, stream=None):
+    """A3 without a workspace: the library's built-in scratch array is used
+    (for callers that cannot allocate device memory; see the header)."""
+    shape = tuple(fixed.shape)
+    g = make_grid(shape)
+    p = al_sim_params()
+    p.kind = SIM_KINDS[sim] if isinstance(sim, str) else int(sim)
+    p.lcc_window = int(window)
+    p.eps = float(eps)
+    value = torch.empty(2, dtype=torch.float64, device=fixed.device)
+    gw = torch.empty(shape, dtype=torch.float32, device=fixed.device) if grad else None
+    _call("al_similarity_noalloc", ctypes.byref(g), ctypes.byref(p), _ptr(fixed), _ptr(warped),
+          _ptr(mask), _ptr(value), _ptr(gw), _stream(stream))
     return value, gw
 
 

@@ -151,6 +151,7 @@ const char *al_status_string(al_status s)
     case AL_ERR_TIMEOUT: return "device wait timed out";
     case AL_ERR_UNSUPPORTED: return "not supported by this build";
     case AL_ERR_WORKSPACE: return "workspace missing or too small";
+    case AL_ERR_SCRATCH_LIMIT: return "problem too large for the built-in scratch";
     }
     return "unknown status";
 }
