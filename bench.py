@@ -39,16 +39,20 @@ WORKLOAD = ("3D 256x256x160 fp32 CT-like pair (ellipsoids in [-1000,1500] HU + N
             "c ~ N(0, 3^2) voxels; one fused forward+adjoint evaluation per step")
 FLUSH_BYTES = 256 << 20
 
-# Algorithmic HBM bytes per voxel of each kernel of the fused LCC path (the
-# minimum each must move): k_fused_fwd reads M and writes W + mask;
-# k_lcc_stats reads F, W, mask and writes the three LCC coefficients;
-# k_lcc_grad reads them with F, W, mask and writes dS/dW; k_fused_gw reads M
-# and dS/dW; the point-wise fused kernels read F and M. Per-launch
-# control-point traffic is added separately (coefficients in).
-KERNEL_BYTES_PER_VOXEL = {
-    "k_fused_fwd": 9.0, "k_lcc_stats": 21.0, "k_lcc_grad": 25.0, "k_fused_gw": 8.0,
-    "k_fused_mse": 8.0, "k_fused_ncc": 8.0,
+# Roofline of each kernel: the resource that bounds it and its algorithmic
+# work per voxel (the minimum its contract implies, without tiling overhead).
+#  - k_lcc_stats is bound by fp32 issue: window statistics with shift
+#    conversions, 478 flop/voxel (z sums 70, x merge 189, y merge 189,
+#    statistics 30; an FMA counts 2);
+#  - the others by HBM: k_fused_fwd reads M and writes W, mask and dM~/dy
+#    (21 B); k_lcc_grad reads the LCC coefficients (16 B), F, W, mask and
+#    writes dS/dW (29 B); k_fused_gw reads dS/dW and dM~/dy (16 B); the
+#    point-wise fused kernels read F and M (8 B).
+KERNEL_ROOF = {
+    "k_lcc_stats": ("alu", 478.0), "k_lcc_grad": ("hbm", 29.0), "k_fused_fwd": ("hbm", 21.0),
+    "k_fused_gw": ("hbm", 16.0), "k_fused_mse": ("hbm", 8.0), "k_fused_ncc": ("hbm", 8.0),
 }
+SM_COUNT, FP32_LANES = 152, 128
 
 
 def parse():
@@ -171,6 +175,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(local_ms, units_per_rank, world, dist=None, device=None):
+    """Whole-job throughput over `world` replicas: all units processed divided by
+    the slowest rank's time (max over ranks). Returns (units/s, max_ms)."""
+    t = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / (t / 1000.0), t
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -181,6 +197,51 @@ def measured_peaks():
         except (OSError, ValueError):
             pass
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(name, nv):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel's sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh).get(name)
+    except (OSError, ValueError):
+        return None
+    if not t:
+        return None
+    h = hashlib.sha1()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_1806_09907_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes_per_voxel"] * nv if h.hexdigest() == t["sources_sha1"] else None
+
+
+def roofline(dom, nv, clock_info):
+    name, (ms_tot, launches) = dom
+    per_launch_s = ms_tot / max(launches, 1) / 1000.0
+    bound, per_voxel = KERNEL_ROOF.get(name, (None, None))
+    if bound is None:
+        return None
+    traffic = kernel_traffic(name, nv)
+    if bound == "hbm":
+        peaks, src = measured_peaks()
+        achieved = per_voxel * nv / per_launch_s / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        unit, note = "GB/s", f"HBM copy bandwidth, {src}"
+    else:
+        mhz = (clock_info or {}).get("sm_max_mhz") or 2070.0
+        achieved = per_voxel * nv / per_launch_s / 1e12
+        peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+        unit = "TFLOP/s"
+        note = f"fp32 FMA peak derived: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 flop x {mhz:.0f} MHz"
+    out = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak, "traffic": traffic, "peak_source": note,
+           "algorithmic_per_voxel": per_voxel, "launch_ms": per_launch_s * 1000.0}
+    if traffic is not None:
+        out["traffic_gbs"] = traffic / per_launch_s / 1e9
+    return out
 
 
 def run_reference(args, shape):
@@ -278,12 +339,7 @@ def main():
     airgb.profile_enable(False)
     kernels = airgb.profile_collect()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * steps / (total_ms / 1000.0)
+    value, total_ms = aggregate(sum(step_ms), steps, world, pg, dev)
 
     # ---- end to end through the public API with host buffers
     Fh, Mh, ch = (torch.from_numpy(a).pin_memory() for a in (F, M, c))
@@ -308,12 +364,7 @@ def main():
         gh.copy_(g, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * e2e_steps / (e2e_ms / 1000.0)
+    e2e_value, e2e_ms = aggregate(e0.elapsed_time(e1), e2e_steps, world, pg, dev)
     h2d = F.nbytes + M.nbytes + c.nbytes
     d2h = vh.numel() * 8 + gh.numel() * 4
 
@@ -325,20 +376,7 @@ def main():
     # ---- roofline of the dominant kernel
     nv = int(np.prod(shape))
     dom = max(kernels.items(), key=lambda kv: kv[1][0]) if kernels else None
-    peaks, peak_src = measured_peaks()
-    roof = None
-    if dom:
-        name, (ms_tot, launches) = dom
-        per_launch_ms = ms_tot / max(launches, 1)
-        bpv = KERNEL_BYTES_PER_VOXEL.get(name)
-        if bpv is not None:
-            algo_bytes = bpv * nv + (c.nbytes if name.startswith("k_fused") else 0)
-            achieved = algo_bytes / (per_launch_ms / 1000.0) / 1e9
-            peak = float(peaks.get("hbm_gbs", 6800.0))
-            roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
-                    "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": peak_src, "algorithmic_bytes": algo_bytes,
-                    "launch_ms": per_launch_ms}
+    roof = roofline(dom, nv, clock_info) if dom else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, t, depth = oracle_sample(F, M, c, args.sim, args.cpu_budget)

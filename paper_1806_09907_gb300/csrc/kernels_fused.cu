@@ -539,8 +539,6 @@ __global__ void __launch_bounds__(kGramThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Scalars: value = {J, S, R, n_mask}; scal = per-mode coefficients of the
-// projected channels in dS/dc.
 template <int K>
 __device__ void sum_parts(const double *__restrict__ p, int nb, double (&t)[K], double *red)
 {
@@ -554,30 +552,36 @@ __device__ void sum_parts(const double *__restrict__ p, int nb, double (&t)[K], 
     block_reduce_d<K>(t, red);
 }
 
-__global__ void k_finalize(int mode, int64_t nv, double lambda, double eps,
-                           const double *__restrict__ mpart, int nbricks,
-                           const double *__restrict__ rpart, int ngram,
-                           const double *__restrict__ lpart, int nlcc, double *__restrict__ value,
-                           double *__restrict__ scal)
+// Scalars of the objective from the fixed-order sums of the partials:
+// writes {J, S, R, n_mask} to value (when not NULL) and the coefficients of
+// the projected channels in dS/dc to the shared array k[3]. Every thread of
+// the block takes part; k is valid for all threads on return.
+struct Parts {
+    const double *mpart, *rpart, *lpart;
+    int nbricks, ngram, nlcc;
+};
+
+__device__ void objective_scalars(int mode, int64_t nv, double lambda, double eps, const Parts &P,
+                                  double *value, double *k, double *red)
 {
-    __shared__ double red[6 * 32];
     double r[1];
-    sum_parts<1>(rpart, ngram, r, red);
+    sum_parts<1>(P.rpart, P.ngram, r, red);
     const double R = r[0] / (double)nv;
     double S = 0.0, n = 0.0;
     if (mode == MODE_MSE) {
         double t[2];
-        sum_parts<2>(mpart, nbricks, t, red);
+        sum_parts<2>(P.mpart, P.nbricks, t, red);
         if (threadIdx.x == 0) {
             n = t[1];
             S = n > 0.0 ? t[0] / n : 0.0;
-            scal[0] = n > 0.0 ? 2.0 / n : 0.0;
+            k[0] = n > 0.0 ? 2.0 / n : 0.0;
         }
     } else if (mode == MODE_NCC) {
         double t[6];
-        sum_parts<6>(mpart, nbricks, t, red);
+        sum_parts<6>(P.mpart, P.nbricks, t, red);
         if (threadIdx.x == 0) {
             n = t[0];
+            k[0] = k[1] = k[2] = 0.0;
             if (n > 0.0) {
                 const double muf = t[1] / n, muw = t[2] / n;
                 const double cov = t[5] - n * muf * muw;
@@ -587,44 +591,59 @@ __global__ void k_finalize(int mode, int64_t nv, double lambda, double eps,
                 const double sD = sqrt(Dd);
                 S = 1.0 - cov / sD;
                 const double al = -1.0 / sD, be = cov * vf / (Dd * sD);
-                scal[0] = al;
-                scal[1] = be;
-                scal[2] = -al * muf - be * muw;
-            } else {
-                scal[0] = scal[1] = scal[2] = 0.0;
+                k[0] = al;
+                k[1] = be;
+                k[2] = -al * muf - be * muw;
             }
         }
     } else {  // LCC
         double t[2];
-        sum_parts<2>(lpart, nlcc, t, red);
+        sum_parts<2>(P.lpart, P.nlcc, t, red);
         if (threadIdx.x == 0) {
             n = t[1];
             S = n > 0.0 ? 1.0 - t[0] / n : 0.0;
-            scal[0] = n > 0.0 ? 1.0 / n : 0.0;
+            k[0] = n > 0.0 ? 1.0 / n : 0.0;
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && value) {
         value[0] = S + lambda * R;
         value[1] = S;
         value[2] = R;
         value[3] = n;
     }
+    __syncthreads();
+}
+
+// Value only (no gradient requested).
+__global__ void k_finalize(int mode, int64_t nv, double lambda, double eps, Parts P,
+                           double *__restrict__ value)
+{
+    __shared__ double red[6 * 32];
+    __shared__ double k[3];
+    objective_scalars(mode, nv, lambda, eps, P, value, k, red);
 }
 
 // Per control point: fixed-order sum of the partials of the bricks that
 // touch it, channel combination, plus lambda * dR/dc.
+// Every block first evaluates the scalars of the objective (the partial
+// sums are few), block 0 writes {J, S, R, n_mask}.
 template <int D, int CH, int BCX, int BCY, int BCZ>
-__global__ void k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, double lambda,
-                       const float *__restrict__ bpart, const double *__restrict__ scal,
-                       const float *__restrict__ gR, float *__restrict__ gc)
+__global__ void __launch_bounds__(256)
+    k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, int64_t nv, double lambda, double eps,
+           Parts P, const float *__restrict__ bpart, const float *__restrict__ gR,
+           float *__restrict__ gc, double *__restrict__ value)
 {
     constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
     constexpr int NPART = CH * JZ * JY * JX;
+    __shared__ double red[6 * 8];
+    __shared__ double ks[3];
+    objective_scalars(mode, nv, lambda, eps, P, blockIdx.x == 0 ? value : nullptr, ks, red);
     const int64_t total = (int64_t)L.nc;
-    float k0 = (float)scal[0], k1 = 0.f, k2 = 0.f;
+    const float k0 = (float)ks[0];
+    float k1 = 0.f, k2 = 0.f;
     if (CH == 3 * D) {
-        k1 = (float)scal[1];
-        k2 = (float)scal[2];
+        k1 = (float)ks[1];
+        k2 = (float)ks[2];
     }
     const float lam = (float)lambda;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -754,7 +773,6 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
                     float *gc, char *ws, cudaStream_t s)
 {
     const Layout lay = make_layout(g, L, kind, window);
-    double *scal = (double *)(ws + lay.scal);
     double *rpart = (double *)(ws + lay.rpart);
     float *gR = (float *)(ws + lay.gR);
     const float gscale = (float)(2.0 / (double)g.nv);
@@ -798,27 +816,27 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     }
     if (e != cudaSuccess)
         return e;
-    prof_begin(s, "k_finalize");
-    k_finalize<<<1, 1024, 0, s>>>(mode, g.nv, lambda, eps, (double *)(ws + lay.mpart),
-                                  lay.nbricks, rpart, lay.ngram, (double *)(ws + lay.lpart),
-                                  lay.nlcc, value, scal);
-    prof_end(s);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
-    if (gc) {
+    Parts parts{(const double *)(ws + lay.mpart), rpart, (const double *)(ws + lay.lpart),
+                lay.nbricks, lay.ngram, lay.nlcc};
+    if (!gc) {
+        ProfScope ps(s, "k_finalize");
+        k_finalize<<<1, 1024, 0, s>>>(mode, g.nv, lambda, eps, parts, value);
+        return cudaGetLastError();
+    }
+    {
         const int th = 256;
         int64_t nb = ((int64_t)L.nc + th - 1) / th;
-        if (nb > 152 * 16)
-            nb = 152 * 16;
+        if (nb > 152 * 2)
+            nb = 152 * 2;
         const float *bp = (const float *)(ws + lay.bpart);
         ProfScope ps(s, "k_ctrl");
         constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
         if (kind == 1)
-            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz,
-                                                                  mode, lambda, bp, scal, gR, gc);
+            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(
+                L, lay.gbx, lay.gby, lay.gbz, mode, g.nv, lambda, eps, parts, bp, gR, gc, value);
         else
-            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz, mode,
-                                                              lambda, bp, scal, gR, gc);
+            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(
+                L, lay.gbx, lay.gby, lay.gbz, mode, g.nv, lambda, eps, parts, bp, gR, gc, value);
         e = cudaGetLastError();
     }
     return e;

@@ -401,7 +401,7 @@ __device__ __forceinline__ void lcc_grad_steps(const Grid &g, int zb, int zc0, i
 // shared memory, the z box sum from a register ring of the last 2R+1 x/y
 // sums (summed directly, no running sums).
 template <int D, int R>
-__global__ void __launch_bounds__(LccB<D, R>::THREADS, 1)
+__global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
     k_lcc_grad(Grid g, const float *__restrict__ F, const float *__restrict__ W,
                const uint8_t *__restrict__ m, const float4 *__restrict__ coef,
                float *__restrict__ gout)
