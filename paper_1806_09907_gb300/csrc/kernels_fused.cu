@@ -45,10 +45,11 @@ struct FCfg {
     static constexpr int NMOM = (MODE == MODE_MSE) ? 2 : (MODE == MODE_NCC ? 6 : 0);
     static constexpr int NPART = CH * JZ * JY * JX;  // floats of one brick's partials
     static constexpr int VC = (MODE == MODE_FWD) ? 2 : 1;  // slices whose loads are in flight
-    // dynamic shared memory: one plane of column partials P[BY][BX][CHS] and
-    // its x contraction X[BY][JX][CHS]
-    static constexpr int nP = (MODE == MODE_FWD) ? 0 : BY * BX * CHS;
-    static constexpr int nX = (MODE == MODE_FWD) ? 0 : BY * JX * CHS;
+    // dynamic shared memory: up to NPL planes of column partials
+    // P[NPL][BY][BX][CHS] and their x contraction X[NPL][BY][JX][CHS]
+    static constexpr int NPL = (D == 3) ? 4 : 1;
+    static constexpr int nP = (MODE == MODE_FWD) ? 0 : NPL * BY * BX * CHS;
+    static constexpr int nX = (MODE == MODE_FWD) ? 0 : NPL * BY * JX * CHS;
     static constexpr size_t dyn_smem = (size_t)(nP + nX) * sizeof(float);
 };
 
@@ -75,6 +76,69 @@ __device__ __forceinline__ void plane_xy(const float (&cb)[D][JZ][JY][JX], int j
     }
 }
 
+// Planes 0..NPL-1 of the thread's column partials qz -> x contraction -> y
+// contraction -> the brick's partial sums of local planes lp0 .. lp0+NPL-1.
+// Every thread of the block calls it. Cell-wise loops with compile-time
+// bounds and two accumulators per output.
+template <int D, int DELTA, int MODE, int NPL>
+__device__ __forceinline__ void flush_planes(int lp0, const float (&qz)[4][FCfg<D, DELTA, MODE>::CHS],
+                                             bool colvalid, int tx, int ty, float *P, float *Xc,
+                                             const float (*wt)[4], float *dst)
+{
+    using C = FCfg<D, DELTA, MODE>;
+    constexpr int CHS = C::CHS, BX = C::BX, BY = C::BY, JX = C::JX, JY = C::JY, JZ = C::JZ;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int a = 0; a < NPL; ++a)
+#pragma unroll
+        for (int k = 0; k < CHS; ++k)
+            P[((a * BY + ty) * BX + tx) * CHS + k] = colvalid ? qz[a][k] : 0.0f;
+    __syncthreads();
+    for (int e = tid; e < NPL * BY * JX * CHS; e += C::THREADS) {
+        const int k = e % CHS, r0 = e / CHS;
+        const int jxl = r0 % JX, r1 = r0 / JX;
+        const int yy = r1 % BY, a = r1 / BY;
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+            const int q = jxl - e4;
+            if (q >= 0 && q < C::BCX) {
+                const float *src = P + ((a * BY + yy) * BX + q * DELTA) * CHS + k;
+#pragma unroll
+                for (int px = 0; px < DELTA; ++px) {
+                    if (px & 1)
+                        s1 = fmaf(wt[px][e4], src[px * CHS], s1);
+                    else
+                        s0 = fmaf(wt[px][e4], src[px * CHS], s0);
+                }
+            }
+        }
+        Xc[((a * BY + yy) * JX + jxl) * CHS + k] = s0 + s1;
+    }
+    __syncthreads();
+    for (int e = tid; e < NPL * JY * JX * CHS; e += C::THREADS) {
+        const int jxl = e % JX, r0 = e / JX;
+        const int jyl = r0 % JY, r1 = r0 / JY;
+        const int k = r1 % CHS, a = r1 / CHS;
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+            const int q = jyl - e4;
+            if (q >= 0 && q < C::BCY) {
+                const float *src = Xc + ((a * BY + q * DELTA) * JX + jxl) * CHS + k;
+#pragma unroll
+                for (int py = 0; py < DELTA; ++py) {
+                    if (py & 1)
+                        s1 = fmaf(wt[py][e4], src[py * JX * CHS], s1);
+                    else
+                        s0 = fmaf(wt[py][e4], src[py * JX * CHS], s0);
+                }
+            }
+        }
+        dst[(k * JZ + lp0 + a) * JY * JX + jyl * JX + jxl] = s0 + s1;
+    }
+}
+
 template <int D, int DELTA, int MODE>
 __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
                                   (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
@@ -87,7 +151,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
     // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
     // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
     using C = FCfg<D, DELTA, MODE>;
-    constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS, BX = C::BX, BY = C::BY;
+    constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS, BX = C::BX;
     constexpr WTab<DELTA> kW{};  // weights of the compile-time z phases
     __shared__ float cb[D][JZ][JY][JX];
     __shared__ float wt[DELTA][4];
@@ -142,38 +206,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
     for (int k = 0; k < (C::NMOM > 0 ? C::NMOM : 1); ++k)
         mom[k] = 0.0f;
 
-    // one plane of column partials -> x then y contraction -> global partials
-    auto flush = [&](int lp, const float (&vals)[CHS]) {
-#pragma unroll
-        for (int k = 0; k < CHS; ++k)
-            P[(ty * BX + tx) * CHS + k] = colvalid ? vals[k] : 0.0f;
-        __syncthreads();
-        for (int e = tid; e < BY * JX * CHS; e += C::THREADS) {
-            const int yy = e / (JX * CHS), r = e - yy * JX * CHS;
-            const int jxl = r / CHS, k = r - jxl * CHS;
-            const int x_lo = max(0, (jxl - 3) * DELTA), x_hi = min(BX, (jxl + 1) * DELTA);
-            float s = 0.0f;
-            for (int xx = x_lo; xx < x_hi; ++xx) {
-                const int q = xx / DELTA;
-                s = fmaf(wt[xx - q * DELTA][jxl - q], P[(yy * BX + xx) * CHS + k], s);
-            }
-            Xc[(yy * JX + jxl) * CHS + k] = s;
-        }
-        __syncthreads();
-        float *dst = bpart + (int64_t)brick * C::NPART;
-        for (int e = tid; e < JY * JX * CHS; e += C::THREADS) {
-            const int k = e / (JY * JX), r = e - k * JY * JX;
-            const int jyl = r / JX, jxl = r - jyl * JX;
-            const int y_lo = max(0, (jyl - 3) * DELTA), y_hi = min(BY, (jyl + 1) * DELTA);
-            float s = 0.0f;
-            for (int yy = y_lo; yy < y_hi; ++yy) {
-                const int q = yy / DELTA;
-                s = fmaf(wt[yy - q * DELTA][jyl - q], Xc[(yy * JX + jxl) * CHS + k], s);
-            }
-            dst[(k * JZ + lp) * JY * JX + jyl * JX + jxl] = s;
-        }
-    };
-
+    float *const dstp = bpart + (int64_t)brick * C::NPART;
     const int cells_z = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
     const int nlayers = (D == 3) ? min(C::BCZ, cells_z - cz0) : 1;
     const int64_t sYm = g.X, sZm = (int64_t)g.X * g.Y;
@@ -182,7 +215,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
         if (cz > 0) {
             // plane cz - 1 has all its contributions: write it out, roll
             if (MODE != MODE_FWD)
-                flush(cz - 1, qz[0]);
+                flush_planes<D, DELTA, MODE, 1>(cz - 1, qz, colvalid, tx, ty, P, Xc, wt, dstp);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -346,10 +379,9 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
         }  // MODE != MODE_GW
     }
     if (MODE != MODE_FWD) {
-        // the last four planes (a single plane in 2D)
-#pragma unroll
-        for (int a = 0; a < (D == 3 ? 4 : 1); ++a)
-            flush((D == 3 ? C::BCZ - 1 : 0) + a, qz[a]);
+        // the last four planes (a single plane in 2D), together
+        flush_planes<D, DELTA, MODE, C::NPL>(D == 3 ? C::BCZ - 1 : 0, qz, colvalid, tx, ty, P, Xc,
+                                             wt, dstp);
     }
     if (C::NMOM > 0) {
         double mm[C::NMOM > 0 ? C::NMOM : 1];
@@ -369,12 +401,6 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
 //   G[j][j+o] = sum_{x=0}^{N-1} b_j(x) b_{j+o}(x),
 //   H[j][j+o] = sum_{x=0}^{N-2} (b_j(x+1)-b_j(x)) (b_{j+o}(x+1)-b_{j+o}(x)),
 // b_j(x) = w[x mod delta][j - x/delta] when that index is in 0..3, else 0.
-__device__ __forceinline__ float bvalue(const Lattice &L, int j, int x)
-{
-    const int q = x / L.delta, a = j - q;
-    return (a >= 0 && a <= 3) ? L.w[x - q * L.delta][a] : 0.0f;
-}
-
 __device__ void band_entry(const Lattice &L, int N, int n, int j, int o, float &G, float &H)
 {
     const int j2 = j + o;
@@ -382,15 +408,30 @@ __device__ void band_entry(const Lattice &L, int N, int n, int j, int o, float &
     H = 0.0f;
     if (j < 0 || j >= n || j2 < 0 || j2 >= n)
         return;
-    const int lo = max(0, (max(j, j2) - 3) * L.delta - 1);
-    const int hi = min(N, (min(j, j2) + 1) * L.delta + 1);
+    const int delta = L.delta;
+    const int lo = max(0, (max(j, j2) - 3) * delta - 1);
+    const int hi = min(N, (min(j, j2) + 1) * delta + 1);
+    // walk x with its cell q and phase p (no divisions in the loop)
+    int q = lo / delta, p = lo - q * delta;
+    auto b = [&](int jj, int qq, int pp) {
+        const int a = jj - qq;
+        return (a >= 0 && a <= 3) ? L.w[pp][a] : 0.0f;
+    };
+    float bj = b(j, q, p), bj2 = b(j2, q, p);
     for (int x = lo; x < hi; ++x) {
-        const float a = bvalue(L, j, x), b = bvalue(L, j2, x);
-        G = fmaf(a, b, G);
-        if (x + 1 < N) {
-            const float da = bvalue(L, j, x + 1) - a, db = bvalue(L, j2, x + 1) - b;
-            H = fmaf(da, db, H);
+        G = fmaf(bj, bj2, G);
+        int qn = q, pn = p + 1;
+        if (pn == delta) {
+            pn = 0;
+            ++qn;
         }
+        const float nj = b(j, qn, pn), nj2 = b(j2, qn, pn);
+        if (x + 1 < N)
+            H = fmaf(nj - bj, nj2 - bj2, H);
+        bj = nj;
+        bj2 = nj2;
+        q = qn;
+        p = pn;
     }
 }
 
