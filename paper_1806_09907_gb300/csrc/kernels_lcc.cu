@@ -39,7 +39,7 @@ struct LccA {
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
     static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
-    static constexpr int ZC = (D == 3) ? 32 : 1;
+    static constexpr int ZC = (D == 3) ? 16 : 1;
     static constexpr int THREADS = 512;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;  // load elements per thread
     // shared memory: raw F / masked W ring, z sums (5 + 2 centre values),
@@ -55,7 +55,7 @@ struct LccB {
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
     static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
-    static constexpr int ZC = (D == 3) ? 32 : 1;
+    static constexpr int ZC = (D == 3) ? 24 : 1;
     static constexpr int THREADS = NC;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;
     static constexpr size_t smem = (size_t)(NL + NX) * sizeof(float4);
