@@ -212,6 +212,24 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
     const int64_t sYm = g.X, sZm = (int64_t)g.X * g.Y;
     constexpr int NCOR = (D == 3) ? 8 : 4;
     for (int cz = 0; cz < C::BCZ; ++cz) {
+        const bool active = cz < nlayers && colvalid;
+        const int zl0 = z0 + cz * DELTA;
+        // GW: the layer's loads are issued before the flush of the previous
+        // plane, so they are in flight while the block contracts it
+        float gv[MODE == MODE_GW ? DELTA : 1], gr[MODE == MODE_GW ? DELTA : 1][D];
+        if constexpr (MODE == MODE_GW) {
+            if (active) {
+#pragma unroll
+                for (int pz = 0; pz < DELTA; ++pz) {
+                    const int z = min(zl0 + pz, g.Z - 1);
+                    const int64_t v = (int64_t)z * sZm + (int64_t)y * sYm + x;
+                    gv[pz] = __ldg(gw_in + v);
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        gr[pz][i] = __ldg(G_io + (int64_t)i * g.nv + v);
+                }
+            }
+        }
         if (cz > 0) {
             // plane cz - 1 has all its contributions: write it out, roll
             if (MODE != MODE_FWD)
@@ -231,22 +249,10 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
             if (MODE != MODE_GW)
                 plane_xy<D, JZ, JY, JX>(cb, cz + 3, qyl, qxl, wx, wy, cxy[3]);
         }
-        if (cz >= nlayers || !colvalid)
+        if (!active)
             continue;
-        const int zl0 = z0 + cz * DELTA;
         if constexpr (MODE == MODE_GW) {
             static_assert(C::VC >= 1, "the GW layer loads all DELTA slices at once");
-            // dS/dW * dM~/dy from memory, all loads of the layer issued first
-            float gv[DELTA], gr[DELTA][D];
-#pragma unroll
-            for (int pz = 0; pz < DELTA; ++pz) {
-                const int z = min(zl0 + pz, g.Z - 1);
-                const int64_t v = (int64_t)z * sZm + (int64_t)y * sYm + x;
-                gv[pz] = __ldg(gw_in + v);
-#pragma unroll
-                for (int i = 0; i < D; ++i)
-                    gr[pz][i] = __ldg(G_io + (int64_t)i * g.nv + v);
-            }
 #pragma unroll
             for (int pz = 0; pz < DELTA; ++pz) {
                 if (zl0 + pz >= g.Z)
