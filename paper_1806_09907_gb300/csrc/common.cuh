@@ -98,6 +98,23 @@ __device__ __forceinline__ bool axis_sample(int x, float u, int n, AxisSample &s
     return true;
 }
 
+// Branch-free form of axis_sample for kernels that load the cell whatever
+// the mask: cell is always in [0, n-2] (so the loads stay in bounds) and,
+// when the sample is inside, equals axis_sample's cell with f its offset
+// (f = 1 on the last face). Returns whether the sample is inside.
+__device__ __forceinline__ bool axis_cell(int x, float u, int n, int &cell, float &f)
+{
+    const float fl = floorf(u);
+    const bool fin = fabsf(fl) < 1.0e9f;  // false for NaN and infinities
+    const int iy = fin ? x + (int)fl : -1;
+    const float fr = u - fl;
+    const bool in = fin && iy >= 0 && (iy < n - 1 || (iy == n - 1 && fr == 0.0f));
+    const int c = min(max(iy, 0), n - 2);
+    cell = c;
+    f = fr + (float)(iy - c);  // iy - c is 1 on the last face, else 0 when inside
+    return in;
+}
+
 // Linear interpolation value and gradient in a 3D cell: corners m[z][y][x].
 struct Interp {
     float v, gx, gy, gz;

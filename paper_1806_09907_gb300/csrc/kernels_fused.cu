@@ -290,34 +290,29 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
                     v = fmaf(kW.w[pz][3], cxy[3][i], v);
                     uu[i] = (D == 3) ? v : cxy[0][i];
                 }
-                AxisSample sx{0, 0.f}, sy{0, 0.f}, sz{0, 0.f};
-                bool in = axis_sample(x, uu[0], g.X, sx);
-                in &= axis_sample(y, uu[1], g.Y, sy);
+                // cells are clamped into the volume even outside the mask, so
+                // every load is in bounds; the values outside are not used
+                int cx, cy, cz = 0;
+                bool in = axis_cell(x, uu[0], g.X, cx, fx[j]);
+                in &= axis_cell(y, uu[1], g.Y, cy, fy[j]);
                 if (D == 3)
-                    in &= axis_sample(z, uu[2], g.Z, sz);
-                in &= (z < g.Z);
-                if (!in)  // any in-volume cell; its values are not used
-                    sx.cell = sy.cell = sz.cell = 0;
-                inb[j] = in;
-                fx[j] = sx.f;
-                fy[j] = sy.f;
-                fz[j] = sz.f;
-                const int64_t base = (D == 3 ? (int64_t)sz.cell * sZm : 0) +
-                                     (int64_t)sy.cell * sYm + sx.cell;
-                mcor[j][0] = __ldg(M + base);
-                mcor[j][1] = __ldg(M + base + 1);
-                mcor[j][2] = __ldg(M + base + sYm);
-                mcor[j][3] = __ldg(M + base + sYm + 1);
+                    in &= axis_cell(z, uu[2], g.Z, cz, fz[j]);
+                inb[j] = in && (z < g.Z);
+                const float *mp = M + ((D == 3 ? cz * g.Y : 0) + cy) * g.X + cx;  // nv < 2^31
+                mcor[j][0] = __ldg(mp);
+                mcor[j][1] = __ldg(mp + 1);
+                mcor[j][2] = __ldg(mp + g.X);
+                mcor[j][3] = __ldg(mp + g.X + 1);
                 if constexpr (D == 3) {
-                    mcor[j][4] = __ldg(M + base + sZm);
-                    mcor[j][5] = __ldg(M + base + sZm + 1);
-                    mcor[j][6] = __ldg(M + base + sZm + sYm);
-                    mcor[j][7] = __ldg(M + base + sZm + sYm + 1);
+                    const int sxy = g.X * g.Y;
+                    mcor[j][4] = __ldg(mp + sxy);
+                    mcor[j][5] = __ldg(mp + sxy + 1);
+                    mcor[j][6] = __ldg(mp + sxy + g.X);
+                    mcor[j][7] = __ldg(mp + sxy + g.X + 1);
                 }
-                const int64_t v = (int64_t)min(z, g.Z - 1) * sZm + (int64_t)y * sYm + x;
                 aux[j] = 0.0f;
                 if (MODE == MODE_MSE || MODE == MODE_NCC)
-                    aux[j] = __ldg(F + v);
+                    aux[j] = __ldg(F + (min(z, g.Z - 1) * g.Y + y) * g.X + x);
 
             }
 #pragma unroll
@@ -333,7 +328,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
                     ip = interp8(mcor[j], fx[j], fy[j], fz[j]);
                 else
                     ip = interp4(mcor[j], fx[j], fy[j]);
-                const int64_t v = (int64_t)z * sZm + (int64_t)y * sYm + x;
+                const int v = (z * g.Y + y) * g.X + x;
                 if (MODE == MODE_FWD) {
                     W_out[v] = inb[j] ? ip.v : 0.0f;
                     m_out[v] = inb[j] ? 1 : 0;
@@ -341,7 +336,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
                         G_io[v] = inb[j] ? ip.gx : 0.0f;
                         G_io[g.nv + v] = inb[j] ? ip.gy : 0.0f;
                         if (D == 3)
-                            G_io[2 * (int64_t)g.nv + v] = inb[j] ? ip.gz : 0.0f;
+                            G_io[2 * g.nv + v] = inb[j] ? ip.gz : 0.0f;
                     }
                 } else if (inb[j]) {
                     const float gr[3] = {ip.gx, ip.gy, ip.gz};
