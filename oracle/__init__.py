@@ -59,9 +59,13 @@ def _load():
     lib.alref_objective_grad.argtypes = [ci, i64p, ci, ci, ci, cd, cd, dp, dp, dp, dp, dp]
     lib.alref_objective_grad_ex.argtypes = [ci, i64p, ci, ci, ci, cd, cd, dp, dp, dp, dp, dp, dp,
                                             dp]
+    lib.alref_adam_step.argtypes = [ci, i64p, ci, cd, cd, cd, cd, ctypes.c_int64, dp, dp, dp, dp]
+    lib.alref_pyramid_level.argtypes = [ci, i64p, dp, ci, dp]
+    lib.alref_bspline_refine.argtypes = [ci, i64p, i64p, ci, dp, dp]
     for name in ("alref_lattice_size", "alref_displacement", "alref_displacement_adjoint",
                  "alref_warp", "alref_mse", "alref_ncc", "alref_lcc", "alref_diffusion",
-                 "alref_objective_grad", "alref_objective_grad_ex"):
+                 "alref_objective_grad", "alref_objective_grad_ex", "alref_adam_step",
+                 "alref_pyramid_level", "alref_bspline_refine"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -196,3 +200,45 @@ def objective_grad(kind, fixed, moving, ctrl, delta, lam, eps=1e-5, window=7, gr
     if intermediates:
         vals["u"], vals["dS_dW"] = u, gw
     return vals, gc
+
+
+def adam_step(shape, delta, ctrl, grad, m, v, step, lr=0.01, betas=(0.9, 0.999), eps=1e-8):
+    """One Adam step on the control points in normalised units (Sec. II-A,
+    Optimization; Kingma and Ba's update). Returns new (ctrl, m, v) arrays."""
+    nd, N = _grid(shape)
+    c, g, mm, vv = _d(ctrl).copy(), _d(grad), _d(m).copy(), _d(v).copy()
+    want = (nd,) + lattice_shape(shape, delta)
+    assert c.shape == want and g.shape == want and mm.shape == want and vv.shape == want
+    _check(_load().alref_adam_step(nd, _p(N, ctypes.c_int64), int(delta), float(lr),
+                                   float(betas[0]), float(betas[1]), float(eps), int(step),
+                                   _p(c), _p(g), _p(mm), _p(vv)), "adam_step")
+    return c, mm, vv
+
+
+def level_shape(shape, factor):
+    """Grid of a pyramid level: every factor-th voxel from voxel 0."""
+    return tuple((n - 1) // factor + 1 for n in shape)
+
+
+def pyramid_level(image, factor):
+    """Gaussian-smoothed (sigma = factor/2, |t| <= 3 sigma, clamped edges),
+    subsampled image of one pyramid level (Sec. IV-A, multi-resolution)."""
+    im = _d(image)
+    nd, N = _grid(im.shape)
+    out = np.zeros(level_shape(im.shape, factor), dtype=np.float64)
+    _check(_load().alref_pyramid_level(nd, _p(N, ctypes.c_int64), _p(im), int(factor), _p(out)),
+           "pyramid_level")
+    return out
+
+
+def bspline_refine(coarse_shape, fine_shape, delta, ctrl_coarse):
+    """Fine-level coefficients whose displacement equals the coarse one
+    (two-scale relation of the cubic B-spline), in fine voxel units."""
+    nd, Nc = _grid(coarse_shape)
+    _, Nf = _grid(fine_shape)
+    c = _d(ctrl_coarse)
+    assert c.shape == (nd,) + lattice_shape(coarse_shape, delta), c.shape
+    out = np.zeros((nd,) + lattice_shape(fine_shape, delta), dtype=np.float64)
+    _check(_load().alref_bspline_refine(nd, _p(Nc, ctypes.c_int64), _p(Nf, ctypes.c_int64),
+                                        int(delta), _p(c), _p(out)), "bspline_refine")
+    return out

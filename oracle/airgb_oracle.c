@@ -562,3 +562,161 @@ done:
     free(u), free(w), free(gy), free(gw), free(gu), free(m);
     return st;
 }
+
+/* ======================================================================== */
+/* The optimisation loop around the objective: Adam on the control points,  */
+/* the Gaussian image pyramid of a multi-resolution registration and the    */
+/* dyadic refinement of the B-spline coefficients between its levels.       */
+/* ======================================================================== */
+
+/* One Adam step (Sec. II-A, Optimization, and Sec. III-G name Adam; the
+ * update is the one Kingma and Ba define) on the control coefficients.
+ * Reading: the step size lr is in the paper's normalised coordinates
+ * (Sec. III-C, Image Warping: the image spans [-1, 1] per axis), so Adam runs
+ * on c~_k = c_k * 2/(N_k - 1); ctrl and grad are in voxel units and m, v hold
+ * the moments of the normalised gradient dJ/dc~_k = dJ/dc_k * (N_k - 1)/2.
+ * With t = step (>= 1):
+ *   m <- beta1 m + (1 - beta1) g~,  v <- beta2 v + (1 - beta2) g~^2
+ *   c~ <- c~ - lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)
+ */
+int alref_adam_step(int ndim, const int64_t *N, int delta, double lr, double beta1, double beta2,
+                    double eps, int64_t step, double *ctrl, const double *grad, double *m,
+                    double *v)
+{
+    int64_t n[3];
+    if (alref_lattice_size(ndim, N, delta, n) || step < 1)
+        return ALREF_ERR_ARG;
+    const int64_t nc = n[0] * n[1] * n[2];
+    const double bc1 = 1.0 - pow(beta1, (double)step);
+    const double bc2 = 1.0 - pow(beta2, (double)step);
+    for (int i = 0; i < ndim; ++i) {
+        const double to_norm = 2.0 / (double)(N[i] - 1); /* voxel -> normalised */
+        for (int64_t j = 0; j < nc; ++j) {
+            const int64_t e = i * nc + j;
+            const double g = grad[e] / to_norm; /* dJ/dc~ */
+            m[e] = beta1 * m[e] + (1.0 - beta1) * g;
+            v[e] = beta2 * v[e] + (1.0 - beta2) * g * g;
+            const double mhat = m[e] / bc1, vhat = v[e] / bc2;
+            double cn = ctrl[e] * to_norm;
+            cn -= lr * mhat / (sqrt(vhat) + eps);
+            ctrl[e] = cn / to_norm;
+        }
+    }
+    return ALREF_OK;
+}
+
+/* Output size of a pyramid level along one axis: the points 0, f, 2f, ...
+ * of the finer grid. */
+static int64_t level_size(int64_t Nk, int factor) { return (Nk - 1) / factor + 1; }
+
+/* One level of the Gaussian image pyramid used by the multi-resolution
+ * strategy of Sec. IV-A (FFD item); the paper gives no filter, so the
+ * reading is: factor f = 1 is the image itself; for f >= 2 the image is
+ * smoothed by a Gaussian of sigma = f/2 voxels, truncated to the taps with
+ * |t| <= 3 sigma and normalised to unit sum, with indices clamped to the
+ * grid, and sampled at every f-th voxel starting at voxel 0 on each active
+ * axis. Computed as the full d-dimensional sum of the product kernel at
+ * every output point. out: level_size per active axis. */
+int alref_pyramid_level(int ndim, const int64_t *N, const double *image, int factor, double *out)
+{
+    if ((ndim != 2 && ndim != 3) || factor < 1 || factor > 8)
+        return ALREF_ERR_ARG;
+    int64_t M[3];
+    for (int k = 0; k < 3; ++k) {
+        if (k < ndim ? N[k] < 2 : N[k] != 1)
+            return ALREF_ERR_ARG;
+        M[k] = k < ndim ? level_size(N[k], factor) : 1;
+    }
+    if (factor == 1) {
+        memcpy(out, image, sizeof(double) * nvox(N));
+        return ALREF_OK;
+    }
+    const double sigma = factor / 2.0;
+    const int r = (int)floor(3.0 * sigma);
+    double w[64];
+    double wsum = 0.0;
+    for (int t = -r; t <= r; ++t) {
+        w[t + r] = exp(-(double)(t * t) / (2.0 * sigma * sigma));
+        wsum += w[t + r];
+    }
+    for (int t = -r; t <= r; ++t)
+        w[t + r] /= wsum;
+    const int rz = ndim == 3 ? r : 0;
+    for (int64_t oz = 0; oz < M[2]; ++oz)
+        for (int64_t oy = 0; oy < M[1]; ++oy)
+            for (int64_t ox = 0; ox < M[0]; ++ox) {
+                double s = 0.0;
+                for (int tz = -rz; tz <= rz; ++tz) {
+                    int64_t z = oz * factor + tz;
+                    z = z < 0 ? 0 : (z > N[2] - 1 ? N[2] - 1 : z);
+                    const double wz = ndim == 3 ? w[tz + r] : 1.0;
+                    for (int ty = -r; ty <= r; ++ty) {
+                        int64_t y = oy * factor + ty;
+                        y = y < 0 ? 0 : (y > N[1] - 1 ? N[1] - 1 : y);
+                        for (int tx = -r; tx <= r; ++tx) {
+                            int64_t x = ox * factor + tx;
+                            x = x < 0 ? 0 : (x > N[0] - 1 ? N[0] - 1 : x);
+                            s += wz * w[ty + r] * w[tx + r] * image[(z * N[1] + y) * N[0] + x];
+                        }
+                    }
+                }
+                out[(oz * M[1] + oy) * M[0] + ox] = s;
+            }
+    return ALREF_OK;
+}
+
+/* Two-scale coefficient of the cubic B-spline: beta3(x) =
+ * sum_o h(o) beta3(2x - o) with h = (1, 4, 6, 4, 1)/8 for o = -2..2. */
+static double two_scale(int64_t o)
+{
+    switch (o) {
+    case -2: case 2: return 1.0 / 8.0;
+    case -1: case 1: return 4.0 / 8.0;
+    case 0: return 6.0 / 8.0;
+    default: return 0.0;
+    }
+}
+
+/* Coefficients on the finer level of the pyramid from those of the coarser
+ * one, such that the fine displacement equals the coarse one exactly
+ * (Sec. IV-A, multi-resolution; the transfer is a reading). The coarse grid
+ * is the fine grid sampled at every second voxel, both lattices have the same
+ * spacing delta in their own voxels, so a coarse basis function is a fine
+ * one dilated by 2 and, by the two-scale relation, a sum of five fine basis
+ * functions: fine point i sits at (i - 1) delta fine voxels and coarse point
+ * j at 2 (j - 1) delta, hence
+ *   c_fine[i] = 2 * sum_j prod_k h((i_k - 1) - 2 (j_k - 1)) c_coarse[j]
+ * (the factor 2 converts coarse voxel units to fine ones). Every fine
+ * coefficient is the full sum over the coarse lattice. */
+int alref_bspline_refine(int ndim, const int64_t *Nc, const int64_t *Nf, int delta,
+                         const double *c_coarse, double *c_fine)
+{
+    int64_t nc[3], nf[3];
+    if (alref_lattice_size(ndim, Nc, delta, nc) || alref_lattice_size(ndim, Nf, delta, nf))
+        return ALREF_ERR_ARG;
+    for (int k = 0; k < ndim; ++k)
+        if (level_size(Nf[k], 2) != Nc[k])
+            return ALREF_ERR_ARG;
+    const int64_t ncc = nc[0] * nc[1] * nc[2], nff = nf[0] * nf[1] * nf[2];
+    for (int i = 0; i < ndim; ++i)
+        for (int64_t fz = 0; fz < nf[2]; ++fz)
+            for (int64_t fy = 0; fy < nf[1]; ++fy)
+                for (int64_t fx = 0; fx < nf[0]; ++fx) {
+                    double s = 0.0;
+                    for (int64_t jz = 0; jz < nc[2]; ++jz) {
+                        const double hz = ndim == 3 ? two_scale((fz - 1) - 2 * (jz - 1)) : 1.0;
+                        if (hz == 0.0)
+                            continue;
+                        for (int64_t jy = 0; jy < nc[1]; ++jy) {
+                            const double hy = two_scale((fy - 1) - 2 * (jy - 1));
+                            if (hy == 0.0)
+                                continue;
+                            for (int64_t jx = 0; jx < nc[0]; ++jx)
+                                s += hz * hy * two_scale((fx - 1) - 2 * (jx - 1)) *
+                                     c_coarse[i * ncc + (jz * nc[1] + jy) * nc[0] + jx];
+                        }
+                    }
+                    c_fine[i * nff + (fz * nf[1] + fy) * nf[0] + fx] = 2.0 * s;
+                }
+    return ALREF_OK;
+}
