@@ -102,7 +102,8 @@ typedef struct {
 /* Similarity measure (Sec. III-B). */
 typedef struct {
     int32_t kind;       /* al_sim_kind */
-    int32_t lcc_window; /* odd window width for LCC, 1..15 (default 7) */
+    int32_t lcc_window; /* odd LCC window width (default 7): 3, 5 or 7; other odd
+                           widths up to 15 return AL_ERR_UNSUPPORTED */
     double eps;         /* added to var_F*var_W, >= 0 (default 1e-5) */
 } al_sim_params;
 
@@ -213,6 +214,60 @@ al_status al_similarity_noalloc(const al_grid *g, const al_sim_params *p, const 
                                 const float *warped, const uint8_t *mask, double *value_dev,
                                 float *grad_warped, al_stream stream);
 size_t al_noalloc_scratch_bytes(void);
+
+/* ---- The optimisation loop around the objective ---------------------------
+ * Gradient-based optimisation of J (Sec. II-A, Optimization) with Adam
+ * (Sec. III-G; the usage example of Sec. IV sets lr = 0.01) and the
+ * multi-resolution strategy of the FFD experiment (Sec. IV-A): Gaussian image
+ * pyramid, coarse-to-fine levels, coefficients carried to the next level. */
+
+/* Adam hyper-parameters. lr is in the paper's normalised coordinates, where
+ * the image spans [-1, 1] per axis (Sec. III-C, Image Warping). */
+typedef struct {
+    double lr;    /* step size, >= 0 (0.01) */
+    double beta1; /* first-moment decay, in [0, 1) (0.9) */
+    double beta2; /* second-moment decay, in [0, 1) (0.999) */
+    double eps;   /* added to sqrt(v^), > 0 (1e-8) */
+} al_adam_params;
+
+/* One Adam step (Kingma and Ba's update) on the control coefficients of bs,
+ * taken in normalised units c~_k = c_k * 2/(N_k - 1): with g~ the normalised
+ * gradient and t = *step_dev + 1,
+ *   m <- beta1 m + (1 - beta1) g~,  v <- beta2 v + (1 - beta2) g~^2,
+ *   c~ <- c~ - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * ctrl (updated in place) and grad_ctrl are in voxel units, ndim * nz*ny*nx
+ * floats; m and v (same size, zero before the first step) hold the moments
+ * in normalised units. step_dev: one int64 on the device, the number of steps
+ * taken so far; the call stores t there after the update, so the call can be
+ * captured in a CUDA graph and replayed. Two launches, no host read. */
+al_status al_adam_step(const al_bspline *bs, const al_adam_params *p, float *ctrl,
+                       const float *grad_ctrl, float *m, float *v, int64_t *step_dev,
+                       al_stream stream);
+
+/* Grid of one pyramid level: every factor-th voxel from voxel 0 on each
+ * active axis, size (N_k - 1)/factor + 1. factor 1..8; AL_ERR_SHAPE if an
+ * active axis of the level would have fewer than 2 voxels. Host only. */
+al_status al_pyramid_grid(const al_grid *g, int32_t factor, al_grid *level);
+
+/* One pyramid level of an image (Sec. IV-A, multi-resolution; the filter is
+ * a reading, the paper gives none): factor 1 copies the image; factor >= 2
+ * smooths it with a Gaussian of sigma = factor/2 voxels, truncated to the
+ * taps |t| <= 3 sigma, normalised to unit sum, with indices clamped to the
+ * grid, and keeps every factor-th voxel from voxel 0. image: the grid *g;
+ * level: the grid al_pyramid_grid returns (overwritten).
+ * Workspace: al_pyramid_workspace_bytes(g, factor) (0 for factor 1). */
+al_status al_pyramid_level(const al_grid *g, const float *image, int32_t factor, float *level,
+                           void *workspace, size_t workspace_bytes, al_stream stream);
+size_t al_pyramid_workspace_bytes(const al_grid *g, int32_t factor);
+
+/* Coefficients of the next finer level whose displacement equals the coarse
+ * one at every coarse voxel (exact dyadic refinement of the cubic B-spline
+ * by its two-scale relation), in fine voxel units. coarse->grid must be
+ * al_pyramid_grid(fine->grid, 2) and both lattices must have the same
+ * spacing (AL_ERR_SHAPE otherwise). ctrl_coarse: ndim planes of the coarse
+ * lattice; ctrl_fine: ndim planes of the fine lattice (overwritten). */
+al_status al_bspline_refine(const al_bspline *coarse, const float *ctrl_coarse,
+                            const al_bspline *fine, float *ctrl_fine, al_stream stream);
 
 /* Synchronise `stream`, then read and clear the current device's kernel
  * error word: AL_OK, AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the

@@ -32,6 +32,8 @@ EXPORTS = (
     "al_objective_grad", "al_objective_workspace_bytes", "al_objective_grad_unfused",
     "al_objective_unfused_workspace_bytes", "al_get_device_error", "al_profile_enable",
     "al_profile_collect", "al_profile_reset", "al_similarity_noalloc", "al_noalloc_scratch_bytes",
+    "al_adam_step", "al_pyramid_grid", "al_pyramid_level", "al_pyramid_workspace_bytes",
+    "al_bspline_refine",
 )
 
 
@@ -58,6 +60,11 @@ class al_sim_params(ctypes.Structure):
 
 class al_problem(ctypes.Structure):
     _fields_ = [("bs", al_bspline), ("sim", al_sim_params), ("lam", ctypes.c_double)]
+
+
+class al_adam_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 _lib = None
@@ -96,6 +103,11 @@ def load():
         "al_profile_reset": ([], I32),
         "al_similarity_noalloc": ([P(al_grid), P(al_sim_params), VP, VP, VP, VP, VP, VP], I32),
         "al_noalloc_scratch_bytes": ([], SZ),
+        "al_adam_step": ([P(al_bspline), P(al_adam_params), VP, VP, VP, VP, VP, VP], I32),
+        "al_pyramid_grid": ([P(al_grid), I32, P(al_grid)], I32),
+        "al_pyramid_level": ([P(al_grid), VP, I32, VP, VP, SZ, VP], I32),
+        "al_pyramid_workspace_bytes": ([P(al_grid), I32], SZ),
+        "al_bspline_refine": ([P(al_bspline), VP, P(al_bspline), VP, VP], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -321,6 +333,64 @@ def al_objective_grad(problem: al_problem, fixed, moving, ctrl, value=None, grad
           _ptr(grad_ctrl if want_grad else None), _ptr(ws), ctypes.c_size_t(ws.numel()),
           _stream(stream))
     return value, (grad_ctrl if want_grad else None)
+
+
+def al_adam_step(shape, spacing, ctrl, grad_ctrl, m, v, step, lr=0.01, betas=(0.9, 0.999),
+                 eps=1e-8, stream=None):
+    """One Adam step on the control points in normalised units, in place on
+    ctrl, m, v; step is a 1-element int64 device tensor (steps taken so far),
+    advanced by the call."""
+    bs = bspline_init(shape, spacing)
+    want = (len(shape),) + lattice_shape(shape, spacing)
+    for t, name in ((ctrl, "ctrl"), (grad_ctrl, "grad_ctrl"), (m, "m"), (v, "v")):
+        _f32(t, want, name)
+    if step.dtype != torch.int64 or step.numel() != 1:
+        raise ValueError("step: expected a 1-element int64 tensor")
+    p = al_adam_params(float(lr), float(betas[0]), float(betas[1]), float(eps))
+    _call("al_adam_step", ctypes.byref(bs), ctypes.byref(p), _ptr(ctrl), _ptr(grad_ctrl), _ptr(m),
+          _ptr(v), _ptr(step), _stream(stream))
+
+
+def pyramid_shape(shape, factor: int):
+    """Shape of a pyramid level (every factor-th voxel from voxel 0)."""
+    g = make_grid(shape)
+    out = al_grid()
+    _call("al_pyramid_grid", ctypes.byref(g), int(factor), ctypes.byref(out))
+    return (out.size[2], out.size[1], out.size[0]) if len(shape) == 3 else \
+        (out.size[1], out.size[0])
+
+
+def al_pyramid_level(image, factor: int, level=None, workspace=None, stream=None):
+    """One Gaussian pyramid level of `image` (sigma = factor/2, subsampled by
+    factor)."""
+    shape = tuple(image.shape)
+    g = make_grid(shape)
+    _f32(image, shape, "image")
+    out_shape = pyramid_shape(shape, factor)
+    if level is None:
+        level = torch.empty(out_shape, dtype=torch.float32, device=image.device)
+    _f32(level, out_shape, "level")
+    nb = load().al_pyramid_workspace_bytes(ctypes.byref(g), int(factor))
+    ws = _workspace(nb, image.device, workspace) if nb > 0 else None
+    _call("al_pyramid_level", ctypes.byref(g), _ptr(image), int(factor), _ptr(level), _ptr(ws),
+          ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
+    return level
+
+
+def al_bspline_refine(coarse_shape, fine_shape, spacing, ctrl_coarse, ctrl_fine=None,
+                      stream=None):
+    """Coefficients on the finer level with the same displacement (fine voxel
+    units); coarse_shape must be pyramid_shape(fine_shape, 2)."""
+    bc, bf = bspline_init(coarse_shape, spacing), bspline_init(fine_shape, spacing)
+    d = len(fine_shape)
+    _f32(ctrl_coarse, (d,) + lattice_shape(coarse_shape, spacing), "ctrl_coarse")
+    if ctrl_fine is None:
+        ctrl_fine = torch.empty((d,) + lattice_shape(fine_shape, spacing), dtype=torch.float32,
+                                device=ctrl_coarse.device)
+    _f32(ctrl_fine, (d,) + lattice_shape(fine_shape, spacing), "ctrl_fine")
+    _call("al_bspline_refine", ctypes.byref(bc), _ptr(ctrl_coarse), ctypes.byref(bf),
+          _ptr(ctrl_fine), _stream(stream))
+    return ctrl_fine
 
 
 def al_get_device_error(stream=None) -> int:

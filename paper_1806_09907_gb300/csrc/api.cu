@@ -414,6 +414,124 @@ al_status al_objective_grad(const al_problem *pr, const float *fixed, const floa
                                  fixed, moving, ctrl, value_dev, grad_ctrl, workspace, S(stream)));
 }
 
+al_status al_adam_step(const al_bspline *bs, const al_adam_params *p, float *ctrl,
+                       const float *grad_ctrl, float *m, float *v, int64_t *step_dev,
+                       al_stream stream)
+{
+    Grid g;
+    Lattice L;
+    al_status st = check_bspline(bs, &g, &L);
+    if (st != AL_OK)
+        return st;
+    if (!p || !ctrl || !grad_ctrl || !m || !v || !step_dev)
+        return AL_ERR_INVALID_ARG;
+    if (!(p->lr >= 0.0) || !isfinite(p->lr) || !(p->beta1 >= 0.0 && p->beta1 < 1.0) ||
+        !(p->beta2 >= 0.0 && p->beta2 < 1.0) || !(p->eps > 0.0) || !isfinite(p->eps))
+        return AL_ERR_INVALID_ARG;
+    if (!aligned16(ctrl) || !aligned16(grad_ctrl) || !aligned16(m) || !aligned16(v) ||
+        !aligned16(step_dev))
+        return AL_ERR_ALIGN;
+    AdamArgs a{};
+    a.beta1 = p->beta1;
+    a.beta2 = p->beta2;
+    a.lr = (float)p->lr;
+    a.eps = (float)p->eps;
+    for (int k = 0; k < 3; ++k)
+        a.h[k] = k < g.ndim ? (float)((bs->grid.size[k] - 1) / 2.0) : 0.0f;
+    a.nc = L.nc;
+    a.ndim = g.ndim;
+    return launched(launch_adam(a, step_dev, ctrl, grad_ctrl, m, v, S(stream)));
+}
+
+al_status al_pyramid_grid(const al_grid *gr, int32_t factor, al_grid *level)
+{
+    if (!level)
+        return AL_ERR_INVALID_ARG;
+    al_status st = check_grid(gr, nullptr);
+    if (st != AL_OK)
+        return st;
+    if (factor < 1 || factor > kMaxPyramidFactor)
+        return AL_ERR_INVALID_ARG;
+    al_grid out = *gr;
+    for (int k = 0; k < gr->ndim; ++k) {
+        out.size[k] = (gr->size[k] - 1) / factor + 1;
+        if (out.size[k] < 2)
+            return AL_ERR_SHAPE;
+    }
+    *level = out;
+    return AL_OK;
+}
+
+size_t al_pyramid_workspace_bytes(const al_grid *gr, int32_t factor)
+{
+    Grid g;
+    al_grid lv;
+    if (check_grid(gr, &g) != AL_OK || al_pyramid_grid(gr, factor, &lv) != AL_OK)
+        return 0;
+    return pyramid_ws(g, factor);
+}
+
+al_status al_pyramid_level(const al_grid *gr, const float *image, int32_t factor, float *level,
+                           void *workspace, size_t workspace_bytes, al_stream stream)
+{
+    Grid g;
+    al_grid lv;
+    al_status st = check_grid(gr, &g);
+    if (st != AL_OK)
+        return st;
+    if ((st = al_pyramid_grid(gr, factor, &lv)) != AL_OK)
+        return st;
+    if (!image || !level)
+        return AL_ERR_INVALID_ARG;
+    const size_t need = pyramid_ws(g, factor);
+    if (need > 0 && (!workspace || workspace_bytes < need))
+        return AL_ERR_WORKSPACE;
+    if (!aligned16(image) || !aligned16(level) || (need > 0 && !aligned16(workspace)))
+        return AL_ERR_ALIGN;
+    // Gaussian taps, sigma = factor/2, |t| <= 3 sigma, unit sum (double, then fp32)
+    GaussTaps t{};
+    if (factor > 1) {
+        const double sigma = factor / 2.0;
+        t.r = (int)floor(3.0 * sigma);
+        double w[sizeof(t.w) / sizeof(t.w[0])], sum = 0.0;
+        for (int k = -t.r; k <= t.r; ++k) {
+            w[k + t.r] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+            sum += w[k + t.r];
+        }
+        for (int k = 0; k <= 2 * t.r; ++k)
+            t.w[k] = (float)(w[k] / sum);
+    }
+    return launched(launch_pyramid(g, factor, t, image, level, workspace, S(stream)));
+}
+
+al_status al_bspline_refine(const al_bspline *coarse, const float *ctrl_coarse,
+                            const al_bspline *fine, float *ctrl_fine, al_stream stream)
+{
+    Grid gc, gf;
+    Lattice Lc, Lf;
+    al_status st = check_bspline(coarse, &gc, &Lc);
+    if (st != AL_OK)
+        return st;
+    if ((st = check_bspline(fine, &gf, &Lf)) != AL_OK)
+        return st;
+    if (!ctrl_coarse || !ctrl_fine)
+        return AL_ERR_INVALID_ARG;
+    if (gc.ndim != gf.ndim || coarse->spacing != fine->spacing)
+        return AL_ERR_SHAPE;
+    const int nc[3] = {Lc.nx, Lc.ny, Lc.nz}, nf[3] = {Lf.nx, Lf.ny, Lf.nz};
+    for (int k = 0; k < gc.ndim; ++k) {
+        if ((fine->grid.size[k] - 1) / 2 + 1 != coarse->grid.size[k])
+            return AL_ERR_SHAPE;
+        // taps of the last fine point: (nf - 2)/2 + 2 must be a coarse index
+        // (the first point, i = 0, takes coarse 0 and 1)
+        if ((nf[k] - 2) / 2 + 2 > nc[k] - 1 || nc[k] < 2)
+            return AL_ERR_SHAPE;
+    }
+    if (!aligned16(ctrl_coarse) || !aligned16(ctrl_fine))
+        return AL_ERR_ALIGN;
+    return launched(launch_refine(gc.ndim, nc, nf, ctrl_coarse, ctrl_fine, S(stream)));
+}
+
 al_status al_get_device_error(al_stream stream)
 {
     if (cudaStreamSynchronize(S(stream)) != cudaSuccess)

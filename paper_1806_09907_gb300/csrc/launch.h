@@ -56,4 +56,28 @@ cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, 
 cudaError_t launch_combine(const double *sim_value /*S, n_mask*/, const double *reg_value /*R*/,
                            double lambda, double *out, cudaStream_t s);
 
+// ---- optimisation loop: Adam, pyramid level, coefficient refinement ---------
+struct AdamArgs {
+    double beta1, beta2;  // bias corrections are formed from these in double
+    float lr, eps;
+    float h[3];  // voxel units per normalised unit, (N_k - 1)/2, per component
+    int nc;      // coefficients per component plane
+    int ndim;
+};
+cudaError_t launch_adam(const AdamArgs &a, int64_t *step, float *ctrl, const float *grad,
+                        float *m, float *v, cudaStream_t s);
+
+constexpr int kMaxPyramidFactor = 8;
+struct GaussTaps {
+    int r;                                     // taps -r..r
+    float w[2 * (3 * kMaxPyramidFactor / 2) + 1];  // normalised to unit sum
+};
+size_t pyramid_ws(const Grid &g, int factor);
+cudaError_t launch_pyramid(const Grid &g, int factor, const GaussTaps &t, const float *image,
+                           float *level, void *ws, cudaStream_t s);
+
+// nc, nf: coarse / fine lattice sizes (x, y, z); taps checked by the caller.
+cudaError_t launch_refine(int ndim, const int *nc, const int *nf, const float *cc, float *cf,
+                          cudaStream_t s);
+
 }  // namespace airgb

@@ -107,3 +107,53 @@ def test_fused_workspace_scales_with_volume(lib):
     b = lib.al_objective_workspace_bytes(ctypes.byref(big))
     # LCC keeps W, the mask and dS/dW: 9 bytes per voxel plus the partials
     assert b > 9 * 160 * 256 * 256 > a > 0
+
+
+def test_pyramid_grid_and_workspace(lib):
+    g = airgb.make_grid((160, 256, 256))
+    out = airgb.al_grid()
+    assert lib.al_pyramid_grid(ctypes.byref(g), 4, ctypes.byref(out)) == 0
+    assert (out.ndim, out.size[0], out.size[1], out.size[2]) == (3, 64, 64, 40)
+    assert lib.al_pyramid_grid(ctypes.byref(g), 2, ctypes.byref(out)) == 0
+    assert (out.size[0], out.size[1], out.size[2]) == (128, 128, 80)
+    assert lib.al_pyramid_grid(ctypes.byref(g), 0, ctypes.byref(out)) == 1
+    assert lib.al_pyramid_grid(ctypes.byref(g), 9, ctypes.byref(out)) == 1
+    tiny = airgb.make_grid((3, 40, 40))  # z would keep a single voxel
+    assert lib.al_pyramid_grid(ctypes.byref(tiny), 4, ctypes.byref(out)) == 2
+    assert lib.al_pyramid_workspace_bytes(ctypes.byref(g), 1) == 0
+    assert lib.al_pyramid_workspace_bytes(ctypes.byref(g), 4) >= 4 * 64 * 256 * 160
+    assert lib.al_pyramid_workspace_bytes(ctypes.byref(tiny), 4) == 0
+    p = ctypes.c_void_p(0x10000)
+    st = lib.al_pyramid_level(ctypes.byref(g), p, 4, p, None, ctypes.c_size_t(0), None)
+    assert st == 8  # workspace needed for factor > 1
+    st = lib.al_pyramid_level(ctypes.byref(g), ctypes.c_void_p(0x10008), 1, p, None,
+                              ctypes.c_size_t(0), None)
+    assert st == 3
+
+
+def test_adam_step_rejects(lib):
+    bs = airgb.bspline_init((20, 24, 28), 4)
+    p = ctypes.c_void_p(0x10000)
+
+    def call(prm, ptr=p, step=p):
+        return lib.al_adam_step(ctypes.byref(bs), ctypes.byref(prm), ptr, p, p, p, step, None)
+
+    ok = airgb.al_adam_params(0.01, 0.9, 0.999, 1e-8)
+    assert call(ok, step=None) == 1
+    assert call(ok, ptr=ctypes.c_void_p(0x10004)) == 3
+    for bad in ((-0.1, 0.9, 0.999, 1e-8), (0.01, 1.0, 0.999, 1e-8), (0.01, 0.9, -0.5, 1e-8),
+                (0.01, 0.9, 0.999, 0.0), (float("nan"), 0.9, 0.999, 1e-8)):
+        assert call(airgb.al_adam_params(*bad)) == 1, bad
+
+
+def test_refine_rejects(lib):
+    p = ctypes.c_void_p(0x10000)
+    fine = airgb.bspline_init((40, 64, 64), 6)
+    coarse = airgb.bspline_init((20, 32, 32), 6)
+    other = airgb.bspline_init((20, 32, 32), 4)
+    wrong = airgb.bspline_init((20, 32, 31), 6)
+    assert lib.al_bspline_refine(ctypes.byref(other), p, ctypes.byref(fine), p, None) == 2
+    assert lib.al_bspline_refine(ctypes.byref(wrong), p, ctypes.byref(fine), p, None) == 2
+    assert lib.al_bspline_refine(ctypes.byref(coarse), ctypes.c_void_p(0x10004),
+                                 ctypes.byref(fine), p, None) == 3
+    assert lib.al_bspline_refine(ctypes.byref(coarse), None, ctypes.byref(fine), p, None) == 1
