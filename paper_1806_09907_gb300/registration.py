@@ -96,6 +96,19 @@ class BsplineAdam(torch.optim.Optimizer):
         self.shape, self.spacing = tuple(shape), int(spacing)
 
     @torch.no_grad()
+    def init_state(self):
+        """Create the moments and the device step counter of every parameter
+        now (zero), so that a CUDA-graph capture of step() contains no
+        initialisation."""
+        for group in self.param_groups:
+            for p in group["params"]:
+                st = self.state[p]
+                if not st:
+                    st["exp_avg"] = torch.zeros_like(p)
+                    st["exp_avg_sq"] = torch.zeros_like(p)
+                    st["step"] = torch.zeros(1, dtype=torch.int64, device=p.device)
+
+    @torch.no_grad()
     def step(self, closure=None):
         loss = None
         if closure is not None:
@@ -107,13 +120,37 @@ class BsplineAdam(torch.optim.Optimizer):
                     continue
                 st = self.state[p]
                 if not st:
-                    st["exp_avg"] = torch.zeros_like(p)
-                    st["exp_avg_sq"] = torch.zeros_like(p)
-                    st["step"] = torch.zeros(1, dtype=torch.int64, device=p.device)
+                    self.init_state()
                 airgb.al_adam_step(self.shape, self.spacing, p, p.grad.contiguous(),
                                    st["exp_avg"], st["exp_avg_sq"], st["step"], lr=group["lr"],
                                    betas=group["betas"], eps=group["eps"])
         return loss
+
+
+class GraphedIteration:
+    """One optimisation iteration -- J through :class:`ObjectiveFunction`,
+    its backward and a :class:`BsplineAdam` step -- captured once in a CUDA
+    graph and replayed, so each iteration costs one graph launch instead of
+    the Python and autograd work of an eager iteration. `ctrl` is updated in
+    place on every replay; ``self.J`` holds the J of the latest replay (taken
+    before its step)."""
+
+    def __init__(self, ctrl, evaluator: Evaluator, fixed, moving, optimizer: BsplineAdam,
+                 recompute=False):
+        optimizer.init_state()
+        # one eager evaluation outside the capture (sets kernel attributes)
+        evaluator.evaluate(fixed, moving, ctrl.detach(),
+                           torch.empty(4, dtype=torch.float64, device=ctrl.device))
+        self.graph = torch.cuda.CUDAGraph()
+        optimizer.zero_grad(set_to_none=True)
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self.J = objective(ctrl, evaluator, fixed, moving, recompute)
+            self.J.backward()
+            optimizer.step()
+
+    def __call__(self):
+        self.graph.replay()
+        return self.J
 
 
 @dataclasses.dataclass
