@@ -78,6 +78,30 @@ __device__ __forceinline__ void merge(Sums &S, float t1f, float t1w, float t2f, 
     S.sfw += fmaf(d, fmaf(n, e, t1w), fmaf(e, t1f, tfw));
 }
 
+// The sums of a partial window (relative to its centre (af, aw), n points)
+// converted to the reference (bf, bw); returned, not accumulated.
+__device__ __forceinline__ Sums shifted(float t1f, float t1w, float t2f, float t2w, float tfw,
+                                        float af, float aw, float bf, float bw, float n)
+{
+    const float d = af - bf, e = aw - bw;
+    Sums o;
+    o.s1f = fmaf(n, d, t1f);
+    o.s1w = fmaf(n, e, t1w);
+    o.s2f = fmaf(d, fmaf(n, d, 2.0f * t1f), t2f);
+    o.s2w = fmaf(e, fmaf(n, e, 2.0f * t1w), t2w);
+    o.sfw = fmaf(d, fmaf(n, e, t1w), fmaf(e, t1f, tfw));
+    return o;
+}
+
+__device__ __forceinline__ void add_to(Sums &S, const Sums &t)
+{
+    S.s1f += t.s1f;
+    S.s1w += t.s1w;
+    S.s2f += t.s2f;
+    S.s2w += t.s2w;
+    S.sfw += t.sfw;
+}
+
 template <int D, int R>
 __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
     k_lcc_stats(Grid g, float eps, const float *__restrict__ F, const float *__restrict__ W,
@@ -169,7 +193,10 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
             }
             __syncthreads();
             // ---- merge along x, two neighbouring outputs per thread sharing
-            //      W1 - 1 of their columns: outputs (ly, tx) and (ly, tx + 1)
+            //      W1 - 1 of their columns: outputs (ly, tx) and (ly, tx + 1).
+            //      The W1 + 1 columns are shifted once, to the centre of the
+            //      first output, and summed into both windows; the second
+            //      window is then shifted to its own centre.
             for (int e = tid; e < NX / 2; e += C::THREADS) {
                 const int ly = e / (TX / 2), tx = 2 * (e - ly * (TX / 2));
                 const int base = ly * LX + tx;
@@ -179,14 +206,15 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
 #pragma unroll
                 for (int d = 0; d <= W1; ++d) {
                     const int c = base + d;
-                    const float t1f = Zs[c], t1w = Zs[NL + c], t2f = Zs[2 * NL + c];
-                    const float t2w = Zs[3 * NL + c], tfw = Zs[4 * NL + c];
-                    const float af = Zs[5 * NL + c], aw = Zs[6 * NL + c];
+                    const Sums t = shifted(Zs[c], Zs[NL + c], Zs[2 * NL + c], Zs[3 * NL + c],
+                                           Zs[4 * NL + c], Zs[5 * NL + c], Zs[6 * NL + c], bf0,
+                                           bw0, n1);
                     if (d < W1)
-                        merge(S0, t1f, t1w, t2f, t2w, tfw, af, aw, bf0, bw0, n1);
+                        add_to(S0, t);
                     if (d > 0)
-                        merge(S1, t1f, t1w, t2f, t2w, tfw, af, aw, bf1, bw1, n1);
+                        add_to(S1, t);
                 }
+                S1 = shifted(S1.s1f, S1.s1w, S1.s2f, S1.s2w, S1.sfw, bf0, bw0, bf1, bw1, n2);
                 const int o = ly * TX + tx;
                 Xs[0 * NX + o] = S0.s1f;
                 Xs[1 * NX + o] = S0.s1w;
@@ -217,19 +245,23 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
                     bfv[h] = Zs[5 * NL + zcol];
                     bwv[h] = Zs[6 * NL + zcol];
                 }
+                // rows shifted once to the first output's centre, summed into
+                // both windows; the second window shifted to its own centre
                 Sums S[2] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
                 for (int d = 0; d <= W1; ++d) {
                     const int r = (ty0 + d) * TX + tx;
                     const int zrow = (ty0 + d) * LX + tx + R;
-                    const float t1f = Xs[r], t1w = Xs[NX + r], t2f = Xs[2 * NX + r];
-                    const float t2w = Xs[3 * NX + r], tfw = Xs[4 * NX + r];
-                    const float af = Zs[5 * NL + zrow], aw = Zs[6 * NL + zrow];
+                    const Sums t = shifted(Xs[r], Xs[NX + r], Xs[2 * NX + r], Xs[3 * NX + r],
+                                           Xs[4 * NX + r], Zs[5 * NL + zrow], Zs[6 * NL + zrow],
+                                           bfv[0], bwv[0], n2);
                     if (d < W1)
-                        merge(S[0], t1f, t1w, t2f, t2w, tfw, af, aw, bfv[0], bwv[0], n2);
+                        add_to(S[0], t);
                     if (d > 0)
-                        merge(S[1], t1f, t1w, t2f, t2w, tfw, af, aw, bfv[1], bwv[1], n2);
+                        add_to(S[1], t);
                 }
+                S[1] = shifted(S[1].s1f, S[1].s1w, S[1].s2f, S[1].s2w, S[1].sfw, bfv[0], bwv[0],
+                               bfv[1], bwv[1], n3);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int x = x0 + tx, y = y0 + ty0 + h;
