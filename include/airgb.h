@@ -204,7 +204,7 @@ size_t al_objective_unfused_workspace_bytes(const al_problem *pr);
  * Arguments and results are those of al_similarity without the workspace.
  * A problem whose workspace (al_similarity_workspace_bytes) exceeds the
  * array returns AL_ERR_SCRATCH_LIMIT and launches nothing: MSE and NCC fit
- * at any size, LCC up to about 250,000 voxels.
+ * at any size, LCC up to about 340,000 voxels.
  * All calls on a device share the array and leave their data in it; calls
  * whose kernels overlap on the GPU race on it, so order them. The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress

@@ -58,8 +58,16 @@ struct LccB {
     static constexpr int ZC = (D == 3) ? 24 : 1;
     static constexpr int THREADS = NC;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;
-    static constexpr size_t smem = (size_t)(NL + NX) * sizeof(float4);
+    // one buffer: the staged slice as planes a', b, c of NL floats, then the
+    // x box sums as three planes of NX floats; two buffers alternate by slice
+    static constexpr int BUF = 3 * NL + 3 * NX;
+    static constexpr size_t smem = (size_t)2 * BUF * sizeof(float);
+    static_assert(LX % 2 == 0 && NL % 2 == 0 && NX % 2 == 0, "rows are read as float2");
+    static_assert(NX / 2 <= THREADS, "one x pair per thread");
 };
+
+// Distance in floats between the planes a', b, c of the LCC coefficients.
+__host__ __device__ inline int64_t lcc_plane(int nv) { return ((int64_t)nv * 4 + 255) / 256 * 64; }
 
 // Merge of a partial window (sums t1f,t1w,t2f,t2w,tfw relative to its centre
 // (af, aw), n points) into sums relative to (bf, bw).
@@ -284,8 +292,12 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
                         rho_sum += rho;
                         cnt += 1.0f;
                     }
-                    if (coef)
-                        reinterpret_cast<float4 *>(coef)[vv[h]] = make_float4(ca, cb, cc, 0.0f);
+                    if (coef) {
+                        const int64_t pl = lcc_plane(g.nv);
+                        coef[vv[h]] = ca;
+                        coef[pl + vv[h]] = cb;
+                        coef[2 * pl + vv[h]] = cc;
+                    }
                 }
             }
         }
@@ -309,26 +321,36 @@ struct CoreVox {
 
 // One slice step of k_lcc_grad. The thread owns core column (tx, ty); P is
 // the ring slot of slice zi (compile time, so the ring stays in registers).
+// The shared buffers alternate with the parity of zi, so a step needs two
+// barriers: after staging, and after the x sums.
 template <int D, int R, int P>
 __device__ __forceinline__ void lcc_grad_step(const Grid &g, int zi, int zc0, int x0, int y0,
-                                              const float4 *__restrict__ coef,
+                                              const float *__restrict__ coef,
                                               const float *__restrict__ F,
                                               const float *__restrict__ W,
                                               const uint8_t *__restrict__ m,
-                                              float *__restrict__ gout, float4 *L4, float4 *X4,
-                                              float4 (&pq)[LccB<D, R>::KL], float3 (&ring)[LccB<D, R>::NR],
-                                              CoreVox &core, int zi_end)
+                                              float *__restrict__ gout, float *smem,
+                                              float (&pa)[LccB<D, R>::KL],
+                                              float (&pb)[LccB<D, R>::KL],
+                                              float (&pc)[LccB<D, R>::KL],
+                                              float3 (&ring)[LccB<D, R>::NR], CoreVox &core,
+                                              int zi_end)
 {
     using C = LccB<D, R>;
-    constexpr int NL = C::NL, LX = C::LX, TX = C::TX, NR = C::NR, W1 = C::W1;
+    constexpr int NL = C::NL, NX = C::NX, LX = C::LX, TX = C::TX, NR = C::NR, W1 = C::W1;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y, pl = lcc_plane(g.nv);
+    float *L = smem + (zi & 1) * C::BUF;
+    float *X = L + 3 * NL;
     // stage slice zi (prefetched), then start fetching zi + 1
 #pragma unroll
     for (int k = 0; k < C::KL; ++k) {
         const int e = tid + k * C::THREADS;
-        if (e < NL)
-            L4[e] = pq[k];
+        if (e < NL) {
+            L[e] = pa[k];
+            L[NL + e] = pb[k];
+            L[2 * NL + e] = pc[k];
+        }
     }
     if (zi + 1 < zi_end) {
         const int zn = zi + 1;
@@ -336,12 +358,16 @@ __device__ __forceinline__ void lcc_grad_step(const Grid &g, int zi, int zc0, in
 #pragma unroll
         for (int k = 0; k < C::KL; ++k) {
             const int e = tid + k * C::THREADS;
-            pq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pa[k] = pb[k] = pc[k] = 0.0f;
             if (e < NL) {
                 const int ly = e / LX, lx = e - ly * LX;
                 const int x = x0 - R + lx, y = y0 - R + ly;
-                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y)
-                    pq[k] = __ldg(coef + (int64_t)zn * sZ + (int64_t)y * sY + x);
+                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
+                    const int64_t v = (int64_t)zn * sZ + (int64_t)y * sY + x;
+                    pa[k] = __ldg(coef + v);
+                    pb[k] = __ldg(coef + pl + v);
+                    pc[k] = __ldg(coef + 2 * pl + v);
+                }
             }
         }
     }
@@ -360,21 +386,28 @@ __device__ __forceinline__ void lcc_grad_step(const Grid &g, int zi, int zc0, in
         core.w = __ldg(W + vn);
     }
     __syncthreads();
-    // x box sums: rows ty and ty + TY (halo rows) of the load region
+    // x box sums of every row of the load region, two neighbouring outputs
+    // per thread: W1 + 1 taps read as float2 (consecutive threads, consecutive
+    // pairs: no bank conflicts)
+    if (tid < NX / 2) {
+        const int ly = tid / (TX / 2), p2 = 2 * (tid - ly * (TX / 2));
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int ly = ty + h * C::TY;
-        if (ly < C::LY) {
-            const float4 *src = L4 + ly * LX + tx;
-            float a = 0.f, b = 0.f, c = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            const float2 *src = reinterpret_cast<const float2 *>(L + k * NL + ly * LX + p2);
+            float v[W1 + 1];
+#pragma unroll
+            for (int q = 0; q <= R; ++q) {
+                const float2 t = src[q];
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+            float s0 = 0.f, s1 = 0.f;
 #pragma unroll
             for (int d = 0; d < W1; ++d) {
-                const float4 q = src[d];
-                a += q.x;
-                b += q.y;
-                c += q.z;
+                s0 += v[d];
+                s1 += v[d + 1];
             }
-            X4[ly * TX + tx] = make_float4(a, b, c, 0.f);
+            *reinterpret_cast<float2 *>(X + k * NX + ly * TX + p2) = make_float2(s0, s1);
         }
     }
     __syncthreads();
@@ -383,10 +416,10 @@ __device__ __forceinline__ void lcc_grad_step(const Grid &g, int zi, int zc0, in
         float a = 0.f, b = 0.f, c = 0.f;
 #pragma unroll
         for (int d = 0; d < W1; ++d) {
-            const float4 q = X4[(ty + d) * TX + tx];
-            a += q.x;
-            b += q.y;
-            c += q.z;
+            const int r = (ty + d) * TX + tx;
+            a += X[r];
+            b += X[NX + r];
+            c += X[2 * NX + r];
         }
         ring[P] = make_float3(a, b, c);
     }
@@ -404,48 +437,48 @@ __device__ __forceinline__ void lcc_grad_step(const Grid &g, int zi, int zc0, in
         }
         gout[vo] = gv;
     }
-    __syncthreads();  // L4 / X4 are rewritten by the next step
 }
 
 template <int D, int R, int P>
 __device__ __forceinline__ void lcc_grad_steps(const Grid &g, int zb, int zc0, int x0, int y0,
-                                               const float4 *__restrict__ coef,
+                                               const float *__restrict__ coef,
                                                const float *__restrict__ F,
                                                const float *__restrict__ W,
                                                const uint8_t *__restrict__ m,
-                                               float *__restrict__ gout, float4 *L4, float4 *X4,
-                                               float4 (&pq)[LccB<D, R>::KL],
+                                               float *__restrict__ gout, float *smem,
+                                               float (&pa)[LccB<D, R>::KL],
+                                               float (&pb)[LccB<D, R>::KL],
+                                               float (&pc)[LccB<D, R>::KL],
                                                float3 (&ring)[LccB<D, R>::NR], CoreVox &core,
                                                int zi_end)
 {
     if constexpr (P < LccB<D, R>::NR) {
         if (zb + P < zi_end) {
-            lcc_grad_step<D, R, P>(g, zb + P, zc0, x0, y0, coef, F, W, m, gout, L4, X4, pq, ring,
-                                   core, zi_end);
-            lcc_grad_steps<D, R, P + 1>(g, zb, zc0, x0, y0, coef, F, W, m, gout, L4, X4, pq, ring,
-                                        core, zi_end);
+            lcc_grad_step<D, R, P>(g, zb + P, zc0, x0, y0, coef, F, W, m, gout, smem, pa, pb, pc,
+                                   ring, core, zi_end);
+            lcc_grad_steps<D, R, P + 1>(g, zb, zc0, x0, y0, coef, F, W, m, gout, smem, pa, pb, pc,
+                                        ring, core, zi_end);
         }
     }
 }
 
 // dS/dW * |X_m| = A' + 2 W B + F C on the mask, with (A', B, C) the box sums
-// of the coefficients. One thread per core column; x and y box sums through
-// shared memory, the z box sum from a register ring of the last 2R+1 x/y
-// sums (summed directly, no running sums).
+// of the coefficients (three planes a', b, c). One thread per core column;
+// x and y box sums through shared memory, the z box sum from a register ring
+// of the last 2R+1 x/y sums (summed directly, no running sums).
 template <int D, int R>
 __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
     k_lcc_grad(Grid g, const float *__restrict__ F, const float *__restrict__ W,
-               const uint8_t *__restrict__ m, const float4 *__restrict__ coef,
+               const uint8_t *__restrict__ m, const float *__restrict__ coef,
                float *__restrict__ gout)
 {
     using C = LccB<D, R>;
-    extern __shared__ float4 sm4[];
-    float4 *L4 = sm4, *X4 = sm4 + C::NL;
+    extern __shared__ float smf[];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
     const int zc0 = blockIdx.z * C::ZC, zc1 = min(zc0 + C::ZC, g.Z);
-    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
-    float4 pq[C::KL];
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y, pl = lcc_plane(g.nv);
+    float pa[C::KL], pb[C::KL], pc[C::KL];
     float3 ring[C::NR];
 #pragma unroll
     for (int t = 0; t < C::NR; ++t)
@@ -456,12 +489,16 @@ __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
 #pragma unroll
         for (int k = 0; k < C::KL; ++k) {
             const int e = tid + k * C::THREADS;
-            pq[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pa[k] = pb[k] = pc[k] = 0.0f;
             if (e < C::NL) {
                 const int ly = e / C::LX, lx = e - ly * C::LX;
                 const int x = x0 - R + lx, y = y0 - R + ly;
-                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y)
-                    pq[k] = __ldg(coef + (int64_t)zs * sZ + (int64_t)y * sY + x);
+                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
+                    const int64_t v = (int64_t)zs * sZ + (int64_t)y * sY + x;
+                    pa[k] = __ldg(coef + v);
+                    pb[k] = __ldg(coef + pl + v);
+                    pc[k] = __ldg(coef + 2 * pl + v);
+                }
             }
         }
     }
@@ -476,8 +513,8 @@ __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
         }
     }
     for (int zb = zs; zb < zi_end; zb += C::NR)
-        lcc_grad_steps<D, R, 0>(g, zb, zc0, x0, y0, coef, F, W, m, gout, L4, X4, pq, ring, core,
-                                zi_end);
+        lcc_grad_steps<D, R, 0>(g, zb, zc0, x0, y0, coef, F, W, m, gout, smf, pa, pb, pc, ring,
+                                core, zi_end);
 }
 
 template <int D, int R>
@@ -506,9 +543,7 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     {
         dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + B::ZC - 1) / B::ZC);
         ProfScope ps(s, "k_lcc_grad");
-        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, F, W, m,
-                                                           reinterpret_cast<const float4 *>(coef),
-                                                           gout);
+        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, F, W, m, coef, gout);
     }
     return cudaGetLastError();
 }
@@ -530,7 +565,7 @@ int lcc_num_blocks(const Grid &g, int window)
     return R == 1 ? lcc_blocks<2, 1>(g) : R == 2 ? lcc_blocks<2, 2>(g) : lcc_blocks<2, 3>(g);
 }
 
-size_t lcc_coef_bytes(const Grid &g) { return ((size_t)g.nv * 16 + 255) / 256 * 256; }
+size_t lcc_coef_bytes(const Grid &g) { return (size_t)3 * lcc_plane(g.nv) * sizeof(float); }
 
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,
                        const uint8_t *m, float *gout, double *part, float *coef, cudaStream_t s)

@@ -56,7 +56,7 @@ def test_noalloc_matches_workspace_entry_point(lib, sim, window, shape):
 def test_noalloc_rejects_problems_beyond_the_scratch(lib):
     limit = lib.al_noalloc_scratch_bytes()
     assert limit == 4 << 20
-    g = airgb.make_grid((64, 128, 128))  # LCC needs 16 bytes per voxel of scratch
+    g = airgb.make_grid((64, 128, 128))  # LCC needs 12 bytes per voxel of scratch
     p = airgb.al_sim_params()
     p.kind, p.lcc_window, p.eps = airgb.AL_SIM_LCC, 7, 1e-5
     assert lib.al_similarity_workspace_bytes(ctypes.byref(g), ctypes.byref(p)) > limit
