@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(kGramThreads)
     __shared__ float GA[H3][T][T], HB[H3][T][T], GB[H3][T][T];
     __shared__ float tG[3][T][7], tH[3][T][7];
     __shared__ double red[kGramThreads / 32];
-    const int j0[3] = {(int)blockIdx.x * T, (int)blockIdx.y * T, (int)blockIdx.z * T};
+    // one component per block: blockIdx.z = component * (z tiles) + z tile
+    const int tz = (L.nz + T - 1) / T, i = (int)blockIdx.z / tz;
+    const int j0[3] = {(int)blockIdx.x * T, (int)blockIdx.y * T, ((int)blockIdx.z - i * tz) * T};
     const int nn[3] = {L.nx, L.ny, L.nz};
     const int NN[3] = {g.X, g.Y, g.Z};
     const int tid = threadIdx.x;
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(kGramThreads)
         band_entry(L, NN[k], nn[k], j0[k] + l, o, tG[k][l][o + 3], tH[k][l][o + 3]);
     }
     float rsum = 0.0f;
-    for (int i = 0; i < 3; ++i) {
+    {
         __syncthreads();
         for (int e = tid; e < H3 * H3 * H3; e += kGramThreads) {
             const int lz = e / (H3 * H3), r = e - lz * H3 * H3, ly = r / H3, lx = r - ly * H3;
@@ -526,7 +528,9 @@ __global__ void __launch_bounds__(kGramThreads)
     __shared__ float A[H2][T], B[H2][T];
     __shared__ float tG[2][T][7], tH[2][T][7];
     __shared__ double red[kGramThreads / 32];
-    const int j0[2] = {(int)blockIdx.x * T, (int)blockIdx.y * T};
+    // one component per block: blockIdx.y = component * (y tiles) + y tile
+    const int ty = (L.ny + T - 1) / T, i = (int)blockIdx.y / ty;
+    const int j0[2] = {(int)blockIdx.x * T, ((int)blockIdx.y - i * ty) * T};
     const int nn[2] = {L.nx, L.ny};
     const int NN[2] = {g.X, g.Y};
     const int tid = threadIdx.x;
@@ -535,7 +539,7 @@ __global__ void __launch_bounds__(kGramThreads)
         band_entry(L, NN[k], nn[k], j0[k] + l, o, tG[k][l][o + 3], tH[k][l][o + 3]);
     }
     float rsum = 0.0f;
-    for (int i = 0; i < 2; ++i) {
+    {
         __syncthreads();
         for (int e = tid; e < H2 * H2; e += kGramThreads) {
             const int ly = e / H2, lx = e - ly * H2;
@@ -751,10 +755,10 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
     const int CH = (kind == 1) ? 3 * D : D;
     const int npart = CH * ((D == 3) ? BCZ + 3 : 1) * (BCY + 3) * (BCX + 3);
     if (D == 3)
-        o.ngram = ((L.nx + kGramT3 - 1) / kGramT3) * ((L.ny + kGramT3 - 1) / kGramT3) *
-                  ((L.nz + kGramT3 - 1) / kGramT3);
+        o.ngram = 3 * ((L.nx + kGramT3 - 1) / kGramT3) * ((L.ny + kGramT3 - 1) / kGramT3) *
+                  ((L.nz + kGramT3 - 1) / kGramT3);  // one block per tile and component
     else
-        o.ngram = ((L.nx + kGramT2 - 1) / kGramT2) * ((L.ny + kGramT2 - 1) / kGramT2);
+        o.ngram = 2 * ((L.nx + kGramT2 - 1) / kGramT2) * ((L.ny + kGramT2 - 1) / kGramT2);
     o.nlcc = (kind == 2) ? lcc_num_blocks(g, window) : 0;
     size_t off = 0;
     o.scal = off;
@@ -822,10 +826,10 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     prof_begin(s, "k_gram");
     if (D == 3) {
         dim3 gg((L.nx + kGramT3 - 1) / kGramT3, (L.ny + kGramT3 - 1) / kGramT3,
-                (L.nz + kGramT3 - 1) / kGramT3);
+                3 * ((L.nz + kGramT3 - 1) / kGramT3));
         k_gram3<<<gg, kGramThreads, 0, s>>>(g, L, c, gscale, gR, rpart);
     } else {
-        dim3 gg((L.nx + kGramT2 - 1) / kGramT2, (L.ny + kGramT2 - 1) / kGramT2);
+        dim3 gg((L.nx + kGramT2 - 1) / kGramT2, 2 * ((L.ny + kGramT2 - 1) / kGramT2));
         k_gram2<<<gg, kGramThreads, 0, s>>>(g, L, c, gscale, gR, rpart);
     }
     prof_end(s);

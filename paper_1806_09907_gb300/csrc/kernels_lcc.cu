@@ -112,8 +112,9 @@ __device__ __forceinline__ void add_to(Sums &S, const Sums &t)
 
 template <int D, int R>
 __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
-    k_lcc_stats(Grid g, float eps, const float *__restrict__ F, const float *__restrict__ W,
-                const uint8_t *__restrict__ m, float *__restrict__ coef, double *__restrict__ part)
+    k_lcc_stats(Grid g, int zc, float eps, const float *__restrict__ F,
+                const float *__restrict__ W, const uint8_t *__restrict__ m,
+                float *__restrict__ coef, double *__restrict__ part)
 {
     using C = LccA<D, R>;
     constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
     __shared__ double red[2 * C::THREADS / 32];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
-    const int zc0 = blockIdx.z * C::ZC, zc1 = min(zc0 + C::ZC, g.Z);
+    const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, g.Z);
     const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
     const float n1 = (float)NR, n2 = (float)(NR * W1), n3 = (float)(NR * W1 * W1);
     const float inv_n = 1.0f / n3;
@@ -468,7 +469,7 @@ __device__ __forceinline__ void lcc_grad_steps(const Grid &g, int zb, int zc0, i
 // of the last 2R+1 x/y sums (summed directly, no running sums).
 template <int D, int R>
 __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
-    k_lcc_grad(Grid g, const float *__restrict__ F, const float *__restrict__ W,
+    k_lcc_grad(Grid g, int zc, const float *__restrict__ F, const float *__restrict__ W,
                const uint8_t *__restrict__ m, const float *__restrict__ coef,
                float *__restrict__ gout)
 {
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
     extern __shared__ float smf[];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
-    const int zc0 = blockIdx.z * C::ZC, zc1 = min(zc0 + C::ZC, g.Z);
+    const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, g.Z);
     const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y, pl = lcc_plane(g.nv);
     float pa[C::KL], pb[C::KL], pc[C::KL];
     float3 ring[C::NR];
@@ -517,6 +518,27 @@ __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
                                 core, zi_end);
 }
 
+// z chunk of an LCC kernel: its default ZC, shortened on small grids so
+// that the launch still has about two blocks per SM of a 152-SM GB300 (down
+// to 2 slices, each chunk re-reading its 2R-slice halo). Depends on the grid
+// only, so workspace sizes and launches agree.
+int lcc_chunk(const Grid &g, int tiles_xy, int zc_default)
+{
+    if (g.ndim != 3)
+        return 1;
+    const int want = 2 * 152;
+    const int chunks = (want + tiles_xy - 1) / tiles_xy;
+    const int zc = (g.Z + chunks - 1) / chunks;
+    return zc < 2 ? 2 : (zc > zc_default ? zc_default : zc);
+}
+
+template <int D, int R>
+int lcc_stats_chunk(const Grid &g)
+{
+    using A = LccA<D, R>;
+    return lcc_chunk(g, ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY), A::ZC);
+}
+
 template <int D, int R>
 cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, const uint8_t *m,
                     float *gout, double *part, float *coef, cudaStream_t s)
@@ -529,9 +551,10 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     if (e != cudaSuccess)
         return e;
     {
-        dim3 grid((g.X + A::TX - 1) / A::TX, (g.Y + A::TY - 1) / A::TY, (g.Z + A::ZC - 1) / A::ZC);
+        const int zc = lcc_stats_chunk<D, R>(g);
+        dim3 grid((g.X + A::TX - 1) / A::TX, (g.Y + A::TY - 1) / A::TY, (g.Z + zc - 1) / zc);
         ProfScope ps(s, "k_lcc_stats");
-        k_lcc_stats<D, R><<<grid, A::THREADS, A::smem, s>>>(g, (float)eps, F, W, m,
+        k_lcc_stats<D, R><<<grid, A::THREADS, A::smem, s>>>(g, zc, (float)eps, F, W, m,
                                                             gout ? coef : nullptr, part);
     }
     if ((e = cudaGetLastError()) != cudaSuccess || !gout)
@@ -541,9 +564,11 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     if (e != cudaSuccess)
         return e;
     {
-        dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + B::ZC - 1) / B::ZC);
+        const int tiles = ((g.X + B::TX - 1) / B::TX) * ((g.Y + B::TY - 1) / B::TY);
+        const int zc = lcc_chunk(g, tiles, B::ZC);
+        dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + zc - 1) / zc);
         ProfScope ps(s, "k_lcc_grad");
-        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, F, W, m, coef, gout);
+        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, zc, F, W, m, coef, gout);
     }
     return cudaGetLastError();
 }
@@ -552,7 +577,8 @@ template <int D, int R>
 int lcc_blocks(const Grid &g)
 {
     using A = LccA<D, R>;
-    return ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY) * ((g.Z + A::ZC - 1) / A::ZC);
+    const int zc = lcc_stats_chunk<D, R>(g);
+    return ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY) * ((g.Z + zc - 1) / zc);
 }
 
 }  // namespace
