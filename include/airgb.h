@@ -269,6 +269,69 @@ size_t al_pyramid_workspace_bytes(const al_grid *g, int32_t factor);
 al_status al_bspline_refine(const al_bspline *coarse, const float *ctrl_coarse,
                             const al_bspline *fine, float *ctrl_fine, al_stream stream);
 
+/* ---- Batches of independent problems ---------------------------------------
+ * Many registration pairs of uneven sizes optimised together (the paper
+ * registers one pair at a time; this is a throughput service of the
+ * library): every iteration of every problem -- the fused objective and
+ * gradient of its MSE objective and its Adam step -- runs in ONE persistent
+ * kernel launch whose blocks take work items from a device queue. A batch
+ * holds problems of one spacing in {4, 6, 8} with the MSE similarity, 2D and
+ * 3D mixed (AL_ERR_UNSUPPORTED otherwise). Each problem's coefficients follow
+ * the same arithmetic as al_objective_grad + al_adam_step, bit for bit. */
+typedef struct al_batch al_batch; /* opaque host-side plan */
+
+/* Plan a batch of `count` problems (host only, allocates host memory only;
+ * free it with al_batch_destroy). */
+al_status al_batch_create(const al_problem *problems, int32_t count, al_batch **out);
+void al_batch_destroy(al_batch *batch);
+/* Device workspace of the batch: queue counters, descriptors, work items and
+ * every problem's partial sums. */
+size_t al_batch_workspace_bytes(const al_batch *batch);
+/* Number of work items of one iteration; per_kind (nullable, 3 entries)
+ * receives the bricks, Gram tiles and control chunks among them. */
+int32_t al_batch_items(const al_batch *batch, int32_t *per_kind);
+
+/* Attach the problems' device arrays (host arrays of `count` device
+ * pointers): fixed and moving images, coefficients (updated in place by
+ * al_batch_step), Adam moments m and v (zero before the first step), and
+ * optional value histories values[i] (nullable array or entries) of rows of
+ * 4 doubles {J, S, R, n_mask}. Uploads the descriptors and the work items to
+ * the workspace with synchronous copies (not capturable; call it before any
+ * capture). The workspace stays bound to the batch until the next bind. */
+al_status al_batch_bind(al_batch *batch, const float *const *fixed, const float *const *moving,
+                        float *const *ctrl, float *const *adam_m, float *const *adam_v,
+                        double *const *values, void *workspace, size_t workspace_bytes);
+
+/* One Adam iteration (Sec. II-A, Optimization) of every problem: J and dJ/dc
+ * at the current coefficients, then the Adam step t = `step` (1-based) as
+ * al_adam_step takes it. When record >= 0, row `record` of each value
+ * history receives {J, S, R, n_mask} before the step. A memset and one
+ * kernel launch on `stream`: capturable in a CUDA graph. */
+al_status al_batch_step(const al_batch *batch, const al_adam_params *p, int64_t step,
+                        int32_t record, al_stream stream);
+
+/* Autotuner: times `iterations` gradient-only iterations (coefficients and
+ * moments untouched) of each work-item order the library knows (4) and
+ * keeps the fastest. ms (nullable, 4 entries) receives the milliseconds per
+ * iteration of each order, chosen (nullable) the order kept. Synchronises
+ * the stream; not capturable. Orders: 0 problems as given, 1 largest
+ * problem first, 2 round-robin over problems, 3 Gram tiles first. */
+al_status al_batch_tune(al_batch *batch, const al_adam_params *p, int32_t iterations,
+                        double *ms, int32_t *chosen, al_stream stream);
+/* Select a work-item order directly (0..3). */
+al_status al_batch_set_policy(al_batch *batch, int32_t policy);
+
+/* Bounded waits. A control chunk waits, polling a device counter, until
+ * every brick and tile of its problem is done; after max_polls polls it
+ * gives up, skips its work and records AL_ERR_TIMEOUT. extra_items > 0 makes
+ * the chunks wait for items that do not exist (a test of the timeout path:
+ * the kernel returns normally). Defaults: 0 and 20,000,000 polls. */
+al_status al_batch_set_wait(al_batch *batch, int32_t extra_items, int64_t max_polls);
+
+/* Synchronise `stream`, then read and clear the batch's error word: AL_OK or
+ * AL_ERR_TIMEOUT. */
+al_status al_batch_status(const al_batch *batch, al_stream stream);
+
 /* Synchronise `stream`, then read and clear the current device's kernel
  * error word: AL_OK, AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the
  * synchronisation itself failed). */

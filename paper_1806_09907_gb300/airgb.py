@@ -33,7 +33,9 @@ EXPORTS = (
     "al_objective_unfused_workspace_bytes", "al_get_device_error", "al_profile_enable",
     "al_profile_collect", "al_profile_reset", "al_similarity_noalloc", "al_noalloc_scratch_bytes",
     "al_adam_step", "al_pyramid_grid", "al_pyramid_level", "al_pyramid_workspace_bytes",
-    "al_bspline_refine",
+    "al_bspline_refine", "al_batch_create", "al_batch_destroy", "al_batch_workspace_bytes",
+    "al_batch_items", "al_batch_bind", "al_batch_step", "al_batch_tune", "al_batch_set_policy",
+    "al_batch_set_wait", "al_batch_status",
 )
 
 
@@ -108,6 +110,16 @@ def load():
         "al_pyramid_level": ([P(al_grid), VP, I32, VP, VP, SZ, VP], I32),
         "al_pyramid_workspace_bytes": ([P(al_grid), I32], SZ),
         "al_bspline_refine": ([P(al_bspline), VP, P(al_bspline), VP, VP], I32),
+        "al_batch_create": ([P(al_problem), I32, P(VP)], I32),
+        "al_batch_destroy": ([VP], None),
+        "al_batch_workspace_bytes": ([VP], SZ),
+        "al_batch_items": ([VP, P(I32)], I32),
+        "al_batch_bind": ([VP, P(VP), P(VP), P(VP), P(VP), P(VP), P(VP), VP, SZ], I32),
+        "al_batch_step": ([VP, P(al_adam_params), ctypes.c_int64, I32, VP], I32),
+        "al_batch_tune": ([VP, P(al_adam_params), I32, P(D), P(I32), VP], I32),
+        "al_batch_set_policy": ([VP, I32], I32),
+        "al_batch_set_wait": ([VP, I32, ctypes.c_int64], I32),
+        "al_batch_status": ([VP, VP], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -391,6 +403,88 @@ def al_bspline_refine(coarse_shape, fine_shape, spacing, ctrl_coarse, ctrl_fine=
     _call("al_bspline_refine", ctypes.byref(bc), _ptr(ctrl_coarse), ctypes.byref(bf),
           _ptr(ctrl_fine), _stream(stream))
     return ctrl_fine
+
+
+class Batch:
+    """Independent MSE problems (2D and 3D, one spacing) optimised together:
+    each iteration of every problem is one launch of the library's
+    persistent batch kernel. pairs: list of (fixed, moving) float32 CUDA
+    tensors. Holds the coefficients (``ctrl[i]``, voxel units, start at
+    zero), the Adam moments and, with history > 0, a (history, 4) float64
+    value history per problem."""
+
+    def __init__(self, pairs, spacing=8, lam=0.1, history=0, device=None):
+        load()
+        self.pairs = [(f, m) for f, m in pairs]
+        n = len(self.pairs)
+        dev = device or self.pairs[0][0].device
+        self.shapes = [tuple(f.shape) for f, _ in self.pairs]
+        self.spacing = int(spacing)
+        probs = (al_problem * n)(*[make_problem(sh, spacing, "mse", lam) for sh in self.shapes])
+        self._problems = probs
+        h = ctypes.c_void_p()
+        _call("al_batch_create", probs, n, ctypes.byref(h))
+        self._h = h
+        for (f, m), sh in zip(self.pairs, self.shapes):
+            _f32(f, sh, "fixed")
+            _f32(m, sh, "moving")
+        self.lattices = [(len(sh),) + lattice_shape(sh, spacing) for sh in self.shapes]
+        z = lambda ls: torch.zeros(ls, dtype=torch.float32, device=dev)
+        self.ctrl = [z(ls) for ls in self.lattices]
+        self.m = [z(ls) for ls in self.lattices]
+        self.v = [z(ls) for ls in self.lattices]
+        self.values = [torch.zeros((history, 4), dtype=torch.float64, device=dev)
+                       for _ in range(n)] if history > 0 else None
+        self.policy = 1  # the library's default order: largest problem first
+        self.workspace = torch.empty(max(int(load().al_batch_workspace_bytes(h)), 256),
+                                     dtype=torch.uint8, device=dev)
+        arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        self._ptrs = [arr([f for f, _ in self.pairs]), arr([m for _, m in self.pairs]),
+                      arr(self.ctrl), arr(self.m), arr(self.v),
+                      arr(self.values) if self.values is not None else None]
+        _call("al_batch_bind", h, *self._ptrs, ctypes.c_void_p(self.workspace.data_ptr()),
+              ctypes.c_size_t(self.workspace.numel()))
+
+    def items(self):
+        per = (ctypes.c_int32 * 3)()
+        total = load().al_batch_items(self._h, per)
+        return total, tuple(per)
+
+    @staticmethod
+    def _adam(lr, betas, eps):
+        return al_adam_params(float(lr), float(betas[0]), float(betas[1]), float(eps))
+
+    def step(self, t, record=-1, lr=0.01, betas=(0.9, 0.999), eps=1e-8, stream=None):
+        """Adam iteration t (1-based) of every problem, one kernel launch."""
+        p = self._adam(lr, betas, eps)
+        _call("al_batch_step", self._h, ctypes.byref(p), int(t), int(record), _stream(stream))
+
+    def tune(self, iterations=3, lr=0.01, betas=(0.9, 0.999), eps=1e-8, stream=None):
+        """Time every work-item order and keep the fastest; returns
+        (chosen order, ms per iteration of each order)."""
+        p = self._adam(lr, betas, eps)
+        ms = (ctypes.c_double * 4)()
+        chosen = ctypes.c_int32()
+        _call("al_batch_tune", self._h, ctypes.byref(p), int(iterations), ms,
+              ctypes.byref(chosen), _stream(stream))
+        self.policy = int(chosen.value)
+        return self.policy, list(ms)
+
+    def set_policy(self, policy):
+        _call("al_batch_set_policy", self._h, int(policy))
+        self.policy = int(policy)
+
+    def set_wait(self, extra_items=0, max_polls=20000000):
+        _call("al_batch_set_wait", self._h, int(extra_items), int(max_polls))
+
+    def status(self, stream=None) -> int:
+        return int(load().al_batch_status(self._h, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.al_batch_destroy(h)
+            self._h = None
 
 
 def al_get_device_error(stream=None) -> int:

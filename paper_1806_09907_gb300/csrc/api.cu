@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include "airgb.h"
+#include "checks.h"
 #include "launch.h"
 
 using namespace airgb;
@@ -14,6 +15,10 @@ __device__ int g_device_error = 0;
 
 constexpr int64_t kMaxAxis = 1 << 20;
 constexpr int64_t kMaxVoxels = ((int64_t)1 << 31) - 1;
+
+}  // namespace
+
+namespace airgb {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -96,6 +101,10 @@ al_status check_sim(const al_sim_params *p, int ndim)
 }
 
 al_status launched(cudaError_t e) { return e == cudaSuccess ? AL_OK : AL_ERR_CUDA; }
+
+}  // namespace airgb
+
+namespace {
 
 cudaStream_t S(al_stream s) { return (cudaStream_t)s; }
 

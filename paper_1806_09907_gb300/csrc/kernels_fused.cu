@@ -139,14 +139,20 @@ __device__ __forceinline__ void flush_planes(int lp0, const float (&qz)[4][FCfg<
     }
 }
 
+// One brick (bx, by, bz) of one problem: the whole per-voxel work of the
+// brick, its partial sums written to bpart / mpart at index `brick`. Every
+// thread of a block of FCfg::THREADS threads calls it; it uses the block's
+// shared memory (static arrays here and FCfg::dyn_smem of dynamic memory).
 template <int D, int DELTA, int MODE>
-__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
-                                  (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
-                                                                                            : 1)
-    k_fused(Grid g, Lattice L, const float *__restrict__ F, const float *__restrict__ M,
-            const float *__restrict__ c, const float *__restrict__ gw_in,
-            float *__restrict__ W_out, uint8_t *__restrict__ m_out, float *__restrict__ G_io,
-            float *__restrict__ bpart, double *__restrict__ mpart)
+__device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
+                                            const float *__restrict__ F,
+                                            const float *__restrict__ M,
+                                            const float *__restrict__ c,
+                                            const float *__restrict__ gw_in,
+                                            float *__restrict__ W_out, uint8_t *__restrict__ m_out,
+                                            float *__restrict__ G_io, float *__restrict__ bpart,
+                                            double *__restrict__ mpart, int bx, int by, int bz,
+                                            int brick)
 {
     // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
     // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
@@ -161,9 +167,8 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int cx0 = blockIdx.x * C::BCX, cy0 = blockIdx.y * C::BCY, cz0 = blockIdx.z * C::BCZ;
+    const int cx0 = bx * C::BCX, cy0 = by * C::BCY, cz0 = bz * C::BCZ;
     const int x = cx0 * DELTA + tx, y = cy0 * DELTA + ty, z0 = (D == 3) ? cz0 * DELTA : 0;
-    const int brick = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 
     if (tid < DELTA * 4)
         wt[tid / 4][tid % 4] = L.w[tid / 4][tid % 4];
@@ -396,6 +401,20 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
     }
 }
 
+template <int D, int DELTA, int MODE>
+__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
+                                  (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
+                                                                                            : 1)
+    k_fused(Grid g, Lattice L, const float *__restrict__ F, const float *__restrict__ M,
+            const float *__restrict__ c, const float *__restrict__ gw_in,
+            float *__restrict__ W_out, uint8_t *__restrict__ m_out, float *__restrict__ G_io,
+            float *__restrict__ bpart, double *__restrict__ mpart)
+{
+    const int brick = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    fused_brick<D, DELTA, MODE>(g, L, F, M, c, gw_in, W_out, m_out, G_io, bpart, mpart,
+                                blockIdx.x, blockIdx.y, blockIdx.z, brick);
+}
+
 // ---------------------------------------------------------------------------
 // Gram-form diffusion regulariser on the control lattice.
 // Band entries of G = B^T B and H = (DB)^T (DB) along one axis of size N:
@@ -438,30 +457,44 @@ __device__ void band_entry(const Lattice &L, int N, int n, int j, int o, float &
 
 constexpr int kGramT3 = 8, kGramT2 = 16, kGramThreads = 256;
 
-__global__ void __launch_bounds__(kGramThreads)
-    k_gram3(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
-            double *__restrict__ rpart)
+// One tile (tile x, y, z) of component i of dR/dc on the lattice; the
+// tile's share of R (before the 1/|X|) goes to *rpart. Every thread of the
+// block calls it (any block size up to 1024).
+// Shared floats a Gram tile needs (carved from the caller's dynamic memory).
+constexpr int kGram3Floats = 14 * 14 * 14 + 2 * 14 * 14 * 8 + 3 * 14 * 8 * 8 + 2 * 3 * 8 * 7;
+constexpr int kGram2Floats = 22 * 22 + 2 * 22 * 16 + 2 * 2 * 16 * 7;
+
+__device__ __forceinline__ void gram3_tile(const Grid &g, const Lattice &L,
+                                           const float *__restrict__ c, float gscale,
+                                           float *__restrict__ gR, int tile_x, int tile_y,
+                                           int tile_z, int i, double *rpart, float *sm)
 {
     constexpr int T = kGramT3, H3 = T + 6;
-    __shared__ float cs[H3][H3][H3];
-    __shared__ float A[H3][H3][T], B[H3][H3][T];
-    __shared__ float GA[H3][T][T], HB[H3][T][T], GB[H3][T][T];
-    __shared__ float tG[3][T][7], tH[3][T][7];
-    __shared__ double red[kGramThreads / 32];
-    // one component per block: blockIdx.z = component * (z tiles) + z tile
-    const int tz = (L.nz + T - 1) / T, i = (int)blockIdx.z / tz;
-    const int j0[3] = {(int)blockIdx.x * T, (int)blockIdx.y * T, ((int)blockIdx.z - i * tz) * T};
+    static_assert(kGram3Floats == H3 * H3 * H3 + 2 * H3 * H3 * T + 3 * H3 * T * T + 2 * 3 * T * 7,
+                  "Gram tile layout");
+    auto cs = reinterpret_cast<float (*)[H3][H3]>(sm);
+    auto A = reinterpret_cast<float (*)[H3][T]>(sm + H3 * H3 * H3);
+    auto B = reinterpret_cast<float (*)[H3][T]>(sm + H3 * H3 * H3 + H3 * H3 * T);
+    float *const g0 = sm + H3 * H3 * H3 + 2 * H3 * H3 * T;
+    auto GA = reinterpret_cast<float (*)[T][T]>(g0);
+    auto HB = reinterpret_cast<float (*)[T][T]>(g0 + H3 * T * T);
+    auto GB = reinterpret_cast<float (*)[T][T]>(g0 + 2 * H3 * T * T);
+    auto tG = reinterpret_cast<float (*)[T][7]>(g0 + 3 * H3 * T * T);
+    auto tH = reinterpret_cast<float (*)[T][7]>(g0 + 3 * H3 * T * T + 3 * T * 7);
+    __shared__ double red[32];
+    const int nthr = blockDim.x;
+    const int j0[3] = {tile_x * T, tile_y * T, tile_z * T};
     const int nn[3] = {L.nx, L.ny, L.nz};
     const int NN[3] = {g.X, g.Y, g.Z};
     const int tid = threadIdx.x;
-    for (int e = tid; e < 3 * T * 7; e += kGramThreads) {
+    for (int e = tid; e < 3 * T * 7; e += nthr) {
         const int k = e / (T * 7), r = e - k * T * 7, l = r / 7, o = r - l * 7 - 3;
         band_entry(L, NN[k], nn[k], j0[k] + l, o, tG[k][l][o + 3], tH[k][l][o + 3]);
     }
     float rsum = 0.0f;
     {
         __syncthreads();
-        for (int e = tid; e < H3 * H3 * H3; e += kGramThreads) {
+        for (int e = tid; e < H3 * H3 * H3; e += nthr) {
             const int lz = e / (H3 * H3), r = e - lz * H3 * H3, ly = r / H3, lx = r - ly * H3;
             const int jx = j0[0] + lx - 3, jy = j0[1] + ly - 3, jz = j0[2] + lz - 3;
             float v = 0.0f;
@@ -470,7 +503,7 @@ __global__ void __launch_bounds__(kGramThreads)
             (&cs[0][0][0])[e] = v;
         }
         __syncthreads();
-        for (int e = tid; e < H3 * H3 * T; e += kGramThreads) {
+        for (int e = tid; e < H3 * H3 * T; e += nthr) {
             const int lz = e / (H3 * T), r = e - lz * H3 * T, ly = r / T, lx = r - ly * T;
             float a = 0.f, b = 0.f;
 #pragma unroll
@@ -483,7 +516,7 @@ __global__ void __launch_bounds__(kGramThreads)
             B[lz][ly][lx] = b;
         }
         __syncthreads();
-        for (int e = tid; e < H3 * T * T; e += kGramThreads) {
+        for (int e = tid; e < H3 * T * T; e += nthr) {
             const int lz = e / (T * T), r = e - lz * T * T, ly = r / T, lx = r - ly * T;
             float ga = 0.f, hb = 0.f, gb = 0.f;
 #pragma unroll
@@ -498,7 +531,7 @@ __global__ void __launch_bounds__(kGramThreads)
             GB[lz][ly][lx] = gb;
         }
         __syncthreads();
-        for (int e = tid; e < T * T * T; e += kGramThreads) {
+        for (int e = tid; e < T * T * T; e += nthr) {
             const int lz = e / (T * T), r = e - lz * T * T, ly = r / T, lx = r - ly * T;
             const int jx = j0[0] + lx, jy = j0[1] + ly, jz = j0[2] + lz;
             if (jx >= L.nx || jy >= L.ny || jz >= L.nz)
@@ -516,32 +549,47 @@ __global__ void __launch_bounds__(kGramThreads)
     double acc[1] = {rsum};
     block_reduce_d<1>(acc, red);
     if (tid == 0)
-        rpart[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc[0];
+        *rpart = acc[0];
 }
 
 __global__ void __launch_bounds__(kGramThreads)
-    k_gram2(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
+    k_gram3(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
             double *__restrict__ rpart)
 {
+    // one component per block: blockIdx.z = component * (z tiles) + z tile
+    const int tz = (L.nz + kGramT3 - 1) / kGramT3, i = (int)blockIdx.z / tz;
+    extern __shared__ float gsm[];
+    gram3_tile(g, L, c, gscale, gR, blockIdx.x, blockIdx.y, (int)blockIdx.z - i * tz, i,
+               rpart + (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x, gsm);
+}
+
+
+__device__ __forceinline__ void gram2_tile(const Grid &g, const Lattice &L,
+                                           const float *__restrict__ c, float gscale,
+                                           float *__restrict__ gR, int tile_x, int tile_y, int i,
+                                           double *rpart, float *sm)
+{
     constexpr int T = kGramT2, H2 = T + 6;
-    __shared__ float cs[H2][H2];
-    __shared__ float A[H2][T], B[H2][T];
-    __shared__ float tG[2][T][7], tH[2][T][7];
-    __shared__ double red[kGramThreads / 32];
-    // one component per block: blockIdx.y = component * (y tiles) + y tile
-    const int ty = (L.ny + T - 1) / T, i = (int)blockIdx.y / ty;
-    const int j0[2] = {(int)blockIdx.x * T, ((int)blockIdx.y - i * ty) * T};
+    static_assert(kGram2Floats == H2 * H2 + 2 * H2 * T + 2 * 2 * T * 7, "Gram tile layout");
+    auto cs = reinterpret_cast<float (*)[H2]>(sm);
+    auto A = reinterpret_cast<float (*)[T]>(sm + H2 * H2);
+    auto B = reinterpret_cast<float (*)[T]>(sm + H2 * H2 + H2 * T);
+    auto tG = reinterpret_cast<float (*)[T][7]>(sm + H2 * H2 + 2 * H2 * T);
+    auto tH = reinterpret_cast<float (*)[T][7]>(sm + H2 * H2 + 2 * H2 * T + 2 * T * 7);
+    __shared__ double red[32];
+    const int nthr = blockDim.x;
+    const int j0[2] = {tile_x * T, tile_y * T};
     const int nn[2] = {L.nx, L.ny};
     const int NN[2] = {g.X, g.Y};
     const int tid = threadIdx.x;
-    for (int e = tid; e < 2 * T * 7; e += kGramThreads) {
+    for (int e = tid; e < 2 * T * 7; e += nthr) {
         const int k = e / (T * 7), r = e - k * T * 7, l = r / 7, o = r - l * 7 - 3;
         band_entry(L, NN[k], nn[k], j0[k] + l, o, tG[k][l][o + 3], tH[k][l][o + 3]);
     }
     float rsum = 0.0f;
     {
         __syncthreads();
-        for (int e = tid; e < H2 * H2; e += kGramThreads) {
+        for (int e = tid; e < H2 * H2; e += nthr) {
             const int ly = e / H2, lx = e - ly * H2;
             const int jx = j0[0] + lx - 3, jy = j0[1] + ly - 3;
             float v = 0.0f;
@@ -550,7 +598,7 @@ __global__ void __launch_bounds__(kGramThreads)
             cs[ly][lx] = v;
         }
         __syncthreads();
-        for (int e = tid; e < H2 * T; e += kGramThreads) {
+        for (int e = tid; e < H2 * T; e += nthr) {
             const int ly = e / T, lx = e - ly * T;
             float a = 0.f, b = 0.f;
 #pragma unroll
@@ -563,7 +611,7 @@ __global__ void __launch_bounds__(kGramThreads)
             B[ly][lx] = b;
         }
         __syncthreads();
-        for (int e = tid; e < T * T; e += kGramThreads) {
+        for (int e = tid; e < T * T; e += nthr) {
             const int ly = e / T, lx = e - ly * T;
             const int jx = j0[0] + lx, jy = j0[1] + ly;
             if (jx >= L.nx || jy >= L.ny)
@@ -581,11 +629,34 @@ __global__ void __launch_bounds__(kGramThreads)
     double acc[1] = {rsum};
     block_reduce_d<1>(acc, red);
     if (tid == 0)
-        rpart[blockIdx.y * gridDim.x + blockIdx.x] = acc[0];
+        *rpart = acc[0];
 }
 
+__global__ void __launch_bounds__(kGramThreads)
+    k_gram2(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
+            double *__restrict__ rpart)
+{
+    // one component per block: blockIdx.y = component * (y tiles) + y tile
+    const int ty = (L.ny + kGramT2 - 1) / kGramT2, i = (int)blockIdx.y / ty;
+    extern __shared__ float gsm[];
+    gram2_tile(g, L, c, gscale, gR, blockIdx.x, (int)blockIdx.y - i * ty, i,
+               rpart + blockIdx.y * gridDim.x + blockIdx.x, gsm);
+}
+
+
 // ---------------------------------------------------------------------------
-template <int K>
+// Load of data that other blocks of the same launch wrote (CG: through L2,
+// bypassing the non-coherent L1) or of data written before the launch.
+template <bool CG, typename T>
+__device__ __forceinline__ T load_part(const T *p)
+{
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+template <int K, bool CG = false>
 __device__ void sum_parts(const double *__restrict__ p, int nb, double (&t)[K], double *red)
 {
 #pragma unroll
@@ -594,7 +665,7 @@ __device__ void sum_parts(const double *__restrict__ p, int nb, double (&t)[K], 
     for (int b = threadIdx.x; b < nb; b += blockDim.x)
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            t[k] += p[(int64_t)b * K + k];
+            t[k] += load_part<CG>(p + (int64_t)b * K + k);
     block_reduce_d<K>(t, red);
 }
 
@@ -607,16 +678,17 @@ struct Parts {
     int nbricks, ngram, nlcc;
 };
 
+template <bool CG = false>
 __device__ void objective_scalars(int mode, int64_t nv, double lambda, double eps, const Parts &P,
                                   double *value, double *k, double *red)
 {
     double r[1];
-    sum_parts<1>(P.rpart, P.ngram, r, red);
+    sum_parts<1, CG>(P.rpart, P.ngram, r, red);
     const double R = r[0] / (double)nv;
     double S = 0.0, n = 0.0;
     if (mode == MODE_MSE) {
         double t[2];
-        sum_parts<2>(P.mpart, P.nbricks, t, red);
+        sum_parts<2, CG>(P.mpart, P.nbricks, t, red);
         if (threadIdx.x == 0) {
             n = t[1];
             S = n > 0.0 ? t[0] / n : 0.0;
@@ -624,7 +696,7 @@ __device__ void objective_scalars(int mode, int64_t nv, double lambda, double ep
         }
     } else if (mode == MODE_NCC) {
         double t[6];
-        sum_parts<6>(P.mpart, P.nbricks, t, red);
+        sum_parts<6, CG>(P.mpart, P.nbricks, t, red);
         if (threadIdx.x == 0) {
             n = t[0];
             k[0] = k[1] = k[2] = 0.0;
@@ -644,7 +716,7 @@ __device__ void objective_scalars(int mode, int64_t nv, double lambda, double ep
         }
     } else {  // LCC
         double t[2];
-        sum_parts<2>(P.lpart, P.nlcc, t, red);
+        sum_parts<2, CG>(P.lpart, P.nlcc, t, red);
         if (threadIdx.x == 0) {
             n = t[1];
             S = n > 0.0 ? 1.0 - t[0] / n : 0.0;
@@ -669,6 +741,60 @@ __global__ void k_finalize(int mode, int64_t nv, double lambda, double eps, Part
     objective_scalars(mode, nv, lambda, eps, P, value, k, red);
 }
 
+// dJ/dc at control point e: the fixed-order sum of the partials of the (at
+// most two per axis) bricks that touch it, the channel combination with the
+// scalars k0..k2, plus lambda * dR/dc. CG: the partials were written by other
+// blocks of the same launch.
+template <int D, int CH, int BCX, int BCY, int BCZ, bool CG>
+__device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, int gbz,
+                                           const float *__restrict__ bpart,
+                                           const float *__restrict__ gR, int64_t e, float k0,
+                                           float k1, float k2, float lam, float (&out)[D])
+{
+    constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
+    constexpr int NPART = CH * JZ * JY * JX;
+    const int64_t total = (int64_t)L.nc;
+    const int jx = (int)(e % L.nx);
+    const int64_t r = e / L.nx;
+    const int jy = (int)(r % L.ny), jz = (int)(r / L.ny);
+    float p[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+        p[k] = 0.0f;
+    const int bz_hi = (D == 3) ? min(jz / BCZ, gbz - 1) : 0;
+    const int bz_lo = (D == 3) ? max(0, jz / BCZ - 1) : 0;
+    for (int bz = bz_lo; bz <= bz_hi; ++bz) {
+        const int lz = (D == 3) ? jz - bz * BCZ : 0;
+        if (lz >= JZ)
+            continue;
+        for (int by = max(0, jy / BCY - 1); by <= min(jy / BCY, gby - 1); ++by) {
+            const int ly = jy - by * BCY;
+            if (ly >= JY)
+                continue;
+            for (int bx = max(0, jx / BCX - 1); bx <= min(jx / BCX, gbx - 1); ++bx) {
+                const int lx = jx - bx * BCX;
+                if (lx >= JX)
+                    continue;
+                const int brick = (bz * gby + by) * gbx + bx;
+                const float *src = bpart + (int64_t)brick * NPART + (lz * JY + ly) * JX + lx;
+#pragma unroll
+                for (int k = 0; k < CH; ++k)
+                    p[k] += CG ? __ldcg(src + k * (JZ * JY * JX)) : __ldg(src + k * (JZ * JY * JX));
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float v;
+        if (CH == 3 * D)
+            v = fmaf(k0, p[i], fmaf(k1, p[D + i], k2 * p[2 * D + i]));
+        else
+            v = k0 * p[i];
+        const float gr = CG ? __ldcg(gR + (int64_t)i * total + e) : __ldg(gR + (int64_t)i * total + e);
+        out[i] = fmaf(lam, gr, v);
+    }
+}
+
 // Per control point: fixed-order sum of the partials of the bricks that
 // touch it, channel combination, plus lambda * dR/dc.
 // Every block first evaluates the scalars of the objective (the partial
@@ -679,8 +805,6 @@ __global__ void __launch_bounds__(256)
            Parts P, const float *__restrict__ bpart, const float *__restrict__ gR,
            float *__restrict__ gc, double *__restrict__ value)
 {
-    constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
-    constexpr int NPART = CH * JZ * JY * JX;
     __shared__ double red[6 * 8];
     __shared__ double ks[3];
     objective_scalars(mode, nv, lambda, eps, P, blockIdx.x == 0 ? value : nullptr, ks, red);
@@ -694,44 +818,12 @@ __global__ void __launch_bounds__(256)
     const float lam = (float)lambda;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int jx = (int)(e % L.nx);
-        const int64_t r = e / L.nx;
-        const int jy = (int)(r % L.ny), jz = (int)(r / L.ny);
-        float p[CH];
+        float v[D];
+        ctrl_point<D, CH, BCX, BCY, BCZ, false>(L, gbx, gby, gbz, bpart, gR, e, k0, k1, k2, lam,
+                                                v);
 #pragma unroll
-        for (int k = 0; k < CH; ++k)
-            p[k] = 0.0f;
-        const int bz_hi = (D == 3) ? min(jz / BCZ, gbz - 1) : 0;
-        const int bz_lo = (D == 3) ? max(0, jz / BCZ - 1) : 0;
-        for (int bz = bz_lo; bz <= bz_hi; ++bz) {
-            const int lz = (D == 3) ? jz - bz * BCZ : 0;
-            if (lz >= JZ)
-                continue;
-            for (int by = max(0, jy / BCY - 1); by <= min(jy / BCY, gby - 1); ++by) {
-                const int ly = jy - by * BCY;
-                if (ly >= JY)
-                    continue;
-                for (int bx = max(0, jx / BCX - 1); bx <= min(jx / BCX, gbx - 1); ++bx) {
-                    const int lx = jx - bx * BCX;
-                    if (lx >= JX)
-                        continue;
-                    const int brick = (bz * gby + by) * gbx + bx;
-                    const float *src = bpart + (int64_t)brick * NPART + (lz * JY + ly) * JX + lx;
-#pragma unroll
-                    for (int k = 0; k < CH; ++k)
-                        p[k] += __ldg(src + k * (JZ * JY * JX));
-                }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            float v;
-            if (CH == 3 * D)
-                v = fmaf(k0, p[i], fmaf(k1, p[D + i], k2 * p[2 * D + i]));
-            else
-                v = k0 * p[i];
-            gc[(int64_t)i * total + e] = fmaf(lam, __ldg(gR + (int64_t)i * total + e), v);
-        }
+        for (int i = 0; i < D; ++i)
+            gc[(int64_t)i * total + e] = v[i];
     }
 }
 
@@ -827,10 +919,10 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     if (D == 3) {
         dim3 gg((L.nx + kGramT3 - 1) / kGramT3, (L.ny + kGramT3 - 1) / kGramT3,
                 3 * ((L.nz + kGramT3 - 1) / kGramT3));
-        k_gram3<<<gg, kGramThreads, 0, s>>>(g, L, c, gscale, gR, rpart);
+        k_gram3<<<gg, kGramThreads, kGram3Floats * sizeof(float), s>>>(g, L, c, gscale, gR, rpart);
     } else {
         dim3 gg((L.nx + kGramT2 - 1) / kGramT2, 2 * ((L.ny + kGramT2 - 1) / kGramT2));
-        k_gram2<<<gg, kGramThreads, 0, s>>>(g, L, c, gscale, gR, rpart);
+        k_gram2<<<gg, kGramThreads, kGram2Floats * sizeof(float), s>>>(g, L, c, gscale, gR, rpart);
     }
     prof_end(s);
     if ((e = cudaGetLastError()) != cudaSuccess)
@@ -888,6 +980,175 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     return e;
 }
 
+// ---------------------------------------------------------------------------
+// Batches: one persistent launch per iteration over many problems.
+//
+// The launch's blocks take work items from a device queue (one atomic
+// counter) in the order of the item list. Phase A items -- the bricks and
+// the Gram tiles of every problem -- come first and wait for nothing; phase B
+// items -- chunks of a problem's control points: fixed-order sum of its
+// brick partials, dJ/dc and the Adam step -- wait until every phase A item of
+// their problem has published its results. Every phase A item is taken
+// before any phase B item, by a block that is running, so a wait only ever
+// waits for running blocks; it is bounded anyway (BatchStep::spin_limit
+// polls, then AL_ERR_TIMEOUT in the error word and the chunk is skipped).
+// The per-item arithmetic is that of k_fused, k_gram and k_ctrl + k_adam, so
+// a problem's coefficients follow the single-problem path bit for bit.
+template <int DELTA>
+struct BCfg {
+    using C3 = FCfg<3, DELTA, MODE_MSE>;
+    using C2 = FCfg<2, DELTA, MODE_MSE>;
+    static constexpr int THREADS = C3::THREADS;
+    static_assert(C2::THREADS == THREADS, "2D and 3D bricks share the block size");
+    static constexpr size_t fsm = C3::dyn_smem > C2::dyn_smem ? C3::dyn_smem : C2::dyn_smem;
+    static constexpr size_t gsm = (size_t)kGram3Floats * sizeof(float);  // > the 2D tile
+    static constexpr size_t dyn_smem = fsm > gsm ? fsm : gsm;
+};
+
+__device__ __forceinline__ int load_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int D, int DELTA>
+__device__ __forceinline__ void batch_ctrl_adam(const BatchProblem &P, const BatchStep &st,
+                                                int64_t e, float k0, float inv_bc1,
+                                                float inv_bc2)
+{
+    constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
+    float gv[D];
+    ctrl_point<D, D, BCX, BCY, BCZ, true>(P.L, P.gbx, P.gby, P.gbz, P.bpart, P.gR, e, k0, 0.0f,
+                                          0.0f, (float)P.lambda, gv);
+    if (!st.update)
+        return;
+    const float b1 = (float)st.beta1, b2 = (float)st.beta2;
+    const float omb1 = (float)(1.0 - st.beta1), omb2 = (float)(1.0 - st.beta2);
+    const int64_t nc = P.L.nc;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const int64_t q = i * nc + e;
+        const float h = P.h[i];
+        const float gn = gv[i] * h;
+        const float mm = fmaf(b1, P.m[q], omb1 * gn);
+        const float vv = fmaf(b2, P.v[q], omb2 * gn * gn);
+        P.m[q] = mm;
+        P.v[q] = vv;
+        const float den = sqrtf(vv * inv_bc2) + st.eps;
+        P.c[q] -= (st.lr * h) * ((mm * inv_bc1) / den);
+    }
+}
+
+template <int DELTA>
+__global__ void __launch_bounds__(BCfg<DELTA>::THREADS, 1)
+    k_batch(const BatchProblem *__restrict__ probs, const BatchItem *__restrict__ items, int nitems,
+            int *__restrict__ counters, BatchStep st)
+{
+    __shared__ int s_item, s_ok;
+    __shared__ double red[6 * 32];
+    __shared__ double ks[3];
+    __shared__ float s_inv_bc[2];
+    if (threadIdx.x == 0) {
+        s_inv_bc[0] = (float)(1.0 / (1.0 - pow(st.beta1, (double)st.t)));
+        s_inv_bc[1] = (float)(1.0 / (1.0 - pow(st.beta2, (double)st.t)));
+    }
+    for (;;) {
+        __syncthreads();  // the previous item is done with shared memory
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(counters, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems)
+            break;
+        const BatchItem w = items[it];
+        const BatchProblem &P = probs[w.prob];
+        if (w.kind == BATCH_BRICK) {
+            const int bx = w.idx % P.gbx, r = w.idx / P.gbx, by = r % P.gby, bz = r / P.gby;
+            if (P.g.ndim == 3)
+                fused_brick<3, DELTA, MODE_MSE>(P.g, P.L, P.F, P.M, P.c, nullptr, nullptr, nullptr,
+                                                nullptr, P.bpart, P.mpart, bx, by, bz, w.idx);
+            else
+                fused_brick<2, DELTA, MODE_MSE>(P.g, P.L, P.F, P.M, P.c, nullptr, nullptr, nullptr,
+                                                nullptr, P.bpart, P.mpart, bx, by, bz, w.idx);
+        } else if (w.kind == BATCH_GRAM) {
+            // tile index = ((component * gtz + tz) * gty + ty) * gtx + tx
+            const int tx = w.idx % P.gtx, r = w.idx / P.gtx, ty = r % P.gty, r2 = r / P.gty;
+            const int tz = r2 % P.gtz, comp = r2 / P.gtz;
+            extern __shared__ float bsm[];
+            if (P.g.ndim == 3)
+                gram3_tile(P.g, P.L, P.c, P.gscale, P.gR, tx, ty, tz, comp, P.rpart + w.idx, bsm);
+            else
+                gram2_tile(P.g, P.L, P.c, P.gscale, P.gR, tx, ty, comp, P.rpart + w.idx, bsm);
+        }
+        if (w.kind != BATCH_CTRL) {
+            __syncthreads();  // every write of the item has been issued
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(counters + 1 + w.prob, 1);
+            }
+            continue;
+        }
+        // phase B: wait (bounded) for the problem's phase A items
+        if (threadIdx.x == 0) {
+            const int need = P.nA + st.extra_wait;
+            long long polls = 0;
+            int ok = 1;
+            while (load_acquire(counters + 1 + w.prob) < need) {
+                if (++polls > st.spin_limit) {
+                    ok = 0;
+                    atomicExch(st.err, 6 /* AL_ERR_TIMEOUT */);
+                    break;
+                }
+                __nanosleep(128);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok)
+            continue;
+        const Parts parts{P.mpart, P.rpart, nullptr, P.nbricks, P.ngram, 0};
+        double *val = (w.idx == 0 && P.values && st.record >= 0) ? P.values + 4 * st.record : nullptr;
+        objective_scalars<true>(MODE_MSE, P.g.nv, P.lambda, 0.0, parts, val, ks, red);
+        const float k0 = (float)ks[0];
+        const int64_t e = (int64_t)w.idx * blockDim.x + threadIdx.x;
+        if (e < P.L.nc) {
+            if (P.g.ndim == 3)
+                batch_ctrl_adam<3, DELTA>(P, st, e, k0, s_inv_bc[0], s_inv_bc[1]);
+            else
+                batch_ctrl_adam<2, DELTA>(P, st, e, k0, s_inv_bc[0], s_inv_bc[1]);
+        }
+    }
+}
+
+template <int DELTA>
+cudaError_t run_batch(int blocks, const BatchProblem *probs, const BatchItem *items, int nitems,
+                      int *counters, const BatchStep &st, cudaStream_t s)
+{
+    using B = BCfg<DELTA>;
+    cudaError_t e = cudaFuncSetAttribute(k_batch<DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)B::dyn_smem);
+    if (e != cudaSuccess)
+        return e;
+    ProfScope ps(s, "k_batch");
+    k_batch<DELTA><<<blocks, B::THREADS, B::dyn_smem, s>>>(probs, items, nitems, counters, st);
+    return cudaGetLastError();
+}
+
+template <int DELTA>
+int batch_occupancy()
+{
+    using B = BCfg<DELTA>;
+    if (cudaFuncSetAttribute(k_batch<DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)B::dyn_smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<DELTA>, B::THREADS, B::dyn_smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
 }  // namespace
 
 bool fused_supported(const Grid &g, const Lattice &L, int kind, int window)
@@ -920,6 +1181,54 @@ cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, 
         case 6: return run_all<2, 6>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
         case 8: return run_all<2, 8>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
         }
+    }
+    return cudaErrorInvalidValue;
+}
+
+void batch_geometry(const Grid &g, const Lattice &L, int *gb, int *gt, int *npart, int *nmom)
+{
+    const int D = g.ndim;
+    const int BCX = brick_bcx(L.delta), BCY = brick_bcy(L.delta), BCZ = brick_bcz(D);
+    const int cx = (g.X + L.delta - 1) / L.delta, cy = (g.Y + L.delta - 1) / L.delta;
+    const int cz = (D == 3) ? (g.Z + L.delta - 1) / L.delta : 1;
+    gb[0] = (cx + BCX - 1) / BCX;
+    gb[1] = (cy + BCY - 1) / BCY;
+    gb[2] = (cz + BCZ - 1) / BCZ;
+    const int T = (D == 3) ? kGramT3 : kGramT2;
+    gt[0] = (L.nx + T - 1) / T;
+    gt[1] = (L.ny + T - 1) / T;
+    gt[2] = (D == 3) ? (L.nz + T - 1) / T : 1;
+    *npart = D * ((D == 3) ? BCZ + 3 : 1) * (BCY + 3) * (BCX + 3);
+    *nmom = 2;
+}
+
+int batch_threads(int delta)
+{
+    switch (delta) {
+    case 4: return BCfg<4>::THREADS;
+    case 6: return BCfg<6>::THREADS;
+    case 8: return BCfg<8>::THREADS;
+    }
+    return 0;
+}
+
+int batch_blocks_per_sm(int delta)
+{
+    switch (delta) {
+    case 4: return batch_occupancy<4>();
+    case 6: return batch_occupancy<6>();
+    case 8: return batch_occupancy<8>();
+    }
+    return 0;
+}
+
+cudaError_t launch_batch(int delta, int blocks, const BatchProblem *probs, const BatchItem *items,
+                         int nitems, int *counters, const BatchStep &st, cudaStream_t s)
+{
+    switch (delta) {
+    case 4: return run_batch<4>(blocks, probs, items, nitems, counters, st, s);
+    case 6: return run_batch<6>(blocks, probs, items, nitems, counters, st, s);
+    case 8: return run_batch<8>(blocks, probs, items, nitems, counters, st, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -80,4 +80,50 @@ cudaError_t launch_pyramid(const Grid &g, int factor, const GaussTaps &t, const 
 cudaError_t launch_refine(int ndim, const int *nc, const int *nf, const float *cc, float *cf,
                           cudaStream_t s);
 
+// ---- batches of independent problems: one persistent launch per iteration ---
+// Device descriptor of one problem of a batch (MSE, the batch's spacing).
+struct BatchProblem {
+    Grid g;
+    Lattice L;
+    const float *F, *M;
+    float *c, *m, *v;  // coefficients (updated in place) and Adam moments
+    double *values;    // [rows][4] history {J, S, R, n_mask}, or null
+    float *bpart;      // brick partials
+    double *mpart;     // brick moment partials
+    double *rpart;     // Gram tile partials of R
+    float *gR;         // lambda-free dR/dc scaled by 2/|X| (as k_gram writes it)
+    float h[3];        // Adam: voxel units per normalised unit, (N_k - 1)/2
+    float gscale;      // 2/|X|
+    double lambda;
+    int gbx, gby, gbz, nbricks;  // brick grid
+    int gtx, gty, gtz, ngram;    // Gram tiles per axis and their total over components
+    int nA;                      // phase-A items: bricks + Gram tiles
+    int nchunks;                 // phase-B items: control-point chunks
+};
+
+enum { BATCH_BRICK = 0, BATCH_GRAM = 1, BATCH_CTRL = 2 };
+struct BatchItem {
+    int prob, kind, idx, pad;
+};
+
+// Arguments of one batched iteration.
+struct BatchStep {
+    double beta1, beta2;  // Adam decays (bias corrections formed in double)
+    float lr, eps;
+    int64_t t;            // 1-based Adam step
+    int record;           // row of each problem's value history to write, < 0: none
+    int update;           // 1: Adam step, 0: gradient only (timing runs)
+    int extra_wait;       // added to the items a control chunk waits for (test hook)
+    long long spin_limit; // polls before a waiting chunk gives up (AL_ERR_TIMEOUT)
+    int *err;             // error word
+};
+
+// Geometry of a problem in a batch of spacing delta: brick grid, Gram tiles,
+// floats of one brick's partials and doubles of its moments.
+void batch_geometry(const Grid &g, const Lattice &L, int *gb, int *gt, int *npart, int *nmom);
+int batch_threads(int delta);               // 0 if delta has no batch kernel
+int batch_blocks_per_sm(int delta);         // resident blocks of the batch kernel per SM
+cudaError_t launch_batch(int delta, int blocks, const BatchProblem *probs, const BatchItem *items,
+                         int nitems, int *counters, const BatchStep &st, cudaStream_t s);
+
 }  // namespace airgb

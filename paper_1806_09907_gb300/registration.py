@@ -169,9 +169,9 @@ class Result:
     seconds: float        # wall time of the whole registration, pyramid included
 
 
-def _level_loop(ev: Evaluator, F, M, c, iterations, lr, betas, eps, values):
+def _level_loop(ev: Evaluator, F, M, c, iterations, lr, betas, eps, values, final=True):
     """`iterations` Adam steps of the objective; values[i] receives J before
-    step i (and values[iterations] the final J)."""
+    step i (and, with final=True, values[iterations] the final J)."""
     m = torch.zeros_like(c)
     v = torch.zeros_like(c)
     step = torch.zeros(1, dtype=torch.int64, device=c.device)
@@ -182,7 +182,8 @@ def _level_loop(ev: Evaluator, F, M, c, iterations, lr, betas, eps, values):
             ev.evaluate(F, M, c, values[i], grad)
             airgb.al_adam_step(ev.shape, ev.spacing, c, grad, m, v, step, lr=lr, betas=betas,
                                eps=eps)
-        ev.evaluate(F, M, c, values[iterations], None)
+        if final:
+            ev.evaluate(F, M, c, values[iterations], None)
 
     return run
 
@@ -244,3 +245,65 @@ def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), it
         prev_shape = shape
     torch.cuda.synchronize(dev)
     return Result(c, levels, time.perf_counter() - t0)
+
+
+@dataclasses.dataclass
+class BatchResult:
+    batch: airgb.Batch    # ctrl[i]: final coefficients; values[i]: J history
+    device_ms: float      # the iterations' device time (CUDA events)
+    policy: int           # work-item order in use
+    tuning_ms: list       # ms per iteration of each order (empty if not tuned)
+
+
+def register_batch(pairs, spacing=8, lam=0.1, iterations=100, lr=0.01, betas=(0.9, 0.999),
+                   eps=1e-8, graph=True, tune=True):
+    """Single-level MSE registration of many (fixed, moving) pairs at once:
+    every iteration of every pair is one launch of the persistent batch
+    kernel; with graph=True all iterations are captured in one CUDA graph and
+    replayed once. values[i][k] holds {J, S, R, n_mask} before step k + 1."""
+    b = airgb.Batch(pairs, spacing, lam, history=iterations)
+    policy, tms = b.policy, []
+    if tune:
+        policy, tms = b.tune(3, lr, betas, eps)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            for k in range(iterations):
+                b.step(k + 1, k, lr, betas, eps)
+        start.record()
+        g.replay()
+        stop.record()
+    else:
+        start.record()
+        for k in range(iterations):
+            b.step(k + 1, k, lr, betas, eps)
+        stop.record()
+    stop.synchronize()
+    st = b.status()
+    if st != 0:
+        raise airgb.AirgbError("al_batch_status", st)
+    return BatchResult(b, start.elapsed_time(stop), policy, tms)
+
+
+def register_sequential(pairs, spacing=8, lam=0.1, iterations=100, lr=0.01, betas=(0.9, 0.999),
+                        eps=1e-8):
+    """The same registrations one pair after another with the single-problem
+    calls (al_objective_grad + al_adam_step per iteration, plain launches).
+    Returns (coefficients, value histories, device ms)."""
+    ctrls, hists = [], []
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = []
+    for F, M in pairs:
+        ev = Evaluator(tuple(F.shape), spacing, "mse", lam, device=F.device)
+        c = torch.zeros(ev.lattice, dtype=torch.float32, device=F.device)
+        vals = torch.empty((iterations + 1, 4), dtype=torch.float64, device=F.device)
+        runs.append((_level_loop(ev, F, M, c, iterations, lr, betas, eps, vals, final=False), c,
+                     vals))
+    start.record()
+    for run, _, _ in runs:
+        run()
+    stop.record()
+    stop.synchronize()
+    return [c for _, c, _ in runs], [v for _, _, v in runs], start.elapsed_time(stop)
+

@@ -40,6 +40,26 @@ def _coords(shape):
     return [grids[nd - 1 - k] for k in range(nd)]  # x first
 
 
+def _field_modes(shape, seed, n_modes, min_wavelength):
+    """Cosine modes of smooth_field: per component a list of (direction,
+    wavelength, phase, amplitude), drawn in a fixed order."""
+    nd = len(shape)
+    g = rng(seed, 1)
+    ext = np.array(shape[::-1], dtype=np.float64)  # sizes in x, y, z order
+    modes = []
+    for _ in range(nd):
+        comp = []
+        for _ in range(n_modes):
+            direction = g.normal(size=nd)
+            direction /= np.linalg.norm(direction)
+            wl = g.uniform(min_wavelength, 2.0 * ext.max())
+            phase = g.uniform(0.0, 2.0 * np.pi)
+            amp = g.normal()
+            comp.append((direction, wl, phase, amp))
+        modes.append(comp)
+    return modes
+
+
 def smooth_field(shape, rms: float, seed: int = FIELD_SEED, n_modes: int = 8,
                  min_wavelength: float = 24.0):
     """Random smooth displacement u*(x): per component a sum of cosine modes
@@ -47,18 +67,11 @@ def smooth_field(shape, rms: float, seed: int = FIELD_SEED, n_modes: int = 8,
     phases, rescaled to the requested root-mean-square (voxel units).
     Returns float64 (d, *shape), component 0 = x."""
     nd = len(shape)
-    g = rng(seed, 1)
     xs = _coords(shape)
-    ext = np.array(shape[::-1], dtype=np.float64)  # sizes in x, y, z order
     u = np.zeros((nd,) + tuple(shape), dtype=np.float64)
-    for i in range(nd):
+    for i, comp in enumerate(_field_modes(shape, seed, n_modes, min_wavelength)):
         acc = np.zeros(tuple(shape), dtype=np.float64)
-        for _ in range(n_modes):
-            direction = g.normal(size=nd)
-            direction /= np.linalg.norm(direction)
-            wl = g.uniform(min_wavelength, 2.0 * ext.max())
-            phase = g.uniform(0.0, 2.0 * np.pi)
-            amp = g.normal()
+        for direction, wl, phase, amp in comp:
             arg = phase
             for k in range(nd):
                 arg = arg + (2.0 * np.pi / wl) * direction[k] * xs[k]
@@ -202,3 +215,60 @@ def ct_pair(shape=(160, 256, 256), noise=20.0, field_rms=3.0, seed=IMAGE_SEED,
     fixed += noise * g.standard_normal(size=fixed.shape)
     moving += noise * g.standard_normal(size=moving.shape)
     return fixed.astype(np.float32), moving.astype(np.float32)
+
+
+def batch_sizes(n2d: int = 32, n3d: int = 32):
+    """Shapes of the batched workload: n2d 2D sizes linearly spaced from 96^2
+    to 512^2 (rounded to multiples of 16) and n3d 3D sizes from 64^3 to
+    192^3 (rounded to multiples of 8)."""
+    s2 = [int(round(v / 16.0)) * 16 for v in np.linspace(96, 512, n2d)]
+    s3 = [int(round(v / 8.0)) * 8 for v in np.linspace(64, 192, n3d)]
+    return [(s, s) for s in s2] + [(s, s, s) for s in s3]
+
+
+def blob_pair_device(shape, n_blobs, sigma_range, field_rms, seed=IMAGE_SEED,
+                     field_seed=FIELD_SEED, device="cuda"):
+    """blob_pair's recipe (same parameters from the same generators),
+    evaluated in float64 with torch on `device`: for workloads too large to
+    render on the host in reasonable time. Returns float32 tensors."""
+    import torch
+
+    nd = len(shape)
+    axes = [torch.arange(n, dtype=torch.float64, device=device) for n in shape]
+    grids = torch.meshgrid(*axes, indexing="ij")
+    xs = [grids[nd - 1 - k] for k in range(nd)]  # x first
+    field = []
+    for comp in _field_modes(shape, field_seed, 8, 4.0 * 8):
+        acc = torch.zeros(tuple(shape), dtype=torch.float64, device=device)
+        for direction, wl, phase, amp in comp:
+            arg = torch.full(tuple(shape), phase, dtype=torch.float64, device=device)
+            for k in range(nd):
+                arg = arg + (2.0 * np.pi / wl) * float(direction[k]) * xs[k]
+            acc = acc + amp * torch.cos(arg)
+        acc = acc - acc.mean()
+        field.append(acc * (field_rms / max(float(torch.sqrt(torch.mean(acc * acc))), 1e-30)))
+    blobs = blob_scene(shape, n_blobs, sigma_range, seed)
+
+    def render(p):
+        img = torch.zeros(tuple(shape), dtype=torch.float64, device=device)
+        for mu, sigma, amp in blobs:
+            r2 = sum((p[k] - float(mu[k])) ** 2 for k in range(nd))
+            img += amp * torch.exp(-r2 / (2.0 * sigma * sigma))
+        return img.to(torch.float32)
+
+    fixed = render(xs)
+    moving = render([xs[k] + field[k] for k in range(nd)])
+    return fixed.contiguous(), moving.contiguous()
+
+
+def batch_pairs(n2d: int = 32, n3d: int = 32, seed: int = IMAGE_SEED, device="cuda"):
+    """The batched workload's (fixed, moving) pairs on `device`: blob pairs
+    (20 blobs, sigma 4..16 in 2D; 60 blobs, sigma 3..12 in 3D; moving
+    deformed by ~2 voxels rms), one seed per pair."""
+    out = []
+    for i, sh in enumerate(batch_sizes(n2d, n3d)):
+        nb, sig = ((20, (4.0, 16.0)) if len(sh) == 2 else (60, (3.0, 12.0)))
+        out.append(blob_pair_device(sh, nb, sig, 2.0, seed + 100 * i, FIELD_SEED + 100 * i,
+                                    device))
+    return out
+

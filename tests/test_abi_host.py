@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_1806_09907_gb300 import airgb
@@ -157,3 +159,55 @@ def test_refine_rejects(lib):
     assert lib.al_bspline_refine(ctypes.byref(coarse), ctypes.c_void_p(0x10004),
                                  ctypes.byref(fine), p, None) == 3
     assert lib.al_bspline_refine(ctypes.byref(coarse), None, ctypes.byref(fine), p, None) == 1
+
+
+def _batch(lib, problems):
+    arr = (airgb.al_problem * len(problems))(*problems)
+    h = ctypes.c_void_p()
+    st = lib.al_batch_create(arr, len(problems), ctypes.byref(h))
+    return st, h
+
+
+def test_batch_plan_counts(lib):
+    shapes = [(96, 96), (200, 136), (40, 48, 56), (64, 64, 64)]
+    st, h = _batch(lib, [airgb.make_problem(s, 8, "mse", 0.1) for s in shapes])
+    assert st == 0
+    per = (ctypes.c_int32 * 3)()
+    total = lib.al_batch_items(h, per)
+    # bricks of 4 x 3 (x 4) cells of 8 voxels, Gram tiles of 16^2 / 8^3
+    # points per component, chunks of 768 control points
+    bricks = gram = chunks = 0
+    for s in shapes:
+        cells = [-(-n // 8) for n in s[::-1]]
+        b = [-(-cells[0] // 4), -(-cells[1] // 3)] + ([-(-cells[2] // 4)] if len(s) == 3 else [])
+        lat = [(n - 1) // 8 + 4 for n in s[::-1]]
+        t = 8 if len(s) == 3 else 16
+        bricks += int(np.prod(b))
+        gram += len(s) * int(np.prod([-(-n // t) for n in lat]))
+        chunks += -(-int(np.prod(lat)) // 768)
+    assert tuple(per) == (bricks, gram, chunks) and total == bricks + gram + chunks
+    assert lib.al_batch_workspace_bytes(h) > 0
+    lib.al_batch_destroy(h)
+
+
+def test_batch_rejects(lib):
+    # one spacing per batch, MSE only, spacings with a batch kernel
+    st, _ = _batch(lib, [airgb.make_problem((64, 64), 8), airgb.make_problem((64, 64), 6)])
+    assert st == 7
+    st, _ = _batch(lib, [airgb.make_problem((64, 64), 8, "lcc")])
+    assert st == 7
+    st, _ = _batch(lib, [airgb.make_problem((64, 64), 5)])
+    assert st == 7
+    h = ctypes.c_void_p()
+    assert lib.al_batch_create(None, 1, ctypes.byref(h)) == 1
+    st, h = _batch(lib, [airgb.make_problem((64, 64), 8)])
+    assert st == 0
+    # no workspace bound yet: nothing is launched
+    p = airgb.al_adam_params(0.01, 0.9, 0.999, 1e-8)
+    assert lib.al_batch_step(h, ctypes.byref(p), 1, -1, None) == 8
+    bad = airgb.al_adam_params(0.01, 1.0, 0.999, 1e-8)
+    assert lib.al_batch_step(h, ctypes.byref(bad), 1, -1, None) == 1
+    assert lib.al_batch_step(h, ctypes.byref(p), 0, -1, None) == 1
+    assert lib.al_batch_set_policy(h, 4) == 1
+    assert lib.al_batch_set_wait(h, 0, 0) == 1
+    lib.al_batch_destroy(h)
