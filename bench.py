@@ -351,7 +351,31 @@ def registration_runs(F, M, dev):
         "device_ms": dev_ms, "wall_s": wall, "ms_per_iteration": dev_ms / 200,
         "eager_ms_per_iteration": eager_ms / 200,
         "mse_start": float(vb[0, 1]), "mse_end": float(vb[1, 1])}
-    return {"pyramid_ct": pyramid, "adam_blobs_128": adam}
+    # 64 uneven pairs, 100 iterations: the persistent batch kernel (tuned
+    # work order, all iterations in one CUDA graph) against the same
+    # registrations one pair after another with plain launches
+    pairs = synth.batch_pairs(32, 32, device=dev)
+    iters = 100
+    registration.register_batch(pairs, 8, LAMBDA, iterations=3, graph=False, tune=False)
+    rb = registration.register_batch(pairs, 8, LAMBDA, iterations=iters, graph=True, tune=True)
+    registration.register_sequential(pairs[:2], 8, LAMBDA, 3)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    cs, hs, seq_ms = registration.register_sequential(pairs, 8, LAMBDA, iters)
+    seq_wall = time.perf_counter() - t0
+    same = all(torch.equal(a, c) for a, c in zip(cs, rb.batch.ctrl))
+    nvox = sum(int(np.prod(tuple(f.shape))) for f, _ in pairs)
+    total, per_kind = rb.batch.items()
+    batch = {
+        "workload": "64 blob pairs of uneven sizes (32 2D from 96^2 to 512^2, 32 3D from 64^3 "
+                    "to 192^3), MSE + 0.1 diffusion, spacing 8, 100 Adam iterations each",
+        "voxels": nvox, "work_items_per_iteration": total,
+        "items_bricks_tiles_chunks": list(per_kind),
+        "batched_device_ms": rb.device_ms, "batched_ms_per_iteration": rb.device_ms / iters,
+        "batched_order": rb.policy, "tuning_ms_per_iteration": rb.tuning_ms,
+        "sequential_device_ms": seq_ms, "sequential_wall_s": seq_wall,
+        "speedup": seq_ms / rb.device_ms, "coefficients_bit_identical": bool(same)}
+    return {"pyramid_ct": pyramid, "adam_blobs_128": adam, "batch_64": batch}
 
 
 def main():
