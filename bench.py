@@ -45,11 +45,11 @@ FLUSH_BYTES = 256 << 20
 #    conversions, 478 flop/voxel (z sums 70, x merge 189, y merge 189,
 #    statistics 30; an FMA counts 2);
 #  - the others by HBM: k_fused_fwd reads M and writes W, mask and dM~/dy
-#    (21 B); k_lcc_grad reads the LCC coefficients (16 B), F, W, mask and
-#    writes dS/dW (29 B); k_fused_gw reads dS/dW and dM~/dy (16 B); the
-#    point-wise fused kernels read F and M (8 B).
+#    (21 B); k_lcc_grad reads the LCC coefficients (three fp32 planes, 12 B),
+#    F, W, mask and writes dS/dW (25 B); k_fused_gw reads dS/dW and dM~/dy
+#    (16 B); the point-wise fused kernels read F and M (8 B).
 KERNEL_ROOF = {
-    "k_lcc_stats": ("alu", 478.0), "k_lcc_grad": ("hbm", 29.0), "k_fused_fwd": ("hbm", 21.0),
+    "k_lcc_stats": ("alu", 478.0), "k_lcc_grad": ("hbm", 25.0), "k_fused_fwd": ("hbm", 21.0),
     "k_fused_gw": ("hbm", 16.0), "k_fused_mse": ("hbm", 8.0), "k_fused_ncc": ("hbm", 8.0),
 }
 SM_COUNT, FP32_LANES = 152, 128
@@ -58,7 +58,7 @@ SM_COUNT, FP32_LANES = 152, 128
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--sim", choices=["lcc", "mse", "ncc"], default="lcc")
