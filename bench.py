@@ -42,14 +42,14 @@ FLUSH_BYTES = 256 << 20
 # Roofline of each kernel: the resource that bounds it and its algorithmic
 # work per voxel (the minimum its contract implies, without tiling overhead).
 #  - k_lcc_stats is bound by fp32 issue: window statistics with shift
-#    conversions, 478 flop/voxel (z sums 70, x merge 189, y merge 189,
+#    conversions, 368 flop/voxel (z sums 70, x merge 134, y merge 134,
 #    statistics 30; an FMA counts 2);
 #  - the others by HBM: k_fused_fwd reads M and writes W, mask and dM~/dy
 #    (21 B); k_lcc_grad reads the LCC coefficients (three fp32 planes, 12 B),
 #    F, W, mask and writes dS/dW (25 B); k_fused_gw reads dS/dW and dM~/dy
 #    (16 B); the point-wise fused kernels read F and M (8 B).
 KERNEL_ROOF = {
-    "k_lcc_stats": ("alu", 478.0), "k_lcc_grad": ("hbm", 25.0), "k_fused_fwd": ("hbm", 21.0),
+    "k_lcc_stats": ("alu", 368.0), "k_lcc_grad": ("hbm", 25.0), "k_fused_fwd": ("hbm", 21.0),
     "k_fused_gw": ("hbm", 16.0), "k_fused_mse": ("hbm", 8.0), "k_fused_ncc": ("hbm", 8.0),
 }
 SM_COUNT, FP32_LANES = 152, 128
