@@ -62,10 +62,15 @@ def _load():
     lib.alref_adam_step.argtypes = [ci, i64p, ci, cd, cd, cd, cd, ctypes.c_int64, dp, dp, dp, dp]
     lib.alref_pyramid_level.argtypes = [ci, i64p, dp, ci, dp]
     lib.alref_bspline_refine.argtypes = [ci, i64p, i64p, ci, dp, dp]
+    lib.alref_exp_field.argtypes = [ci, i64p, ci, dp, dp, dp]
+    lib.alref_exp_field_adjoint.argtypes = [ci, i64p, ci, dp, dp, dp]
+    lib.alref_objective_grad_diffeo.argtypes = [ci, i64p, ci, ci, ci, ci, cd, cd, dp, dp, dp, dp,
+                                                dp]
     for name in ("alref_lattice_size", "alref_displacement", "alref_displacement_adjoint",
                  "alref_warp", "alref_mse", "alref_ncc", "alref_lcc", "alref_diffusion",
                  "alref_objective_grad", "alref_objective_grad_ex", "alref_adam_step",
-                 "alref_pyramid_level", "alref_bspline_refine"):
+                 "alref_pyramid_level", "alref_bspline_refine", "alref_exp_field",
+                 "alref_exp_field_adjoint", "alref_objective_grad_diffeo"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -242,3 +247,45 @@ def bspline_refine(coarse_shape, fine_shape, delta, ctrl_coarse):
     _check(_load().alref_bspline_refine(nd, _p(Nc, ctypes.c_int64), _p(Nf, ctypes.c_int64),
                                         int(delta), _p(c), _p(out)), "bspline_refine")
     return out
+
+
+def exp_field(velocity, steps=6, trajectory=False):
+    """f = exp(v) by scaling and squaring (Sec. III-D): the displacement u_K
+    of the diffeomorphism, (d, *shape); with trajectory=True also the inputs
+    u_0 .. u_{K-1} of the squarings, (K, d, *shape)."""
+    v = _d(velocity)
+    nd, N = _grid(v.shape[1:])
+    u = np.zeros_like(v)
+    traj = np.zeros((max(int(steps), 1),) + v.shape) if trajectory else None
+    _check(_load().alref_exp_field(nd, _p(N, ctypes.c_int64), int(steps), _p(v), _p(u),
+                                   _p(traj) if trajectory else None), "exp_field")
+    return (u, traj[:int(steps)]) if trajectory else u
+
+
+def exp_field_adjoint(trajectory, grad_u, steps=6):
+    """(d u_K / d v)^T grad_u from the trajectory of :func:`exp_field`."""
+    g = _d(grad_u)
+    nd, N = _grid(g.shape[1:])
+    t = _d(trajectory) if int(steps) > 0 else np.zeros((1,) + g.shape)
+    gv = np.zeros_like(g)
+    _check(_load().alref_exp_field_adjoint(nd, _p(N, ctypes.c_int64), int(steps), _p(t), _p(g),
+                                           _p(gv)), "exp_field_adjoint")
+    return gv
+
+
+def objective_grad_diffeo(kind, fixed, moving, ctrl, delta, lam, steps=6, eps=1e-5, window=7,
+                          grad=True):
+    """J = S(M o exp(v), F) + lam R_diff(u_K), v the B-spline field of c, and
+    dJ/dc. Returns ({"J","S","R","n_mask"}, g_ctrl or None)."""
+    f, m, c = _d(fixed), _d(moving), _d(ctrl)
+    nd, N = _grid(f.shape)
+    assert c.shape == (nd,) + lattice_shape(f.shape, delta), c.shape
+    out = np.zeros(4, dtype=np.float64)
+    gc = np.zeros_like(c) if grad else None
+    _check(_load().alref_objective_grad_diffeo(nd, _p(N, ctypes.c_int64), int(delta), int(steps),
+                                               int(kind), int(window), float(eps), float(lam),
+                                               _p(f), _p(m), _p(c), _p(out),
+                                               _p(gc) if grad else None), "objective_grad_diffeo")
+    return {"J": float(out[0]), "S": float(out[1]), "R": float(out[2]),
+            "n_mask": float(out[3])}, gc
+

@@ -720,3 +720,246 @@ int alref_bspline_refine(int ndim, const int64_t *Nc, const int64_t *Nf, int del
                 }
     return ALREF_OK;
 }
+
+/* ======================================================================== */
+/* Diffeomorphic B-spline transformation (Sec. III-D): f = exp(v) of the     */
+/* stationary velocity field v = sum_j c_j k(x_j, x), by scaling and         */
+/* squaring (the method of the works the section cites; the number of        */
+/* squarings K is a reading, the paper gives none):                          */
+/*   u_0 = v / 2^K,  u_{k+1}(x) = u_k(x) + u~_k(x + u_k(x)),  f = x + u_K.   */
+/* u~_k is the linear interpolant of u_k at a position clamped to the grid   */
+/* [0, N-1] per axis (a field has no mask; reading); the floor cell is       */
+/* clamped to [0, N-2].                                                      */
+/* ======================================================================== */
+
+/* Cell and offset of the clamped position p along an axis of n points, and
+ * whether p was inside [0, n-1] (outside, the interpolant is constant along
+ * that axis, so its derivative there is 0). */
+static int field_cell(double p, int64_t n, int64_t *cell, double *f)
+{
+    int inside = 1;
+    if (!(p >= 0.0)) { /* also NaN */
+        p = 0.0;
+        inside = 0;
+    } else if (p > (double)(n - 1)) {
+        p = (double)(n - 1);
+        inside = 0;
+    }
+    int64_t c = (int64_t)floor(p);
+    if (c > n - 2)
+        c = n - 2;
+    *cell = c;
+    *f = p - (double)c;
+    return inside;
+}
+
+/* Linear interpolation of the ndim component planes of u at position p
+ * (x, y[, z]): value out[i]; derivative d[i][a] = d out[i] / d p_a (zero
+ * along clamped axes). Corner weights are products of (1 - f) and f. */
+static void field_sample(int ndim, const int64_t *N, const double *u, const double *p,
+                         double *out, double d[3][3], int64_t cell[3], double frac[3], int in[3])
+{
+    const int64_t nv = nvox(N);
+    for (int a = 0; a < 3; ++a) {
+        if (a < ndim) {
+            in[a] = field_cell(p[a], N[a], &cell[a], &frac[a]);
+        } else {
+            cell[a] = 0;
+            frac[a] = 0.0;
+            in[a] = 0;
+        }
+    }
+    for (int i = 0; i < ndim; ++i) {
+        out[i] = 0.0;
+        for (int a = 0; a < 3; ++a)
+            d[i][a] = 0.0;
+        const int nz = ndim == 3 ? 2 : 1;
+        for (int cz = 0; cz < nz; ++cz)
+            for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                    const double wx = cx ? frac[0] : 1.0 - frac[0];
+                    const double wy = cy ? frac[1] : 1.0 - frac[1];
+                    const double wz = ndim == 3 ? (cz ? frac[2] : 1.0 - frac[2]) : 1.0;
+                    const int64_t v = ((cell[2] + cz) * N[1] + cell[1] + cy) * N[0] + cell[0] + cx;
+                    const double val = u[i * nv + v];
+                    out[i] += wx * wy * wz * val;
+                    /* derivative of each weight factor: d(1-f)/dp = -1, df/dp = +1 */
+                    d[i][0] += (cx ? 1.0 : -1.0) * wy * wz * val;
+                    d[i][1] += (cy ? 1.0 : -1.0) * wx * wz * val;
+                    if (ndim == 3)
+                        d[i][2] += (cz ? 1.0 : -1.0) * wx * wy * val;
+                }
+        for (int a = 0; a < ndim; ++a)
+            if (!in[a])
+                d[i][a] = 0.0;
+    }
+}
+
+/* f = exp(v): u_out = u_K (ndim planes). traj (nullable) receives u_0 ..
+ * u_{K-1}, the inputs of the K squarings, K * ndim * nv doubles. */
+int alref_exp_field(int ndim, const int64_t *N, int K, const double *v, double *u_out,
+                    double *traj)
+{
+    if ((ndim != 2 && ndim != 3) || K < 0 || K > 30)
+        return ALREF_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (a < ndim ? N[a] < 2 : N[a] != 1)
+            return ALREF_ERR_ARG;
+    const int64_t nv = nvox(N);
+    double *cur = (double *)malloc(sizeof(double) * ndim * nv);
+    double *nxt = (double *)malloc(sizeof(double) * ndim * nv);
+    if (!cur || !nxt) {
+        free(cur), free(nxt);
+        return ALREF_ERR_ARG;
+    }
+    const double s = ldexp(1.0, -K);
+    for (int64_t e = 0; e < ndim * nv; ++e)
+        cur[e] = v[e] * s;
+    for (int k = 0; k < K; ++k) {
+        if (traj)
+            memcpy(traj + (int64_t)k * ndim * nv, cur, sizeof(double) * ndim * nv);
+        for (int64_t z = 0; z < N[2]; ++z)
+            for (int64_t y = 0; y < N[1]; ++y)
+                for (int64_t x = 0; x < N[0]; ++x) {
+                    const int64_t vox = (z * N[1] + y) * N[0] + x;
+                    double p[3] = {(double)x, (double)y, (double)z}, out[3], d[3][3], fr[3];
+                    int64_t cell[3];
+                    int in[3];
+                    for (int a = 0; a < ndim; ++a)
+                        p[a] += cur[a * nv + vox];
+                    field_sample(ndim, N, cur, p, out, d, cell, fr, in);
+                    for (int i = 0; i < ndim; ++i)
+                        nxt[i * nv + vox] = cur[i * nv + vox] + out[i];
+                }
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    memcpy(u_out, cur, sizeof(double) * ndim * nv);
+    free(cur), free(nxt);
+    return ALREF_OK;
+}
+
+/* Adjoint of alref_exp_field: g_v = (d u_K / d v)^T g_u, from the
+ * trajectory u_0 .. u_{K-1}. Per squaring, with p(x) = x + u_k(x):
+ *   g_k(y) = g_{k+1}(y) + (d u~_k / d p at p(y))^T g_{k+1}(y)
+ *            + sum_x w_y(p(x)) g_{k+1}(x),
+ * the last sum the transpose of the interpolation (w_y the weight of node y);
+ * then g_v = g_0 / 2^K. */
+int alref_exp_field_adjoint(int ndim, const int64_t *N, int K, const double *traj,
+                            const double *g_u, double *g_v)
+{
+    if ((ndim != 2 && ndim != 3) || K < 0 || K > 30)
+        return ALREF_ERR_ARG;
+    const int64_t nv = nvox(N);
+    double *g = (double *)malloc(sizeof(double) * ndim * nv);
+    double *h = (double *)malloc(sizeof(double) * ndim * nv);
+    if (!g || !h) {
+        free(g), free(h);
+        return ALREF_ERR_ARG;
+    }
+    memcpy(g, g_u, sizeof(double) * ndim * nv);
+    for (int k = K - 1; k >= 0; --k) {
+        const double *u = traj + (int64_t)k * ndim * nv;
+        memcpy(h, g, sizeof(double) * ndim * nv);
+        for (int64_t z = 0; z < N[2]; ++z)
+            for (int64_t y = 0; y < N[1]; ++y)
+                for (int64_t x = 0; x < N[0]; ++x) {
+                    const int64_t vox = (z * N[1] + y) * N[0] + x;
+                    double p[3] = {(double)x, (double)y, (double)z}, out[3], d[3][3], fr[3];
+                    int64_t cell[3];
+                    int in[3];
+                    for (int a = 0; a < ndim; ++a)
+                        p[a] += u[a * nv + vox];
+                    field_sample(ndim, N, u, p, out, d, cell, fr, in);
+                    /* position term: u_k(x) moves the sample point */
+                    for (int a = 0; a < ndim; ++a)
+                        for (int i = 0; i < ndim; ++i)
+                            h[a * nv + vox] += d[i][a] * g[i * nv + vox];
+                    /* sampled-field term: scatter to the corners */
+                    const int nz = ndim == 3 ? 2 : 1;
+                    for (int cz = 0; cz < nz; ++cz)
+                        for (int cy = 0; cy < 2; ++cy)
+                            for (int cx = 0; cx < 2; ++cx) {
+                                const double wx = cx ? fr[0] : 1.0 - fr[0];
+                                const double wy = cy ? fr[1] : 1.0 - fr[1];
+                                const double wz = ndim == 3 ? (cz ? fr[2] : 1.0 - fr[2]) : 1.0;
+                                const int64_t node =
+                                    ((cell[2] + cz) * N[1] + cell[1] + cy) * N[0] + cell[0] + cx;
+                                for (int i = 0; i < ndim; ++i)
+                                    h[i * nv + node] += wx * wy * wz * g[i * nv + vox];
+                            }
+                }
+        double *t = g;
+        g = h;
+        h = t;
+    }
+    const double s = ldexp(1.0, -K);
+    for (int64_t e = 0; e < ndim * nv; ++e)
+        g_v[e] = g[e] * s;
+    free(g), free(h);
+    return ALREF_OK;
+}
+
+/* J = S(M o (x + u_K), F) + lambda R_diff(u_K) for the diffeomorphic
+ * B-spline model, u_K = exp(v) - x with v the B-spline field of c, and
+ * dJ/dc by the chain rule: A5 + A4 on u_K, the exponential's adjoint, A6. */
+int alref_objective_grad_diffeo(int ndim, const int64_t *N, int delta, int K, int kind,
+                                int window, double eps, double lambda, const double *fixed,
+                                const double *moving, const double *ctrl, double *out,
+                                double *g_ctrl)
+{
+    int64_t n[3];
+    if (alref_lattice_size(ndim, N, delta, n) || K < 0 || K > 30)
+        return ALREF_ERR_ARG;
+    const int64_t nv = nvox(N);
+    double *v = (double *)malloc(sizeof(double) * ndim * nv);
+    double *u = (double *)malloc(sizeof(double) * ndim * nv);
+    double *traj = (double *)malloc(sizeof(double) * (K > 0 ? K : 1) * ndim * nv);
+    double *w = (double *)malloc(sizeof(double) * nv);
+    double *gy = (double *)malloc(sizeof(double) * ndim * nv);
+    double *gw = (double *)malloc(sizeof(double) * nv);
+    double *gu = (double *)malloc(sizeof(double) * ndim * nv);
+    double *gv = (double *)malloc(sizeof(double) * ndim * nv);
+    uint8_t *m = (uint8_t *)malloc(nv);
+    int st = ALREF_ERR_ARG;
+    if (!v || !u || !traj || !w || !gy || !gw || !gu || !gv || !m)
+        goto done;
+    if ((st = alref_displacement(ndim, N, delta, ctrl, v)))
+        goto done;
+    if ((st = alref_exp_field(ndim, N, K, v, u, traj)))
+        goto done;
+    if ((st = alref_warp(ndim, N, moving, u, w, m, gy)))
+        goto done;
+    double S = 0.0, R = 0.0;
+    if (kind == 0)
+        st = alref_mse(N, fixed, w, m, &S, gw);
+    else if (kind == 1)
+        st = alref_ncc(N, fixed, w, m, eps, &S, gw);
+    else if (kind == 2)
+        st = alref_lcc(ndim, N, fixed, w, m, window, eps, &S, gw);
+    else
+        st = ALREF_ERR_ARG;
+    if (st)
+        goto done;
+    if ((st = alref_diffusion(ndim, N, u, &R, gu)))
+        goto done;
+    double cnt = 0.0;
+    for (int64_t e = 0; e < nv; ++e)
+        cnt += m[e];
+    out[0] = S + lambda * R;
+    out[1] = S;
+    out[2] = R;
+    out[3] = cnt;
+    if (g_ctrl) {
+        for (int i = 0; i < ndim; ++i)
+            for (int64_t e = 0; e < nv; ++e)
+                gu[i * nv + e] = (m[e] ? gw[e] * gy[i * nv + e] : 0.0) + lambda * gu[i * nv + e];
+        if ((st = alref_exp_field_adjoint(ndim, N, K, traj, gu, gv)))
+            goto done;
+        st = alref_displacement_adjoint(ndim, N, delta, gv, g_ctrl);
+    }
+done:
+    free(v), free(u), free(traj), free(w), free(gy), free(gw), free(gu), free(gv), free(m);
+    return st;
+}
