@@ -269,6 +269,47 @@ size_t al_pyramid_workspace_bytes(const al_grid *g, int32_t factor);
 al_status al_bspline_refine(const al_bspline *coarse, const float *ctrl_coarse,
                             const al_bspline *fine, float *ctrl_fine, al_stream stream);
 
+/* ---- Diffeomorphic B-spline transformation (Sec. III-D) ---------------------
+ * f = exp(v) of the stationary velocity field v (here the B-spline field of
+ * c), computed by scaling and squaring, the method of the works the section
+ * cites: u_0 = v / 2^steps, u_{k+1}(x) = u_k(x) + u~_k(x + u_k(x)),
+ * f = x + u_steps. u~_k is the linear interpolant of u_k at the sample
+ * position clamped to the grid (a field has no mask; along a clamped axis
+ * its derivative is 0). steps: 0..20 (the paper gives no number; 6 is this
+ * library's default in its bindings). The inverse is exp(-v). */
+
+/* disp = exp(v) - x (ndim planes, voxel units). trajectory (nullable):
+ * steps * ndim * nv floats receiving u_0 .. u_{steps-1}, the inputs of the
+ * squarings, which al_exp_field_adjoint needs. Without a trajectory and with
+ * steps > 0 the call needs a workspace of al_exp_field_workspace_bytes(g). */
+al_status al_exp_field(const al_grid *g, int32_t steps, const float *velocity, float *disp,
+                       float *trajectory, void *workspace, size_t workspace_bytes,
+                       al_stream stream);
+size_t al_exp_field_workspace_bytes(const al_grid *g);
+
+/* Adjoint of al_exp_field: grad_velocity = (d disp / d v)^T grad_disp, from
+ * its trajectory. The transposed interpolation of each squaring is a scatter;
+ * it is summed in 64-bit fixed point with integer atomics (scaled per
+ * squaring from the largest |gradient|), so the result is deterministic.
+ * Workspace: al_exp_field_adjoint_workspace_bytes(g) (12 * ndim bytes per
+ * voxel). */
+al_status al_exp_field_adjoint(const al_grid *g, int32_t steps, const float *trajectory,
+                               const float *grad_disp, float *grad_velocity, void *workspace,
+                               size_t workspace_bytes, al_stream stream);
+size_t al_exp_field_adjoint_workspace_bytes(const al_grid *g);
+
+/* J = S(M o f, F) + lambda R_diff(u_steps) with f = exp(v), v the B-spline
+ * field of ctrl, and dJ/dc (grad_ctrl nullable): A1, the exponential, A2,
+ * A3 and A4 on u_steps, then A5, the exponential's adjoint and A6, through
+ * the step kernels. value_dev: {J, S, R, n_mask}. The workspace keeps the
+ * trajectory (steps + 5 fields of ndim planes and 3 scalar volumes):
+ * al_objective_diffeo_workspace_bytes(pr, steps). */
+al_status al_objective_grad_diffeo(const al_problem *pr, int32_t steps, const float *fixed,
+                                   const float *moving, const float *ctrl, double *value_dev,
+                                   float *grad_ctrl, void *workspace, size_t workspace_bytes,
+                                   al_stream stream);
+size_t al_objective_diffeo_workspace_bytes(const al_problem *pr, int32_t steps);
+
 /* ---- Batches of independent problems ---------------------------------------
  * Many registration pairs of uneven sizes optimised together (the paper
  * registers one pair at a time; this is a throughput service of the

@@ -35,7 +35,9 @@ EXPORTS = (
     "al_adam_step", "al_pyramid_grid", "al_pyramid_level", "al_pyramid_workspace_bytes",
     "al_bspline_refine", "al_batch_create", "al_batch_destroy", "al_batch_workspace_bytes",
     "al_batch_items", "al_batch_bind", "al_batch_step", "al_batch_tune", "al_batch_set_policy",
-    "al_batch_set_wait", "al_batch_status",
+    "al_batch_set_wait", "al_batch_status", "al_exp_field", "al_exp_field_workspace_bytes",
+    "al_exp_field_adjoint", "al_exp_field_adjoint_workspace_bytes", "al_objective_grad_diffeo",
+    "al_objective_diffeo_workspace_bytes",
 )
 
 
@@ -120,6 +122,12 @@ def load():
         "al_batch_set_policy": ([VP, I32], I32),
         "al_batch_set_wait": ([VP, I32, ctypes.c_int64], I32),
         "al_batch_status": ([VP, VP], I32),
+        "al_exp_field": ([P(al_grid), I32, VP, VP, VP, VP, SZ, VP], I32),
+        "al_exp_field_workspace_bytes": ([P(al_grid)], SZ),
+        "al_exp_field_adjoint": ([P(al_grid), I32, VP, VP, VP, VP, SZ, VP], I32),
+        "al_exp_field_adjoint_workspace_bytes": ([P(al_grid)], SZ),
+        "al_objective_grad_diffeo": ([P(al_problem), I32, VP, VP, VP, VP, VP, VP, SZ, VP], I32),
+        "al_objective_diffeo_workspace_bytes": ([P(al_problem), I32], SZ),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -403,6 +411,63 @@ def al_bspline_refine(coarse_shape, fine_shape, spacing, ctrl_coarse, ctrl_fine=
     _call("al_bspline_refine", ctypes.byref(bc), _ptr(ctrl_coarse), ctypes.byref(bf),
           _ptr(ctrl_fine), _stream(stream))
     return ctrl_fine
+
+
+def al_exp_field(velocity, steps=6, trajectory=False, stream=None):
+    """f = exp(v) by scaling and squaring: the displacement u (d, *shape);
+    with trajectory=True also u_0 .. u_{K-1} (K, d, *shape) for the adjoint."""
+    shape = tuple(velocity.shape[1:])
+    g = make_grid(shape)
+    _f32(velocity, (len(shape),) + shape, "velocity")
+    u = torch.empty_like(velocity)
+    traj = (torch.empty((max(int(steps), 1),) + tuple(velocity.shape), dtype=torch.float32,
+                        device=velocity.device) if trajectory else None)
+    ws = None
+    if not trajectory and steps > 0:
+        ws = _workspace(load().al_exp_field_workspace_bytes(ctypes.byref(g)), velocity.device)
+    _call("al_exp_field", ctypes.byref(g), int(steps), _ptr(velocity), _ptr(u), _ptr(traj),
+          _ptr(ws), ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
+    return (u, traj[:int(steps)]) if trajectory else u
+
+
+def al_exp_field_adjoint(trajectory, grad_disp, steps=6, stream=None):
+    """(d u_K / d v)^T grad_disp from the trajectory of al_exp_field."""
+    shape = tuple(grad_disp.shape[1:])
+    g = make_grid(shape)
+    gv = torch.empty_like(grad_disp)
+    ws = _workspace(load().al_exp_field_adjoint_workspace_bytes(ctypes.byref(g)), grad_disp.device)
+    traj = trajectory.contiguous() if steps > 0 else None
+    _call("al_exp_field_adjoint", ctypes.byref(g), int(steps), _ptr(traj), _ptr(grad_disp),
+          _ptr(gv), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    return gv
+
+
+def objective_diffeo_workspace_bytes(problem: al_problem, steps: int) -> int:
+    n = load().al_objective_diffeo_workspace_bytes(ctypes.byref(problem), int(steps))
+    if n == 0:
+        raise AirgbError("al_objective_diffeo_workspace_bytes", 1)
+    return int(n)
+
+
+def al_objective_grad_diffeo(problem: al_problem, fixed, moving, ctrl, steps=6, value=None,
+                             grad_ctrl=None, workspace=None, want_grad=True, stream=None):
+    """J and dJ/dc of the diffeomorphic B-spline model (f = exp(v))."""
+    shape = tuple(fixed.shape)
+    d = len(shape)
+    _f32(fixed, shape, "fixed")
+    _f32(moving, shape, "moving")
+    lat = (problem.bs.n[2], problem.bs.n[1], problem.bs.n[0]) if d == 3 else \
+        (problem.bs.n[1], problem.bs.n[0])
+    _f32(ctrl, (d,) + lat, "ctrl")
+    if value is None:
+        value = torch.empty(4, dtype=torch.float64, device=fixed.device)
+    if want_grad and grad_ctrl is None:
+        grad_ctrl = torch.empty_like(ctrl)
+    ws = _workspace(objective_diffeo_workspace_bytes(problem, steps), fixed.device, workspace)
+    _call("al_objective_grad_diffeo", ctypes.byref(problem), int(steps), _ptr(fixed),
+          _ptr(moving), _ptr(ctrl), _ptr(value), _ptr(grad_ctrl if want_grad else None), _ptr(ws),
+          ctypes.c_size_t(ws.numel()), _stream(stream))
+    return value, (grad_ctrl if want_grad else None)
 
 
 class Batch:

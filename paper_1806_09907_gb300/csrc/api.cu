@@ -541,6 +541,165 @@ al_status al_bspline_refine(const al_bspline *coarse, const float *ctrl_coarse,
     return launched(launch_refine(gc.ndim, nc, nf, ctrl_coarse, ctrl_fine, S(stream)));
 }
 
+static bool steps_ok(int32_t steps) { return steps >= 0 && steps <= 20; }
+
+al_status al_exp_field(const al_grid *gr, int32_t steps, const float *velocity, float *disp,
+                       float *trajectory, void *workspace, size_t workspace_bytes,
+                       al_stream stream)
+{
+    Grid g;
+    al_status st = check_grid(gr, &g);
+    if (st != AL_OK)
+        return st;
+    if (!steps_ok(steps))
+        return AL_ERR_INVALID_ARG;
+    if (!velocity || !disp)
+        return AL_ERR_INVALID_ARG;
+    const size_t field = (size_t)g.ndim * g.nv * sizeof(float);
+    const bool need_tmp = steps > 0 && !trajectory;
+    if (need_tmp && (!workspace || workspace_bytes < field))
+        return AL_ERR_WORKSPACE;
+    if (!aligned16(velocity) || !aligned16(disp) || (trajectory && !aligned16(trajectory)) ||
+        (need_tmp && !aligned16(workspace)))
+        return AL_ERR_ALIGN;
+    return launched(launch_exp(g, steps, velocity, disp, trajectory,
+                               need_tmp ? (float *)workspace : nullptr, S(stream)));
+}
+
+size_t al_exp_field_workspace_bytes(const al_grid *gr)
+{
+    Grid g;
+    if (check_grid(gr, &g) != AL_OK)
+        return 0;
+    return (size_t)g.ndim * g.nv * sizeof(float);
+}
+
+al_status al_exp_field_adjoint(const al_grid *gr, int32_t steps, const float *trajectory,
+                               const float *grad_disp, float *grad_velocity, void *workspace,
+                               size_t workspace_bytes, al_stream stream)
+{
+    Grid g;
+    al_status st = check_grid(gr, &g);
+    if (st != AL_OK)
+        return st;
+    if (!steps_ok(steps))
+        return AL_ERR_INVALID_ARG;
+    if (!grad_disp || !grad_velocity || (steps > 0 && !trajectory))
+        return AL_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < exp_adjoint_ws(g))
+        return AL_ERR_WORKSPACE;
+    if ((trajectory && !aligned16(trajectory)) || !aligned16(grad_disp) ||
+        !aligned16(grad_velocity) || !aligned16(workspace))
+        return AL_ERR_ALIGN;
+    return launched(
+        launch_exp_adjoint(g, steps, trajectory, grad_disp, grad_velocity, workspace, S(stream)));
+}
+
+size_t al_exp_field_adjoint_workspace_bytes(const al_grid *gr)
+{
+    Grid g;
+    if (check_grid(gr, &g) != AL_OK)
+        return 0;
+    return exp_adjoint_ws(g);
+}
+
+namespace {
+
+// Workspace of the diffeomorphic objective: v, the trajectory, u_K, W, mask,
+// dS/dW, dJ/du, dJ/dv, value slots, and scratch shared by the step calls.
+struct DiffeoLayout {
+    size_t v, traj, u, W, m, gW, gu, gv, vals, scratch, total;
+};
+
+DiffeoLayout diffeo_layout(const Grid &g, const Lattice &L, int kind, int window, int K)
+{
+    DiffeoLayout o{};
+    const size_t nv = (size_t)g.nv, field = a256(nv * g.ndim * 4);
+    size_t off = 0;
+    o.v = off;
+    off += field;
+    o.traj = off;
+    off += (size_t)K * field;
+    o.u = off;
+    off += field;
+    o.W = off;
+    off += a256(nv * 4);
+    o.m = off;
+    off += a256(nv);
+    o.gW = off;
+    off += a256(nv * 4);
+    o.gu = off;
+    off += field;
+    o.gv = off;
+    off += field;
+    o.vals = off;
+    off += 256;
+    o.scratch = off;
+    size_t mx = similarity_ws(g, kind, window);
+    const size_t cand[3] = {regulariser_ws(g), displacement_adjoint_ws(g, L), exp_adjoint_ws(g)};
+    for (size_t c : cand)
+        mx = c > mx ? c : mx;
+    off += a256(mx);
+    o.total = off;
+    return o;
+}
+
+}  // namespace
+
+size_t al_objective_diffeo_workspace_bytes(const al_problem *pr, int32_t steps)
+{
+    Grid g;
+    Lattice L;
+    if (check_problem(pr, &g, &L) != AL_OK || !steps_ok(steps))
+        return 0;
+    return diffeo_layout(g, L, pr->sim.kind, pr->sim.lcc_window, steps).total;
+}
+
+al_status al_objective_grad_diffeo(const al_problem *pr, int32_t steps, const float *fixed,
+                                   const float *moving, const float *ctrl, double *value_dev,
+                                   float *grad_ctrl, void *workspace, size_t workspace_bytes,
+                                   al_stream stream)
+{
+    Grid g;
+    Lattice L;
+    al_status st = check_problem(pr, &g, &L);
+    if (st != AL_OK)
+        return st;
+    if (!steps_ok(steps))
+        return AL_ERR_INVALID_ARG;
+    if (!fixed || !moving || !ctrl || !value_dev)
+        return AL_ERR_INVALID_ARG;
+    const DiffeoLayout lay = diffeo_layout(g, L, pr->sim.kind, pr->sim.lcc_window, steps);
+    if (!workspace || workspace_bytes < lay.total)
+        return AL_ERR_WORKSPACE;
+    if (!aligned16(fixed) || !aligned16(moving) || !aligned16(ctrl) || !aligned16(value_dev) ||
+        !aligned16(workspace) || (grad_ctrl && !aligned16(grad_ctrl)))
+        return AL_ERR_ALIGN;
+    char *w = (char *)workspace;
+    float *v = (float *)(w + lay.v), *traj = steps > 0 ? (float *)(w + lay.traj) : nullptr;
+    float *u = (float *)(w + lay.u), *W = (float *)(w + lay.W), *gW = (float *)(w + lay.gW);
+    float *gu = (float *)(w + lay.gu), *gv = (float *)(w + lay.gv);
+    uint8_t *m = (uint8_t *)(w + lay.m);
+    double *vals = (double *)(w + lay.vals);
+    void *scratch = w + lay.scratch;
+    const cudaStream_t s = S(stream);
+    if (launch_displacement(g, L, ctrl, v, s) != cudaSuccess ||
+        launch_exp(g, steps, v, u, traj, nullptr, s) != cudaSuccess ||
+        launch_warp(g, moving, u, W, m, s) != cudaSuccess ||
+        launch_similarity(g, pr->sim.kind, pr->sim.lcc_window, pr->sim.eps, fixed, W, m, vals,
+                          grad_ctrl ? gW : nullptr, scratch, s) != cudaSuccess ||
+        launch_regulariser(g, u, pr->lambda, vals + 2, grad_ctrl ? gu : nullptr, scratch, s) !=
+            cudaSuccess)
+        return AL_ERR_CUDA;
+    if (grad_ctrl) {
+        if (launch_warp_adjoint(g, moving, u, m, gW, gu, 1, s) != cudaSuccess ||
+            launch_exp_adjoint(g, steps, traj, gu, gv, scratch, s) != cudaSuccess ||
+            launch_displacement_adjoint(g, L, gv, grad_ctrl, scratch, s) != cudaSuccess)
+            return AL_ERR_CUDA;
+    }
+    return launched(launch_combine(vals, vals + 2, pr->lambda, value_dev, s));
+}
+
 al_status al_get_device_error(al_stream stream)
 {
     if (cudaStreamSynchronize(S(stream)) != cudaSuccess)

@@ -1,0 +1,329 @@
+// Diffeomorphic B-spline transformation (Sec. III-D): f = exp(v) of the
+// stationary velocity field v by scaling and squaring,
+//   u_0 = v / 2^K,  u_{k+1}(x) = u_k(x) + u~_k(x + u_k(x)),  f = x + u_K,
+// and the adjoint of that map. u~_k is the linear interpolant of u_k at the
+// sample position clamped to the grid (a field has no mask); along a clamped
+// axis the interpolant is constant, so its derivative there is 0.
+//
+// The adjoint of one squaring is, with p(x) = x + u_k(x),
+//   g_k(y) = g_{k+1}(y) + (du~_k/dp at p(y))^T g_{k+1}(y)
+//            + sum_x w_y(p(x)) g_{k+1}(x).
+// The first two terms are local. The last is the transpose of the
+// interpolation, a scatter from every sample to the corners of its cell.
+// It is accumulated in 64-bit fixed point with integer atomics: integer
+// addition is associative, so the result does not depend on the order in
+// which the atomics land (deterministic, unlike float atomics). The scale
+// 2^s is chosen per step from the largest |g| (an exact max reduction) so
+// that a node can take 2^20 contributions of the largest size without
+// overflow; the fixed point then resolves 2^-42 of that size, far below fp32
+// rounding of the contributions themselves.
+#include "launch.h"
+#include "profile.h"
+
+namespace airgb {
+
+namespace {
+
+constexpr int kDiffeoThreads = 256;
+
+int blocks_for(int64_t n)
+{
+    int64_t b = (n + kDiffeoThreads - 1) / kDiffeoThreads;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// Cell and offset of the position x + u along an axis of n points, clamped
+// into [0, n - 1]; returns whether the position was inside (a non-finite u
+// counts as outside, at 0). The integer part of u is split off first, so x +
+// u is not rounded in fp32.
+__device__ __forceinline__ bool field_axis(int x, float u, int n, int &cell, float &f)
+{
+    const float fl = floorf(u);
+    if (!(fabsf(fl) < 1.0e9f)) {  // non-finite or far outside
+        const bool hi = u > 0.0f;   // NaN -> low face
+        cell = hi ? n - 2 : 0;
+        f = hi ? 1.0f : 0.0f;
+        return false;
+    }
+    const int iy = x + (int)fl;
+    const float fr = u - fl;
+    if (iy < 0) {
+        cell = 0;
+        f = 0.0f;
+        return false;
+    }
+    if (iy > n - 1 || (iy == n - 1 && fr > 0.0f)) {
+        cell = n - 2;
+        f = 1.0f;
+        return false;
+    }
+    cell = min(iy, n - 2);
+    f = fr + (float)(iy - cell);
+    return true;
+}
+
+struct FieldSample {
+    int cell[3];
+    float f[3];
+    bool in[3];
+};
+
+template <int D>
+__device__ __forceinline__ FieldSample field_sample(const Grid &g, int x, int y, int z,
+                                                    const float *__restrict__ u, int64_t v)
+{
+    FieldSample s;
+    s.in[0] = field_axis(x, __ldg(u + v), g.X, s.cell[0], s.f[0]);
+    s.in[1] = field_axis(y, __ldg(u + g.nv + v), g.Y, s.cell[1], s.f[1]);
+    if (D == 3) {
+        s.in[2] = field_axis(z, __ldg(u + 2 * (int64_t)g.nv + v), g.Z, s.cell[2], s.f[2]);
+    } else {
+        s.cell[2] = 0;
+        s.f[2] = 0.0f;
+        s.in[2] = false;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kDiffeoThreads)
+    k_scale(const float *__restrict__ in, float *__restrict__ out, float s, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = in[e] * s;
+}
+
+// One squaring: out = u + u~(x + u).
+template <int D>
+__global__ void __launch_bounds__(kDiffeoThreads)
+    k_compose(Grid g, const float *__restrict__ u, float *__restrict__ out)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((int64_t)g.X * g.Y));
+        const FieldSample s = field_sample<D>(g, x, y, z, u, v);
+        const int64_t base = ((int64_t)s.cell[2] * g.Y + s.cell[1]) * g.X + s.cell[0];
+        const int64_t sx = 1, sy = g.X, sz = (int64_t)g.X * g.Y;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float *p = u + (int64_t)i * g.nv + base;
+            float r;
+            if (D == 3) {
+                const float c00 = (1.0f - s.f[0]) * __ldg(p) + s.f[0] * __ldg(p + sx);
+                const float c10 = (1.0f - s.f[0]) * __ldg(p + sy) + s.f[0] * __ldg(p + sy + sx);
+                const float c01 = (1.0f - s.f[0]) * __ldg(p + sz) + s.f[0] * __ldg(p + sz + sx);
+                const float c11 =
+                    (1.0f - s.f[0]) * __ldg(p + sz + sy) + s.f[0] * __ldg(p + sz + sy + sx);
+                const float c0 = (1.0f - s.f[1]) * c00 + s.f[1] * c10;
+                const float c1 = (1.0f - s.f[1]) * c01 + s.f[1] * c11;
+                r = (1.0f - s.f[2]) * c0 + s.f[2] * c1;
+            } else {
+                const float c0 = (1.0f - s.f[0]) * __ldg(p) + s.f[0] * __ldg(p + sx);
+                const float c1 = (1.0f - s.f[0]) * __ldg(p + sy) + s.f[0] * __ldg(p + sy + sx);
+                r = (1.0f - s.f[1]) * c0 + s.f[1] * c1;
+            }
+            out[(int64_t)i * g.nv + v] = __ldg(u + (int64_t)i * g.nv + v) + r;
+        }
+    }
+}
+
+// Largest |g| over n floats, as the bits of a non-negative float (ordered
+// like unsigned integers), by atomicMax: exact and order-independent.
+__global__ void __launch_bounds__(kDiffeoThreads)
+    k_absmax(const float *__restrict__ gin, int64_t n, unsigned int *__restrict__ out)
+{
+    float m = 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float a = fabsf(gin[e]);
+        m = a > m ? a : m;  // a NaN never wins
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, __float_as_uint(m));
+}
+
+// 2^s for the fixed-point scatter: |w g| < 2^e, so every contribution stays
+// below 2^(s + e) = 2^42 and 2^20 of them below 2^62.
+__device__ __forceinline__ float fixed_scale(unsigned int maxbits)
+{
+    int e = 0;
+    frexpf(__uint_as_float(maxbits), &e);
+    const int s = min(42 - e, 100);
+    return ldexpf(1.0f, s);
+}
+
+// Local terms of one squaring's adjoint into h, the scatter into acc.
+template <int D>
+__global__ void __launch_bounds__(kDiffeoThreads)
+    k_compose_adjoint(Grid g, const float *__restrict__ u, const float *__restrict__ gin,
+                      float *__restrict__ h, unsigned long long *__restrict__ acc,
+                      const unsigned int *__restrict__ maxbits)
+{
+    const float S = fixed_scale(*maxbits);
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((int64_t)g.X * g.Y));
+        const FieldSample s = field_sample<D>(g, x, y, z, u, v);
+        const int64_t base = ((int64_t)s.cell[2] * g.Y + s.cell[1]) * g.X + s.cell[0];
+        const int64_t sy = g.X, sz = (int64_t)g.X * g.Y;
+        float gv[D], loc[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            gv[i] = __ldg(gin + (int64_t)i * g.nv + v);
+            loc[i] = gv[i];
+        }
+        // derivative of the interpolant of each component at the sample
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const float *p = u + (int64_t)i * g.nv + base;
+            float d0, d1, d2 = 0.0f;
+            if (D == 3) {
+                const float a000 = __ldg(p), a001 = __ldg(p + 1), a010 = __ldg(p + sy),
+                            a011 = __ldg(p + sy + 1), a100 = __ldg(p + sz),
+                            a101 = __ldg(p + sz + 1), a110 = __ldg(p + sz + sy),
+                            a111 = __ldg(p + sz + sy + 1);
+                const float fx = s.f[0], fy = s.f[1], fz = s.f[2];
+                d0 = (1.0f - fz) * ((1.0f - fy) * (a001 - a000) + fy * (a011 - a010)) +
+                     fz * ((1.0f - fy) * (a101 - a100) + fy * (a111 - a110));
+                d1 = (1.0f - fz) * ((1.0f - fx) * (a010 - a000) + fx * (a011 - a001)) +
+                     fz * ((1.0f - fx) * (a110 - a100) + fx * (a111 - a101));
+                d2 = (1.0f - fy) * ((1.0f - fx) * (a100 - a000) + fx * (a101 - a001)) +
+                     fy * ((1.0f - fx) * (a110 - a010) + fx * (a111 - a011));
+            } else {
+                const float a00 = __ldg(p), a01 = __ldg(p + 1), a10 = __ldg(p + sy),
+                            a11 = __ldg(p + sy + 1);
+                d0 = (1.0f - s.f[1]) * (a01 - a00) + s.f[1] * (a11 - a10);
+                d1 = (1.0f - s.f[0]) * (a10 - a00) + s.f[0] * (a11 - a01);
+            }
+            if (s.in[0])
+                loc[0] = fmaf(d0, gv[i], loc[0]);
+            if (s.in[1])
+                loc[1] = fmaf(d1, gv[i], loc[1]);
+            if (D == 3 && s.in[2])
+                loc[D - 1] = fmaf(d2, gv[i], loc[D - 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+            h[(int64_t)i * g.nv + v] = loc[i];
+        // transposed interpolation: the sample's weights onto the corners
+#pragma unroll
+        for (int cz = 0; cz < (D == 3 ? 2 : 1); ++cz)
+#pragma unroll
+            for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                for (int cx = 0; cx < 2; ++cx) {
+                    const float w = (cx ? s.f[0] : 1.0f - s.f[0]) * (cy ? s.f[1] : 1.0f - s.f[1]) *
+                                    (D == 3 ? (cz ? s.f[2] : 1.0f - s.f[2]) : 1.0f);
+                    if (w == 0.0f)
+                        continue;
+                    const int64_t node = base + cz * sz + cy * sy + cx;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        const long long q = __float2ll_rn(w * gv[i] * S);
+                        if (q != 0)
+                            atomicAdd(acc + (int64_t)i * g.nv + node, (unsigned long long)q);
+                    }
+                }
+    }
+}
+
+// h += acc / 2^s; acc back to zero for the next step.
+__global__ void __launch_bounds__(kDiffeoThreads)
+    k_compose_finish(float *__restrict__ h, unsigned long long *__restrict__ acc, int64_t n,
+                     const unsigned int *__restrict__ maxbits)
+{
+    const float inv = 1.0f / fixed_scale(*maxbits);  // a power of two: exact
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const long long q = (long long)acc[e];
+        if (q != 0) {
+            h[e] += __ll2float_rn(q) * inv;
+            acc[e] = 0ull;
+        }
+    }
+}
+
+template <int D>
+cudaError_t exp_run(const Grid &g, int K, const float *v, float *u, float *traj, float *tmp,
+                    cudaStream_t s)
+{
+    const int64_t n = (int64_t)D * g.nv;
+    const float sc = ldexpf(1.0f, -K);
+    // u_0 -> traj[0] (or tmp); each squaring writes the next buffer
+    ProfScope ps(s, "k_exp");
+    float *cur = traj ? traj : (K % 2 == 0 ? u : tmp);
+    if (K == 0)
+        cur = u;
+    k_scale<<<blocks_for(n), kDiffeoThreads, 0, s>>>(v, cur, sc, n);
+    cudaError_t e = cudaGetLastError();
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        float *nxt;
+        if (k == K - 1)
+            nxt = u;
+        else if (traj)
+            nxt = traj + (int64_t)(k + 1) * n;
+        else
+            nxt = (cur == tmp) ? u : tmp;
+        k_compose<D><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, cur, nxt);
+        e = cudaGetLastError();
+        cur = nxt;
+    }
+    return e;
+}
+
+template <int D>
+cudaError_t exp_adjoint_run(const Grid &g, int K, const float *traj, const float *gu, float *gv,
+                            char *ws, cudaStream_t s)
+{
+    const int64_t n = (int64_t)D * g.nv;
+    unsigned long long *acc = (unsigned long long *)ws;
+    float *b0 = (float *)(ws + ((size_t)n * 8 + 255) / 256 * 256);
+    float *b1 = b0 + ((size_t)n * 4 + 255) / 256 * 64;
+    unsigned int *mx = (unsigned int *)(b1 + ((size_t)n * 4 + 255) / 256 * 64);
+    ProfScope ps(s, "k_exp_adjoint");
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)n * 8, s);
+    const float *gin = gu;
+    float *out = b0;
+    for (int k = K - 1; k >= 0 && e == cudaSuccess; --k) {
+        const float *u = traj + (int64_t)k * n;
+        if ((e = cudaMemsetAsync(mx, 0, sizeof(unsigned int), s)) != cudaSuccess)
+            break;
+        k_absmax<<<blocks_for(n) < 4 * 152 ? blocks_for(n) : 4 * 152, kDiffeoThreads, 0, s>>>(
+            gin, n, mx);
+        k_compose_adjoint<D><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, u, gin, out, acc, mx);
+        k_compose_finish<<<blocks_for(n), kDiffeoThreads, 0, s>>>(out, acc, n, mx);
+        e = cudaGetLastError();
+        gin = out;
+        out = (out == b0) ? b1 : b0;
+    }
+    if (e != cudaSuccess)
+        return e;
+    k_scale<<<blocks_for(n), kDiffeoThreads, 0, s>>>(gin, gv, ldexpf(1.0f, -K), n);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t exp_adjoint_ws(const Grid &g)
+{
+    const size_t n = (size_t)g.ndim * g.nv;
+    return (n * 8 + 255) / 256 * 256 + 2 * ((n * 4 + 255) / 256 * 256) + 256;
+}
+
+cudaError_t launch_exp(const Grid &g, int K, const float *v, float *u, float *traj, float *tmp,
+                       cudaStream_t s)
+{
+    return g.ndim == 3 ? exp_run<3>(g, K, v, u, traj, tmp, s) : exp_run<2>(g, K, v, u, traj, tmp, s);
+}
+
+cudaError_t launch_exp_adjoint(const Grid &g, int K, const float *traj, const float *gu, float *gv,
+                               void *ws, cudaStream_t s)
+{
+    return g.ndim == 3 ? exp_adjoint_run<3>(g, K, traj, gu, gv, (char *)ws, s)
+                       : exp_adjoint_run<2>(g, K, traj, gu, gv, (char *)ws, s);
+}
+
+}  // namespace airgb

@@ -126,4 +126,13 @@ int batch_blocks_per_sm(int delta);         // resident blocks of the batch kern
 cudaError_t launch_batch(int delta, int blocks, const BatchProblem *probs, const BatchItem *items,
                          int nitems, int *counters, const BatchStep &st, cudaStream_t s);
 
+// ---- diffeomorphic transformation: exp(v) by scaling and squaring ------------
+// traj (nullable): u_0 .. u_{K-1}; tmp: a field buffer, needed when traj is
+// NULL and K > 0.
+cudaError_t launch_exp(const Grid &g, int K, const float *v, float *u, float *traj, float *tmp,
+                       cudaStream_t s);
+size_t exp_adjoint_ws(const Grid &g);
+cudaError_t launch_exp_adjoint(const Grid &g, int K, const float *traj, const float *gu, float *gv,
+                               void *ws, cudaStream_t s);
+
 }  // namespace airgb

@@ -29,22 +29,31 @@ from . import airgb
 
 class Evaluator:
     """The problem and workspace of one objective (shared by calls on the
-    same stream; calls must not overlap on the GPU)."""
+    same stream; calls must not overlap on the GPU). diffeo_steps: None for
+    the plain B-spline model, else the number of squarings of the
+    diffeomorphic model f = exp(v) (Sec. III-D)."""
 
     def __init__(self, shape, spacing, sim="mse", lam=0.1, eps=1e-5, window=7, device="cuda",
-                 fused=True):
+                 fused=True, diffeo_steps=None):
         self.shape = tuple(shape)
         self.spacing = int(spacing)
         self.problem = airgb.make_problem(shape, spacing, sim, lam, eps, window)
         self.fused = fused
+        self.diffeo_steps = None if diffeo_steps is None else int(diffeo_steps)
         self.lattice = (len(shape),) + airgb.lattice_shape(shape, spacing)
-        self.workspace = torch.empty(airgb.objective_workspace_bytes(self.problem, fused),
-                                     dtype=torch.uint8, device=device)
+        nbytes = (airgb.objective_workspace_bytes(self.problem, fused) if self.diffeo_steps is None
+                  else airgb.objective_diffeo_workspace_bytes(self.problem, self.diffeo_steps))
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.last_value = None  # {J, S, R, n_mask} of the latest forward
 
     def evaluate(self, fixed, moving, ctrl, value, grad=None):
-        airgb.al_objective_grad(self.problem, fixed, moving, ctrl, value, grad, self.workspace,
-                                want_grad=grad is not None, fused=self.fused)
+        if self.diffeo_steps is not None:
+            airgb.al_objective_grad_diffeo(self.problem, fixed, moving, ctrl, self.diffeo_steps,
+                                           value, grad, self.workspace,
+                                           want_grad=grad is not None)
+        else:
+            airgb.al_objective_grad(self.problem, fixed, moving, ctrl, value, grad,
+                                    self.workspace, want_grad=grad is not None, fused=self.fused)
 
 
 class ObjectiveFunction(torch.autograd.Function):
@@ -190,7 +199,7 @@ def _level_loop(ev: Evaluator, F, M, c, iterations, lr, betas, eps, values, fina
 
 def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), iterations=150,
              lr=0.01, betas=(0.9, 0.999), eps=1e-8, sim_eps=1e-5, window=7, ctrl=None,
-             graph=True):
+             graph=True, diffeo_steps=None):
     """Coarse-to-fine B-spline registration of `moving` onto `fixed`.
 
     factors: pyramid factors from coarse to fine, each twice the next, ending
@@ -199,6 +208,8 @@ def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), it
     single-level registration) and are refined exactly between levels. With
     graph=True each level's iterations are captured in one CUDA graph and
     replayed once; graph=False issues the same launches directly.
+    diffeo_steps: None for the plain B-spline model, else the squarings of
+    the diffeomorphic model (the coefficients then parametrise the velocity).
     """
     factors = tuple(int(f) for f in factors)
     if factors[-1] != 1 or any(a != 2 * b for a, b in zip(factors, factors[1:])):
@@ -216,7 +227,8 @@ def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), it
         F = airgb.al_pyramid_level(fixed, f)
         M = airgb.al_pyramid_level(moving, f)
         shape = tuple(F.shape)
-        ev = Evaluator(shape, spacing, sim, lam, sim_eps, window, device=dev)
+        ev = Evaluator(shape, spacing, sim, lam, sim_eps, window, device=dev,
+                       diffeo_steps=diffeo_steps)
         if c is None:
             c = ctrl.clone() if ctrl is not None else torch.zeros(ev.lattice, dtype=torch.float32,
                                                                   device=dev)
