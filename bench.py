@@ -280,13 +280,13 @@ def run_reference(args, shape):
     return 0
 
 
-def registration_runs(F, M, dev):
+def registration_runs(F, M, c, dev):
     """Optimisation-loop timings, outside the headline timed region: the
     three-level LCC pyramid on the headline pair (one CUDA graph per level)
     and 200 Adam iterations on the 128^3 blob pair through the autograd
     Function. Device times from CUDA events on the launching stream."""
     import torch
-    from paper_1806_09907_gb300 import registration, synth
+    from paper_1806_09907_gb300 import airgb, registration, synth
 
     Fd, Md = torch.from_numpy(F).to(dev), torch.from_numpy(M).to(dev)
     kw = dict(spacing=SPACING, sim="lcc", lam=LAMBDA, factors=(4, 2, 1), iterations=150)
@@ -338,10 +338,10 @@ def registration_runs(F, M, dev):
     adam_run(5, False)
     adam_run(5, True)
     _, eager_ms, eager_wall = adam_run(200, False)
-    c, dev_ms, wall = adam_run(200, True)
+    cb, dev_ms, wall = adam_run(200, True)
     vb = torch.empty((2, 4), dtype=torch.float64, device=dev)
-    evb.evaluate(Fb, Mb, torch.zeros_like(c), vb[0])
-    evb.evaluate(Fb, Mb, c.detach(), vb[1])
+    evb.evaluate(Fb, Mb, torch.zeros_like(cb), vb[0])
+    evb.evaluate(Fb, Mb, cb.detach(), vb[1])
     vb = vb.cpu().numpy()
     adam = {
         "workload": "3D 128^3 blob pair (60 blobs, sigma 3-12), MSE + 0.1 diffusion, spacing 8 "
@@ -375,7 +375,31 @@ def registration_runs(F, M, dev):
         "batched_order": rb.policy, "tuning_ms_per_iteration": rb.tuning_ms,
         "sequential_device_ms": seq_ms, "sequential_wall_s": seq_wall,
         "speedup": seq_ms / rb.device_ms, "coefficients_bit_identical": bool(same)}
-    return {"pyramid_ct": pyramid, "adam_blobs_128": adam, "batch_64": batch}
+    # the diffeomorphic model on the headline pair: one forward+adjoint
+    # evaluation through the step kernels, 6 squarings
+    pr = airgb.make_problem(tuple(F.shape), SPACING, "lcc", LAMBDA, 1e-5, WINDOW)
+    K = 6
+    cd = torch.from_numpy(c).to(dev)
+    wsd = torch.empty(airgb.objective_diffeo_workspace_bytes(pr, K), dtype=torch.uint8, device=dev)
+    vd = torch.empty(4, dtype=torch.float64, device=dev)
+    gd = torch.empty_like(cd)
+    for _ in range(2):
+        airgb.al_objective_grad_diffeo(pr, Fd, Md, cd, K, vd, gd, wsd)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_eval = 5
+    e0.record()
+    for _ in range(n_eval):
+        airgb.al_objective_grad_diffeo(pr, Fd, Md, cd, K, vd, gd, wsd)
+    e1.record()
+    e1.synchronize()
+    diffeo = {
+        "workload": "the headline pair and coefficients, diffeomorphic model f = exp(v) with 6 "
+                    "squarings; LCC 7^3 + 0.1 diffusion of u_6; one forward+adjoint evaluation",
+        "ms_per_eval": e0.elapsed_time(e1) / n_eval,
+        "evals_per_s": 1000.0 * n_eval / e0.elapsed_time(e1),
+        "workspace_bytes": int(wsd.numel()), "J": float(vd[0])}
+    return {"pyramid_ct": pyramid, "adam_blobs_128": adam, "batch_64": batch,
+            "diffeo_ct": diffeo}
 
 
 def main():
@@ -485,7 +509,7 @@ def main():
                          f"z-slab of the workload ({t:.1f} s), scaled by voxel count"}
     reg = None
     if world == 1 and not args.no_registration:
-        reg = registration_runs(F, M, dev)
+        reg = registration_runs(F, M, c, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
