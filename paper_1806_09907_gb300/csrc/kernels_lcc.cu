@@ -42,11 +42,13 @@ struct LccA {
     static constexpr int ZC = (D == 3) ? 16 : 1;
     static constexpr int THREADS = 512;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;  // load elements per thread
-    // shared memory: raw F / masked W ring, z sums (5 + 2 centre values),
-    // x-merged sums, mask ring (bytes, at the end)
-    static constexpr int oRF = 0, oRW = oRF + NR * NL, oZ = oRW + NR * NL, oX = oZ + 7 * NL;
+    // shared memory: ring of (F, masked W) pairs, z sums (5 planes + 2 of
+    // centre values), x-merged sums, mask ring (bytes, at the end)
+    static constexpr int oRFW = 0, oZ = oRFW + 2 * NR * NL, oX = oZ + 7 * NL;
     static constexpr int oM = oX + 5 * NX;  // in floats; mask bytes start here
     static constexpr size_t smem = (size_t)oM * 4 + (size_t)NR * NL;
+    static_assert(LX % 2 == 0 && NL % 2 == 0 && NX % 2 == 0 && TX % 2 == 0,
+                  "column pairs are read as float2");
 };
 
 template <int D, int R>
@@ -110,6 +112,230 @@ __device__ __forceinline__ void add_to(Sums &S, const Sums &t)
     S.sfw += t.sfw;
 }
 
+// Registers a k_lcc_stats thread carries from slice to slice.
+template <int KL>
+struct StatsCarry {
+    float pf[KL], pw[KL];  // prefetched slice: F, W
+    uint8_t pm[KL];        // and the mask
+    float rho_sum, cnt;
+};
+
+template <int D, int R>
+__device__ __forceinline__ void lcc_stats_prefetch(const Grid &g, int zi, int x0, int y0,
+                                                   const float *__restrict__ F,
+                                                   const float *__restrict__ W,
+                                                   const uint8_t *__restrict__ m,
+                                                   StatsCarry<LccA<D, R>::KL> &st)
+{
+    using C = LccA<D, R>;
+    const int tid = threadIdx.x;
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+    const bool zin = zi >= 0 && zi < g.Z;
+#pragma unroll
+    for (int k = 0; k < C::KL; ++k) {
+        const int e = tid + k * C::THREADS;
+        st.pf[k] = 0.0f;
+        st.pw[k] = 0.0f;
+        st.pm[k] = 0;
+        if (e < C::NL) {
+            const int ly = e / C::LX, lx = e - ly * C::LX;
+            const int x = x0 - R + lx, y = y0 - R + ly;
+            if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
+                const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
+                st.pm[k] = __ldg(m + v);
+                st.pf[k] = __ldg(F + v);
+                st.pw[k] = __ldg(W + v);  // masked when staged (no dependent load)
+            }
+        }
+    }
+}
+
+// One input slice zi of k_lcc_stats. P is its ring slot (compile time), so
+// every ring address below is a constant offset.
+template <int D, int R, int P>
+__device__ __forceinline__ void lcc_stats_step(const Grid &g, float eps, int zi, int zc0,
+                                               int zi_end, int x0, int y0,
+                                               const float *__restrict__ F,
+                                               const float *__restrict__ W,
+                                               const uint8_t *__restrict__ m,
+                                               float *__restrict__ coef, float *sm,
+                                               StatsCarry<LccA<D, R>::KL> &st)
+{
+    using C = LccA<D, R>;
+    constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
+    constexpr int W1 = C::W1, RZ = C::RZ;
+    constexpr int OLDEST = (P + 1) % NR, CS = (P + 1 + RZ) % NR;  // slots
+    float2 *rFW = reinterpret_cast<float2 *>(sm + C::oRFW);
+    float *Zs = sm + C::oZ, *Xs = sm + C::oX;
+    uint8_t *rM = reinterpret_cast<uint8_t *>(sm + C::oM);
+    const int tid = threadIdx.x;
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+    const float n1 = (float)NR, n2 = (float)(NR * W1), n3 = (float)(NR * W1 * W1);
+    const float inv_n = 1.0f / n3;
+#pragma unroll
+    for (int k = 0; k < C::KL; ++k) {
+        const int e = tid + k * C::THREADS;
+        if (e < NL) {
+            rFW[P * NL + e] = make_float2(st.pf[k], st.pm[k] ? st.pw[k] : 0.0f);
+            rM[P * NL + e] = st.pm[k];
+        }
+    }
+    if (zi + 1 < zi_end)
+        lcc_stats_prefetch<D, R>(g, zi + 1, x0, y0, F, W, m, st);  // in flight meanwhile
+    __syncthreads();
+    const int zc = zi - RZ;
+    if (zc >= zc0) {
+        // ---- z sums of every column, relative to the column's centre value
+        for (int e = tid; e < NL; e += C::THREADS) {
+            const float2 a = rFW[CS * NL + e];
+            float s1f = 0.f, s1w = 0.f, s2f = 0.f, s2w = 0.f, sfw = 0.f;
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                const float2 q = rFW[((OLDEST + t) % NR) * NL + e];
+                const float f = q.x - a.x, w = q.y - a.y;
+                s1f += f;
+                s1w += w;
+                s2f = fmaf(f, f, s2f);
+                s2w = fmaf(w, w, s2w);
+                sfw = fmaf(f, w, sfw);
+            }
+            Zs[0 * NL + e] = s1f;
+            Zs[1 * NL + e] = s1w;
+            Zs[2 * NL + e] = s2f;
+            Zs[3 * NL + e] = s2w;
+            Zs[4 * NL + e] = sfw;
+            Zs[5 * NL + e] = a.x;
+            Zs[6 * NL + e] = a.y;
+        }
+        __syncthreads();
+        // ---- merge along x, two neighbouring outputs per thread sharing
+        //      W1 - 1 of their columns: outputs (ly, tx) and (ly, tx + 1).
+        //      The W1 + 1 columns (read as float2 pairs from every plane) are
+        //      shifted once, to the centre of the first output, and summed
+        //      into both windows; the second window is then shifted to its
+        //      own centre.
+        for (int e = tid; e < NX / 2; e += C::THREADS) {
+            const int ly = e / (TX / 2), tx = 2 * (e - ly * (TX / 2));
+            const int base = ly * LX + tx;
+            const float bf0 = Zs[5 * NL + base + R], bw0 = Zs[6 * NL + base + R];
+            const float bf1 = Zs[5 * NL + base + R + 1], bw1 = Zs[6 * NL + base + R + 1];
+            Sums S0{0.f, 0.f, 0.f, 0.f, 0.f}, S1{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int d2 = 0; d2 <= W1; d2 += 2) {
+                float2 q[7];
+#pragma unroll
+                for (int k = 0; k < 7; ++k)
+                    q[k] = *reinterpret_cast<const float2 *>(Zs + k * NL + base + d2);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int d = d2 + h;
+                    const Sums t = h == 0 ? shifted(q[0].x, q[1].x, q[2].x, q[3].x, q[4].x, q[5].x,
+                                                    q[6].x, bf0, bw0, n1)
+                                          : shifted(q[0].y, q[1].y, q[2].y, q[3].y, q[4].y, q[5].y,
+                                                    q[6].y, bf0, bw0, n1);
+                    if (d < W1)
+                        add_to(S0, t);
+                    if (d > 0)
+                        add_to(S1, t);
+                }
+            }
+            S1 = shifted(S1.s1f, S1.s1w, S1.s2f, S1.s2w, S1.sfw, bf0, bw0, bf1, bw1, n2);
+            const int o = ly * TX + tx;
+            *reinterpret_cast<float2 *>(Xs + 0 * NX + o) = make_float2(S0.s1f, S1.s1f);
+            *reinterpret_cast<float2 *>(Xs + 1 * NX + o) = make_float2(S0.s1w, S1.s1w);
+            *reinterpret_cast<float2 *>(Xs + 2 * NX + o) = make_float2(S0.s2f, S1.s2f);
+            *reinterpret_cast<float2 *>(Xs + 3 * NX + o) = make_float2(S0.s2w, S1.s2w);
+            *reinterpret_cast<float2 *>(Xs + 4 * NX + o) = make_float2(S0.sfw, S1.sfw);
+        }
+        __syncthreads();
+        // ---- merge along y (two outputs per thread, rows ty and ty + 1)
+        //      and evaluate the statistics of the core voxels
+        for (int e = tid; e < NC / 2; e += C::THREADS) {
+            const int tp = e / TX, tx = e - tp * TX;
+            const int ty0 = 2 * tp;
+            float bfv[2], bwv[2];
+            bool on[2];
+            int64_t vv[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ty = ty0 + h, x = x0 + tx, y = y0 + ty;
+                const int zcol = (ty + R) * LX + tx + R;
+                on[h] = x < g.X && y < g.Y && rM[CS * NL + zcol];
+                vv[h] = (int64_t)zc * sZ + (int64_t)y * sY + x;
+                bfv[h] = Zs[5 * NL + zcol];
+                bwv[h] = Zs[6 * NL + zcol];
+            }
+            // rows shifted once to the first output's centre, summed into
+            // both windows; the second window shifted to its own centre
+            Sums S[2] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int d = 0; d <= W1; ++d) {
+                const int r = (ty0 + d) * TX + tx;
+                const int zrow = (ty0 + d) * LX + tx + R;
+                const Sums t = shifted(Xs[r], Xs[NX + r], Xs[2 * NX + r], Xs[3 * NX + r],
+                                       Xs[4 * NX + r], Zs[5 * NL + zrow], Zs[6 * NL + zrow],
+                                       bfv[0], bwv[0], n2);
+                if (d < W1)
+                    add_to(S[0], t);
+                if (d > 0)
+                    add_to(S[1], t);
+            }
+            S[1] = shifted(S[1].s1f, S[1].s1w, S[1].s2f, S[1].s2w, S[1].sfw, bfv[0], bwv[0],
+                           bfv[1], bwv[1], n3);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + tx, y = y0 + ty0 + h;
+                if (x >= g.X || y >= g.Y)
+                    continue;
+                float ca = 0.f, cb = 0.f, cc = 0.f;
+                if (on[h]) {
+                    const Sums &T = S[h];
+                    const float cov = fmaf(-T.s1f * T.s1w, inv_n, T.sfw);
+                    const float vf = fmaf(-T.s1f * T.s1f, inv_n, T.s2f);
+                    const float vw = fmaf(-T.s1w * T.s1w, inv_n, T.s2w);
+                    const float Dd = fmaf(vf, vw, eps);
+                    const float rs = rsqrtf(Dd);
+                    const float rs3 = rs * rs * rs;
+                    const float rho = cov * rs;
+                    cb = 0.5f * cov * vf * rs3;  // -drho/dS_WW
+                    cc = -rs;                    // -drho/dS_FW
+                    const float a = (T.s1f * rs - cov * vf * T.s1w * rs3) * inv_n;  // -drho/dS_W
+                    ca = a - 2.0f * bwv[h] * cb - bfv[h] * cc;
+                    st.rho_sum += rho;
+                    st.cnt += 1.0f;
+                }
+                if (coef) {
+                    const int64_t pl = lcc_plane(g.nv);
+                    coef[vv[h]] = ca;
+                    coef[pl + vv[h]] = cb;
+                    coef[2 * pl + vv[h]] = cc;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int D, int R, int P>
+__device__ __forceinline__ void lcc_stats_steps(const Grid &g, float eps, int zb, int zc0,
+                                                int zi_end, int x0, int y0,
+                                                const float *__restrict__ F,
+                                                const float *__restrict__ W,
+                                                const uint8_t *__restrict__ m,
+                                                float *__restrict__ coef, float *sm,
+                                                StatsCarry<LccA<D, R>::KL> &st)
+{
+    if constexpr (P < LccA<D, R>::NR) {
+        if (zb + P < zi_end) {
+            lcc_stats_step<D, R, P>(g, eps, zb + P, zc0, zi_end, x0, y0, F, W, m, coef, sm, st);
+            lcc_stats_steps<D, R, P + 1>(g, eps, zb, zc0, zi_end, x0, y0, F, W, m, coef, sm, st);
+        }
+    }
+}
+
+// Window statistics of a tile of 32 x 16 columns streamed along z in chunks
+// of zc output slices: the ring holds the last 2R+1 input slices (slice zi in
+// slot (zi - first) mod (2R+1)).
 template <int D, int R>
 __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
     k_lcc_stats(Grid g, int zc, float eps, const float *__restrict__ F,
@@ -117,197 +343,20 @@ __global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
                 float *__restrict__ coef, double *__restrict__ part)
 {
     using C = LccA<D, R>;
-    constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
-    constexpr int W1 = C::W1;
     extern __shared__ float sm[];
-    float *rF = sm + C::oRF, *rW = sm + C::oRW, *Zs = sm + C::oZ, *Xs = sm + C::oX;
-    uint8_t *rM = reinterpret_cast<uint8_t *>(sm + C::oM);
     __shared__ double red[2 * C::THREADS / 32];
-    const int tid = threadIdx.x;
     const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
     const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, g.Z);
-    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
-    const float n1 = (float)NR, n2 = (float)(NR * W1), n3 = (float)(NR * W1 * W1);
-    const float inv_n = 1.0f / n3;
-    float rho_sum = 0.0f, cnt = 0.0f;
-
-    // register prefetch of one slice of the load region (F, masked W, mask)
-    float pf[C::KL], pw[C::KL];
-    uint8_t pm[C::KL];
-    auto prefetch = [&](int zi) {
-        const bool zin = zi >= 0 && zi < g.Z;
-#pragma unroll
-        for (int k = 0; k < C::KL; ++k) {
-            const int e = tid + k * C::THREADS;
-            pf[k] = 0.0f;
-            pw[k] = 0.0f;
-            pm[k] = 0;
-            if (e < NL) {
-                const int ly = e / LX, lx = e - ly * LX;
-                const int x = x0 - R + lx, y = y0 - R + ly;
-                if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
-                    const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
-                    pm[k] = __ldg(m + v);
-                    pf[k] = __ldg(F + v);
-                    pw[k] = __ldg(W + v);  // masked when staged (no dependent load)
-                }
-            }
-        }
-    };
-
-    int slot = 0;  // ring slot of the newest slice
-    const int zi_end = zc1 + C::RZ;
-    prefetch(zc0 - C::RZ);
-    for (int zi = zc0 - C::RZ; zi < zi_end; ++zi) {
-#pragma unroll
-        for (int k = 0; k < C::KL; ++k) {
-            const int e = tid + k * C::THREADS;
-            if (e < NL) {
-                rF[slot * NL + e] = pf[k];
-                rW[slot * NL + e] = pm[k] ? pw[k] : 0.0f;
-                rM[slot * NL + e] = pm[k];
-            }
-        }
-        if (zi + 1 < zi_end)
-            prefetch(zi + 1);  // in flight while this slice is processed
-        __syncthreads();
-        const int zc = zi - C::RZ;
-        if (zc >= zc0) {
-            const int oldest = (slot + 1 == NR) ? 0 : slot + 1;
-            int cs = oldest + C::RZ;
-            if (cs >= NR)
-                cs -= NR;
-            // ---- z sums of every column, relative to the column's centre value
-            for (int e = tid; e < NL; e += C::THREADS) {
-                const float af = rF[cs * NL + e], aw = rW[cs * NL + e];
-                float s1f = 0.f, s1w = 0.f, s2f = 0.f, s2w = 0.f, sfw = 0.f;
-                int sl = oldest;
-#pragma unroll
-                for (int t = 0; t < NR; ++t) {
-                    const float f = rF[sl * NL + e] - af, w = rW[sl * NL + e] - aw;
-                    s1f += f;
-                    s1w += w;
-                    s2f = fmaf(f, f, s2f);
-                    s2w = fmaf(w, w, s2w);
-                    sfw = fmaf(f, w, sfw);
-                    sl = (sl + 1 == NR) ? 0 : sl + 1;
-                }
-                Zs[0 * NL + e] = s1f;
-                Zs[1 * NL + e] = s1w;
-                Zs[2 * NL + e] = s2f;
-                Zs[3 * NL + e] = s2w;
-                Zs[4 * NL + e] = sfw;
-                Zs[5 * NL + e] = af;
-                Zs[6 * NL + e] = aw;
-            }
-            __syncthreads();
-            // ---- merge along x, two neighbouring outputs per thread sharing
-            //      W1 - 1 of their columns: outputs (ly, tx) and (ly, tx + 1).
-            //      The W1 + 1 columns are shifted once, to the centre of the
-            //      first output, and summed into both windows; the second
-            //      window is then shifted to its own centre.
-            for (int e = tid; e < NX / 2; e += C::THREADS) {
-                const int ly = e / (TX / 2), tx = 2 * (e - ly * (TX / 2));
-                const int base = ly * LX + tx;
-                const float bf0 = Zs[5 * NL + base + R], bw0 = Zs[6 * NL + base + R];
-                const float bf1 = Zs[5 * NL + base + R + 1], bw1 = Zs[6 * NL + base + R + 1];
-                Sums S0{0.f, 0.f, 0.f, 0.f, 0.f}, S1{0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int d = 0; d <= W1; ++d) {
-                    const int c = base + d;
-                    const Sums t = shifted(Zs[c], Zs[NL + c], Zs[2 * NL + c], Zs[3 * NL + c],
-                                           Zs[4 * NL + c], Zs[5 * NL + c], Zs[6 * NL + c], bf0,
-                                           bw0, n1);
-                    if (d < W1)
-                        add_to(S0, t);
-                    if (d > 0)
-                        add_to(S1, t);
-                }
-                S1 = shifted(S1.s1f, S1.s1w, S1.s2f, S1.s2w, S1.sfw, bf0, bw0, bf1, bw1, n2);
-                const int o = ly * TX + tx;
-                Xs[0 * NX + o] = S0.s1f;
-                Xs[1 * NX + o] = S0.s1w;
-                Xs[2 * NX + o] = S0.s2f;
-                Xs[3 * NX + o] = S0.s2w;
-                Xs[4 * NX + o] = S0.sfw;
-                Xs[0 * NX + o + 1] = S1.s1f;
-                Xs[1 * NX + o + 1] = S1.s1w;
-                Xs[2 * NX + o + 1] = S1.s2f;
-                Xs[3 * NX + o + 1] = S1.s2w;
-                Xs[4 * NX + o + 1] = S1.sfw;
-            }
-            __syncthreads();
-            // ---- merge along y (two outputs per thread, rows ty and ty + 1)
-            //      and evaluate the statistics of the core voxels
-            for (int e = tid; e < NC / 2; e += C::THREADS) {
-                const int tp = e / TX, tx = e - tp * TX;
-                const int ty0 = 2 * tp;
-                float bfv[2], bwv[2];
-                bool on[2];
-                int64_t vv[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int ty = ty0 + h, x = x0 + tx, y = y0 + ty;
-                    const int zcol = (ty + R) * LX + tx + R;
-                    on[h] = x < g.X && y < g.Y && rM[cs * NL + zcol];
-                    vv[h] = (int64_t)zc * sZ + (int64_t)y * sY + x;
-                    bfv[h] = Zs[5 * NL + zcol];
-                    bwv[h] = Zs[6 * NL + zcol];
-                }
-                // rows shifted once to the first output's centre, summed into
-                // both windows; the second window shifted to its own centre
-                Sums S[2] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-                for (int d = 0; d <= W1; ++d) {
-                    const int r = (ty0 + d) * TX + tx;
-                    const int zrow = (ty0 + d) * LX + tx + R;
-                    const Sums t = shifted(Xs[r], Xs[NX + r], Xs[2 * NX + r], Xs[3 * NX + r],
-                                           Xs[4 * NX + r], Zs[5 * NL + zrow], Zs[6 * NL + zrow],
-                                           bfv[0], bwv[0], n2);
-                    if (d < W1)
-                        add_to(S[0], t);
-                    if (d > 0)
-                        add_to(S[1], t);
-                }
-                S[1] = shifted(S[1].s1f, S[1].s1w, S[1].s2f, S[1].s2w, S[1].sfw, bfv[0], bwv[0],
-                               bfv[1], bwv[1], n3);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int x = x0 + tx, y = y0 + ty0 + h;
-                    if (x >= g.X || y >= g.Y)
-                        continue;
-                    float ca = 0.f, cb = 0.f, cc = 0.f;
-                    if (on[h]) {
-                        const Sums &T = S[h];
-                        const float cov = fmaf(-T.s1f * T.s1w, inv_n, T.sfw);
-                        const float vf = fmaf(-T.s1f * T.s1f, inv_n, T.s2f);
-                        const float vw = fmaf(-T.s1w * T.s1w, inv_n, T.s2w);
-                        const float Dd = fmaf(vf, vw, eps);
-                        const float rs = rsqrtf(Dd);
-                        const float rs3 = rs * rs * rs;
-                        const float rho = cov * rs;
-                        cb = 0.5f * cov * vf * rs3;  // -drho/dS_WW
-                        cc = -rs;                    // -drho/dS_FW
-                        const float a = (T.s1f * rs - cov * vf * T.s1w * rs3) * inv_n;  // -drho/dS_W
-                        ca = a - 2.0f * bwv[h] * cb - bfv[h] * cc;
-                        rho_sum += rho;
-                        cnt += 1.0f;
-                    }
-                    if (coef) {
-                        const int64_t pl = lcc_plane(g.nv);
-                        coef[vv[h]] = ca;
-                        coef[pl + vv[h]] = cb;
-                        coef[2 * pl + vv[h]] = cc;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        slot = (slot + 1 == NR) ? 0 : slot + 1;
-    }
-    double acc[2] = {rho_sum, cnt};
+    StatsCarry<C::KL> st;
+    st.rho_sum = 0.0f;
+    st.cnt = 0.0f;
+    const int zs = zc0 - C::RZ, zi_end = zc1 + C::RZ;
+    lcc_stats_prefetch<D, R>(g, zs, x0, y0, F, W, m, st);
+    for (int zb = zs; zb < zi_end; zb += C::NR)
+        lcc_stats_steps<D, R, 0>(g, eps, zb, zc0, zi_end, x0, y0, F, W, m, coef, sm, st);
+    double acc[2] = {st.rho_sum, st.cnt};
     block_reduce_d<2>(acc, red);
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         part[2 * b] = acc[0];
         part[2 * b + 1] = acc[1];
