@@ -398,8 +398,53 @@ def registration_runs(F, M, c, dev):
         "ms_per_eval": e0.elapsed_time(e1) / n_eval,
         "evals_per_s": 1000.0 * n_eval / e0.elapsed_time(e1),
         "workspace_bytes": int(wsd.numel()), "J": float(vd[0])}
+    # the other objective configurations, one forward+adjoint evaluation each:
+    # MSE on the headline pair, the 128^3 blob pair (spacing 8, MSE), and the
+    # 2D 128^2 blob pair (spacing 8, MSE; L2-resident and launch-latency
+    # bound, so timed as CUDA-graph replays of 100 evaluations)
+    def timed(ev, Fx, Mx, cx, n, graph=False):
+        val = torch.empty(4, dtype=torch.float64, device=dev)
+        gr = torch.empty_like(cx)
+        for _ in range(3):
+            ev.evaluate(Fx, Mx, cx, val, gr)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if graph:
+            gph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gph, capture_error_mode="thread_local"):
+                for _ in range(n):
+                    ev.evaluate(Fx, Mx, cx, val, gr)
+            a.record()
+            gph.replay()
+            b.record()
+        else:
+            a.record()
+            for _ in range(n):
+                ev.evaluate(Fx, Mx, cx, val, gr)
+            b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / n
+
+    others = {}
+    ev_mse = registration.Evaluator(tuple(F.shape), SPACING, "mse", LAMBDA, device=dev)
+    ms = timed(ev_mse, Fd, Md, cd, 20)
+    others["mse_ct"] = {"workload": "the headline pair and coefficients, MSE + 0.1 diffusion",
+                        "ms_per_eval": ms, "evals_per_s": 1000.0 / ms}
+    Fb3, Mb3 = (torch.from_numpy(a).to(dev) for a in synth.blobs_3d_128())
+    c3 = torch.from_numpy(synth.random_ctrl((19, 19, 19), 3, 1.0, synth.FIELD_SEED)).to(dev)
+    ms = timed(registration.Evaluator((128, 128, 128), 8, "mse", LAMBDA, device=dev), Fb3, Mb3,
+               c3, 50)
+    others["blobs_3d_128"] = {"workload": "3D 128^3 blob pair, MSE + 0.1 diffusion, spacing 8, "
+                                          "c ~ N(0, 1)", "ms_per_eval": ms,
+                              "evals_per_s": 1000.0 / ms}
+    Fb2, Mb2 = (torch.from_numpy(a).to(dev) for a in synth.blobs_2d_128())
+    c2 = torch.from_numpy(synth.random_ctrl((19, 19), 2, 1.0, synth.FIELD_SEED)).to(dev)
+    ms = timed(registration.Evaluator((128, 128), 8, "mse", LAMBDA, device=dev), Fb2, Mb2, c2,
+               100, graph=True)
+    others["blobs_2d_128"] = {"workload": "2D 128^2 blob pair, MSE + 0.1 diffusion, spacing 8, "
+                                          "c ~ N(0, 1); CUDA-graph replay of 100 evaluations",
+                              "us_per_eval": 1000.0 * ms}
     return {"pyramid_ct": pyramid, "adam_blobs_128": adam, "batch_64": batch,
-            "diffeo_ct": diffeo}
+            "diffeo_ct": diffeo, "objective_configs": others}
 
 
 def main():
