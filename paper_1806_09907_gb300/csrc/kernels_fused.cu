@@ -44,7 +44,7 @@ struct FCfg {
     static constexpr int CHS = CH > 0 ? CH : 1;  // storage size
     static constexpr int NMOM = (MODE == MODE_MSE) ? 2 : (MODE == MODE_NCC ? 6 : 0);
     static constexpr int NPART = CH * JZ * JY * JX;  // floats of one brick's partials
-    static constexpr int VC = (MODE == MODE_FWD) ? 2 : 1;  // slices whose loads are in flight
+    static constexpr int VC = (MODE == MODE_FWD || MODE == MODE_MSE) ? 2 : 1;  // slices whose loads are in flight
     // dynamic shared memory: up to NPL planes of column partials
     // P[NPL][BY][BX][CHS] and their x contraction X[NPL][BY][JX][CHS]
     static constexpr int NPL = (D == 3) ? 4 : 1;
