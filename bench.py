@@ -59,7 +59,7 @@ def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=300)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--sim", choices=["lcc", "mse", "ncc"], default="lcc")
     p.add_argument("--shape", type=str, default=None, help="Z,Y,X (default 160,256,256)")
@@ -581,7 +581,11 @@ def main():
                    "l2": "flushed by a 256 MiB write before every timed step",
                    "timing": "per-step CUDA events on the launching stream"},
         "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
-                    "max": max(step_ms)},
+                    "max": max(step_ms), "p10": float(np.percentile(step_ms, 10)),
+                    "p90": float(np.percentile(step_ms, 90))},
+        # algorithmic bytes of one evaluation (read F and M once, c in and
+        # dJ/dc out) over the step time
+        "effective_gbs": (8.0 * nv + 8.0 * c.size) / (total_ms / steps) / 1e6,
         "kernels": {k: {"total_ms": v[0], "launches": v[1], "avg_us": 1000.0 * v[0] / max(v[1], 1)}
                     for k, v in kernels.items()},
         "gpu_launches": int(sum(v[1] for v in kernels.values())),

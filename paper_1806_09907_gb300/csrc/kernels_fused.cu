@@ -214,7 +214,6 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
     float *const dstp = bpart + (int64_t)brick * C::NPART;
     const int cells_z = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
     const int nlayers = (D == 3) ? min(C::BCZ, cells_z - cz0) : 1;
-    const int64_t sYm = g.X, sZm = (int64_t)g.X * g.Y;
     constexpr int NCOR = (D == 3) ? 8 : 4;
     for (int cz = 0; cz < C::BCZ; ++cz) {
         const bool active = cz < nlayers && colvalid;
@@ -224,14 +223,17 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
         float gv[MODE == MODE_GW ? DELTA : 1], gr[MODE == MODE_GW ? DELTA : 1][D];
         if constexpr (MODE == MODE_GW) {
             if (active) {
+                // 32-bit voxel offsets (nv < 2^31), one per slice, shared by
+                // the D + 1 planes read
+                const int v0 = (min(zl0, g.Z - 1) * g.Y + y) * g.X + x;
+                const int sxy = g.X * g.Y;
 #pragma unroll
                 for (int pz = 0; pz < DELTA; ++pz) {
-                    const int z = min(zl0 + pz, g.Z - 1);
-                    const int64_t v = (int64_t)z * sZm + (int64_t)y * sYm + x;
+                    const int v = zl0 + pz < g.Z ? v0 + pz * sxy : v0 + (g.Z - 1 - zl0) * sxy;
                     gv[pz] = __ldg(gw_in + v);
 #pragma unroll
                     for (int i = 0; i < D; ++i)
-                        gr[pz][i] = __ldg(G_io + (int64_t)i * g.nv + v);
+                        gr[pz][i] = __ldg(G_io + i * g.nv + v);
                 }
             }
         }
