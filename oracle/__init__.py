@@ -20,7 +20,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "airgb_oracle.c")
+_SRCS = [os.path.join(_HERE, "airgb_oracle.c"), os.path.join(_HERE, "initnet_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -29,9 +29,11 @@ MSE, NCC, LCC = 0, 1, 2
 
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` with gcc (portable C11)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(
+        os.path.getmtime(_LIB) < os.path.getmtime(src) for src in _SRCS)
+    if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + _SRCS + ["-lm"],
                        check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -66,11 +68,15 @@ def _load():
     lib.alref_exp_field_adjoint.argtypes = [ci, i64p, ci, dp, dp, dp]
     lib.alref_objective_grad_diffeo.argtypes = [ci, i64p, ci, ci, ci, ci, cd, cd, dp, dp, dp, dp,
                                                 dp]
+    lib.alref_conv3d.argtypes = [ci, i64p, ci, ci, ci, dp, dp, dp, ci, dp]
+    lib.alref_conv3d_dgrad.argtypes = [ci, i64p, ci, ci, ci, dp, dp, dp]
+    lib.alref_conv3d_wgrad.argtypes = [ci, i64p, ci, ci, ci, dp, dp, dp, dp]
     for name in ("alref_lattice_size", "alref_displacement", "alref_displacement_adjoint",
                  "alref_warp", "alref_mse", "alref_ncc", "alref_lcc", "alref_diffusion",
                  "alref_objective_grad", "alref_objective_grad_ex", "alref_adam_step",
                  "alref_pyramid_level", "alref_bspline_refine", "alref_exp_field",
-                 "alref_exp_field_adjoint", "alref_objective_grad_diffeo"):
+                 "alref_exp_field_adjoint", "alref_objective_grad_diffeo", "alref_conv3d",
+                 "alref_conv3d_dgrad", "alref_conv3d_wgrad"):
         getattr(lib, name).restype = ci
     _lib = lib
     return lib

@@ -272,3 +272,50 @@ def batch_pairs(n2d: int = 32, n3d: int = 32, seed: int = IMAGE_SEED, device="cu
                                     device))
     return out
 
+
+
+# --------------------------------------------------------------------------
+# Learned initialisation: network weights and training pairs.
+# --------------------------------------------------------------------------
+
+def conv_weights(shapes, seed: int, head_scale: float = 0.1):
+    """He-normal weights for 3x3x3 convolution layers, zero biases.
+
+    shapes: [(cout, 27, cin)] per layer, in order. Weights ~ N(0, 2/(27 cin)),
+    the last layer's scaled by head_scale so that the initial prediction is
+    small. Returns [(w float32 (cout, 27, cin), b float32 (cout,))]."""
+    g = rng(seed, 6)
+    out = []
+    for k, (cout, taps, cin) in enumerate(shapes):
+        std = np.sqrt(2.0 / (taps * cin))
+        if k == len(shapes) - 1:
+            std *= head_scale
+        w = (std * g.standard_normal(size=(cout, taps, cin))).astype(np.float32)
+        out.append((w, np.zeros(cout, dtype=np.float32)))
+    return out
+
+
+def blob_table(count: int, shape, n_blobs: int = 60, sigma_range=(3.0, 12.0), seed: int = 0):
+    """Blob scenes of `count` volumes as one float32 table (count, n_blobs, 5):
+    centre x, y, z (uniform in the domain), sigma (uniform in sigma_range) and
+    amplitude (uniform in [0, 1]) per blob, volume i drawn from stream
+    (seed, 7) in order. 3D shapes (Z, Y, X) only."""
+    assert len(shape) == 3
+    g = rng(seed, 7)
+    t = np.empty((count, n_blobs, 5), dtype=np.float64)
+    hi = np.array([shape[2] - 1, shape[1] - 1, shape[0] - 1], dtype=np.float64)
+    t[:, :, 0:3] = g.uniform(0.0, 1.0, size=(count, n_blobs, 3)) * hi
+    t[:, :, 3] = g.uniform(sigma_range[0], sigma_range[1], size=(count, n_blobs))
+    t[:, :, 4] = g.uniform(0.0, 1.0, size=(count, n_blobs))
+    return t.astype(np.float32)
+
+
+def render_blob_table(shape, table):
+    """Host rendering of one row of blob_table in float64:
+    sum_b a_b exp(-|x - mu_b|^2 / (2 sigma_b^2)) on a (Z, Y, X) grid."""
+    x, y, z = _coords(shape)
+    img = np.zeros(tuple(shape), dtype=np.float64)
+    for mx, my, mz, s, a in np.asarray(table, dtype=np.float64):
+        r2 = (x - mx) ** 2 + (y - my) ** 2 + (z - mz) ** 2
+        img += a * np.exp(-r2 / (2.0 * s * s))
+    return img
