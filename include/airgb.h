@@ -373,9 +373,132 @@ al_status al_batch_set_wait(al_batch *batch, int32_t extra_items, int64_t max_po
  * AL_ERR_TIMEOUT. */
 al_status al_batch_status(const al_batch *batch, al_stream stream);
 
+/* ---- Learned initialisation: convolution layers and the network ------------
+ * The paper names learning-based registration as planned work (Sec. I and
+ * Sec. V) without a network. This library trains a 3D convolutional
+ * encoder-decoder that maps a fixed/moving pair to the cubic B-spline
+ * coefficients of spacing 8, which the plain optimiser (al_objective_grad +
+ * al_adam_step) then refines. The layers below are the dense contractions of
+ * that network, on the tensor cores (tcgen05, bf16 x bf16 with fp32
+ * accumulation).
+ *
+ * Layout: channels last, [b][z][y][x][c], bf16 (uint16 storage) unless a
+ * call says fp32. Weights are fp32 masters w[co][t][ci], tap
+ * t = (dz+1)*9 + (dy+1)*3 + (dx+1) for offsets in {-1, 0, 1}^3; the layer
+ * kernels read them as bf16 copies packed by al_conv3d_pack. */
+typedef struct {
+    int32_t batch;   /* volumes in the batch, >= 1 */
+    int32_t cin;     /* input channels: 2, or a multiple of 8 up to 256 */
+    int32_t cout;    /* output channels: a multiple of 16 up to 128 (pad with zero weights) */
+    int32_t stride;  /* 1 or 2 */
+    int64_t size[3]; /* input grid D, H, W (z, y, x), each 1 .. 2^20; batch*D*H*W < 2^31 */
+} al_conv3d;
+
+/* Output grid (D, H, W): (n - 1)/stride + 1 per axis (zero padding 1). */
+al_status al_conv3d_output_size(const al_conv3d *cv, int64_t *out_size);
+
+/* Bytes of the packed bf16 weights for the forward pass (dgrad = 0) or the
+ * input adjoint (dgrad = 1; needs cin a multiple of 16 up to 128); 0 for an
+ * invalid layer. */
+size_t al_conv3d_packed_bytes(const al_conv3d *cv, int32_t dgrad);
+
+/* Round the fp32 weights (cout x 27 x cin) to bf16 and lay them out as the
+ * layer kernels read them (K slices of 64 in the tensor cores' shared-memory
+ * tile layout). Either packed pointer may be NULL (not both). */
+al_status al_conv3d_pack(const al_conv3d *cv, const float *weight, void *packed_fwd,
+                         void *packed_dgrad, al_stream stream);
+
+/* out[b][o][co] = bias[co] + sum_t sum_ci in[b][stride*o + d_t][ci] w[co][t][ci]
+ * (in = 0 outside the grid); relu != 0 applies max(., 0). input bf16
+ * (batch x D x H x W x cin); bias fp32 (cout, nullable); output bf16, or fp32
+ * when out_f32 != 0 (batch x output grid x cout). */
+al_status al_conv3d_forward(const al_conv3d *cv, const void *input, const void *packed_fwd,
+                            const float *bias, int32_t relu, int32_t out_f32, void *output,
+                            al_stream stream);
+
+/* Input adjoint of the layer's linear part:
+ *   g_in[b][p][ci] = sum_{t, co} g_out[b][(p - d_t)/stride][co] w[co][t][ci]
+ * over the output voxels that exist (integer, in range). Then, optionally,
+ * g_in += addend[b][p][addend_offset + ci] (bf16, addend_stride channels per
+ * voxel; both multiples of 8), and g_in *= (relu_input[b][p][ci] > 0) when
+ * relu_input (bf16, cin channels) is given: the derivative of the ReLU
+ * that produced this layer's input. grad_output bf16 (cout channels),
+ * grad_input bf16 (cin channels, a multiple of 16). */
+al_status al_conv3d_backward_data(const al_conv3d *cv, const void *grad_output,
+                                  const void *packed_dgrad, const void *relu_input,
+                                  const void *addend, int32_t addend_stride,
+                                  int32_t addend_offset, void *grad_input, al_stream stream);
+
+/* Weight and bias adjoints:
+ *   g_w[co][t][ci] = sum_b sum_o g_out[b][o][co] in[b][stride*o + d_t][ci]
+ *   g_b[co]        = sum_b sum_o g_out[b][o][co]
+ * fp32, overwritten (grad_bias nullable). The sum over voxels is split over
+ * blocks whose partials (the workspace) are added in a fixed order, so the
+ * result is deterministic. */
+size_t al_conv3d_backward_weight_workspace_bytes(const al_conv3d *cv);
+al_status al_conv3d_backward_weight(const al_conv3d *cv, const void *input,
+                                    const void *grad_output, float *grad_weight, float *grad_bias,
+                                    void *workspace, size_t workspace_bytes, al_stream stream);
+
+/* The network's input: x[b][v] = (F[b][v], M[b][v]) as two bf16 channels,
+ * from fp32 volumes of `batch` x size[0] x size[1] x size[2] (z, y, x). */
+al_status al_initnet_input(int32_t batch, const int64_t *size, const float *fixed,
+                           const float *moving, void *x, al_stream stream);
+
+/* cat = [up(e4), e3] on e3's grid n3 (z, y, x): up(e4)[z][y][x] =
+ * e4[z/2][y/2][x/2], e4 on the grid (n3 - 1)/2 + 1, c4 + c3 channels (both
+ * multiples of 8), bf16. */
+al_status al_initnet_upcat(int32_t batch, const int64_t *n3, int32_t c4, int32_t c3,
+                           const void *e4, const void *e3, void *cat, al_stream stream);
+/* Transpose for the up-sampled channels, times the ReLU factor of e4:
+ * grad_e4[v][c] = (e4[v][c] > 0) sum_{fine voxels copied from v} grad_cat[f][c]. */
+al_status al_initnet_upcat_adjoint(int32_t batch, const int64_t *n3, int32_t c4, int32_t c3,
+                                   const void *grad_cat, const void *e4, void *grad_e4,
+                                   al_stream stream);
+
+/* Head -> control coefficients of the spacing-8 lattice of bs (3D):
+ * ctrl[b][i][jz][jy][jx] = head[b][clamp(jz-1)][clamp(jy-1)][clamp(jx-1)][i]
+ * (control point j sits at voxel 8 (j - 1), where head voxel j - 1 sits;
+ * points beyond the grid take the nearest). head fp32 on n3 = (N - 1)/8 + 1
+ * per axis with `channels` per voxel (>= 3, a multiple of 4). */
+al_status al_initnet_head_to_ctrl(const al_bspline *bs, int32_t batch, const int64_t *n3,
+                                  int32_t channels, const float *head, float *ctrl,
+                                  al_stream stream);
+/* Its transpose: grad_head (bf16, zero beyond channel 2) from grad_ctrl. */
+al_status al_initnet_head_adjoint(const al_bspline *bs, int32_t batch, const int64_t *n3,
+                                  int32_t channels, const float *grad_ctrl, void *grad_head,
+                                  al_stream stream);
+
+/* Training loss of the network: the mean squared difference of two B-spline
+ * displacement fields (Sec. III-C),
+ *   L = 1/(3 |X| batch) sum_b sum_i sum_x (u_i(x) - u*_i(x))^2, u = B c, u* = B c*,
+ * computed exactly on the lattice as e^T (G_z x G_y x G_x) e with e = c - c*
+ * and G = B^T B per axis (banded), and dL/dc = 2/(3 |X| batch) (G x G x G) e.
+ * ctrl, ctrl_true, grad_ctrl: batch x 3 coefficient planes; loss_dev: one
+ * double. Workspace: al_field_loss_workspace_bytes(batch). At most about
+ * 8,000 control points per component (AL_ERR_UNSUPPORTED beyond). */
+size_t al_field_loss_workspace_bytes(int32_t batch);
+al_status al_field_loss(const al_bspline *bs, int32_t batch, const float *ctrl,
+                        const float *ctrl_true, double *loss_dev, float *grad_ctrl,
+                        void *workspace, size_t workspace_bytes, al_stream stream);
+
+/* Adam (Kingma and Ba; Sec. III-G) on a flat fp32 array of n parameters:
+ * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+ * p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), t = *step + 1
+ * read from the device counter, which is then incremented (capturable). */
+al_status al_adam_flat(const al_adam_params *p, int64_t n, int64_t *step, float *param,
+                       const float *grad, float *m, float *v, al_stream stream);
+
+/* Training volumes: out[v][z][y][x] = sum_b a_b exp(-|x - mu_b|^2/(2 sigma_b^2))
+ * for `count` volumes of size (z, y, x), blob table[v][b] = {mu_x, mu_y,
+ * mu_z, sigma, a} (fp32, n_blobs per volume). */
+al_status al_render_blobs(const int64_t *size, int32_t count, int32_t n_blobs, const float *table,
+                          float *out, al_stream stream);
+
 /* Synchronise `stream`, then read and clear the current device's kernel
- * error word: AL_OK, AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the
- * synchronisation itself failed). */
+ * error words (the objective's and the convolution layers'): AL_OK,
+ * AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the synchronisation itself
+ * failed). */
 al_status al_get_device_error(al_stream stream);
 
 /* Instrumentation (not part of the method). When enabled, every kernel the

@@ -209,3 +209,16 @@ def field_loss(shape, c, c_true):
         loss += float(np.sum(e * e)) / (3.0 * nvox)
         g[b] = displacement_adjoint(shape, SPACING, e) * (2.0 / (3.0 * nvox))
     return loss / nb, g / nb
+
+
+def adam_flat(p, g, m, v, t, lr, betas=(0.9, 0.999), eps=1e-8):
+    """One Adam step (Kingma and Ba; Sec. III-G) on a flat array at step t >= 1:
+    m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+    p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). Returns (p, m, v)."""
+    p, g, m, v = _d(p), _d(g), _d(m), _d(v)
+    b1, b2 = betas
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

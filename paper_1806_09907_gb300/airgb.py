@@ -37,7 +37,12 @@ EXPORTS = (
     "al_batch_items", "al_batch_bind", "al_batch_step", "al_batch_tune", "al_batch_set_policy",
     "al_batch_set_wait", "al_batch_status", "al_exp_field", "al_exp_field_workspace_bytes",
     "al_exp_field_adjoint", "al_exp_field_adjoint_workspace_bytes", "al_objective_grad_diffeo",
-    "al_objective_diffeo_workspace_bytes",
+    "al_objective_diffeo_workspace_bytes", "al_conv3d_output_size", "al_conv3d_packed_bytes",
+    "al_conv3d_pack", "al_conv3d_forward", "al_conv3d_backward_data",
+    "al_conv3d_backward_weight_workspace_bytes", "al_conv3d_backward_weight", "al_initnet_input",
+    "al_initnet_upcat", "al_initnet_upcat_adjoint", "al_initnet_head_to_ctrl",
+    "al_initnet_head_adjoint", "al_field_loss_workspace_bytes", "al_field_loss", "al_adam_flat",
+    "al_render_blobs",
 )
 
 
@@ -64,6 +69,11 @@ class al_sim_params(ctypes.Structure):
 
 class al_problem(ctypes.Structure):
     _fields_ = [("bs", al_bspline), ("sim", al_sim_params), ("lam", ctypes.c_double)]
+
+
+class al_conv3d(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("cin", ctypes.c_int32), ("cout", ctypes.c_int32),
+                ("stride", ctypes.c_int32), ("size", ctypes.c_int64 * 3)]
 
 
 class al_adam_params(ctypes.Structure):
@@ -128,6 +138,24 @@ def load():
         "al_exp_field_adjoint_workspace_bytes": ([P(al_grid)], SZ),
         "al_objective_grad_diffeo": ([P(al_problem), I32, VP, VP, VP, VP, VP, VP, SZ, VP], I32),
         "al_objective_diffeo_workspace_bytes": ([P(al_problem), I32], SZ),
+        "al_conv3d_output_size": ([P(al_conv3d), P(ctypes.c_int64)], I32),
+        "al_conv3d_packed_bytes": ([P(al_conv3d), I32], SZ),
+        "al_conv3d_pack": ([P(al_conv3d), VP, VP, VP, VP], I32),
+        "al_conv3d_forward": ([P(al_conv3d), VP, VP, VP, I32, I32, VP, VP], I32),
+        "al_conv3d_backward_data": ([P(al_conv3d), VP, VP, VP, VP, I32, I32, VP, VP], I32),
+        "al_conv3d_backward_weight_workspace_bytes": ([P(al_conv3d)], SZ),
+        "al_conv3d_backward_weight": ([P(al_conv3d), VP, VP, VP, VP, VP, SZ, VP], I32),
+        "al_initnet_input": ([I32, P(ctypes.c_int64), VP, VP, VP, VP], I32),
+        "al_initnet_upcat": ([I32, P(ctypes.c_int64), I32, I32, VP, VP, VP, VP], I32),
+        "al_initnet_upcat_adjoint": ([I32, P(ctypes.c_int64), I32, I32, VP, VP, VP, VP], I32),
+        "al_initnet_head_to_ctrl": ([P(al_bspline), I32, P(ctypes.c_int64), I32, VP, VP, VP],
+                                    I32),
+        "al_initnet_head_adjoint": ([P(al_bspline), I32, P(ctypes.c_int64), I32, VP, VP, VP],
+                                    I32),
+        "al_field_loss_workspace_bytes": ([I32], SZ),
+        "al_field_loss": ([P(al_bspline), I32, VP, VP, VP, VP, VP, SZ, VP], I32),
+        "al_adam_flat": ([P(al_adam_params), ctypes.c_int64, VP, VP, VP, VP, VP, VP], I32),
+        "al_render_blobs": ([P(ctypes.c_int64), I32, I32, VP, VP, VP], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -594,3 +622,193 @@ class Objective:
         return al_objective_grad(self.problem, fixed, moving, ctrl, self.value,
                                  self.grad if want_grad else None, self.workspace,
                                  want_grad=want_grad, fused=self.fused, stream=stream)
+
+
+# ---------------------------------------------- learned initialisation ----
+# Activations are torch.bfloat16 tensors shaped (batch, D, H, W, C), channels
+# last; weights are float32 (cout, 27, cin) masters.
+
+def make_conv(batch, size, cin, cout, stride) -> al_conv3d:
+    cv = al_conv3d()
+    cv.batch, cv.cin, cv.cout, cv.stride = int(batch), int(cin), int(cout), int(stride)
+    for k in range(3):
+        cv.size[k] = int(size[k])
+    return cv
+
+
+def conv_output_size(cv: al_conv3d):
+    out = (ctypes.c_int64 * 3)()
+    _call("al_conv3d_output_size", ctypes.byref(cv), out)
+    return tuple(int(v) for v in out)
+
+
+def _i64x3(v):
+    a = (ctypes.c_int64 * 3)()
+    for k in range(3):
+        a[k] = int(v[k])
+    return a
+
+
+def _act(t, shape, what, dtype=torch.bfloat16):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: expected {dtype} {tuple(shape)}, got {t.dtype} "
+                         f"{tuple(t.shape)}")
+    return _ptr(t)
+
+
+def al_conv3d_pack(cv, weight, fwd=True, dgrad=True, stream=None):
+    """bf16 weight copies in the layer kernels' layout: (packed_fwd, packed_dgrad)."""
+    _f32(weight, (cv.cout, 27, cv.cin), "weight")
+    pf = pd = None
+    if fwd:
+        pf = torch.empty(load().al_conv3d_packed_bytes(ctypes.byref(cv), 0), dtype=torch.uint8,
+                         device=weight.device)
+    if dgrad:
+        n = load().al_conv3d_packed_bytes(ctypes.byref(cv), 1)
+        if n == 0:
+            raise ValueError("dgrad packing needs cin a multiple of 16")
+        pd = torch.empty(n, dtype=torch.uint8, device=weight.device)
+    _call("al_conv3d_pack", ctypes.byref(cv), _ptr(weight), _ptr(pf), _ptr(pd), _stream(stream))
+    return pf, pd
+
+
+def al_conv3d_forward(cv, x, packed_fwd, bias=None, relu=True, out_f32=False, out=None,
+                      stream=None):
+    osz = conv_output_size(cv)
+    _act(x, (cv.batch,) + tuple(cv.size) + (cv.cin,), "input")
+    shape = (cv.batch,) + osz + (cv.cout,)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32 if out_f32 else torch.bfloat16,
+                          device=x.device)
+    _act(out, shape, "output", torch.float32 if out_f32 else torch.bfloat16)
+    if bias is not None:
+        _f32(bias, (cv.cout,), "bias")
+    _call("al_conv3d_forward", ctypes.byref(cv), _ptr(x), _ptr(packed_fwd), _ptr(bias),
+          int(bool(relu)), int(bool(out_f32)), _ptr(out), _stream(stream))
+    return out
+
+
+def al_conv3d_backward_data(cv, grad_out, packed_dgrad, relu_input=None, addend=None,
+                            addend_offset=0, grad_in=None, stream=None):
+    osz = conv_output_size(cv)
+    _act(grad_out, (cv.batch,) + osz + (cv.cout,), "grad_output")
+    shape = (cv.batch,) + tuple(cv.size) + (cv.cin,)
+    if relu_input is not None:
+        _act(relu_input, shape, "relu_input")
+    stride = 0
+    if addend is not None:
+        if addend.dtype != torch.bfloat16 or tuple(addend.shape[:4]) != shape[:4]:
+            raise ValueError("addend: bf16 on the input grid expected")
+        stride = int(addend.shape[4])
+    if grad_in is None:
+        grad_in = torch.empty(shape, dtype=torch.bfloat16, device=grad_out.device)
+    _act(grad_in, shape, "grad_input")
+    _call("al_conv3d_backward_data", ctypes.byref(cv), _ptr(grad_out), _ptr(packed_dgrad),
+          _ptr(relu_input), _ptr(addend), int(stride), int(addend_offset), _ptr(grad_in),
+          _stream(stream))
+    return grad_in
+
+
+def al_conv3d_backward_weight(cv, x, grad_out, grad_weight=None, grad_bias=None, workspace=None,
+                              stream=None):
+    osz = conv_output_size(cv)
+    _act(x, (cv.batch,) + tuple(cv.size) + (cv.cin,), "input")
+    _act(grad_out, (cv.batch,) + osz + (cv.cout,), "grad_output")
+    if grad_weight is None:
+        grad_weight = torch.empty((cv.cout, 27, cv.cin), dtype=torch.float32, device=x.device)
+    if grad_bias is None:
+        grad_bias = torch.empty(cv.cout, dtype=torch.float32, device=x.device)
+    nb = load().al_conv3d_backward_weight_workspace_bytes(ctypes.byref(cv))
+    ws = _workspace(nb, x.device, workspace)
+    _call("al_conv3d_backward_weight", ctypes.byref(cv), _ptr(x), _ptr(grad_out),
+          _ptr(grad_weight), _ptr(grad_bias), _ptr(ws), ctypes.c_size_t(ws.numel()),
+          _stream(stream))
+    return grad_weight, grad_bias
+
+
+def conv_wgrad_workspace_bytes(cv) -> int:
+    return int(load().al_conv3d_backward_weight_workspace_bytes(ctypes.byref(cv)))
+
+
+def al_initnet_input(fixed, moving, out=None, stream=None):
+    """(batch, D, H, W) fp32 pair -> (batch, D, H, W, 2) bf16."""
+    shape = tuple(fixed.shape)
+    _f32(fixed, shape, "fixed")
+    _f32(moving, shape, "moving")
+    if out is None:
+        out = torch.empty(shape + (2,), dtype=torch.bfloat16, device=fixed.device)
+    _call("al_initnet_input", int(shape[0]), _i64x3(shape[1:]), _ptr(fixed), _ptr(moving),
+          _ptr(out), _stream(stream))
+    return out
+
+
+def al_initnet_upcat(e4, e3, out=None, stream=None):
+    nb, n3, c3, c4 = e3.shape[0], tuple(e3.shape[1:4]), e3.shape[4], e4.shape[4]
+    if out is None:
+        out = torch.empty((nb,) + n3 + (c4 + c3,), dtype=torch.bfloat16, device=e3.device)
+    _call("al_initnet_upcat", int(nb), _i64x3(n3), int(c4), int(c3), _ptr(e4), _ptr(e3),
+          _ptr(out), _stream(stream))
+    return out
+
+
+def al_initnet_upcat_adjoint(grad_cat, e4, out=None, stream=None):
+    nb, n3 = grad_cat.shape[0], tuple(grad_cat.shape[1:4])
+    c4 = e4.shape[4]
+    c3 = grad_cat.shape[4] - c4
+    if out is None:
+        out = torch.empty_like(e4)
+    _call("al_initnet_upcat_adjoint", int(nb), _i64x3(n3), int(c4), int(c3), _ptr(grad_cat),
+          _ptr(e4), _ptr(out), _stream(stream))
+    return out
+
+
+def al_initnet_head_to_ctrl(shape, head, out=None, stream=None):
+    """head (batch, n3z, n3y, n3x, C) fp32 -> (batch, 3, nz, ny, nx) at spacing 8."""
+    bs = bspline_init(shape, 8)
+    nb = head.shape[0]
+    if out is None:
+        out = torch.empty((nb, 3) + lattice_shape(shape, 8), dtype=torch.float32,
+                          device=head.device)
+    _call("al_initnet_head_to_ctrl", ctypes.byref(bs), int(nb), _i64x3(head.shape[1:4]),
+          int(head.shape[4]), _ptr(head), _ptr(out), _stream(stream))
+    return out
+
+
+def al_initnet_head_adjoint(shape, grad_ctrl, head_shape, out=None, stream=None):
+    bs = bspline_init(shape, 8)
+    nb = grad_ctrl.shape[0]
+    if out is None:
+        out = torch.empty(tuple(head_shape), dtype=torch.bfloat16, device=grad_ctrl.device)
+    _call("al_initnet_head_adjoint", ctypes.byref(bs), int(nb), _i64x3(head_shape[1:4]),
+          int(head_shape[4]), _ptr(grad_ctrl), _ptr(out), _stream(stream))
+    return out
+
+
+def al_field_loss(shape, ctrl, ctrl_true, loss=None, grad=None, workspace=None, stream=None):
+    """Mean squared displacement-field difference (spacing 8) and its gradient."""
+    bs = bspline_init(shape, 8)
+    nb = ctrl.shape[0]
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=ctrl.device)
+    if grad is None:
+        grad = torch.empty_like(ctrl)
+    ws = _workspace(load().al_field_loss_workspace_bytes(int(nb)), ctrl.device, workspace)
+    _call("al_field_loss", ctypes.byref(bs), int(nb), _ptr(ctrl), _ptr(ctrl_true), _ptr(loss),
+          _ptr(grad), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream(stream))
+    return loss, grad
+
+
+def al_adam_flat(param, grad, m, v, step, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, stream=None):
+    p = al_adam_params()
+    p.lr, p.beta1, p.beta2, p.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
+    _call("al_adam_flat", ctypes.byref(p), ctypes.c_int64(param.numel()), _ptr(step),
+          _ptr(param), _ptr(grad), _ptr(m), _ptr(v), _stream(stream))
+
+
+def al_render_blobs(shape, table, out=None, stream=None):
+    """table (count, n_blobs, 5) fp32 on the device -> (count, *shape) fp32 volumes."""
+    count, nbl = int(table.shape[0]), int(table.shape[1])
+    if out is None:
+        out = torch.empty((count,) + tuple(shape), dtype=torch.float32, device=table.device)
+    _call("al_render_blobs", _i64x3(shape), count, nbl, _ptr(table), _ptr(out), _stream(stream))
+    return out

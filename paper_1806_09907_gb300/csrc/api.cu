@@ -712,6 +712,11 @@ al_status al_get_device_error(al_stream stream)
         if (cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)) != cudaSuccess)
             return AL_ERR_CUDA;
     }
+    const int hc = conv_device_error(true);
+    if (hc < 0)
+        return AL_ERR_CUDA;
+    if (h == 0)
+        h = hc;
     return h == 0 ? AL_OK : (al_status)h;
 }
 

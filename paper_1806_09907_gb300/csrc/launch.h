@@ -135,4 +135,66 @@ size_t exp_adjoint_ws(const Grid &g);
 cudaError_t launch_exp_adjoint(const Grid &g, int K, const float *traj, const float *gu, float *gv,
                                void *ws, cudaStream_t s);
 
+// ---- learned initialisation: convolution layers and the network's glue ------
+// A 3x3x3 convolution layer, zero padding 1: batch nb of D x H x W voxels
+// (z, y, x) with cin channels in, cout out, stride 1 or 2. Channels last, bf16.
+struct ConvLayer {
+    int nb, D, H, W, cin, cout, stride;
+};
+int conv_out_size(int n, int stride);
+int conv_slices(int kreal);
+size_t conv_packed_elems(const ConvLayer &l, int dgrad);
+void conv_wgrad_plan(const ConvLayer &l, int *mtiles, int *splits, int *kper);
+size_t conv_wgrad_ws_bytes(const ConvLayer &l);
+cudaError_t launch_conv_pack(const ConvLayer &l, const float *w, void *fwd, void *dgrad,
+                             cudaStream_t s);
+cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *wpk,
+                                const float *bias, int relu, int out_f32, void *out,
+                                cudaStream_t s);
+cudaError_t launch_conv_dgrad(const ConvLayer &l, const void *gout, const void *wpk,
+                              const void *mask, const void *addend, int add_stride, int add_off,
+                              void *gin, cudaStream_t s);
+cudaError_t launch_conv_wgrad(const ConvLayer &l, const void *in, const void *gout, float *gw,
+                              float *gb, void *ws, cudaStream_t s);
+// Kernel error word of the layers (AL_ERR_TIMEOUT after a bounded wait ran
+// out), read and optionally cleared; -1 if the copy failed.
+int conv_device_error(bool clear);
+
+// Grids of the network's two coarsest levels: n3 (e3, the head) and n4 (e4),
+// (z, y, x); lat = spacing-8 lattice sizes (x, y, z).
+struct NetGrid {
+    int nb;
+    int n3[3], n4[3];
+    int lat[3];
+};
+cudaError_t launch_net_input(int64_t n, const float *F, const float *M, void *x, cudaStream_t s);
+cudaError_t launch_upcat(const NetGrid &g, int c4, int c3, const void *e4, const void *e3,
+                         void *cat, cudaStream_t s);
+cudaError_t launch_upcat_adjoint(const NetGrid &g, int c4, int c3, const void *gcat,
+                                 const void *e4, void *ge4, cudaStream_t s);
+cudaError_t launch_head_to_ctrl(const NetGrid &g, int ch, const float *h, float *c, cudaStream_t s);
+cudaError_t launch_head_adjoint(const NetGrid &g, int ch, const float *gc, void *gh,
+                                cudaStream_t s);
+
+struct FieldLossArgs {
+    int n[3];      // lattice nx, ny, nz
+    int N[3];      // grid X, Y, Z
+    int delta;     // spacing
+    double gscale; // 2 / (3 |X| nb)
+    double lscale; // 1 / (3 |X| nb)
+};
+size_t field_loss_smem(const FieldLossArgs &a);
+cudaError_t launch_field_loss(const FieldLossArgs &a, int nb, const float *c, const float *ct,
+                              float *gc, double *part, double *loss, cudaStream_t s);
+
+struct AdamFlatArgs {
+    double beta1, beta2;
+    float lr, eps;
+    int64_t n;
+};
+cudaError_t launch_adam_flat(const AdamFlatArgs &a, int64_t *step, float *p, const float *g,
+                             float *m, float *v, cudaStream_t s);
+cudaError_t launch_render_blobs(int D, int H, int W, int count, int nblobs, const float *table,
+                                float *out, cudaStream_t s);
+
 }  // namespace airgb

@@ -1,0 +1,338 @@
+"""Learned initialisation of the B-spline registration.
+
+The paper names learning-based registration as planned work (Sec. I and
+Sec. V) without a network. Here a small 3D convolutional encoder-decoder
+predicts the cubic B-spline coefficients (spacing 8, voxel units) of a
+fixed/moving pair; the plain optimiser (the objective and Adam of Sec. II-A
+and III-G) then refines the prediction, starts from zero instead when the
+prediction's objective is worse (the fallback), and its result measures the
+prediction's error.
+
+Network (channels last, bf16 activations, fp32 master weights, every layer a
+hand-written tcgen05 kernel of libairgb):
+
+    e1 = relu(conv_s2(x,  2 -> 16))        x = [F, M]
+    e2 = relu(conv_s2(e1, 16 -> 32))
+    e3 = relu(conv_s2(e2, 32 -> 48))       voxel i of e3 sits at voxel 8 i
+    e4 = relu(conv_s2(e3, 48 -> 64))
+    d1 = relu(conv_s1([up(e4), e3], 112 -> 48))
+    d2 = relu(conv_s1(d1, 48 -> 48))
+    h  = conv_s1(d2, 48 -> 3)              stored with 16 channels, 13 zero
+    c[i][j] = h[clamp(j - 1)][i]           control point j sits at voxel 8 (j - 1)
+
+Training pairs are made by the method itself: a blob volume M (Gaussian blobs
+as in the paper-shaped 3D workloads), coefficients c* ~ N(0, sigma^2) and
+F = M o (x + B c*) through the library's own expansion and warp, so that c*
+registers M onto F exactly (J(c*) = 0 where the mask keeps voxels). The loss
+is the mean squared difference of the predicted and true displacement fields.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import airgb, registration, synth
+
+SPACING = 8
+# (cin, cout stored, cout used, stride, relu) per layer, in order
+LAYERS = (
+    (2, 16, 16, 2, True),
+    (16, 32, 32, 2, True),
+    (32, 48, 48, 2, True),
+    (48, 64, 64, 2, True),
+    (112, 48, 48, 1, True),
+    (48, 48, 48, 1, True),
+    (48, 16, 3, 1, False),
+)
+
+
+def _out(n, s):
+    return (n - 1) // s + 1
+
+
+class InitNet:
+    """Weights, their packed bf16 copies and the activations of one batch
+    size and volume shape (z, y, x). All parameters live in one flat fp32
+    tensor (weights then bias per layer) so that one Adam launch updates
+    them; `grad` has the same layout."""
+
+    def __init__(self, shape, batch, device="cuda", seed=1806, head_scale=0.1):
+        self.shape = tuple(int(s) for s in shape)
+        self.batch = int(batch)
+        self.device = torch.device(device)
+        sizes = [self.shape]
+        for k in range(4):
+            sizes.append(tuple(_out(n, 2) for n in sizes[-1]))
+        self.grids = sizes  # input, e1, e2, e3, e4
+        n3 = sizes[3]
+        self.layer_in = [sizes[0], sizes[1], sizes[2], sizes[3], n3, n3, n3]
+        self.convs = [airgb.make_conv(self.batch, self.layer_in[k], cin, cout, s)
+                      for k, (cin, cout, _, s, _) in enumerate(LAYERS)]
+        counts = [cout * 27 * cin + cout for cin, cout, _, _, _ in LAYERS]
+        self.offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        self.params = torch.zeros(int(self.offsets[-1]), dtype=torch.float32, device=self.device)
+        self.grad = torch.zeros_like(self.params)
+        init = synth.conv_weights([(used, 27, cin) for cin, _, used, _, _ in LAYERS], seed,
+                                  head_scale)
+        for k, ((w, b), (cin, cout, used, _, _)) in enumerate(zip(init, LAYERS)):
+            self.weight(k)[:used].copy_(torch.from_numpy(w))
+            self.bias(k)[:used].copy_(torch.from_numpy(b))
+        self.packed = [None] * len(LAYERS)
+        self.wspaces = [torch.empty(max(airgb.conv_wgrad_workspace_bytes(cv), 256),
+                                    dtype=torch.uint8, device=self.device) for cv in self.convs]
+        self.acts = {}
+        self.pack()
+
+    # ---- parameter views ----
+    def weight(self, k, flat=None):
+        flat = self.params if flat is None else flat
+        cin, cout = LAYERS[k][0], LAYERS[k][1]
+        o = int(self.offsets[k])
+        return flat[o:o + cout * 27 * cin].view(cout, 27, cin)
+
+    def bias(self, k, flat=None):
+        flat = self.params if flat is None else flat
+        cin, cout = LAYERS[k][0], LAYERS[k][1]
+        o = int(self.offsets[k]) + cout * 27 * cin
+        return flat[o:o + cout]
+
+    def pack(self, stream=None):
+        """bf16 copies of the weights in the layer kernels' layout."""
+        for k, cv in enumerate(self.convs):
+            self.packed[k] = airgb.al_conv3d_pack(cv, self.weight(k), True, k > 0, stream=stream)
+
+    # ---- forward / backward ----
+    def forward(self, fixed, moving, out=None, stream=None):
+        """fixed, moving: (batch, *shape) fp32 -> coefficients (batch, 3, nz, ny, nx)."""
+        A = self.acts
+        A["x"] = airgb.al_initnet_input(fixed, moving, out=A.get("x"), stream=stream)
+        a = A["x"]
+        for k, name in enumerate(("e1", "e2", "e3", "e4")):
+            a = airgb.al_conv3d_forward(self.convs[k], a, self.packed[k][0], self.bias(k),
+                                        relu=True, out=A.get(name), stream=stream)
+            A[name] = a
+        A["cat"] = airgb.al_initnet_upcat(A["e4"], A["e3"], out=A.get("cat"), stream=stream)
+        A["d1"] = airgb.al_conv3d_forward(self.convs[4], A["cat"], self.packed[4][0], self.bias(4),
+                                          relu=True, out=A.get("d1"), stream=stream)
+        A["d2"] = airgb.al_conv3d_forward(self.convs[5], A["d1"], self.packed[5][0], self.bias(5),
+                                          relu=True, out=A.get("d2"), stream=stream)
+        A["h"] = airgb.al_conv3d_forward(self.convs[6], A["d2"], self.packed[6][0], self.bias(6),
+                                         relu=False, out_f32=True, out=A.get("h"), stream=stream)
+        return airgb.al_initnet_head_to_ctrl(self.shape, A["h"], out=out, stream=stream)
+
+    def backward(self, grad_ctrl, stream=None):
+        """Fills self.grad with the gradient of the parameters for dL/dc = grad_ctrl."""
+        A, G = self.acts, {}
+        # every entry of self.grad is overwritten below; the padded head rows
+        # get exact zeros because their output gradient channels are zero
+
+        def wgrad(k, x, g):
+            airgb.al_conv3d_backward_weight(
+                self.convs[k], x, g, grad_weight=self.weight(k, self.grad),
+                grad_bias=self.bias(k, self.grad), workspace=self.wspaces[k], stream=stream)
+
+        G["h"] = airgb.al_initnet_head_adjoint(self.shape, grad_ctrl, A["h"].shape,
+                                               out=A.get("gh"), stream=stream)
+        A["gh"] = G["h"]
+        wgrad(6, A["d2"], G["h"])
+        G["d2"] = airgb.al_conv3d_backward_data(self.convs[6], G["h"], self.packed[6][1],
+                                                relu_input=A["d2"], grad_in=A.get("gd2"),
+                                                stream=stream)
+        A["gd2"] = G["d2"]
+        wgrad(5, A["d1"], G["d2"])
+        G["d1"] = airgb.al_conv3d_backward_data(self.convs[5], G["d2"], self.packed[5][1],
+                                                relu_input=A["d1"], grad_in=A.get("gd1"),
+                                                stream=stream)
+        A["gd1"] = G["d1"]
+        wgrad(4, A["cat"], G["d1"])
+        G["cat"] = airgb.al_conv3d_backward_data(self.convs[4], G["d1"], self.packed[4][1],
+                                                 grad_in=A.get("gcat"), stream=stream)
+        A["gcat"] = G["cat"]
+        G["e4"] = airgb.al_initnet_upcat_adjoint(G["cat"], A["e4"], out=A.get("ge4"),
+                                                 stream=stream)
+        A["ge4"] = G["e4"]
+        wgrad(3, A["e3"], G["e4"])
+        G["e3"] = airgb.al_conv3d_backward_data(self.convs[3], G["e4"], self.packed[3][1],
+                                                relu_input=A["e3"], addend=G["cat"],
+                                                addend_offset=LAYERS[3][1], grad_in=A.get("ge3"),
+                                                stream=stream)
+        A["ge3"] = G["e3"]
+        wgrad(2, A["e2"], G["e3"])
+        G["e2"] = airgb.al_conv3d_backward_data(self.convs[2], G["e3"], self.packed[2][1],
+                                                relu_input=A["e2"], grad_in=A.get("ge2"),
+                                                stream=stream)
+        A["ge2"] = G["e2"]
+        wgrad(1, A["e1"], G["e2"])
+        G["e1"] = airgb.al_conv3d_backward_data(self.convs[1], G["e2"], self.packed[1][1],
+                                                relu_input=A["e1"], grad_in=A.get("ge1"),
+                                                stream=stream)
+        A["ge1"] = G["e1"]
+        wgrad(0, A["x"], G["e1"])
+        return self.grad
+
+    def layer_params(self):
+        """[(w (cout_used, 27, cin), b (cout_used,))] as float64 numpy arrays."""
+        out = []
+        for k, (cin, cout, used, _, _) in enumerate(LAYERS):
+            out.append((self.weight(k)[:used].double().cpu().numpy(),
+                        self.bias(k)[:used].double().cpu().numpy()))
+        return out
+
+
+# --------------------------------------------------------------- training --
+
+class PairSource:
+    """Training or test pairs made by the method: M = blob volume (60 blobs,
+    sigma 3..12 voxels), c* ~ N(0, sigma^2) voxels on the spacing-8 lattice,
+    F = M o (x + B c*) through al_displacement and al_warp. Pair i of a
+    source is fixed by (seed, i)."""
+
+    def __init__(self, shape, batch, sigma=4.0, seed=0, device="cuda", n_blobs=60):
+        self.shape = tuple(shape)
+        self.batch = int(batch)
+        self.sigma = float(sigma)
+        self.seed = int(seed)
+        self.n_blobs = int(n_blobs)
+        self.device = torch.device(device)
+        self.lattice = (3,) + airgb.lattice_shape(self.shape, SPACING)
+        self.F = torch.empty((self.batch,) + self.shape, dtype=torch.float32, device=self.device)
+        self.M = torch.empty_like(self.F)
+        if int(np.prod(self.shape)) % 4:
+            raise ValueError("the voxel count must be a multiple of 4 (16-byte aligned volumes)")
+        self.ctrl = torch.empty((self.batch,) + self.lattice, dtype=torch.float32,
+                                device=self.device)
+        # one pair's coefficients: a batch slice is not 16-byte aligned in general
+        self.ctrl_one = torch.empty(self.lattice, dtype=torch.float32, device=self.device)
+        self.disp = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
+        self.mask = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
+
+    def host_draw(self, first):
+        """Blob tables and coefficients of pairs first .. first + batch - 1."""
+        tables = np.empty((self.batch, self.n_blobs, 5), dtype=np.float32)
+        ctrl = np.empty((self.batch,) + self.lattice, dtype=np.float32)
+        for b in range(self.batch):
+            idx = self.seed * 1_000_003 + first + b
+            tables[b] = synth.blob_table(1, self.shape, self.n_blobs, seed=idx)[0]
+            ctrl[b] = synth.random_ctrl(self.lattice[1:], 3, self.sigma, seed=idx)
+        return tables, ctrl
+
+    def make(self, first, stream=None):
+        tables, ctrl = self.host_draw(first)
+        t = torch.from_numpy(tables).to(self.device, non_blocking=True)
+        self.ctrl.copy_(torch.from_numpy(ctrl), non_blocking=True)
+        airgb.al_render_blobs(self.shape, t, out=self.M, stream=stream)
+        for b in range(self.batch):
+            self.ctrl_one.copy_(torch.from_numpy(ctrl[b]))
+            airgb.al_displacement(self.shape, SPACING, self.ctrl_one, disp=self.disp,
+                                  stream=stream)
+            airgb.al_warp(self.M[b], self.disp, warped=self.F[b], mask=self.mask, stream=stream)
+        return self.F, self.M, self.ctrl
+
+
+@dataclasses.dataclass
+class TrainResult:
+    steps: int
+    pairs: int
+    seconds: float
+    losses: np.ndarray  # loss of each step (device values, read at the end)
+
+
+def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigma=4.0, seed=0,
+          log_every=0):
+    """Adam on the field loss over `pairs` method-generated pairs, net.batch
+    per step. Returns the per-step losses and the wall time."""
+    dev = net.device
+    src = PairSource(net.shape, net.batch, sigma, seed, dev)
+    steps = (int(pairs) + net.batch - 1) // net.batch
+    m = torch.zeros_like(net.params)
+    v = torch.zeros_like(net.params)
+    step = torch.zeros(1, dtype=torch.int64, device=dev)
+    losses = torch.empty(steps, dtype=torch.float64, device=dev)
+    gc = torch.empty((net.batch,) + src.lattice, dtype=torch.float32, device=dev)
+    c = torch.empty_like(gc)
+    lws = torch.empty(256, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        F, M, ct = src.make(i * net.batch)
+        net.forward(F, M, out=c)
+        airgb.al_field_loss(net.shape, c, ct, loss=losses[i:i + 1], grad=gc, workspace=lws)
+        net.backward(gc)
+        airgb.al_adam_flat(net.params, net.grad, m, v, step, lr=lr, betas=betas, eps=eps)
+        net.pack()
+        if log_every and (i + 1) % log_every == 0:
+            print(f"step {i + 1}/{steps} loss {float(losses[i]):.4f}", flush=True)
+    torch.cuda.synchronize(dev)
+    return TrainResult(steps, steps * net.batch, time.perf_counter() - t0, losses.cpu().numpy())
+
+
+# ------------------------------------------------------------ evaluation --
+
+@dataclasses.dataclass
+class PairReport:
+    plain_final_mse: float
+    plain_ms: float          # 200 plain iterations (device time)
+    init_mse: float          # MSE at the network's prediction, before refinement
+    zero_mse: float          # MSE at c = 0
+    fallback: bool           # prediction rejected (J worse than at c = 0)
+    iterations_to_plain: int  # refinement iterations until MSE <= plain_final_mse (-1: never)
+    learned_ms: float        # inference + those iterations (device time, measured)
+    field_rmse_pred: float   # rms |u_pred - u*| over voxels
+    field_rmse_plain: float  # rms |u_plain - u*|
+
+
+def _field_rmse(shape, c, c_true):
+    loss, _ = airgb.al_field_loss(shape, c[None].contiguous(), c_true[None].contiguous())
+    return float(np.sqrt(3.0 * float(loss)))
+
+
+def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, lam=0.1):
+    """Plain optimiser from zero for `iterations`, then the network's
+    prediction refined by the same optimiser until it reaches the plain
+    method's final MSE. net_single must have batch 1."""
+    shape = tuple(F.shape)
+    plain = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
+                                   iterations=iterations, lr=lr)
+    pv = plain.levels[0].values.cpu().numpy()
+    target = float(pv[-1, 1])
+    ev = registration.Evaluator(shape, SPACING, "mse", lam, device=F.device)
+    # inference, timed on the device
+    c0 = torch.empty((3,) + airgb.lattice_shape(shape, SPACING), dtype=torch.float32,
+                     device=F.device)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    net_single.forward(F[None], M[None], out=c0[None])  # warm (kernel attributes)
+    start.record()
+    net_single.forward(F[None], M[None], out=c0[None])
+    stop.record()
+    stop.synchronize()
+    infer_ms = start.elapsed_time(stop)
+    val0 = torch.empty(4, dtype=torch.float64, device=F.device)
+    valz = torch.empty(4, dtype=torch.float64, device=F.device)
+    ev.evaluate(F, M, c0, val0, None)
+    ev.evaluate(F, M, torch.zeros_like(c0), valz, None)
+    j0, jz = float(val0[0]), float(valz[0])
+    fallback = not (j0 <= jz)
+    start_c = torch.zeros_like(c0) if fallback else c0
+    refine = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
+                                   iterations=iterations, lr=lr, ctrl=start_c)
+    rv = refine.levels[0].values.cpu().numpy()
+    hit = np.nonzero(rv[:, 1] <= target)[0]
+    k = int(hit[0]) if len(hit) else -1
+    learned_ms = float("nan")
+    if k >= 0:
+        # the measured run: inference + exactly k refinement iterations
+        if k > 0:
+            again = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam,
+                                          factors=(1,), iterations=k, lr=lr, ctrl=start_c)
+            learned_ms = infer_ms + again.levels[0].ms
+        else:
+            learned_ms = infer_ms
+    return PairReport(
+        plain_final_mse=target, plain_ms=plain.levels[0].ms,
+        init_mse=float(val0[1]), zero_mse=float(valz[1]), fallback=fallback,
+        iterations_to_plain=k, learned_ms=learned_ms,
+        field_rmse_pred=_field_rmse(shape, c0, c_true),
+        field_rmse_plain=_field_rmse(shape, plain.ctrl, c_true))

@@ -190,3 +190,19 @@ def test_network_backward_matches_central_differences():
                 fd = (lp - lm) / (2 * h)
                 assert abs(fd - garr[idx]) <= 1e-6 * max(abs(fd), 1.0), (k, which, idx, fd,
                                                                          garr[idx])
+
+
+def test_adam_flat_matches_torch_adam():
+    """Three steps against torch.optim.Adam in float64 (a library routine)."""
+    torch = pytest.importorskip("torch")
+    g = _rng(14)
+    p0 = g.normal(0, 1, 50)
+    grads = [g.normal(0, 1e-2, 50) for _ in range(3)]
+    pt = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([pt], lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for t, gr in enumerate(grads, start=1):
+        pt.grad = torch.tensor(gr, dtype=torch.float64)
+        opt.step()
+        p, m, v = initnet.adam_flat(p, gr, m, v, t, 3e-3)
+    np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-13, atol=1e-15)
