@@ -14,6 +14,7 @@ oracle instead, on a bounded slab of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -64,6 +65,10 @@ def parse():
     p.add_argument("--sim", choices=["lcc", "mse", "ncc"], default="lcc")
     p.add_argument("--shape", type=str, default=None, help="Z,Y,X (default 160,256,256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--learned-pairs", type=int, default=20000,
+                   help="training pairs of the learned initialisation (0: skip it)")
+    p.add_argument("--learned-test", type=int, default=4,
+                   help="held-out pairs of the time-to-MSE comparison")
     p.add_argument("--no-registration", action="store_true",
                    help="skip the optimisation-loop timings (registration object)")
     p.add_argument("--cpu-budget", type=float, default=20.0,
@@ -447,6 +452,62 @@ def registration_runs(F, M, c, dev):
             "diffeo_ct": diffeo, "objective_configs": others}
 
 
+def learned_init_runs(dev, pairs, n_test):
+    """Learned initialisation: train the encoder-decoder on `pairs`
+    method-generated 128^3 pairs (batch 16), then on `n_test` held-out pairs
+    compare the plain optimiser (200 Adam iterations from zero) with the
+    network's prediction refined by the same optimiser until it reaches the
+    plain method's final MSE."""
+    from paper_1806_09907_gb300 import learned_init
+
+    shape, batch = (128, 128, 128), 16
+    net = learned_init.InitNet(shape, batch, dev, seed=1806)
+    # warm-up: kernel attributes and one step of every launch
+    learned_init.train(learned_init.InitNet(shape, batch, dev, seed=1), pairs=batch)
+    tr = learned_init.train(net, pairs=pairs, lr=1e-3, sigma=4.0, seed=0)
+    one = learned_init.InitNet(shape, 1, dev, seed=1806)
+    one.params.copy_(net.params)
+    one.pack()
+    src = learned_init.PairSource(shape, 1, 4.0, seed=424242, device=dev)
+    reports = []
+    for i in range(n_test):
+        F, M, ct = src.make(i)
+        reports.append(learned_init.evaluate_pair(one, F[0].clone(), M[0].clone(),
+                                                  ct[0].clone()))
+    ok = [r for r in reports if r.iterations_to_plain >= 0]
+
+    def mean(key, rs=reports):
+        return float(np.mean([getattr(r, key) for r in rs])) if rs else None
+
+    L = tr.losses
+    return {
+        "workload": "3D 128^3 blob pairs (60 blobs, sigma 3-12), c* ~ N(0, 4^2) voxels at "
+                    "spacing 8, F = M o (x + B c*); encoder-decoder 16/32/48/64 channels, bf16 "
+                    "weights and activations, fp32 accumulation (tcgen05); plain optimiser: MSE + "
+                    "0.1 diffusion, Adam lr 0.01 (normalised units), 200 iterations from zero",
+        "train": {"pairs": tr.pairs, "steps": tr.steps, "batch": batch, "seconds": tr.seconds,
+                  "ms_per_step": 1000.0 * tr.seconds / tr.steps,
+                  "loss_first_50": float(np.mean(L[:50])), "loss_last_50": float(np.mean(L[-50:]))},
+        "test_pairs": n_test,
+        "reached_plain_mse": len(ok),
+        "fallbacks": int(sum(r.fallback for r in reports)),
+        "plain_ms_mean": mean("plain_ms"),
+        "infer_ms_mean": mean("infer_ms"),
+        "learned_ms_mean": mean("learned_ms", ok),
+        "iterations_to_plain_mean": mean("iterations_to_plain", ok),
+        "speedup": (float(np.mean([r.plain_ms for r in ok]) / np.mean([r.learned_ms for r in ok]))
+                    if ok else None),
+        "iterations_to_plain_best_mse": [r.iterations_to_best for r in reports],
+        "mse": {"zero": mean("zero_mse"), "prediction": mean("init_mse"),
+                "plain_final": mean("plain_final_mse"), "plain_best": mean("plain_best_mse"),
+                "refined_final": mean("refined_final_mse")},
+        "field_rmse_vox": {"zero": mean("field_rmse_zero"), "prediction": mean("field_rmse_pred"),
+                           "plain_final": mean("field_rmse_plain"),
+                           "refined_final": mean("field_rmse_refined")},
+        "pairs": [dataclasses.asdict(r) for r in reports],
+    }
+
+
 def main():
     args = parse()
     shape = tuple(int(s) for s in args.shape.split(",")) if args.shape else SHAPE
@@ -571,6 +632,8 @@ def main():
     reg = None
     if world == 1 and not args.no_registration:
         reg = registration_runs(F, M, c, dev)
+        if args.learned_pairs > 0:
+            reg["learned_init"] = learned_init_runs(dev, args.learned_pairs, args.learned_test)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,

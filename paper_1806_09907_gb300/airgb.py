@@ -784,6 +784,10 @@ def al_initnet_head_adjoint(shape, grad_ctrl, head_shape, out=None, stream=None)
     return out
 
 
+def field_loss_workspace_bytes(batch) -> int:
+    return int(load().al_field_loss_workspace_bytes(int(batch)))
+
+
 def al_field_loss(shape, ctrl, ctrl_true, loss=None, grad=None, workspace=None, stream=None):
     """Mean squared displacement-field difference (spacing 8) and its gradient."""
     bs = bspline_init(shape, 8)

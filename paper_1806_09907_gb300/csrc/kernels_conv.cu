@@ -9,23 +9,30 @@
 //   forward   out[o][co]   = sum_{t, ci} in[s o + d_t][ci] * w[co][t][ci]
 //             M = output voxels, N = cout, K = 27 cin (k = t cin + ci)
 //   dgrad     g_in[p][ci]  = sum_{t, co} g_out[(p - d_t)/s][co] * w[co][t][ci]
-//             M = input voxels,  N = cin,  K = 27 cout (k = t cout + co)
-//             (terms whose (p - d_t)/s is not an integer in range are 0)
+//             M = input voxels,  N = cin,  K = (live taps) cout (k = tap cout + co)
+//             With stride 2 only the taps whose (p - d_t)/2 is an integer
+//             reach p: one per axis where p is even (d = 0), two where it
+//             is odd (d = -1, +1). The input voxels are split into the 8
+//             parity classes of (z, y, x), and each class runs over its own
+//             1 to 8 taps instead of 27.
 //   wgrad     g_w[(t,ci)][co] = sum_o in[s o + d_t][ci] * g_out[o][co]
 //             M = 27 cin (+1: a row of ones gives the bias gradient),
 //             N = cout, K = output voxels (split over blocks, partials
 //             summed in a fixed order by k_wgrad_reduce)
 //
 // Activations are bf16, channels last ([b][z][y][x][c]); accumulation is
-// fp32 in tensor memory. One CTA of 4 warps owns a 128-row tile of D in TMEM
-// (tcgen05.alloc), stages K in slices of 64 through a 3-deep shared-memory
-// ring, and one thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32,
-// M = 128, K = 16 per instruction) on shared-memory descriptors; a
-// tcgen05.commit per slice frees its ring slot, and the epilogue reads D
-// back with tcgen05.ld. The weight operand of the forward and dgrad passes
-// is stored pre-tiled in the shared-memory layout, so each slice of it
-// arrives with one cp.async.bulk on an mbarrier; the im2col operand is
-// gathered by the threads (16-byte loads, zero padding at the faces).
+// fp32 in tensor memory. A CTA of 4 warps owns a 128-row tile of D in TMEM
+// (tcgen05.alloc) and walks a stream of work items (one K slice of 64 of a
+// tile each, tile after tile, the CTA's tiles strided by the grid). The
+// threads gather the im2col operand of the item three slices ahead with
+// cp.async (16-byte copies, zero-filled at the faces) into a 4-slot
+// shared-memory ring; the weight operand of the forward and dgrad passes is
+// stored pre-tiled in the shared-memory layout, so each slice of it arrives
+// with one cp.async.bulk on an mbarrier. One thread issues tcgen05.mma
+// (kind::f16, bf16 x bf16 -> f32, M = 128, K = 16 per instruction) on
+// shared-memory descriptors and a tcgen05.commit frees the slot; after the
+// last slice of a tile the threads read D back with tcgen05.ld while the
+// next tile's gathers are already in flight.
 //
 // Shared-memory operand layout (no swizzle): 8 x 8 core matrices of 128 B
 // (eight 16-byte rows). For the K-major operands (forward, dgrad) a row is 8
@@ -53,12 +60,13 @@ namespace {
 __device__ int g_conv_error = 0;
 
 constexpr int kThreads = 128;
-constexpr int kStages = 3;
+constexpr int kStages = 4;                    // shared-memory ring slots
 constexpr int kBK = 64;                       // K elements per ring slot
 constexpr int kATile = 128 * kBK * 2;         // bytes of one A slot (16 KB)
 constexpr int kTargetUnits = 1216;            // wgrad blocks aimed at: 152 SMs x 8
 constexpr int kMaxN = 128;
 constexpr int kErrTimeout = 6;                // AL_ERR_TIMEOUT
+constexpr int kMaxClasses = 8;
 
 enum { FWD = 0, DGRAD = 1, WGRAD = 2 };
 
@@ -73,11 +81,14 @@ struct ConvArgs {
     int D, H, W, Do, Ho, Wo;     // input and output grid of the layer
     int cin, cout, stride;
     int N;                       // GEMM N
-    int Kreal;                   // FWD 27 cin, DGRAD 27 cout, WGRAD voxels per split
-    int nst;                     // ring slots (K slices of 64) per unit
-    int units, mtiles;           // work units; WGRAD: M tiles (units = mtiles x splits)
+    int Kreal;                   // FWD 27 cin; DGRAD 27 cout (stride 1); WGRAD voxels per split
+    int units, mtiles;           // work units (tiles); WGRAD: M tiles (units = mtiles x splits)
     int rows;                    // FWD: output voxels; DGRAD: input voxels; WGRAD: output voxels
     int relu, out_f32, add_stride, add_off;
+    int classes;                 // DGRAD with stride 2: 8 parity classes; otherwise 1
+    int cls_unit0[kMaxClasses + 1];  // first unit of each class; [classes] = units
+    int cls_nst[kMaxClasses];        // K slices of a unit of each class
+    int cls_slice0[kMaxClasses];     // first packed weight slice of each class
     uint32_t idesc, tmem_cols;
 };
 
@@ -234,10 +245,6 @@ __device__ __forceinline__ uint4 ldg16(const __nv_bfloat16 *p)
     return __ldg(reinterpret_cast<const uint4 *>(p));
 }
 
-__device__ __forceinline__ void sts16(uint8_t *p, const uint4 &v)
-{
-    *reinterpret_cast<uint4 *>(p) = v;
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -254,39 +261,330 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 __device__ __forceinline__ int kmajor_off(int r, int kc) { return (r >> 3) * 1024 + kc * 128 + (r & 7) * 16; }
 __device__ __forceinline__ int mnmajor_off(int g, int k) { return g * 1024 + (k >> 3) * 128 + (k & 7) * 16; }
 
-// ---- operand fills ---------------------------------------------------------
-// One 16-byte group of 8 consecutive channels [c0, c0 + 8) of voxel (b, z, y,
-// x) of a channels-last volume with C channels, zero outside the grid.
-__device__ __forceinline__ uint4 load_group(const __nv_bfloat16 *__restrict__ v, int b, int z,
-                                            int y, int x, int D, int H, int W, int C, int c0)
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool ok)
 {
-    if (z < 0 || z >= D || y < 0 || y >= H || x < 0 || x >= W)
-        return make_uint4(0, 0, 0, 0);
-    return ldg16(v + ((((size_t)b * D + z) * H + y) * W + x) * C + c0);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(ok ? 16 : 0)
+                 : "memory");
 }
 
-// Same for C not a multiple of 8: element e of the group is flat index
-// first + e of the (tap, channel) sequence, each an individual 2-byte load.
-// Used by the 2-channel input layer only.
-__device__ __forceinline__ uint4 load_group_scalar(const __nv_bfloat16 *__restrict__ v, int b,
-                                                   int z0, int y0, int x0, int D, int H, int W,
-                                                   int C, int first, int kend)
+__device__ __forceinline__ void cp4(uint32_t dst, const void *src, bool ok)
 {
-    uint32_t w[4] = {0, 0, 0, 0};
-    const uint16_t *raw = reinterpret_cast<const uint16_t *>(v);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int k = first + e;
-        if (k >= kend)
-            break;
-        const int t = k / C, c = k - t * C;
-        const int z = z0 + t / 9, y = y0 + (t / 3) % 3, x = x0 + t % 3;
-        if (z < 0 || z >= D || y < 0 || y >= H || x < 0 || x >= W)
-            continue;
-        const uint32_t h = __ldg(raw + ((((size_t)b * D + z) * H + y) * W + x) * C + c);
-        w[e >> 1] |= h << (16 * (e & 1));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                 "r"(ok ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ bool inside(int z, int y, int x, int D, int H, int W)
+{
+    return (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W;
+}
+
+__device__ __forceinline__ size_t vox_index(int b, int z, int y, int x, int D, int H, int W)
+{
+    return (((size_t)b * D + z) * H + y) * W + x;
+}
+
+// Position of a work item: unit u (a 128-row tile; its class and index in
+// the class), slice kk of the unit's nst slices.
+struct Cursor {
+    int u, kk, cls, tile, nst;
+};
+
+__device__ __forceinline__ void cursor_set(Cursor &c, int units, int classes, const int *unit0,
+                                           const int *nst)
+{
+    if (c.u >= units) {
+        c.nst = 0;
+        return;
     }
-    return make_uint4(w[0], w[1], w[2], w[3]);
+    int k = 0;
+    while (k + 1 < classes && c.u >= unit0[k + 1])
+        ++k;
+    c.cls = k;
+    c.tile = c.u - unit0[k];
+    c.nst = nst[k];
+}
+
+// Parity class geometry of the stride-2 dgrad: class bits (z, y, x), the
+// number of input voxels of the class per axis, and its taps per axis.
+struct ClassGeo {
+    int cz, cy, cx, Qz, Qy, Qx, rows;
+};
+
+__device__ __forceinline__ ClassGeo class_geo(const ConvArgs &a, int cls)
+{
+    ClassGeo g;
+    g.cz = (cls >> 2) & 1;
+    g.cy = (cls >> 1) & 1;
+    g.cx = cls & 1;
+    g.Qz = (a.D - g.cz + 1) / 2;
+    g.Qy = (a.H - g.cy + 1) / 2;
+    g.Qx = (a.W - g.cx + 1) / 2;
+    g.rows = g.Qz * g.Qy * g.Qx * (a.rows / (a.D * a.H * a.W));
+    return g;
+}
+
+// ---- operand fills (one work item, this thread's share) ---------------------
+// FWD: row tid of the tile is output voxel `row`; 8 chunks of 8 K elements.
+template <int MODE>
+__device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, uint8_t *A,
+                                          uint8_t *B, int tid, const int *slice0)
+{
+    const uint32_t sA = (uint32_t)__cvta_generic_to_shared(A);
+    if (MODE == FWD) {
+        const int row = c.tile * 128 + tid;
+        const bool valid = row < a.rows;
+        int r = valid ? row : 0;
+        const int ox = r % a.Wo;
+        r /= a.Wo;
+        const int oy = r % a.Ho;
+        r /= a.Ho;
+        const int oz = r % a.Do;
+        const int b = r / a.Do;
+        const int z0 = oz * a.stride - 1, y0 = oy * a.stride - 1, x0 = ox * a.stride - 1;
+        if (a.cin == 2) {
+            // K = 54: word t (2 channels) of tap t; chunk t / 4, word t % 4
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(a.act);
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int z = z0 + t / 9, y = y0 + (t / 3) % 3, x = x0 + t % 3;
+                const bool ok = valid && t < 27 && inside(z, y, x, a.D, a.H, a.W);
+                cp4(sA + kmajor_off(tid, t >> 2) + (t & 3) * 4,
+                    ok ? src + vox_index(b, z, y, x, a.D, a.H, a.W) : src, ok);
+            }
+        } else {
+            const int k0 = c.kk * kBK;
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
+                const int k = k0 + kc * 8;
+                const int t = k / a.cin, ci = k - t * a.cin;
+                const int z = z0 + t / 9, y = y0 + (t / 3) % 3, x = x0 + t % 3;
+                const bool ok = valid && k < a.Kreal && inside(z, y, x, a.D, a.H, a.W);
+                cp16(sA + kmajor_off(tid, kc),
+                     ok ? a.act + vox_index(b, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act, ok);
+            }
+        }
+    } else if (MODE == DGRAD) {
+        const int k0 = c.kk * kBK;
+        if (a.classes == 1) {
+            const int row = c.tile * 128 + tid;
+            const bool valid = row < a.rows;
+            int r = valid ? row : 0;
+            const int x = r % a.W;
+            r /= a.W;
+            const int y = r % a.H;
+            r /= a.H;
+            const int z = r % a.D;
+            const int b = r / a.D;
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
+                const int k = k0 + kc * 8;
+                const int t = k / a.cout, co = k - t * a.cout;
+                // stride 1: output voxel p - d
+                const int oz = z - (t / 9 - 1), oy = y - ((t / 3) % 3 - 1), ox = x - (t % 3 - 1);
+                const bool ok = valid && k < a.Kreal && inside(oz, oy, ox, a.Do, a.Ho, a.Wo);
+                cp16(sA + kmajor_off(tid, kc),
+                     ok ? a.act + vox_index(b, oz, oy, ox, a.Do, a.Ho, a.Wo) * a.cout + co : a.act,
+                     ok);
+            }
+        } else {
+            const ClassGeo g = class_geo(a, c.cls);
+            const int row = c.tile * 128 + tid;
+            const bool valid = row < g.rows;
+            int r = valid ? row : 0;
+            const int qx = r % g.Qx;
+            r /= g.Qx;
+            const int qy = r % g.Qy;
+            r /= g.Qy;
+            const int qz = r % g.Qz;
+            const int b = r / g.Qz;
+            const int ny = 1 + g.cy, nx = 1 + g.cx;
+            const int ntaps = (1 + g.cz) * ny * nx;
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
+                const int k = k0 + kc * 8;
+                const int ti = k / a.cout, co = k - ti * a.cout;
+                const int ix = ti % nx, iy = (ti / nx) % ny, iz = ti / (nx * ny);
+                // odd axis: tap d = -1 (i = 0) reads output q + 1, d = +1 reads q
+                const int oz = qz + (g.cz & (iz == 0)), oy = qy + (g.cy & (iy == 0)),
+                          ox = qx + (g.cx & (ix == 0));
+                const bool ok = valid && ti < ntaps && inside(oz, oy, ox, a.Do, a.Ho, a.Wo);
+                cp16(sA + kmajor_off(tid, kc),
+                     ok ? a.act + vox_index(b, oz, oy, ox, a.Do, a.Ho, a.Wo) * a.cout + co : a.act,
+                     ok);
+            }
+        }
+    } else {
+        // A: rows m = (t, ci) of M tile mt, K = 64 voxels; 1024 16-byte rows
+        const int mt = c.u % a.mtiles;
+        const int vbeg = (c.u / a.mtiles) * a.Kreal;
+        const int vend = min(vbeg + a.Kreal, a.rows);
+        const int kbase = vbeg + c.kk * kBK;
+        const int kreal = 27 * a.cin;
+#pragma unroll 2
+        for (int i = 0; i < 8; ++i) {
+            const int idx = tid + i * kThreads;
+            const int krow = idx & 7, cm = idx >> 3;
+            const int g = cm & 15, kg = cm >> 4;
+            const int k = kg * 8 + krow;
+            const int vox = kbase + k;
+            const int m0 = mt * 128 + g * 8;
+            const uint32_t dst = sA + mnmajor_off(g, k);
+            const bool vok = vox < vend;
+            int r = vok ? vox : 0;
+            const int ox = r % a.Wo;
+            r /= a.Wo;
+            const int oy = r % a.Ho;
+            r /= a.Ho;
+            const int oz = r % a.Do;
+            const int bb = r / a.Do;
+            const int zz = oz * a.stride - 1, yy = oy * a.stride - 1, xx = ox * a.stride - 1;
+            if (a.cin == 2) {
+                // words w: tap m0/2 + w (2 channels each); tap 27 = the bias row
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(a.act);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int t = m0 / 2 + w;
+                    if (t == 27) {
+                        *reinterpret_cast<uint32_t *>(A + mnmajor_off(g, k) + 4 * w) =
+                            vok ? 0x3F80u : 0u;
+                    } else {
+                        const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
+                        const bool ok = vok && t < 27 && inside(z, y, x, a.D, a.H, a.W);
+                        cp4(dst + 4 * w, ok ? src + vox_index(bb, z, y, x, a.D, a.H, a.W) : src,
+                            ok);
+                    }
+                }
+            } else if (m0 == kreal) {
+                *reinterpret_cast<uint4 *>(A + mnmajor_off(g, k)) =
+                    make_uint4(vok ? 0x3F80u : 0u, 0u, 0u, 0u);
+            } else {
+                const int t = m0 / a.cin, ci = m0 - t * a.cin;
+                const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
+                const bool ok = vok && m0 < kreal && inside(z, y, x, a.D, a.H, a.W);
+                cp16(dst, ok ? a.act + vox_index(bb, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act,
+                     ok);
+            }
+        }
+        // B: rows n = co (N / 8 groups) x 64 voxels
+        const uint32_t sB = (uint32_t)__cvta_generic_to_shared(B);
+        const int ng = a.N >> 3;
+        for (int idx = tid; idx < ng * kBK; idx += kThreads) {
+            const int krow = idx & 7, cm = idx >> 3;
+            const int g = cm % ng, kg = cm / ng;
+            const int k = kg * 8 + krow;
+            const int vox = kbase + k;
+            const bool ok = vox < vend;
+            cp16(sB + mnmajor_off(g, k), ok ? a.gout + (size_t)vox * a.cout + g * 8 : a.gout, ok);
+        }
+    }
+    (void)slice0;
+}
+
+// ---- epilogue: row tid of the finished tile from TMEM lane tid -------------
+template <int MODE>
+__device__ __forceinline__ void epilogue(const ConvArgs &a, const Cursor &c, uint32_t lane_addr,
+                                         int tid)
+{
+    size_t orow = 0;
+    bool valid = true;
+    if (MODE == FWD) {
+        const int row = c.tile * 128 + tid;
+        valid = row < a.rows;
+        orow = (size_t)row;
+    } else if (MODE == DGRAD) {
+        if (a.classes == 1) {
+            const int row = c.tile * 128 + tid;
+            valid = row < a.rows;
+            orow = (size_t)row;
+        } else {
+            const ClassGeo g = class_geo(a, c.cls);
+            const int row = c.tile * 128 + tid;
+            valid = row < g.rows;
+            int r = valid ? row : 0;
+            const int qx = r % g.Qx;
+            r /= g.Qx;
+            const int qy = r % g.Qy;
+            r /= g.Qy;
+            const int qz = r % g.Qz;
+            const int b = r / g.Qz;
+            orow = vox_index(b, 2 * qz + g.cz, 2 * qy + g.cy, 2 * qx + g.cx, a.D, a.H, a.W);
+        }
+    } else {
+        const int mt = c.u % a.mtiles, split = c.u / a.mtiles;
+        orow = (size_t)split * a.mtiles * 128 + (size_t)mt * 128 + tid;
+    }
+    for (int c0 = 0; c0 < a.N; c0 += 16) {
+        float v[16];
+        tc_load16(lane_addr + (uint32_t)c0, v);
+        if (!valid)
+            continue;
+        if (MODE == FWD) {
+            if (a.bias) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    v[i] += __ldg(a.bias + c0 + i);
+            }
+            if (a.relu) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    v[i] = fmaxf(v[i], 0.0f);
+            }
+        } else if (MODE == DGRAD) {
+            if (a.addend) {
+                const uint4 *p = reinterpret_cast<const uint4 *>(a.addend + orow * a.add_stride +
+                                                                 a.add_off + c0);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint4 w = __ldg(p + q);
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        v[8 * q + 2 * h] += bf16_lo(ws[h]);
+                        v[8 * q + 2 * h + 1] += bf16_hi(ws[h]);
+                    }
+                }
+            }
+            if (a.mask) {
+                const uint4 *p = reinterpret_cast<const uint4 *>(a.mask + orow * a.N + c0);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint4 w = __ldg(p + q);
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        if (!(bf16_lo(ws[h]) > 0.0f))
+                            v[8 * q + 2 * h] = 0.0f;
+                        if (!(bf16_hi(ws[h]) > 0.0f))
+                            v[8 * q + 2 * h + 1] = 0.0f;
+                    }
+                }
+            }
+        }
+        if (MODE == WGRAD || (MODE == FWD && a.out_f32)) {
+            float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + orow * a.N + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+            uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out) + orow * a.N +
+                                                 c0);
+            o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                              pack_bf16(v[6], v[7]));
+            o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]),
+                              pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
+        }
+    }
 }
 
 // ---- the kernel ------------------------------------------------------------
@@ -300,10 +598,19 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
     uint8_t *sB = sA + kStages * kATile;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kStages * btile);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+    int *s_unit0 = reinterpret_cast<int *>(tslot + 1);
+    int *s_nst = s_unit0 + kMaxClasses + 1;
+    int *s_slice0 = s_nst + kMaxClasses;
     const uint32_t bar_full = smem_u32(bars), bar_free = bar_full + 8 * kStages,
                    bar_done = bar_full + 16 * kStages;
     const int tid = threadIdx.x, warp = tid >> 5;
 
+    if (tid < kMaxClasses + 1)
+        s_unit0[tid] = a.cls_unit0[tid < a.classes ? tid : a.classes];
+    if (tid < kMaxClasses) {
+        s_nst[tid] = a.cls_nst[tid < a.classes ? tid : 0];
+        s_slice0[tid] = a.cls_slice0[tid < a.classes ? tid : 0];
+    }
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(bar_full + 8 * s, 1);
@@ -321,288 +628,141 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
     tc_after_sync();
     const uint32_t tmem = *tslot;
 
-    uint32_t it = 0, nunit = 0;
-    for (int u = blockIdx.x; u < a.units; u += gridDim.x, ++nunit) {
-        // ---- per-unit geometry ----
-        int row = 0, b = 0, z0 = 0, y0 = 0, x0 = 0;
-        bool valid = false;
-        int mt = 0, vbeg = 0, vend = 0;
-        if (MODE == FWD || MODE == DGRAD) {
-            row = u * 128 + tid;
-            valid = row < a.rows;
-            int r = valid ? row : 0;
-            const int X = MODE == FWD ? a.Wo : a.W, Y = MODE == FWD ? a.Ho : a.H,
-                      Z = MODE == FWD ? a.Do : a.D;
-            const int x = r % X;
-            r /= X;
-            const int y = r % Y;
-            r /= Y;
-            const int z = r % Z;
-            b = r / Z;
-            if (MODE == FWD) {
-                z0 = z * a.stride - 1;
-                y0 = y * a.stride - 1;
-                x0 = x * a.stride - 1;
-            } else {
-                z0 = z;
-                y0 = y;
-                x0 = x;
-            }
-        } else {
-            mt = u % a.mtiles;
-            vbeg = (u / a.mtiles) * a.Kreal;
-            vend = min(vbeg + a.Kreal, a.rows);
-        }
+    Cursor prod;
+    prod.u = blockIdx.x;
+    prod.kk = 0;
+    cursor_set(prod, a.units, a.classes, s_unit0, s_nst);
+    Cursor cons = prod;
+    uint32_t pit = 0, cit = 0, nunit = 0;
 
-        for (int kk = 0; kk < a.nst; ++kk, ++it) {
-            const int s = (int)(it % kStages);
-            const uint32_t use = it / kStages;
+    auto produce = [&]() {
+        if (prod.u < a.units) {
+            const int s = (int)(pit % kStages);
+            const uint32_t use = pit / kStages;
             if (use > 0)
                 mbar_wait(bar_free + 8 * s, (use - 1) & 1);
-            uint8_t *A = sA + s * kATile;
             uint8_t *B = sB + s * btile;
             if (MODE != WGRAD && tid == 0) {
                 mbar_expect_tx(bar_full + 8 * s, (uint32_t)btile);
-                bulk_load(smem_u32(B), a.wpk + (size_t)kk * a.N * kBK, (uint32_t)btile,
-                          bar_full + 8 * s);
+                bulk_load(smem_u32(B),
+                          a.wpk + (size_t)(s_slice0[prod.cls] + prod.kk) * a.N * kBK,
+                          (uint32_t)btile, bar_full + 8 * s);
             }
-            if (MODE == FWD) {
-                uint4 v[8];
-                const int k0 = kk * kBK;
-                if ((a.cin & 7) == 0) {
-#pragma unroll
-                    for (int kc = 0; kc < 8; ++kc) {
-                        const int k = k0 + kc * 8;
-                        v[kc] = make_uint4(0, 0, 0, 0);
-                        if (valid && k < a.Kreal) {
-                            const int t = k / a.cin, c = k - t * a.cin;
-                            v[kc] = load_group(a.act, b, z0 + t / 9, y0 + (t / 3) % 3, x0 + t % 3,
-                                               a.D, a.H, a.W, a.cin, c);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int kc = 0; kc < 8; ++kc)
-                        v[kc] = valid ? load_group_scalar(a.act, b, z0, y0, x0, a.D, a.H, a.W,
-                                                          a.cin, k0 + kc * 8, a.Kreal)
-                                      : make_uint4(0, 0, 0, 0);
-                }
-#pragma unroll
-                for (int kc = 0; kc < 8; ++kc)
-                    sts16(A + kmajor_off(tid, kc), v[kc]);
-            } else if (MODE == DGRAD) {
-                uint4 v[8];
-                const int k0 = kk * kBK;
-#pragma unroll
-                for (int kc = 0; kc < 8; ++kc) {
-                    const int k = k0 + kc * 8;
-                    v[kc] = make_uint4(0, 0, 0, 0);
-                    if (valid && k < a.Kreal) {
-                        const int t = k / a.cout, c = k - t * a.cout;
-                        // output voxel o with s o + d = p, per axis
-                        const int nz = z0 - (t / 9 - 1), ny = y0 - ((t / 3) % 3 - 1),
-                                  nx = x0 - (t % 3 - 1);
-                        const bool ok = a.stride == 1 ? true
-                                                      : (nz >= 0 && ny >= 0 && nx >= 0 &&
-                                                         ((nz | ny | nx) & 1) == 0);
-                        if (ok)
-                            v[kc] = load_group(a.act, b, nz / a.stride, ny / a.stride,
-                                               nx / a.stride, a.Do, a.Ho, a.Wo, a.cout, c);
-                    }
-                }
-#pragma unroll
-                for (int kc = 0; kc < 8; ++kc)
-                    sts16(A + kmajor_off(tid, kc), v[kc]);
-            } else {
-                // A: rows m = (t, ci) of M tile mt, K = 64 voxels from vbeg + 64 kk.
-                // 16 M groups x 64 K rows = 1024 16-byte rows, 8 per thread.
-                const int kbase = vbeg + kk * kBK;
-                const int kreal = 27 * a.cin;
-#pragma unroll 2
-                for (int i = 0; i < 8; ++i) {
-                    const int idx = tid + i * kThreads;
-                    const int krow = idx & 7, cm = idx >> 3;
-                    const int g = cm & 15, kg = cm >> 4;
-                    const int k = kg * 8 + krow;
-                    const int vox = kbase + k;
-                    const int m0 = mt * 128 + g * 8;
-                    uint4 val = make_uint4(0, 0, 0, 0);
-                    if (vox < vend) {
-                        int r = vox;
-                        const int ox = r % a.Wo;
-                        r /= a.Wo;
-                        const int oy = r % a.Ho;
-                        r /= a.Ho;
-                        const int oz = r % a.Do;
-                        const int bb = r / a.Do;
-                        const int zz = oz * a.stride - 1, yy = oy * a.stride - 1,
-                                  xx = ox * a.stride - 1;
-                        if ((a.cin & 7) == 0) {
-                            if (m0 < kreal) {
-                                const int t = m0 / a.cin, c = m0 - t * a.cin;
-                                val = load_group(a.act, bb, zz + t / 9, yy + (t / 3) % 3,
-                                                 xx + t % 3, a.D, a.H, a.W, a.cin, c);
-                            } else if (m0 == kreal) {
-                                val.x = 0x3F80u;  // bf16 1.0 in element 0: the bias row
-                            }
-                        } else {
-                            val = load_group_scalar(a.act, bb, zz, yy, xx, a.D, a.H, a.W, a.cin,
-                                                    m0, kreal);
-                            if (m0 <= kreal && kreal < m0 + 8) {
-                                const int e = kreal - m0;
-                                const uint32_t one = 0x3F80u << (16 * (e & 1));
-                                switch (e >> 1) {
-                                case 0: val.x |= one; break;
-                                case 1: val.y |= one; break;
-                                case 2: val.z |= one; break;
-                                default: val.w |= one; break;
-                                }
-                            }
-                        }
-                    }
-                    sts16(A + mnmajor_off(g, k), val);
-                }
-                // B: rows n = co (N / 8 groups) x 64 voxels.
-                const int ng = a.N >> 3;
-                for (int idx = tid; idx < ng * kBK; idx += kThreads) {
-                    const int krow = idx & 7, cm = idx >> 3;
-                    const int g = cm % ng, kg = cm / ng;
-                    const int k = kg * 8 + krow;
-                    const int vox = kbase + k;
-                    uint4 val = make_uint4(0, 0, 0, 0);
-                    if (vox < vend)
-                        val = ldg16(a.gout + (size_t)vox * a.cout + g * 8);
-                    sts16(B + mnmajor_off(g, k), val);
-                }
-            }
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                if (MODE != WGRAD)
-                    mbar_wait(bar_full + 8 * s, use & 1);
-                tc_after_sync();
-                const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-#pragma unroll
-                for (int j = 0; j < kBK / 16; ++j)
-                    tc_mma(tmem, sdesc(a0 + 256 * j), sdesc(b0 + 256 * j), a.idesc,
-                           (kk | j) != 0);
-                tc_commit(bar_free + 8 * s);
+            fill_item<MODE>(a, prod, sA + s * kATile, B, tid, s_slice0);
+            ++pit;
+            if (++prod.kk >= prod.nst) {
+                prod.kk = 0;
+                prod.u += gridDim.x;
+                cursor_set(prod, a.units, a.classes, s_unit0, s_nst);
             }
         }
-        if (tid == 0)
-            tc_commit(bar_done);
-        mbar_wait(bar_done, nunit & 1);
-        tc_after_sync();
+        cp_commit();
+    };
 
-        // ---- epilogue: row tid of the tile from TMEM lane tid ----
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < a.N; c0 += 16) {
-            float v[16];
-            tc_load16(lane_addr + (uint32_t)c0, v);
-            if (MODE == FWD) {
-                if (!valid)
-                    continue;
-                if (a.bias) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        v[i] += __ldg(a.bias + c0 + i);
-                }
-                if (a.relu) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        v[i] = fmaxf(v[i], 0.0f);
-                }
-                if (a.out_f32) {
-                    float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out) +
-                                                           (size_t)row * a.N + c0);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                } else {
-                    uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out) +
-                                                         (size_t)row * a.N + c0);
-                    o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                      pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                    o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]),
-                                      pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
-                }
-            } else if (MODE == DGRAD) {
-                if (!valid)
-                    continue;
-                if (a.addend) {
-                    const uint4 *p = reinterpret_cast<const uint4 *>(
-                        a.addend + (size_t)row * a.add_stride + a.add_off + c0);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const uint4 w = __ldg(p + q);
-                        v[8 * q + 0] += bf16_lo(w.x);
-                        v[8 * q + 1] += bf16_hi(w.x);
-                        v[8 * q + 2] += bf16_lo(w.y);
-                        v[8 * q + 3] += bf16_hi(w.y);
-                        v[8 * q + 4] += bf16_lo(w.z);
-                        v[8 * q + 5] += bf16_hi(w.z);
-                        v[8 * q + 6] += bf16_lo(w.w);
-                        v[8 * q + 7] += bf16_hi(w.w);
-                    }
-                }
-                if (a.mask) {
-                    const uint4 *p =
-                        reinterpret_cast<const uint4 *>(a.mask + (size_t)row * a.N + c0);
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const uint4 w = __ldg(p + q);
-                        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            if (!(bf16_lo(ws[h]) > 0.0f))
-                                v[8 * q + 2 * h] = 0.0f;
-                            if (!(bf16_hi(ws[h]) > 0.0f))
-                                v[8 * q + 2 * h + 1] = 0.0f;
-                        }
-                    }
-                }
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.out) +
-                                                     (size_t)row * a.N + c0);
-                o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                  pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]),
-                                  pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
-            } else {
-                const int split = u / a.mtiles;
-                const size_t m = (size_t)split * a.mtiles * 128 + (size_t)mt * 128 + tid;
-                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + m * a.N + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            }
-        }
-        tc_before_sync();
+#pragma unroll 1
+    for (int j = 0; j < kStages - 1; ++j)
+        produce();
+
+#pragma unroll 1
+    while (cons.u < a.units) {
+        produce();
+        cp_wait<kStages - 1>();
+        fence_proxy_async();
         __syncthreads();
+        const int s = (int)(cit % kStages);
+        const uint32_t use = cit / kStages;
+        if (tid == 0) {
+            if (MODE != WGRAD)
+                mbar_wait(bar_full + 8 * s, use & 1);
+            tc_after_sync();
+            const uint32_t a0 = smem_u32(sA + s * kATile), b0 = smem_u32(sB + s * btile);
+#pragma unroll
+            for (int j = 0; j < kBK / 16; ++j)
+                tc_mma(tmem, sdesc(a0 + 256 * j), sdesc(b0 + 256 * j), a.idesc,
+                       (cons.kk | j) != 0);
+            tc_commit(bar_free + 8 * s);
+        }
+        ++cit;
+        if (cons.kk == cons.nst - 1) {
+            if (tid == 0)
+                tc_commit(bar_done);
+            mbar_wait(bar_done, nunit & 1);
+            tc_after_sync();
+            epilogue<MODE>(a, cons, tmem + ((uint32_t)(warp * 32) << 16), tid);
+            tc_before_sync();
+            __syncthreads();
+            ++nunit;
+        }
+        if (++cons.kk >= cons.nst) {
+            cons.kk = 0;
+            cons.u += gridDim.x;
+            cursor_set(cons, a.units, a.classes, s_unit0, s_nst);
+        }
     }
+    cp_wait<0>();
+    __syncthreads();
     if (warp == 0)
         tmem_dealloc(tmem, a.tmem_cols);
 }
 
 // Weight slices in the shared-memory layout of the B operand: slice s holds
 // rows n < N and K elements [64 s, 64 s + 64), K-major, zero beyond the real
-// rows and K. fwd: B[n = co][k = t cin + ci] = w[co][t][ci] (the master
-// layout's own order); dgrad: B[n = ci][k = t cout + co] = w[co][t][ci].
-__global__ void k_pack_weights(const float *__restrict__ w, int cin, int cout, int N, int nst,
-                               int dgrad, __nv_bfloat16 *__restrict__ out)
+// rows and K. mode 0 (forward): B[n = co][k = t cin + ci] = w[co][t][ci], the
+// master layout's own order. mode 1 (dgrad, stride 1): B[n = ci][k = t cout
+// + co] = w[co][t][ci]. mode 2 (dgrad, stride 2): the slices of the 8 parity
+// classes one after the other, class c over its own taps in the order of
+// class_tap.
+__device__ __forceinline__ int class_ntaps(int cls)
 {
-    const int total = nst * N * kBK;
+    return (1 + ((cls >> 2) & 1)) * (1 + ((cls >> 1) & 1)) * (1 + (cls & 1));
+}
+
+// Tap t (0..26) of tap index ti of a parity class: per odd axis i = 0 is
+// d = -1 and i = 1 is d = +1; an even axis has d = 0 only.
+__device__ __forceinline__ int class_tap(int cls, int ti)
+{
+    const int cz = (cls >> 2) & 1, cy = (cls >> 1) & 1, cx = cls & 1;
+    const int ny = 1 + cy, nx = 1 + cx;
+    const int ix = ti % nx, iy = (ti / nx) % ny, iz = ti / (nx * ny);
+    const int dz = cz ? 2 * iz - 1 : 0, dy = cy ? 2 * iy - 1 : 0, dx = cx ? 2 * ix - 1 : 0;
+    return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+}
+
+__global__ void k_pack_weights(const float *__restrict__ w, int cin, int cout, int N, int nslices,
+                               int mode, __nv_bfloat16 *__restrict__ out)
+{
+    const int total = nslices * N * kBK;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        const int s = e / (N * kBK), rem = e - s * N * kBK;
+        int s = e / (N * kBK);
+        const int rem = e - s * N * kBK;
         const int g = rem / 512, r2 = rem - g * 512;
         const int kc = r2 / 64, r3 = r2 - kc * 64;
-        const int n = g * 8 + r3 / 8, k = s * kBK + kc * 8 + (r3 & 7);
+        const int n = g * 8 + r3 / 8;
         float val = 0.0f;
-        if (!dgrad) {
+        if (mode == 0) {
+            const int k = s * kBK + kc * 8 + (r3 & 7);
             if (n < cout && k < 27 * cin)
                 val = w[(size_t)n * 27 * cin + k];
-        } else if (n < cin && k < 27 * cout) {
-            const int t = k / cout, co = k - t * cout;
-            val = w[((size_t)co * 27 + t) * cin + n];
+        } else if (mode == 1) {
+            const int k = s * kBK + kc * 8 + (r3 & 7);
+            if (n < cin && k < 27 * cout) {
+                const int t = k / cout, co = k - t * cout;
+                val = w[((size_t)co * 27 + t) * cin + n];
+            }
+        } else {
+            int cls = 0;
+            while (cls < 7) {
+                const int ns = (class_ntaps(cls) * cout + kBK - 1) / kBK;
+                if (s < ns)
+                    break;
+                s -= ns;
+                ++cls;
+            }
+            const int k = s * kBK + kc * 8 + (r3 & 7);
+            if (n < cin && k < class_ntaps(cls) * cout) {
+                const int ti = k / cout, co = k - ti * cout;
+                val = w[((size_t)co * 27 + class_tap(cls, ti)) * cin + n];
+            }
         }
         out[e] = __float2bfloat16_rn(val);
     }
@@ -651,7 +811,35 @@ uint32_t tmem_cols_for(int N)
     return c;
 }
 
-size_t conv_smem_bytes(int N) { return 1024 + kStages * (size_t)kATile + kStages * (size_t)N * 128 + 64; }
+// Dynamic shared memory: 1024-byte alignment slack, the ring's A and B
+// slots, 2 kStages + 1 mbarriers, the TMEM address and the class tables.
+size_t conv_smem_bytes(int N)
+{
+    return 1024 + kStages * (size_t)kATile + kStages * (size_t)N * 128 + 8 * (2 * kStages + 1) +
+           4 + 4 * (3 * kMaxClasses + 1);
+}
+
+// Parity classes of the stride-2 dgrad (host side): units, K slices and
+// first packed slice of each class; returns the total number of units.
+int dgrad_classes(const ConvLayer &l, int *unit0, int *nst, int *slice0, int *total_slices)
+{
+    int u = 0, sl = 0;
+    for (int c = 0; c < kMaxClasses; ++c) {
+        const int cz = (c >> 2) & 1, cy = (c >> 1) & 1, cx = c & 1;
+        const int64_t rows = (int64_t)l.nb * ((l.D - cz + 1) / 2) * ((l.H - cy + 1) / 2) *
+                             ((l.W - cx + 1) / 2);
+        const int ntaps = (1 + cz) * (1 + cy) * (1 + cx);
+        unit0[c] = u;
+        nst[c] = (ntaps * l.cout + kBK - 1) / kBK;
+        slice0[c] = sl;
+        u += (int)((rows + 127) / 128);
+        sl += nst[c];
+    }
+    unit0[kMaxClasses] = u;
+    if (total_slices)
+        *total_slices = sl;
+    return u;
+}
 
 struct DevInfo {
     int sms = 0;
@@ -709,8 +897,13 @@ int conv_slices(int kreal) { return (kreal + kBK - 1) / kBK; }
 
 size_t conv_packed_elems(const ConvLayer &l, int dgrad)
 {
-    const int N = dgrad ? l.cin : l.cout;
-    return (size_t)conv_slices(27 * (dgrad ? l.cout : l.cin)) * N * kBK;
+    if (!dgrad)
+        return (size_t)conv_slices(27 * l.cin) * l.cout * kBK;
+    if (l.stride == 1)
+        return (size_t)conv_slices(27 * l.cout) * l.cin * kBK;
+    int u0[kMaxClasses + 1], ns[kMaxClasses], s0[kMaxClasses], total = 0;
+    dgrad_classes(l, u0, ns, s0, &total);
+    return (size_t)total * l.cin * kBK;
 }
 
 void conv_wgrad_plan(const ConvLayer &l, int *mtiles, int *splits, int *kper)
@@ -748,9 +941,10 @@ cudaError_t launch_conv_pack(const ConvLayer &l, const float *w, void *fwd, void
             w, l.cin, l.cout, l.cout, nst, 0, static_cast<__nv_bfloat16 *>(fwd));
     }
     if (dgrad) {
-        const int nst = conv_slices(27 * l.cout);
+        const int nst = (int)(conv_packed_elems(l, 1) / ((size_t)l.cin * kBK));
         k_pack_weights<<<blocks_for((int64_t)nst * l.cin * kBK, 256), 256, 0, s>>>(
-            w, l.cin, l.cout, l.cin, nst, 1, static_cast<__nv_bfloat16 *>(dgrad));
+            w, l.cin, l.cout, l.cin, nst, l.stride == 1 ? 1 : 2,
+            static_cast<__nv_bfloat16 *>(dgrad));
     }
     return cudaGetLastError();
 }
@@ -767,7 +961,18 @@ static ConvArgs base_args(const ConvLayer &l)
     a.cin = l.cin;
     a.cout = l.cout;
     a.stride = l.stride;
+    a.classes = 1;
     return a;
+}
+
+// One class covering every unit, nst slices each.
+static void single_class(ConvArgs &a, int nst)
+{
+    a.classes = 1;
+    a.cls_unit0[0] = 0;
+    a.cls_unit0[1] = a.units;
+    a.cls_nst[0] = nst;
+    a.cls_slice0[0] = 0;
 }
 
 cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *wpk,
@@ -780,9 +985,9 @@ cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *
     a.out = out;
     a.N = l.cout;
     a.Kreal = 27 * l.cin;
-    a.nst = conv_slices(a.Kreal);
     a.rows = l.nb * a.Do * a.Ho * a.Wo;
     a.units = (a.rows + 127) / 128;
+    single_class(a, conv_slices(a.Kreal));
     a.relu = relu;
     a.out_f32 = out_f32;
     a.idesc = make_idesc(a.N, false);
@@ -810,9 +1015,14 @@ cudaError_t launch_conv_dgrad(const ConvLayer &l, const void *gout, const void *
     a.out = gin;
     a.N = l.cin;
     a.Kreal = 27 * l.cout;
-    a.nst = conv_slices(a.Kreal);
     a.rows = l.nb * l.D * l.H * l.W;
-    a.units = (a.rows + 127) / 128;
+    if (l.stride == 1) {
+        a.units = (a.rows + 127) / 128;
+        single_class(a, conv_slices(a.Kreal));
+    } else {
+        a.classes = kMaxClasses;
+        a.units = dgrad_classes(l, a.cls_unit0, a.cls_nst, a.cls_slice0, nullptr);
+    }
     a.idesc = make_idesc(a.N, false);
     a.tmem_cols = tmem_cols_for(a.N);
     int grid = 0;
@@ -835,10 +1045,10 @@ cudaError_t launch_conv_wgrad(const ConvLayer &l, const void *in, const void *go
     a.out = ws;
     a.N = l.cout;
     a.Kreal = kp;
-    a.nst = kp / kBK;
     a.rows = l.nb * a.Do * a.Ho * a.Wo;
     a.mtiles = mt;
     a.units = mt * sp;
+    single_class(a, kp / kBK);
     a.idesc = make_idesc(a.N, true);
     a.tmem_cols = tmem_cols_for(a.N);
     int grid = 0;

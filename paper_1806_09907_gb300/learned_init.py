@@ -253,7 +253,8 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
     losses = torch.empty(steps, dtype=torch.float64, device=dev)
     gc = torch.empty((net.batch,) + src.lattice, dtype=torch.float32, device=dev)
     c = torch.empty_like(gc)
-    lws = torch.empty(256, dtype=torch.uint8, device=dev)
+    lws = torch.empty(max(airgb.field_loss_workspace_bytes(net.batch), 256), dtype=torch.uint8,
+                      device=dev)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for i in range(steps):
@@ -273,15 +274,23 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
 
 @dataclasses.dataclass
 class PairReport:
-    plain_final_mse: float
-    plain_ms: float          # 200 plain iterations (device time)
-    init_mse: float          # MSE at the network's prediction, before refinement
-    zero_mse: float          # MSE at c = 0
-    fallback: bool           # prediction rejected (J worse than at c = 0)
+    plain_final_mse: float    # MSE after the plain optimiser's iterations
+    plain_best_mse: float     # lowest MSE the plain run passed through
+    plain_ms: float           # the plain iterations (device time)
+    zero_mse: float           # MSE at c = 0
+    init_mse: float           # MSE at the network's prediction, before refinement
+    init_J: float             # J = MSE + lambda R at the prediction
+    zero_J: float             # J at c = 0
+    fallback: bool            # prediction rejected: its MSE is worse than at c = 0
+    infer_ms: float           # network inference (device time)
     iterations_to_plain: int  # refinement iterations until MSE <= plain_final_mse (-1: never)
-    learned_ms: float        # inference + those iterations (device time, measured)
-    field_rmse_pred: float   # rms |u_pred - u*| over voxels
-    field_rmse_plain: float  # rms |u_plain - u*|
+    learned_ms: float         # inference + those iterations, measured (device time)
+    iterations_to_best: int   # refinement iterations until MSE <= plain_best_mse (-1: never)
+    refined_final_mse: float  # MSE after as many refinement iterations as the plain run
+    field_rmse_zero: float    # rms |u*| over voxels (the error of c = 0)
+    field_rmse_pred: float    # rms |u_pred - u*|
+    field_rmse_plain: float   # rms |u_plain - u*|
+    field_rmse_refined: float  # rms |u_refined - u*|
 
 
 def _field_rmse(shape, c, c_true):
@@ -289,17 +298,23 @@ def _field_rmse(shape, c, c_true):
     return float(np.sqrt(3.0 * float(loss)))
 
 
+def _first(values, target):
+    hit = np.nonzero(values <= target)[0]
+    return int(hit[0]) if len(hit) else -1
+
+
 def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, lam=0.1):
     """Plain optimiser from zero for `iterations`, then the network's
-    prediction refined by the same optimiser until it reaches the plain
-    method's final MSE. net_single must have batch 1."""
+    prediction refined by the same optimiser: iterations and device time
+    until it reaches the plain method's final MSE. The prediction is
+    rejected (the refinement starts from zero, as the plain method) when its
+    MSE is worse than at c = 0. net_single must have batch 1."""
     shape = tuple(F.shape)
     plain = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
-                                   iterations=iterations, lr=lr)
+                                  iterations=iterations, lr=lr)
     pv = plain.levels[0].values.cpu().numpy()
-    target = float(pv[-1, 1])
+    target, best = float(pv[-1, 1]), float(pv[:, 1].min())
     ev = registration.Evaluator(shape, SPACING, "mse", lam, device=F.device)
-    # inference, timed on the device
     c0 = torch.empty((3,) + airgb.lattice_shape(shape, SPACING), dtype=torch.float32,
                      device=F.device)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -311,28 +326,30 @@ def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, la
     infer_ms = start.elapsed_time(stop)
     val0 = torch.empty(4, dtype=torch.float64, device=F.device)
     valz = torch.empty(4, dtype=torch.float64, device=F.device)
+    zero = torch.zeros_like(c0)
     ev.evaluate(F, M, c0, val0, None)
-    ev.evaluate(F, M, torch.zeros_like(c0), valz, None)
-    j0, jz = float(val0[0]), float(valz[0])
-    fallback = not (j0 <= jz)
-    start_c = torch.zeros_like(c0) if fallback else c0
+    ev.evaluate(F, M, zero, valz, None)
+    fallback = not (float(val0[1]) <= float(valz[1]))
+    start_c = zero if fallback else c0
     refine = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
                                    iterations=iterations, lr=lr, ctrl=start_c)
     rv = refine.levels[0].values.cpu().numpy()
-    hit = np.nonzero(rv[:, 1] <= target)[0]
-    k = int(hit[0]) if len(hit) else -1
+    k = _first(rv[:, 1], target)
     learned_ms = float("nan")
-    if k >= 0:
-        # the measured run: inference + exactly k refinement iterations
-        if k > 0:
-            again = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam,
-                                          factors=(1,), iterations=k, lr=lr, ctrl=start_c)
-            learned_ms = infer_ms + again.levels[0].ms
-        else:
-            learned_ms = infer_ms
+    if k == 0:
+        learned_ms = infer_ms
+    elif k > 0:
+        # the measured run: exactly k refinement iterations after the inference
+        again = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
+                                      iterations=k, lr=lr, ctrl=start_c)
+        learned_ms = infer_ms + again.levels[0].ms
     return PairReport(
-        plain_final_mse=target, plain_ms=plain.levels[0].ms,
-        init_mse=float(val0[1]), zero_mse=float(valz[1]), fallback=fallback,
-        iterations_to_plain=k, learned_ms=learned_ms,
+        plain_final_mse=target, plain_best_mse=best, plain_ms=plain.levels[0].ms,
+        zero_mse=float(valz[1]), init_mse=float(val0[1]), init_J=float(val0[0]),
+        zero_J=float(valz[0]), fallback=fallback, infer_ms=infer_ms, iterations_to_plain=k,
+        learned_ms=learned_ms, iterations_to_best=_first(rv[:, 1], best),
+        refined_final_mse=float(rv[-1, 1]),
+        field_rmse_zero=_field_rmse(shape, zero, c_true),
         field_rmse_pred=_field_rmse(shape, c0, c_true),
-        field_rmse_plain=_field_rmse(shape, plain.ctrl, c_true))
+        field_rmse_plain=_field_rmse(shape, plain.ctrl, c_true),
+        field_rmse_refined=_field_rmse(shape, refine.ctrl, c_true))
