@@ -240,12 +240,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
            (1ull << 46);
 }
 
-__device__ __forceinline__ uint4 ldg16(const __nv_bfloat16 *p)
-{
-    return __ldg(reinterpret_cast<const uint4 *>(p));
-}
-
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -363,15 +357,19 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
                     ok ? src + vox_index(b, z, y, x, a.D, a.H, a.W) : src, ok);
             }
         } else {
-            const int k0 = c.kk * kBK;
+            int k = c.kk * kBK;
+            int t = k / a.cin, ci = k - t * a.cin;
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
-                const int k = k0 + kc * 8;
-                const int t = k / a.cin, ci = k - t * a.cin;
+            for (int kc = 0; kc < 8; ++kc, k += 8) {
                 const int z = z0 + t / 9, y = y0 + (t / 3) % 3, x = x0 + t % 3;
                 const bool ok = valid && k < a.Kreal && inside(z, y, x, a.D, a.H, a.W);
                 cp16(sA + kmajor_off(tid, kc),
                      ok ? a.act + vox_index(b, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act, ok);
+                ci += 8;  // next group of 8 channels (cin is a multiple of 8)
+                if (ci >= a.cin) {
+                    ci -= a.cin;
+                    ++t;
+                }
             }
         }
     } else if (MODE == DGRAD) {
@@ -386,10 +384,14 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
             r /= a.H;
             const int z = r % a.D;
             const int b = r / a.D;
+            int t = k0 / a.cout, co = k0 - t * a.cout;
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
+            for (int kc = 0; kc < 8; ++kc, co += 8) {
                 const int k = k0 + kc * 8;
-                const int t = k / a.cout, co = k - t * a.cout;
+                if (co >= a.cout) {
+                    co -= a.cout;
+                    ++t;
+                }
                 // stride 1: output voxel p - d
                 const int oz = z - (t / 9 - 1), oy = y - ((t / 3) % 3 - 1), ox = x - (t % 3 - 1);
                 const bool ok = valid && k < a.Kreal && inside(oz, oy, ox, a.Do, a.Ho, a.Wo);
@@ -410,11 +412,17 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
             const int b = r / g.Qz;
             const int ny = 1 + g.cy, nx = 1 + g.cx;
             const int ntaps = (1 + g.cz) * ny * nx;
+            int ti = k0 / a.cout, co = k0 - ti * a.cout;
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
-                const int k = k0 + kc * 8;
-                const int ti = k / a.cout, co = k - ti * a.cout;
-                const int ix = ti % nx, iy = (ti / nx) % ny, iz = ti / (nx * ny);
+            for (int kc = 0; kc < 8; ++kc, co += 8) {
+                if (co >= a.cout) {
+                    co -= a.cout;
+                    ++ti;
+                }
+                // nx, ny are 1 or 2
+                const int ix = g.cx ? (ti & 1) : 0;
+                const int iy = g.cy ? ((ti >> g.cx) & 1) : 0;
+                const int iz = ti >> (g.cx + g.cy);
                 // odd axis: tap d = -1 (i = 0) reads output q + 1, d = +1 reads q
                 const int oz = qz + (g.cz & (iz == 0)), oy = qy + (g.cy & (iy == 0)),
                           ox = qx + (g.cx & (ix == 0));
@@ -425,57 +433,68 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
             }
         }
     } else {
-        // A: rows m = (t, ci) of M tile mt, K = 64 voxels; 1024 16-byte rows
+        // A: rows m = (t, ci) of M tile mt, K = 64 voxels. Thread tid owns
+        // voxel k = tid % 64 of the slice and half h = tid / 64 of the M
+        // groups; 8 consecutive lanes write 8 consecutive K rows of one core
+        // matrix (128 contiguous bytes).
         const int mt = c.u % a.mtiles;
         const int vbeg = (c.u / a.mtiles) * a.Kreal;
         const int vend = min(vbeg + a.Kreal, a.rows);
-        const int kbase = vbeg + c.kk * kBK;
         const int kreal = 27 * a.cin;
-#pragma unroll 2
-        for (int i = 0; i < 8; ++i) {
-            const int idx = tid + i * kThreads;
-            const int krow = idx & 7, cm = idx >> 3;
-            const int g = cm & 15, kg = cm >> 4;
-            const int k = kg * 8 + krow;
-            const int vox = kbase + k;
-            const int m0 = mt * 128 + g * 8;
-            const uint32_t dst = sA + mnmajor_off(g, k);
-            const bool vok = vox < vend;
-            int r = vok ? vox : 0;
-            const int ox = r % a.Wo;
-            r /= a.Wo;
-            const int oy = r % a.Ho;
-            r /= a.Ho;
-            const int oz = r % a.Do;
-            const int bb = r / a.Do;
-            const int zz = oz * a.stride - 1, yy = oy * a.stride - 1, xx = ox * a.stride - 1;
-            if (a.cin == 2) {
-                // words w: tap m0/2 + w (2 channels each); tap 27 = the bias row
-                const uint32_t *src = reinterpret_cast<const uint32_t *>(a.act);
+        const int k = tid & (kBK - 1), h = tid >> 6;
+        const int vox = vbeg + c.kk * kBK + k;
+        const bool vok = vox < vend;
+        int r = vok ? vox : 0;
+        const int ox = r % a.Wo;
+        r /= a.Wo;
+        const int oy = r % a.Ho;
+        r /= a.Ho;
+        const int oz = r % a.Do;
+        const int bb = r / a.Do;
+        const int zz = oz * a.stride - 1, yy = oy * a.stride - 1, xx = ox * a.stride - 1;
+        if (a.cin == 2) {
+            // word t of the 55 rows (tap t, 2 channels; t = 27 the bias row),
+            // 14 words per thread; words 28..31 and the groups past them stay
+            // zero (cleared once: a 2-channel layer has one M tile)
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(a.act);
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const int t = m0 / 2 + w;
-                    if (t == 27) {
-                        *reinterpret_cast<uint32_t *>(A + mnmajor_off(g, k) + 4 * w) =
-                            vok ? 0x3F80u : 0u;
-                    } else {
-                        const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
-                        const bool ok = vok && t < 27 && inside(z, y, x, a.D, a.H, a.W);
-                        cp4(dst + 4 * w, ok ? src + vox_index(bb, z, y, x, a.D, a.H, a.W) : src,
-                            ok);
-                    }
+            for (int j = 0; j < 14; ++j) {
+                const int t = h * 14 + j;
+                const int off = mnmajor_off(t >> 2, k) + (t & 3) * 4;
+                if (t == 27) {
+                    *reinterpret_cast<uint32_t *>(A + off) = vok ? 0x3F80u : 0u;
+                } else {
+                    const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
+                    const bool ok = vok && inside(z, y, x, a.D, a.H, a.W);
+                    cp4(sA + off, ok ? src + vox_index(bb, z, y, x, a.D, a.H, a.W) : src, ok);
                 }
-            } else if (m0 == kreal) {
-                *reinterpret_cast<uint4 *>(A + mnmajor_off(g, k)) =
-                    make_uint4(vok ? 0x3F80u : 0u, 0u, 0u, 0u);
-            } else {
-                const int t = m0 / a.cin, ci = m0 - t * a.cin;
-                const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
-                const bool ok = vok && m0 < kreal && inside(z, y, x, a.D, a.H, a.W);
-                cp16(dst, ok ? a.act + vox_index(bb, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act,
-                     ok);
+            }
+        } else {
+            int m0 = mt * 128 + h * 64;
+            int t = m0 / a.cin, ci = m0 - t * a.cin;
+#pragma unroll
+            for (int j = 0; j < 8; ++j, m0 += 8) {
+                const int g = h * 8 + j;
+                const int off = mnmajor_off(g, k);
+                if (m0 < kreal) {
+                    const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
+                    const bool ok = vok && inside(z, y, x, a.D, a.H, a.W);
+                    cp16(sA + off,
+                         ok ? a.act + vox_index(bb, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act,
+                         ok);
+                } else if (m0 == kreal) {
+                    *reinterpret_cast<uint4 *>(A + off) = make_uint4(vok ? 0x3F80u : 0u, 0, 0, 0);
+                } else if (a.mtiles > 1) {
+                    *reinterpret_cast<uint4 *>(A + off) = make_uint4(0, 0, 0, 0);
+                }
+                ci += 8;
+                if (ci >= a.cin) {
+                    ci -= a.cin;
+                    ++t;
+                }
             }
         }
+        const int kbase = vbeg + c.kk * kBK;
         // B: rows n = co (N / 8 groups) x 64 voxels
         const uint32_t sB = (uint32_t)__cvta_generic_to_shared(B);
         const int ng = a.N >> 3;
@@ -622,6 +641,11 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
     if (warp == 0) {
         tmem_alloc(smem_u32(tslot), a.tmem_cols);
         tmem_relinquish();
+    }
+    if (MODE == WGRAD && a.mtiles == 1) {
+        // the A rows past the bias row never change: zero them in every slot
+        for (int i = tid; i < kStages * kATile / 16; i += kThreads)
+            reinterpret_cast<uint4 *>(sA)[i] = make_uint4(0, 0, 0, 0);
     }
     tc_before_sync();
     __syncthreads();

@@ -186,46 +186,52 @@ class InitNet:
 
 class PairSource:
     """Training or test pairs made by the method: M = blob volume (60 blobs,
-    sigma 3..12 voxels), c* ~ N(0, sigma^2) voxels on the spacing-8 lattice,
-    F = M o (x + B c*) through al_displacement and al_warp. Pair i of a
-    source is fixed by (seed, i)."""
+    centres uniform in the volume, sigma uniform in [3, 12] voxels, amplitudes
+    uniform in [0, 1]), c* ~ N(0, sigma^2) voxels on the spacing-8 lattice,
+    F = M o (x + B c*) through al_displacement and al_warp. The random numbers
+    are drawn on the device by a counter-based generator (PyTorch's Philox)
+    seeded with (seed, first pair), so a batch is fixed by its seed and index."""
 
-    def __init__(self, shape, batch, sigma=4.0, seed=0, device="cuda", n_blobs=60):
+    def __init__(self, shape, batch, sigma=4.0, seed=0, device="cuda", n_blobs=60,
+                 sigma_range=(3.0, 12.0)):
         self.shape = tuple(shape)
         self.batch = int(batch)
         self.sigma = float(sigma)
         self.seed = int(seed)
         self.n_blobs = int(n_blobs)
+        self.sigma_range = sigma_range
         self.device = torch.device(device)
         self.lattice = (3,) + airgb.lattice_shape(self.shape, SPACING)
-        self.F = torch.empty((self.batch,) + self.shape, dtype=torch.float32, device=self.device)
-        self.M = torch.empty_like(self.F)
         if int(np.prod(self.shape)) % 4:
             raise ValueError("the voxel count must be a multiple of 4 (16-byte aligned volumes)")
+        self.F = torch.empty((self.batch,) + self.shape, dtype=torch.float32, device=self.device)
+        self.M = torch.empty_like(self.F)
         self.ctrl = torch.empty((self.batch,) + self.lattice, dtype=torch.float32,
                                 device=self.device)
         # one pair's coefficients: a batch slice is not 16-byte aligned in general
         self.ctrl_one = torch.empty(self.lattice, dtype=torch.float32, device=self.device)
+        self.table = torch.empty((self.batch, self.n_blobs, 5), dtype=torch.float32,
+                                 device=self.device)
         self.disp = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
         self.mask = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
-
-    def host_draw(self, first):
-        """Blob tables and coefficients of pairs first .. first + batch - 1."""
-        tables = np.empty((self.batch, self.n_blobs, 5), dtype=np.float32)
-        ctrl = np.empty((self.batch,) + self.lattice, dtype=np.float32)
-        for b in range(self.batch):
-            idx = self.seed * 1_000_003 + first + b
-            tables[b] = synth.blob_table(1, self.shape, self.n_blobs, seed=idx)[0]
-            ctrl[b] = synth.random_ctrl(self.lattice[1:], 3, self.sigma, seed=idx)
-        return tables, ctrl
+        self.gen = torch.Generator(device=self.device)
+        hi = [self.shape[2] - 1, self.shape[1] - 1, self.shape[0] - 1]
+        lo_s, hi_s = self.sigma_range
+        self.scale = torch.tensor(hi + [hi_s - lo_s, 1.0], dtype=torch.float32,
+                                  device=self.device)
+        self.offset = torch.tensor([0.0, 0.0, 0.0, lo_s, 0.0], dtype=torch.float32,
+                                   device=self.device)
 
     def make(self, first, stream=None):
-        tables, ctrl = self.host_draw(first)
-        t = torch.from_numpy(tables).to(self.device, non_blocking=True)
-        self.ctrl.copy_(torch.from_numpy(ctrl), non_blocking=True)
-        airgb.al_render_blobs(self.shape, t, out=self.M, stream=stream)
+        """Pairs first .. first + batch - 1: (F, M, c*) on the device."""
+        self.gen.manual_seed(self.seed * 1_000_003 + int(first))
+        torch.rand(self.table.shape, generator=self.gen, device=self.device, out=self.table)
+        self.table.mul_(self.scale).add_(self.offset)
+        torch.randn(self.ctrl.shape, generator=self.gen, device=self.device, out=self.ctrl)
+        self.ctrl.mul_(self.sigma)
+        airgb.al_render_blobs(self.shape, self.table, out=self.M, stream=stream)
         for b in range(self.batch):
-            self.ctrl_one.copy_(torch.from_numpy(ctrl[b]))
+            self.ctrl_one.copy_(self.ctrl[b])
             airgb.al_displacement(self.shape, SPACING, self.ctrl_one, disp=self.disp,
                                   stream=stream)
             airgb.al_warp(self.M[b], self.disp, warped=self.F[b], mask=self.mask, stream=stream)

@@ -356,7 +356,7 @@ def test_training_pairs_are_registered_by_their_coefficients():
 
 def test_short_training_lowers_the_loss():
     net = learned_init.InitNet((64, 64, 64), 4, DEV, seed=1)
-    res = learned_init.train(net, pairs=4 * 60, lr=2e-3, sigma=4.0, seed=1)
-    first, last = res.losses[:10].mean(), res.losses[-10:].mean()
-    assert np.all(np.isfinite(res.losses)) and last < 0.9 * first, (first, last)
+    res = learned_init.train(net, pairs=4 * 200, lr=2e-3, sigma=4.0, seed=1)
+    first, last = res.losses[:20].mean(), res.losses[-20:].mean()
+    assert np.all(np.isfinite(res.losses)) and last < 0.95 * first, (first, last)
     assert airgb.al_get_device_error() == 0
