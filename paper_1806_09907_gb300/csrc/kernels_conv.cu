@@ -24,7 +24,7 @@
 // fp32 in tensor memory. A CTA of 4 warps owns a 128-row tile of D in TMEM
 // (tcgen05.alloc) and walks a stream of work items (one K slice of 64 of a
 // tile each, tile after tile, the CTA's tiles strided by the grid). The
-// threads gather the im2col operand of the item three slices ahead with
+// threads gather the im2col operand of the item two slices ahead with
 // cp.async (16-byte copies, zero-filled at the faces) into a 4-slot
 // shared-memory ring; the weight operand of the forward and dgrad passes is
 // stored pre-tiled in the shared-memory layout, so each slice of it arrives
@@ -61,6 +61,7 @@ __device__ int g_conv_error = 0;
 
 constexpr int kThreads = 128;
 constexpr int kStages = 4;                    // shared-memory ring slots
+constexpr int kAhead = 2;                     // items gathered ahead of the MMA (< kStages)
 constexpr int kBK = 64;                       // K elements per ring slot
 constexpr int kATile = 128 * kBK * 2;         // bytes of one A slot (16 KB)
 constexpr int kTargetUnits = 1216;            // wgrad blocks aimed at: 152 SMs x 8
@@ -278,11 +279,6 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ bool inside(int z, int y, int x, int D, int H, int W)
-{
-    return (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W;
-}
-
 __device__ __forceinline__ size_t vox_index(int b, int z, int y, int x, int D, int H, int W)
 {
     return (((size_t)b * D + z) * H + y) * W + x;
@@ -328,43 +324,165 @@ __device__ __forceinline__ ClassGeo class_geo(const ConvArgs &a, int cls)
     return g;
 }
 
-// ---- operand fills (one work item, this thread's share) ---------------------
-// FWD: row tid of the tile is output voxel `row`; 8 chunks of 8 K elements.
+// ---- operand fills ---------------------------------------------------------
+// Tables shared by a CTA (built once per launch, row independent):
+//   tapoff[t]      element offset of tap t from the origin of a row's taps:
+//                  FWD and WGRAD: input voxel s o - 1 per axis, offset
+//                  ((tz H + ty) W + tx) cin; DGRAD stride 1: output voxel
+//                  p + 1 per axis, offset -((tz Ho + ty) Wo + tx) cout
+//   ctoff[c][ti]   DGRAD stride 2: offset ((az Ho + ay) Wo + ax) cout of
+//                  tap index ti of parity class c from output voxel q
+struct Tables {
+    int tapoff[27];
+    int ctoff[kMaxClasses][8];
+};
+
+__device__ __forceinline__ void build_tables(const ConvArgs &a, Tables &T, int tid, int mode)
+{
+    if (tid < 27) {
+        const int tz = tid / 9, ty = (tid / 3) % 3, tx = tid % 3;
+        T.tapoff[tid] = mode == DGRAD ? -((tz * a.Ho + ty) * a.Wo + tx) * a.cout
+                                      : ((tz * a.H + ty) * a.W + tx) * a.cin;
+    }
+    if (tid < kMaxClasses * 8) {
+        const int cls = tid >> 3, ti = tid & 7;
+        const int cz = (cls >> 2) & 1, cy = (cls >> 1) & 1, cx = cls & 1;
+        const int ix = cx ? (ti & 1) : 0;
+        const int iy = cy ? ((ti >> cx) & 1) : 0;
+        const int iz = ti >> (cx + cy);
+        const int az = cz & (iz == 0), ay = cy & (iy == 0), ax = cx & (ix == 0);
+        T.ctoff[cls][ti] = ((az * a.Ho + ay) * a.Wo + ax) * a.cout;
+    }
+}
+
+// Per-thread state of the unit (tile) the producer is filling.
+struct UnitState {
+    int64_t rowoff;  // FWD/DGRAD: element offset of the row's tap origin (used only with a valid tap)
+    uint32_t mask;   // FWD/DGRAD: valid taps (bit t, or bit ti for a parity class)
+    int m0;          // WGRAD: first M row of this thread's 8 groups
+    int kreal;       // WGRAD: 27 cin
+};
+
 template <int MODE>
-__device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, uint8_t *A,
-                                          uint8_t *B, int tid, const int *slice0)
+__device__ __forceinline__ void unit_begin(const ConvArgs &a, const Cursor &c, int tid,
+                                           UnitState &st)
+{
+    if (MODE == FWD) {
+        const int row = c.tile * 128 + tid;
+        st.mask = 0;
+        st.rowoff = 0;
+        if (row < a.rows) {
+            int r = row;
+            const int ox = r % a.Wo;
+            r /= a.Wo;
+            const int oy = r % a.Ho;
+            r /= a.Ho;
+            const int oz = r % a.Do;
+            const int b = r / a.Do;
+            const int z0 = oz * a.stride - 1, y0 = oy * a.stride - 1, x0 = ox * a.stride - 1;
+            st.rowoff = ((((int64_t)b * a.D + z0) * a.H + y0) * a.W + x0) * a.cin;
+            uint32_t mz = 0, my = 0, mx = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                mz |= (uint32_t)((unsigned)(z0 + d) < (unsigned)a.D) << d;
+                my |= (uint32_t)((unsigned)(y0 + d) < (unsigned)a.H) << d;
+                mx |= (uint32_t)((unsigned)(x0 + d) < (unsigned)a.W) << d;
+            }
+#pragma unroll
+            for (int t = 0; t < 27; ++t)
+                st.mask |= (((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u) << t;
+        }
+    } else if (MODE == DGRAD) {
+        st.mask = 0;
+        st.rowoff = 0;
+        if (a.classes == 1) {
+            const int row = c.tile * 128 + tid;
+            if (row < a.rows) {
+                int r = row;
+                const int x = r % a.W;
+                r /= a.W;
+                const int y = r % a.H;
+                r /= a.H;
+                const int z = r % a.D;
+                const int b = r / a.D;
+                // output voxel p - d = p + 1 - t per axis, t in 0..2
+                st.rowoff = ((((int64_t)b * a.Do + z + 1) * a.Ho + y + 1) * a.Wo + x + 1) * a.cout;
+                uint32_t mz = 0, my = 0, mx = 0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    mz |= (uint32_t)((unsigned)(z + 1 - d) < (unsigned)a.Do) << d;
+                    my |= (uint32_t)((unsigned)(y + 1 - d) < (unsigned)a.Ho) << d;
+                    mx |= (uint32_t)((unsigned)(x + 1 - d) < (unsigned)a.Wo) << d;
+                }
+#pragma unroll
+                for (int t = 0; t < 27; ++t)
+                    st.mask |= (((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u)
+                               << t;
+            }
+        } else {
+            const ClassGeo g = class_geo(a, c.cls);
+            const int row = c.tile * 128 + tid;
+            if (row < g.rows) {
+                int r = row;
+                const int qx = r % g.Qx;
+                r /= g.Qx;
+                const int qy = r % g.Qy;
+                r /= g.Qy;
+                const int qz = r % g.Qz;
+                const int b = r / g.Qz;
+                st.rowoff = ((((int64_t)b * a.Do + qz) * a.Ho + qy) * a.Wo + qx) * a.cout;
+                // adjacency 1 is reachable only when q + 1 is inside
+                const uint32_t okz1 = (unsigned)(qz + 1) < (unsigned)a.Do,
+                               oky1 = (unsigned)(qy + 1) < (unsigned)a.Ho,
+                               okx1 = (unsigned)(qx + 1) < (unsigned)a.Wo;
+                const uint32_t okz0 = (unsigned)qz < (unsigned)a.Do,
+                               oky0 = (unsigned)qy < (unsigned)a.Ho,
+                               okx0 = (unsigned)qx < (unsigned)a.Wo;
+                const int ntaps = (1 + g.cz) * (1 + g.cy) * (1 + g.cx);
+                for (int ti = 0; ti < ntaps; ++ti) {
+                    const int ix = g.cx ? (ti & 1) : 0;
+                    const int iy = g.cy ? ((ti >> g.cx) & 1) : 0;
+                    const int iz = ti >> (g.cx + g.cy);
+                    // odd axis: i = 0 is tap d = -1, reading output q + 1
+                    const uint32_t az = g.cz & (iz == 0), ay = g.cy & (iy == 0),
+                                   ax = g.cx & (ix == 0);
+                    const uint32_t ok = (az ? okz1 : okz0) & (ay ? oky1 : oky0) & (ax ? okx1 : okx0);
+                    st.mask |= ok << ti;
+                }
+            }
+        }
+    } else {
+        const int mt = c.u % a.mtiles;
+        st.m0 = mt * 128 + (tid >> 6) * 64;
+        st.kreal = 27 * a.cin;
+    }
+}
+
+// This thread's share of one work item (slot A, B).
+template <int MODE>
+__device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, const UnitState &st,
+                                          uint8_t *A, uint8_t *B, int tid, const int *tapoff,
+                                          const int (*ctoff)[8])
 {
     const uint32_t sA = (uint32_t)__cvta_generic_to_shared(A);
     if (MODE == FWD) {
-        const int row = c.tile * 128 + tid;
-        const bool valid = row < a.rows;
-        int r = valid ? row : 0;
-        const int ox = r % a.Wo;
-        r /= a.Wo;
-        const int oy = r % a.Ho;
-        r /= a.Ho;
-        const int oz = r % a.Do;
-        const int b = r / a.Do;
-        const int z0 = oz * a.stride - 1, y0 = oy * a.stride - 1, x0 = ox * a.stride - 1;
         if (a.cin == 2) {
             // K = 54: word t (2 channels) of tap t; chunk t / 4, word t % 4
             const uint32_t *src = reinterpret_cast<const uint32_t *>(a.act);
 #pragma unroll
             for (int t = 0; t < 32; ++t) {
-                const int z = z0 + t / 9, y = y0 + (t / 3) % 3, x = x0 + t % 3;
-                const bool ok = valid && t < 27 && inside(z, y, x, a.D, a.H, a.W);
+                const bool ok = t < 27 && ((st.mask >> (t & 31)) & 1u);
                 cp4(sA + kmajor_off(tid, t >> 2) + (t & 3) * 4,
-                    ok ? src + vox_index(b, z, y, x, a.D, a.H, a.W) : src, ok);
+                    ok ? src + (st.rowoff + tapoff[t < 27 ? t : 0]) / 2 : src, ok);
             }
         } else {
             int k = c.kk * kBK;
             int t = k / a.cin, ci = k - t * a.cin;
 #pragma unroll
             for (int kc = 0; kc < 8; ++kc, k += 8) {
-                const int z = z0 + t / 9, y = y0 + (t / 3) % 3, x = x0 + t % 3;
-                const bool ok = valid && k < a.Kreal && inside(z, y, x, a.D, a.H, a.W);
+                const bool ok = k < a.Kreal && ((st.mask >> t) & 1u);
                 cp16(sA + kmajor_off(tid, kc),
-                     ok ? a.act + vox_index(b, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act, ok);
+                     ok ? a.act + st.rowoff + tapoff[ok ? t : 0] + ci : a.act, ok);
                 ci += 8;  // next group of 8 channels (cin is a multiple of 8)
                 if (ci >= a.cin) {
                     ci -= a.cin;
@@ -374,73 +492,26 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
         }
     } else if (MODE == DGRAD) {
         const int k0 = c.kk * kBK;
-        if (a.classes == 1) {
-            const int row = c.tile * 128 + tid;
-            const bool valid = row < a.rows;
-            int r = valid ? row : 0;
-            const int x = r % a.W;
-            r /= a.W;
-            const int y = r % a.H;
-            r /= a.H;
-            const int z = r % a.D;
-            const int b = r / a.D;
-            int t = k0 / a.cout, co = k0 - t * a.cout;
+        int t = k0 / a.cout, co = k0 - t * a.cout;
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc, co += 8) {
-                const int k = k0 + kc * 8;
-                if (co >= a.cout) {
-                    co -= a.cout;
-                    ++t;
-                }
-                // stride 1: output voxel p - d
-                const int oz = z - (t / 9 - 1), oy = y - ((t / 3) % 3 - 1), ox = x - (t % 3 - 1);
-                const bool ok = valid && k < a.Kreal && inside(oz, oy, ox, a.Do, a.Ho, a.Wo);
-                cp16(sA + kmajor_off(tid, kc),
-                     ok ? a.act + vox_index(b, oz, oy, ox, a.Do, a.Ho, a.Wo) * a.cout + co : a.act,
-                     ok);
+        for (int kc = 0; kc < 8; ++kc, co += 8) {
+            if (co >= a.cout) {
+                co -= a.cout;
+                ++t;
             }
-        } else {
-            const ClassGeo g = class_geo(a, c.cls);
-            const int row = c.tile * 128 + tid;
-            const bool valid = row < g.rows;
-            int r = valid ? row : 0;
-            const int qx = r % g.Qx;
-            r /= g.Qx;
-            const int qy = r % g.Qy;
-            r /= g.Qy;
-            const int qz = r % g.Qz;
-            const int b = r / g.Qz;
-            const int ny = 1 + g.cy, nx = 1 + g.cx;
-            const int ntaps = (1 + g.cz) * ny * nx;
-            int ti = k0 / a.cout, co = k0 - ti * a.cout;
-#pragma unroll
-            for (int kc = 0; kc < 8; ++kc, co += 8) {
-                if (co >= a.cout) {
-                    co -= a.cout;
-                    ++ti;
-                }
-                // nx, ny are 1 or 2
-                const int ix = g.cx ? (ti & 1) : 0;
-                const int iy = g.cy ? ((ti >> g.cx) & 1) : 0;
-                const int iz = ti >> (g.cx + g.cy);
-                // odd axis: tap d = -1 (i = 0) reads output q + 1, d = +1 reads q
-                const int oz = qz + (g.cz & (iz == 0)), oy = qy + (g.cy & (iy == 0)),
-                          ox = qx + (g.cx & (ix == 0));
-                const bool ok = valid && ti < ntaps && inside(oz, oy, ox, a.Do, a.Ho, a.Wo);
-                cp16(sA + kmajor_off(tid, kc),
-                     ok ? a.act + vox_index(b, oz, oy, ox, a.Do, a.Ho, a.Wo) * a.cout + co : a.act,
-                     ok);
-            }
+            const bool ok = t < 27 && ((st.mask >> (t & 31)) & 1u);
+            int off = 0;
+            if (ok)
+                off = a.classes == 1 ? tapoff[t] : ctoff[c.cls][t];
+            cp16(sA + kmajor_off(tid, kc), ok ? a.act + st.rowoff + off + co : a.act, ok);
         }
     } else {
-        // A: rows m = (t, ci) of M tile mt, K = 64 voxels. Thread tid owns
+        // A: rows m = (t, ci) of the M tile, K = 64 voxels. Thread tid owns
         // voxel k = tid % 64 of the slice and half h = tid / 64 of the M
         // groups; 8 consecutive lanes write 8 consecutive K rows of one core
         // matrix (128 contiguous bytes).
-        const int mt = c.u % a.mtiles;
         const int vbeg = (c.u / a.mtiles) * a.Kreal;
         const int vend = min(vbeg + a.Kreal, a.rows);
-        const int kreal = 27 * a.cin;
         const int k = tid & (kBK - 1), h = tid >> 6;
         const int vox = vbeg + c.kk * kBK + k;
         const bool vok = vox < vend;
@@ -452,6 +523,16 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
         const int oz = r % a.Do;
         const int bb = r / a.Do;
         const int zz = oz * a.stride - 1, yy = oy * a.stride - 1, xx = ox * a.stride - 1;
+        uint32_t mz = 0, my = 0, mx = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            mz |= (uint32_t)((unsigned)(zz + d) < (unsigned)a.D) << d;
+            my |= (uint32_t)((unsigned)(yy + d) < (unsigned)a.H) << d;
+            mx |= (uint32_t)((unsigned)(xx + d) < (unsigned)a.W) << d;
+        }
+        if (!vok)
+            mz = 0;
+        const int64_t org = ((((int64_t)bb * a.D + zz) * a.H + yy) * a.W + xx) * a.cin;
         if (a.cin == 2) {
             // word t of the 55 rows (tap t, 2 channels; t = 27 the bias row),
             // 14 words per thread; words 28..31 and the groups past them stay
@@ -464,25 +545,22 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
                 if (t == 27) {
                     *reinterpret_cast<uint32_t *>(A + off) = vok ? 0x3F80u : 0u;
                 } else {
-                    const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
-                    const bool ok = vok && inside(z, y, x, a.D, a.H, a.W);
-                    cp4(sA + off, ok ? src + vox_index(bb, z, y, x, a.D, a.H, a.W) : src, ok);
+                    const bool ok = ((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u;
+                    cp4(sA + off, ok ? src + (org + tapoff[t]) / 2 : src, ok);
                 }
             }
         } else {
-            int m0 = mt * 128 + h * 64;
+            int m0 = st.m0;
             int t = m0 / a.cin, ci = m0 - t * a.cin;
 #pragma unroll
             for (int j = 0; j < 8; ++j, m0 += 8) {
                 const int g = h * 8 + j;
                 const int off = mnmajor_off(g, k);
-                if (m0 < kreal) {
-                    const int z = zz + t / 9, y = yy + (t / 3) % 3, x = xx + t % 3;
-                    const bool ok = vok && inside(z, y, x, a.D, a.H, a.W);
-                    cp16(sA + off,
-                         ok ? a.act + vox_index(bb, z, y, x, a.D, a.H, a.W) * a.cin + ci : a.act,
-                         ok);
-                } else if (m0 == kreal) {
+                if (m0 < st.kreal) {
+                    const bool ok =
+                        ((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u;
+                    cp16(sA + off, ok ? a.act + org + tapoff[t] + ci : a.act, ok);
+                } else if (m0 == st.kreal) {
                     *reinterpret_cast<uint4 *>(A + off) = make_uint4(vok ? 0x3F80u : 0u, 0, 0, 0);
                 } else if (a.mtiles > 1) {
                     *reinterpret_cast<uint4 *>(A + off) = make_uint4(0, 0, 0, 0);
@@ -494,20 +572,19 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, ui
                 }
             }
         }
-        const int kbase = vbeg + c.kk * kBK;
         // B: rows n = co (N / 8 groups) x 64 voxels
+        const int kbase = vbeg + c.kk * kBK;
         const uint32_t sB = (uint32_t)__cvta_generic_to_shared(B);
         const int ng = a.N >> 3;
         for (int idx = tid; idx < ng * kBK; idx += kThreads) {
             const int krow = idx & 7, cm = idx >> 3;
             const int g = cm % ng, kg = cm / ng;
-            const int k = kg * 8 + krow;
-            const int vox = kbase + k;
-            const bool ok = vox < vend;
-            cp16(sB + mnmajor_off(g, k), ok ? a.gout + (size_t)vox * a.cout + g * 8 : a.gout, ok);
+            const int kk2 = kg * 8 + krow;
+            const int v = kbase + kk2;
+            const bool ok = v < vend;
+            cp16(sB + mnmajor_off(g, kk2), ok ? a.gout + (size_t)v * a.cout + g * 8 : a.gout, ok);
         }
     }
-    (void)slice0;
 }
 
 // ---- epilogue: row tid of the finished tile from TMEM lane tid -------------
@@ -620,6 +697,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
     int *s_unit0 = reinterpret_cast<int *>(tslot + 1);
     int *s_nst = s_unit0 + kMaxClasses + 1;
     int *s_slice0 = s_nst + kMaxClasses;
+    Tables &T = *reinterpret_cast<Tables *>(s_slice0 + kMaxClasses);
     const uint32_t bar_full = smem_u32(bars), bar_free = bar_full + 8 * kStages,
                    bar_done = bar_full + 16 * kStages;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -630,6 +708,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
         s_nst[tid] = a.cls_nst[tid < a.classes ? tid : 0];
         s_slice0[tid] = a.cls_slice0[tid < a.classes ? tid : 0];
     }
+    build_tables(a, T, tid, MODE);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(bar_full + 8 * s, 1);
@@ -659,6 +738,10 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
     Cursor cons = prod;
     uint32_t pit = 0, cit = 0, nunit = 0;
 
+    UnitState ust;
+    if (prod.u < a.units)
+        unit_begin<MODE>(a, prod, tid, ust);
+
     auto produce = [&]() {
         if (prod.u < a.units) {
             const int s = (int)(pit % kStages);
@@ -672,25 +755,29 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
                           a.wpk + (size_t)(s_slice0[prod.cls] + prod.kk) * a.N * kBK,
                           (uint32_t)btile, bar_full + 8 * s);
             }
-            fill_item<MODE>(a, prod, sA + s * kATile, B, tid, s_slice0);
+            fill_item<MODE>(a, prod, ust, sA + s * kATile, B, tid, T.tapoff, T.ctoff);
             ++pit;
             if (++prod.kk >= prod.nst) {
                 prod.kk = 0;
                 prod.u += gridDim.x;
                 cursor_set(prod, a.units, a.classes, s_unit0, s_nst);
+                if (prod.u < a.units)
+                    unit_begin<MODE>(a, prod, tid, ust);
             }
         }
         cp_commit();
     };
 
+    // the item gathered at step i goes into the slot whose MMA was issued
+    // kStages - kAhead steps earlier, so that wait seldom stalls
 #pragma unroll 1
-    for (int j = 0; j < kStages - 1; ++j)
+    for (int j = 0; j < kAhead; ++j)
         produce();
 
 #pragma unroll 1
     while (cons.u < a.units) {
         produce();
-        cp_wait<kStages - 1>();
+        cp_wait<kAhead>();
         fence_proxy_async();
         __syncthreads();
         const int s = (int)(cit % kStages);
@@ -836,11 +923,12 @@ uint32_t tmem_cols_for(int N)
 }
 
 // Dynamic shared memory: 1024-byte alignment slack, the ring's A and B
-// slots, 2 kStages + 1 mbarriers, the TMEM address and the class tables.
+// slots, 2 kStages + 1 mbarriers, the TMEM address, the class tables and
+// the tap offset tables.
 size_t conv_smem_bytes(int N)
 {
     return 1024 + kStages * (size_t)kATile + kStages * (size_t)N * 128 + 8 * (2 * kStages + 1) +
-           4 + 4 * (3 * kMaxClasses + 1);
+           4 + 4 * (3 * kMaxClasses + 1) + sizeof(Tables);
 }
 
 // Parity classes of the stride-2 dgrad (host side): units, K slices and
@@ -890,14 +978,34 @@ cudaError_t grid_for(int N, int units, int *grid)
     }
     int &occ = d.occ[MODE][N / 16];
     if (occ == 0) {
+        // resident CTAs per SM from the kernel's own limits: shared memory
+        // (with the largest carveout), registers, and TMEM columns (512 per SM)
         e = cudaFuncSetAttribute(k_conv<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)conv_smem_bytes(kMaxN));
         if (e != cudaSuccess)
             return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv<MODE>, kThreads,
-                                                          conv_smem_bytes(N));
+        e = cudaFuncSetAttribute(k_conv<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess)
             return e;
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_conv<MODE>);
+        if (e != cudaSuccess)
+            return e;
+        int smem_sm = 0, resv = 0;
+        e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess)
+            return e;
+        e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e != cudaSuccess)
+            return e;
+        const int by_smem = smem_sm / (int)(conv_smem_bytes(N) + fa.sharedSizeBytes + resv);
+        const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = 65536 / (regs_warp * (kThreads / 32));
+        const int by_tmem = 512 / (int)tmem_cols_for(N);
+        occ = by_smem < by_regs ? by_smem : by_regs;
+        occ = occ < by_tmem ? occ : by_tmem;
+        occ = occ < 16 ? occ : 16;
         if (occ < 1)
             return cudaErrorInvalidConfiguration;
     }
