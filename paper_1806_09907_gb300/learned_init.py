@@ -304,6 +304,23 @@ def _field_rmse(shape, c, c_true):
     return float(np.sqrt(3.0 * float(loss)))
 
 
+def inference_ms(net_single: InitNet, F, M, out):
+    """The network's prediction for one pair into `out`, replayed from a CUDA
+    graph (its launches captured once); returns the device time of the replay."""
+    Fb, Mb, ob = F[None], M[None], out[None]
+    net_single.forward(Fb, Mb, out=ob)  # kernel attributes and activation buffers
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        net_single.forward(Fb, Mb, out=ob)
+    graph.replay()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    graph.replay()
+    stop.record()
+    stop.synchronize()
+    return start.elapsed_time(stop)
+
+
 def _first(values, target):
     hit = np.nonzero(values <= target)[0]
     return int(hit[0]) if len(hit) else -1
@@ -323,13 +340,7 @@ def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, la
     ev = registration.Evaluator(shape, SPACING, "mse", lam, device=F.device)
     c0 = torch.empty((3,) + airgb.lattice_shape(shape, SPACING), dtype=torch.float32,
                      device=F.device)
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    net_single.forward(F[None], M[None], out=c0[None])  # warm (kernel attributes)
-    start.record()
-    net_single.forward(F[None], M[None], out=c0[None])
-    stop.record()
-    stop.synchronize()
-    infer_ms = start.elapsed_time(stop)
+    infer_ms = inference_ms(net_single, F, M, c0)
     val0 = torch.empty(4, dtype=torch.float64, device=F.device)
     valz = torch.empty(4, dtype=torch.float64, device=F.device)
     zero = torch.zeros_like(c0)
