@@ -683,6 +683,39 @@ __device__ __forceinline__ void epilogue(const ConvArgs &a, const Cursor &c, uin
     }
 }
 
+// Before the last MMAs of a dgrad tile complete: pull this row's ReLU-factor
+// and addend channels towards L2, so the epilogue's reads do not wait on DRAM.
+__device__ __forceinline__ void dgrad_prefetch(const ConvArgs &a, const Cursor &c, int tid)
+{
+    size_t orow;
+    if (a.classes == 1) {
+        const int row = c.tile * 128 + tid;
+        if (row >= a.rows)
+            return;
+        orow = (size_t)row;
+    } else {
+        const ClassGeo g = class_geo(a, c.cls);
+        const int row = c.tile * 128 + tid;
+        if (row >= g.rows)
+            return;
+        int r = row;
+        const int qx = r % g.Qx;
+        r /= g.Qx;
+        const int qy = r % g.Qy;
+        r /= g.Qy;
+        const int qz = r % g.Qz;
+        const int b = r / g.Qz;
+        orow = vox_index(b, 2 * qz + g.cz, 2 * qy + g.cy, 2 * qx + g.cx, a.D, a.H, a.W);
+    }
+    if (a.mask)
+        for (int c0 = 0; c0 < a.N; c0 += 64)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.mask + orow * a.N + c0));
+    if (a.addend)
+        for (int c0 = 0; c0 < a.N; c0 += 64)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.addend + orow * a.add_stride +
+                                                          a.add_off + c0));
+}
+
 // ---- the kernel ------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
@@ -795,6 +828,8 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
         }
         ++cit;
         if (cons.kk == cons.nst - 1) {
+            if (MODE == DGRAD)
+                dgrad_prefetch(a, cons, tid);
             if (tid == 0)
                 tc_commit(bar_done);
             mbar_wait(bar_done, nunit & 1);
@@ -879,29 +914,33 @@ __global__ void k_pack_weights(const float *__restrict__ w, int cin, int cout, i
     }
 }
 
-// g_w[co][t][ci] and g_b[co] from the wgrad partials [split][mtiles*128][N],
-// summed over the splits in order, in double.
+// g_w[co][t][ci] and g_b[co] from the wgrad partials [split][mrows][N]: one
+// block per M row m = t cin + ci (m = 27 cin is the bias row). Thread j adds
+// the splits j / N, j / N + G, ... of column co = j % N (G = blockDim / N
+// groups, coalesced reads of the N columns of a split), in order and in
+// double; the G group sums are then added in order by one thread per
+// column, so the result does not depend on timing.
 __global__ void k_wgrad_reduce(const float *__restrict__ part, int splits, int mrows, int N,
                                int cin, int cout, float *__restrict__ gw, float *__restrict__ gb)
 {
-    const int nw = cout * 27 * cin;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nw + cout;
-         e += gridDim.x * blockDim.x) {
-        int m, co;
-        if (e < nw) {
-            co = e / (27 * cin);
-            m = e - co * 27 * cin;  // t cin + ci
-        } else {
-            co = e - nw;
-            m = 27 * cin;
-        }
-        double acc = 0.0;
-        for (int s = 0; s < splits; ++s)
-            acc += (double)part[((size_t)s * mrows + m) * N + co];
-        if (e < nw)
-            gw[e] = (float)acc;
+    __shared__ double red[256];
+    const int m = blockIdx.x;
+    const int groups = blockDim.x / N;
+    const int co = threadIdx.x % N, grp = threadIdx.x / N;
+    double acc = 0.0;
+    if (grp < groups)
+        for (int sp = grp; sp < splits; sp += groups)
+            acc += (double)part[((size_t)sp * mrows + m) * N + co];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < N && co < cout) {
+        double tot = 0.0;
+        for (int gi = 0; gi < groups; ++gi)
+            tot += red[gi * N + co];
+        if (m < 27 * cin)
+            gw[(size_t)co * 27 * cin + m] = (float)tot;
         else if (gb)
-            gb[co] = (float)acc;
+            gb[co] = (float)tot;
     }
 }
 
@@ -1195,8 +1234,9 @@ cudaError_t launch_conv_wgrad(const ConvLayer &l, const void *in, const void *go
     if (e != cudaSuccess)
         return e;
     ProfScope ps(s, "k_wgrad_reduce");
-    k_wgrad_reduce<<<blocks_for((int64_t)l.cout * 27 * l.cin + l.cout, 256), 256, 0, s>>>(
-        static_cast<const float *>(ws), sp, mt * 128, a.N, l.cin, l.cout, gw, gb);
+    // one block per M row (27 cin weights rows and the bias row)
+    k_wgrad_reduce<<<27 * l.cin + 1, 256, 0, s>>>(static_cast<const float *>(ws), sp, mt * 128,
+                                                  a.N, l.cin, l.cout, gw, gb);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,8 @@
 //                    so the loss is exactly the mean squared difference of
 //                    the two displacement fields, computed on the lattice.
 //  * k_adam_flat     Adam (Sec. III-G) on a flat fp32 parameter array
-//  * k_render_blobs  training volumes: sums of isotropic Gaussian blobs
+//  * k_render_blobs  training volumes: sums of isotropic Gaussian blobs (fast
+//                    exponential: relative error ~1e-6, synthetic data only)
 //
 // All are memory- or latency-bound elementwise/gather kernels sized to the
 // data; none needs scratch beyond what its caller passes.
@@ -179,20 +180,21 @@ __global__ void k_head_adjoint(NetGrid g, int ch, const float *__restrict__ gc,
 }
 
 // Cubic B-spline kernel k_B1D (Sec. III-C) at r (in units of the spacing).
-__device__ __forceinline__ double kb3(double r)
+__device__ __forceinline__ float kb3(float r)
 {
-    const double a = fabs(r);
-    if (a < 1.0)
-        return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
-    if (a < 2.0) {
-        const double t = 2.0 - a;
-        return t * t * t / 6.0;
+    const float a = fabsf(r);
+    if (a < 1.0f)
+        return 2.0f / 3.0f - a * a + 0.5f * a * a * a;
+    if (a < 2.0f) {
+        const float t = 2.0f - a;
+        return t * t * t * (1.0f / 6.0f);
     }
-    return 0.0;
+    return 0.0f;
 }
 
 // One block per (pair, component). Shared: the three banded Gram matrices
-// (double, n x 7 each), two float planes of the lattice, reduction scratch.
+// (n x 7 each; fp32 sums of at most 4 delta terms), two float planes of the
+// lattice, reduction scratch.
 __global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float *__restrict__ c,
                                                    const float *__restrict__ ct,
                                                    float *__restrict__ gc, double *__restrict__ part)
@@ -200,12 +202,11 @@ __global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float 
     extern __shared__ double fsm[];
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int np = nx * ny * nz;
-    double *G[3] = {fsm, fsm + 7 * nx, fsm + 7 * (nx + ny)};
-    float *b0 = reinterpret_cast<float *>(fsm + 7 * (nx + ny + nz));
+    double *red = fsm;  // kT doubles
+    float *Gs = reinterpret_cast<float *>(fsm + kT);
+    float *G[3] = {Gs, Gs + 7 * nx, Gs + 7 * (nx + ny)};
+    float *b0 = Gs + 7 * (nx + ny + nz);
     float *b1 = b0 + np;
-    // b0 starts 8-byte aligned and the two planes hold 2 np floats, so the
-    // doubles after them are 8-byte aligned too
-    double *red = reinterpret_cast<double *>(b1 + np);
     const int nn[3] = {nx, ny, nz};
     // Gram entries G[j][d + 3] = sum_x k((x - 8 (j-1))/8) k((x - 8 (j+d-1))/8).
     for (int e = threadIdx.x; e < 7 * (nx + ny + nz); e += blockDim.x) {
@@ -215,13 +216,14 @@ __global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float 
             ++ax;
         }
         const int j = r / 7, d = r % 7 - 3, j2 = j + d;
-        double acc = 0.0;
+        float acc = 0.0f;
         if (j2 >= 0 && j2 < nn[ax]) {
             const int D = a.delta, N = a.N[ax];
+            const float inv = 1.0f / (float)D;
             const int p1 = D * (j - 1), p2 = D * (j2 - 1);
             const int lo = max(0, max(p1, p2) - 2 * D), hi = min(N - 1, min(p1, p2) + 2 * D);
             for (int x = lo; x <= hi; ++x)
-                acc += kb3((double)(x - p1) / D) * kb3((double)(x - p2) / D);
+                acc += kb3((float)(x - p1) * inv) * kb3((float)(x - p2) * inv);
         }
         G[ax][r] = acc;
     }
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float 
         float acc = 0.0f;
         for (int d = -3; d <= 3; ++d)
             if (x + d >= 0 && x + d < nx)
-                acc += (float)G[0][x * 7 + d + 3] * b0[p + d];
+                acc += G[0][x * 7 + d + 3] * b0[p + d];
         b1[p] = acc;
     }
     __syncthreads();
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float 
         float acc = 0.0f;
         for (int d = -3; d <= 3; ++d)
             if (y + d >= 0 && y + d < ny)
-                acc += (float)G[1][y * 7 + d + 3] * b1[p + d * nx];
+                acc += G[1][y * 7 + d + 3] * b1[p + d * nx];
         b0[p] = acc;
     }
     __syncthreads();
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float 
         float acc = 0.0f;
         for (int d = -3; d <= 3; ++d)
             if (z + d >= 0 && z + d < nz)
-                acc += (float)G[2][z * 7 + d + 3] * b0[p + d * nx * ny];
+                acc += G[2][z * 7 + d + 3] * b0[p + d * nx * ny];
         const float e = c[off + p] - ct[off + p];
         dot += (double)e * (double)acc;
         gc[off + p] = (float)(a.gscale * acc);
@@ -333,7 +335,7 @@ __global__ void k_render_blobs(int D, int H, int W, int nblobs, const float *__r
         float acc = 0.0f;
         for (int b = 0; b < nblobs; ++b) {
             const float dx = x - tb[5 * b], dy = y - tb[5 * b + 1], dz = z - tb[5 * b + 2];
-            acc += tb[5 * b + 4] * expf((dx * dx + dy * dy + dz * dz) * tb[5 * b + 3]);
+            acc += tb[5 * b + 4] * __expf((dx * dx + dy * dy + dz * dz) * tb[5 * b + 3]);
         }
         out[(int64_t)vol * nv + i] = acc;
     }
@@ -389,8 +391,8 @@ cudaError_t launch_head_adjoint(const NetGrid &g, int ch, const float *gc, void 
 size_t field_loss_smem(const FieldLossArgs &a)
 {
     const int np = a.n[0] * a.n[1] * a.n[2];
-    return sizeof(double) * 7 * (a.n[0] + a.n[1] + a.n[2]) + sizeof(float) * 2 * np +
-           sizeof(double) * kT;
+    return sizeof(double) * kT + sizeof(float) * 7 * (a.n[0] + a.n[1] + a.n[2]) +
+           sizeof(float) * 2 * np;
 }
 
 cudaError_t launch_field_loss(const FieldLossArgs &a, int nb, const float *c, const float *ct,

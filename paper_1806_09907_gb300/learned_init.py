@@ -370,3 +370,31 @@ def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, la
         field_rmse_pred=_field_rmse(shape, c0, c_true),
         field_rmse_plain=_field_rmse(shape, plain.ctrl, c_true),
         field_rmse_refined=_field_rmse(shape, refine.ctrl, c_true))
+
+
+def _main():
+    """Training steps of the network at a given batch and volume size, for
+    timing and profiling: python -m paper_1806_09907_gb300.learned_init
+    --batch 16 --size 128 --steps 3 runs 3 steps (pair generation, forward,
+    field loss, backward, Adam, packing) and prints the device time of each."""
+    import argparse
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--batch", type=int, default=16)
+    p.add_argument("--size", type=int, default=128)
+    p.add_argument("--steps", type=int, default=3)
+    args = p.parse_args()
+    dev = torch.device("cuda", 0)
+    net = InitNet((args.size,) * 3, args.batch, dev, seed=1806)
+    for i in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        res = train(net, pairs=args.batch, lr=1e-3, seed=i)
+        b.record()
+        b.synchronize()
+        print(f"step {i}: {a.elapsed_time(b):.3f} ms, loss {float(res.losses[0]):.4f}", flush=True)
+    assert airgb.al_get_device_error() == 0
+
+
+if __name__ == "__main__":
+    _main()
