@@ -211,3 +211,78 @@ def test_batch_rejects(lib):
     assert lib.al_batch_set_policy(h, 4) == 1
     assert lib.al_batch_set_wait(h, 0, 0) == 1
     lib.al_batch_destroy(h)
+
+
+# ---- learned initialisation: layer and glue argument checks ----------------
+
+def _conv(batch=2, size=(8, 8, 8), cin=16, cout=32, stride=2):
+    return airgb.make_conv(batch, size, cin, cout, stride)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(cin=3), 2),            # channels: 2 or a multiple of 8
+    (dict(cin=264), 2),          # at most 256 input channels
+    (dict(cout=24), 2),          # output channels: a multiple of 16
+    (dict(cout=144), 2),         # at most 128
+    (dict(stride=3), 1),         # stride 1 or 2
+    (dict(batch=0), 1),
+    (dict(size=(0, 8, 8)), 2),
+    (dict(batch=1024, size=(1024, 1024, 8)), 2),  # 2^33 voxels
+])
+def test_conv_layer_shape_checks(lib, kw, status):
+    cv = _conv(**kw)
+    out = (ctypes.c_int64 * 3)()
+    assert lib.al_conv3d_output_size(ctypes.byref(cv), out) == status
+    assert lib.al_conv3d_packed_bytes(ctypes.byref(cv), 0) == 0
+
+
+def test_conv_layer_sizes(lib):
+    cv = _conv(size=(9, 12, 10))
+    assert airgb.conv_output_size(cv) == (5, 6, 5)
+    # forward: ceil(27 cin / 64) slices of cout x 64 bf16
+    assert lib.al_conv3d_packed_bytes(ctypes.byref(cv), 0) == 7 * 32 * 64 * 2
+    # stride-2 input adjoint: the 8 parity classes' own slices (1, 2, 4 or 8
+    # taps of 32 channels: 1 + 3 * 1 + 3 * 2 + 4 = 14 slices of 16 x 64)
+    assert lib.al_conv3d_packed_bytes(ctypes.byref(cv), 1) == 14 * 16 * 64 * 2
+    assert lib.al_conv3d_packed_bytes(ctypes.byref(_conv(stride=1)), 1) == 14 * 16 * 64 * 2
+    assert lib.al_conv3d_packed_bytes(ctypes.byref(_conv(cin=2)), 1) == 0  # no dgrad for 2
+    assert lib.al_conv3d_backward_weight_workspace_bytes(ctypes.byref(cv)) > 0
+
+
+def test_conv_calls_reject_before_launching(lib):
+    cv = _conv()
+    p = ctypes.byref(cv)
+    a, b = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10004)
+    assert lib.al_conv3d_forward(p, None, a, None, 1, 0, a, None) == 1
+    assert lib.al_conv3d_forward(p, a, a, None, 1, 0, b, None) == 3
+    assert lib.al_conv3d_pack(p, a, None, None, None) == 1
+    assert lib.al_conv3d_pack(ctypes.byref(_conv(cin=2)), a, None, a, None) == 7
+    # the input adjoint needs cin a multiple of 16
+    assert lib.al_conv3d_backward_data(ctypes.byref(_conv(cin=8)), a, a, None, None, 0, 0, a,
+                                       None) == 7
+    # addend stride/offset must be multiples of 8 that hold the cin channels
+    assert lib.al_conv3d_backward_data(p, a, a, None, a, 20, 0, a, None) == 1
+    assert lib.al_conv3d_backward_data(p, a, a, None, a, 32, 24, a, None) == 1
+    ws = lib.al_conv3d_backward_weight_workspace_bytes(p)
+    assert lib.al_conv3d_backward_weight(p, a, a, a, None, a, ws - 1, None) == 8
+    assert lib.al_conv3d_backward_weight(p, a, a, a, None, None, ws, None) == 8
+
+
+def test_initnet_glue_checks(lib):
+    a = ctypes.c_void_p(0x10000)
+    n3 = (ctypes.c_int64 * 3)(16, 16, 16)
+    assert lib.al_initnet_upcat(2, n3, 64, 44, a, a, a, None) == 1      # channels % 8
+    assert lib.al_initnet_upcat(0, n3, 64, 48, a, a, a, None) == 1
+    bs = airgb.bspline_init((128, 128, 128), 8)
+    bad = (ctypes.c_int64 * 3)(15, 16, 16)  # the head must sit on (N - 1)/8 + 1 voxels
+    assert lib.al_initnet_head_to_ctrl(ctypes.byref(bs), 2, bad, 16, a, a, None) == 2
+    bs6 = airgb.bspline_init((128, 128, 128), 6)
+    assert lib.al_initnet_head_to_ctrl(ctypes.byref(bs6), 2, n3, 16, a, a, None) == 7
+    assert lib.al_field_loss_workspace_bytes(4) == 4 * 3 * 8
+    assert lib.al_field_loss(ctypes.byref(bs), 4, a, a, a, a, None, 0, None) == 8
+    p = airgb.al_adam_params()
+    p.lr, p.beta1, p.beta2, p.eps = 0.0, 0.9, 0.999, 1e-8
+    assert lib.al_adam_flat(ctypes.byref(p), 10, a, a, a, a, a, None) == 1  # lr > 0
+    sz = (ctypes.c_int64 * 3)(8, 8, 8)
+    assert lib.al_render_blobs(sz, 0, 10, a, a, None) == 1
+    assert lib.al_render_blobs(sz, 1, 10, a, ctypes.c_void_p(0x10004), None) == 3

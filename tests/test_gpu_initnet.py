@@ -139,6 +139,26 @@ def test_conv_wgrad_parity(nb, dims, cin, cout, stride):
         assert rel <= 1e-5, rel
 
 
+# edge shapes: one voxel along an axis, batch 1, 8 input channels (no input
+# adjoint), the largest N (128), a long K (256 input channels)
+EDGE_CASES = [
+    (1, (1, 5, 9), 16, 16, 2),
+    (1, (2, 1, 3), 32, 16, 1),
+    (3, (7, 6, 5), 8, 16, 2),
+    (1, (6, 7, 9), 64, 128, 1),
+    (1, (4, 5, 6), 256, 32, 2),
+    (2, (13, 3, 17), 2, 32, 2),
+]
+
+
+@pytest.mark.parametrize("nb,dims,cin,cout,stride", EDGE_CASES)
+def test_conv_edge_shapes(nb, dims, cin, cout, stride):
+    test_conv_forward_parity(nb, dims, cin, cout, stride, relu=False)
+    test_conv_wgrad_parity(nb, dims, cin, cout, stride)
+    if cin % 16 == 0 and cin <= 128:
+        test_conv_dgrad_parity(nb, dims, cin, cout, stride)
+
+
 def test_glue_kernels_exact():
     g = np.random.default_rng(6)
     nb, n3 = 2, (5, 6, 7)
