@@ -391,7 +391,8 @@ typedef struct {
     int32_t cin;     /* input channels: 2, or a multiple of 8 up to 256 */
     int32_t cout;    /* output channels: a multiple of 16 up to 128 (pad with zero weights) */
     int32_t stride;  /* 1 or 2 */
-    int64_t size[3]; /* input grid D, H, W (z, y, x), each 1 .. 2^20; batch*D*H*W < 2^31 */
+    int64_t size[3]; /* input grid D, H, W (z, y, x), each 1 .. 2^20; batch*D*H*W < 2^31,
+                        3*H*W*cin and 3*Ho*Wo*cout < 2^31 */
 } al_conv3d;
 
 /* Output grid (D, H, W): (n - 1)/stride + 1 per axis (zero padding 1). */

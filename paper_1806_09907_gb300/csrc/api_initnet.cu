@@ -29,6 +29,12 @@ al_status check_conv(const al_conv3d *cv, ConvLayer *l)
     const int64_t vin = (int64_t)cv->batch * cv->size[0] * cv->size[1] * cv->size[2];
     if (vin > kMaxRows)
         return AL_ERR_SHAPE;
+    // the kernels keep tap offsets (up to 3 planes of a volume's channels) in
+    // 32-bit integers
+    const int64_t plane_in = cv->size[1] * cv->size[2] * (int64_t)cv->cin;
+    const int64_t ho = (cv->size[1] - 1) / cv->stride + 1, wo = (cv->size[2] - 1) / cv->stride + 1;
+    if (3 * plane_in >= kMaxRows || 3 * ho * wo * (int64_t)cv->cout >= kMaxRows)
+        return AL_ERR_SHAPE;
     l->nb = cv->batch;
     l->D = (int)cv->size[0];
     l->H = (int)cv->size[1];

@@ -228,6 +228,7 @@ def _conv(batch=2, size=(8, 8, 8), cin=16, cout=32, stride=2):
     (dict(batch=0), 1),
     (dict(size=(0, 8, 8)), 2),
     (dict(batch=1024, size=(1024, 1024, 8)), 2),  # 2^33 voxels
+    (dict(batch=1, size=(2, 8192, 8192), cin=16), 2),  # tap offsets beyond 32 bits
 ])
 def test_conv_layer_shape_checks(lib, kw, status):
     cv = _conv(**kw)
