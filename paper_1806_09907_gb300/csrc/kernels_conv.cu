@@ -25,7 +25,7 @@
 // (tcgen05.alloc) and walks a stream of work items (one K slice of 64 of a
 // tile each, tile after tile, the CTA's tiles strided by the grid). The
 // threads gather the im2col operand of the item two slices ahead with
-// cp.async (16-byte copies, zero-filled at the faces) into a 4-slot
+// cp.async (16-byte copies, zero-filled at the faces) into a 3-slot
 // shared-memory ring; the weight operand of the forward and dgrad passes is
 // stored pre-tiled in the shared-memory layout, so each slice of it arrives
 // with one cp.async.bulk on an mbarrier. One thread issues tcgen05.mma
@@ -60,7 +60,7 @@ namespace {
 __device__ int g_conv_error = 0;
 
 constexpr int kThreads = 128;
-constexpr int kStages = 4;                    // shared-memory ring slots
+constexpr int kStages = 3;                    // shared-memory ring slots
 constexpr int kAhead = 2;                     // items gathered ahead of the MMA (< kStages)
 constexpr int kBK = 64;                       // K elements per ring slot
 constexpr int kATile = 128 * kBK * 2;         // bytes of one A slot (16 KB)
