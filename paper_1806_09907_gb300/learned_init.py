@@ -247,12 +247,15 @@ class TrainResult:
 
 
 def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigma=4.0, seed=0,
-          log_every=0):
+          log_every=0, epochs=1, lr_final=None):
     """Adam on the field loss over `pairs` method-generated pairs, net.batch
-    per step. Returns the per-step losses and the wall time."""
+    per step, `epochs` passes over the same pairs. The step size decays from
+    lr to lr_final along a half cosine when lr_final is given (else stays lr).
+    Returns the per-step losses and the wall time."""
     dev = net.device
     src = PairSource(net.shape, net.batch, sigma, seed, dev)
-    steps = (int(pairs) + net.batch - 1) // net.batch
+    per_epoch = (int(pairs) + net.batch - 1) // net.batch
+    steps = per_epoch * int(epochs)
     m = torch.zeros_like(net.params)
     v = torch.zeros_like(net.params)
     step = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -264,11 +267,13 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for i in range(steps):
-        F, M, ct = src.make(i * net.batch)
+        F, M, ct = src.make((i % per_epoch) * net.batch)
         net.forward(F, M, out=c)
         airgb.al_field_loss(net.shape, c, ct, loss=losses[i:i + 1], grad=gc, workspace=lws)
         net.backward(gc)
-        airgb.al_adam_flat(net.params, net.grad, m, v, step, lr=lr, betas=betas, eps=eps)
+        lr_i = lr if lr_final is None else \
+            lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * i / max(steps - 1, 1)))
+        airgb.al_adam_flat(net.params, net.grad, m, v, step, lr=lr_i, betas=betas, eps=eps)
         net.pack()
         if log_every and (i + 1) % log_every == 0:
             print(f"step {i + 1}/{steps} loss {float(losses[i]):.4f}", flush=True)
