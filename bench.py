@@ -108,11 +108,11 @@ def cpu_model():
     return "unknown"
 
 
-def oracle_sample(F, M, c, sim, budget_s):
+def oracle_sample(F, M, c, sim, budget_s, depth=None):
     """Time the oracle (single-threaded, as it stands) on a z-slab of the
-    workload whose depth is chosen so one evaluation takes about budget_s.
-    Returns (evals/s of the full workload scaled by voxel count, seconds,
-    slab depth)."""
+    workload whose depth is chosen so one evaluation takes about budget_s
+    (or of the given depth). Returns (evals/s of the full workload scaled by
+    voxel count, seconds, slab depth)."""
     import oracle
     kind = {"mse": oracle.MSE, "ncc": oracle.NCC, "lcc": oracle.LCC}[sim]
     Z = F.shape[0]
@@ -124,6 +124,9 @@ def oracle_sample(F, M, c, sim, budget_s):
         oracle.objective_grad(kind, F[:depth], M[:depth], c[:, :nz], SPACING, LAMBDA, 1e-5, WINDOW)
         return time.perf_counter() - t0
 
+    if depth is not None:
+        t = run(depth)
+        return (depth / Z) / t, t, depth
     probe = min(4, Z)
     t_probe = run(probe)
     depth = int(max(2, min(Z, budget_s / max(t_probe / probe, 1e-9))))
@@ -257,10 +260,11 @@ def run_reference(args, shape):
         return 0
     F, M, c = workload(shape)
     steps, warmup = max(1, args.steps), max(0, args.warmup)
-    budget = max(1.0, 150.0 / (steps + warmup))  # whole run within a few minutes
+    budget = max(0.5, 120.0 / (steps + warmup))  # whole run within a few minutes
     vals, times, depth = [], [], None
     for i in range(warmup + steps):
-        v, t, depth = oracle_sample(F, M, c, args.sim, budget)
+        # the slab depth is probed once; every later step times the same slab
+        v, t, depth = oracle_sample(F, M, c, args.sim, budget, depth)
         if i >= warmup:
             vals.append(v)
             times.append(t * shape[0] / depth)  # seconds per full-workload evaluation
