@@ -19,7 +19,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libairgb.so")
+# AIRGB_CHECKED=1 loads the bounds-checked build (libairgb_check.so) instead
+LIB_PATH = os.path.join(_HERE, "libairgb_check.so" if os.environ.get("AIRGB_CHECKED") == "1"
+                        else "libairgb.so")
 
 AL_SIM_MSE, AL_SIM_NCC, AL_SIM_LCC = 0, 1, 2
 SIM_KINDS = {"mse": AL_SIM_MSE, "ncc": AL_SIM_NCC, "lcc": AL_SIM_LCC}

@@ -3,8 +3,10 @@
 Each translation unit under ``csrc/`` is compiled in parallel, then linked
 into ``paper_1806_09907_gb300/libairgb.so``. Rebuilds only when a source is
 newer than the library. ``AIRGB_PTXAS_VERBOSE=1`` adds ``-Xptxas -v``
-(register / spill / shared-memory report); ``AIRGB_CHECK=1`` builds the
-bounds-checked variant.
+(register / spill / shared-memory report). ``build(checked=True)`` (or
+``AIRGB_CHECK=1``) builds the bounds-checked variant ``libairgb_check.so``
+(-DAL_CHECK=1: kernels verify their gather indices and record AL_ERR_BOUNDS
+instead of reading out of range) beside the regular library.
 """
 from __future__ import annotations
 
@@ -19,7 +21,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libairgb.so")
+LIB_CHECK = os.path.join(HERE, "libairgb_check.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+BUILD_DIR_CHECK = os.path.join(HERE, "_build_check")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,11 +34,11 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libairgb")
 
 
-def _flags():
+def _flags(checked=False):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
     if os.environ.get("AIRGB_PTXAS_VERBOSE") == "1":
         f += ["-Xptxas", "-v"]
-    if os.environ.get("AIRGB_CHECK") == "1":
+    if checked:
         f += ["-DAL_CHECK=1"]
     return f
 
@@ -43,25 +47,30 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
     deps += glob.glob(os.path.join(INCLUDE, "*.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libairgb.so; returns its path."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = None) -> str:
+    """Compile and link libairgb.so (or, checked, libairgb_check.so); returns
+    its path."""
+    if checked is None:
+        checked = os.environ.get("AIRGB_CHECK") == "1"
+    lib = LIB_CHECK if checked else LIB
+    build_dir = BUILD_DIR_CHECK if checked else BUILD_DIR
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    flags = _flags()
+    os.makedirs(build_dir, exist_ok=True)
+    flags = _flags(checked)
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -72,13 +81,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

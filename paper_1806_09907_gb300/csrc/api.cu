@@ -712,11 +712,14 @@ al_status al_get_device_error(al_stream stream)
         if (cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)) != cudaSuccess)
             return AL_ERR_CUDA;
     }
-    const int hc = conv_device_error(true);
-    if (hc < 0)
-        return AL_ERR_CUDA;
-    if (h == 0)
-        h = hc;
+    const int others[4] = {conv_device_error(true), unit_error_basic(true),
+                           unit_error_fused(true), unit_error_conv(true)};
+    for (int k = 0; k < 4; ++k) {
+        if (others[k] < 0)
+            return AL_ERR_CUDA;
+        if (h == 0)
+            h = others[k];
+    }
     return h == 0 ? AL_OK : (al_status)h;
 }
 

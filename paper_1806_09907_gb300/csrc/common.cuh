@@ -5,9 +5,51 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifndef AL_CHECK
+#define AL_CHECK 0
+#endif
+
 namespace airgb {
 
 constexpr int kMaxDelta = 32;
+
+// Kernel error word of this translation unit (every .cu file that includes
+// this header has its own). A checked build (AL_CHECK=1) records
+// AL_ERR_BOUNDS (5) here when an index leaves its range and the access is
+// skipped; al_get_device_error reads and clears the words of every unit.
+static __device__ int g_unit_error = 0;
+
+// True when 0 <= i < n; in a checked build a false result is recorded.
+// Unchecked builds compile it to `true`.
+__device__ __forceinline__ bool al_index_ok(int64_t i, int64_t n)
+{
+#if AL_CHECK
+    if (i < 0 || i >= n) {
+        atomicExch(&g_unit_error, 5);
+        return false;
+    }
+#else
+    (void)i;
+    (void)n;
+#endif
+    return true;
+}
+
+// Host reader of this unit's error word (read, then clear when asked);
+// -1 if a copy failed. Instantiated once per unit that checks indices.
+#define AL_UNIT_ERROR_READER(fn)                                                  \
+    int fn(bool clear)                                                            \
+    {                                                                             \
+        int h = 0;                                                                \
+        if (cudaMemcpyFromSymbol(&h, g_unit_error, sizeof(int)) != cudaSuccess)  \
+            return -1;                                                            \
+        if (h != 0 && clear) {                                                    \
+            const int zero = 0;                                                   \
+            if (cudaMemcpyToSymbol(g_unit_error, &zero, sizeof(int)) != cudaSuccess) \
+                return -1;                                                        \
+        }                                                                         \
+        return h;                                                                 \
+    }
 
 // Image grid. 2D grids have Z = 1. nv = X*Y*Z < 2^31 (checked on the host).
 struct Grid {
@@ -120,12 +162,14 @@ struct Interp {
     float v, gx, gy, gz;
 };
 
-__device__ __forceinline__ Interp trilinear(const float *__restrict__ M, int X, int Y,
+__device__ __forceinline__ Interp trilinear(const float *__restrict__ M, int X, int Y, int Z,
                                             const AxisSample &sx, const AxisSample &sy,
                                             const AxisSample &sz)
 {
-    const int64_t base = ((int64_t)sz.cell * Y + sy.cell) * X + sx.cell;
+    int64_t base = ((int64_t)sz.cell * Y + sy.cell) * X + sx.cell;
     const int64_t sY = X, sZ = (int64_t)X * Y;
+    if (!(al_index_ok(sx.cell, X - 1) & al_index_ok(sy.cell, Y - 1) & al_index_ok(sz.cell, Z - 1)))
+        base = 0;  // checked builds only: the cell left the volume
     const float m000 = __ldg(M + base), m001 = __ldg(M + base + 1);
     const float m010 = __ldg(M + base + sY), m011 = __ldg(M + base + sY + 1);
     const float m100 = __ldg(M + base + sZ), m101 = __ldg(M + base + sZ + 1);
@@ -149,10 +193,12 @@ __device__ __forceinline__ Interp trilinear(const float *__restrict__ M, int X, 
     return r;
 }
 
-__device__ __forceinline__ Interp bilinear(const float *__restrict__ M, int X,
+__device__ __forceinline__ Interp bilinear(const float *__restrict__ M, int X, int Y,
                                            const AxisSample &sx, const AxisSample &sy)
 {
-    const int64_t base = (int64_t)sy.cell * X + sx.cell;
+    int64_t base = (int64_t)sy.cell * X + sx.cell;
+    if (!(al_index_ok(sx.cell, X - 1) & al_index_ok(sy.cell, Y - 1)))
+        base = 0;  // checked builds only: the cell left the image
     const float m00 = __ldg(M + base), m01 = __ldg(M + base + 1);
     const float m10 = __ldg(M + base + X), m11 = __ldg(M + base + X + 1);
     const float fx = sx.f, fy = sy.f;

@@ -120,7 +120,7 @@ __global__ void k_warp(Grid g, const float *__restrict__ M, const float *__restr
             in &= axis_sample(z, __ldg(u + 2 * (int64_t)g.nv + v), g.Z, sz);
         float w = 0.0f;
         if (in)
-            w = (D == 3) ? trilinear(M, g.X, g.Y, sx, sy, sz).v : bilinear(M, g.X, sx, sy).v;
+            w = (D == 3) ? trilinear(M, g.X, g.Y, g.Z, sx, sy, sz).v : bilinear(M, g.X, g.Y, sx, sy).v;
         W[v] = w;
         mask[v] = in ? 1 : 0;
     }
@@ -147,7 +147,7 @@ __global__ void k_warp_adjoint(Grid g, const float *__restrict__ M, const float 
                 in &= axis_sample(z, __ldg(u + 2 * (int64_t)g.nv + v), g.Z, sz);
             if (in) {
                 const Interp ip =
-                    (D == 3) ? trilinear(M, g.X, g.Y, sx, sy, sz) : bilinear(M, g.X, sx, sy);
+                    (D == 3) ? trilinear(M, g.X, g.Y, g.Z, sx, sy, sz) : bilinear(M, g.X, g.Y, sx, sy);
                 gx = gwv * ip.gx;
                 gy = gwv * ip.gy;
                 gz = gwv * ip.gz;
@@ -342,5 +342,7 @@ cudaError_t launch_combine(const double *sim_value, const double *reg_value, dou
     k_combine<<<1, 32, 0, s>>>(sim_value, reg_value, lambda, out);
     return cudaGetLastError();
 }
+
+AL_UNIT_ERROR_READER(unit_error_basic)
 
 }  // namespace airgb

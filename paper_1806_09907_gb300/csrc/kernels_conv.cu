@@ -86,6 +86,7 @@ struct ConvArgs {
     int units, mtiles;           // work units (tiles); WGRAD: M tiles (units = mtiles x splits)
     int rows;                    // FWD: output voxels; DGRAD: input voxels; WGRAD: output voxels
     int relu, out_f32, add_stride, add_off;
+    int64_t act_elems, gout_elems;  // elements of act and gout (checked builds)
     int classes;                 // DGRAD with stride 2: 8 parity classes; otherwise 1
     int cls_unit0[kMaxClasses + 1];  // first unit of each class; [classes] = units
     int cls_nst[kMaxClasses];        // K slices of a unit of each class
@@ -471,7 +472,9 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
             const uint32_t *src = reinterpret_cast<const uint32_t *>(a.act);
 #pragma unroll
             for (int t = 0; t < 32; ++t) {
-                const bool ok = t < 27 && ((st.mask >> (t & 31)) & 1u);
+                bool ok = t < 27 && ((st.mask >> (t & 31)) & 1u);
+                if (ok && !(al_index_ok(st.rowoff + tapoff[t], a.act_elems - 1)))
+                    ok = false;
                 cp4(sA + kmajor_off(tid, t >> 2) + (t & 3) * 4,
                     ok ? src + (st.rowoff + tapoff[t < 27 ? t : 0]) / 2 : src, ok);
             }
@@ -480,7 +483,9 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
             int t = k / a.cin, ci = k - t * a.cin;
 #pragma unroll
             for (int kc = 0; kc < 8; ++kc, k += 8) {
-                const bool ok = k < a.Kreal && ((st.mask >> t) & 1u);
+                bool ok = k < a.Kreal && ((st.mask >> t) & 1u);
+                if (ok && !al_index_ok(st.rowoff + tapoff[t] + ci, a.act_elems - 7))
+                    ok = false;
                 cp16(sA + kmajor_off(tid, kc),
                      ok ? a.act + st.rowoff + tapoff[ok ? t : 0] + ci : a.act, ok);
                 ci += 8;  // next group of 8 channels (cin is a multiple of 8)
@@ -499,10 +504,12 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
                 co -= a.cout;
                 ++t;
             }
-            const bool ok = t < 27 && ((st.mask >> (t & 31)) & 1u);
+            bool ok = t < 27 && ((st.mask >> (t & 31)) & 1u);
             int off = 0;
             if (ok)
                 off = a.classes == 1 ? tapoff[t] : ctoff[c.cls][t];
+            if (ok && !al_index_ok(st.rowoff + off + co, a.act_elems - 7))
+                ok = false;
             cp16(sA + kmajor_off(tid, kc), ok ? a.act + st.rowoff + off + co : a.act, ok);
         }
     } else {
@@ -545,7 +552,9 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
                 if (t == 27) {
                     *reinterpret_cast<uint32_t *>(A + off) = vok ? 0x3F80u : 0u;
                 } else {
-                    const bool ok = ((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u;
+                    bool ok = ((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u;
+                    if (ok && !al_index_ok(org + tapoff[t], a.act_elems - 1))
+                        ok = false;
                     cp4(sA + off, ok ? src + (org + tapoff[t]) / 2 : src, ok);
                 }
             }
@@ -557,8 +566,9 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
                 const int g = h * 8 + j;
                 const int off = mnmajor_off(g, k);
                 if (m0 < st.kreal) {
-                    const bool ok =
-                        ((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u;
+                    bool ok = ((mz >> (t / 9)) & (my >> ((t / 3) % 3)) & (mx >> (t % 3))) & 1u;
+                    if (ok && !al_index_ok(org + tapoff[t] + ci, a.act_elems - 7))
+                        ok = false;
                     cp16(sA + off, ok ? a.act + org + tapoff[t] + ci : a.act, ok);
                 } else if (m0 == st.kreal) {
                     *reinterpret_cast<uint4 *>(A + off) = make_uint4(vok ? 0x3F80u : 0u, 0, 0, 0);
@@ -581,7 +591,9 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
             const int g = cm % ng, kg = cm / ng;
             const int kk2 = kg * 8 + krow;
             const int v = kbase + kk2;
-            const bool ok = v < vend;
+            bool ok = v < vend;
+            if (ok && !al_index_ok((int64_t)v * a.cout + g * 8, a.gout_elems - 7))
+                ok = false;
             cp16(sB + mnmajor_off(g, kk2), ok ? a.gout + (size_t)v * a.cout + g * 8 : a.gout, ok);
         }
     }
@@ -1150,6 +1162,7 @@ cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *
                                 const float *bias, int relu, int out_f32, void *out, cudaStream_t s)
 {
     ConvArgs a = base_args(l);
+    a.act_elems = (int64_t)l.nb * l.D * l.H * l.W * l.cin;
     a.act = static_cast<const __nv_bfloat16 *>(in);
     a.wpk = static_cast<const __nv_bfloat16 *>(wpk);
     a.bias = bias;
@@ -1177,6 +1190,7 @@ cudaError_t launch_conv_dgrad(const ConvLayer &l, const void *gout, const void *
                               void *gin, cudaStream_t s)
 {
     ConvArgs a = base_args(l);
+    a.act_elems = (int64_t)l.nb * a.Do * a.Ho * a.Wo * l.cout;
     a.act = static_cast<const __nv_bfloat16 *>(gout);
     a.wpk = static_cast<const __nv_bfloat16 *>(wpk);
     a.mask = static_cast<const __nv_bfloat16 *>(mask);
@@ -1209,6 +1223,8 @@ cudaError_t launch_conv_wgrad(const ConvLayer &l, const void *in, const void *go
                               float *gb, void *ws, cudaStream_t s)
 {
     ConvArgs a = base_args(l);
+    a.act_elems = (int64_t)l.nb * l.D * l.H * l.W * l.cin;
+    a.gout_elems = (int64_t)l.nb * a.Do * a.Ho * a.Wo * l.cout;
     int mt, sp, kp;
     conv_wgrad_plan(l, &mt, &sp, &kp);
     a.act = static_cast<const __nv_bfloat16 *>(in);
@@ -1252,5 +1268,7 @@ int conv_device_error(bool clear)
     }
     return h;
 }
+
+AL_UNIT_ERROR_READER(unit_error_conv)
 
 }  // namespace airgb

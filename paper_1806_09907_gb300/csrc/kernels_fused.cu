@@ -305,6 +305,9 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                 if (D == 3)
                     in &= axis_cell(z, uu[2], g.Z, cz, fz[j]);
                 inb[j] = in && (z < g.Z);
+                if (!(al_index_ok(cx, g.X - 1) & al_index_ok(cy, g.Y - 1) &
+                      al_index_ok(cz, D == 3 ? g.Z - 1 : 1)))
+                    cx = cy = cz = 0;  // checked builds only: the cell left the volume
                 const float *mp = M + ((D == 3 ? cz * g.Y : 0) + cy) * g.X + cx;  // nv < 2^31
                 mcor[j][0] = __ldg(mp);
                 mcor[j][1] = __ldg(mp + 1);
@@ -318,7 +321,8 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                     mcor[j][7] = __ldg(mp + sxy + g.X + 1);
                 }
                 aux[j] = 0.0f;
-                if (MODE == MODE_MSE || MODE == MODE_NCC)
+                if ((MODE == MODE_MSE || MODE == MODE_NCC) &&
+                    al_index_ok((min(z, g.Z - 1) * g.Y + y) * g.X + x, g.nv))
                     aux[j] = __ldg(F + (min(z, g.Z - 1) * g.Y + y) * g.X + x);
 
             }
@@ -1234,5 +1238,7 @@ cudaError_t launch_batch(int delta, int blocks, const BatchProblem *probs, const
     }
     return cudaErrorInvalidValue;
 }
+
+AL_UNIT_ERROR_READER(unit_error_fused)
 
 }  // namespace airgb

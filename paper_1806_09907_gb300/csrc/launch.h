@@ -159,6 +159,11 @@ cudaError_t launch_conv_wgrad(const ConvLayer &l, const void *in, const void *go
 // Kernel error word of the layers (AL_ERR_TIMEOUT after a bounded wait ran
 // out), read and optionally cleared; -1 if the copy failed.
 int conv_device_error(bool clear);
+// Error words of the units with checked-build index checks (AL_ERR_BOUNDS),
+// read and optionally cleared; -1 if the copy failed.
+int unit_error_basic(bool clear);
+int unit_error_fused(bool clear);
+int unit_error_conv(bool clear);
 
 // Grids of the network's two coarsest levels: n3 (e3, the head) and n4 (e4),
 // (z, y, x); lat = spacing-8 lattice sizes (x, y, z).

@@ -15,13 +15,17 @@ Three pieces, all driving kernels of libairgb through the binding:
 * :func:`register` -- coarse-to-fine registration: Gaussian pyramid levels
   of both images, Adam iterations of the objective per level (captured in one
   CUDA graph per level by default) and exact B-spline refinement of the
-  coefficients between levels.
+  coefficients between levels. With ``checkpoint`` it writes the state after
+  every level (:class:`Checkpoint`, an ``.npz`` file), and ``resume`` starts
+  from such a file at the next level.
 """
 from __future__ import annotations
 
 import dataclasses
+import os
 import time
 
+import numpy as np
 import torch
 
 from . import airgb
@@ -197,9 +201,35 @@ def _level_loop(ev: Evaluator, F, M, c, iterations, lr, betas, eps, values, fina
     return run
 
 
+@dataclasses.dataclass
+class Checkpoint:
+    """State of a coarse-to-fine registration after `levels_done` levels: the
+    coefficients of the last finished level (voxel units, on that level's
+    grid) and what they belong to. Adam's moments restart at every level, so
+    nothing else is needed to continue."""
+    levels_done: int
+    factors: tuple
+    shape: tuple          # grid of the last finished level (z, y, x)
+    spacing: int
+    ctrl: np.ndarray      # float32 (d, nz, ny, nx)
+
+    def save(self, path):
+        tmp = f"{path}.{os.getpid()}.tmp.npz"
+        np.savez(tmp, levels_done=self.levels_done, factors=np.asarray(self.factors),
+                 shape=np.asarray(self.shape), spacing=self.spacing, ctrl=self.ctrl)
+        os.replace(tmp, path)
+
+    @staticmethod
+    def load(path):
+        with np.load(path) as z:
+            return Checkpoint(int(z["levels_done"]), tuple(int(f) for f in z["factors"]),
+                              tuple(int(n) for n in z["shape"]), int(z["spacing"]),
+                              np.array(z["ctrl"], dtype=np.float32))
+
+
 def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), iterations=150,
              lr=0.01, betas=(0.9, 0.999), eps=1e-8, sim_eps=1e-5, window=7, ctrl=None,
-             graph=True, diffeo_steps=None):
+             graph=True, diffeo_steps=None, checkpoint=None, resume=None, max_levels=None):
     """Coarse-to-fine B-spline registration of `moving` onto `fixed`.
 
     factors: pyramid factors from coarse to fine, each twice the next, ending
@@ -210,6 +240,12 @@ def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), it
     replayed once; graph=False issues the same launches directly.
     diffeo_steps: None for the plain B-spline model, else the squarings of
     the diffeomorphic model (the coefficients then parametrise the velocity).
+    checkpoint: path of an .npz file rewritten after every finished level.
+    resume: a Checkpoint (or its path) of the same factors and spacing; the
+    registration continues at the level after its last finished one, from
+    its coefficients, and returns only the levels it ran.
+    max_levels: stop after running this many levels in this call (the rest
+    can follow later from the checkpoint).
     """
     factors = tuple(int(f) for f in factors)
     if factors[-1] != 1 or any(a != 2 * b for a, b in zip(factors, factors[1:])):
@@ -223,7 +259,19 @@ def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), it
     t0 = time.perf_counter()
     levels, c = [], None
     prev_shape = None
-    for f, n_it in zip(factors, iters):
+    first = 0
+    if resume is not None:
+        ck = Checkpoint.load(resume) if isinstance(resume, (str, os.PathLike)) else resume
+        if ck.factors != factors or ck.spacing != int(spacing):
+            raise ValueError("the checkpoint belongs to other pyramid factors or spacing")
+        first = ck.levels_done
+        c = torch.from_numpy(ck.ctrl).to(dev)
+        prev_shape = ck.shape
+    for li, (f, n_it) in enumerate(zip(factors, iters)):
+        if li < first:
+            continue
+        if max_levels is not None and len(levels) >= int(max_levels):
+            break
         F = airgb.al_pyramid_level(fixed, f)
         M = airgb.al_pyramid_level(moving, f)
         shape = tuple(F.shape)
@@ -255,6 +303,8 @@ def register(fixed, moving, spacing=6, sim="lcc", lam=0.1, factors=(4, 2, 1), it
         stop.synchronize()
         levels.append(Level(f, shape, n_it, values, start.elapsed_time(stop)))
         prev_shape = shape
+        if checkpoint is not None:
+            Checkpoint(li + 1, factors, shape, int(spacing), c.cpu().numpy()).save(checkpoint)
     torch.cuda.synchronize(dev)
     return Result(c, levels, time.perf_counter() - t0)
 

@@ -287,3 +287,16 @@ def test_initnet_glue_checks(lib):
     sz = (ctypes.c_int64 * 3)(8, 8, 8)
     assert lib.al_render_blobs(sz, 0, 10, a, a, None) == 1
     assert lib.al_render_blobs(sz, 1, 10, a, ctypes.c_void_p(0x10004), None) == 3
+
+
+def test_registration_checkpoint_roundtrip(tmp_path):
+    from paper_1806_09907_gb300 import registration
+
+    c = np.random.default_rng(3).normal(0, 1, (3, 7, 8, 9)).astype(np.float32)
+    ck = registration.Checkpoint(2, (4, 2, 1), (40, 64, 64), 6, c)
+    path = str(tmp_path / "s.npz")
+    ck.save(path)
+    back = registration.Checkpoint.load(path)
+    assert (back.levels_done, back.factors, back.shape, back.spacing) == (2, (4, 2, 1),
+                                                                        (40, 64, 64), 6)
+    assert back.ctrl.dtype == np.float32 and np.array_equal(back.ctrl, c)

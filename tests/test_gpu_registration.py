@@ -319,3 +319,19 @@ def test_register_adam_200_iterations_config_128():
     vals = host(r.levels[0].values)
     print(f"MSE {vals[0, 1]:.4e} -> {vals[-1, 1]:.4e} in {r.levels[0].ms:.1f} ms")
     assert vals[-1, 1] < 0.5 * vals[0, 1]
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    """A two-level registration stopped after its first level and resumed
+    from the checkpoint ends with the coefficients of the uninterrupted run."""
+    F, M = (dev(a) for a in synth.ct_pair((24, 40, 36), n_inner=6))
+    kw = dict(spacing=6, sim="lcc", lam=0.1, factors=(2, 1), iterations=15)
+    full = registration.register(F, M, **kw)
+    path = str(tmp_path / "state.npz")
+    part = registration.register(F, M, checkpoint=path, max_levels=1, **kw)
+    ck = registration.Checkpoint.load(path)
+    assert ck.levels_done == 1 and len(part.levels) == 1 and ck.shape == part.levels[0].shape
+    rest = registration.register(F, M, resume=path, checkpoint=path, **kw)
+    assert len(rest.levels) == 1 and rest.levels[0].factor == 1
+    assert torch.equal(rest.ctrl, full.ctrl)
+    assert registration.Checkpoint.load(path).levels_done == 2
