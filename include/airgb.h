@@ -412,10 +412,17 @@ al_status al_conv3d_pack(const al_conv3d *cv, const float *weight, void *packed_
 /* out[b][o][co] = bias[co] + sum_t sum_ci in[b][stride*o + d_t][ci] w[co][t][ci]
  * (in = 0 outside the grid); relu != 0 applies max(., 0). input bf16
  * (batch x D x H x W x cin); bias fp32 (cout, nullable); output bf16, or fp32
- * when out_f32 != 0 (batch x output grid x cout). */
+ * when out_f32 != 0 (batch x output grid x cout).
+ * workspace (nullable): when the layer has few output tiles (small batches,
+ * coarse levels) the sum over K is split into up to 8 partitions run by
+ * separate CTAs, whose fp32 partials (al_conv3d_forward_workspace_bytes, 0
+ * when the layer is not split) are then added in a fixed order. A NULL or
+ * smaller workspace runs the layer unsplit; both are deterministic and agree
+ * to fp32 rounding. */
+size_t al_conv3d_forward_workspace_bytes(const al_conv3d *cv);
 al_status al_conv3d_forward(const al_conv3d *cv, const void *input, const void *packed_fwd,
                             const float *bias, int32_t relu, int32_t out_f32, void *output,
-                            al_stream stream);
+                            void *workspace, size_t workspace_bytes, al_stream stream);
 
 /* Input adjoint of the layer's linear part:
  *   g_in[b][p][ci] = sum_{t, co} g_out[b][(p - d_t)/stride][co] w[co][t][ci]

@@ -40,7 +40,8 @@ EXPORTS = (
     "al_batch_set_wait", "al_batch_status", "al_exp_field", "al_exp_field_workspace_bytes",
     "al_exp_field_adjoint", "al_exp_field_adjoint_workspace_bytes", "al_objective_grad_diffeo",
     "al_objective_diffeo_workspace_bytes", "al_conv3d_output_size", "al_conv3d_packed_bytes",
-    "al_conv3d_pack", "al_conv3d_forward", "al_conv3d_backward_data",
+    "al_conv3d_pack", "al_conv3d_forward", "al_conv3d_forward_workspace_bytes",
+    "al_conv3d_backward_data",
     "al_conv3d_backward_weight_workspace_bytes", "al_conv3d_backward_weight", "al_initnet_input",
     "al_initnet_upcat", "al_initnet_upcat_adjoint", "al_initnet_head_to_ctrl",
     "al_initnet_head_adjoint", "al_field_loss_workspace_bytes", "al_field_loss", "al_adam_flat",
@@ -143,7 +144,8 @@ def load():
         "al_conv3d_output_size": ([P(al_conv3d), P(ctypes.c_int64)], I32),
         "al_conv3d_packed_bytes": ([P(al_conv3d), I32], SZ),
         "al_conv3d_pack": ([P(al_conv3d), VP, VP, VP, VP], I32),
-        "al_conv3d_forward": ([P(al_conv3d), VP, VP, VP, I32, I32, VP, VP], I32),
+        "al_conv3d_forward": ([P(al_conv3d), VP, VP, VP, I32, I32, VP, VP, SZ, VP], I32),
+        "al_conv3d_forward_workspace_bytes": ([P(al_conv3d)], SZ),
         "al_conv3d_backward_data": ([P(al_conv3d), VP, VP, VP, VP, I32, I32, VP, VP], I32),
         "al_conv3d_backward_weight_workspace_bytes": ([P(al_conv3d)], SZ),
         "al_conv3d_backward_weight": ([P(al_conv3d), VP, VP, VP, VP, VP, SZ, VP], I32),
@@ -674,8 +676,14 @@ def al_conv3d_pack(cv, weight, fwd=True, dgrad=True, stream=None):
     return pf, pd
 
 
+def conv_forward_workspace_bytes(cv) -> int:
+    return int(load().al_conv3d_forward_workspace_bytes(ctypes.byref(cv)))
+
+
 def al_conv3d_forward(cv, x, packed_fwd, bias=None, relu=True, out_f32=False, out=None,
-                      stream=None):
+                      workspace=None, split=True, stream=None):
+    """split=True passes a workspace (the given one, else a new one) so that
+    layers with few output tiles split their K sum over more CTAs."""
     osz = conv_output_size(cv)
     _act(x, (cv.batch,) + tuple(cv.size) + (cv.cin,), "input")
     shape = (cv.batch,) + osz + (cv.cout,)
@@ -685,8 +693,14 @@ def al_conv3d_forward(cv, x, packed_fwd, bias=None, relu=True, out_f32=False, ou
     _act(out, shape, "output", torch.float32 if out_f32 else torch.bfloat16)
     if bias is not None:
         _f32(bias, (cv.cout,), "bias")
+    ws, nbytes = None, 0
+    if split:
+        nbytes = conv_forward_workspace_bytes(cv)
+        if nbytes:
+            ws = _workspace(nbytes, x.device, workspace)
     _call("al_conv3d_forward", ctypes.byref(cv), _ptr(x), _ptr(packed_fwd), _ptr(bias),
-          int(bool(relu)), int(bool(out_f32)), _ptr(out), _stream(stream))
+          int(bool(relu)), int(bool(out_f32)), _ptr(out), _ptr(ws),
+          ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
     return out
 
 

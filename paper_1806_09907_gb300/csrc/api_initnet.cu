@@ -110,9 +110,17 @@ al_status al_conv3d_pack(const al_conv3d *cv, const float *weight, void *packed_
     return ok_launch(launch_conv_pack(l, weight, packed_fwd, packed_dgrad, St(stream)));
 }
 
+size_t al_conv3d_forward_workspace_bytes(const al_conv3d *cv)
+{
+    ConvLayer l;
+    if (check_conv(cv, &l) != AL_OK)
+        return 0;
+    return conv_fwd_ws_bytes(l);
+}
+
 al_status al_conv3d_forward(const al_conv3d *cv, const void *input, const void *packed_fwd,
                             const float *bias, int32_t relu, int32_t out_f32, void *output,
-                            al_stream stream)
+                            void *workspace, size_t workspace_bytes, al_stream stream)
 {
     ConvLayer l;
     al_status st = check_conv(cv, &l);
@@ -124,10 +132,15 @@ al_status al_conv3d_forward(const al_conv3d *cv, const void *input, const void *
                          conv_out_size(l.H, l.stride) * conv_out_size(l.W, l.stride);
     if (vout > kMaxRows)
         return AL_ERR_SHAPE;
-    if (!aligned16(input) || !aligned16(packed_fwd) || !aligned16(output) || !aligned16(bias))
+    if (!aligned16(input) || !aligned16(packed_fwd) || !aligned16(output) || !aligned16(bias) ||
+        !aligned16(workspace))
         return AL_ERR_ALIGN;
+    // a workspace too small for the split-K partials runs the layer unsplit
+    void *ws = workspace && workspace_bytes >= conv_fwd_ws_bytes(l) && conv_fwd_ws_bytes(l) > 0
+                   ? workspace
+                   : nullptr;
     return ok_launch(launch_conv_forward(l, input, packed_fwd, bias, relu ? 1 : 0,
-                                         out_f32 ? 1 : 0, output, St(stream)));
+                                         out_f32 ? 1 : 0, output, ws, St(stream)));
 }
 
 al_status al_conv3d_backward_data(const al_conv3d *cv, const void *grad_output,

@@ -87,6 +87,7 @@ struct ConvArgs {
     int rows;                    // FWD: output voxels; DGRAD: input voxels; WGRAD: output voxels
     int relu, out_f32, add_stride, add_off;
     int64_t act_elems, gout_elems;  // elements of act and gout (checked builds)
+    float *part;                 // FWD with split K: fp32 partials [class][rows][N]
     int classes;                 // DGRAD with stride 2: 8 parity classes; otherwise 1
     int cls_unit0[kMaxClasses + 1];  // first unit of each class; [classes] = units
     int cls_nst[kMaxClasses];        // K slices of a unit of each class
@@ -463,7 +464,7 @@ __device__ __forceinline__ void unit_begin(const ConvArgs &a, const Cursor &c, i
 template <int MODE>
 __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, const UnitState &st,
                                           uint8_t *A, uint8_t *B, int tid, const int *tapoff,
-                                          const int (*ctoff)[8])
+                                          const int (*ctoff)[8], int kslice0)
 {
     const uint32_t sA = (uint32_t)__cvta_generic_to_shared(A);
     if (MODE == FWD) {
@@ -479,7 +480,8 @@ __device__ __forceinline__ void fill_item(const ConvArgs &a, const Cursor &c, co
                     ok ? src + (st.rowoff + tapoff[t < 27 ? t : 0]) / 2 : src, ok);
             }
         } else {
-            int k = c.kk * kBK;
+            // with split K the unit's slices start at slice kslice0 of the layer
+            int k = (kslice0 + c.kk) * kBK;
             int t = k / a.cin, ci = k - t * a.cin;
 #pragma unroll
             for (int kc = 0; kc < 8; ++kc, k += 8) {
@@ -637,6 +639,14 @@ __device__ __forceinline__ void epilogue(const ConvArgs &a, const Cursor &c, uin
         tc_load16(lane_addr + (uint32_t)c0, v);
         if (!valid)
             continue;
+        if (MODE == FWD && a.part) {
+            // split K: this K partition's partial sums, reduced by k_fwd_reduce
+            float4 *o = reinterpret_cast<float4 *>(a.part + ((size_t)c.cls * a.rows + orow) * a.N + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            continue;
+        }
         if (MODE == FWD) {
             if (a.bias) {
 #pragma unroll
@@ -800,7 +810,8 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs a)
                           a.wpk + (size_t)(s_slice0[prod.cls] + prod.kk) * a.N * kBK,
                           (uint32_t)btile, bar_full + 8 * s);
             }
-            fill_item<MODE>(a, prod, ust, sA + s * kATile, B, tid, T.tapoff, T.ctoff);
+            fill_item<MODE>(a, prod, ust, sA + s * kATile, B, tid, T.tapoff, T.ctoff,
+                            MODE == FWD ? s_slice0[prod.cls] : 0);
             ++pit;
             if (++prod.kk >= prod.nst) {
                 prod.kk = 0;
@@ -953,6 +964,29 @@ __global__ void k_wgrad_reduce(const float *__restrict__ part, int splits, int m
             gw[(size_t)co * 27 * cin + m] = (float)tot;
         else if (gb)
             gb[co] = (float)tot;
+    }
+}
+
+// Split-K forward: out[row][n] = act(sum_p part[p][row][n] + bias[n]), the
+// partitions added in order; bf16 or fp32 output.
+__global__ void k_fwd_reduce(const float *__restrict__ part, int parts, int64_t rows, int N,
+                             const float *__restrict__ bias, int relu, int out_f32,
+                             void *__restrict__ out)
+{
+    const int64_t total = rows * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        for (int p = 0; p < parts; ++p)
+            v += part[(size_t)p * total + e];
+        if (bias)
+            v += __ldg(bias + (int)(e % N));
+        if (relu)
+            v = fmaxf(v, 0.0f);
+        if (out_f32)
+            static_cast<float *>(out)[e] = v;
+        else
+            static_cast<__nv_bfloat16 *>(out)[e] = __float2bfloat16_rn(v);
     }
 }
 
@@ -1158,8 +1192,39 @@ static void single_class(ConvArgs &a, int nst)
     a.cls_slice0[0] = 0;
 }
 
+// K partitions of the forward pass: split only when the tiles alone give
+// fewer than two per SM of a 152-SM GB300, at least two K slices per
+// partition, at most 8; a function of the shape only, so workspace sizes and
+// launches agree.
+int conv_fwd_splits(const ConvLayer &l)
+{
+    const int64_t rows = (int64_t)l.nb * conv_out_size(l.D, l.stride) *
+                         conv_out_size(l.H, l.stride) * conv_out_size(l.W, l.stride);
+    const int64_t tiles = (rows + 127) / 128;
+    const int nst = conv_slices(27 * l.cin);
+    if (tiles >= 2 * 152 || nst < 4)
+        return 1;
+    int64_t sp = (kTargetUnits + tiles - 1) / tiles;
+    if (sp > nst / 2)
+        sp = nst / 2;
+    if (sp > kMaxClasses)
+        sp = kMaxClasses;
+    return sp < 2 ? 1 : (int)sp;
+}
+
+size_t conv_fwd_ws_bytes(const ConvLayer &l)
+{
+    const int sp = conv_fwd_splits(l);
+    if (sp == 1)
+        return 0;
+    const int64_t rows = (int64_t)l.nb * conv_out_size(l.D, l.stride) *
+                         conv_out_size(l.H, l.stride) * conv_out_size(l.W, l.stride);
+    return (size_t)sp * rows * l.cout * sizeof(float);
+}
+
 cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *wpk,
-                                const float *bias, int relu, int out_f32, void *out, cudaStream_t s)
+                                const float *bias, int relu, int out_f32, void *out, void *ws,
+                                cudaStream_t s)
 {
     ConvArgs a = base_args(l);
     a.act_elems = (int64_t)l.nb * l.D * l.H * l.W * l.cin;
@@ -1170,8 +1235,25 @@ cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *
     a.N = l.cout;
     a.Kreal = 27 * l.cin;
     a.rows = l.nb * a.Do * a.Ho * a.Wo;
-    a.units = (a.rows + 127) / 128;
-    single_class(a, conv_slices(a.Kreal));
+    const int tiles = (a.rows + 127) / 128;
+    const int nst = conv_slices(a.Kreal);
+    const int sp = ws ? conv_fwd_splits(l) : 1;
+    if (sp == 1) {
+        a.units = tiles;
+        single_class(a, nst);
+    } else {
+        // K partitions as classes over the same tiles: partition p has the
+        // slices [p nst / sp, (p + 1) nst / sp)
+        a.part = static_cast<float *>(ws);
+        a.classes = sp;
+        for (int p = 0; p < sp; ++p) {
+            a.cls_unit0[p] = p * tiles;
+            a.cls_slice0[p] = p * nst / sp;
+            a.cls_nst[p] = (p + 1) * nst / sp - p * nst / sp;
+        }
+        a.cls_unit0[sp] = sp * tiles;
+        a.units = sp * tiles;
+    }
     a.relu = relu;
     a.out_f32 = out_f32;
     a.idesc = make_idesc(a.N, false);
@@ -1180,8 +1262,16 @@ cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *
     cudaError_t e = grid_for<FWD>(a.N, a.units, &grid);
     if (e != cudaSuccess)
         return e;
-    ProfScope ps(s, "k_conv_fwd");
-    k_conv<FWD><<<grid, kThreads, conv_smem_bytes(a.N), s>>>(a);
+    {
+        ProfScope ps(s, "k_conv_fwd");
+        k_conv<FWD><<<grid, kThreads, conv_smem_bytes(a.N), s>>>(a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess || sp == 1)
+        return e;
+    ProfScope ps(s, "k_fwd_reduce");
+    k_fwd_reduce<<<blocks_for((int64_t)a.rows * a.N, 256), 256, 0, s>>>(
+        a.part, sp, a.rows, a.N, bias, relu, out_f32, out);
     return cudaGetLastError();
 }
 

@@ -148,8 +148,11 @@ void conv_wgrad_plan(const ConvLayer &l, int *mtiles, int *splits, int *kper);
 size_t conv_wgrad_ws_bytes(const ConvLayer &l);
 cudaError_t launch_conv_pack(const ConvLayer &l, const float *w, void *fwd, void *dgrad,
                              cudaStream_t s);
+int conv_fwd_splits(const ConvLayer &l);
+size_t conv_fwd_ws_bytes(const ConvLayer &l);
+// ws (nullable, conv_fwd_ws_bytes): split-K partials; NULL runs unsplit.
 cudaError_t launch_conv_forward(const ConvLayer &l, const void *in, const void *wpk,
-                                const float *bias, int relu, int out_f32, void *out,
+                                const float *bias, int relu, int out_f32, void *out, void *ws,
                                 cudaStream_t s);
 cudaError_t launch_conv_dgrad(const ConvLayer &l, const void *gout, const void *wpk,
                               const void *mask, const void *addend, int add_stride, int add_off,

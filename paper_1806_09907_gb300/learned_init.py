@@ -83,6 +83,9 @@ class InitNet:
         self.packed = [None] * len(LAYERS)
         self.wspaces = [torch.empty(max(airgb.conv_wgrad_workspace_bytes(cv), 256),
                                     dtype=torch.uint8, device=self.device) for cv in self.convs]
+        # split-K partials of the forward layers that have few output tiles
+        self.fspaces = [torch.empty(max(airgb.conv_forward_workspace_bytes(cv), 256),
+                                    dtype=torch.uint8, device=self.device) for cv in self.convs]
         self.acts = {}
         self.pack()
 
@@ -112,15 +115,19 @@ class InitNet:
         a = A["x"]
         for k, name in enumerate(("e1", "e2", "e3", "e4")):
             a = airgb.al_conv3d_forward(self.convs[k], a, self.packed[k][0], self.bias(k),
-                                        relu=True, out=A.get(name), stream=stream)
+                                        relu=True, out=A.get(name), workspace=self.fspaces[k],
+                                        stream=stream)
             A[name] = a
         A["cat"] = airgb.al_initnet_upcat(A["e4"], A["e3"], out=A.get("cat"), stream=stream)
         A["d1"] = airgb.al_conv3d_forward(self.convs[4], A["cat"], self.packed[4][0], self.bias(4),
-                                          relu=True, out=A.get("d1"), stream=stream)
+                                          relu=True, out=A.get("d1"), workspace=self.fspaces[4],
+                                          stream=stream)
         A["d2"] = airgb.al_conv3d_forward(self.convs[5], A["d1"], self.packed[5][0], self.bias(5),
-                                          relu=True, out=A.get("d2"), stream=stream)
+                                          relu=True, out=A.get("d2"), workspace=self.fspaces[5],
+                                          stream=stream)
         A["h"] = airgb.al_conv3d_forward(self.convs[6], A["d2"], self.packed[6][0], self.bias(6),
-                                         relu=False, out_f32=True, out=A.get("h"), stream=stream)
+                                         relu=False, out_f32=True, out=A.get("h"),
+                                         workspace=self.fspaces[6], stream=stream)
         return airgb.al_initnet_head_to_ctrl(self.shape, A["h"], out=out, stream=stream)
 
     def backward(self, grad_ctrl, stream=None):

@@ -248,14 +248,20 @@ def test_conv_layer_sizes(lib):
     assert lib.al_conv3d_packed_bytes(ctypes.byref(_conv(stride=1)), 1) == 14 * 16 * 64 * 2
     assert lib.al_conv3d_packed_bytes(ctypes.byref(_conv(cin=2)), 1) == 0  # no dgrad for 2
     assert lib.al_conv3d_backward_weight_workspace_bytes(ctypes.byref(cv)) > 0
+    # split K only for layers with few output tiles and enough K slices
+    few = _conv(batch=1, size=(9, 10, 11), cin=112, cout=48, stride=1)  # 8 tiles, 48 slices
+    assert lib.al_conv3d_forward_workspace_bytes(ctypes.byref(few)) == 8 * 990 * 48 * 4
+    many = _conv(batch=16, size=(128, 128, 128), cin=2, cout=16, stride=2)
+    assert lib.al_conv3d_forward_workspace_bytes(ctypes.byref(many)) == 0
 
 
 def test_conv_calls_reject_before_launching(lib):
     cv = _conv()
     p = ctypes.byref(cv)
     a, b = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10004)
-    assert lib.al_conv3d_forward(p, None, a, None, 1, 0, a, None) == 1
-    assert lib.al_conv3d_forward(p, a, a, None, 1, 0, b, None) == 3
+    assert lib.al_conv3d_forward(p, None, a, None, 1, 0, a, None, 0, None) == 1
+    assert lib.al_conv3d_forward(p, a, a, None, 1, 0, b, None, 0, None) == 3
+    assert lib.al_conv3d_forward(p, a, a, None, 1, 0, a, b, 1 << 20, None) == 3
     assert lib.al_conv3d_pack(p, a, None, None, None) == 1
     assert lib.al_conv3d_pack(ctypes.byref(_conv(cin=2)), a, None, a, None) == 7
     # the input adjoint needs cin a multiple of 16

@@ -380,3 +380,27 @@ def test_short_training_lowers_the_loss():
     first, last = res.losses[:20].mean(), res.losses[-20:].mean()
     assert np.all(np.isfinite(res.losses)) and last < 0.95 * first, (first, last)
     assert airgb.al_get_device_error() == 0
+
+
+@pytest.mark.parametrize("nb,dims,cin,cout,stride", [(1, (9, 10, 11), 112, 48, 1),
+                                                     (1, (8, 8, 8), 48, 64, 2),
+                                                     (1, (16, 16, 16), 32, 48, 2)])
+def test_conv_forward_split_k(nb, dims, cin, cout, stride):
+    """Layers with few output tiles split their K sum over up to 8 CTAs; the
+    result agrees with the unsplit launch within the fp32 accumulation bound
+    (both are sums of the same products in different orders)."""
+    x, w32, b = _layer(9, nb, dims, cin, cout)
+    cv = airgb.make_conv(nb, dims, cin, cout, stride)
+    assert airgb.conv_forward_workspace_bytes(cv) > 0
+    pf, _ = airgb.al_conv3d_pack(cv, torch.from_numpy(w32).to(DEV), True, False)
+    xb, bd = _to_dev_bf16(x), torch.from_numpy(b).to(DEV)
+    ys = _np(airgb.al_conv3d_forward(cv, xb, pf, bd, relu=False, out_f32=True, split=True))
+    yu = _np(airgb.al_conv3d_forward(cv, xb, pf, bd, relu=False, out_f32=True, split=False))
+    ys2 = _np(airgb.al_conv3d_forward(cv, xb, pf, bd, relu=False, out_f32=True, split=True))
+    assert np.array_equal(ys, ys2), "split-K forward not deterministic"
+    wq = _bf16(w32)
+    S = onet.conv3d(np.abs(x), np.abs(wq), np.abs(b.astype(np.float64)), stride, False)
+    ref = onet.conv3d(x, wq, b.astype(np.float64), stride, False)
+    n = 27 * cin
+    assert np.all(np.abs(ys - ref) <= n * U * S)
+    assert np.all(np.abs(ys - yu) <= 2 * n * U * S)
