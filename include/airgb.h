@@ -499,7 +499,8 @@ al_status al_adam_flat(const al_adam_params *p, int64_t n, int64_t *step, float 
 
 /* Training volumes: out[v][z][y][x] = sum_b a_b exp(-|x - mu_b|^2/(2 sigma_b^2))
  * for `count` volumes of size (z, y, x), blob table[v][b] = {mu_x, mu_y,
- * mu_z, sigma, a} (fp32, n_blobs per volume). */
+ * mu_z, sigma, a} (fp32, n_blobs per volume; sigma > 0). Terms of blobs more
+ * than 6 sigma from a voxel's 8^3 brick are dropped (each below 1.6e-8 a). */
 al_status al_render_blobs(const int64_t *size, int32_t count, int32_t n_blobs, const float *table,
                           float *out, al_stream stream);
 
