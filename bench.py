@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--learned-pairs", type=int, default=20000,
                    help="training pairs of the learned initialisation (0: skip it)")
-    p.add_argument("--learned-test", type=int, default=4,
+    p.add_argument("--learned-test", type=int, default=8,
                    help="held-out pairs of the time-to-MSE comparison")
     p.add_argument("--no-registration", action="store_true",
                    help="skip the optimisation-loop timings (registration object)")
