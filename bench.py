@@ -462,13 +462,40 @@ def learned_init_runs(dev, pairs, n_test):
     compare the plain optimiser (200 Adam iterations from zero) with the
     network's prediction refined by the same optimiser until it reaches the
     plain method's final MSE."""
-    from paper_1806_09907_gb300 import learned_init
+    from paper_1806_09907_gb300 import airgb, learned_init
 
     shape, batch = (128, 128, 128), 16
     net = learned_init.InitNet(shape, batch, dev, seed=1806)
     # warm-up: kernel attributes and one step of every launch
     learned_init.train(learned_init.InitNet(shape, batch, dev, seed=1), pairs=batch)
     tr = learned_init.train(net, pairs=pairs, lr=1e-3, sigma=4.0, seed=0)
+    # one training step's kernels (library event timing, a separate network)
+    prof = learned_init.InitNet(shape, batch, dev, seed=7)
+    learned_init.train(prof, pairs=batch, seed=5)
+    airgb.profile_reset()
+    airgb.profile_enable(True)
+    n_prof = 5
+    learned_init.train(prof, pairs=n_prof * batch, seed=5)
+    step_kernels = {k: {"us_per_step": 1000.0 * t / n_prof, "launches_per_step": n // n_prof}
+                    for k, (t, n) in airgb.profile_collect().items()}
+    airgb.profile_enable(False)
+    airgb.profile_reset()
+    # algorithmic tensor work of the layers per step: forward, input adjoint
+    # (not for the first layer) and weight adjoint, 2 flop per multiply-add
+    conv_flop = 0.0
+    for k, cv in enumerate(prof.convs):
+        cin, cout = learned_init.LAYERS[k][0], learned_init.LAYERS[k][2]
+        osz = airgb.conv_output_size(cv)
+        per_pass = 2.0 * batch * np.prod(osz) * cout * 27 * cin
+        conv_flop += per_pass * (3 if k > 0 else 2)
+    conv_us = sum(v["us_per_step"] for k, v in step_kernels.items() if k.startswith("k_conv"))
+    peaks, psrc = measured_peaks()
+    peak = peaks.get("bf16_tflops")
+    tensor = {"flop_per_step": conv_flop, "conv_us_per_step": conv_us,
+              "achieved_tflops": conv_flop / conv_us / 1e6 if conv_us else None,
+              "peak_tflops": peak, "unit": "TFLOP/s",
+              "peak_source": f"bf16 dense, burst ({psrc})",
+              "frac": (conv_flop / conv_us / 1e6 / peak) if (conv_us and peak) else None}
     one = learned_init.InitNet(shape, 1, dev, seed=1806)
     one.params.copy_(net.params)
     one.pack()
@@ -492,6 +519,8 @@ def learned_init_runs(dev, pairs, n_test):
         "train": {"pairs": tr.pairs, "steps": tr.steps, "batch": batch, "seconds": tr.seconds,
                   "ms_per_step": 1000.0 * tr.seconds / tr.steps,
                   "loss_first_50": float(np.mean(L[:50])), "loss_last_50": float(np.mean(L[-50:]))},
+        "step_kernels": step_kernels,
+        "conv_tensor": tensor,
         "test_pairs": n_test,
         "reached_plain_mse": len(ok),
         "fallbacks": int(sum(r.fallback for r in reports)),

@@ -938,22 +938,39 @@ __global__ void k_pack_weights(const float *__restrict__ w, int cin, int cout, i
 }
 
 // g_w[co][t][ci] and g_b[co] from the wgrad partials [split][mrows][N]: one
-// block per M row m = t cin + ci (m = 27 cin is the bias row). Thread j adds
-// the splits j / N, j / N + G, ... of column co = j % N (G = blockDim / N
-// groups, coalesced reads of the N columns of a split), in order and in
-// double; the G group sums are then added in order by one thread per
-// column, so the result does not depend on timing.
-__global__ void k_wgrad_reduce(const float *__restrict__ part, int splits, int mrows, int N,
-                               int cin, int cout, float *__restrict__ gw, float *__restrict__ gb)
+// block of kReduceThreads per M row m = t cin + ci (m = 27 cin is the bias
+// row). Thread j adds the splits j / N, j / N + G, ... of column co = j % N
+// (G = kReduceThreads / N groups, coalesced reads of the N columns of a
+// split), in order and in double; the G group sums are then added in order
+// by one thread per column, so the result does not depend on timing.
+constexpr int kReduceThreads = 512;
+
+__global__ void __launch_bounds__(kReduceThreads)
+    k_wgrad_reduce(const float *__restrict__ part, int splits, int mrows, int N, int cin,
+                   int cout, float *__restrict__ gw, float *__restrict__ gb)
 {
-    __shared__ double red[256];
+    __shared__ double red[kReduceThreads];
     const int m = blockIdx.x;
-    const int groups = blockDim.x / N;
+    const int groups = kReduceThreads / N;
     const int co = threadIdx.x % N, grp = threadIdx.x / N;
     double acc = 0.0;
-    if (grp < groups)
-        for (int sp = grp; sp < splits; sp += groups)
-            acc += (double)part[((size_t)sp * mrows + m) * N + co];
+    if (grp < groups) {
+        const float *p = part + (size_t)m * N + co;
+        const size_t step = (size_t)mrows * N;
+        int sp = grp;
+        // four independent loads in flight per thread
+        for (; sp + 3 * groups < splits; sp += 4 * groups) {
+            const float a = p[(size_t)sp * step], b = p[(size_t)(sp + groups) * step],
+                        c = p[(size_t)(sp + 2 * groups) * step],
+                        d = p[(size_t)(sp + 3 * groups) * step];
+            acc += (double)a;
+            acc += (double)b;
+            acc += (double)c;
+            acc += (double)d;
+        }
+        for (; sp < splits; sp += groups)
+            acc += (double)p[(size_t)sp * step];
+    }
     red[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < N && co < cout) {
@@ -1341,8 +1358,8 @@ cudaError_t launch_conv_wgrad(const ConvLayer &l, const void *in, const void *go
         return e;
     ProfScope ps(s, "k_wgrad_reduce");
     // one block per M row (27 cin weights rows and the bias row)
-    k_wgrad_reduce<<<27 * l.cin + 1, 256, 0, s>>>(static_cast<const float *>(ws), sp, mt * 128,
-                                                  a.N, l.cin, l.cout, gw, gb);
+    k_wgrad_reduce<<<27 * l.cin + 1, kReduceThreads, 0, s>>>(static_cast<const float *>(ws), sp,
+                                                             mt * 128, a.N, l.cin, l.cout, gw, gb);
     return cudaGetLastError();
 }
 
