@@ -404,3 +404,18 @@ def test_conv_forward_split_k(nb, dims, cin, cout, stride):
     n = 27 * cin
     assert np.all(np.abs(ys - ref) <= n * U * S)
     assert np.all(np.abs(ys - yu) <= 2 * n * U * S)
+
+
+def test_inference_graph_replay_equals_eager():
+    """One-pair inference replayed from a CUDA graph (split-K layers
+    included) gives the eager forward's coefficients bit for bit."""
+    shape = (40, 33, 48)
+    net = learned_init.InitNet(shape, 1, DEV, seed=4, head_scale=1.0)
+    src = learned_init.PairSource(shape, 1, 3.0, seed=2, device=DEV)
+    F, M, _ = src.make(0)
+    lat = (3,) + airgb.lattice_shape(shape, 8)
+    eager = net.forward(F, M, out=torch.empty((1,) + lat, device=DEV)).clone()
+    out = torch.empty(lat, device=DEV)
+    ms = learned_init.inference_ms(net, F[0].clone(), M[0].clone(), out)
+    torch.cuda.synchronize()
+    assert ms > 0 and torch.equal(out, eager[0])
