@@ -7,7 +7,8 @@
 // its moment sums leave it. k_ctrl then sums, for every control point, the
 // partials of the (at most 2 per axis) bricks that touch it in a fixed
 // order, so the result is deterministic without atomics. The regulariser is
-// evaluated on the control lattice in Gram form (k_gram):
+// evaluated on the control lattice in Gram form, by extra blocks of the
+// first k_fused launch (Gram tiles):
 //   R = (1/|X|) sum_i c_i^T (Gz(x)Gy(x)Hx + Gz(x)Hy(x)Gx + Hz(x)Gy(x)Gx) c_i,
 // G = B^T B and H = (DB)^T (DB) per axis (B the sampled 1D B-spline matrix,
 // D the forward difference), which equals the voxel-grid definition exactly.
@@ -407,20 +408,6 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
     }
 }
 
-template <int D, int DELTA, int MODE>
-__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
-                                  (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
-                                                                                            : 1)
-    k_fused(Grid g, Lattice L, const float *__restrict__ F, const float *__restrict__ M,
-            const float *__restrict__ c, const float *__restrict__ gw_in,
-            float *__restrict__ W_out, uint8_t *__restrict__ m_out, float *__restrict__ G_io,
-            float *__restrict__ bpart, double *__restrict__ mpart)
-{
-    const int brick = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    fused_brick<D, DELTA, MODE>(g, L, F, M, c, gw_in, W_out, m_out, G_io, bpart, mpart,
-                                blockIdx.x, blockIdx.y, blockIdx.z, brick);
-}
-
 // ---------------------------------------------------------------------------
 // Gram-form diffusion regulariser on the control lattice.
 // Band entries of G = B^T B and H = (DB)^T (DB) along one axis of size N:
@@ -461,7 +448,7 @@ __device__ void band_entry(const Lattice &L, int N, int n, int j, int o, float &
     }
 }
 
-constexpr int kGramT3 = 8, kGramT2 = 16, kGramThreads = 256;
+constexpr int kGramT3 = 8, kGramT2 = 16;
 
 // One tile (tile x, y, z) of component i of dR/dc on the lattice; the
 // tile's share of R (before the 1/|X|) goes to *rpart. Every thread of the
@@ -558,18 +545,6 @@ __device__ __forceinline__ void gram3_tile(const Grid &g, const Lattice &L,
         *rpart = acc[0];
 }
 
-__global__ void __launch_bounds__(kGramThreads)
-    k_gram3(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
-            double *__restrict__ rpart)
-{
-    // one component per block: blockIdx.z = component * (z tiles) + z tile
-    const int tz = (L.nz + kGramT3 - 1) / kGramT3, i = (int)blockIdx.z / tz;
-    extern __shared__ float gsm[];
-    gram3_tile(g, L, c, gscale, gR, blockIdx.x, blockIdx.y, (int)blockIdx.z - i * tz, i,
-               rpart + (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x, gsm);
-}
-
-
 __device__ __forceinline__ void gram2_tile(const Grid &g, const Lattice &L,
                                            const float *__restrict__ c, float gscale,
                                            float *__restrict__ gR, int tile_x, int tile_y, int i,
@@ -637,18 +612,6 @@ __device__ __forceinline__ void gram2_tile(const Grid &g, const Lattice &L,
     if (tid == 0)
         *rpart = acc[0];
 }
-
-__global__ void __launch_bounds__(kGramThreads)
-    k_gram2(Grid g, Lattice L, const float *__restrict__ c, float gscale, float *__restrict__ gR,
-            double *__restrict__ rpart)
-{
-    // one component per block: blockIdx.y = component * (y tiles) + y tile
-    const int ty = (L.ny + kGramT2 - 1) / kGramT2, i = (int)blockIdx.y / ty;
-    extern __shared__ float gsm[];
-    gram2_tile(g, L, c, gscale, gR, blockIdx.x, (int)blockIdx.y - i * ty, i,
-               rpart + blockIdx.y * gridDim.x + blockIdx.x, gsm);
-}
-
 
 // ---------------------------------------------------------------------------
 // Load of data that other blocks of the same launch wrote (CG: through L2,
@@ -887,27 +850,81 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
     return o;
 }
 
+// Gram tiles run by the blocks after the bricks of a k_fused launch (none
+// when ngram = 0): the regulariser needs only c, so its tiles share the
+// launch of the first brick pass instead of a launch of their own. Placed
+// after the bricks they fill the last wave; placed first they delayed the
+// bricks' streaming loads and measured slower.
+struct GramBlocks {
+    float *gR;
+    double *rpart;
+    float gscale;
+    int gbx, gby, nbricks;     // brick grid (x, y) and number of bricks
+    int gtx, gty, gtz, ngram;  // Gram tiles per axis (gtz = 1 in 2D), total over components
+};
+
+template <int D, int DELTA, int MODE>
+__global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
+                                  (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
+                                                                                            : 1)
+    k_fused(Grid g, Lattice L, const float *__restrict__ F, const float *__restrict__ M,
+            const float *__restrict__ c, const float *__restrict__ gw_in,
+            float *__restrict__ W_out, uint8_t *__restrict__ m_out, float *__restrict__ G_io,
+            float *__restrict__ bpart, double *__restrict__ mpart, GramBlocks gb)
+{
+    const int b = blockIdx.x;
+    if (b < gb.nbricks) {
+        const int bx = b % gb.gbx, by = (b / gb.gbx) % gb.gby, bz = b / (gb.gbx * gb.gby);
+        fused_brick<D, DELTA, MODE>(g, L, F, M, c, gw_in, W_out, m_out, G_io, bpart, mpart, bx,
+                                    by, bz, b);
+        return;
+    }
+    // tile index w = ((component * gtz + tz) * gty + ty) * gtx + tx, its R partial at rpart[w]
+    const int w = b - gb.nbricks;
+    const int tx = w % gb.gtx, r = w / gb.gtx, ty = r % gb.gty, r2 = r / gb.gty;
+    const int tz = r2 % gb.gtz, comp = r2 / gb.gtz;
+    extern __shared__ float gtile_sm[];
+    if constexpr (D == 3)
+        gram3_tile(g, L, c, gb.gscale, gb.gR, tx, ty, tz, comp, gb.rpart + w, gtile_sm);
+    else
+        gram2_tile(g, L, c, gb.gscale, gb.gR, tx, ty, comp, gb.rpart + w, gtile_sm);
+}
+
 template <int D, int DELTA, int MODE>
 cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay, char *ws,
                              const float *F, const float *M, const float *c, const float *gw,
-                             float *Wo, uint8_t *mo, float *G, cudaStream_t s)
+                             float *Wo, uint8_t *mo, float *G, bool with_gram, cudaStream_t s)
 {
     using C = FCfg<D, DELTA, MODE>;
-    dim3 grid(lay.gbx, lay.gby, lay.gbz);
+    GramBlocks gb{};
+    gb.gR = (float *)(ws + lay.gR);
+    gb.rpart = (double *)(ws + lay.rpart);
+    gb.gscale = (float)(2.0 / (double)g.nv);
+    gb.gbx = lay.gbx;
+    gb.gby = lay.gby;
+    gb.nbricks = lay.nbricks;
+    const int T = (D == 3) ? kGramT3 : kGramT2;
+    gb.gtx = (L.nx + T - 1) / T;
+    gb.gty = (L.ny + T - 1) / T;
+    gb.gtz = (D == 3) ? (L.nz + T - 1) / T : 1;
+    gb.ngram = with_gram ? lay.ngram : 0;
+    const size_t gsm = (size_t)((D == 3) ? kGram3Floats : kGram2Floats) * sizeof(float);
+    const size_t dyn = (with_gram && gsm > C::dyn_smem) ? gsm : C::dyn_smem;
     ProfScope ps(s, MODE == MODE_MSE   ? "k_fused_mse"
                     : MODE == MODE_NCC ? "k_fused_ncc"
                     : MODE == MODE_FWD ? "k_fused_fwd"
                                        : "k_fused_gw");
-    if (C::dyn_smem > 0) {  // static + dynamic may pass 48 KB: always opt in
+    if (dyn > 0) {  // static + dynamic may pass 48 KB: always opt in
+        const size_t most = gsm > C::dyn_smem ? gsm : C::dyn_smem;
         cudaError_t e = cudaFuncSetAttribute(k_fused<D, DELTA, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::dyn_smem);
+                                             (int)most);
         if (e != cudaSuccess)
             return e;
     }
-    k_fused<D, DELTA, MODE><<<grid, C::THREADS, C::dyn_smem, s>>>(
-        g, L, F, M, c, gw, Wo, mo, G, (float *)(ws + lay.bpart),
-        (double *)(ws + lay.mpart));
+    k_fused<D, DELTA, MODE><<<lay.nbricks + gb.ngram, C::THREADS, dyn, s>>>(
+        g, L, F, M, c, gw, Wo, mo, G, (float *)(ws + lay.bpart), (double *)(ws + lay.mpart),
+        gb);
     return cudaGetLastError();
 }
 
@@ -919,35 +936,23 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     const Layout lay = make_layout(g, L, kind, window);
     double *rpart = (double *)(ws + lay.rpart);
     float *gR = (float *)(ws + lay.gR);
-    const float gscale = (float)(2.0 / (double)g.nv);
     cudaError_t e;
-    prof_begin(s, "k_gram");
-    if (D == 3) {
-        dim3 gg((L.nx + kGramT3 - 1) / kGramT3, (L.ny + kGramT3 - 1) / kGramT3,
-                3 * ((L.nz + kGramT3 - 1) / kGramT3));
-        k_gram3<<<gg, kGramThreads, kGram3Floats * sizeof(float), s>>>(g, L, c, gscale, gR, rpart);
-    } else {
-        dim3 gg((L.nx + kGramT2 - 1) / kGramT2, 2 * ((L.ny + kGramT2 - 1) / kGramT2));
-        k_gram2<<<gg, kGramThreads, kGram2Floats * sizeof(float), s>>>(g, L, c, gscale, gR, rpart);
-    }
-    prof_end(s);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
     int mode;
     if (kind == 0) {
         mode = MODE_MSE;
         e = run_fused_kernel<D, DELTA, MODE_MSE>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr,
-                                                 nullptr, s);
+                                                 nullptr, true, s);
     } else if (kind == 1) {
         mode = MODE_NCC;
         e = run_fused_kernel<D, DELTA, MODE_NCC>(g, L, lay, ws, F, M, c, nullptr, nullptr, nullptr,
-                                                 nullptr, s);
+                                                 nullptr, true, s);
     } else {
         mode = 2;
         float *Wb = (float *)(ws + lay.Wb), *gb = (float *)(ws + lay.gb);
         uint8_t *mb = (uint8_t *)(ws + lay.mb);
         float *Gb = gc ? (float *)(ws + lay.Gb) : nullptr;
-        e = run_fused_kernel<D, DELTA, MODE_FWD>(g, L, lay, ws, F, M, c, nullptr, Wb, mb, Gb, s);
+        e = run_fused_kernel<D, DELTA, MODE_FWD>(g, L, lay, ws, F, M, c, nullptr, Wb, mb, Gb, true,
+                                                 s);
         if (e != cudaSuccess)
             return e;
         e = launch_lcc(g, window, eps, F, Wb, mb, gc ? gb : nullptr, (double *)(ws + lay.lpart),
@@ -956,7 +961,7 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
             return e;
         if (gc)
             e = run_fused_kernel<D, DELTA, MODE_GW>(g, L, lay, ws, F, M, c, gb, nullptr, nullptr,
-                                                    Gb, s);
+                                                    Gb, false, s);
     }
     if (e != cudaSuccess)
         return e;
@@ -998,7 +1003,7 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
 // before any phase B item, by a block that is running, so a wait only ever
 // waits for running blocks; it is bounded anyway (BatchStep::spin_limit
 // polls, then AL_ERR_TIMEOUT in the error word and the chunk is skipped).
-// The per-item arithmetic is that of k_fused, k_gram and k_ctrl + k_adam, so
+// The per-item arithmetic is that of k_fused (bricks, Gram tiles) and k_ctrl + k_adam, so
 // a problem's coefficients follow the single-problem path bit for bit.
 template <int DELTA>
 struct BCfg {

@@ -71,22 +71,10 @@ struct LccB {
 // Distance in floats between the planes a', b, c of the LCC coefficients.
 __host__ __device__ inline int64_t lcc_plane(int nv) { return ((int64_t)nv * 4 + 255) / 256 * 64; }
 
-// Merge of a partial window (sums t1f,t1w,t2f,t2w,tfw relative to its centre
-// (af, aw), n points) into sums relative to (bf, bw).
+// Window sums (of F, W, F^2, W^2, FW) relative to a reference (bf, bw).
 struct Sums {
     float s1f, s1w, s2f, s2w, sfw;
 };
-
-__device__ __forceinline__ void merge(Sums &S, float t1f, float t1w, float t2f, float t2w,
-                                      float tfw, float af, float aw, float bf, float bw, float n)
-{
-    const float d = af - bf, e = aw - bw;
-    S.s1f += fmaf(n, d, t1f);
-    S.s1w += fmaf(n, e, t1w);
-    S.s2f += fmaf(d, fmaf(n, d, 2.0f * t1f), t2f);
-    S.s2w += fmaf(e, fmaf(n, e, 2.0f * t1w), t2w);
-    S.sfw += fmaf(d, fmaf(n, e, t1w), fmaf(e, t1f, tfw));
-}
 
 // The sums of a partial window (relative to its centre (af, aw), n points)
 // converted to the reference (bf, bw); returned, not accumulated.
