@@ -279,7 +279,7 @@ def run_reference(args, shape):
                    "similarity": f"{args.sim}{WINDOW if args.sim == 'lcc' else ''}",
                    "lambda": LAMBDA, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "cpu": cpu_model(),
+                         "cpu": cpu_model(), "host_cores": cpu_cores(),
                          "sample": f"one FP64 oracle forward+adjoint per step on a "
                                    f"{shape[2]}x{shape[1]}x{depth} z-slab, time scaled by "
                                    f"voxel count to the full volume"},
@@ -660,6 +660,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         v, t, depth = oracle_sample(F, M, c, args.sim, args.cpu_budget)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
+               "host_cores": cpu_cores(),
                "sample": f"one FP64 oracle forward+adjoint on a {shape[2]}x{shape[1]}x{depth} "
                          f"z-slab of the workload ({t:.1f} s), scaled by voxel count"}
     reg = None
