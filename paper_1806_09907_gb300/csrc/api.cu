@@ -712,9 +712,9 @@ al_status al_get_device_error(al_stream stream)
         if (cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)) != cudaSuccess)
             return AL_ERR_CUDA;
     }
-    const int others[4] = {conv_device_error(true), unit_error_basic(true),
-                           unit_error_fused(true), unit_error_conv(true)};
-    for (int k = 0; k < 4; ++k) {
+    const int others[5] = {conv_device_error(true), unit_error_basic(true),
+                           unit_error_fused(true), unit_error_conv(true), unit_error_lcc(true)};
+    for (int k = 0; k < 5; ++k) {
         if (others[k] < 0)
             return AL_ERR_CUDA;
         if (h == 0)

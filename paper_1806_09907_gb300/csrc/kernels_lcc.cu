@@ -24,8 +24,16 @@
 // are taken directly from the ring (relative to the column's centre value),
 // then merged along x and along y with the conversion above. It writes
 // (a', b, c) per voxel and per-block {sum rho, count} partials.
-// k_lcc_grad: plain box sums of (a', b, c) (stored as float4 per voxel; z
-// through a register ring of x/y sums) and dS/dW * |X_m| on the mask.
+// k_lcc_grad: plain box sums of (a', b, c) (three planes; z through a
+// register ring of x/y sums) and dS/dW * |X_m| on the mask. When the row
+// pitch allows a tensor map (X a multiple of 4), k_lcc_grad_tma stages the
+// coefficient slices with TMA tile loads into a ring of shared-memory slots
+// instead of register prefetches; both give the same sums in the same order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "launch.h"
 #include "profile.h"
 
@@ -65,6 +73,30 @@ struct LccB {
     static constexpr int BUF = 3 * NL + 3 * NX;
     static constexpr size_t smem = (size_t)2 * BUF * sizeof(float);
     static_assert(LX % 2 == 0 && NL % 2 == 0 && NX % 2 == 0, "rows are read as float2");
+    static_assert(NX / 2 <= THREADS, "one x pair per thread");
+};
+
+// k_lcc_grad_tma: the tile of LccB with its coefficient slices staged by
+// one 4D TMA tile load each (x, y, z, plane). A TMA row must start on a
+// 16-byte boundary, so the staged row runs from x0 - 4 to x0 + 35 (40
+// floats) and column x0 - R sits at XOFF = 4 - R. Out-of-range elements of
+// the box arrive as zeros, as the zero padding of the box sums wants.
+template <int D, int R>
+struct LccT {
+    static constexpr int TX = 32, TY = 16;
+    static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
+    static constexpr int LXT = 40, XOFF = 4 - R, LY = TY + 2 * R;
+    static constexpr int NX = LY * TX, NC = TX * TY;
+    static constexpr int ZC = (D == 3) ? 24 : 1;
+    static constexpr int THREADS = NC;
+    static constexpr int NS = 4;                 // slices in flight
+    static constexpr int PLANE = LY * LXT;       // floats of one staged plane
+    static constexpr uint32_t BOX_BYTES = 3u * PLANE * 4u;
+    static constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128);
+    static constexpr int oX = NS * STAGE;        // two buffers of x sums, 3 planes of NX
+    static constexpr int oBar = oX + 2 * 3 * NX * 4;
+    static constexpr size_t smem = (size_t)oBar + NS * 8 + 128;  // + base alignment slack
+    static_assert(R >= 1 && R <= 4 && XOFF + TX + 2 * R <= LXT, "staged row covers the halo");
     static_assert(NX / 2 <= THREADS, "one x pair per thread");
 };
 
@@ -555,6 +587,245 @@ __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
                                 core, zi_end);
 }
 
+// ---- TMA-staged variant ----------------------------------------------------
+constexpr int kErrTimeout = 6;  // AL_ERR_TIMEOUT
+
+__device__ __forceinline__ uint32_t lsm_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool lbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with this parity, for about one second of
+// %globaltimer at most; false if it did not complete.
+__device__ __noinline__ bool lbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (lbar_try_wait(bar, parity))
+        return true;
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!lbar_try_wait(bar, parity)) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull)
+            return false;
+    }
+    return true;
+}
+
+// Issue the TMA load of slice k of the block's z range into ring slot k % NS.
+template <int D, int R>
+__device__ __forceinline__ void lcc_tma_issue(const CUtensorMap *map, uint32_t sbase, int k,
+                                              int x0, int y0, int z)
+{
+    using C = LccT<D, R>;
+    const int slot = k % C::NS;
+    const uint32_t dst = sbase + slot * C::STAGE, bar = sbase + C::oBar + 8 * slot;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(C::BOX_BYTES)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x0 - 4), "r"(y0 - R), "r"(z), "r"(0),
+        "r"(bar)
+        : "memory");
+}
+
+// One slice step of k_lcc_grad_tma (slice k of the block's range, zi its z).
+// Returns false when the slice's TMA load did not arrive in time (then every
+// thread of the block returns false at the same step).
+template <int D, int R, int P>
+__device__ __forceinline__ bool lcc_grad_tma_step(const CUtensorMap *map, const Grid &g, int k,
+                                                  int zs, int zc0, int x0, int y0, int nslices,
+                                                  const float *__restrict__ F,
+                                                  const float *__restrict__ W,
+                                                  const uint8_t *__restrict__ m,
+                                                  float *__restrict__ gout, unsigned char *sm,
+                                                  float3 (&ring)[LccT<D, R>::NR], CoreVox &core,
+                                                  int &kfail)
+{
+    using C = LccT<D, R>;
+    constexpr int NX = C::NX, TX = C::TX, NR = C::NR, W1 = C::W1, LXT = C::LXT;
+    constexpr int PLANE = C::PLANE, OFF = C::XOFF & 1, NF2 = (OFF + W1 + 2) / 2;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
+    const int zi = zs + k, slot = k % C::NS;
+    const uint32_t sbase = lsm_u32(sm);
+    const bool arrived = lbar_wait(sbase + C::oBar + 8 * slot, (uint32_t)(k / C::NS) & 1u);
+    const float *L = reinterpret_cast<const float *>(sm + slot * C::STAGE);
+    float *X = reinterpret_cast<float *>(sm + C::oX) + (k & 1) * 3 * NX;
+    // the core voxel of the output slice zo = zi - RZ (fetched one step ago);
+    // start fetching the core voxel of the next output slice
+    const int zo = zi - C::RZ;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool out = zo >= zc0 && x < g.X && y < g.Y;
+    const int64_t vo = (int64_t)zo * sZ + (int64_t)y * sY + x;
+    const uint8_t mo = core.m;
+    const float fo = core.f, wo = core.w;
+    if (zo + 1 >= zc0 && zo + 1 < zs + nslices - C::RZ && x < g.X && y < g.Y) {
+        const int64_t vn = vo + sZ;
+        core.m = __ldg(m + vn);
+        core.f = __ldg(F + vn);
+        core.w = __ldg(W + vn);
+    }
+    // x box sums of every row of the staged slice, two neighbouring outputs
+    // per thread, taps read as float2 from the even column at or below the
+    // first tap
+    if (arrived && tid < NX / 2) {
+        const int ly = tid / (TX / 2), p2 = 2 * (tid - ly * (TX / 2));
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) {
+            const float2 *src =
+                reinterpret_cast<const float2 *>(L + q3 * PLANE + ly * LXT + p2 + (C::XOFF - OFF));
+            float v[2 * NF2];
+#pragma unroll
+            for (int q = 0; q < NF2; ++q) {
+                const float2 t = src[q];
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int d = 0; d < W1; ++d) {
+                s0 += v[OFF + d];
+                s1 += v[OFF + d + 1];
+            }
+            *reinterpret_cast<float2 *>(X + q3 * NX + ly * TX + p2) = make_float2(s0, s1);
+        }
+    }
+    // every thread has read slot `slot`: it may be refilled with slice k + NS
+    if (__syncthreads_or(!arrived)) {
+        kfail = k;
+        return false;
+    }
+    if (tid == 0 && k + C::NS < nslices) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        lcc_tma_issue<D, R>(map, sbase, k + C::NS, x0, y0, zi + C::NS);
+    }
+    // y box sum of this column: this slice's entry of the z ring
+    {
+        float a = 0.f, b = 0.f, c = 0.f;
+#pragma unroll
+        for (int d = 0; d < W1; ++d) {
+            const int r = (ty + d) * TX + tx;
+            a += X[r];
+            b += X[NX + r];
+            c += X[2 * NX + r];
+        }
+        ring[P] = make_float3(a, b, c);
+    }
+    if (out) {
+        float gv = 0.0f;
+        if (mo) {
+            float A = 0.f, B = 0.f, Cc = 0.f;
+#pragma unroll
+            for (int t = 0; t < NR; ++t) {
+                A += ring[t].x;
+                B += ring[t].y;
+                Cc += ring[t].z;
+            }
+            gv = fmaf(2.0f * wo, B, fmaf(fo, Cc, A));
+        }
+        gout[vo] = gv;
+    }
+    return true;
+}
+
+template <int D, int R, int P>
+__device__ __forceinline__ bool lcc_grad_tma_steps(const CUtensorMap *map, const Grid &g, int kb,
+                                                   int zs, int zc0, int x0, int y0, int nslices,
+                                                   const float *__restrict__ F,
+                                                   const float *__restrict__ W,
+                                                   const uint8_t *__restrict__ m,
+                                                   float *__restrict__ gout, unsigned char *sm,
+                                                   float3 (&ring)[LccT<D, R>::NR], CoreVox &core,
+                                                   int &kfail)
+{
+    if constexpr (P < LccT<D, R>::NR) {
+        if (kb + P < nslices) {
+            if (!lcc_grad_tma_step<D, R, P>(map, g, kb + P, zs, zc0, x0, y0, nslices, F, W, m,
+                                            gout, sm, ring, core, kfail))
+                return false;
+            return lcc_grad_tma_steps<D, R, P + 1>(map, g, kb, zs, zc0, x0, y0, nslices, F, W, m,
+                                                   gout, sm, ring, core, kfail);
+        }
+    }
+    return true;
+}
+
+// k_lcc_grad with TMA-staged coefficient slices: the block's z range (its
+// chunk and the 2R halo slices) streams through NS shared-memory slots, each
+// filled by one tile load of the three planes; thread 0 refills a slot once
+// every thread has passed the barrier after its x sums. Every wait is
+// bounded: a slice that does not arrive within about a second records
+// AL_ERR_TIMEOUT, and thread 0 waits (bounded again) for the loads still in
+// flight before the block returns.
+template <int D, int R>
+__global__ void __launch_bounds__(LccT<D, R>::THREADS, 2)
+    k_lcc_grad_tma(const __grid_constant__ CUtensorMap map, Grid g, int zc,
+                   const float *__restrict__ F, const float *__restrict__ W,
+                   const uint8_t *__restrict__ m, float *__restrict__ gout)
+{
+    using C = LccT<D, R>;
+    extern __shared__ unsigned char lsm_raw[];
+    unsigned char *sm = lsm_raw + ((128u - (lsm_u32(lsm_raw) & 127u)) & 127u);
+    const uint32_t sbase = lsm_u32(sm);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+    const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, g.Z);
+    const int zs = zc0 - C::RZ, nslices = zc1 + C::RZ - zs;
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < C::NS; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + C::oBar + 8 * k)
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < C::NS && k < nslices; ++k)
+            lcc_tma_issue<D, R>(&map, sbase, k, x0, y0, zs + k);
+    float3 ring[C::NR];
+#pragma unroll
+    for (int t = 0; t < C::NR; ++t)
+        ring[t] = make_float3(0.f, 0.f, 0.f);
+    CoreVox core{0, 0.f, 0.f};
+    {
+        const int x = x0 + tid % C::TX, y = y0 + tid / C::TX;
+        if (x < g.X && y < g.Y) {  // first output slice is zc0
+            const int64_t v = (int64_t)zc0 * ((int64_t)g.X * g.Y) + (int64_t)y * g.X + x;
+            core.m = __ldg(m + v);
+            core.f = __ldg(F + v);
+            core.w = __ldg(W + v);
+        }
+    }
+    int kfail = -1;
+    for (int kb = 0; kb < nslices; kb += C::NR) {
+        if (lcc_grad_tma_steps<D, R, 0>(&map, g, kb, zs, zc0, x0, y0, nslices, F, W, m, gout, sm,
+                                        ring, core, kfail))
+            continue;
+        // slice kfail timed out: record it, then let the loads issued for
+        // slices kfail .. kfail + NS - 1 land before the block's memory goes
+        if (tid == 0) {
+            atomicExch(&g_unit_error, kErrTimeout);
+            for (int k = kfail; k < kfail + C::NS && k < nslices; ++k)
+                lbar_wait(sbase + C::oBar + 8 * (k % C::NS), (uint32_t)(k / C::NS) & 1u);
+        }
+        return;
+    }
+}
+
 // z chunk of an LCC kernel: its default ZC, shortened on small grids so
 // that the launch still has about two blocks per SM of a 152-SM GB300 (down
 // to 2 slices, each chunk re-reading its 2R-slice halo). Depends on the grid
@@ -574,6 +845,46 @@ int lcc_stats_chunk(const Grid &g)
 {
     using A = LccA<D, R>;
     return lcc_chunk(g, ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY), A::ZC);
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of the coefficient planes as a 4D fp32 tensor (X, Y, Z, plane)
+// with boxes of 40 x (16 + 2R) x 1 x 3. False when TMA cannot address it:
+// the row pitch X * 4 B must be a multiple of 16 B and the base 16-B aligned
+// (the encoder checks both); the caller then uses the register-staged kernel.
+template <int D, int R>
+bool lcc_coef_tmap(CUtensorMap *map, const Grid &g, const float *coef)
+{
+    using C = LccT<D, R>;
+    if (g.X % 4 != 0 || ((uintptr_t)coef & 15u) != 0)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc)
+        return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.X, (cuuint64_t)g.Y, (cuuint64_t)g.Z, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.X * 4, (cuuint64_t)g.X * g.Y * 4,
+                                   (cuuint64_t)lcc_plane(g.nv) * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)C::LXT, (cuuint32_t)C::LY, 1, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(coef), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
 }
 
 template <int D, int R>
@@ -596,8 +907,15 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     }
     if ((e = cudaGetLastError()) != cudaSuccess || !gout)
         return e;
-    e = cudaFuncSetAttribute(k_lcc_grad<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)B::smem);
+    using T = LccT<D, R>;
+    static_assert(T::smem <= 227 * 1024 && T::TX == B::TX && T::TY == B::TY && T::ZC == B::ZC,
+                  "both gradient kernels tile alike");
+    CUtensorMap map;
+    const bool tma = lcc_coef_tmap<D, R>(&map, g, coef);
+    e = tma ? cudaFuncSetAttribute(k_lcc_grad_tma<D, R>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem)
+            : cudaFuncSetAttribute(k_lcc_grad<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)B::smem);
     if (e != cudaSuccess)
         return e;
     {
@@ -605,7 +923,10 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
         const int zc = lcc_chunk(g, tiles, B::ZC);
         dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + zc - 1) / zc);
         ProfScope ps(s, "k_lcc_grad");
-        k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, zc, F, W, m, coef, gout);
+        if (tma)
+            k_lcc_grad_tma<D, R><<<grid, T::THREADS, T::smem, s>>>(map, g, zc, F, W, m, gout);
+        else
+            k_lcc_grad<D, R><<<grid, B::THREADS, B::smem, s>>>(g, zc, F, W, m, coef, gout);
     }
     return cudaGetLastError();
 }
@@ -629,6 +950,8 @@ int lcc_num_blocks(const Grid &g, int window)
 }
 
 size_t lcc_coef_bytes(const Grid &g) { return (size_t)3 * lcc_plane(g.nv) * sizeof(float); }
+
+AL_UNIT_ERROR_READER(unit_error_lcc)
 
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,
                        const uint8_t *m, float *gout, double *part, float *coef, cudaStream_t s)

@@ -167,6 +167,7 @@ int conv_device_error(bool clear);
 int unit_error_basic(bool clear);
 int unit_error_fused(bool clear);
 int unit_error_conv(bool clear);
+int unit_error_lcc(bool clear);
 
 // Grids of the network's two coarsest levels: n3 (e3, the head) and n4 (e4),
 // (z, y, x); lat = spacing-8 lattice sizes (x, y, z).

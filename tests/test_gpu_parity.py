@@ -128,7 +128,9 @@ def test_warp_face_tie_and_shift():
 
 # ----------------------------------------------------------------------- A3 --
 
-@pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (40, 64, 33)])
+# X a multiple of 4 ((50, 92), (21, 40, 68)): the LCC gradient stages its
+# coefficient slices by TMA; otherwise by register prefetch.
+@pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (40, 64, 33), (50, 92), (21, 40, 68)])
 @pytest.mark.parametrize("sim,window", [("mse", 7), ("ncc", 7), ("lcc", 3), ("lcc", 5), ("lcc", 7)])
 def test_similarity(shape, sim, window):
     rng = np.random.default_rng(14)
