@@ -47,7 +47,8 @@ struct LccA {
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
     static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
-    static constexpr int ZC = (D == 3) ? 16 : 1;
+    static constexpr int ZC = (D == 3) ? 64 : 1;  // most output slices per block
+    static constexpr double HALO = 0.1;  // a halo slice is only staged (relative cost)
     static constexpr int THREADS = 512;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;  // load elements per thread
     // shared memory: ring of (F, masked W) pairs, z sums (5 planes + 2 of
@@ -65,7 +66,8 @@ struct LccB {
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
     static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
-    static constexpr int ZC = (D == 3) ? 24 : 1;
+    static constexpr int ZC = (D == 3) ? 64 : 1;  // most output slices per block
+    static constexpr double HALO = 1.0;  // a halo slice takes its x/y box sums too
     static constexpr int THREADS = NC;
     static constexpr int KL = (NL + THREADS - 1) / THREADS;
     // one buffer: the staged slice as planes a', b, c of NL floats, then the
@@ -87,7 +89,8 @@ struct LccT {
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LXT = 40, XOFF = 4 - R, LY = TY + 2 * R;
     static constexpr int NX = LY * TX, NC = TX * TY;
-    static constexpr int ZC = (D == 3) ? 24 : 1;
+    static constexpr int ZC = (D == 3) ? 64 : 1;  // most output slices per block
+    static constexpr double HALO = 1.0;  // a halo slice takes its x/y box sums too
     static constexpr int THREADS = NC;
     static constexpr int NS = 4;                 // slices in flight
     static constexpr int PLANE = LY * LXT;       // floats of one staged plane
@@ -826,25 +829,44 @@ __global__ void __launch_bounds__(LccT<D, R>::THREADS, 2)
     }
 }
 
-// z chunk of an LCC kernel: its default ZC, shortened on small grids so
-// that the launch still has about two blocks per SM of a 152-SM GB300 (down
-// to 2 slices, each chunk re-reading its 2R-slice halo). Depends on the grid
+// z chunk (output slices per block) of an LCC kernel. The blocks of a launch
+// do equal work and run in waves of 2 x 152 (two resident blocks per SM of
+// a 152-SM GB300), so the chunk minimises
+//   waves x (chunk + 2 rz x halo),
+// halo being the cost of one of the 2 rz halo slices a chunk re-reads
+// relative to an output slice; a last wave that is barely filled costs as
+// much as a full one. At least 2 slices, at most zc_max. Depends on the grid
 // only, so workspace sizes and launches agree.
-int lcc_chunk(const Grid &g, int tiles_xy, int zc_default)
+int lcc_chunk(const Grid &g, int tiles_xy, int zc_max, int rz, double halo)
 {
     if (g.ndim != 3)
         return 1;
-    const int want = 2 * 152;
-    const int chunks = (want + tiles_xy - 1) / tiles_xy;
-    const int zc = (g.Z + chunks - 1) / chunks;
-    return zc < 2 ? 2 : (zc > zc_default ? zc_default : zc);
+    const int64_t slots = 2 * 152;
+    int best = 2;
+    double best_cost = 0.0;
+    for (int chunks = 1; chunks <= g.Z; ++chunks) {
+        const int zc = (g.Z + chunks - 1) / chunks;
+        if (zc > zc_max)
+            continue;
+        if (zc < 2)
+            break;
+        const int n = (g.Z + zc - 1) / zc;  // chunks launched with this zc
+        const int64_t waves = ((int64_t)tiles_xy * n + slots - 1) / slots;
+        const double cost = (double)waves * (zc + 2.0 * rz * halo);
+        if (best_cost == 0.0 || cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
 }
 
 template <int D, int R>
 int lcc_stats_chunk(const Grid &g)
 {
     using A = LccA<D, R>;
-    return lcc_chunk(g, ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY), A::ZC);
+    return lcc_chunk(g, ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY), A::ZC, A::RZ,
+                     A::HALO);
 }
 
 // The driver's tensor-map encoder, looked up once through the runtime.
@@ -908,7 +930,8 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     if ((e = cudaGetLastError()) != cudaSuccess || !gout)
         return e;
     using T = LccT<D, R>;
-    static_assert(T::smem <= 227 * 1024 && T::TX == B::TX && T::TY == B::TY && T::ZC == B::ZC,
+    static_assert(T::smem <= 227 * 1024 && T::TX == B::TX && T::TY == B::TY && T::ZC == B::ZC &&
+                      T::HALO == B::HALO,
                   "both gradient kernels tile alike");
     CUtensorMap map;
     const bool tma = lcc_coef_tmap<D, R>(&map, g, coef);
@@ -920,7 +943,7 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
         return e;
     {
         const int tiles = ((g.X + B::TX - 1) / B::TX) * ((g.Y + B::TY - 1) / B::TY);
-        const int zc = lcc_chunk(g, tiles, B::ZC);
+        const int zc = lcc_chunk(g, tiles, B::ZC, B::RZ, B::HALO);
         dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + zc - 1) / zc);
         ProfScope ps(s, "k_lcc_grad");
         if (tma)
