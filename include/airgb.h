@@ -505,9 +505,11 @@ al_status al_render_blobs(const int64_t *size, int32_t count, int32_t n_blobs, c
                           float *out, al_stream stream);
 
 /* Synchronise `stream`, then read and clear the current device's kernel
- * error words (the objective's and the convolution layers'): AL_OK,
- * AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the synchronisation itself
- * failed). */
+ * error words (the objective's, the LCC kernels' and the convolution
+ * layers'): AL_OK, AL_ERR_BOUNDS or AL_ERR_TIMEOUT (AL_ERR_CUDA if the
+ * synchronisation itself failed). AL_ERR_TIMEOUT comes from a bounded wait
+ * on an asynchronous copy (the TMA slices of the LCC gradient, the weight
+ * slices of a convolution layer) or on another block (al_batch_step). */
 al_status al_get_device_error(al_stream stream);
 
 /* Instrumentation (not part of the method). When enabled, every kernel the
