@@ -512,6 +512,17 @@ al_status al_render_blobs(const int64_t *size, int32_t count, int32_t n_blobs, c
  * slices of a convolution layer) or on another block (al_batch_step). */
 al_status al_get_device_error(al_stream stream);
 
+/* Test of the LCC gradient's bounded waits (not part of the method). With
+ * drop_slice >= 0, the TMA-staged LCC gradient kernel (used when X is a
+ * multiple of 4) does not issue the load of slice `drop_slice` of each
+ * block's z range. The wait for that slice runs out after about a second,
+ * the block records AL_ERR_TIMEOUT, waits for its other loads in flight and
+ * returns without writing its outputs. -1 (the default) restores normal
+ * staging. Applies to launches issued after the call on the current device;
+ * blocking (a copy to device constant memory). AL_ERR_INVALID_ARG if
+ * drop_slice < -1. */
+al_status al_lcc_set_wait(int32_t drop_slice);
+
 /* Instrumentation (not part of the method). When enabled, every kernel the
  * library launches is bracketed by two CUDA events recorded on the
  * launching stream. al_profile_collect synchronises on the recorded events,

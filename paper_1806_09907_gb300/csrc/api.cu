@@ -700,6 +700,13 @@ al_status al_objective_grad_diffeo(const al_problem *pr, int32_t steps, const fl
     return launched(launch_combine(vals, vals + 2, pr->lambda, value_dev, s));
 }
 
+al_status al_lcc_set_wait(int32_t drop_slice)
+{
+    if (drop_slice < -1)
+        return AL_ERR_INVALID_ARG;
+    return lcc_set_drop_slice((int)drop_slice) == cudaSuccess ? AL_OK : AL_ERR_CUDA;
+}
+
 al_status al_get_device_error(al_stream stream)
 {
     if (cudaStreamSynchronize(S(stream)) != cudaSuccess)

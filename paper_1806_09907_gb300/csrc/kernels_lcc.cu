@@ -626,12 +626,19 @@ __device__ __noinline__ bool lbar_wait(uint32_t bar, uint32_t parity)
     return true;
 }
 
+// Test of the bounded waits of k_lcc_grad_tma: the slice (index within each
+// block's z range) whose load is not issued, so the wait for it runs out;
+// -1 = none.
+__constant__ int c_lcc_drop_slice = -1;
+
 // Issue the TMA load of slice k of the block's z range into ring slot k % NS.
 template <int D, int R>
 __device__ __forceinline__ void lcc_tma_issue(const CUtensorMap *map, uint32_t sbase, int k,
                                               int x0, int y0, int z)
 {
     using C = LccT<D, R>;
+    if (k == c_lcc_drop_slice)
+        return;
     const int slot = k % C::NS;
     const uint32_t dst = sbase + slot * C::STAGE, bar = sbase + C::oBar + 8 * slot;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
@@ -975,6 +982,11 @@ int lcc_num_blocks(const Grid &g, int window)
 size_t lcc_coef_bytes(const Grid &g) { return (size_t)3 * lcc_plane(g.nv) * sizeof(float); }
 
 AL_UNIT_ERROR_READER(unit_error_lcc)
+
+cudaError_t lcc_set_drop_slice(int slice)
+{
+    return cudaMemcpyToSymbol(c_lcc_drop_slice, &slice, sizeof(int));
+}
 
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,
                        const uint8_t *m, float *gout, double *part, float *coef, cudaStream_t s)

@@ -213,6 +213,10 @@ def test_batch_rejects(lib):
     lib.al_batch_destroy(h)
 
 
+def test_lcc_wait_hook_rejects_bad_slice(lib):
+    assert lib.al_lcc_set_wait(-2) == 1
+
+
 # ---- learned initialisation: layer and glue argument checks ----------------
 
 def _conv(batch=2, size=(8, 8, 8), cin=16, cout=32, stride=2):

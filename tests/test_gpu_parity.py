@@ -147,6 +147,30 @@ def test_similarity(shape, sim, window):
     assert rel_l2(gw, gr) <= G_TOL
 
 
+def test_lcc_tma_wait_timeout_is_reported_and_recoverable():
+    """A TMA slice load that is never issued (the test hook) makes the LCC
+    gradient's bounded wait run out: the call returns, AL_ERR_TIMEOUT is
+    reported once, and the next call on the same context is correct."""
+    shape = (9, 24, 40)  # X a multiple of 4: TMA-staged gradient
+    rng = np.random.default_rng(18)
+    F = (rng.normal(size=shape) * 30.0 - 700.0).astype(np.float32)
+    Wv = (0.8 * F + rng.normal(size=shape) * 20.0 - 100.0).astype(np.float32)
+    m = np.ones(shape, dtype=np.uint8)
+    airgb.al_get_device_error()
+    airgb.al_lcc_set_wait(1)
+    try:
+        airgb.al_similarity("lcc", dev(F), dev(Wv), dev(m), eps=1e-5, window=7)
+        assert airgb.al_get_device_error() == 6  # AL_ERR_TIMEOUT
+    finally:
+        airgb.al_lcc_set_wait(-1)
+    assert airgb.al_get_device_error() == 0
+    val, gw = airgb.al_similarity("lcc", dev(F), dev(Wv), dev(m), eps=1e-5, window=7)
+    assert airgb.al_get_device_error() == 0
+    S, gr = oracle.similarity(airgb.SIM_KINDS["lcc"], F, Wv, m, eps=1e-5, window=7)
+    assert abs(host(val)[0] - S) <= J_TOL * abs(S)
+    assert rel_l2(host(gw), gr) <= G_TOL
+
+
 # ----------------------------------------------------------------------- A4 --
 
 @pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (2, 2, 2)])
