@@ -249,6 +249,36 @@ def test_lcc_huge_window_is_zero_padded_pearson():
         assert S == pytest.approx(1.0 - rho, abs=1e-12)
 
 
+def test_lcc_windows_match_pearson_brute_force():
+    """LCC (Sec. III-B) on tiny grids with windows that differ from voxel to
+    voxel: at every masked voxel rho is numpy's Pearson correlation of the
+    w^d window samples of F and the masked W, read from zero-padded copies
+    (eps = 0); S = 1 - mean over the mask. dS/dW matches central differences
+    of S in W at masked voxels."""
+    g = np.random.default_rng(11)
+    for shape, w in (((7, 9), 3), ((7, 9), 5), ((4, 5, 6), 3)):
+        r = w // 2
+        F = g.normal(size=shape)
+        W = 0.6 * F + g.normal(size=shape)
+        m = (g.uniform(size=shape) > 0.25).astype(np.uint8)
+        S, gw = oracle.similarity(oracle.LCC, F, W, m, eps=0.0, window=w)
+        Fp = np.pad(F, r)
+        Wp = np.pad(W * m, r)
+        rhos = []
+        for idx in zip(*np.nonzero(m)):
+            win = tuple(slice(i, i + w) for i in idx)
+            rhos.append(np.corrcoef(Fp[win].ravel(), Wp[win].ravel())[0, 1])
+        assert S == pytest.approx(1.0 - np.mean(rhos), abs=1e-12)
+        h = 1e-6
+        for idx in list(zip(*np.nonzero(m)))[::7]:
+            Wa, Wb = W.copy(), W.copy()
+            Wa[idx] += h
+            Wb[idx] -= h
+            Sa, _ = oracle.similarity(oracle.LCC, F, Wa, m, eps=0.0, window=w)
+            Sb, _ = oracle.similarity(oracle.LCC, F, Wb, m, eps=0.0, window=w)
+            assert gw[idx] == pytest.approx((Sa - Sb) / (2 * h), rel=1e-5, abs=1e-8)
+
+
 def test_lcc_identical_images():
     """Identical images: every local correlation is 1, S = 0, gradient 0 (eps = 0)."""
     g = np.random.default_rng(9)
