@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "airgb.h"
+#include "checks.h"
 #include "launch.h"
 
 namespace {
@@ -72,6 +73,13 @@ al_status al_similarity_noalloc(const al_grid *g, const al_sim_params *p, const 
     }
     if (need > kNoAllocScratchBytes)
         return AL_ERR_SCRATCH_LIMIT;
+    // the pointer checks of al_similarity, before the address lookup (which
+    // is the first CUDA call)
+    if (!fixed || !warped || !mask || !value_dev)
+        return AL_ERR_INVALID_ARG;
+    if (!airgb::aligned16(fixed) || !airgb::aligned16(warped) || !airgb::aligned16(mask) ||
+        !airgb::aligned16(value_dev) || (grad_warped && !airgb::aligned16(grad_warped)))
+        return AL_ERR_ALIGN;
     void *scratch = nullptr;
     const al_status st = scratch_address(&scratch);
     if (st != AL_OK)

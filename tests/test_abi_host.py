@@ -84,6 +84,96 @@ def test_calls_reject_bad_pointers_before_launching(lib):
     assert lib.al_displacement(ctypes.byref(bad), a, a, None) == 2
 
 
+def _sim_params(kind="lcc", window=7, eps=1e-5):
+    p = airgb.al_sim_params()
+    p.kind, p.lcc_window, p.eps = airgb.SIM_KINDS.get(kind, 5), window, eps
+    return p
+
+
+def test_step_calls_reject_before_launching(lib):
+    """A1-A6 step calls: NULL arrays (1), misaligned arrays (3), bad grids
+    (2), short workspaces (8) and bad parameters (1) are reported on the
+    host; none of these calls reaches the GPU (there is none here)."""
+    P, Mis = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10004)
+    big = ctypes.c_size_t(1 << 30)
+    g = airgb.make_grid((16, 20, 24))
+    bad = airgb.make_grid((16, 20, 24))
+    bad.ndim = 4
+    bs = airgb.bspline_init((16, 20, 24), 4)
+    nb = lib.al_displacement_adjoint_workspace_bytes(ctypes.byref(bs))
+    assert nb > 0
+    assert lib.al_displacement_adjoint(ctypes.byref(bs), None, P, P, big, None) == 1
+    assert lib.al_displacement_adjoint(ctypes.byref(bs), P, P, P, ctypes.c_size_t(nb - 1),
+                                       None) == 8
+    assert lib.al_displacement_adjoint(ctypes.byref(bs), Mis, P, P, big, None) == 3
+    assert lib.al_warp(ctypes.byref(g), None, P, P, P, None) == 1
+    assert lib.al_warp(ctypes.byref(g), P, Mis, P, P, None) == 3
+    assert lib.al_warp(ctypes.byref(bad), P, P, P, P, None) == 2
+    assert lib.al_warp_adjoint(ctypes.byref(g), P, P, None, P, P, 0, None) == 1
+    assert lib.al_warp_adjoint(ctypes.byref(g), P, P, P, P, P, 2, None) == 1  # accumulate
+    sp = _sim_params()
+    n = lib.al_similarity_workspace_bytes(ctypes.byref(g), ctypes.byref(sp))
+    assert n > 0
+    assert lib.al_similarity_workspace_bytes(ctypes.byref(g), ctypes.byref(_sim_params(window=9))) == 0
+    assert lib.al_similarity(ctypes.byref(g), ctypes.byref(sp), P, P, P, P, P, P,
+                             ctypes.c_size_t(n - 1), None) == 8
+    assert lib.al_similarity(ctypes.byref(g), ctypes.byref(sp), P, P, None, P, P, P,
+                             ctypes.c_size_t(n), None) == 1
+    assert lib.al_similarity(ctypes.byref(g), ctypes.byref(sp), P, Mis, P, P, P, P,
+                             ctypes.c_size_t(n), None) == 3
+    for badp in (_sim_params(eps=-1.0), _sim_params(kind="none")):
+        assert lib.al_similarity(ctypes.byref(g), ctypes.byref(badp), P, P, P, P, P, P,
+                                 ctypes.c_size_t(n), None) == 1
+    nr = lib.al_regulariser_workspace_bytes(ctypes.byref(g))
+    assert lib.al_regulariser(ctypes.byref(g), None, ctypes.c_double(1.0), P, P, P,
+                              ctypes.c_size_t(nr), None) == 1
+    assert lib.al_regulariser(ctypes.byref(g), P, ctypes.c_double(float("nan")), P, P, P,
+                              ctypes.c_size_t(nr), None) == 1
+    pr = airgb.make_problem((16, 20, 24), 4, "lcc", 0.1)
+    nu = lib.al_objective_unfused_workspace_bytes(ctypes.byref(pr))
+    assert lib.al_objective_grad_unfused(ctypes.byref(pr), P, P, P, P, P, P,
+                                         ctypes.c_size_t(nu - 1), None) == 8
+
+
+def test_noalloc_limits_and_pointers(lib):
+    """The allocation-free similarity: a problem beyond the built-in 4 MiB
+    scratch (LCC on 128x128x64) returns AL_ERR_SCRATCH_LIMIT; NULL and
+    misaligned arrays are reported before the first CUDA call."""
+    P, Mis = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10004)
+    assert lib.al_noalloc_scratch_bytes() == 4 << 20
+    sp = _sim_params()
+    big = airgb.make_grid((64, 128, 128))
+    assert lib.al_similarity_noalloc(ctypes.byref(big), ctypes.byref(sp), P, P, P, P, P,
+                                     None) == 9
+    g = airgb.make_grid((16, 20, 24))
+    assert lib.al_similarity_noalloc(ctypes.byref(g), ctypes.byref(sp), None, P, P, P, P,
+                                     None) == 1
+    assert lib.al_similarity_noalloc(ctypes.byref(g), ctypes.byref(sp), P, P, P, P, Mis,
+                                     None) == 3
+
+
+def test_diffeo_calls_reject_before_launching(lib):
+    """Scaling and squaring: steps outside 0..20 (1), a missing workspace or
+    trajectory (8 / 1), short workspaces (8)."""
+    P = ctypes.c_void_p(0x10000)
+    big = ctypes.c_size_t(1 << 30)
+    g = airgb.make_grid((16, 20, 24))
+    assert lib.al_exp_field_workspace_bytes(ctypes.byref(g)) > 0
+    for steps in (-1, 21):
+        assert lib.al_exp_field(ctypes.byref(g), steps, P, P, None, P, big, None) == 1
+    assert lib.al_exp_field(ctypes.byref(g), 6, P, P, None, None, ctypes.c_size_t(0), None) == 8
+    assert lib.al_exp_field_adjoint(ctypes.byref(g), 6, None, P, P, P, big, None) == 1
+    assert lib.al_exp_field_adjoint(ctypes.byref(g), 6, P, P, P, P, ctypes.c_size_t(1),
+                                    None) == 8
+    pr = airgb.make_problem((16, 20, 24), 4, "lcc", 0.1)
+    nd = lib.al_objective_diffeo_workspace_bytes(ctypes.byref(pr), 6)
+    assert nd > 0 and lib.al_objective_diffeo_workspace_bytes(ctypes.byref(pr), 21) == 0
+    assert lib.al_objective_grad_diffeo(ctypes.byref(pr), 6, P, P, P, P, P, P,
+                                        ctypes.c_size_t(nd - 1), None) == 8
+    assert lib.al_objective_grad_diffeo(ctypes.byref(pr), 21, P, P, P, P, P, P,
+                                        ctypes.c_size_t(nd), None) == 1
+
+
 def test_workspace_checks(lib):
     pr = airgb.make_problem((24, 20, 18), 4, "lcc", 0.1)
     need = lib.al_objective_workspace_bytes(ctypes.byref(pr))
