@@ -307,6 +307,34 @@ def test_lcc_wait_hook_rejects_bad_slice(lib):
     assert lib.al_lcc_set_wait(-2) == 1
 
 
+def test_batch_bind_tune_status_reject(lib):
+    """Binding checks every device pointer (NULL 1, misaligned 3) and the
+    workspace (8) on the host; tuning needs a bound workspace (8) and at
+    least one iteration (1); a NULL batch is an invalid argument."""
+    st, h = _batch(lib, [airgb.make_problem((64, 64), 8), airgb.make_problem((32, 40, 48), 8)])
+    assert st == 0
+    ws = lib.al_batch_workspace_bytes(h)
+    a = ctypes.c_void_p(0x10000)
+    two = ctypes.c_void_p * 2
+    ok = two(0x10000, 0x20000)
+
+    def bind(fixed=ok, workspace=a, nbytes=ws):
+        return lib.al_batch_bind(h, fixed, ok, ok, ok, ok, None, workspace,
+                                 ctypes.c_size_t(nbytes))
+
+    assert bind(fixed=None) == 1
+    assert bind(fixed=two(0x10000, None)) == 1
+    assert bind(fixed=two(0x10000, 0x20004)) == 3
+    assert bind(nbytes=ws - 1) == 8
+    assert bind(workspace=None) == 8
+    p = airgb.al_adam_params(0.01, 0.9, 0.999, 1e-8)
+    assert lib.al_batch_tune(h, ctypes.byref(p), 5, None, None, None) == 8  # not bound
+    assert lib.al_batch_tune(h, ctypes.byref(p), 0, None, None, None) == 1
+    assert lib.al_batch_status(None, None) == 1
+    assert lib.al_batch_bind(None, ok, ok, ok, ok, ok, None, a, ctypes.c_size_t(ws)) == 1
+    lib.al_batch_destroy(h)
+
+
 # ---- learned initialisation: layer and glue argument checks ----------------
 
 def _conv(batch=2, size=(8, 8, 8), cin=16, cout=32, stride=2):
@@ -387,6 +415,18 @@ def test_initnet_glue_checks(lib):
     sz = (ctypes.c_int64 * 3)(8, 8, 8)
     assert lib.al_render_blobs(sz, 0, 10, a, a, None) == 1
     assert lib.al_render_blobs(sz, 1, 10, a, ctypes.c_void_p(0x10004), None) == 3
+    mis = ctypes.c_void_p(0x10004)
+    assert lib.al_initnet_input(2, sz, None, a, a, None) == 1
+    assert lib.al_initnet_input(0, sz, a, a, a, None) == 1
+    assert lib.al_initnet_input(2, sz, a, mis, a, None) == 3
+    assert lib.al_initnet_input(2, (ctypes.c_int64 * 3)(0, 8, 8), a, a, a, None) == 2
+    assert lib.al_initnet_upcat_adjoint(2, n3, 60, 48, a, a, a, None) == 1  # channels % 8
+    assert lib.al_initnet_upcat_adjoint(2, n3, 64, 48, None, a, a, None) == 1
+    assert lib.al_initnet_upcat_adjoint(2, n3, 64, 48, a, mis, a, None) == 3
+    assert lib.al_initnet_head_adjoint(ctypes.byref(bs), 2, n3, 6, a, a, None) == 2  # % 4
+    assert lib.al_initnet_head_adjoint(ctypes.byref(bs), 2, n3, 16, None, a, None) == 1
+    assert lib.al_initnet_head_adjoint(ctypes.byref(bs), 2, bad, 16, a, a, None) == 2
+    assert lib.al_initnet_head_adjoint(ctypes.byref(bs6), 2, n3, 16, a, a, None) == 7
 
 
 def test_registration_checkpoint_roundtrip(tmp_path):
