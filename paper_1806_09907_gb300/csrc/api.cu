@@ -102,6 +102,27 @@ al_status check_sim(const al_sim_params *p, int ndim)
 
 al_status launched(cudaError_t e) { return e == cudaSuccess ? AL_OK : AL_ERR_CUDA; }
 
+int device_sms()
+{
+    constexpr int kDevices = 64, kFallback = 152;
+    static int cache[kDevices] = {};  // idempotent writes: a race stores the same value
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return kFallback;
+    }
+    if (dev >= 0 && dev < kDevices && cache[dev] > 0)
+        return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return kFallback;
+    }
+    if (dev >= 0 && dev < kDevices)
+        cache[dev] = n;
+    return n;
+}
+
 }  // namespace airgb
 
 namespace {

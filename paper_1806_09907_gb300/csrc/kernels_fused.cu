@@ -840,7 +840,7 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
         o.gb = off;
         off += align256((size_t)g.nv * 4);
         o.lpart = off;
-        off += align256((size_t)o.nlcc * 2 * 8);
+        off += align256((size_t)lcc_max_blocks(g, window) * 2 * 8);
         o.coef = off;
         off += lcc_coef_bytes(g);
         o.Gb = off;
@@ -955,7 +955,8 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
                                                  s);
         if (e != cudaSuccess)
             return e;
-        e = launch_lcc(g, window, eps, F, Wb, mb, gc ? gb : nullptr, (double *)(ws + lay.lpart),
+        e = launch_lcc(g, window, eps, F, Wb, mb, true, gc ? gb : nullptr,
+                       (double *)(ws + lay.lpart),
                        (float *)(ws + lay.coef), s);
         if (e != cudaSuccess)
             return e;
@@ -975,8 +976,8 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     {
         const int th = 256;
         int64_t nb = ((int64_t)L.nc + th - 1) / th;
-        if (nb > 152 * 2)
-            nb = 152 * 2;
+        if (nb > 2 * device_sms())
+            nb = 2 * device_sms();
         const float *bp = (const float *)(ws + lay.bpart);
         ProfScope ps(s, "k_ctrl");
         constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);

@@ -8,22 +8,30 @@
 //
 // Numerics. fp32 local sums S_FF - S_F^2/n cancel catastrophically when the
 // intensities are large compared with their local spread (CT: -1000 HU with
-// 20 HU noise). Every partial sum here is therefore taken relative to the
-// value at the centre of its own window, and merging windows converts the
-// partial sums to the new centre exactly:
+// 20 HU noise). The sums are therefore taken relative to a reference value
+// (r_F, r_W) that is itself a sample of every window summed relative to it:
+// then the sums of squares are at most about n times the window's own spread
+// (a window holding its reference cannot be more homogeneous than that), and
+// in homogeneous regions they are of the size of the noise. Sums taken
+// relative to one reference are converted to another exactly,
 //   sum (v - b)   = sum (v - a) + n (a - b)
-//   sum (v - b)^2 = sum (v - a)^2 + 2 (a - b) sum (v - a) + n (a - b)^2
-// (and the cross term likewise), so every quantity stays of the size of the
-// local spread. The statistics are shift invariant, so the derivatives with
-// respect to the shifted sums are the derivatives with respect to the plain
-// ones, and the shift re-enters the gradient as
-//   a'(x) = a(x) - 2 W(x) b(x) - F(x) c(x),   dS/dW(y) ~ A' + 2 W B + F C.
+//   sum (v - b)^2 = sum (v - a)^2 + (a - b) (sum (v - a) + sum (v - b))
+// (and the cross term likewise). The statistics are shift invariant, so the
+// derivatives with respect to the shifted sums are the derivatives with
+// respect to the plain ones, and the shift re-enters the gradient as
+//   a'(x) = a(x) - 2 r_W(x) b(x) - r_F(x) c(x),   dS/dW(y) ~ A' + 2 W B + F C.
 //
-// k_lcc_stats: z-streaming tiles. Per input slice the tile (with an R halo)
-// enters a ring of 2R+1 slices in shared memory; the z sums of every column
-// are taken directly from the ring (relative to the column's centre value),
-// then merged along x and along y with the conversion above. It writes
-// (a', b, c) per voxel and per-block {sum rho, count} partials.
+// k_lcc_stats: z-streaming tiles of 32 x 16 output columns. The references
+// are shared by runs of outputs, each reference at most R (in z: RZ) from
+// every output of its run, hence inside all their windows:
+//   z: the output slices of a chunk form groups of 2RZ+1; the z sums of a
+//      column are relative to the column's own value at the group's middle
+//      slice and slide from one output slice to the next (restarted at each
+//      group, so rounding does not build up);
+//   x: runs of G neighbouring outputs of a row share the reference of the
+//      run's column at offset G/2; the column sums are converted to it;
+//   y: runs of G rows share the reference of the run's row at offset G/2.
+// It writes (a', b, c) per voxel and per-block {sum rho, count} partials.
 // k_lcc_grad: plain box sums of (a', b, c) (three planes; z through a
 // register ring of x/y sums) and dS/dW * |X_m| on the mask. When the row
 // pitch allows a tensor map (X a multiple of 4), k_lcc_grad_tma stages the
@@ -33,6 +41,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <string.h>
 
 #include "launch.h"
 #include "profile.h"
@@ -40,25 +49,6 @@
 namespace airgb {
 
 namespace {
-
-template <int D, int R>
-struct LccA {
-    static constexpr int TX = 32, TY = 16;
-    static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
-    static constexpr int LX = TX + 2 * R, LY = TY + 2 * R;
-    static constexpr int NL = LX * LY, NX = LY * TX, NC = TX * TY;
-    static constexpr int ZC = (D == 3) ? 64 : 1;  // most output slices per block
-    static constexpr double HALO = 0.1;  // a halo slice is only staged (relative cost)
-    static constexpr int THREADS = 512;
-    static constexpr int KL = (NL + THREADS - 1) / THREADS;  // load elements per thread
-    // shared memory: ring of (F, masked W) pairs, z sums (5 planes + 2 of
-    // centre values), x-merged sums, mask ring (bytes, at the end)
-    static constexpr int oRFW = 0, oZ = oRFW + 2 * NR * NL, oX = oZ + 7 * NL;
-    static constexpr int oM = oX + 5 * NX;  // in floats; mask bytes start here
-    static constexpr size_t smem = (size_t)oM * 4 + (size_t)NR * NL;
-    static_assert(LX % 2 == 0 && NL % 2 == 0 && NX % 2 == 0 && TX % 2 == 0,
-                  "column pairs are read as float2");
-};
 
 template <int D, int R>
 struct LccB {
@@ -106,278 +96,479 @@ struct LccT {
 // Distance in floats between the planes a', b, c of the LCC coefficients.
 __host__ __device__ inline int64_t lcc_plane(int nv) { return ((int64_t)nv * 4 + 255) / 256 * 64; }
 
-// Window sums (of F, W, F^2, W^2, FW) relative to a reference (bf, bw).
-struct Sums {
-    float s1f, s1w, s2f, s2w, sfw;
+// ---- bounded waits, TMA helpers ---------------------------------------------
+constexpr int kErrTimeout = 6;  // AL_ERR_TIMEOUT
+
+__device__ __forceinline__ uint32_t lsm_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool lbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with this parity, for about one second of
+// %globaltimer at most; false if it did not complete.
+__device__ __noinline__ bool lbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (lbar_try_wait(bar, parity))
+        return true;
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!lbar_try_wait(bar, parity)) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull)
+            return false;
+    }
+    return true;
+}
+
+// Test of the bounded waits of the LCC kernels: the slice (index within each
+// block's z range) whose load is not issued, so the wait for it runs out;
+// -1 = none.
+__constant__ int c_lcc_drop_slice = -1;
+
+// ---- packed fp32 pairs (the f32x2 arithmetic of sm_100 and later) -----------
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b)  // a - b as one fma: b * -1 + a
+{
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Window sums relative to a reference (r_F, r_W), packed by image:
+// s1 = (sum f, sum w), s2 = (sum f^2, sum w^2), fw = sum f w, with
+// f = F - r_F and w = W - r_W.
+struct Mom {
+    float2 s1, s2;
+    float fw;
 };
 
-// The sums of a partial window (relative to its centre (af, aw), n points)
-// converted to the reference (bf, bw); returned, not accumulated.
-__device__ __forceinline__ Sums shifted(float t1f, float t1w, float t2f, float t2w, float tfw,
-                                        float af, float aw, float bf, float bw, float n)
+__device__ __forceinline__ Mom mom_zero()
 {
-    const float d = af - bf, e = aw - bw;
-    Sums o;
-    o.s1f = fmaf(n, d, t1f);
-    o.s1w = fmaf(n, e, t1w);
-    o.s2f = fmaf(d, fmaf(n, d, 2.0f * t1f), t2f);
-    o.s2w = fmaf(e, fmaf(n, e, 2.0f * t1w), t2w);
-    o.sfw = fmaf(d, fmaf(n, e, t1w), fmaf(e, t1f, tfw));
+    return Mom{make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
+}
+
+__device__ __forceinline__ void mom_add(Mom &S, const Mom &t)
+{
+    S.s1 = f2add(S.s1, t.s1);
+    S.s2 = f2add(S.s2, t.s2);
+    S.fw += t.fw;
+}
+
+// S + t - u: the window slides by one input
+__device__ __forceinline__ void mom_slide(Mom &S, const Mom &t, const Mom &u)
+{
+    S.s1 = f2add(S.s1, f2sub(t.s1, u.s1));
+    S.s2 = f2add(S.s2, f2sub(t.s2, u.s2));
+    S.fw += t.fw - u.fw;
+}
+
+// Sums of a partial window of n points relative to a = (a_F, a_W),
+// converted to the reference b (exact in real arithmetic):
+//   s1' = s1 + n d,  s2' = s2 + d (s1 + s1'),  fw' = fw + d_F s1_W + d_W s1_F'
+// with d = a - b.
+__device__ __forceinline__ Mom mom_conv(const Mom &t, float2 a, float2 b, float2 n)
+{
+    const float2 d = f2sub(a, b);
+    Mom o;
+    o.s1 = f2fma(n, d, t.s1);
+    o.s2 = f2fma(d, f2add(t.s1, o.s1), t.s2);
+    o.fw = fmaf(d.x, t.s1.y, fmaf(d.y, o.s1.x, t.fw));
     return o;
 }
 
-__device__ __forceinline__ void add_to(Sums &S, const Sums &t)
-{
-    S.s1f += t.s1f;
-    S.s1w += t.s1w;
-    S.s2f += t.s2f;
-    S.s2w += t.s2w;
-    S.sfw += t.sfw;
-}
-
-// Registers a k_lcc_stats thread carries from slice to slice.
-template <int KL>
-struct StatsCarry {
-    float pf[KL], pw[KL];  // prefetched slice: F, W
-    uint8_t pm[KL];        // and the mask
-    float rho_sum, cnt;
+// Tile of k_lcc_stats: TX x TY output columns streamed along z. The input
+// region (the tile and its R halo, LX x LY columns) of a slice is staged in
+// a ring of NS slots as two planes (F, masked W) of LY rows of LXT floats:
+// staged column c holds x = x0 - 4 + c (a TMA row starts on 16 bytes), so
+// input column lx sits at c = lx + XOFF. Runs of GX outputs of a row (GY of
+// a column) share a reference, at run offset OX (OY). The x-run sums are
+// double-buffered: the x runs of slice z and the y runs of slice z - 1 run
+// at the same time, on separate warps.
+template <int D, int R>
+struct LccS {
+    static constexpr int TX = 32, TY = 16, THREADS = 512;
+    static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
+    static constexpr int GX = (R >= 2) ? 4 : 2, OX = GX / 2;
+    static constexpr int GY = 2, OY = 1;
+    static constexpr int NFX = GX + 2 * R, NFY = GY + 2 * R;  // inputs of a run
+    static constexpr int NGX = TX / GX, NGY = TY / GY;
+    static constexpr int LX = TX + 2 * R, LY = TY + 2 * R, NL = LX * LY;
+    static constexpr int LXT = 40, XOFF = 4 - R;
+    static constexpr int P = (D == 3) ? 2 : 0;   // slices loaded ahead of use
+    static constexpr int NS = NR + P;            // ring slots
+    static constexpr int LXP = LX + 1, XP = TX + 1;  // odd row pitches: conflict-free runs
+    static constexpr int KL = (NL + THREADS - 1) / THREADS;  // columns per thread
+    static constexpr int NXT = NGX * LY, NYT = TX * NGY;     // x-run and y-run threads
+    static constexpr int Y0 = THREADS - NYT;                 // first y-run thread
+    static constexpr int ZC = (D == 3) ? 64 : 1;  // most output slices per block
+    static constexpr double HALO = 0.1;  // a halo slice is only staged (relative cost)
+    static constexpr int BOX = LY * LXT * 4;              // bytes of one plane's TMA box
+    static constexpr int PLANE = (BOX + 127) / 128 * 128;  // a tensor copy lands on 128 bytes
+    static constexpr int SLOT = 2 * PLANE;
+    // shared memory (bytes from a 128-byte aligned base): the ring; z sums of
+    // the input columns (Zq = (s1, s2) as float4, Zf = fw); two buffers of
+    // x-run sums (Xq, Xf) and of the runs' references (XR); the mbarriers
+    static constexpr int oRing = 0;
+    static constexpr int oZq = oRing + NS * SLOT;
+    static constexpr int oZf = oZq + LY * LXP * 16;
+    static constexpr int XBUF = (LY * XP * 20 + LY * NGX * 8 + 15) / 16 * 16;
+    static constexpr int oX = (oZf + LY * LXP * 4 + 15) / 16 * 16;  // + b * XBUF: Xq, Xf, XR
+    static constexpr int oBar = (oX + 2 * XBUF + 7) / 8 * 8;
+    static constexpr size_t smem = (size_t)oBar + NS * 8 + 128;  // + base alignment slack
+    static_assert(TX % GX == 0 && TY % GY == 0 && (LX % 2) == 0, "tile of runs");
+    static_assert(OX <= R && GX - 1 - OX <= R && OY <= R && GY - 1 - OY <= R,
+                  "a run's reference lies in all its windows");
+    static_assert(R >= 1 && R <= 4 && XOFF + LX <= LXT, "staged row covers the halo");
+    static_assert(NXT <= THREADS && NYT <= THREADS && (LY * XP * 20) % 8 == 0,
+                  "one run per thread (x runs and y runs on separate threads where they fit)");
+    static_assert(PLANE % 128 == 0 && SLOT % 128 == 0 && XBUF % 16 == 0,
+                  "TMA destinations on 128 bytes, float4 rows on 16");
 };
 
+// Stage slice k (local index; z = its slice) of a block into ring slot s:
+// one TMA box per plane, or (unaligned rows) per-thread cp.async with zero
+// fill, each thread arriving on the slot's mbarrier when its copies land.
+template <int D, int R, bool TMA>
+__device__ __forceinline__ void lcc_stage(const CUtensorMap *mapF, const CUtensorMap *mapW,
+                                          const Grid &g, const float *__restrict__ F,
+                                          const float *__restrict__ Wm, uint32_t sbase, int k,
+                                          int s, int x0, int y0, int z)
+{
+    using C = LccS<D, R>;
+    const uint32_t dst = sbase + C::oRing + s * C::SLOT, bar = sbase + C::oBar + 8 * s;
+    const bool drop = (k == c_lcc_drop_slice);
+    if constexpr (TMA) {
+        if (threadIdx.x != 0 || drop)
+            return;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)(2 * C::BOX))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+            "l"(reinterpret_cast<uint64_t>(mapF)), "r"(x0 - 4), "r"(y0 - R), "r"(z), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst + C::PLANE),
+            "l"(reinterpret_cast<uint64_t>(mapW)), "r"(x0 - 4), "r"(y0 - R), "r"(z), "r"(bar)
+            : "memory");
+    } else {
+        if (drop)
+            return;
+        const bool zin = z >= 0 && z < g.Z;
+#pragma unroll
+        for (int q = 0; q < C::KL; ++q) {
+            const int e = threadIdx.x + q * C::THREADS;
+            if (e < C::NL) {
+                const int ly = e / C::LX, lx = e - ly * C::LX;
+                const int x = x0 - R + lx, y = y0 - R + ly;
+                const bool in = zin && x >= 0 && x < g.X && y >= 0 && y < g.Y;
+                const int64_t v = in ? ((int64_t)z * g.Y + y) * g.X + x : 0;
+                const uint32_t o = (uint32_t)(ly * C::LXT + lx + C::XOFF) * 4u;
+                const uint32_t n = in ? 4u : 0u;  // 0: fill with zeros
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + o),
+                             "l"(F + v), "r"(n)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + C::PLANE + o),
+                             "l"(Wm + v), "r"(n)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+    }
+}
+
+// Statistics of one output voxel from its window sums S (relative to the
+// reference b): adds rho to the thread's partials, returns (a', b, c).
+__device__ __forceinline__ float3 lcc_coefs(const Mom &S, float2 b, float inv_n, float eps,
+                                            float &rho_sum, float &cnt)
+{
+    const float2 v2 = f2fma(__fmul2_rn(S.s1, S.s1), make_float2(-inv_n, -inv_n), S.s2);
+    const float cov = fmaf(-S.s1.x * S.s1.y, inv_n, S.fw);
+    const float vf = fmaxf(v2.x, 0.0f), vw = fmaxf(v2.y, 0.0f);
+    const float Dd = fmaf(vf, vw, eps);
+    const float rs = rsqrtf(Dd);
+    const float rs3 = rs * rs * rs;
+    const float cb = 0.5f * cov * vf * rs3;  // -drho/dS_WW
+    const float cc = -rs;                    // -drho/dS_FW
+    const float a = (S.s1.x * rs - cov * vf * S.s1.y * rs3) * inv_n;  // -drho/dS_W
+    rho_sum += cov * rs;
+    cnt += 1.0f;
+    return make_float3(a - 2.0f * b.y * cb - b.x * cc, cb, cc);
+}
+
+// The x runs of one output slice: thread t < NXT takes row ly = t % LY and
+// run gx = t / LY (consecutive lanes, consecutive rows), converts the NFX z
+// sums of its columns to the reference of the run's column OX (read, like
+// the columns' own references, from the ring's slot rs of the z group's
+// middle slice) and writes the GX window sums and the reference to buffer X.
 template <int D, int R>
-__device__ __forceinline__ void lcc_stats_prefetch(const Grid &g, int zi, int x0, int y0,
-                                                   const float *__restrict__ F,
-                                                   const float *__restrict__ W,
-                                                   const uint8_t *__restrict__ m,
-                                                   StatsCarry<LccA<D, R>::KL> &st)
+__device__ __forceinline__ void lcc_xruns(int t, const float *ringr, const float4 *Zq,
+                                          const float *Zf, unsigned char *X, float2 n1)
 {
-    using C = LccA<D, R>;
-    const int tid = threadIdx.x;
-    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
-    const bool zin = zi >= 0 && zi < g.Z;
+    using C = LccS<D, R>;
+    constexpr int GX = C::GX, W1 = C::W1, LXT = C::LXT, PL = C::PLANE / 4;
+    float4 *Xq = reinterpret_cast<float4 *>(X);
+    float *Xf = reinterpret_cast<float *>(X + C::LY * C::XP * 16);
+    float2 *XR = reinterpret_cast<float2 *>(X + C::LY * C::XP * 20);
+    const int ly = t % C::LY, gx = t / C::LY;
+    const int rb = ly * C::LXP + GX * gx, sb = ly * LXT + GX * gx + C::XOFF;
+    const float2 b = make_float2(ringr[sb + C::OX + R], ringr[PL + sb + C::OX + R]);
+    Mom acc = mom_zero(), keep[GX - 1];
 #pragma unroll
-    for (int k = 0; k < C::KL; ++k) {
-        const int e = tid + k * C::THREADS;
-        st.pf[k] = 0.0f;
-        st.pw[k] = 0.0f;
-        st.pm[k] = 0;
-        if (e < C::NL) {
-            const int ly = e / C::LX, lx = e - ly * C::LX;
-            const int x = x0 - R + lx, y = y0 - R + ly;
-            if (zin && x >= 0 && x < g.X && y >= 0 && y < g.Y) {
-                const int64_t v = (int64_t)zi * sZ + (int64_t)y * sY + x;
-                st.pm[k] = __ldg(m + v);
-                st.pf[k] = __ldg(F + v);
-                st.pw[k] = __ldg(W + v);  // masked when staged (no dependent load)
-            }
+    for (int k = 0; k < C::NFX; ++k) {
+        const float4 t4 = Zq[rb + k];
+        const Mom tm{make_float2(t4.x, t4.y), make_float2(t4.z, t4.w), Zf[rb + k]};
+        const Mom c = mom_conv(tm, make_float2(ringr[sb + k], ringr[PL + sb + k]), b, n1);
+        if (k < GX - 1)
+            keep[k] = c;
+        if (k < W1)
+            mom_add(acc, c);
+        else
+            mom_slide(acc, c, keep[k - W1]);
+        if (k >= W1 - 1) {
+            const int o = ly * C::XP + GX * gx + k - (W1 - 1);
+            Xq[o] = make_float4(acc.s1.x, acc.s1.y, acc.s2.x, acc.s2.y);
+            Xf[o] = acc.fw;
         }
     }
+    XR[ly * C::NGX + gx] = b;
 }
 
-// One input slice zi of k_lcc_stats. P is its ring slot (compile time), so
-// every ring address below is a constant offset.
-template <int D, int R, int P>
-__device__ __forceinline__ void lcc_stats_step(const Grid &g, float eps, int zi, int zc0,
-                                               int zi_end, int x0, int y0,
-                                               const float *__restrict__ F,
-                                               const float *__restrict__ W,
-                                               const uint8_t *__restrict__ m,
-                                               float *__restrict__ coef, float *sm,
-                                               StatsCarry<LccA<D, R>::KL> &st)
+// The y runs of one output slice: thread t < NYT takes column x = t % TX and
+// run hy = t / TX, converts the NFY x-run sums of its rows to the reference
+// of the run's row OY and evaluates the statistics of its GY voxels
+// (mask bits mk, first voxel index v, the next one v + X).
+template <int D, int R>
+__device__ __forceinline__ void lcc_yruns(int t, const Grid &g, const unsigned char *X,
+                                          unsigned mk, int64_t v, int gxv, int gyv0, float2 n2,
+                                          float inv_n, float eps, int64_t pl,
+                                          float *__restrict__ coef, float &rho_sum, float &cnt)
 {
-    using C = LccA<D, R>;
-    constexpr int NL = C::NL, NX = C::NX, NC = C::NC, LX = C::LX, TX = C::TX, NR = C::NR;
-    constexpr int W1 = C::W1, RZ = C::RZ;
-    constexpr int OLDEST = (P + 1) % NR, CS = (P + 1 + RZ) % NR;  // slots
-    float2 *rFW = reinterpret_cast<float2 *>(sm + C::oRFW);
-    float *Zs = sm + C::oZ, *Xs = sm + C::oX;
-    uint8_t *rM = reinterpret_cast<uint8_t *>(sm + C::oM);
-    const int tid = threadIdx.x;
-    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
-    const float n1 = (float)NR, n2 = (float)(NR * W1), n3 = (float)(NR * W1 * W1);
-    const float inv_n = 1.0f / n3;
+    using C = LccS<D, R>;
+    constexpr int GY = C::GY, W1 = C::W1;
+    const float4 *Xq = reinterpret_cast<const float4 *>(X);
+    const float *Xf = reinterpret_cast<const float *>(X + C::LY * C::XP * 16);
+    const float2 *XR = reinterpret_cast<const float2 *>(X + C::LY * C::XP * 20);
+    const int x = t % C::TX, hy = t / C::TX, gx = x / C::GX;
+    const float2 b = XR[(GY * hy + C::OY + R) * C::NGX + gx];
+    Mom acc = mom_zero(), keep[GY - 1];
 #pragma unroll
-    for (int k = 0; k < C::KL; ++k) {
-        const int e = tid + k * C::THREADS;
-        if (e < NL) {
-            rFW[P * NL + e] = make_float2(st.pf[k], st.pm[k] ? st.pw[k] : 0.0f);
-            rM[P * NL + e] = st.pm[k];
-        }
-    }
-    if (zi + 1 < zi_end)
-        lcc_stats_prefetch<D, R>(g, zi + 1, x0, y0, F, W, m, st);  // in flight meanwhile
-    __syncthreads();
-    const int zc = zi - RZ;
-    if (zc >= zc0) {
-        // ---- z sums of every column, relative to the column's centre value
-        for (int e = tid; e < NL; e += C::THREADS) {
-            const float2 a = rFW[CS * NL + e];
-            float s1f = 0.f, s1w = 0.f, s2f = 0.f, s2w = 0.f, sfw = 0.f;
-#pragma unroll
-            for (int t = 0; t < NR; ++t) {
-                const float2 q = rFW[((OLDEST + t) % NR) * NL + e];
-                const float f = q.x - a.x, w = q.y - a.y;
-                s1f += f;
-                s1w += w;
-                s2f = fmaf(f, f, s2f);
-                s2w = fmaf(w, w, s2w);
-                sfw = fmaf(f, w, sfw);
-            }
-            Zs[0 * NL + e] = s1f;
-            Zs[1 * NL + e] = s1w;
-            Zs[2 * NL + e] = s2f;
-            Zs[3 * NL + e] = s2w;
-            Zs[4 * NL + e] = sfw;
-            Zs[5 * NL + e] = a.x;
-            Zs[6 * NL + e] = a.y;
-        }
-        __syncthreads();
-        // ---- merge along x, two neighbouring outputs per thread sharing
-        //      W1 - 1 of their columns: outputs (ly, tx) and (ly, tx + 1).
-        //      The W1 + 1 columns (read as float2 pairs from every plane) are
-        //      shifted once, to the centre of the first output, and summed
-        //      into both windows; the second window is then shifted to its
-        //      own centre.
-        for (int e = tid; e < NX / 2; e += C::THREADS) {
-            const int ly = e / (TX / 2), tx = 2 * (e - ly * (TX / 2));
-            const int base = ly * LX + tx;
-            const float bf0 = Zs[5 * NL + base + R], bw0 = Zs[6 * NL + base + R];
-            const float bf1 = Zs[5 * NL + base + R + 1], bw1 = Zs[6 * NL + base + R + 1];
-            Sums S0{0.f, 0.f, 0.f, 0.f, 0.f}, S1{0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int d2 = 0; d2 <= W1; d2 += 2) {
-                float2 q[7];
-#pragma unroll
-                for (int k = 0; k < 7; ++k)
-                    q[k] = *reinterpret_cast<const float2 *>(Zs + k * NL + base + d2);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int d = d2 + h;
-                    const Sums t = h == 0 ? shifted(q[0].x, q[1].x, q[2].x, q[3].x, q[4].x, q[5].x,
-                                                    q[6].x, bf0, bw0, n1)
-                                          : shifted(q[0].y, q[1].y, q[2].y, q[3].y, q[4].y, q[5].y,
-                                                    q[6].y, bf0, bw0, n1);
-                    if (d < W1)
-                        add_to(S0, t);
-                    if (d > 0)
-                        add_to(S1, t);
-                }
-            }
-            S1 = shifted(S1.s1f, S1.s1w, S1.s2f, S1.s2w, S1.sfw, bf0, bw0, bf1, bw1, n2);
-            const int o = ly * TX + tx;
-            *reinterpret_cast<float2 *>(Xs + 0 * NX + o) = make_float2(S0.s1f, S1.s1f);
-            *reinterpret_cast<float2 *>(Xs + 1 * NX + o) = make_float2(S0.s1w, S1.s1w);
-            *reinterpret_cast<float2 *>(Xs + 2 * NX + o) = make_float2(S0.s2f, S1.s2f);
-            *reinterpret_cast<float2 *>(Xs + 3 * NX + o) = make_float2(S0.s2w, S1.s2w);
-            *reinterpret_cast<float2 *>(Xs + 4 * NX + o) = make_float2(S0.sfw, S1.sfw);
-        }
-        __syncthreads();
-        // ---- merge along y (two outputs per thread, rows ty and ty + 1)
-        //      and evaluate the statistics of the core voxels
-        for (int e = tid; e < NC / 2; e += C::THREADS) {
-            const int tp = e / TX, tx = e - tp * TX;
-            const int ty0 = 2 * tp;
-            float bfv[2], bwv[2];
-            bool on[2];
-            int64_t vv[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int ty = ty0 + h, x = x0 + tx, y = y0 + ty;
-                const int zcol = (ty + R) * LX + tx + R;
-                on[h] = x < g.X && y < g.Y && rM[CS * NL + zcol];
-                vv[h] = (int64_t)zc * sZ + (int64_t)y * sY + x;
-                bfv[h] = Zs[5 * NL + zcol];
-                bwv[h] = Zs[6 * NL + zcol];
-            }
-            // rows shifted once to the first output's centre, summed into
-            // both windows; the second window shifted to its own centre
-            Sums S[2] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-            for (int d = 0; d <= W1; ++d) {
-                const int r = (ty0 + d) * TX + tx;
-                const int zrow = (ty0 + d) * LX + tx + R;
-                const Sums t = shifted(Xs[r], Xs[NX + r], Xs[2 * NX + r], Xs[3 * NX + r],
-                                       Xs[4 * NX + r], Zs[5 * NL + zrow], Zs[6 * NL + zrow],
-                                       bfv[0], bwv[0], n2);
-                if (d < W1)
-                    add_to(S[0], t);
-                if (d > 0)
-                    add_to(S[1], t);
-            }
-            S[1] = shifted(S[1].s1f, S[1].s1w, S[1].s2f, S[1].s2w, S[1].sfw, bfv[0], bwv[0],
-                           bfv[1], bwv[1], n3);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = x0 + tx, y = y0 + ty0 + h;
-                if (x >= g.X || y >= g.Y)
-                    continue;
-                float ca = 0.f, cb = 0.f, cc = 0.f;
-                if (on[h]) {
-                    const Sums &T = S[h];
-                    const float cov = fmaf(-T.s1f * T.s1w, inv_n, T.sfw);
-                    const float vf = fmaf(-T.s1f * T.s1f, inv_n, T.s2f);
-                    const float vw = fmaf(-T.s1w * T.s1w, inv_n, T.s2w);
-                    const float Dd = fmaf(vf, vw, eps);
-                    const float rs = rsqrtf(Dd);
-                    const float rs3 = rs * rs * rs;
-                    const float rho = cov * rs;
-                    cb = 0.5f * cov * vf * rs3;  // -drho/dS_WW
-                    cc = -rs;                    // -drho/dS_FW
-                    const float a = (T.s1f * rs - cov * vf * T.s1w * rs3) * inv_n;  // -drho/dS_W
-                    ca = a - 2.0f * bwv[h] * cb - bfv[h] * cc;
-                    st.rho_sum += rho;
-                    st.cnt += 1.0f;
-                }
+    for (int k = 0; k < C::NFY; ++k) {
+        const int ly = GY * hy + k;
+        const float4 t4 = Xq[ly * C::XP + x];
+        const Mom tm{make_float2(t4.x, t4.y), make_float2(t4.z, t4.w), Xf[ly * C::XP + x]};
+        const Mom c = mom_conv(tm, XR[ly * C::NGX + gx], b, n2);
+        if (k < GY - 1)
+            keep[k] = c;
+        if (k < W1)
+            mom_add(acc, c);
+        else
+            mom_slide(acc, c, keep[k - W1]);
+        if (k >= W1 - 1) {
+            const int j = k - (W1 - 1);
+            if (gxv < g.X && gyv0 + j < g.Y) {
+                float3 cf = make_float3(0.f, 0.f, 0.f);
+                if ((mk >> j) & 1u)
+                    cf = lcc_coefs(acc, b, inv_n, eps, rho_sum, cnt);
                 if (coef) {
-                    const int64_t pl = lcc_plane(g.nv);
-                    coef[vv[h]] = ca;
-                    coef[pl + vv[h]] = cb;
-                    coef[2 * pl + vv[h]] = cc;
+                    const int64_t vj = v + (int64_t)j * g.X;
+                    coef[vj] = cf.x;
+                    coef[pl + vj] = cf.y;
+                    coef[2 * pl + vj] = cf.z;
                 }
             }
-        }
-    }
-    __syncthreads();
-}
-
-template <int D, int R, int P>
-__device__ __forceinline__ void lcc_stats_steps(const Grid &g, float eps, int zb, int zc0,
-                                                int zi_end, int x0, int y0,
-                                                const float *__restrict__ F,
-                                                const float *__restrict__ W,
-                                                const uint8_t *__restrict__ m,
-                                                float *__restrict__ coef, float *sm,
-                                                StatsCarry<LccA<D, R>::KL> &st)
-{
-    if constexpr (P < LccA<D, R>::NR) {
-        if (zb + P < zi_end) {
-            lcc_stats_step<D, R, P>(g, eps, zb + P, zc0, zi_end, x0, y0, F, W, m, coef, sm, st);
-            lcc_stats_steps<D, R, P + 1>(g, eps, zb, zc0, zi_end, x0, y0, F, W, m, coef, sm, st);
         }
     }
 }
 
 // Window statistics of a tile of 32 x 16 columns streamed along z in chunks
-// of zc output slices: the ring holds the last 2R+1 input slices (slice zi in
-// slot (zi - first) mod (2R+1)).
-template <int D, int R>
-__global__ void __launch_bounds__(LccA<D, R>::THREADS, 2)
-    k_lcc_stats(Grid g, int zc, float eps, const float *__restrict__ F,
-                const float *__restrict__ W, const uint8_t *__restrict__ m,
+// of zc output slices (W masked: zero off the mask). Per output slice z:
+//   A: z sums of every input column (all threads; restarted at the first
+//      slice of each group of NR, else slid by one slice) -> barrier ->
+//   B: x runs of slice z (NXT threads) while the y runs and the statistics
+//      of slice z - 1 run on the last NYT threads -> barrier,
+// and the y runs of the chunk's last slice after the loop. The ring holds
+// slices up to z + RZ + P. A slice that does not arrive within about a
+// second records AL_ERR_TIMEOUT and ends the block (after the copies in
+// flight have landed).
+template <int D, int R, bool TMA>
+__global__ void __launch_bounds__(LccS<D, R>::THREADS, 2)
+    k_lcc_stats(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapW,
+                Grid g, int zc, float eps, const float *__restrict__ F,
+                const float *__restrict__ Wm, const uint8_t *__restrict__ m,
                 float *__restrict__ coef, double *__restrict__ part)
 {
-    using C = LccA<D, R>;
-    extern __shared__ float sm[];
+    using C = LccS<D, R>;
+    constexpr int NS = C::NS, NR = C::NR, RZ = C::RZ, W1 = C::W1, PL = C::PLANE / 4;
+    constexpr int LX = C::LX, LXT = C::LXT, LXP = C::LXP, TX = C::TX;
+    extern __shared__ unsigned char lsm_raw[];
+    unsigned char *sm = lsm_raw + ((128u - (lsm_u32(lsm_raw) & 127u)) & 127u);
     __shared__ double red[2 * C::THREADS / 32];
-    const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+    const uint32_t sbase = lsm_u32(sm);
+    const float *ring = reinterpret_cast<const float *>(sm + C::oRing);
+    float4 *Zq = reinterpret_cast<float4 *>(sm + C::oZq);
+    float *Zf = reinterpret_cast<float *>(sm + C::oZf);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * C::TY;
     const int zc0 = blockIdx.z * zc, zc1 = min(zc0 + zc, g.Z);
-    StatsCarry<C::KL> st;
-    st.rho_sum = 0.0f;
-    st.cnt = 0.0f;
-    const int zs = zc0 - C::RZ, zi_end = zc1 + C::RZ;
-    lcc_stats_prefetch<D, R>(g, zs, x0, y0, F, W, m, st);
-    for (int zb = zs; zb < zi_end; zb += C::NR)
-        lcc_stats_steps<D, R, 0>(g, eps, zb, zc0, zi_end, x0, y0, F, W, m, coef, sm, st);
-    double acc[2] = {st.rho_sum, st.cnt};
+    const int zs = zc0 - RZ, nsl = zc1 + RZ - zs;  // input slices zs .. zs + nsl - 1
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sbase + C::oBar + 8 * k),
+                         "r"(TMA ? 1 : C::THREADS)
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    for (int k = 0; k < NS && k < nsl; ++k)
+        lcc_stage<D, R, TMA>(&mapF, &mapW, g, F, Wm, sbase, k, k, x0, y0, zs + k);
+    // the thread's input columns: staged offset and z-sum offset
+    int ro[C::KL], pe[C::KL];
+#pragma unroll
+    for (int q = 0; q < C::KL; ++q) {
+        const int e = tid + q * C::THREADS;
+        const int ly = e / LX, lx = e - ly * LX;
+        ro[q] = e < C::NL ? ly * LXT + lx + C::XOFF : -1;
+        pe[q] = ly * LXP + lx;
+    }
+    Mom zsum[C::KL];
+#pragma unroll
+    for (int q = 0; q < C::KL; ++q)
+        zsum[q] = mom_zero();
+    // y-run threads: their column, first row, voxel index and mask bits of
+    // the output slice they do next (loaded one slice ahead)
+    const int ty = tid - C::Y0;
+    const bool ythr = ty >= 0;
+    const int yx = ythr ? ty % TX : 0, gxv = x0 + yx, gyv0 = y0 + C::GY * (ythr ? ty / TX : 0);
+    const int64_t sxy = (int64_t)g.X * g.Y;
+    int64_t yv = ((int64_t)zc0 * g.Y + gyv0) * g.X + gxv;  // voxel of the y thread's slice
+    unsigned ymask = 0;
+    auto load_mask = [&](int64_t v) {
+        unsigned mk = 0;
+#pragma unroll
+        for (int j = 0; j < C::GY; ++j)
+            if (gxv < g.X && gyv0 + j < g.Y && __ldg(m + v + (int64_t)j * g.X))
+                mk |= 1u << j;
+        return mk;
+    };
+    if (ythr)
+        ymask = load_mask(yv);
+    const float2 n1 = make_float2((float)NR, (float)NR);
+    const float2 n2 = make_float2((float)(NR * W1), (float)(NR * W1));
+    const float inv_n = 1.0f / (float)(NR * W1 * W1);
+    const int64_t pl = lcc_plane(g.nv);
+    float rho_sum = 0.0f, cnt = 0.0f;
+    int kfail = -1, iss = min(NS, nsl);  // first unconfirmed slice on failure, slices issued
+    int snew = 2 * RZ % NS, sold = NS - 1, sref = 0;  // ring slots: slice z + RZ, z - RZ - 1, ref
+    int nz = zc1 - zc0;
+    for (int i = 0; i < nz; ++i) {
+        // ---- A: the window's slices (all of them first, then the new one)
+        bool ok = true;
+        {
+            const int k0 = i == 0 ? 0 : 2 * RZ + i;
+            int sk = i == 0 ? 0 : snew;
+            for (int k = k0; k <= 2 * RZ + i; ++k, sk = sk + 1 == NS ? 0 : sk + 1) {
+                const uint32_t bar = sbase + C::oBar + 8 * sk, par = (uint32_t)(k / NS) & 1u;
+                if (!lbar_try_wait(bar, par))
+                    ok &= lbar_wait(bar, par);
+            }
+        }
+        const bool restart = i % NR == 0;
+        if (restart)
+            sref = snew;  // reference slice of the group: its middle slice z + RZ
+        const float *Fn = ring + snew * (C::SLOT / 4), *Fo = ring + sold * (C::SLOT / 4);
+        const float *Fr = ring + sref * (C::SLOT / 4);
+#pragma unroll
+        for (int q = 0; q < C::KL; ++q) {
+            if (ro[q] < 0)
+                continue;
+            Mom &S = zsum[q];
+            const float2 r = make_float2(Fr[ro[q]], Fr[PL + ro[q]]);
+            if (restart) {
+                S = mom_zero();
+                int st = sold;  // slices z - RZ .. z + RZ follow slice z - RZ - 1
+#pragma unroll
+                for (int tt = 0; tt < NR; ++tt) {
+                    st = st + 1 == NS ? 0 : st + 1;
+                    const float *Ft = ring + st * (C::SLOT / 4);
+                    const float2 d = f2sub(make_float2(Ft[ro[q]], Ft[PL + ro[q]]), r);
+                    S.s1 = f2add(S.s1, d);
+                    S.s2 = f2fma(d, d, S.s2);
+                    S.fw = fmaf(d.x, d.y, S.fw);
+                }
+            } else {
+                const float2 fn = f2sub(make_float2(Fn[ro[q]], Fn[PL + ro[q]]), r);
+                const float2 fo = f2sub(make_float2(Fo[ro[q]], Fo[PL + ro[q]]), r);
+                const float2 dd = f2sub(fn, fo), ss = f2add(fn, fo);
+                S.s1 = f2add(S.s1, dd);
+                S.s2 = f2fma(dd, ss, S.s2);
+                S.fw = fmaf(fn.x, fn.y, fmaf(-fo.x, fo.y, S.fw));
+            }
+            Zq[pe[q]] = make_float4(S.s1.x, S.s1.y, S.s2.x, S.s2.y);
+            Zf[pe[q]] = S.fw;
+        }
+        if (__syncthreads_or(!ok)) {
+            kfail = i == 0 ? 0 : 2 * RZ + i;
+            break;
+        }
+        // the slot of slice z - RZ - 1 (local i - 1) is free: refill it
+        if (i > 0 && i - 1 + NS < nsl) {
+            if (TMA && tid == 0)  // the slot was read through the generic proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            lcc_stage<D, R, TMA>(&mapF, &mapW, g, F, Wm, sbase, i - 1 + NS, sold, x0, y0,
+                                 zs + i - 1 + NS);
+            iss = i + NS;
+        }
+        // ---- B: x runs of slice z, y runs of slice z - 1
+        unsigned char *Xb = sm + C::oX + (i & 1) * C::XBUF;
+        if (tid < C::NXT)
+            lcc_xruns<D, R>(tid, Fr, Zq, Zf, Xb, n1);
+        if (ythr && i > 0) {
+            lcc_yruns<D, R>(ty, g, sm + C::oX + ((i - 1) & 1) * C::XBUF, ymask, yv, gxv, gyv0,
+                            n2, inv_n, eps, pl, coef, rho_sum, cnt);
+            yv += sxy;
+            if (i < nz)
+                ymask = load_mask(yv);
+        }
+        __syncthreads();
+        snew = snew + 1 == NS ? 0 : snew + 1;
+        sold = sold + 1 == NS ? 0 : sold + 1;
+    }
+    if (kfail >= 0) {
+        // a slice timed out: record it and let the copies in flight land
+        // before the block's shared memory goes
+        if (TMA) {
+            if (tid == 0) {
+                atomicExch(&g_unit_error, kErrTimeout);
+                for (int k = kfail; k < iss; ++k)
+                    lbar_wait(sbase + C::oBar + 8 * (k % NS), (uint32_t)(k / NS) & 1u);
+            }
+        } else {
+            if (tid == 0)
+                atomicExch(&g_unit_error, kErrTimeout);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        }
+        return;
+    }
+    // ---- the y runs of the chunk's last slice
+    if (ythr && nz > 0)
+        lcc_yruns<D, R>(ty, g, sm + C::oX + ((nz - 1) & 1) * C::XBUF, ymask, yv, gxv, gyv0, n2,
+                        inv_n, eps, pl, coef, rho_sum, cnt);
+    double acc[2] = {rho_sum, cnt};
     block_reduce_d<2>(acc, red);
     if (threadIdx.x == 0) {
         const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -591,46 +782,6 @@ __global__ void __launch_bounds__(LccB<D, R>::THREADS, 2)
 }
 
 // ---- TMA-staged variant ----------------------------------------------------
-constexpr int kErrTimeout = 6;  // AL_ERR_TIMEOUT
-
-__device__ __forceinline__ uint32_t lsm_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool lbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase of `bar` with this parity, for about one second of
-// %globaltimer at most; false if it did not complete.
-__device__ __noinline__ bool lbar_wait(uint32_t bar, uint32_t parity)
-{
-    if (lbar_try_wait(bar, parity))
-        return true;
-    uint64_t t0, t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    while (!lbar_try_wait(bar, parity)) {
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 1000000000ull)
-            return false;
-    }
-    return true;
-}
-
-// Test of the bounded waits of k_lcc_grad_tma: the slice (index within each
-// block's z range) whose load is not issued, so the wait for it runs out;
-// -1 = none.
-__constant__ int c_lcc_drop_slice = -1;
-
 // Issue the TMA load of slice k of the block's z range into ring slot k % NS.
 template <int D, int R>
 __device__ __forceinline__ void lcc_tma_issue(const CUtensorMap *map, uint32_t sbase, int k,
@@ -837,18 +988,19 @@ __global__ void __launch_bounds__(LccT<D, R>::THREADS, 2)
 }
 
 // z chunk (output slices per block) of an LCC kernel. The blocks of a launch
-// do equal work and run in waves of 2 x 152 (two resident blocks per SM of
-// a 152-SM GB300), so the chunk minimises
+// do equal work and run in waves of 2 x sms (two resident blocks per SM), so
+// the chunk minimises
 //   waves x (chunk + 2 rz x halo),
 // halo being the cost of one of the 2 rz halo slices a chunk re-reads
 // relative to an output slice; a last wave that is barely filled costs as
-// much as a full one. At least 2 slices, at most zc_max. Depends on the grid
-// only, so workspace sizes and launches agree.
-int lcc_chunk(const Grid &g, int tiles_xy, int zc_max, int rz, double halo)
+// much as a full one. At least 2 slices, at most zc_max. Workspaces are
+// sized for the smallest chunk (lcc_max_blocks), so a workspace sized on one
+// device serves a device with any SM count.
+int lcc_chunk(const Grid &g, int tiles_xy, int zc_max, int rz, double halo, int sms)
 {
     if (g.ndim != 3)
         return 1;
-    const int64_t slots = 2 * 152;
+    const int64_t slots = 2 * (int64_t)sms;
     int best = 2;
     double best_cost = 0.0;
     for (int chunks = 1; chunks <= g.Z; ++chunks) {
@@ -871,9 +1023,9 @@ int lcc_chunk(const Grid &g, int tiles_xy, int zc_max, int rz, double halo)
 template <int D, int R>
 int lcc_stats_chunk(const Grid &g)
 {
-    using A = LccA<D, R>;
+    using A = LccS<D, R>;
     return lcc_chunk(g, ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY), A::ZC, A::RZ,
-                     A::HALO);
+                     A::HALO, device_sms());
 }
 
 // The driver's tensor-map encoder, looked up once through the runtime.
@@ -916,25 +1068,88 @@ bool lcc_coef_tmap(CUtensorMap *map, const Grid &g, const float *coef)
            CUDA_SUCCESS;
 }
 
+// Tensor map of a volume as a 3D fp32 tensor (X, Y, Z) with boxes of the
+// statistics tile's staged slice (LXT x LY x 1). False when TMA cannot
+// address it (row pitch X * 4 B not a multiple of 16 B, or an unaligned
+// base); the caller then stages by cp.async.
 template <int D, int R>
-cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, const uint8_t *m,
-                    float *gout, double *part, float *coef, cudaStream_t s)
+bool lcc_vol_tmap(CUtensorMap *map, const Grid &g, const float *p)
 {
-    using A = LccA<D, R>;
-    using B = LccB<D, R>;
-    static_assert(A::smem <= 227 * 1024 && B::smem <= 227 * 1024, "LCC tile too large");
-    cudaError_t e = cudaFuncSetAttribute(k_lcc_stats<D, R>,
+    using C = LccS<D, R>;
+    if (g.X % 4 != 0 || ((uintptr_t)p & 15u) != 0)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.X, (cuuint64_t)g.Y, (cuuint64_t)g.Z};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.X * 4, (cuuint64_t)g.X * g.Y * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)C::LXT, (cuuint32_t)C::LY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(p), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// Wm = W where the mask is set, else 0.
+__global__ void k_mask_w(int64_t nv, const float *__restrict__ W, const uint8_t *__restrict__ m,
+                         float *__restrict__ Wm)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x)
+        Wm[v] = __ldg(m + v) ? __ldg(W + v) : 0.0f;
+}
+
+template <int D, int R, bool TMA>
+cudaError_t lcc_stats_launch(const Grid &g, double eps, const CUtensorMap &mF,
+                             const CUtensorMap &mW, const float *F, const float *Wm,
+                             const uint8_t *m, float *coef, double *part, cudaStream_t s)
+{
+    using A = LccS<D, R>;
+    cudaError_t e = cudaFuncSetAttribute(k_lcc_stats<D, R, TMA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A::smem);
     if (e != cudaSuccess)
         return e;
-    {
-        const int zc = lcc_stats_chunk<D, R>(g);
-        dim3 grid((g.X + A::TX - 1) / A::TX, (g.Y + A::TY - 1) / A::TY, (g.Z + zc - 1) / zc);
-        ProfScope ps(s, "k_lcc_stats");
-        k_lcc_stats<D, R><<<grid, A::THREADS, A::smem, s>>>(g, zc, (float)eps, F, W, m,
-                                                            gout ? coef : nullptr, part);
+    const int zc = lcc_stats_chunk<D, R>(g);
+    dim3 grid((g.X + A::TX - 1) / A::TX, (g.Y + A::TY - 1) / A::TY, (g.Z + zc - 1) / zc);
+    ProfScope ps(s, "k_lcc_stats");
+    k_lcc_stats<D, R, TMA><<<grid, A::THREADS, A::smem, s>>>(mF, mW, g, zc, (float)eps, F, Wm, m,
+                                                             coef, part);
+    return cudaGetLastError();
+}
+
+template <int D, int R>
+cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, const uint8_t *m,
+                    bool w_masked, float *gout, double *part, float *coef, cudaStream_t s)
+{
+    using A = LccS<D, R>;
+    using B = LccB<D, R>;
+    static_assert(A::smem <= 113 * 1024, "two statistics tiles per SM");
+    static_assert(B::smem <= 227 * 1024, "LCC tile too large");
+    cudaError_t e;
+    const float *Wm = W;
+    if (!w_masked) {
+        // the statistics read W masked; a scratch copy goes where the
+        // gradient (or, value only, the unused coefficients) will be written
+        float *scratch = gout ? gout : coef;
+        const int th = 256;
+        int64_t nb = ((int64_t)g.nv + th - 1) / th;
+        if (nb > 8 * (int64_t)device_sms())
+            nb = 8 * (int64_t)device_sms();
+        ProfScope ps(s, "k_mask_w");
+        k_mask_w<<<(int)nb, th, 0, s>>>(g.nv, W, m, scratch);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        Wm = scratch;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess || !gout)
+    CUtensorMap mF, mW;
+    memset(&mF, 0, sizeof(mF));
+    memset(&mW, 0, sizeof(mW));
+    const bool tma_s = lcc_vol_tmap<D, R>(&mF, g, F) && lcc_vol_tmap<D, R>(&mW, g, Wm);
+    e = tma_s ? lcc_stats_launch<D, R, true>(g, eps, mF, mW, F, Wm, m, gout ? coef : nullptr, part, s)
+              : lcc_stats_launch<D, R, false>(g, eps, mF, mW, F, Wm, m, gout ? coef : nullptr, part,
+                                               s);
+    if (e != cudaSuccess || !gout)
         return e;
     using T = LccT<D, R>;
     static_assert(T::smem <= 227 * 1024 && T::TX == B::TX && T::TY == B::TY && T::ZC == B::ZC &&
@@ -950,7 +1165,7 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
         return e;
     {
         const int tiles = ((g.X + B::TX - 1) / B::TX) * ((g.Y + B::TY - 1) / B::TY);
-        const int zc = lcc_chunk(g, tiles, B::ZC, B::RZ, B::HALO);
+        const int zc = lcc_chunk(g, tiles, B::ZC, B::RZ, B::HALO, device_sms());
         dim3 grid((g.X + B::TX - 1) / B::TX, (g.Y + B::TY - 1) / B::TY, (g.Z + zc - 1) / zc);
         ProfScope ps(s, "k_lcc_grad");
         if (tma)
@@ -961,23 +1176,33 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
     return cudaGetLastError();
 }
 
+// Blocks of k_lcc_stats on the current device (chunk from its SM count), or
+// (most = true) the most any device launches: chunks of 2 slices.
 template <int D, int R>
-int lcc_blocks(const Grid &g)
+int lcc_blocks(const Grid &g, bool most)
 {
-    using A = LccA<D, R>;
-    const int zc = lcc_stats_chunk<D, R>(g);
+    using A = LccS<D, R>;
+    const int zc = most ? (g.ndim == 3 ? 2 : 1) : lcc_stats_chunk<D, R>(g);
     return ((g.X + A::TX - 1) / A::TX) * ((g.Y + A::TY - 1) / A::TY) * ((g.Z + zc - 1) / zc);
+}
+
+int lcc_blocks_any(const Grid &g, int window, bool most)
+{
+    const int R = window / 2;
+    if (g.ndim == 3)
+        return R == 1   ? lcc_blocks<3, 1>(g, most)
+               : R == 2 ? lcc_blocks<3, 2>(g, most)
+                        : lcc_blocks<3, 3>(g, most);
+    return R == 1 ? lcc_blocks<2, 1>(g, most)
+           : R == 2 ? lcc_blocks<2, 2>(g, most)
+                    : lcc_blocks<2, 3>(g, most);
 }
 
 }  // namespace
 
-int lcc_num_blocks(const Grid &g, int window)
-{
-    const int R = window / 2;
-    if (g.ndim == 3)
-        return R == 1 ? lcc_blocks<3, 1>(g) : R == 2 ? lcc_blocks<3, 2>(g) : lcc_blocks<3, 3>(g);
-    return R == 1 ? lcc_blocks<2, 1>(g) : R == 2 ? lcc_blocks<2, 2>(g) : lcc_blocks<2, 3>(g);
-}
+int lcc_num_blocks(const Grid &g, int window) { return lcc_blocks_any(g, window, false); }
+
+int lcc_max_blocks(const Grid &g, int window) { return lcc_blocks_any(g, window, true); }
 
 size_t lcc_coef_bytes(const Grid &g) { return (size_t)3 * lcc_plane(g.nv) * sizeof(float); }
 
@@ -989,17 +1214,18 @@ cudaError_t lcc_set_drop_slice(int slice)
 }
 
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,
-                       const uint8_t *m, float *gout, double *part, float *coef, cudaStream_t s)
+                       const uint8_t *m, bool w_masked, float *gout, double *part, float *coef,
+                       cudaStream_t s)
 {
     const int R = window / 2;
     if (g.ndim == 3) {
-        if (R == 1) return lcc_run<3, 1>(g, eps, F, W, m, gout, part, coef, s);
-        if (R == 2) return lcc_run<3, 2>(g, eps, F, W, m, gout, part, coef, s);
-        return lcc_run<3, 3>(g, eps, F, W, m, gout, part, coef, s);
+        if (R == 1) return lcc_run<3, 1>(g, eps, F, W, m, w_masked, gout, part, coef, s);
+        if (R == 2) return lcc_run<3, 2>(g, eps, F, W, m, w_masked, gout, part, coef, s);
+        return lcc_run<3, 3>(g, eps, F, W, m, w_masked, gout, part, coef, s);
     }
-    if (R == 1) return lcc_run<2, 1>(g, eps, F, W, m, gout, part, coef, s);
-    if (R == 2) return lcc_run<2, 2>(g, eps, F, W, m, gout, part, coef, s);
-    return lcc_run<2, 3>(g, eps, F, W, m, gout, part, coef, s);
+    if (R == 1) return lcc_run<2, 1>(g, eps, F, W, m, w_masked, gout, part, coef, s);
+    if (R == 2) return lcc_run<2, 2>(g, eps, F, W, m, w_masked, gout, part, coef, s);
+    return lcc_run<2, 3>(g, eps, F, W, m, w_masked, gout, part, coef, s);
 }
 
 }  // namespace airgb

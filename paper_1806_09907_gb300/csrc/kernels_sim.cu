@@ -203,7 +203,7 @@ size_t similarity_ws(const Grid &g, int kind, int window)
 {
     const size_t scal = 256;
     if (kind == 2)
-        return scal + align256((size_t)lcc_num_blocks(g, window) * 2 * sizeof(double)) +
+        return scal + align256((size_t)lcc_max_blocks(g, window) * 2 * sizeof(double)) +
                lcc_coef_bytes(g);
     return scal + align256((size_t)red_blocks(g.nv) * 3 * sizeof(double));
 }
@@ -230,8 +230,9 @@ cudaError_t launch_similarity(const Grid &g, int kind, int window, double eps, c
             k_ncc_grad<<<nb, th, 0, s>>>(g.nv, F, W, m, scal, grad);
     } else {
         const int lb = lcc_num_blocks(g, window);
-        float *coef = (float *)((char *)part + align256((size_t)lb * 2 * sizeof(double)));
-        cudaError_t e = launch_lcc(g, window, eps, F, W, m, grad, part, coef, s);
+        float *coef = (float *)((char *)part +
+                                align256((size_t)lcc_max_blocks(g, window) * 2 * sizeof(double)));
+        cudaError_t e = launch_lcc(g, window, eps, F, W, m, false, grad, part, coef, s);
         if (e != cudaSuccess)
             return e;
         k_lcc_finalize<<<1, 1024, 0, s>>>(part, lb, value, scal);

@@ -35,15 +35,25 @@ cudaError_t launch_similarity(const Grid &g, int kind, int window, double eps, c
                               const float *warped, const uint8_t *mask, double *value_dev,
                               float *grad_warped, void *ws, cudaStream_t s);
 
+// Streaming multiprocessors of the current device (queried once per device;
+// 152, a GB300's count, if the query fails). Sizes grids and z chunks only:
+// no workspace size depends on it.
+int device_sms();
+
 // LCC statistics + exact gradient, shared by the unfused similarity and the
 // fused objective: grad_unscaled = dS/dW * |X_m| (nullable; needs `coef`,
 // lcc_coef_bytes(g) of scratch), per-block {sum of rho over masked voxels, masked
-// voxel count} partials (lcc_num_blocks(g, window) blocks).
+// voxel count} partials (lcc_num_blocks(g, window) blocks on the current
+// device; lcc_max_blocks(g, window) bounds it on any device and sizes the
+// partials' workspace).
 int lcc_num_blocks(const Grid &g, int window);
+int lcc_max_blocks(const Grid &g, int window);
 size_t lcc_coef_bytes(const Grid &g);
+// w_masked: the warped image is already zero off the mask (else a masked
+// copy is made in grad_unscaled, or in coef when grad_unscaled is NULL).
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *fixed,
-                       const float *warped, const uint8_t *mask, float *grad_unscaled,
-                       double *block_partials, float *coef, cudaStream_t s);
+                       const float *warped, const uint8_t *mask, bool w_masked,
+                       float *grad_unscaled, double *block_partials, float *coef, cudaStream_t s);
 
 // ---- A7: fused objective -----------------------------------------------------
 bool fused_supported(const Grid &g, const Lattice &L, int kind, int window);
