@@ -246,6 +246,44 @@ __device__ __forceinline__ Interp interp4(const float (&c)[4], float fx, float f
     return r;
 }
 
+// Shared-memory address of a generic pointer into shared memory.
+__device__ __forceinline__ uint32_t al_smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One test of an mbarrier phase (parity); true once it has completed.
+__device__ __forceinline__ bool al_mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for an mbarrier phase for about one second of %globaltimer at most;
+// false if it did not complete (the caller records AL_ERR_TIMEOUT).
+__device__ __noinline__ inline bool al_mbar_wait_slow(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!al_mbar_try_wait(bar, parity)) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull)
+            return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool al_mbar_wait(uint32_t bar, uint32_t parity)
+{
+    return al_mbar_try_wait(bar, parity) || al_mbar_wait_slow(bar, parity);
+}
+
 // Deterministic block reduction of K doubles per thread (fixed tree).
 // `scratch` holds at least K * (blockDim.x / 32) doubles. Result valid in
 // thread 0 (written back into v).

@@ -955,14 +955,21 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
                                                  s);
         if (e != cudaSuccess)
             return e;
-        e = launch_lcc(g, window, eps, F, Wb, mb, true, gc ? gb : nullptr,
-                       (double *)(ws + lay.lpart),
-                       (float *)(ws + lay.coef), s);
-        if (e != cudaSuccess)
-            return e;
-        if (gc)
+        float *coef = (float *)(ws + lay.coef);
+        if (!gc) {
+            e = launch_lcc(g, window, eps, F, Wb, mb, true, nullptr, (double *)(ws + lay.lpart),
+                           coef, s);
+        } else {
+            // statistics -> coefficient planes -> dS/dW * |X_m| -> projection
+            e = launch_lcc_stats(g, window, eps, F, Wb, mb, (double *)(ws + lay.lpart), coef, s);
+            if (e != cudaSuccess)
+                return e;
+            e = launch_lcc_grad(g, window, F, Wb, mb, coef, gb, s);
+            if (e != cudaSuccess)
+                return e;
             e = run_fused_kernel<D, DELTA, MODE_GW>(g, L, lay, ws, F, M, c, gb, nullptr, nullptr,
                                                     Gb, false, s);
+        }
     }
     if (e != cudaSuccess)
         return e;

@@ -218,7 +218,9 @@ struct LccS {
     static constexpr int SLOT = 2 * PLANE;
     // shared memory (bytes from a 128-byte aligned base): the ring; z sums of
     // the input columns (Zq = (s1, s2) as float4, Zf = fw); two buffers of
-    // x-run sums (Xq, Xf) and of the runs' references (XR); the mbarriers
+    // x-run sums (Xq, Xf) and of the runs' references (XR); the mbarriers.
+    // The columns' references are read from the ring's slot of the z group's
+    // middle slice, which stays in the ring for the whole group.
     static constexpr int oRing = 0;
     static constexpr int oZq = oRing + NS * SLOT;
     static constexpr int oZf = oZq + LY * LXP * 16;
@@ -312,8 +314,8 @@ __device__ __forceinline__ float3 lcc_coefs(const Mom &S, float2 b, float inv_n,
 // The x runs of one output slice: thread t < NXT takes row ly = t % LY and
 // run gx = t / LY (consecutive lanes, consecutive rows), converts the NFX z
 // sums of its columns to the reference of the run's column OX (read, like
-// the columns' own references, from the ring's slot rs of the z group's
-// middle slice) and writes the GX window sums and the reference to buffer X.
+// the columns' own references, from the ring's slot of the z group's middle
+// slice) and writes the GX window sums and the reference to buffer X.
 template <int D, int R>
 __device__ __forceinline__ void lcc_xruns(int t, const float *ringr, const float4 *Zq,
                                           const float *Zf, unsigned char *X, float2 n1)
@@ -1119,6 +1121,10 @@ cudaError_t lcc_stats_launch(const Grid &g, double eps, const CUtensorMap &mF,
 }
 
 template <int D, int R>
+cudaError_t lcc_grad_run(const Grid &g, const float *F, const float *W, const uint8_t *m,
+                         float *gout, float *coef, cudaStream_t s);
+
+template <int D, int R>
 cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, const uint8_t *m,
                     bool w_masked, float *gout, double *part, float *coef, cudaStream_t s)
 {
@@ -1151,6 +1157,17 @@ cudaError_t lcc_run(const Grid &g, double eps, const float *F, const float *W, c
                                                s);
     if (e != cudaSuccess || !gout)
         return e;
+    return lcc_grad_run<D, R>(g, F, W, m, gout, coef, s);
+}
+
+// dS/dW * |X_m| from the coefficient planes (k_lcc_grad_tma, or k_lcc_grad
+// when the row pitch cannot be a tensor-map stride).
+template <int D, int R>
+cudaError_t lcc_grad_run(const Grid &g, const float *F, const float *W, const uint8_t *m,
+                         float *gout, float *coef, cudaStream_t s)
+{
+    using B = LccB<D, R>;
+    cudaError_t e;
     using T = LccT<D, R>;
     static_assert(T::smem <= 227 * 1024 && T::TX == B::TX && T::TY == B::TY && T::ZC == B::ZC &&
                       T::HALO == B::HALO,
@@ -1211,6 +1228,73 @@ AL_UNIT_ERROR_READER(unit_error_lcc)
 cudaError_t lcc_set_drop_slice(int slice)
 {
     return cudaMemcpyToSymbol(c_lcc_drop_slice, &slice, sizeof(int));
+}
+
+bool encode_tmap_f32(CUtensorMap *map, int rank, const uint64_t *dims, const uint64_t *strides,
+                     const uint32_t *box, const void *base)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || rank < 1 || rank > 5 || ((uintptr_t)base & 15u) != 0)
+        return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i + 1 < rank)
+            st[i] = strides[i];
+    }
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d,
+               st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+int64_t lcc_coef_plane(const Grid &g) { return lcc_plane(g.nv); }
+
+namespace {
+template <int D, int R>
+cudaError_t lcc_stats_only(const Grid &g, double eps, const float *F, const float *Wm,
+                           const uint8_t *m, double *part, float *coef, cudaStream_t s)
+{
+    CUtensorMap mF, mW;
+    memset(&mF, 0, sizeof(mF));
+    memset(&mW, 0, sizeof(mW));
+    const bool tma = lcc_vol_tmap<D, R>(&mF, g, F) && lcc_vol_tmap<D, R>(&mW, g, Wm);
+    return tma ? lcc_stats_launch<D, R, true>(g, eps, mF, mW, F, Wm, m, coef, part, s)
+               : lcc_stats_launch<D, R, false>(g, eps, mF, mW, F, Wm, m, coef, part, s);
+}
+}  // namespace
+
+cudaError_t launch_lcc_stats(const Grid &g, int window, double eps, const float *F,
+                             const float *Wm, const uint8_t *m, double *part, float *coef,
+                             cudaStream_t s)
+{
+    const int R = window / 2;
+    if (g.ndim == 3) {
+        if (R == 1) return lcc_stats_only<3, 1>(g, eps, F, Wm, m, part, coef, s);
+        if (R == 2) return lcc_stats_only<3, 2>(g, eps, F, Wm, m, part, coef, s);
+        return lcc_stats_only<3, 3>(g, eps, F, Wm, m, part, coef, s);
+    }
+    if (R == 1) return lcc_stats_only<2, 1>(g, eps, F, Wm, m, part, coef, s);
+    if (R == 2) return lcc_stats_only<2, 2>(g, eps, F, Wm, m, part, coef, s);
+    return lcc_stats_only<2, 3>(g, eps, F, Wm, m, part, coef, s);
+}
+
+cudaError_t launch_lcc_grad(const Grid &g, int window, const float *F, const float *W,
+                            const uint8_t *m, const float *coef, float *gout, cudaStream_t s)
+{
+    const int R = window / 2;
+    float *cf = const_cast<float *>(coef);
+    if (g.ndim == 3) {
+        if (R == 1) return lcc_grad_run<3, 1>(g, F, W, m, gout, cf, s);
+        if (R == 2) return lcc_grad_run<3, 2>(g, F, W, m, gout, cf, s);
+        return lcc_grad_run<3, 3>(g, F, W, m, gout, cf, s);
+    }
+    if (R == 1) return lcc_grad_run<2, 1>(g, F, W, m, gout, cf, s);
+    if (R == 2) return lcc_grad_run<2, 2>(g, F, W, m, gout, cf, s);
+    return lcc_grad_run<2, 3>(g, F, W, m, gout, cf, s);
 }
 
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *F, const float *W,

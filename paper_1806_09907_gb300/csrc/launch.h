@@ -2,6 +2,7 @@
 // Each returns cudaSuccess or the launch error; none synchronises.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -54,6 +55,24 @@ size_t lcc_coef_bytes(const Grid &g);
 cudaError_t launch_lcc(const Grid &g, int window, double eps, const float *fixed,
                        const float *warped, const uint8_t *mask, bool w_masked,
                        float *grad_unscaled, double *block_partials, float *coef, cudaStream_t s);
+
+// LCC statistics alone, W already masked: per-block partials and the
+// coefficient planes (a', b, c) in coef (lcc_coef_bytes(g)).
+cudaError_t launch_lcc_stats(const Grid &g, int window, double eps, const float *fixed,
+                             const float *warped_masked, const uint8_t *mask,
+                             double *block_partials, float *coef, cudaStream_t s);
+// dS/dW * |X_m| from the coefficient planes of launch_lcc_stats (W masked).
+cudaError_t launch_lcc_grad(const Grid &g, int window, const float *fixed,
+                            const float *warped_masked, const uint8_t *mask, const float *coef,
+                            float *grad_unscaled, cudaStream_t s);
+// Tiled fp32 tensor map of rank 1..5 (dims and box in elements, x first;
+// byte strides of dims 1..rank-1), zero fill outside the tensor. False when
+// the driver's encoder is unavailable or rejects the layout (base not
+// 16-byte aligned, a stride not a multiple of 16 bytes, ...).
+bool encode_tmap_f32(CUtensorMap *map, int rank, const uint64_t *dims, const uint64_t *strides,
+                     const uint32_t *box, const void *base);
+// Distance in floats between the coefficient planes a', b, c.
+int64_t lcc_coef_plane(const Grid &g);
 
 // ---- A7: fused objective -----------------------------------------------------
 bool fused_supported(const Grid &g, const Lattice &L, int kind, int window);
