@@ -207,9 +207,11 @@ size_t al_objective_unfused_workspace_bytes(const al_problem *pr);
  * at any size, LCC up to about 340,000 voxels.
  * All calls on a device share the array and leave their data in it; calls
  * whose kernels overlap on the GPU race on it, so order them. The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress
- * with that device current) and caches it: make it before any stream
- * capture. */
+ * in each context of a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current) and caches it with the
+ * context's id, so a call after a device reset looks it up again: make the
+ * first call of a context before any stream capture. A failed lookup
+ * returns AL_ERR_CUDA and leaves no runtime error set. */
 al_status al_similarity_noalloc(const al_grid *g, const al_sim_params *p, const float *fixed,
                                 const float *warped, const uint8_t *mask, double *value_dev,
                                 float *grad_warped, al_stream stream);

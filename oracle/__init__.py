@@ -14,6 +14,7 @@ component planes ``(d, Z, Y, X)`` / ``(d, nz, ny, nx)`` with component 0 = x.
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 
@@ -27,15 +28,31 @@ _lib = None
 MSE, NCC, LCC = 0, 1, 2
 
 
+_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared"]
+
+
+def _digest() -> str:
+    """SHA-256 of the oracle's sources and flags (a library built from other
+    sources, or copied from another machine, is rebuilt)."""
+    h = hashlib.sha256(" ".join(_CFLAGS).encode())
+    for src in _SRCS:
+        with open(src, "rb") as f:
+            h.update(os.path.basename(src).encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` with gcc (portable C11)."""
-    stale = not os.path.exists(_LIB) or any(
-        os.path.getmtime(_LIB) < os.path.getmtime(src) for src in _SRCS)
+    stamp = _LIB + ".sha256"
+    digest = _digest()
+    stale = not os.path.exists(_LIB) or not os.path.exists(stamp) or open(stamp).read().strip() != digest
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp] + _SRCS + ["-lm"],
-                       check=True)
+        subprocess.run(["gcc"] + _CFLAGS + ["-o", tmp] + _SRCS + ["-lm"], check=True)
         os.replace(tmp, _LIB)
+        with open(stamp + ".tmp", "w") as f:
+            f.write(digest + "\n")
+        os.replace(stamp + ".tmp", stamp)
     return _LIB
 
 

@@ -14,6 +14,8 @@ Layouts (see the header): volumes are float32 tensors shaped (Z, Y, X) or
 from __future__ import annotations
 
 import ctypes
+import functools
+import threading
 import os
 
 import torch
@@ -174,8 +176,21 @@ def status_string(status: int) -> str:
     return load().al_status_string(int(status)).decode()
 
 
+# The device of the tensors of the call being marshalled: set by _ptr, read
+# by _stream (the default stream is that device's current stream) and by
+# _call, which runs the C call with that device current.
+_tls = threading.local()
+
+
 def _call(name, *args):
-    st = getattr(load(), name)(*args)
+    dev = getattr(_tls, "dev", None)
+    _tls.dev = None
+    fn = getattr(load(), name)
+    if dev is not None:
+        with torch.cuda.device(dev):
+            st = fn(*args)
+    else:
+        st = fn(*args)
     if st != 0:
         raise AirgbError(name, st)
 
@@ -223,6 +238,12 @@ def _ptr(t):
         raise ValueError("tensors must live on a CUDA device")
     if not t.is_contiguous():
         raise ValueError("tensors must be contiguous")
+    dev = getattr(_tls, "dev", None)
+    if dev is None:
+        _tls.dev = t.device
+    elif dev != t.device:
+        _tls.dev = None
+        raise ValueError(f"the tensors of one call must share a device ({dev} and {t.device})")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -233,8 +254,10 @@ def _f32(t, shape, what):
 
 
 def _stream(stream=None):
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is None:
+        dev = getattr(_tls, "dev", None)
+        stream = torch.cuda.current_stream(dev) if dev is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
 
 
 def _workspace(nbytes, device, ws=None):
@@ -839,3 +862,18 @@ def al_render_blobs(shape, table, out=None, stream=None):
         out = torch.empty((count,) + tuple(shape), dtype=torch.float32, device=table.device)
     _call("al_render_blobs", _i64x3(shape), count, nbl, _ptr(table), _ptr(out), _stream(stream))
     return out
+
+
+def _fresh_call_state(fn):
+    """Entry points start with no device recorded (a call that failed while
+    marshalling must not leave its device behind)."""
+    @functools.wraps(fn)
+    def wrapped(*a, **k):
+        _tls.dev = None
+        return fn(*a, **k)
+    return wrapped
+
+
+for _name in [n for n in list(globals())
+              if n.startswith("al_") and type(globals()[n]) is type(_fresh_call_state)]:
+    globals()[_name] = _fresh_call_state(globals()[_name])

@@ -1,8 +1,10 @@
 """Build libairgb.so in-tree with nvcc for sm_103a (GB300).
 
 Each translation unit under ``csrc/`` is compiled in parallel, then linked
-into ``paper_1806_09907_gb300/libairgb.so``. Rebuilds only when a source is
-newer than the library. ``AIRGB_PTXAS_VERBOSE=1`` adds ``-Xptxas -v``
+into ``paper_1806_09907_gb300/libairgb.so``. A library is reused only when
+the SHA-256 of its sources, headers, compiler flags and nvcc version equals
+the one recorded beside it at build time (``<library>.sha256``); a library
+copied from elsewhere, or built from other sources, is rebuilt. ``AIRGB_PTXAS_VERBOSE=1`` adds ``-Xptxas -v``
 (register / spill / shared-memory report). ``build(checked=True)`` (or
 ``AIRGB_CHECK=1``) builds the bounds-checked variant ``libairgb_check.so``
 (-DAL_CHECK=1: kernels verify their gather indices and record AL_ERR_BOUNDS
@@ -11,6 +13,7 @@ instead of reading out of range) beside the regular library.
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -47,13 +50,34 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale(lib=LIB) -> bool:
-    if not os.path.exists(lib):
-        return True
-    t = os.path.getmtime(lib)
+def _nvcc_version() -> str:
+    r = subprocess.run([_nvcc(), "--version"], capture_output=True, text=True)
+    return r.stdout
+
+
+def _digest(checked: bool) -> str:
+    """SHA-256 of everything the library is built from."""
+    h = hashlib.sha256()
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
     deps += glob.glob(os.path.join(INCLUDE, "*.h"))
-    return any(os.path.getmtime(d) > t for d in deps)
+    for d in sorted(deps):
+        h.update(os.path.relpath(d, HERE).encode() + b"\0")
+        with open(d, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(_flags(checked)).encode())
+    h.update(_nvcc_version().encode())
+    return h.hexdigest()
+
+
+def _stamp(lib) -> str:
+    return lib + ".sha256"
+
+
+def _stale(lib=LIB, checked=False) -> bool:
+    if not os.path.exists(lib) or not os.path.exists(_stamp(lib)):
+        return True
+    with open(_stamp(lib)) as f:
+        return f.read().strip() != _digest(checked)
 
 
 def build(force: bool = False, verbose: bool = False, checked: bool = None) -> str:
@@ -63,8 +87,9 @@ def build(force: bool = False, verbose: bool = False, checked: bool = None) -> s
         checked = os.environ.get("AIRGB_CHECK") == "1"
     lib = LIB_CHECK if checked else LIB
     build_dir = BUILD_DIR_CHECK if checked else BUILD_DIR
-    if not force and not _stale(lib):
+    if not force and not _stale(lib, checked):
         return lib
+    digest = _digest(checked)
     nvcc = _nvcc()
     os.makedirs(build_dir, exist_ok=True)
     flags = _flags(checked)
@@ -87,6 +112,9 @@ def build(force: bool = False, verbose: bool = False, checked: bool = None) -> s
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib)
+    with open(_stamp(lib) + ".tmp", "w") as f:
+        f.write(digest + "\n")
+    os.replace(_stamp(lib) + ".tmp", _stamp(lib))
     return lib
 
 

@@ -23,7 +23,6 @@ namespace {
 size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
 constexpr int kPolicies = 4;
-constexpr int kSMs = 152;  // GB300
 
 struct ProbPlan {
     Grid g;
@@ -121,7 +120,7 @@ al_status launch_step(const al_batch &b, const BatchStep &st, cudaStream_t s)
     int *counters = (int *)(b.ws + b.off_counters);
     if (cudaMemsetAsync(counters, 0, sizeof(int) * (1 + b.prob.size()), s) != cudaSuccess)
         return AL_ERR_CUDA;
-    const int blocks = b.blocks > 0 ? b.blocks : kSMs;
+    const int blocks = b.blocks > 0 ? b.blocks : device_sms();
     return launched(launch_batch(b.delta, blocks, (const BatchProblem *)(b.ws + b.off_desc),
                                  (const BatchItem *)(b.ws + b.off_items), b.nitems, counters, st,
                                  s));
@@ -293,7 +292,7 @@ al_status al_batch_bind(al_batch *b, const float *const *fixed, const float *con
     const int occ = batch_blocks_per_sm(b->delta);
     if (occ < 1)
         return AL_ERR_CUDA;
-    b->blocks = occ * kSMs;
+    b->blocks = occ * device_sms();  // persistent: resident blocks of every SM
     return upload_items(*b, b->policy);
 }
 

@@ -238,7 +238,8 @@ __global__ void k_combine(const double *__restrict__ sim, const double *__restri
 int elementwise_grid(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
-    return (int)(b < 152 * 64 ? (b < 1 ? 1 : b) : 152 * 64);
+    const int64_t most = 64 * (int64_t)device_sms();  // grid-stride loops beyond this
+    return (int)(b < most ? (b < 1 ? 1 : b) : most);
 }
 
 }  // namespace

@@ -64,7 +64,10 @@ constexpr int kStages = 3;                    // shared-memory ring slots
 constexpr int kAhead = 2;                     // items gathered ahead of the MMA (< kStages)
 constexpr int kBK = 64;                       // K elements per ring slot
 constexpr int kATile = 128 * kBK * 2;         // bytes of one A slot (16 KB)
-constexpr int kTargetUnits = 1216;            // wgrad blocks aimed at: 152 SMs x 8
+// wgrad and split-K blocks aimed at (8 per SM of a 152-SM GB300). A constant,
+// not the device's SM count: the split counts size workspaces, which must not
+// depend on the device the sizes are queried on.
+constexpr int kTargetUnits = 1216;
 constexpr int kMaxN = 128;
 constexpr int kErrTimeout = 6;                // AL_ERR_TIMEOUT
 constexpr int kMaxClasses = 8;
@@ -1118,8 +1121,8 @@ cudaError_t grid_for(int N, int units, int *grid)
 int blocks_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
-    if (b > 152 * 32)
-        b = 152 * 32;
+    if (b > 32 * (int64_t)device_sms())  // grid-stride loops beyond this
+        b = 32 * (int64_t)device_sms();
     return (int)(b < 1 ? 1 : b);
 }
 

@@ -291,7 +291,8 @@ cudaError_t exp_adjoint_run(const Grid &g, int K, const float *traj, const float
         const float *u = traj + (int64_t)k * n;
         if ((e = cudaMemsetAsync(mx, 0, sizeof(unsigned int), s)) != cudaSuccess)
             break;
-        k_absmax<<<blocks_for(n) < 4 * 152 ? blocks_for(n) : 4 * 152, kDiffeoThreads, 0, s>>>(
+        k_absmax<<<blocks_for(n) < 4 * device_sms() ? blocks_for(n) : 4 * device_sms(),
+                   kDiffeoThreads, 0, s>>>(
             gin, n, mx);
         k_compose_adjoint<D><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, u, gin, out, acc, mx);
         k_compose_finish<<<blocks_for(n), kDiffeoThreads, 0, s>>>(out, acc, n, mx);

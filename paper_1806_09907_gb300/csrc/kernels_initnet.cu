@@ -36,8 +36,8 @@ constexpr int kT = 256;
 int blocks(int64_t n)
 {
     int64_t b = (n + kT - 1) / kT;
-    if (b > 152 * 64)
-        b = 152 * 64;
+    if (b > 64 * (int64_t)device_sms())  // grid-stride loops beyond this
+        b = 64 * (int64_t)device_sms();
     return (int)(b < 1 ? 1 : b);
 }
 

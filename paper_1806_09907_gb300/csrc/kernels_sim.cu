@@ -9,6 +9,8 @@ namespace airgb {
 namespace {
 
 constexpr int kRedThreads = 256;
+// At most 8 blocks per SM of a 152-SM GB300: the count sizes the partials'
+// workspace, so it is a constant, not the current device's SM count.
 constexpr int kRedBlocksMax = 152 * 8;
 
 int red_blocks(int64_t nv)

@@ -17,9 +17,14 @@
 // cleared between calls.
 //
 // Host code may not use the array's name as a device address (in host code
-// it is a host-side stand-in). The first call on each device looks up the
-// device address with cudaGetSymbolAddress, with that device current, and
-// caches it; make that first call before any stream capture.
+// it is a host-side stand-in). The first call in each context of a device
+// looks up the device address with cudaGetSymbolAddress, with that device
+// current, and caches it together with the context's id: after a device
+// reset (a new primary context, where the module and the array may move) the
+// next call looks the address up again. Make the first call of a context
+// before any stream capture.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "airgb.h"
@@ -35,21 +40,63 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// Id of the current context (driver entry points looked up once through the
+// runtime); 0 when it cannot be read, which forces a fresh lookup.
+unsigned long long current_ctx_id()
+{
+    using GetCur = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCur get_cur = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<GetCur>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch in the current context of the current
+// device (looked up once per context). A failed runtime call's error is
+// cleared before returning, so later calls do not see it.
 al_status scratch_address(void **out)
 {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess)
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
         return AL_ERR_CUDA;
+    }
     if (dev < 0 || dev >= kMaxDevices)
         return AL_ERR_UNSUPPORTED;
+    // 0 before the runtime has made a context current: then the lookup below
+    // (which does) runs and the id is read after it
+    const unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            g_scratch_addr[dev] = nullptr;
             return AL_ERR_CUDA;
+        }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx != 0 ? ctx : current_ctx_id();
     }
     *out = g_scratch_addr[dev];
     return AL_OK;
