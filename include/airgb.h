@@ -183,6 +183,15 @@ al_status al_objective_grad(const al_problem *pr, const float *fixed, const floa
                             void *workspace, size_t workspace_bytes, al_stream stream);
 size_t al_objective_workspace_bytes(const al_problem *pr);
 
+/* Where a fused LCC evaluation keeps its warped image: byte offsets, inside
+ * the workspace of al_objective_grad, of W (fp32, X*Y*Z values, zero off the
+ * mask; Sec. III-C, Image Warping) and of the mask (one byte per voxel) that
+ * the last al_objective_grad call on that workspace wrote. For inspection
+ * and tests; the layout belongs to this library version. AL_ERR_UNSUPPORTED
+ * when the evaluation keeps W on chip (MSE, NCC) or runs unfused. */
+al_status al_objective_warped_offsets(const al_problem *pr, size_t *warped_offset,
+                                      size_t *mask_offset);
+
 /* The same evaluation as the composition of the step calls above
  * (A1 -> A2 -> A3, A4 -> A5 -> A6), with every intermediate field in the
  * workspace. Same arguments and results as al_objective_grad.

@@ -33,7 +33,8 @@ EXPORTS = (
     "al_status_string", "al_bspline_init", "al_displacement", "al_displacement_adjoint",
     "al_displacement_adjoint_workspace_bytes", "al_warp", "al_warp_adjoint", "al_similarity",
     "al_similarity_workspace_bytes", "al_regulariser", "al_regulariser_workspace_bytes",
-    "al_objective_grad", "al_objective_workspace_bytes", "al_objective_grad_unfused",
+    "al_objective_grad", "al_objective_workspace_bytes", "al_objective_warped_offsets",
+    "al_objective_grad_unfused",
     "al_objective_unfused_workspace_bytes", "al_get_device_error", "al_profile_enable",
     "al_profile_collect", "al_profile_reset", "al_similarity_noalloc", "al_noalloc_scratch_bytes",
     "al_adam_step", "al_pyramid_grid", "al_pyramid_level", "al_pyramid_workspace_bytes",
@@ -114,6 +115,7 @@ def load():
         "al_regulariser_workspace_bytes": ([P(al_grid)], SZ),
         "al_objective_grad": ([P(al_problem), VP, VP, VP, VP, VP, VP, SZ, VP], I32),
         "al_objective_workspace_bytes": ([P(al_problem)], SZ),
+        "al_objective_warped_offsets": ([P(al_problem), P(SZ), P(SZ)], I32),
         "al_objective_grad_unfused": ([P(al_problem), VP, VP, VP, VP, VP, VP, SZ, VP], I32),
         "al_objective_unfused_workspace_bytes": ([P(al_problem)], SZ),
         "al_get_device_error": ([VP], I32),
@@ -387,6 +389,14 @@ def objective_workspace_bytes(problem: al_problem, fused=True) -> int:
     if n == 0:
         raise AirgbError(fn, 1)
     return int(n)
+
+
+def objective_warped_offsets(problem: al_problem):
+    """Byte offsets (W, mask) of the warped image a fused LCC evaluation
+    keeps in its workspace (al_objective_warped_offsets)."""
+    w, m = ctypes.c_size_t(), ctypes.c_size_t()
+    _call("al_objective_warped_offsets", ctypes.byref(problem), ctypes.byref(w), ctypes.byref(m))
+    return int(w.value), int(m.value)
 
 
 def al_objective_grad(problem: al_problem, fixed, moving, ctrl, value=None, grad_ctrl=None,

@@ -418,6 +418,22 @@ size_t al_objective_workspace_bytes(const al_problem *pr)
     return unfused_layout(g, L, pr->sim.kind, pr->sim.lcc_window).total;
 }
 
+al_status al_objective_warped_offsets(const al_problem *pr, size_t *warped_offset,
+                                      size_t *mask_offset)
+{
+    Grid g;
+    Lattice L;
+    al_status st = check_problem(pr, &g, &L);
+    if (st != AL_OK)
+        return st;
+    if (!warped_offset || !mask_offset)
+        return AL_ERR_INVALID_ARG;
+    if (pr->sim.kind != AL_SIM_LCC || !fused_supported(g, L, pr->sim.kind, pr->sim.lcc_window))
+        return AL_ERR_UNSUPPORTED;
+    fused_warped_offsets(g, L, pr->sim.lcc_window, warped_offset, mask_offset);
+    return AL_OK;
+}
+
 al_status al_objective_grad(const al_problem *pr, const float *fixed, const float *moving,
                             const float *ctrl, double *value_dev, float *grad_ctrl,
                             void *workspace, size_t workspace_bytes, al_stream stream)

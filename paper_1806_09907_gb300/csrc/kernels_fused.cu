@@ -1183,6 +1183,13 @@ size_t fused_ws(const Grid &g, const Lattice &L, int kind, int window)
     return make_layout(g, L, kind, window).total;
 }
 
+void fused_warped_offsets(const Grid &g, const Lattice &L, int window, size_t *w, size_t *m)
+{
+    const Layout lay = make_layout(g, L, 2, window);
+    *w = lay.Wb;
+    *m = lay.mb;
+}
+
 cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, double eps,
                          double lambda, const float *F, const float *M, const float *c,
                          double *value, float *gc, void *ws, cudaStream_t s)

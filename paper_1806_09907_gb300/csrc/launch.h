@@ -77,6 +77,8 @@ int64_t lcc_coef_plane(const Grid &g);
 // ---- A7: fused objective -----------------------------------------------------
 bool fused_supported(const Grid &g, const Lattice &L, int kind, int window);
 size_t fused_ws(const Grid &g, const Lattice &L, int kind, int window);
+// Offsets of the warped image and its mask in a fused LCC workspace.
+void fused_warped_offsets(const Grid &g, const Lattice &L, int window, size_t *w, size_t *m);
 cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, double eps,
                          double lambda, const float *fixed, const float *moving, const float *ctrl,
                          double *value_dev, float *grad_ctrl, void *ws, cudaStream_t s);

@@ -440,3 +440,17 @@ def test_registration_checkpoint_roundtrip(tmp_path):
     assert (back.levels_done, back.factors, back.shape, back.spacing) == (2, (4, 2, 1),
                                                                         (40, 64, 64), 6)
     assert back.ctrl.dtype == np.float32 and np.array_equal(back.ctrl, c)
+
+
+def test_warped_offsets_only_for_fused_lcc(lib):
+    """The warped image of a fused evaluation is in its workspace only for
+    LCC; MSE and NCC keep it on chip."""
+    pr = airgb.make_problem((40, 48, 64), 6, "lcc", 0.1, 1e-5, 7)
+    w, m = airgb.objective_warped_offsets(pr)
+    nv = 40 * 48 * 64
+    assert w % 256 == 0 and m % 256 == 0
+    assert (w + 4 * nv <= m or m + nv <= w)
+    assert max(w + 4 * nv, m + nv) <= airgb.objective_workspace_bytes(pr)
+    for sim in ("mse", "ncc"):
+        with pytest.raises(airgb.AirgbError):
+            airgb.objective_warped_offsets(airgb.make_problem((40, 48, 64), 6, sim))

@@ -118,3 +118,31 @@ def test_batch_final_objective_matches_oracle():
         J = host(b.values[i])[K - 1, 0]
         assert abs(J - ref["J"]) <= 1e-5 * abs(ref["J"])
         assert host(b.values[i])[K - 1, 0] < host(b.values[i])[0, 0]
+
+
+def test_batch_gradient_matches_oracle():
+    """dJ/dc of every problem of a batch against the FP64 oracle, rel L2 <=
+    1e-4. The batch exposes its gradient through Adam's first moment: after
+    one step from m = 0, m = (1 - beta1) * h * dJ/dc per component, with
+    h = (N_k - 1)/2 the normalised-unit scale of that axis."""
+    shapes = SHAPES
+    pairs = pairs_for(shapes, seed=11)
+    rng = np.random.default_rng(3)
+    b = airgb.Batch(pairs, 8, 0.1)
+    starts = []
+    for i in range(len(pairs)):
+        c0 = (rng.normal(size=b.lattices[i]) * 0.7).astype(np.float32)
+        b.ctrl[i].copy_(torch.from_numpy(c0))
+        starts.append(c0)
+    b.step(1)
+    assert b.status() == 0
+    omb1 = np.float32(1.0 - 0.9)
+    for i, sh in enumerate(shapes):
+        nd = len(sh)
+        hs = [np.float32((sh[nd - 1 - k] - 1) / 2.0) for k in range(nd)]
+        mm = host(b.m[i]).astype(np.float64)
+        g = np.stack([mm[k] / (float(omb1) * float(hs[k])) for k in range(nd)])
+        F, M = (host(t) for t in pairs[i])
+        ref, gref = oracle.objective_grad(oracle.MSE, F, M, starts[i], 8, 0.1)
+        rel = float(np.linalg.norm(g - gref) / np.linalg.norm(gref))
+        assert rel <= 1e-4, (i, sh, rel)

@@ -270,10 +270,37 @@ def _ambiguity(shape, delta, u, M, gw, window, sim, band):
     return excl, bound, n_kink, n_face
 
 
+def check_fused_lcc_warped(pr, ws, M, u_ref, band):
+    """The warped image and mask a fused LCC evaluation left in its workspace
+    against the oracle's warp of M by the FP64 displacement: the mask bit for
+    bit except samples within `band` of a face (fp32 rounding of y), W within
+    1e-5 x (max M - min M) where both masks are set."""
+    shape, nv = M.shape, M.size
+    w_off, m_off = airgb.objective_warped_offsets(pr)
+    Wg = host(ws[w_off:w_off + 4 * nv].view(torch.float32)).reshape(shape)
+    mg = host(ws[m_off:m_off + nv]).reshape(shape)
+    Wr, mr = oracle.warp(M, u_ref)
+    nd = len(shape)
+    near = np.zeros(shape, dtype=bool)
+    for k in range(nd):
+        n = shape[nd - 1 - k]
+        y = u_ref[k] + np.arange(n).reshape([-1 if a == nd - 1 - k else 1 for a in range(nd)])
+        near |= (np.abs(y) < band) | (np.abs(y - (n - 1)) < band)
+    diff = mg != mr
+    assert not np.any(diff & ~near), int((diff & ~near).sum())
+    both = (mg == 1) & (mr == 1)
+    err = float(np.abs(Wg - Wr)[both].max()) if both.any() else 0.0
+    tol = W_TOL * float(M.max() - M.min())
+    assert err <= tol, (err, tol)
+    assert np.all(Wg[mg == 0] == 0.0)
+    return err / float(M.max() - M.min()), int(diff.sum())
+
+
 def check_objective(F, M, c, delta, sim, window=7, lam=0.1, fused=True):
     shape = F.shape
     pr = airgb.make_problem(shape, delta, sim, lam, 1e-5, window)
-    val, g = airgb.al_objective_grad(pr, dev(F), dev(M), dev(c), fused=fused)
+    ws = torch.empty(airgb.objective_workspace_bytes(pr, fused), dtype=torch.uint8, device="cuda")
+    val, g = airgb.al_objective_grad(pr, dev(F), dev(M), dev(c), workspace=ws, fused=fused)
     ug = airgb.al_displacement(shape, delta, dev(c))
     val, g, ug = host(val), host(g), host(ug)
     ref, gref = oracle.objective_grad(airgb.SIM_KINDS[sim], F, M, c, delta, lam, 1e-5, window,
@@ -289,10 +316,18 @@ def check_objective(F, M, c, delta, sim, window=7, lam=0.1, fused=True):
     assert abs(val[1] - ref["S"]) <= J_TOL * abs(ref["J"])
     assert abs(val[0] - ref["J"]) <= J_TOL * abs(ref["J"])
     keep = ~excl
-    assert keep.mean() > 0.5, (n_kink, n_face, keep.mean())
+    # entries reachable from a sample within the ambiguity band are bounded
+    # below; every other entry is held to the rel-L2 bar (at least 95% of them)
+    print(f"kept {keep.mean():.6f} of {keep.size} gradient entries "
+          f"({n_kink} kink and {n_face} face samples)")
+    assert keep.mean() >= 0.95, (n_kink, n_face, keep.mean())
     assert rel_l2(g[keep], gref[keep]) <= G_TOL
     err = np.abs(g - gref)[excl]
     assert np.all(err <= bound[excl] + G_TOL * np.abs(gref).max())
+    if sim == "lcc" and fused and delta in (4, 6, 8):
+        werr, nflip = check_fused_lcc_warped(pr, ws, M, ref["u"], max(2 * uerr, 1e-9))
+        print(f"fused LCC warped image: max |W - W_ref| = {werr:.2e} x range, "
+              f"{nflip} mask bits on a face")
     return val, g
 
 
@@ -375,6 +410,23 @@ def test_full_3d_128_mse():
     F, M = synth.blobs_3d_128()
     c = synth.random_ctrl(oracle.lattice_shape(F.shape, 8), 3, 1.0, 9907)
     check_objective(F, M, c, 8, "mse")
+
+
+def test_warp_ct_256x256x160():
+    """A2 at the benchmark size: the CT moving image warped by the
+    displacement of the benchmark's coefficients (the same fp32 field on both
+    sides), against the oracle: mask bit for bit, W within 1e-5 x range."""
+    F, M = synth.ct_pair()
+    c = synth.random_ctrl(oracle.lattice_shape(F.shape, 6), 3, 3.0, 9907)
+    u = airgb.al_displacement(F.shape, 6, dev(c))
+    W, m = airgb.al_warp(dev(M), u)
+    W, m, u = host(W), host(m), host(u)
+    Wr, mr = oracle.warp(M, u)
+    np.testing.assert_array_equal(m, mr)
+    err = float(np.abs(W - Wr).max())
+    assert err <= W_TOL * float(M.max() - M.min()), err
+    print(f"warp 256x256x160: max |W - W_ref| = {err / float(M.max() - M.min()):.2e} x range, "
+          f"{int(m.sum())} of {m.size} inside")
 
 
 @pytest.mark.parametrize("sim", ["lcc", "mse"])
