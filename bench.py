@@ -483,7 +483,10 @@ def registration_runs(F, M, c, dev):
         "voxels": nvox, "work_items_per_iteration": total,
         "items_bricks_tiles_chunks": list(per_kind),
         "batched_device_ms": rb.device_ms, "batched_ms_per_iteration": rb.device_ms / iters,
-        "batched_order": rb.policy, "tuning_ms_per_iteration": rb.tuning_ms,
+        "batched_order": rb.policy, "batched_tile": rb.tile,
+        "batched_tile_cells": list(rb.tile_cells),
+        "tuning_ms_per_iteration": rb.tuning_ms,
+        "default_tile_ms_per_iteration": min(rb.tuning_ms[0]) if rb.tuning_ms else None,
         "sequential_device_ms": seq_ms, "sequential_wall_s": seq_wall,
         "speedup": seq_ms / rb.device_ms, "coefficients_bit_identical": bool(same)}
     # the diffeomorphic model on the headline pair: one forward+adjoint

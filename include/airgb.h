@@ -363,15 +363,30 @@ al_status al_batch_step(const al_batch *batch, const al_adam_params *p, int64_t 
                         int32_t record, al_stream stream);
 
 /* Autotuner: times `iterations` gradient-only iterations (coefficients and
- * moments untouched) of each work-item order the library knows (4) and
- * keeps the fastest. ms (nullable, 4 entries) receives the milliseconds per
- * iteration of each order, chosen (nullable) the order kept. Synchronises
- * the stream; not capturable. Orders: 0 problems as given, 1 largest
- * problem first, 2 round-robin over problems, 3 Gram tiles first. */
+ * moments untouched) of every (brick tile, work-item order) configuration
+ * and keeps the fastest. The batch kernel is built for al_batch_tiles()
+ * brick tiles of the batch's spacing (tile 0 is al_objective_grad's brick;
+ * a tile sets the cells of control lattice a block covers in x and y, hence
+ * its threads, its share of shared memory and registers, and the number of
+ * work items); the orders are 0 problems as given, 1 largest problem first,
+ * 2 round-robin over problems, 3 Gram tiles first. ms (nullable,
+ * al_batch_tiles() x 4 entries, tile-major) receives the milliseconds per
+ * iteration of each configuration, chosen_tile / chosen_policy (nullable)
+ * the one kept. Synchronises the stream and rewrites the bound descriptors;
+ * not capturable. Coefficients follow al_objective_grad + al_adam_step bit
+ * for bit with tile 0; with another tile the partial sums are grouped by
+ * other bricks, so they agree to fp32 rounding. */
 al_status al_batch_tune(al_batch *batch, const al_adam_params *p, int32_t iterations,
-                        double *ms, int32_t *chosen, al_stream stream);
+                        double *ms, int32_t *chosen_tile, int32_t *chosen_policy,
+                        al_stream stream);
 /* Select a work-item order directly (0..3). */
 al_status al_batch_set_policy(al_batch *batch, int32_t policy);
+/* Select a brick tile directly (0 .. al_batch_tiles() - 1; 0 by default).
+ * After binding it rewrites the bound descriptors with synchronous copies. */
+al_status al_batch_set_tile(al_batch *batch, int32_t tile);
+/* Number of brick tiles; cells (nullable, 2 per tile) receives each tile's
+ * control cells per block in x and y. */
+int32_t al_batch_tiles(const al_batch *batch, int32_t *cells);
 
 /* Bounded waits. A control chunk waits, polling a device counter, until
  * every brick and tile of its problem is done; after max_polls polls it

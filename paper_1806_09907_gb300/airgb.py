@@ -38,7 +38,8 @@ EXPORTS = (
     "al_objective_unfused_workspace_bytes", "al_get_device_error", "al_profile_enable",
     "al_profile_collect", "al_profile_reset", "al_similarity_noalloc", "al_noalloc_scratch_bytes",
     "al_adam_step", "al_pyramid_grid", "al_pyramid_level", "al_pyramid_workspace_bytes",
-    "al_bspline_refine", "al_batch_create", "al_batch_destroy", "al_batch_workspace_bytes",
+    "al_bspline_refine", "al_batch_create", "al_batch_destroy", "al_batch_workspace_bytes", "al_batch_set_tile",
+    "al_batch_tiles",
     "al_batch_items", "al_batch_bind", "al_batch_step", "al_batch_tune", "al_batch_set_policy",
     "al_batch_set_wait", "al_batch_status", "al_exp_field", "al_exp_field_workspace_bytes",
     "al_exp_field_adjoint", "al_exp_field_adjoint_workspace_bytes", "al_objective_grad_diffeo",
@@ -136,8 +137,10 @@ def load():
         "al_batch_items": ([VP, P(I32)], I32),
         "al_batch_bind": ([VP, P(VP), P(VP), P(VP), P(VP), P(VP), P(VP), VP, SZ], I32),
         "al_batch_step": ([VP, P(al_adam_params), ctypes.c_int64, I32, VP], I32),
-        "al_batch_tune": ([VP, P(al_adam_params), I32, P(D), P(I32), VP], I32),
+        "al_batch_tune": ([VP, P(al_adam_params), I32, P(D), P(I32), P(I32), VP], I32),
         "al_batch_set_policy": ([VP, I32], I32),
+        "al_batch_set_tile": ([VP, I32], I32),
+        "al_batch_tiles": ([VP, P(I32)], I32),
         "al_batch_set_wait": ([VP, I32, ctypes.c_int64], I32),
         "al_batch_status": ([VP, VP], I32),
         "al_exp_field": ([P(al_grid), I32, VP, VP, VP, VP, SZ, VP], I32),
@@ -567,6 +570,7 @@ class Batch:
         self.values = [torch.zeros((history, 4), dtype=torch.float64, device=dev)
                        for _ in range(n)] if history > 0 else None
         self.policy = 1  # the library's default order: largest problem first
+        self.tile = 0    # the single-problem path's brick
         self.workspace = torch.empty(max(int(load().al_batch_workspace_bytes(h)), 256),
                                      dtype=torch.uint8, device=dev)
         arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
@@ -590,20 +594,33 @@ class Batch:
         p = self._adam(lr, betas, eps)
         _call("al_batch_step", self._h, ctypes.byref(p), int(t), int(record), _stream(stream))
 
+    def tiles(self):
+        """The brick tiles of the batch kernel: (cells in x, cells in y) each."""
+        n = load().al_batch_tiles(self._h, None)
+        cells = (ctypes.c_int32 * (2 * n))()
+        load().al_batch_tiles(self._h, cells)
+        return [(cells[2 * t], cells[2 * t + 1]) for t in range(n)]
+
     def tune(self, iterations=3, lr=0.01, betas=(0.9, 0.999), eps=1e-8, stream=None):
-        """Time every work-item order and keep the fastest; returns
-        (chosen order, ms per iteration of each order)."""
+        """Time every (brick tile, work-item order) configuration and keep
+        the fastest; returns (tile, order, ms per iteration as a
+        tiles x orders list of lists)."""
         p = self._adam(lr, betas, eps)
-        ms = (ctypes.c_double * 4)()
-        chosen = ctypes.c_int32()
-        _call("al_batch_tune", self._h, ctypes.byref(p), int(iterations), ms,
-              ctypes.byref(chosen), _stream(stream))
-        self.policy = int(chosen.value)
-        return self.policy, list(ms)
+        nt = len(self.tiles())
+        ms = (ctypes.c_double * (4 * nt))()
+        tile, policy = ctypes.c_int32(), ctypes.c_int32()
+        _call("al_batch_tune", self._h, ctypes.byref(p), int(iterations), ms, ctypes.byref(tile),
+              ctypes.byref(policy), _stream(stream))
+        self.tile, self.policy = int(tile.value), int(policy.value)
+        return self.tile, self.policy, [list(ms[4 * t:4 * t + 4]) for t in range(nt)]
 
     def set_policy(self, policy):
         _call("al_batch_set_policy", self._h, int(policy))
         self.policy = int(policy)
+
+    def set_tile(self, tile):
+        _call("al_batch_set_tile", self._h, int(tile))
+        self.tile = int(tile)
 
     def set_wait(self, extra_items=0, max_polls=20000000):
         _call("al_batch_set_wait", self._h, int(extra_items), int(max_polls))

@@ -23,12 +23,16 @@ namespace {
 size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
 constexpr int kPolicies = 4;
+constexpr int kMaxTiles = 4;
 
+// A problem's plan for every brick tile of the batch kernel (the workspace
+// holds the largest tile's partials, so a tile can change after binding).
 struct ProbPlan {
     Grid g;
     Lattice L;
     double lambda;
-    int gb[3], gt[3], npart, nmom, nbricks, ngram, nchunks;
+    int gt[3], ngram, nmom;
+    int gb[kMaxTiles][3], npart[kMaxTiles], nbricks[kMaxTiles], nchunks[kMaxTiles];
     size_t bpart, mpart, rpart, gR;  // workspace offsets
     double work;                     // voxels, for ordering
 };
@@ -39,9 +43,12 @@ struct al_batch {
     int delta = 0;
     std::vector<ProbPlan> prob;
     size_t off_counters = 0, off_err = 0, off_desc = 0, off_items = 0, total = 0;
-    int nitems = 0;
+    int ntiles = 1;
+    int tile = 0;                       // brick tile of the batch kernel in use
+    int nitems = 0;                     // items of one iteration with that tile
     int policy = 1;
     int blocks = 0;
+    std::vector<BatchProblem> desc;     // bound descriptors (host copy)
     int extra_wait = 0;
     long long spin_limit = 20000000;  // about 3 s of polling
     char *ws = nullptr;               // bound workspace
@@ -58,7 +65,7 @@ namespace {
 //  3: every Gram tile first (largest problem first), then the bricks.
 std::vector<BatchItem> make_items(const al_batch &b, int policy)
 {
-    const int n = (int)b.prob.size();
+    const int n = (int)b.prob.size(), t = b.tile;
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i)
         order[i] = i;
@@ -73,7 +80,7 @@ std::vector<BatchItem> make_items(const al_batch &b, int policy)
             more = false;
             for (int i = 0; i < n; ++i) {
                 const ProbPlan &p = b.prob[i];
-                if (nb[i] < p.nbricks) {
+                if (nb[i] < p.nbricks[t]) {
                     v.push_back({i, BATCH_BRICK, nb[i]++, 0});
                     more = true;
                 } else if (ng[i] < p.ngram) {
@@ -87,20 +94,58 @@ std::vector<BatchItem> make_items(const al_batch &b, int policy)
             for (int t = 0; t < b.prob[i].ngram; ++t)
                 v.push_back({i, BATCH_GRAM, t, 0});
         for (int i : order)
-            for (int k = 0; k < b.prob[i].nbricks; ++k)
+            for (int k = 0; k < b.prob[i].nbricks[t]; ++k)
                 v.push_back({i, BATCH_BRICK, k, 0});
     } else {
         for (int i : order) {
-            for (int k = 0; k < b.prob[i].nbricks; ++k)
+            for (int k = 0; k < b.prob[i].nbricks[t]; ++k)
                 v.push_back({i, BATCH_BRICK, k, 0});
             for (int t = 0; t < b.prob[i].ngram; ++t)
                 v.push_back({i, BATCH_GRAM, t, 0});
         }
     }
     for (int i : order)
-        for (int k = 0; k < b.prob[i].nchunks; ++k)
+        for (int k = 0; k < b.prob[i].nchunks[t]; ++k)
             v.push_back({i, BATCH_CTRL, k, 0});
     return v;
+}
+
+int count_items(const al_batch &b, int t)
+{
+    int n = 0;
+    for (const ProbPlan &p : b.prob)
+        n += p.nbricks[t] + p.ngram + p.nchunks[t];
+    return n;
+}
+
+// Select brick tile t: the descriptors' brick geometry, the launch size and
+// the work items (in the current order) follow it.
+al_status use_tile(al_batch &b, int t)
+{
+    const int occ = batch_blocks_per_sm(b.delta, t);
+    if (occ < 1)
+        return AL_ERR_CUDA;
+    for (size_t i = 0; i < b.prob.size(); ++i) {
+        const ProbPlan &p = b.prob[i];
+        BatchProblem &q = b.desc[i];
+        q.gbx = p.gb[t][0];
+        q.gby = p.gb[t][1];
+        q.gbz = p.gb[t][2];
+        q.nbricks = p.nbricks[t];
+        q.nA = p.nbricks[t] + p.ngram;
+        q.nchunks = p.nchunks[t];
+    }
+    if (cudaMemcpy(b.ws + b.off_desc, b.desc.data(), sizeof(BatchProblem) * b.desc.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return AL_ERR_CUDA;
+    b.tile = t;
+    b.nitems = count_items(b, t);
+    b.blocks = occ * device_sms();  // persistent: resident blocks of every SM
+    const std::vector<BatchItem> v = make_items(b, b.policy);
+    if (cudaMemcpy(b.ws + b.off_items, v.data(), v.size() * sizeof(BatchItem),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return AL_ERR_CUDA;
+    return AL_OK;
 }
 
 al_status upload_items(al_batch &b, int policy)
@@ -121,7 +166,8 @@ al_status launch_step(const al_batch &b, const BatchStep &st, cudaStream_t s)
     if (cudaMemsetAsync(counters, 0, sizeof(int) * (1 + b.prob.size()), s) != cudaSuccess)
         return AL_ERR_CUDA;
     const int blocks = b.blocks > 0 ? b.blocks : device_sms();
-    return launched(launch_batch(b.delta, blocks, (const BatchProblem *)(b.ws + b.off_desc),
+    return launched(launch_batch(b.delta, b.tile, blocks,
+                                 (const BatchProblem *)(b.ws + b.off_desc),
                                  (const BatchItem *)(b.ws + b.off_items), b.nitems, counters, st,
                                  s));
 }
@@ -176,7 +222,7 @@ al_status al_batch_create(const al_problem *problems, int32_t count, al_batch **
             st = check_sim(&pr.sim, p.g.ndim);
         if (st == AL_OK && !isfinite(pr.lambda))
             st = AL_ERR_INVALID_ARG;
-        if (st == AL_OK && (pr.sim.kind != AL_SIM_MSE || batch_threads(pr.bs.spacing) == 0 ||
+        if (st == AL_OK && (pr.sim.kind != AL_SIM_MSE || batch_threads(pr.bs.spacing, 0) == 0 ||
                             (i > 0 && pr.bs.spacing != problems[0].bs.spacing)))
             st = AL_ERR_UNSUPPORTED;  // MSE, one spacing in {4, 6, 8}
         if (st != AL_OK) {
@@ -184,24 +230,33 @@ al_status al_batch_create(const al_problem *problems, int32_t count, al_batch **
             return st;
         }
         p.lambda = pr.lambda;
-        batch_geometry(p.g, p.L, p.gb, p.gt, &p.npart, &p.nmom);
-        p.nbricks = p.gb[0] * p.gb[1] * p.gb[2];
+        b->ntiles = batch_tiles() < kMaxTiles ? batch_tiles() : kMaxTiles;
+        for (int t = 0; t < b->ntiles; ++t) {
+            batch_geometry(p.g, p.L, t, p.gb[t], p.gt, &p.npart[t], &p.nmom);
+            p.nbricks[t] = p.gb[t][0] * p.gb[t][1] * p.gb[t][2];
+            const int threads = batch_threads(pr.bs.spacing, t);
+            p.nchunks[t] = (p.L.nc + threads - 1) / threads;
+        }
         p.ngram = p.g.ndim * p.gt[0] * p.gt[1] * p.gt[2];
-        const int threads = batch_threads(pr.bs.spacing);
-        p.nchunks = (p.L.nc + threads - 1) / threads;
         p.work = (double)p.g.nv;
-        nitems += p.nbricks + p.ngram + p.nchunks;
         b->prob.push_back(p);
     }
     b->delta = problems[0].bs.spacing;
-    b->nitems = nitems;
+    for (int t = 0; t < b->ntiles; ++t)
+        nitems = std::max(nitems, count_items(*b, t));
+    b->nitems = count_items(*b, 0);
     b->off_items = off;
     off += a256(sizeof(BatchItem) * (size_t)nitems);
     for (ProbPlan &p : b->prob) {
+        size_t part = 0, mom = 0;  // the largest tile's partials
+        for (int t = 0; t < b->ntiles; ++t) {
+            part = std::max(part, (size_t)p.nbricks[t] * p.npart[t]);
+            mom = std::max(mom, (size_t)p.nbricks[t] * p.nmom);
+        }
         p.bpart = off;
-        off += a256((size_t)p.nbricks * p.npart * sizeof(float));
+        off += a256(part * sizeof(float));
         p.mpart = off;
-        off += a256((size_t)p.nbricks * p.nmom * sizeof(double));
+        off += a256(mom * sizeof(double));
         p.rpart = off;
         off += a256((size_t)p.ngram * sizeof(double));
         p.gR = off;
@@ -223,9 +278,9 @@ int32_t al_batch_items(const al_batch *b, int32_t *per_kind)
     if (per_kind) {
         per_kind[0] = per_kind[1] = per_kind[2] = 0;
         for (const ProbPlan &p : b->prob) {
-            per_kind[0] += p.nbricks;
+            per_kind[0] += p.nbricks[b->tile];
             per_kind[1] += p.ngram;
-            per_kind[2] += p.nchunks;
+            per_kind[2] += p.nchunks[b->tile];
         }
     }
     return b->nitems;
@@ -273,27 +328,16 @@ al_status al_batch_bind(al_batch *b, const float *const *fixed, const float *con
             q.h[k] = k < p.g.ndim ? (float)((N[k] - 1) / 2.0) : 0.0f;
         q.gscale = (float)(2.0 / (double)p.g.nv);
         q.lambda = p.lambda;
-        q.gbx = p.gb[0];
-        q.gby = p.gb[1];
-        q.gbz = p.gb[2];
-        q.nbricks = p.nbricks;
         q.gtx = p.gt[0];
         q.gty = p.gt[1];
         q.gtz = p.gt[2];
-        q.ngram = p.ngram;
-        q.nA = p.nbricks + p.ngram;
-        q.nchunks = p.nchunks;
+        q.ngram = p.ngram;  // brick geometry: use_tile
     }
-    if (cudaMemcpy(ws + b->off_desc, d.data(), sizeof(BatchProblem) * n,
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(ws + b->off_err, 0, sizeof(int)) != cudaSuccess)
+    if (cudaMemset(ws + b->off_err, 0, sizeof(int)) != cudaSuccess)
         return AL_ERR_CUDA;
     b->ws = ws;
-    const int occ = batch_blocks_per_sm(b->delta);
-    if (occ < 1)
-        return AL_ERR_CUDA;
-    b->blocks = occ * device_sms();  // persistent: resident blocks of every SM
-    return upload_items(*b, b->policy);
+    b->desc = d;
+    return use_tile(*b, b->tile);
 }
 
 al_status al_batch_step(const al_batch *b, const al_adam_params *p, int64_t step, int32_t record,
@@ -307,7 +351,7 @@ al_status al_batch_step(const al_batch *b, const al_adam_params *p, int64_t step
 }
 
 al_status al_batch_tune(al_batch *b, const al_adam_params *p, int32_t iterations, double *ms,
-                        int32_t *chosen, al_stream stream)
+                        int32_t *chosen_tile, int32_t *chosen_policy, al_stream stream)
 {
     if (!b || !adam_ok(p) || iterations < 1)
         return AL_ERR_INVALID_ARG;
@@ -319,10 +363,16 @@ al_status al_batch_tune(al_batch *b, const al_adam_params *p, int32_t iterations
         return AL_ERR_CUDA;
     const BatchStep st = step_args(*b, *p, 1, -1, 0);  // gradients only: state unchanged
     double best = 1e300;
-    int best_policy = b->policy;
+    int best_policy = b->policy, best_tile = b->tile;
     al_status rc = AL_OK;
-    for (int pol = 0; pol < kPolicies && rc == AL_OK; ++pol) {
-        if ((rc = upload_items(*b, pol)) != AL_OK)
+    for (int cfg = 0; cfg < b->ntiles * kPolicies && rc == AL_OK; ++cfg) {
+        const int tile = cfg / kPolicies, pol = cfg % kPolicies;
+        if (cudaStreamSynchronize(s) != cudaSuccess) {  // the bound descriptors are rewritten
+            rc = AL_ERR_CUDA;
+            break;
+        }
+        b->policy = pol;
+        if ((rc = use_tile(*b, tile)) != AL_OK)
             break;
         for (int w = 0; w < 2 && rc == AL_OK; ++w)
             rc = launch_step(*b, st, s);
@@ -340,19 +390,45 @@ al_status al_batch_tune(al_batch *b, const al_adam_params *p, int32_t iterations
         }
         const double per = (double)t / iterations;
         if (ms)
-            ms[pol] = per;
+            ms[cfg] = per;
         if (per < best) {
             best = per;
             best_policy = pol;
+            best_tile = tile;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != AL_OK)
         return rc;
-    if (chosen)
-        *chosen = best_policy;
-    return upload_items(*b, best_policy);
+    if (chosen_tile)
+        *chosen_tile = best_tile;
+    if (chosen_policy)
+        *chosen_policy = best_policy;
+    b->policy = best_policy;
+    return use_tile(*b, best_tile);
+}
+
+al_status al_batch_set_tile(al_batch *b, int32_t tile)
+{
+    if (!b || tile < 0 || tile >= b->ntiles)
+        return AL_ERR_INVALID_ARG;
+    if (!b->ws) {
+        b->tile = tile;
+        b->nitems = count_items(*b, tile);
+        return AL_OK;
+    }
+    return use_tile(*b, tile);
+}
+
+int32_t al_batch_tiles(const al_batch *b, int32_t *cells)
+{
+    if (!b)
+        return 0;
+    if (cells)
+        for (int t = 0; t < b->ntiles; ++t)
+            batch_tile_cells(b->delta, t, &cells[2 * t], &cells[2 * t + 1]);
+    return b->ntiles;
 }
 
 al_status al_batch_set_policy(al_batch *b, int32_t policy)

@@ -35,9 +35,31 @@ __host__ __device__ constexpr int brick_bcx(int delta) { return delta <= 4 ? 8 :
 __host__ __device__ constexpr int brick_bcy(int delta) { return delta <= 4 ? 4 : 3; }
 __host__ __device__ constexpr int brick_bcz(int ndim) { return ndim == 3 ? 4 : 1; }
 
-template <int D, int DELTA, int MODE>
+// Brick tiles the batch kernel is built for, per spacing: control cells per
+// block in x and y, and the resident blocks per SM the kernel is compiled
+// for (its register budget). Tile 0 is the single-problem path's brick at
+// one block per SM; the others are the batch autotuner's alternatives (every
+// axis still spans >= 3 cells):
+//   spacing 4: (8, 4, 1), (8, 4, 2), (6, 4, 2)
+//   spacing 6: (4, 3, 1), (4, 3, 2), (3, 3, 2)
+//   spacing 8: (4, 3, 1), (3, 3, 1), (3, 4, 1)
+constexpr int kBatchTiles = 3;
+__host__ __device__ constexpr int batch_tile_bcx(int delta, int t)
+{
+    return delta <= 4 ? (t == 2 ? 6 : 8) : (t == 0 || (t == 1 && delta == 6) ? 4 : 3);
+}
+__host__ __device__ constexpr int batch_tile_bcy(int delta, int t)
+{
+    return delta <= 4 ? 4 : (delta == 8 && t == 2 ? 4 : 3);
+}
+__host__ __device__ constexpr int batch_tile_minb(int delta, int t)
+{
+    return delta == 8 || t == 0 ? 1 : 2;
+}
+
+template <int D, int DELTA, int MODE, int BCX_ = brick_bcx(DELTA), int BCY_ = brick_bcy(DELTA)>
 struct FCfg {
-    static constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
+    static constexpr int BCX = BCX_, BCY = BCY_, BCZ = brick_bcz(D);
     static constexpr int BX = BCX * DELTA, BY = BCY * DELTA;
     static constexpr int THREADS = BX * BY;
     static constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
@@ -81,12 +103,13 @@ __device__ __forceinline__ void plane_xy(const float (&cb)[D][JZ][JY][JX], int j
 // contraction -> the brick's partial sums of local planes lp0 .. lp0+NPL-1.
 // Every thread of the block calls it. Cell-wise loops with compile-time
 // bounds and two accumulators per output.
-template <int D, int DELTA, int MODE, int NPL>
+template <int D, int DELTA, int MODE, int NPL, int BCX_ = brick_bcx(DELTA),
+          int BCY_ = brick_bcy(DELTA)>
 __device__ __forceinline__ void flush_planes(int lp0, const float (&qz)[4][FCfg<D, DELTA, MODE>::CHS],
                                              bool colvalid, int tx, int ty, float *P, float *Xc,
                                              const float (*wt)[4], float *dst)
 {
-    using C = FCfg<D, DELTA, MODE>;
+    using C = FCfg<D, DELTA, MODE, BCX_, BCY_>;
     constexpr int CHS = C::CHS, BX = C::BX, BY = C::BY, JX = C::JX, JY = C::JY, JZ = C::JZ;
     const int tid = threadIdx.x;
 #pragma unroll
@@ -144,7 +167,7 @@ __device__ __forceinline__ void flush_planes(int lp0, const float (&qz)[4][FCfg<
 // brick, its partial sums written to bpart / mpart at index `brick`. Every
 // thread of a block of FCfg::THREADS threads calls it; it uses the block's
 // shared memory (static arrays here and FCfg::dyn_smem of dynamic memory).
-template <int D, int DELTA, int MODE>
+template <int D, int DELTA, int MODE, int BCX_ = brick_bcx(DELTA), int BCY_ = brick_bcy(DELTA)>
 __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                                             const float *__restrict__ F,
                                             const float *__restrict__ M,
@@ -157,7 +180,7 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
 {
     // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
     // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
-    using C = FCfg<D, DELTA, MODE>;
+    using C = FCfg<D, DELTA, MODE, BCX_, BCY_>;
     constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS, BX = C::BX;
     constexpr WTab<DELTA> kW{};  // weights of the compile-time z phases
     __shared__ float cb[D][JZ][JY][JX];
@@ -241,7 +264,8 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
         if (cz > 0) {
             // plane cz - 1 has all its contributions: write it out, roll
             if (MODE != MODE_FWD)
-                flush_planes<D, DELTA, MODE, 1>(cz - 1, qz, colvalid, tx, ty, P, Xc, wt, dstp);
+                flush_planes<D, DELTA, MODE, 1, BCX_, BCY_>(cz - 1, qz, colvalid, tx, ty, P, Xc,
+                                                            wt, dstp);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -393,7 +417,8 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
     }
     if (MODE != MODE_FWD) {
         // the last four planes (a single plane in 2D), together
-        flush_planes<D, DELTA, MODE, C::NPL>(D == 3 ? C::BCZ - 1 : 0, qz, colvalid, tx, ty, P, Xc,
+        flush_planes<D, DELTA, MODE, C::NPL, BCX_, BCY_>(D == 3 ? C::BCZ - 1 : 0, qz, colvalid,
+                                                         tx, ty, P, Xc,
                                              wt, dstp);
     }
     if (C::NMOM > 0) {
@@ -1013,11 +1038,13 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
 // polls, then AL_ERR_TIMEOUT in the error word and the chunk is skipped).
 // The per-item arithmetic is that of k_fused (bricks, Gram tiles) and k_ctrl + k_adam, so
 // a problem's coefficients follow the single-problem path bit for bit.
-template <int DELTA>
+template <int DELTA, int T>
 struct BCfg {
-    using C3 = FCfg<3, DELTA, MODE_MSE>;
-    using C2 = FCfg<2, DELTA, MODE_MSE>;
+    static constexpr int BCX = batch_tile_bcx(DELTA, T), BCY = batch_tile_bcy(DELTA, T);
+    using C3 = FCfg<3, DELTA, MODE_MSE, BCX, BCY>;
+    using C2 = FCfg<2, DELTA, MODE_MSE, BCX, BCY>;
     static constexpr int THREADS = C3::THREADS;
+    static constexpr int MINB = batch_tile_minb(DELTA, T);  // resident blocks per SM
     static_assert(C2::THREADS == THREADS, "2D and 3D bricks share the block size");
     static constexpr size_t fsm = C3::dyn_smem > C2::dyn_smem ? C3::dyn_smem : C2::dyn_smem;
     static constexpr size_t gsm = (size_t)kGram3Floats * sizeof(float);  // > the 2D tile
@@ -1031,12 +1058,13 @@ __device__ __forceinline__ int load_acquire(const int *p)
     return v;
 }
 
-template <int D, int DELTA>
+template <int D, int DELTA, int T>
 __device__ __forceinline__ void batch_ctrl_adam(const BatchProblem &P, const BatchStep &st,
                                                 int64_t e, float k0, float inv_bc1,
                                                 float inv_bc2)
 {
-    constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
+    constexpr int BCX = batch_tile_bcx(DELTA, T), BCY = batch_tile_bcy(DELTA, T);
+    constexpr int BCZ = brick_bcz(D);
     float gv[D];
     ctrl_point<D, D, BCX, BCY, BCZ, true>(P.L, P.gbx, P.gby, P.gbz, P.bpart, P.gR, e, k0, 0.0f,
                                           0.0f, (float)P.lambda, gv);
@@ -1059,8 +1087,8 @@ __device__ __forceinline__ void batch_ctrl_adam(const BatchProblem &P, const Bat
     }
 }
 
-template <int DELTA>
-__global__ void __launch_bounds__(BCfg<DELTA>::THREADS, 1)
+template <int DELTA, int T>
+__global__ void __launch_bounds__(BCfg<DELTA, T>::THREADS, BCfg<DELTA, T>::MINB)
     k_batch(const BatchProblem *__restrict__ probs, const BatchItem *__restrict__ items, int nitems,
             int *__restrict__ counters, BatchStep st)
 {
@@ -1084,12 +1112,15 @@ __global__ void __launch_bounds__(BCfg<DELTA>::THREADS, 1)
         const BatchProblem &P = probs[w.prob];
         if (w.kind == BATCH_BRICK) {
             const int bx = w.idx % P.gbx, r = w.idx / P.gbx, by = r % P.gby, bz = r / P.gby;
+            constexpr int BCX = BCfg<DELTA, T>::BCX, BCY = BCfg<DELTA, T>::BCY;
             if (P.g.ndim == 3)
-                fused_brick<3, DELTA, MODE_MSE>(P.g, P.L, P.F, P.M, P.c, nullptr, nullptr, nullptr,
-                                                nullptr, P.bpart, P.mpart, bx, by, bz, w.idx);
+                fused_brick<3, DELTA, MODE_MSE, BCX, BCY>(P.g, P.L, P.F, P.M, P.c, nullptr, nullptr,
+                                                          nullptr, nullptr, P.bpart, P.mpart, bx,
+                                                          by, bz, w.idx);
             else
-                fused_brick<2, DELTA, MODE_MSE>(P.g, P.L, P.F, P.M, P.c, nullptr, nullptr, nullptr,
-                                                nullptr, P.bpart, P.mpart, bx, by, bz, w.idx);
+                fused_brick<2, DELTA, MODE_MSE, BCX, BCY>(P.g, P.L, P.F, P.M, P.c, nullptr, nullptr,
+                                                          nullptr, nullptr, P.bpart, P.mpart, bx,
+                                                          by, bz, w.idx);
         } else if (w.kind == BATCH_GRAM) {
             // tile index = ((component * gtz + tz) * gty + ty) * gtx + tx
             const int tx = w.idx % P.gtx, r = w.idx / P.gtx, ty = r % P.gty, r2 = r / P.gty;
@@ -1133,40 +1164,56 @@ __global__ void __launch_bounds__(BCfg<DELTA>::THREADS, 1)
         const int64_t e = (int64_t)w.idx * blockDim.x + threadIdx.x;
         if (e < P.L.nc) {
             if (P.g.ndim == 3)
-                batch_ctrl_adam<3, DELTA>(P, st, e, k0, s_inv_bc[0], s_inv_bc[1]);
+                batch_ctrl_adam<3, DELTA, T>(P, st, e, k0, s_inv_bc[0], s_inv_bc[1]);
             else
-                batch_ctrl_adam<2, DELTA>(P, st, e, k0, s_inv_bc[0], s_inv_bc[1]);
+                batch_ctrl_adam<2, DELTA, T>(P, st, e, k0, s_inv_bc[0], s_inv_bc[1]);
         }
     }
 }
 
-template <int DELTA>
+template <int DELTA, int T>
 cudaError_t run_batch(int blocks, const BatchProblem *probs, const BatchItem *items, int nitems,
                       int *counters, const BatchStep &st, cudaStream_t s)
 {
-    using B = BCfg<DELTA>;
-    cudaError_t e = cudaFuncSetAttribute(k_batch<DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using B = BCfg<DELTA, T>;
+    cudaError_t e = cudaFuncSetAttribute(k_batch<DELTA, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)B::dyn_smem);
     if (e != cudaSuccess)
         return e;
     ProfScope ps(s, "k_batch");
-    k_batch<DELTA><<<blocks, B::THREADS, B::dyn_smem, s>>>(probs, items, nitems, counters, st);
+    k_batch<DELTA, T><<<blocks, B::THREADS, B::dyn_smem, s>>>(probs, items, nitems, counters, st);
     return cudaGetLastError();
 }
 
-template <int DELTA>
+template <int DELTA, int T>
 int batch_occupancy()
 {
-    using B = BCfg<DELTA>;
-    if (cudaFuncSetAttribute(k_batch<DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using B = BCfg<DELTA, T>;
+    if (cudaFuncSetAttribute(k_batch<DELTA, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)B::dyn_smem) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<DELTA>, B::THREADS, B::dyn_smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<DELTA, T>, B::THREADS,
+                                                      B::dyn_smem) != cudaSuccess)
         return 0;
     return n;
 }
+
+// (delta, tile) -> f<delta, tile>(args...), or `fail` for an unknown pair.
+#define AL_BATCH_DISPATCH(delta, tile, fail, CALL)          \
+    switch ((delta) * 16 + (tile)) {                        \
+    case 4 * 16 + 0: return CALL(4, 0);                     \
+    case 4 * 16 + 1: return CALL(4, 1);                     \
+    case 4 * 16 + 2: return CALL(4, 2);                     \
+    case 6 * 16 + 0: return CALL(6, 0);                     \
+    case 6 * 16 + 1: return CALL(6, 1);                     \
+    case 6 * 16 + 2: return CALL(6, 2);                     \
+    case 8 * 16 + 0: return CALL(8, 0);                     \
+    case 8 * 16 + 1: return CALL(8, 1);                     \
+    case 8 * 16 + 2: return CALL(8, 2);                     \
+    }                                                       \
+    return fail;
 
 }  // namespace
 
@@ -1211,10 +1258,12 @@ cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, 
     return cudaErrorInvalidValue;
 }
 
-void batch_geometry(const Grid &g, const Lattice &L, int *gb, int *gt, int *npart, int *nmom)
+void batch_geometry(const Grid &g, const Lattice &L, int tile, int *gb, int *gt, int *npart,
+                    int *nmom)
 {
     const int D = g.ndim;
-    const int BCX = brick_bcx(L.delta), BCY = brick_bcy(L.delta), BCZ = brick_bcz(D);
+    const int BCX = batch_tile_bcx(L.delta, tile), BCY = batch_tile_bcy(L.delta, tile);
+    const int BCZ = brick_bcz(D);
     const int cx = (g.X + L.delta - 1) / L.delta, cy = (g.Y + L.delta - 1) / L.delta;
     const int cz = (D == 3) ? (g.Z + L.delta - 1) / L.delta : 1;
     gb[0] = (cx + BCX - 1) / BCX;
@@ -1228,35 +1277,35 @@ void batch_geometry(const Grid &g, const Lattice &L, int *gb, int *gt, int *npar
     *nmom = 2;
 }
 
-int batch_threads(int delta)
+int batch_tiles() { return kBatchTiles; }
+
+void batch_tile_cells(int delta, int tile, int *bcx, int *bcy)
 {
-    switch (delta) {
-    case 4: return BCfg<4>::THREADS;
-    case 6: return BCfg<6>::THREADS;
-    case 8: return BCfg<8>::THREADS;
-    }
-    return 0;
+    *bcx = batch_tile_bcx(delta, tile);
+    *bcy = batch_tile_bcy(delta, tile);
 }
 
-int batch_blocks_per_sm(int delta)
+int batch_threads(int delta, int tile)
 {
-    switch (delta) {
-    case 4: return batch_occupancy<4>();
-    case 6: return batch_occupancy<6>();
-    case 8: return batch_occupancy<8>();
-    }
-    return 0;
+#define AL_THREADS(d, t) BCfg<d, t>::THREADS
+    AL_BATCH_DISPATCH(delta, tile, 0, AL_THREADS)
+#undef AL_THREADS
 }
 
-cudaError_t launch_batch(int delta, int blocks, const BatchProblem *probs, const BatchItem *items,
-                         int nitems, int *counters, const BatchStep &st, cudaStream_t s)
+int batch_blocks_per_sm(int delta, int tile)
 {
-    switch (delta) {
-    case 4: return run_batch<4>(blocks, probs, items, nitems, counters, st, s);
-    case 6: return run_batch<6>(blocks, probs, items, nitems, counters, st, s);
-    case 8: return run_batch<8>(blocks, probs, items, nitems, counters, st, s);
-    }
-    return cudaErrorInvalidValue;
+#define AL_OCC(d, t) batch_occupancy<d, t>()
+    AL_BATCH_DISPATCH(delta, tile, 0, AL_OCC)
+#undef AL_OCC
+}
+
+cudaError_t launch_batch(int delta, int tile, int blocks, const BatchProblem *probs,
+                         const BatchItem *items, int nitems, int *counters, const BatchStep &st,
+                         cudaStream_t s)
+{
+#define AL_RUN(d, t) run_batch<d, t>(blocks, probs, items, nitems, counters, st, s)
+    AL_BATCH_DISPATCH(delta, tile, cudaErrorInvalidValue, AL_RUN)
+#undef AL_RUN
 }
 
 AL_UNIT_ERROR_READER(unit_error_fused)

@@ -149,13 +149,19 @@ struct BatchStep {
     int *err;             // error word
 };
 
-// Geometry of a problem in a batch of spacing delta: brick grid, Gram tiles,
-// floats of one brick's partials and doubles of its moments.
-void batch_geometry(const Grid &g, const Lattice &L, int *gb, int *gt, int *npart, int *nmom);
-int batch_threads(int delta);               // 0 if delta has no batch kernel
-int batch_blocks_per_sm(int delta);         // resident blocks of the batch kernel per SM
-cudaError_t launch_batch(int delta, int blocks, const BatchProblem *probs, const BatchItem *items,
-                         int nitems, int *counters, const BatchStep &st, cudaStream_t s);
+// The batch kernel is built for batch_tiles() brick tiles per spacing (tile
+// 0: the single-problem path's brick). Geometry of a problem in a batch of
+// spacing delta with a tile: brick grid, Gram tiles, floats of one brick's
+// partials and doubles of its moments.
+int batch_tiles();
+void batch_tile_cells(int delta, int tile, int *bcx, int *bcy);
+void batch_geometry(const Grid &g, const Lattice &L, int tile, int *gb, int *gt, int *npart,
+                    int *nmom);
+int batch_threads(int delta, int tile);        // 0 if (delta, tile) has no batch kernel
+int batch_blocks_per_sm(int delta, int tile);  // resident blocks of the batch kernel per SM
+cudaError_t launch_batch(int delta, int tile, int blocks, const BatchProblem *probs,
+                         const BatchItem *items, int nitems, int *counters, const BatchStep &st,
+                         cudaStream_t s);
 
 // ---- diffeomorphic transformation: exp(v) by scaling and squaring ------------
 // traj (nullable): u_0 .. u_{K-1}; tmp: a field buffer, needed when traj is

@@ -314,7 +314,9 @@ class BatchResult:
     batch: airgb.Batch    # ctrl[i]: final coefficients; values[i]: J history
     device_ms: float      # the iterations' device time (CUDA events)
     policy: int           # work-item order in use
-    tuning_ms: list       # ms per iteration of each order (empty if not tuned)
+    tuning_ms: list       # ms per iteration of each (tile, order) (empty if not tuned)
+    tile: int = 0         # brick tile in use
+    tile_cells: tuple = ()  # control cells per block in x and y of that tile
 
 
 def register_batch(pairs, spacing=8, lam=0.1, iterations=100, lr=0.01, betas=(0.9, 0.999),
@@ -324,9 +326,9 @@ def register_batch(pairs, spacing=8, lam=0.1, iterations=100, lr=0.01, betas=(0.
     kernel; with graph=True all iterations are captured in one CUDA graph and
     replayed once. values[i][k] holds {J, S, R, n_mask} before step k + 1."""
     b = airgb.Batch(pairs, spacing, lam, history=iterations)
-    policy, tms = b.policy, []
+    tile, policy, tms = b.tile, b.policy, []
     if tune:
-        policy, tms = b.tune(3, lr, betas, eps)
+        tile, policy, tms = b.tune(3, lr, betas, eps)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if graph:
         g = torch.cuda.CUDAGraph()
@@ -345,7 +347,7 @@ def register_batch(pairs, spacing=8, lam=0.1, iterations=100, lr=0.01, betas=(0.
     st = b.status()
     if st != 0:
         raise airgb.AirgbError("al_batch_status", st)
-    return BatchResult(b, start.elapsed_time(stop), policy, tms)
+    return BatchResult(b, start.elapsed_time(stop), policy, tms, tile, b.tiles()[tile])
 
 
 def register_sequential(pairs, spacing=8, lam=0.1, iterations=100, lr=0.01, betas=(0.9, 0.999),

@@ -328,8 +328,11 @@ def test_batch_bind_tune_status_reject(lib):
     assert bind(nbytes=ws - 1) == 8
     assert bind(workspace=None) == 8
     p = airgb.al_adam_params(0.01, 0.9, 0.999, 1e-8)
-    assert lib.al_batch_tune(h, ctypes.byref(p), 5, None, None, None) == 8  # not bound
-    assert lib.al_batch_tune(h, ctypes.byref(p), 0, None, None, None) == 1
+    assert lib.al_batch_tune(h, ctypes.byref(p), 5, None, None, None, None) == 8  # not bound
+    assert lib.al_batch_tune(h, ctypes.byref(p), 0, None, None, None, None) == 1
+    assert lib.al_batch_set_tile(h, -1) == 1
+    assert lib.al_batch_set_tile(h, lib.al_batch_tiles(h, None)) == 1
+    assert lib.al_batch_set_tile(h, 1) == 0  # before binding: recorded for the bind
     assert lib.al_batch_status(None, None) == 1
     assert lib.al_batch_bind(None, ok, ok, ok, ok, ok, None, a, ctypes.c_size_t(ws)) == 1
     lib.al_batch_destroy(h)
