@@ -143,18 +143,27 @@ __device__ __forceinline__ bool axis_sample(int x, float u, int n, AxisSample &s
 // Branch-free form of axis_sample for kernels that load the cell whatever
 // the mask: cell is always in [0, n-2] (so the loads stay in bounds) and,
 // when the sample is inside, equals axis_sample's cell with f its offset
-// (f = 1 on the last face). Returns whether the sample is inside.
-__device__ __forceinline__ bool axis_cell(int x, float u, int n, int &cell, float &f)
+// (f = 1 on the last face). Returns whether the sample is inside; f is
+// meaningful only then. lo = -x and hi = n - 1 - x (exact floats, n < 2^22):
+// y = x + u lies in [0, n-1] exactly when lo <= u <= hi, which is false for
+// NaN and infinities too.
+//
+// floor(u) comes from one round-toward-minus-infinity add of 1.5 * 2^23:
+// for |u| < 2^22 the sum lies in [2^23, 2^24], where floats are the
+// integers, so it is exactly floor(u) + 1.5 * 2^23 and its low mantissa bits
+// hold floor(u) as an integer. Every inside sample has |u| < 2^22; for the
+// others the cell is clamped into range whatever the bits hold.
+__device__ __forceinline__ bool axis_cell(int x, float u, float lo, float hi, int n, int &cell,
+                                          float &f)
 {
-    const float fl = floorf(u);
-    const bool fin = fabsf(fl) < 1.0e9f;  // false for NaN and infinities
-    const int iy = fin ? x + (int)fl : -1;
-    const float fr = u - fl;
-    const bool in = fin && iy >= 0 && (iy < n - 1 || (iy == n - 1 && fr == 0.0f));
+    constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
+    const float t = __fadd_rd(u, kMagic);
+    const int iy = (int)((unsigned)x + (unsigned)__float_as_int(t) - 0x4B400000u);
+    const float fr = u - (t - kMagic);
     const int c = min(max(iy, 0), n - 2);
     cell = c;
-    f = fr + (float)(iy - c);  // iy - c is 1 on the last face, else 0 when inside
-    return in;
+    f = iy > c ? fr + 1.0f : fr;  // the last face: weight 1 on the last voxel
+    return u >= lo && u <= hi;
 }
 
 // Linear interpolation value and gradient in a 3D cell: corners m[z][y][x].

@@ -16,6 +16,8 @@
 // LCC needs W in a neighbourhood, so it runs as: k_fused<FWD> writes W, the
 // mask and dM~/dy, k_lcc_stats and k_lcc_grad turn W into dS/dW, and
 // k_fused<GW> projects dS/dW * dM~/dy onto the control points.
+#include <string.h>
+
 #include "launch.h"
 #include "profile.h"
 
@@ -68,13 +70,140 @@ struct FCfg {
     static constexpr int NMOM = (MODE == MODE_MSE) ? 2 : (MODE == MODE_NCC ? 6 : 0);
     static constexpr int NPART = CH * JZ * JY * JX;  // floats of one brick's partials
     static constexpr int VC = (MODE == MODE_FWD || MODE == MODE_MSE) ? 2 : 1;  // slices whose loads are in flight
-    // dynamic shared memory: up to NPL planes of column partials
-    // P[NPL][BY][BX][CHS] and their x contraction X[NPL][BY][JX][CHS]
+    // dynamic shared memory of the flush of up to NPL planes (flush_planes):
+    // region A, the column partials P[NPL][BY][BX][CHS], later their x
+    // contraction; region B, the per-cell sums S1[NPL][BY][BCX][4][CHS], later
+    // S2[NPL][BCY][4][JX][CHS]
     static constexpr int NPL = (D == 3) ? 4 : 1;
     static constexpr int nP = (MODE == MODE_FWD) ? 0 : NPL * BY * BX * CHS;
-    static constexpr int nX = (MODE == MODE_FWD) ? 0 : NPL * BY * JX * CHS;
+    static constexpr int nX = (MODE == MODE_FWD) ? 0 : NPL * BY * BCX * 4 * CHS;
     static constexpr size_t dyn_smem = (size_t)(nP + nX) * sizeof(float);
 };
+
+// Shared-memory staging of a 3D brick by TMA (single-problem path, X a
+// multiple of 4 so that image rows can be tensor-map rows):
+// * the moving image: one box of (BX + 2 HX) x (BY + 2 HY) voxels per slice,
+//   from (x0 - HX, y0 - HY), in a ring of NSLOT slices. While layer l (its
+//   DELTA output slices from zl = z0 + l DELTA) is computed, slices
+//   zl - HZ .. zl + DELTA + HZ - 1 are resident and the DELTA slices the next
+//   layer adds are in flight. A sample whose trilinear cell lies inside that
+//   window reads its 8 corners from shared memory, any other from global
+//   memory (|u| <= HZ voxels keeps every sample inside);
+// * the fixed image (MSE, NCC): one box of BX x BY x DELTA voxels per layer,
+//   two layers buffered;
+// * the control lattice: c's rows (nx floats) are not tensor-map rows, so it
+//   is copied through a one-dimensional view: one box per lattice plane of
+//   the brick's D x JZ x JY x JX block when the plane's JY rows fit one box of
+//   at most 256 floats (the box starts at the plane's first point rounded
+//   down to a 16-byte boundary), else one box of 16 floats per row; the
+//   boxes are then compacted into the brick's lattice block.
+// Copies land on mbarriers with bounded waits: batch b (the first: the
+// resident slices of layer 0; then the DELTA new slices and the fixed-image
+// layer of layer b) on barrier b % 2, the lattice rows on barrier 2.
+// Coordinates outside the volume or the lattice read zeros.
+__host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+
+template <int DELTA, int MODE>
+struct TCfg {
+    using C = FCfg<3, DELTA, MODE>;
+    static constexpr int BX = C::BX, BY = C::BY;
+    static constexpr int HX = 4, HY = 4, HZ = 4;  // HX keeps x0 - HX on a 16-byte boundary
+    static constexpr int TWX = BX + 2 * HX, TWY = BY + 2 * HY;
+    static constexpr int SLOTB = TWX * TWY * 4;
+    static constexpr int NRES = DELTA + 2 * HZ;  // slices resident while a layer is computed
+    static constexpr int NSLOT = NRES + DELTA;   // + the next layer's new slices
+    static constexpr int NF = (MODE == MODE_FWD) ? 0 : 2;
+    static constexpr int FSLOTB = BX * BY * DELTA * 4;
+    static constexpr int NROW = 3 * C::JZ * C::JY;  // lattice rows
+    static constexpr int LBOX = 16;                  // floats per row copy (offset <= 3, JX <= 11)
+    static constexpr int NPLN = 3 * C::JZ;           // lattice planes (one box each, <= 1 KB)
+    static constexpr int LSTAGE = NROW * 128 > NPLN * 1024 ? NROW * 128 : NPLN * 1024;
+    static constexpr int nP1 = (MODE == MODE_FWD) ? 0 : BY * BX * C::CHS;   // one-plane flush
+    static constexpr int nX1 = (MODE == MODE_FWD) ? 0 : BY * C::BCX * 4 * C::CHS;
+    static constexpr int oRing = 0;
+    static constexpr int oF = oRing + NSLOT * SLOTB;
+    static constexpr int oU = oF + NF * FSLOTB;  // lattice rows, later the flush buffers
+    static constexpr int nU = (LSTAGE > (nP1 + nX1) * 4) ? LSTAGE : (nP1 + nX1) * 4;
+    static constexpr int oBar = oU + round128(nU);
+    static constexpr int bytes = oBar + 3 * 8;
+    static_assert(SLOTB % 128 == 0 && FSLOTB % 128 == 0, "TMA destinations are 128-byte aligned");
+    static_assert(C::JX + 3 <= LBOX, "a lattice row copy holds the row");
+    static_assert(BX % 4 == 0, "brick origins stay on 16-byte boundaries");
+    static_assert(TWX <= 256 && TWY <= 256 && BX <= 256 && BY <= 256, "TMA box limits");
+};
+
+// Tensor maps of a brick staged by TMA (addresses of kernel parameters) and
+// the lattice copies: lbox floats per box into slots of lslot bytes, one box
+// per plane (lplane) or per row.
+struct BrickMaps {
+    const CUtensorMap *M, *F, *c;
+    int lbox, lslot, lplane;
+};
+
+// Host choice of the lattice copies of a brick (plane boxes when a plane's
+// rows fit one box of at most 256 floats).
+template <int DELTA>
+void lattice_boxes(const Lattice &L, int *lbox, int *lslot, int *lplane)
+{
+    using C = FCfg<3, DELTA, MODE_FWD>;
+    const int span = (C::JY - 1) * L.nx + C::JX + 3;  // offset <= 3
+    if (span <= 256) {
+        *lbox = (span + 3) / 4 * 4;
+        *lslot = round128(*lbox * 4);
+        *lplane = 1;
+    } else {
+        *lbox = 16;
+        *lslot = 128;
+        *lplane = 0;
+    }
+}
+
+constexpr int kFusedTimeout = 6;  // AL_ERR_TIMEOUT
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const CUtensorMap *map, int x,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2}], [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// Batch b of a brick's copies (issued by one thread): the moving-image
+// slices it adds to the ring and, for MSE/NCC, the fixed-image layer b.
+template <int DELTA, int MODE>
+__device__ __forceinline__ void brick_issue(const BrickMaps &tm, uint32_t sbase, int b, int x0,
+                                            int y0, int z0)
+{
+    using T = TCfg<DELTA, MODE>;
+    const uint32_t bar = sbase + T::oBar + 8 * (b & 1);
+    const int r0 = b == 0 ? 0 : T::NRES + (b - 1) * DELTA, r1 = T::NRES + b * DELTA;
+    mbar_expect(bar, (uint32_t)((r1 - r0) * T::SLOTB + (T::NF > 0 ? T::FSLOTB : 0)));
+    for (int r = r0; r < r1; ++r) {
+        const int slot = r % T::NSLOT;
+        tma_load_3d(sbase + T::oRing + slot * T::SLOTB, tm.M, x0 - T::HX, y0 - T::HY,
+                    z0 - T::HZ + r, bar);
+    }
+    if constexpr (T::NF > 0)
+        tma_load_3d(sbase + T::oF + (b & 1) * T::FSLOTB, tm.F, x0, y0, z0 + b * DELTA, bar);
+}
 
 // xy contraction of control plane jz for the column (qx + px/DELTA, ...):
 // sum_b wy[b] sum_e wx[e] cb[i][jz][qy + b][qx + e].
@@ -101,74 +230,107 @@ __device__ __forceinline__ void plane_xy(const float (&cb)[D][JZ][JY][JX], int j
 
 // Planes 0..NPL-1 of the thread's column partials qz -> x contraction -> y
 // contraction -> the brick's partial sums of local planes lp0 .. lp0+NPL-1.
-// Every thread of the block calls it. Cell-wise loops with compile-time
-// bounds and two accumulators per output.
+// Every thread of the block calls it. Each axis takes two steps: the four
+// weighted sums of every cell (the DELTA voxels of the cell times the
+// compile-time weights of their phases), then for every control point the
+// sum over the (up to four) cells it supports. A holds the column partials,
+// later the x contraction; B the per-cell sums of x, later those of y.
 template <int D, int DELTA, int MODE, int NPL, int BCX_ = brick_bcx(DELTA),
           int BCY_ = brick_bcy(DELTA)>
 __device__ __forceinline__ void flush_planes(int lp0, const float (&qz)[4][FCfg<D, DELTA, MODE>::CHS],
-                                             bool colvalid, int tx, int ty, float *P, float *Xc,
-                                             const float (*wt)[4], float *dst)
+                                             bool colvalid, int tx, int ty, float *A, float *B,
+                                             float *dst)
 {
     using C = FCfg<D, DELTA, MODE, BCX_, BCY_>;
     constexpr int CHS = C::CHS, BX = C::BX, BY = C::BY, JX = C::JX, JY = C::JY, JZ = C::JZ;
+    constexpr int BCX = C::BCX, BCY = C::BCY;
+    constexpr WTab<DELTA> kW{};
     const int tid = threadIdx.x;
 #pragma unroll
     for (int a = 0; a < NPL; ++a)
 #pragma unroll
         for (int k = 0; k < CHS; ++k)
-            P[((a * BY + ty) * BX + tx) * CHS + k] = colvalid ? qz[a][k] : 0.0f;
+            A[((a * BY + ty) * BX + tx) * CHS + k] = colvalid ? qz[a][k] : 0.0f;
     __syncthreads();
-    for (int e = tid; e < NPL * BY * JX * CHS; e += C::THREADS) {
-        const int k = e % CHS, r0 = e / CHS;
-        const int jxl = r0 % JX, r1 = r0 / JX;
-        const int yy = r1 % BY, a = r1 / BY;
-        float s0 = 0.0f, s1 = 0.0f;
+    // x, per cell: S1[(a BY + y) BCX + qx][q][k] = sum_px w[px][q] P[a][y][qx DELTA + px][k]
+    for (int e = tid; e < NPL * BY * BCX * CHS; e += C::THREADS) {
+        const int k = e % CHS, r = e / CHS;
+        const int qx = r % BCX, ay = r / BCX;
+        const float *src = A + (ay * BX + qx * DELTA) * CHS + k;
+        float sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4) {
-            const int q = jxl - e4;
-            if (q >= 0 && q < C::BCX) {
-                const float *src = P + ((a * BY + yy) * BX + q * DELTA) * CHS + k;
+        for (int px = 0; px < DELTA; ++px) {
+            const float v = src[px * CHS];
 #pragma unroll
-                for (int px = 0; px < DELTA; ++px) {
-                    if (px & 1)
-                        s1 = fmaf(wt[px][e4], src[px * CHS], s1);
-                    else
-                        s0 = fmaf(wt[px][e4], src[px * CHS], s0);
-                }
-            }
+            for (int q = 0; q < 4; ++q)
+                sq[q] = fmaf(kW.w[px][q], v, sq[q]);
         }
-        Xc[((a * BY + yy) * JX + jxl) * CHS + k] = s0 + s1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            B[(r * 4 + q) * CHS + k] = sq[q];
     }
     __syncthreads();
-    for (int e = tid; e < NPL * JY * JX * CHS; e += C::THREADS) {
-        const int jxl = e % JX, r0 = e / JX;
-        const int jyl = r0 % JY, r1 = r0 / JY;
-        const int k = r1 % CHS, a = r1 / CHS;
-        float s0 = 0.0f, s1 = 0.0f;
+    // x, per control point jx: cells jx - 3 .. jx (into A; P is dead)
+    for (int e = tid; e < NPL * BY * JX * CHS; e += C::THREADS) {
+        const int k = e % CHS, r = e / CHS;
+        const int jx = r % JX, ay = r / JX;
+        float sum = 0.0f;
 #pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4) {
-            const int q = jyl - e4;
-            if (q >= 0 && q < C::BCY) {
-                const float *src = Xc + ((a * BY + q * DELTA) * JX + jxl) * CHS + k;
-#pragma unroll
-                for (int py = 0; py < DELTA; ++py) {
-                    if (py & 1)
-                        s1 = fmaf(wt[py][e4], src[py * JX * CHS], s1);
-                    else
-                        s0 = fmaf(wt[py][e4], src[py * JX * CHS], s0);
-                }
-            }
+        for (int q = 0; q < 4; ++q) {
+            const int qx = jx - q;
+            if (qx >= 0 && qx < BCX)
+                sum += B[((ay * BCX + qx) * 4 + q) * CHS + k];
         }
-        dst[(k * JZ + lp0 + a) * JY * JX + jyl * JX + jxl] = s0 + s1;
+        A[r * CHS + k] = sum;
+    }
+    __syncthreads();
+    // y, per cell: S2[a BCY + qy][q][jx][k] = sum_py w[py][q] X[a][qy DELTA + py][jx][k]
+    for (int e = tid; e < NPL * BCY * JX * CHS; e += C::THREADS) {
+        const int k = e % CHS, r = e / CHS;
+        const int jx = r % JX, aq = r / JX;
+        const int a = aq / BCY, qy = aq - a * BCY;
+        const float *src = A + ((a * BY + qy * DELTA) * JX + jx) * CHS + k;
+        float sq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int py = 0; py < DELTA; ++py) {
+            const float v = src[py * JX * CHS];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                sq[q] = fmaf(kW.w[py][q], v, sq[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            B[((aq * 4 + q) * JX + jx) * CHS + k] = sq[q];
+    }
+    __syncthreads();
+    // y, per control point jy: cells jy - 3 .. jy
+    for (int e = tid; e < NPL * JY * JX * CHS; e += C::THREADS) {
+        const int jx = e % JX, r = e / JX;
+        const int jy = r % JY, r1 = r / JY;
+        const int k = r1 % CHS, a = r1 / CHS;
+        float sum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int qy = jy - q;
+            if (qy >= 0 && qy < BCY)
+                sum += B[(((a * BCY + qy) * 4 + q) * JX + jx) * CHS + k];
+        }
+        dst[(k * JZ + lp0 + a) * JY * JX + jy * JX + jx] = sum;
     }
 }
 
 // One brick (bx, by, bz) of one problem: the whole per-voxel work of the
 // brick, its partial sums written to bpart / mpart at index `brick`. Every
 // thread of a block of FCfg::THREADS threads calls it; it uses the block's
-// shared memory (static arrays here and FCfg::dyn_smem of dynamic memory).
-template <int D, int DELTA, int MODE, int BCX_ = brick_bcx(DELTA), int BCY_ = brick_bcy(DELTA)>
-__device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
+// shared memory (static arrays here and FCfg::dyn_smem of dynamic memory,
+// or TCfg::bytes + 128 with TMA). With TMA (3D, MSE/NCC/FWD) the lattice
+// block, the moving-image neighbourhood and the fixed image arrive by
+// tensor-map copies (TCfg); the arithmetic is the same either way, so both
+// give the same bits. Returns false if a copy did not land in time (the
+// brick's partials are then not written).
+template <int D, int DELTA, int MODE, int BCX_ = brick_bcx(DELTA), int BCY_ = brick_bcy(DELTA),
+          bool TMA = false>
+__device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                                             const float *__restrict__ F,
                                             const float *__restrict__ M,
                                             const float *__restrict__ c,
@@ -176,37 +338,103 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                                             float *__restrict__ W_out, uint8_t *__restrict__ m_out,
                                             float *__restrict__ G_io, float *__restrict__ bpart,
                                             double *__restrict__ mpart, int bx, int by, int bz,
-                                            int brick)
+                                            int brick, BrickMaps tm = BrickMaps{})
 {
     // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
     // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
     using C = FCfg<D, DELTA, MODE, BCX_, BCY_>;
+    using T = TCfg<DELTA, MODE == MODE_GW ? MODE_FWD : MODE>;
+    static_assert(!TMA || (D == 3 && MODE != MODE_GW && BCX_ == brick_bcx(DELTA) &&
+                           BCY_ == brick_bcy(DELTA)),
+                  "TMA staging: 3D single-problem bricks that gather");
     constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS, BX = C::BX;
     constexpr WTab<DELTA> kW{};  // weights of the compile-time z phases
     __shared__ float cb[D][JZ][JY][JX];
     __shared__ float wt[DELTA][4];
     __shared__ double red[(C::NMOM > 0 ? C::NMOM : 1) * ((C::THREADS + 31) / 32)];
     extern __shared__ float dsm[];
-    float *P = dsm, *Xc = dsm + C::nP;
+    unsigned char *sm = reinterpret_cast<unsigned char *>(dsm);
+    if constexpr (TMA)
+        sm += (128u - (al_smem_u32(dsm) & 127u)) & 127u;
+    const uint32_t sbase = al_smem_u32(sm);
+    float *P = TMA ? reinterpret_cast<float *>(sm + T::oU) : dsm;
+    float *Xc = TMA ? P + T::nP1 : dsm + C::nP;
+    const float *ring = reinterpret_cast<const float *>(sm + T::oRing);
+    const float *Fs = reinterpret_cast<const float *>(sm + T::oF);
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
     const int cx0 = bx * C::BCX, cy0 = by * C::BCY, cz0 = bz * C::BCZ;
     const int x = cx0 * DELTA + tx, y = cy0 * DELTA + ty, z0 = (D == 3) ? cz0 * DELTA : 0;
+    const int x0 = cx0 * DELTA, y0 = cy0 * DELTA;
 
     if (tid < DELTA * 4)
         wt[tid / 4][tid % 4] = L.w[tid / 4][tid % 4];
-    for (int e = tid; e < D * JZ * JY * JX; e += C::THREADS) {
-        const int i = e / (JZ * JY * JX);
-        int r = e - i * JZ * JY * JX;
-        const int lz = r / (JY * JX);
-        r -= lz * JY * JX;
-        const int ly = r / JX, lx = r - ly * JX;
-        const int jx = cx0 + lx, jy = cy0 + ly, jz = cz0 + lz;
-        float v = 0.0f;
-        if (jx < L.nx && jy < L.ny && jz < L.nz)
-            v = __ldg(c + (((int64_t)i * L.nz + jz) * L.ny + jy) * L.nx + jx);
-        cb[i][lz][ly][lx] = v;
+    bool ok = true;
+    if constexpr (TMA) {
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + T::oBar + 8 * k)
+                             : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            brick_issue<DELTA, MODE>(tm, sbase, 0, x0, y0, z0);
+            if (C::BCZ > 1)
+                brick_issue<DELTA, MODE>(tm, sbase, 1, x0, y0, z0);
+        }
+        // lattice boxes (one per plane or one per row), issued by the lanes
+        // of warp 1
+        const uint32_t lbar = sbase + T::oBar + 16;
+        const int nbox = tm.lplane ? D * JZ : D * JZ * JY;
+        if (tid >> 5 == 1) {
+            const int lane = tid & 31;
+            if (lane == 0)
+                mbar_expect(lbar, (uint32_t)(nbox * tm.lbox * 4));
+            __syncwarp();
+            for (int r = lane; r < nbox; r += 32) {
+                const int pl = tm.lplane ? r : r / JY, ly = tm.lplane ? 0 : r % JY;
+                const int i = pl / JZ, lz = pl % JZ;
+                const int row = ((i * L.nz + cz0 + lz) * L.ny + cy0 + ly) * L.nx;
+                tma_load_1d(sbase + T::oU + r * tm.lslot, tm.c, (row + cx0) & ~3, lbar);
+            }
+        }
+        ok = al_mbar_wait(lbar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(&g_unit_error, kFusedTimeout);
+                al_mbar_wait(sbase + T::oBar, 0);
+                if (C::BCZ > 1)
+                    al_mbar_wait(sbase + T::oBar + 8, 0);
+                al_mbar_wait(lbar, 0);
+            }
+            return false;
+        }
+        const float *boxes = reinterpret_cast<const float *>(sm + T::oU);
+        for (int e = tid; e < D * JZ * JY * JX; e += C::THREADS) {
+            const int r = e / JX, lx = e - r * JX;  // r = (i JZ + lz) JY + ly
+            const int pl = r / JY, ly = r - pl * JY;
+            const int i = pl / JZ, lz = pl - i * JZ;
+            const int row = ((i * L.nz + cz0 + lz) * L.ny + cy0 + (tm.lplane ? 0 : ly)) * L.nx;
+            const int b = tm.lplane ? pl : r;  // the box holding the point
+            const int o = ((row + cx0) & 3) + (tm.lplane ? ly * L.nx : 0) + lx;
+            (&cb[0][0][0][0])[e] = boxes[b * (tm.lslot / 4) + o];
+        }
+    } else {
+        for (int e = tid; e < D * JZ * JY * JX; e += C::THREADS) {
+            const int i = e / (JZ * JY * JX);
+            int r = e - i * JZ * JY * JX;
+            const int lz = r / (JY * JX);
+            r -= lz * JY * JX;
+            const int ly = r / JX, lx = r - ly * JX;
+            const int jx = cx0 + lx, jy = cy0 + ly, jz = cz0 + lz;
+            float v = 0.0f;
+            if (jx < L.nx && jy < L.ny && jz < L.nz)
+                v = __ldg(c + (((int64_t)i * L.nz + jz) * L.ny + jy) * L.nx + jx);
+            cb[i][lz][ly][lx] = v;
+        }
     }
     __syncthreads();
 
@@ -219,6 +447,9 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
         wy[e] = wt[py][e];
     }
     const bool colvalid = x < g.X && y < g.Y;
+    // sample bounds of axis_cell: y = x + u inside when -x <= u <= n - 1 - x
+    const float lox = (float)(-x), hix = (float)(g.X - 1 - x);
+    const float loy = (float)(-y), hiy = (float)(g.Y - 1 - y);
     float cxy[4][D];  // xy-contracted control values of the four active planes
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -239,9 +470,12 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
     const int cells_z = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
     const int nlayers = (D == 3) ? min(C::BCZ, cells_z - cz0) : 1;
     constexpr int NCOR = (D == 3) ? 8 : 4;
+    constexpr int VC = TMA ? 1 : C::VC;  // slices whose loads are in flight together
+    int fail_layer = -1;
     for (int cz = 0; cz < C::BCZ; ++cz) {
         const bool active = cz < nlayers && colvalid;
         const int zl0 = z0 + cz * DELTA;
+        const float loz0 = (float)(-zl0), hiz0 = (float)(g.Z - 1 - zl0);  // slice zl0 + pz: - pz
         // GW: the layer's loads are issued before the flush of the previous
         // plane, so they are in flight while the block contracts it
         float gv[MODE == MODE_GW ? DELTA : 1], gr[MODE == MODE_GW ? DELTA : 1][D];
@@ -265,7 +499,7 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
             // plane cz - 1 has all its contributions: write it out, roll
             if (MODE != MODE_FWD)
                 flush_planes<D, DELTA, MODE, 1, BCX_, BCY_>(cz - 1, qz, colvalid, tx, ty, P, Xc,
-                                                            wt, dstp);
+                                                            dstp);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -280,6 +514,19 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                 qz[3][k] = 0.0f;
             if (MODE != MODE_GW)
                 plane_xy<D, JZ, JY, JX>(cb, cz + 3, qyl, qxl, wx, wy, cxy[3]);
+        }
+        if constexpr (TMA) {
+            // this layer's copies; then every thread is past layer cz - 1, so
+            // the slots it used take the next layer's copies
+            ok = al_mbar_wait(sbase + T::oBar + 8 * (cz & 1), (uint32_t)(cz >> 1) & 1u);
+            if (__syncthreads_or(!ok)) {
+                fail_layer = cz;
+                break;
+            }
+            if (tid == 0 && cz >= 1 && cz + 1 < C::BCZ) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                brick_issue<DELTA, MODE>(tm, sbase, cz + 1, x0, y0, z0);
+            }
         }
         if (!active)
             continue;
@@ -302,13 +549,14 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                 }
             }
         } else {
+        const float *Fl = Fs + (cz & 1) * (T::FSLOTB / 4) + ty * BX + tx;
 #pragma unroll
-        for (int p0 = 0; p0 < DELTA; p0 += C::VC) {
+        for (int p0 = 0; p0 < DELTA; p0 += VC) {
             // issue every load of VC slices, then use them
-            float mcor[C::VC][NCOR], aux[C::VC], fx[C::VC], fy[C::VC], fz[C::VC];
-            bool inb[C::VC];
+            float mcor[VC][NCOR], aux[VC], fx[VC], fy[VC], fz[VC];
+            bool inb[VC];
 #pragma unroll
-            for (int j = 0; j < C::VC; ++j) {
+            for (int j = 0; j < VC; ++j) {
                 const int pz = p0 + j;
                 if (pz >= DELTA)
                     break;
@@ -324,35 +572,65 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
                 }
                 // cells are clamped into the volume even outside the mask, so
                 // every load is in bounds; the values outside are not used
-                int cx, cy, cz = 0;
-                bool in = axis_cell(x, uu[0], g.X, cx, fx[j]);
-                in &= axis_cell(y, uu[1], g.Y, cy, fy[j]);
+                int kx, ky, kz = 0;
+                bool in = axis_cell(x, uu[0], lox, hix, g.X, kx, fx[j]);
+                in &= axis_cell(y, uu[1], loy, hiy, g.Y, ky, fy[j]);
                 if (D == 3)
-                    in &= axis_cell(z, uu[2], g.Z, cz, fz[j]);
+                    in &= axis_cell(z, uu[2], loz0 - (float)pz, hiz0 - (float)pz, g.Z, kz, fz[j]);
                 inb[j] = in && (z < g.Z);
-                if (!(al_index_ok(cx, g.X - 1) & al_index_ok(cy, g.Y - 1) &
-                      al_index_ok(cz, D == 3 ? g.Z - 1 : 1)))
-                    cx = cy = cz = 0;  // checked builds only: the cell left the volume
-                const float *mp = M + ((D == 3 ? cz * g.Y : 0) + cy) * g.X + cx;  // nv < 2^31
-                mcor[j][0] = __ldg(mp);
-                mcor[j][1] = __ldg(mp + 1);
-                mcor[j][2] = __ldg(mp + g.X);
-                mcor[j][3] = __ldg(mp + g.X + 1);
-                if constexpr (D == 3) {
-                    const int sxy = g.X * g.Y;
-                    mcor[j][4] = __ldg(mp + sxy);
-                    mcor[j][5] = __ldg(mp + sxy + 1);
-                    mcor[j][6] = __ldg(mp + sxy + g.X);
-                    mcor[j][7] = __ldg(mp + sxy + g.X + 1);
+                if (!(al_index_ok(kx, g.X - 1) & al_index_ok(ky, g.Y - 1) &
+                      al_index_ok(kz, D == 3 ? g.Z - 1 : 1)))
+                    kx = ky = kz = 0;  // checked builds only: the cell left the volume
+                bool staged = false;
+                if constexpr (TMA) {
+                    // the cell and its +1 neighbours inside the staged window
+                    const unsigned rx = (unsigned)(kx - (x0 - T::HX));
+                    const unsigned ry = (unsigned)(ky - (y0 - T::HY));
+                    const unsigned rz = (unsigned)(kz - (zl0 - T::HZ));
+                    staged = rx <= (unsigned)(T::TWX - 2) && ry <= (unsigned)(T::TWY - 2) &&
+                             rz <= (unsigned)(T::NRES - 2);
+                    if (staged) {
+                        const int k0 = kz - (z0 - T::HZ);  // ring index of slice kz
+                        const int s0 = k0 >= T::NSLOT ? k0 - T::NSLOT : k0;
+                        const int s1 = k0 + 1 >= T::NSLOT ? k0 + 1 - T::NSLOT : k0 + 1;
+                        const int o = (int)ry * T::TWX + (int)rx;
+                        const float *p0s = ring + s0 * (T::SLOTB / 4) + o;
+                        const float *p1s = ring + s1 * (T::SLOTB / 4) + o;
+                        mcor[j][0] = p0s[0];
+                        mcor[j][1] = p0s[1];
+                        mcor[j][2] = p0s[T::TWX];
+                        mcor[j][3] = p0s[T::TWX + 1];
+                        mcor[j][4] = p1s[0];
+                        mcor[j][5] = p1s[1];
+                        mcor[j][6] = p1s[T::TWX];
+                        mcor[j][7] = p1s[T::TWX + 1];
+                    }
+                }
+                if (!staged) {
+                    const float *mp = M + ((D == 3 ? kz * g.Y : 0) + ky) * g.X + kx;  // nv < 2^31
+                    mcor[j][0] = __ldg(mp);
+                    mcor[j][1] = __ldg(mp + 1);
+                    mcor[j][2] = __ldg(mp + g.X);
+                    mcor[j][3] = __ldg(mp + g.X + 1);
+                    if constexpr (D == 3) {
+                        const int sxy = g.X * g.Y;
+                        mcor[j][4] = __ldg(mp + sxy);
+                        mcor[j][5] = __ldg(mp + sxy + 1);
+                        mcor[j][6] = __ldg(mp + sxy + g.X);
+                        mcor[j][7] = __ldg(mp + sxy + g.X + 1);
+                    }
                 }
                 aux[j] = 0.0f;
-                if ((MODE == MODE_MSE || MODE == MODE_NCC) &&
-                    al_index_ok((min(z, g.Z - 1) * g.Y + y) * g.X + x, g.nv))
-                    aux[j] = __ldg(F + (min(z, g.Z - 1) * g.Y + y) * g.X + x);
-
+                if constexpr (MODE == MODE_MSE || MODE == MODE_NCC) {
+                    if constexpr (TMA) {
+                        aux[j] = Fl[pz * (BX * C::BY)];  // zeros beyond the volume (unused)
+                    } else if (al_index_ok((min(z, g.Z - 1) * g.Y + y) * g.X + x, g.nv)) {
+                        aux[j] = __ldg(F + (min(z, g.Z - 1) * g.Y + y) * g.X + x);
+                    }
+                }
             }
 #pragma unroll
-            for (int j = 0; j < C::VC; ++j) {
+            for (int j = 0; j < VC; ++j) {
                 const int pz = p0 + j;
                 if (pz >= DELTA)
                     break;
@@ -415,11 +693,40 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
         }
         }  // MODE != MODE_GW
     }
+    if constexpr (TMA) {
+        if (fail_layer >= 0) {
+            // record the timeout; let the copies in flight land before the
+            // block's shared memory goes
+            if (tid == 0) {
+                atomicExch(&g_unit_error, kFusedTimeout);
+                // unconfirmed: batch fail_layer, and batch 1 when layer 0 failed
+                const int last = fail_layer == 0 ? min(1, C::BCZ - 1) : fail_layer;
+                for (int b = fail_layer; b <= last; ++b)
+                    al_mbar_wait(sbase + T::oBar + 8 * (b & 1), (uint32_t)(b >> 1) & 1u);
+            }
+            return false;
+        }
+    }
     if (MODE != MODE_FWD) {
-        // the last four planes (a single plane in 2D), together
-        flush_planes<D, DELTA, MODE, C::NPL, BCX_, BCY_>(D == 3 ? C::BCZ - 1 : 0, qz, colvalid,
-                                                         tx, ty, P, Xc,
-                                             wt, dstp);
+        if constexpr (TMA) {
+            // the last four planes one at a time (the staging leaves room for one)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                flush_planes<D, DELTA, MODE, 1, BCX_, BCY_>(C::BCZ - 1 + a, qz, colvalid, tx, ty,
+                                                            P, Xc, dstp);
+                if (a < 3) {
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int k = 0; k < CHS; ++k)
+                            qz[b][k] = qz[b + 1][k];
+                }
+            }
+        } else {
+            // the last four planes (a single plane in 2D), together
+            flush_planes<D, DELTA, MODE, C::NPL, BCX_, BCY_>(D == 3 ? C::BCZ - 1 : 0, qz,
+                                                             colvalid, tx, ty, P, Xc, dstp);
+        }
     }
     if (C::NMOM > 0) {
         double mm[C::NMOM > 0 ? C::NMOM : 1];
@@ -431,6 +738,7 @@ __device__ __forceinline__ void fused_brick(const Grid &g, const Lattice &L,
             for (int k = 0; k < C::NMOM; ++k)
                 mpart[(int64_t)brick * C::NMOM + k] = mm[k];
     }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -915,6 +1223,62 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
         gram2_tile(g, L, c, gb.gscale, gb.gR, tx, ty, comp, gb.rpart + w, gtile_sm);
 }
 
+// k_fused for 3D bricks staged by TMA (MSE, NCC, FWD; X a multiple of 4).
+template <int DELTA, int MODE>
+__global__ void __launch_bounds__(FCfg<3, DELTA, MODE>::THREADS,
+                                  (FCfg<3, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
+                                                                                             : 1)
+    k_fused_tma(const __grid_constant__ CUtensorMap mapM, const __grid_constant__ CUtensorMap mapF,
+                const __grid_constant__ CUtensorMap mapC, int3 lb, Grid g, Lattice L,
+                const float *__restrict__ F, const float *__restrict__ M,
+                const float *__restrict__ c, float *__restrict__ W_out,
+                uint8_t *__restrict__ m_out, float *__restrict__ G_io, float *__restrict__ bpart,
+                double *__restrict__ mpart, GramBlocks gb)
+{
+    const int b = blockIdx.x;
+    if (b < gb.nbricks) {
+        const int bx = b % gb.gbx, by = (b / gb.gbx) % gb.gby, bz = b / (gb.gbx * gb.gby);
+        fused_brick<3, DELTA, MODE, brick_bcx(DELTA), brick_bcy(DELTA), true>(
+            g, L, F, M, c, nullptr, W_out, m_out, G_io, bpart, mpart, bx, by, bz, b,
+            BrickMaps{&mapM, &mapF, &mapC, lb.x, lb.y, lb.z});
+        return;
+    }
+    const int w = b - gb.nbricks;
+    const int tx = w % gb.gtx, r = w / gb.gtx, ty = r % gb.gty, r2 = r / gb.gty;
+    const int tz = r2 % gb.gtz, comp = r2 / gb.gtz;
+    extern __shared__ float gtile_sm[];
+    gram3_tile(g, L, c, gb.gscale, gb.gR, tx, ty, tz, comp, gb.rpart + w, gtile_sm);
+}
+
+// Tensor maps of the TMA brick path; false when the volume does not allow
+// them (rows not on 16-byte boundaries, a box larger than the volume) or an
+// encoding fails, and the launch then takes the gathering path.
+template <int DELTA, int MODE>
+bool brick_tmaps(const Grid &g, const Lattice &L, const float *F, const float *M, const float *c,
+                 CUtensorMap *mM, CUtensorMap *mF, CUtensorMap *mC, int *lbox, int *lslot,
+                 int *lplane)
+{
+    using T = TCfg<DELTA, MODE>;
+    memset(mM, 0, sizeof(*mM));
+    memset(mF, 0, sizeof(*mF));
+    memset(mC, 0, sizeof(*mC));
+    if (g.ndim != 3 || g.X % 4 != 0 || g.X < T::TWX || g.Y < T::TWY || g.Z < DELTA)
+        return false;
+    const uint64_t dims[3] = {(uint64_t)g.X, (uint64_t)g.Y, (uint64_t)g.Z};
+    const uint64_t strides[2] = {(uint64_t)g.X * 4, (uint64_t)g.X * g.Y * 4};
+    const uint32_t boxM[3] = {(uint32_t)T::TWX, (uint32_t)T::TWY, 1u};
+    const uint32_t boxF[3] = {(uint32_t)T::BX, (uint32_t)T::BY, (uint32_t)DELTA};
+    lattice_boxes<DELTA>(L, lbox, lslot, lplane);
+    const uint64_t dimC[1] = {(uint64_t)3 * L.nc};
+    const uint32_t boxC[1] = {(uint32_t)*lbox};
+    if (!encode_tmap_f32(mM, 3, dims, strides, boxM, M) ||
+        !encode_tmap_f32(mC, 1, dimC, nullptr, boxC, c))
+        return false;
+    if (T::NF > 0 && !encode_tmap_f32(mF, 3, dims, strides, boxF, F))
+        return false;
+    return true;
+}
+
 template <int D, int DELTA, int MODE>
 cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay, char *ws,
                              const float *F, const float *M, const float *c, const float *gw,
@@ -939,6 +1303,23 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
                     : MODE == MODE_NCC ? "k_fused_ncc"
                     : MODE == MODE_FWD ? "k_fused_fwd"
                                        : "k_fused_gw");
+    if constexpr (D == 3 && MODE != MODE_GW) {
+        CUtensorMap mM, mF, mC;
+        int lbox = 0, lslot = 0, lplane = 0;
+        if (brick_tmaps<DELTA, MODE>(g, L, F, M, c, &mM, &mF, &mC, &lbox, &lslot, &lplane)) {
+            using T = TCfg<DELTA, MODE>;
+            const size_t tdyn = (size_t)T::bytes + 128 > gsm ? (size_t)T::bytes + 128 : gsm;
+            cudaError_t e = cudaFuncSetAttribute(k_fused_tma<DELTA, MODE>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)tdyn);
+            if (e != cudaSuccess)
+                return e;
+            k_fused_tma<DELTA, MODE><<<lay.nbricks + gb.ngram, C::THREADS, tdyn, s>>>(
+                mM, mF, mC, int3{lbox, lslot, lplane}, g, L, F, M, c, Wo, mo, G,
+                (float *)(ws + lay.bpart), (double *)(ws + lay.mpart), gb);
+            return cudaGetLastError();
+        }
+    }
     if (dyn > 0) {  // static + dynamic may pass 48 KB: always opt in
         const size_t most = gsm > C::dyn_smem ? gsm : C::dyn_smem;
         cudaError_t e = cudaFuncSetAttribute(k_fused<D, DELTA, MODE>,
