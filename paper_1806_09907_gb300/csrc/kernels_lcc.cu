@@ -73,24 +73,38 @@ struct LccB {
 // 16-byte boundary, so the staged row runs from x0 - 4 to x0 + 35 (40
 // floats) and column x0 - R sits at XOFF = 4 - R. Out-of-range elements of
 // the box arrive as zeros, as the zero padding of the box sums wants.
+// dS/dW * |X_m| = A' + 2 W B + F C on the mask, with (A', B, C) the box sums
+// of the coefficient planes (a', b, c). Per staged slice k, between two
+// barriers:
+// * x runs (threads 0 .. NXT-1): four neighbouring outputs of one row of the
+//   slice from 2R + 4 taps (a first sum, then sliding), into Xs[k % 2];
+// * every thread, for its output column: the y sum of slice k - 1 from
+//   Xs[(k - 1) % 2], then the z sums, sliding through a register ring of the
+//   last 2R + 1 x/y sums and recomputed from the ring every 2R + 1 slices so
+//   rounding does not build up; an output slice is complete once its last
+//   slice has entered.
+// After the barrier thread 0 refills the slot.
 template <int D, int R>
 struct LccT {
     static constexpr int TX = 32, TY = 16;
     static constexpr int RZ = (D == 3) ? R : 0, NR = 2 * RZ + 1, W1 = 2 * R + 1;
     static constexpr int LXT = 40, XOFF = 4 - R, LY = TY + 2 * R;
-    static constexpr int NX = LY * TX, NC = TX * TY;
     static constexpr int ZC = (D == 3) ? 64 : 1;  // most output slices per block
     static constexpr double HALO = 1.0;  // a halo slice takes its x/y box sums too
-    static constexpr int THREADS = NC;
-    static constexpr int NS = 4;                 // slices in flight
-    static constexpr int PLANE = LY * LXT;       // floats of one staged plane
+    static constexpr int GX = 4;                    // outputs per x run
+    static constexpr int NXT = LY * (TX / GX);      // x-run threads
+    static constexpr int THREADS = TX * TY;         // one output column each
+    static constexpr int NS = 4;                    // slices in flight
+    static constexpr int PLANE = LY * LXT;          // floats of one staged plane
     static constexpr uint32_t BOX_BYTES = 3u * PLANE * 4u;
     static constexpr int STAGE = (int)((BOX_BYTES + 127) / 128 * 128);
-    static constexpr int oX = NS * STAGE;        // two buffers of x sums, 3 planes of NX
-    static constexpr int oBar = oX + 2 * 3 * NX * 4;
+    static constexpr int XS = 3 * LY * TX;          // floats of one x-sum buffer
+    static constexpr int oX = NS * STAGE;           // two x-sum buffers
+    static constexpr int oBar = oX + 2 * XS * 4;
     static constexpr size_t smem = (size_t)oBar + NS * 8 + 128;  // + base alignment slack
     static_assert(R >= 1 && R <= 4 && XOFF + TX + 2 * R <= LXT, "staged row covers the halo");
-    static_assert(NX / 2 <= THREADS, "one x pair per thread");
+    static_assert(GX + 2 * R <= 12, "an x run reads three float4 of a staged row");
+    static_assert(NXT <= THREADS, "one x run per thread at most");
 };
 
 // Distance in floats between the planes a', b, c of the LCC coefficients.
@@ -805,135 +819,161 @@ __device__ __forceinline__ void lcc_tma_issue(const CUtensorMap *map, uint32_t s
         : "memory");
 }
 
-// One slice step of k_lcc_grad_tma (slice k of the block's range, zi its z).
-// Returns false when the slice's TMA load did not arrive in time (then every
-// thread of the block returns false at the same step).
+// x runs of one staged row (k_lcc_grad_tma): run t covers outputs
+// x0 + 4r .. x0 + 4r + 3 of row ly, from staged columns 4r .. 4r + 11.
+template <int D, int R>
+__device__ __forceinline__ void lcc_grad_xrun(const float *L, float *Xb, int t)
+{
+    using C = LccT<D, R>;
+    constexpr int RUNS = C::TX / C::GX, J0 = 4 - R;
+    const int ly = t / RUNS, r = t - ly * RUNS;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const float4 *src =
+            reinterpret_cast<const float4 *>(L + f * C::PLANE + ly * C::LXT + 4 * r);
+        float v[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 t4 = src[q];
+            v[4 * q] = t4.x;
+            v[4 * q + 1] = t4.y;
+            v[4 * q + 2] = t4.z;
+            v[4 * q + 3] = t4.w;
+        }
+        float o[4];
+        float s = v[J0];
+#pragma unroll
+        for (int d = 1; d <= 2 * R; ++d)
+            s += v[J0 + d];
+        o[0] = s;
+#pragma unroll
+        for (int i = 1; i < 4; ++i) {
+            s = (s - v[J0 + i - 1]) + v[J0 + i + 2 * R];
+            o[i] = s;
+        }
+        *reinterpret_cast<float4 *>(Xb + (f * C::LY + ly) * C::TX + 4 * r) =
+            make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Per-thread state of the y/z phase: the output column (tx, ty), the ring of
+// the last NR x/y sums, the running z sums and the core voxel (mask, F, W)
+// of the next output slice.
+template <int D, int R>
+struct GradYZ {
+    float3 ring[LccT<D, R>::NR];
+    float3 zs;
+    CoreVox core;
+};
+
+// Slice step k of k_lcc_grad_tma; P = k % NR at compile time (the block's
+// steps run in groups of NR), so the ring stays in registers. Returns false
+// when slice k did not arrive in time (every thread returns false at the same
+// step).
 template <int D, int R, int P>
 __device__ __forceinline__ bool lcc_grad_tma_step(const CUtensorMap *map, const Grid &g, int k,
-                                                  int zs, int zc0, int x0, int y0, int nslices,
+                                                  int zs, int zc1, int x0, int y0, int nslices,
                                                   const float *__restrict__ F,
                                                   const float *__restrict__ W,
                                                   const uint8_t *__restrict__ m,
                                                   float *__restrict__ gout, unsigned char *sm,
-                                                  float3 (&ring)[LccT<D, R>::NR], CoreVox &core,
-                                                  int &kfail)
+                                                  GradYZ<D, R> &st, int &kfail)
 {
     using C = LccT<D, R>;
-    constexpr int NX = C::NX, TX = C::TX, NR = C::NR, W1 = C::W1, LXT = C::LXT;
-    constexpr int PLANE = C::PLANE, OFF = C::XOFF & 1, NF2 = (OFF + W1 + 2) / 2;
+    constexpr int TX = C::TX, LY = C::LY, NR = C::NR;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int64_t sY = g.X, sZ = (int64_t)g.X * g.Y;
-    const int zi = zs + k, slot = k % C::NS;
     const uint32_t sbase = lsm_u32(sm);
-    const bool arrived = lbar_wait(sbase + C::oBar + 8 * slot, (uint32_t)(k / C::NS) & 1u);
-    const float *L = reinterpret_cast<const float *>(sm + slot * C::STAGE);
-    float *X = reinterpret_cast<float *>(sm + C::oX) + (k & 1) * 3 * NX;
-    // the core voxel of the output slice zo = zi - RZ (fetched one step ago);
-    // start fetching the core voxel of the next output slice
-    const int zo = zi - C::RZ;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool out = zo >= zc0 && x < g.X && y < g.Y;
-    const int64_t vo = (int64_t)zo * sZ + (int64_t)y * sY + x;
-    const uint8_t mo = core.m;
-    const float fo = core.f, wo = core.w;
-    if (zo + 1 >= zc0 && zo + 1 < zs + nslices - C::RZ && x < g.X && y < g.Y) {
-        const int64_t vn = vo + sZ;
-        core.m = __ldg(m + vn);
-        core.f = __ldg(F + vn);
-        core.w = __ldg(W + vn);
+    float *Xs = reinterpret_cast<float *>(sm + C::oX);
+    bool ok = true;
+    // x runs of slice k
+    if (k < nslices && tid < C::NXT) {
+        const int slot = k % C::NS;
+        const uint32_t bar = sbase + C::oBar + 8 * slot, par = (uint32_t)(k / C::NS) & 1u;
+        ok = lbar_try_wait(bar, par) || lbar_wait(bar, par);
+        if (ok)
+            lcc_grad_xrun<D, R>(reinterpret_cast<const float *>(sm + slot * C::STAGE),
+                                Xs + (k & 1) * C::XS, tid);
     }
-    // x box sums of every row of the staged slice, two neighbouring outputs
-    // per thread, taps read as float2 from the even column at or below the
-    // first tap
-    if (arrived && tid < NX / 2) {
-        const int ly = tid / (TX / 2), p2 = 2 * (tid - ly * (TX / 2));
+    // y sum of slice k - 1 for this thread's output column, its z sums
+    if (k >= 1) {
+        const int kk = k - 1;
+        constexpr int IDX = (P + NR - 1) % NR;  // ring slot of slice kk
+        const float *Xb = Xs + (kk & 1) * C::XS + ty * TX + tx;
+        float a = 0.f, b = 0.f, c = 0.f;
 #pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-            const float2 *src =
-                reinterpret_cast<const float2 *>(L + q3 * PLANE + ly * LXT + p2 + (C::XOFF - OFF));
-            float v[2 * NF2];
+        for (int d = 0; d < 2 * R + 1; ++d) {
+            a += Xb[d * TX];
+            b += Xb[(LY + d) * TX];
+            c += Xb[(2 * LY + d) * TX];
+        }
+        const float3 old = st.ring[IDX];
+        st.ring[IDX] = make_float3(a, b, c);
+        if (IDX == NR - 1) {
+            // the ring holds slices kk - NR + 1 .. kk: recompute the sums
+            float3 s = st.ring[0];
 #pragma unroll
-            for (int q = 0; q < NF2; ++q) {
-                const float2 t = src[q];
-                v[2 * q] = t.x;
-                v[2 * q + 1] = t.y;
+            for (int q = 1; q < NR; ++q) {
+                s.x += st.ring[q].x;
+                s.y += st.ring[q].y;
+                s.z += st.ring[q].z;
             }
-            float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-            for (int d = 0; d < W1; ++d) {
-                s0 += v[OFF + d];
-                s1 += v[OFF + d + 1];
+            st.zs = s;
+        } else {
+            st.zs = make_float3((st.zs.x - old.x) + a, (st.zs.y - old.y) + b,
+                                (st.zs.z - old.z) + c);
+        }
+        if (kk >= 2 * C::RZ) {  // output slice zs + kk - RZ is complete
+            const int zo = zs + kk - C::RZ, x = x0 + tx, y = y0 + ty;
+            if (x < g.X && y < g.Y) {
+                const int64_t sZ = (int64_t)g.X * g.Y;
+                const int64_t vo = (int64_t)zo * sZ + (int64_t)y * g.X + x;
+                const CoreVox cv = st.core;
+                if (zo + 1 < zc1) {
+                    st.core.m = __ldg(m + vo + sZ);
+                    st.core.f = __ldg(F + vo + sZ);
+                    st.core.w = __ldg(W + vo + sZ);
+                }
+                gout[vo] = cv.m ? fmaf(2.0f * cv.w, st.zs.y, fmaf(cv.f, st.zs.z, st.zs.x)) : 0.0f;
             }
-            *reinterpret_cast<float2 *>(X + q3 * NX + ly * TX + p2) = make_float2(s0, s1);
         }
     }
-    // every thread has read slot `slot`: it may be refilled with slice k + NS
-    if (__syncthreads_or(!arrived)) {
+    // every thread is done with slot k % NS and with x buffer (k - 1) % 2
+    if (__syncthreads_or(!ok)) {
         kfail = k;
         return false;
     }
     if (tid == 0 && k + C::NS < nslices) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        lcc_tma_issue<D, R>(map, sbase, k + C::NS, x0, y0, zi + C::NS);
-    }
-    // y box sum of this column: this slice's entry of the z ring
-    {
-        float a = 0.f, b = 0.f, c = 0.f;
-#pragma unroll
-        for (int d = 0; d < W1; ++d) {
-            const int r = (ty + d) * TX + tx;
-            a += X[r];
-            b += X[NX + r];
-            c += X[2 * NX + r];
-        }
-        ring[P] = make_float3(a, b, c);
-    }
-    if (out) {
-        float gv = 0.0f;
-        if (mo) {
-            float A = 0.f, B = 0.f, Cc = 0.f;
-#pragma unroll
-            for (int t = 0; t < NR; ++t) {
-                A += ring[t].x;
-                B += ring[t].y;
-                Cc += ring[t].z;
-            }
-            gv = fmaf(2.0f * wo, B, fmaf(fo, Cc, A));
-        }
-        gout[vo] = gv;
+        lcc_tma_issue<D, R>(map, sbase, k + C::NS, x0, y0, zs + k + C::NS);
     }
     return true;
 }
 
 template <int D, int R, int P>
 __device__ __forceinline__ bool lcc_grad_tma_steps(const CUtensorMap *map, const Grid &g, int kb,
-                                                   int zs, int zc0, int x0, int y0, int nslices,
+                                                   int zs, int zc1, int x0, int y0, int nslices,
                                                    const float *__restrict__ F,
                                                    const float *__restrict__ W,
                                                    const uint8_t *__restrict__ m,
                                                    float *__restrict__ gout, unsigned char *sm,
-                                                   float3 (&ring)[LccT<D, R>::NR], CoreVox &core,
-                                                   int &kfail)
+                                                   GradYZ<D, R> &st, int &kfail)
 {
     if constexpr (P < LccT<D, R>::NR) {
-        if (kb + P < nslices) {
-            if (!lcc_grad_tma_step<D, R, P>(map, g, kb + P, zs, zc0, x0, y0, nslices, F, W, m,
-                                            gout, sm, ring, core, kfail))
+        if (kb + P <= nslices) {
+            if (!lcc_grad_tma_step<D, R, P>(map, g, kb + P, zs, zc1, x0, y0, nslices, F, W, m,
+                                            gout, sm, st, kfail))
                 return false;
-            return lcc_grad_tma_steps<D, R, P + 1>(map, g, kb, zs, zc0, x0, y0, nslices, F, W, m,
-                                                   gout, sm, ring, core, kfail);
+            return lcc_grad_tma_steps<D, R, P + 1>(map, g, kb, zs, zc1, x0, y0, nslices, F, W, m,
+                                                   gout, sm, st, kfail);
         }
     }
     return true;
 }
 
-// k_lcc_grad with TMA-staged coefficient slices: the block's z range (its
-// chunk and the 2R halo slices) streams through NS shared-memory slots, each
-// filled by one tile load of the three planes; thread 0 refills a slot once
-// every thread has passed the barrier after its x sums. Every wait is
-// bounded: a slice that does not arrive within about a second records
-// AL_ERR_TIMEOUT, and thread 0 waits (bounded again) for the loads still in
-// flight before the block returns.
+// k_lcc_grad with TMA-staged coefficient slices (tile and phases: LccT).
+// Every wait is bounded: a slice that does not arrive within about a second
+// records AL_ERR_TIMEOUT, and thread 0 waits (bounded again) for the loads
+// still in flight before the block returns.
 template <int D, int R>
 __global__ void __launch_bounds__(LccT<D, R>::THREADS, 2)
     k_lcc_grad_tma(const __grid_constant__ CUtensorMap map, Grid g, int zc,
@@ -959,24 +999,25 @@ __global__ void __launch_bounds__(LccT<D, R>::THREADS, 2)
     if (tid == 0)
         for (int k = 0; k < C::NS && k < nslices; ++k)
             lcc_tma_issue<D, R>(&map, sbase, k, x0, y0, zs + k);
-    float3 ring[C::NR];
+    GradYZ<D, R> st;
 #pragma unroll
-    for (int t = 0; t < C::NR; ++t)
-        ring[t] = make_float3(0.f, 0.f, 0.f);
-    CoreVox core{0, 0.f, 0.f};
+    for (int q = 0; q < C::NR; ++q)
+        st.ring[q] = make_float3(0.f, 0.f, 0.f);
+    st.zs = make_float3(0.f, 0.f, 0.f);
+    st.core = CoreVox{0, 0.f, 0.f};
     {
         const int x = x0 + tid % C::TX, y = y0 + tid / C::TX;
         if (x < g.X && y < g.Y) {  // first output slice is zc0
             const int64_t v = (int64_t)zc0 * ((int64_t)g.X * g.Y) + (int64_t)y * g.X + x;
-            core.m = __ldg(m + v);
-            core.f = __ldg(F + v);
-            core.w = __ldg(W + v);
+            st.core.m = __ldg(m + v);
+            st.core.f = __ldg(F + v);
+            st.core.w = __ldg(W + v);
         }
     }
     int kfail = -1;
-    for (int kb = 0; kb < nslices; kb += C::NR) {
-        if (lcc_grad_tma_steps<D, R, 0>(&map, g, kb, zs, zc0, x0, y0, nslices, F, W, m, gout, sm,
-                                        ring, core, kfail))
+    for (int kb = 0; kb <= nslices; kb += C::NR) {
+        if (lcc_grad_tma_steps<D, R, 0>(&map, g, kb, zs, zc1, x0, y0, nslices, F, W, m, gout, sm,
+                                        st, kfail))
             continue;
         // slice kfail timed out: record it, then let the loads issued for
         // slices kfail .. kfail + NS - 1 land before the block's memory goes

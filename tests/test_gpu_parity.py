@@ -330,7 +330,9 @@ def check_objective(F, M, c, delta, sim, window=7, lam=0.1, fused=True):
     assert int(excl.sum()) <= reach, (int(excl.sum()), reach)
     if F.size >= 100_000:
         assert keep.mean() >= 0.95, (n_kink, n_face, keep.mean())
-    assert rel_l2(g[keep], gref[keep]) <= G_TOL
+    rel = rel_l2(g[keep], gref[keep])
+    print(f"dJ/dc rel L2 {rel:.3e}, J rel {abs(val[0] - ref['J']) / abs(ref['J']):.3e}")
+    assert rel <= G_TOL
     err = np.abs(g - gref)[excl]
     assert np.all(err <= bound[excl] + G_TOL * np.abs(gref).max())
     if sim == "lcc" and fused and delta in (4, 6, 8):
