@@ -69,7 +69,7 @@ struct FCfg {
     static constexpr int CHS = CH > 0 ? CH : 1;  // storage size
     static constexpr int NMOM = (MODE == MODE_MSE) ? 2 : (MODE == MODE_NCC ? 6 : 0);
     static constexpr int NPART = CH * JZ * JY * JX;  // floats of one brick's partials
-    static constexpr int VC = (MODE == MODE_FWD || MODE == MODE_MSE) ? 2 : 1;  // slices whose loads are in flight
+    static constexpr int VC = (MODE == MODE_FWD) ? 2 : 1;  // slices whose gathers are in flight together
     // dynamic shared memory of the flush of up to NPL planes (flush_planes):
     // region A, the column partials P[NPL][BY][BX][CHS], later their x
     // contraction; region B, the per-cell sums S1[NPL][BY][BCX][4][CHS], later
@@ -77,7 +77,11 @@ struct FCfg {
     static constexpr int NPL = (D == 3) ? 4 : 1;
     static constexpr int nP = (MODE == MODE_FWD) ? 0 : NPL * BY * BX * CHS;
     static constexpr int nX = (MODE == MODE_FWD) ? 0 : NPL * BY * BCX * 4 * CHS;
-    static constexpr size_t dyn_smem = (size_t)(nP + nX) * sizeof(float);
+    // the x contractions of the lattice rows of four planes, per voxel column
+    // (plane_rows), after the flush buffers; GW does not expand
+    static constexpr int RPL = D * JY * BX;  // floats of one plane's row contractions
+    static constexpr int nR = (MODE == MODE_GW) ? 0 : 4 * RPL;
+    static constexpr size_t dyn_smem = (size_t)(nP + nX + nR) * sizeof(float);
 };
 
 // Shared-memory staging of a 3D brick by TMA (single-problem path, X a
@@ -123,7 +127,8 @@ struct TCfg {
     static constexpr int oRing = 0;
     static constexpr int oF = oRing + NSLOT * SLOTB;
     static constexpr int oU = oF + NF * FSLOTB;  // lattice rows, later the flush buffers
-    static constexpr int nU = (LSTAGE > (nP1 + nX1) * 4) ? LSTAGE : (nP1 + nX1) * 4;
+    static constexpr int oR = (nP1 + nX1) * 4;  // row contractions, inside the union
+    static constexpr int nU = (LSTAGE > oR + C::nR * 4) ? LSTAGE : oR + C::nR * 4;
     static constexpr int oBar = oU + round128(nU);
     static constexpr int bytes = oBar + 3 * 8;
     static_assert(SLOTB % 128 == 0 && FSLOTB % 128 == 0, "TMA destinations are 128-byte aligned");
@@ -205,24 +210,44 @@ __device__ __forceinline__ void brick_issue(const BrickMaps &tm, uint32_t sbase,
         tma_load_3d(sbase + T::oF + (b & 1) * T::FSLOTB, tm.F, x0, y0, z0 + b * DELTA, bar);
 }
 
-// xy contraction of control plane jz for the column (qx + px/DELTA, ...):
-// sum_b wy[b] sum_e wx[e] cb[i][jz][qy + b][qx + e].
-template <int D, int JZ, int JY, int JX>
-__device__ __forceinline__ void plane_xy(const float (&cb)[D][JZ][JY][JX], int jz, int qy, int qx,
-                                         const float (&wx)[4], const float (&wy)[4], float (&out)[D])
+// xy contraction of control plane jz for the voxel columns of a brick, in
+// two steps that share the x contraction among the DELTA columns of a cell
+// row:
+// plane_rows (every thread of the block): for each of its items (component
+// i, lattice row ly, voxel column tx = the thread's own column),
+//   Rw[i][ly][tx] = sum_e wx[e] cb[i][jz][ly][qx + e];
+// plane_cols (after a barrier): the thread's column,
+//   out[i] = sum_b wy[b] Rw[i][qy + b][tx].
+template <int D, int JZ, int JY, int JX, int BX, int THREADS>
+__device__ __forceinline__ void plane_rows(const float (&cb)[D][JZ][JY][JX], int jz, int qx,
+                                           const float (&wx)[4], float *Rw)
+{
+    if (jz >= JZ)
+        return;
+    for (int e = threadIdx.x; e < D * JY * BX; e += THREADS) {
+        const int r = e / BX;  // i * JY + ly; e % BX is the thread's column
+        const float *row = &cb[0][0][0][0] + ((r / JY) * JZ + jz) * (JY * JX) + (r % JY) * JX + qx;
+        float v = wx[0] * row[0];
+        v = fmaf(wx[1], row[1], v);
+        v = fmaf(wx[2], row[2], v);
+        v = fmaf(wx[3], row[3], v);
+        Rw[e] = v;
+    }
+}
+
+template <int D, int JZ, int JY, int BX>
+__device__ __forceinline__ void plane_cols(const float *Rw, int jz, int qy, int tx,
+                                           const float (&wy)[4], float (&out)[D])
 {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         float acc = 0.0f;
         if (jz < JZ) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                float r = wx[0] * cb[i][jz][qy + b][qx];
-                r = fmaf(wx[1], cb[i][jz][qy + b][qx + 1], r);
-                r = fmaf(wx[2], cb[i][jz][qy + b][qx + 2], r);
-                r = fmaf(wx[3], cb[i][jz][qy + b][qx + 3], r);
-                acc = fmaf(wy[b], r, acc);
-            }
+            const float *col = Rw + (i * JY + qy) * BX + tx;
+            acc = wy[0] * col[0];
+            acc = fmaf(wy[1], col[BX], acc);
+            acc = fmaf(wy[2], col[2 * BX], acc);
+            acc = fmaf(wy[3], col[3 * BX], acc);
         }
         out[i] = acc;
     }
@@ -359,6 +384,7 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     const uint32_t sbase = al_smem_u32(sm);
     float *P = TMA ? reinterpret_cast<float *>(sm + T::oU) : dsm;
     float *Xc = TMA ? P + T::nP1 : dsm + C::nP;
+    float *Rw = TMA ? reinterpret_cast<float *>(sm + T::oU + T::oR) : dsm + C::nP + C::nX;
     const float *ring = reinterpret_cast<const float *>(sm + T::oRing);
     const float *Fs = reinterpret_cast<const float *>(sm + T::oF);
 
@@ -451,10 +477,15 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     const float lox = (float)(-x), hix = (float)(g.X - 1 - x);
     const float loy = (float)(-y), hiy = (float)(g.Y - 1 - y);
     float cxy[4][D];  // xy-contracted control values of the four active planes
+    if constexpr (MODE != MODE_GW) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-        if (MODE != MODE_GW)
-            plane_xy<D, JZ, JY, JX>(cb, a, qyl, qxl, wx, wy, cxy[a]);
+        for (int a = 0; a < 4; ++a)
+            plane_rows<D, JZ, JY, JX, BX, C::THREADS>(cb, a, qxl, wx, Rw + a * C::RPL);
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            plane_cols<D, JZ, JY, BX>(Rw + a * C::RPL, a, qyl, tx, wy, cxy[a]);
+    }
     float qz[4][CHS];  // column partial sums of the four active planes
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -512,8 +543,11 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
 #pragma unroll
             for (int k = 0; k < CHS; ++k)
                 qz[3][k] = 0.0f;
+            // row contractions of plane cz + 3 (into the buffer of plane
+            // cz - 1, last read before the previous layer's barrier)
             if (MODE != MODE_GW)
-                plane_xy<D, JZ, JY, JX>(cb, cz + 3, qyl, qxl, wx, wy, cxy[3]);
+                plane_rows<D, JZ, JY, JX, BX, C::THREADS>(cb, cz + 3, qxl, wx,
+                                                          Rw + ((cz + 3) & 3) * C::RPL);
         }
         if constexpr (TMA) {
             // this layer's copies; then every thread is past layer cz - 1, so
@@ -527,7 +561,11 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 brick_issue<DELTA, MODE>(tm, sbase, cz + 1, x0, y0, z0);
             }
+        } else if (MODE != MODE_GW && cz > 0) {
+            __syncthreads();  // the row contractions of plane cz + 3 are written
         }
+        if (MODE != MODE_GW && cz > 0)
+            plane_cols<D, JZ, JY, BX>(Rw + ((cz + 3) & 3) * C::RPL, cz + 3, qyl, tx, wy, cxy[3]);
         if (!active)
             continue;
         if constexpr (MODE == MODE_GW) {
@@ -1048,10 +1086,10 @@ __global__ void k_finalize(int mode, int64_t nv, double lambda, double eps, Part
 // scalars k0..k2, plus lambda * dR/dc. CG: the partials were written by other
 // blocks of the same launch.
 template <int D, int CH, int BCX, int BCY, int BCZ, bool CG>
-__device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, int gbz,
-                                           const float *__restrict__ bpart,
-                                           const float *__restrict__ gR, int64_t e, float k0,
-                                           float k1, float k2, float lam, float (&out)[D])
+__device__ __forceinline__ void ctrl_sum(const Lattice &L, int gbx, int gby, int gbz,
+                                         const float *__restrict__ bpart,
+                                         const float *__restrict__ gR, int64_t e, float (&p)[CH],
+                                         float (&gr)[D])
 {
     constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
     constexpr int NPART = CH * JZ * JY * JX;
@@ -1059,7 +1097,6 @@ __device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, i
     const int jx = (int)(e % L.nx);
     const int64_t r = e / L.nx;
     const int jy = (int)(r % L.ny), jz = (int)(r / L.ny);
-    float p[CH];
 #pragma unroll
     for (int k = 0; k < CH; ++k)
         p[k] = 0.0f;
@@ -1086,21 +1123,41 @@ __device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, i
         }
     }
 #pragma unroll
+    for (int i = 0; i < D; ++i)
+        gr[i] = CG ? __ldcg(gR + (int64_t)i * total + e) : __ldg(gR + (int64_t)i * total + e);
+}
+
+template <int D, int CH>
+__device__ __forceinline__ void ctrl_combine(const float (&p)[CH], const float (&gr)[D], float k0,
+                                             float k1, float k2, float lam, float (&out)[D])
+{
+#pragma unroll
     for (int i = 0; i < D; ++i) {
         float v;
         if (CH == 3 * D)
             v = fmaf(k0, p[i], fmaf(k1, p[D + i], k2 * p[2 * D + i]));
         else
             v = k0 * p[i];
-        const float gr = CG ? __ldcg(gR + (int64_t)i * total + e) : __ldg(gR + (int64_t)i * total + e);
-        out[i] = fmaf(lam, gr, v);
+        out[i] = fmaf(lam, gr[i], v);
     }
 }
 
-// Per control point: fixed-order sum of the partials of the bricks that
-// touch it, channel combination, plus lambda * dR/dc.
-// Every block first evaluates the scalars of the objective (the partial
-// sums are few), block 0 writes {J, S, R, n_mask}.
+template <int D, int CH, int BCX, int BCY, int BCZ, bool CG>
+__device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, int gbz,
+                                           const float *__restrict__ bpart,
+                                           const float *__restrict__ gR, int64_t e, float k0,
+                                           float k1, float k2, float lam, float (&out)[D])
+{
+    float p[CH], gr[D];
+    ctrl_sum<D, CH, BCX, BCY, BCZ, CG>(L, gbx, gby, gbz, bpart, gR, e, p, gr);
+    ctrl_combine<D, CH>(p, gr, k0, k1, k2, lam, out);
+}
+
+// Per control point (one per thread): fixed-order sum of the partials of the
+// bricks that touch it, channel combination, plus lambda * dR/dc. Every
+// block also evaluates the scalars of the objective (the partial sums are
+// few); a thread issues its point's loads first, so their latency overlaps
+// that reduction. Block 0 writes {J, S, R, n_mask}.
 template <int D, int CH, int BCX, int BCY, int BCZ>
 __global__ void __launch_bounds__(256)
     k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, int64_t nv, double lambda, double eps,
@@ -1109,24 +1166,25 @@ __global__ void __launch_bounds__(256)
 {
     __shared__ double red[6 * 8];
     __shared__ double ks[3];
-    objective_scalars(mode, nv, lambda, eps, P, blockIdx.x == 0 ? value : nullptr, ks, red);
     const int64_t total = (int64_t)L.nc;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float p[CH], gr[D];
+    if (e < total)
+        ctrl_sum<D, CH, BCX, BCY, BCZ, false>(L, gbx, gby, gbz, bpart, gR, e, p, gr);
+    objective_scalars(mode, nv, lambda, eps, P, blockIdx.x == 0 ? value : nullptr, ks, red);
+    if (e >= total)
+        return;
     const float k0 = (float)ks[0];
     float k1 = 0.f, k2 = 0.f;
     if (CH == 3 * D) {
         k1 = (float)ks[1];
         k2 = (float)ks[2];
     }
-    const float lam = (float)lambda;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        float v[D];
-        ctrl_point<D, CH, BCX, BCY, BCZ, false>(L, gbx, gby, gbz, bpart, gR, e, k0, k1, k2, lam,
-                                                v);
+    float v[D];
+    ctrl_combine<D, CH>(p, gr, k0, k1, k2, (float)lambda, v);
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-            gc[(int64_t)i * total + e] = v[i];
-    }
+    for (int i = 0; i < D; ++i)
+        gc[(int64_t)i * total + e] = v[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -1388,9 +1446,7 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     }
     {
         const int th = 256;
-        int64_t nb = ((int64_t)L.nc + th - 1) / th;
-        if (nb > 2 * device_sms())
-            nb = 2 * device_sms();
+        const int64_t nb = ((int64_t)L.nc + th - 1) / th;  // one control point per thread
         const float *bp = (const float *)(ws + lay.bpart);
         ProfScope ps(s, "k_ctrl");
         constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);

@@ -380,7 +380,7 @@ __device__ __forceinline__ void lcc_yruns(int t, const Grid &g, const unsigned c
     const float2 *XR = reinterpret_cast<const float2 *>(X + C::LY * C::XP * 20);
     const int x = t % C::TX, hy = t / C::TX, gx = x / C::GX;
     const float2 b = XR[(GY * hy + C::OY + R) * C::NGX + gx];
-    Mom acc = mom_zero(), keep[GY - 1];
+    Mom acc = mom_zero(), keep[GY > 1 ? GY - 1 : 1];
 #pragma unroll
     for (int k = 0; k < C::NFY; ++k) {
         const int ly = GY * hy + k;
