@@ -242,6 +242,30 @@ __device__ __forceinline__ Interp interp8(const float (&c)[8], float fx, float f
     return r;
 }
 
+// interp8 on corners paired by z: c2[q] = (c[q], c[q + 4]) for q = y x bits.
+// The pairs go through packed f32x2 operations (each lane one correctly
+// rounded operation), so the result equals interp8's bit for bit.
+__device__ __forceinline__ Interp interp8_z2(const float2 (&c2)[4], float fx, float fy, float fz)
+{
+    const float gx_ = 1.0f - fx, gy_ = 1.0f - fy, gz_ = 1.0f - fz;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 fx2 = make_float2(fx, fx), gx2 = make_float2(gx_, gx_);
+    const float2 fy2 = make_float2(fy, fy), gy2 = make_float2(gy_, gy_);
+    const float2 dlo = __ffma2_rn(c2[0], m1, c2[1]);  // (d00, d10)
+    const float2 dhi = __ffma2_rn(c2[2], m1, c2[3]);  // (d01, d11)
+    const float2 alo = __ffma2_rn(fx2, c2[1], __fmul2_rn(gx2, c2[0]));  // (a00, a10)
+    const float2 ahi = __ffma2_rn(fx2, c2[3], __fmul2_rn(gx2, c2[2]));  // (a01, a11)
+    const float2 e = __ffma2_rn(alo, m1, ahi);                          // (e0, e1)
+    const float2 b = __ffma2_rn(fy2, ahi, __fmul2_rn(gy2, alo));        // (b0, b1)
+    const float2 gxp = __ffma2_rn(fy2, __ffma2_rn(dlo, m1, dhi), dlo);  // (gx0, gx1)
+    Interp r;
+    r.v = fmaf(fz, b.y, gz_ * b.x);
+    r.gz = b.y - b.x;
+    r.gy = fmaf(fz, e.y - e.x, e.x);
+    r.gx = fmaf(fz, gxp.y - gxp.x, gxp.x);
+    return r;
+}
+
 __device__ __forceinline__ Interp interp4(const float (&c)[4], float fx, float fy)
 {
     const float gx_ = 1.0f - fx;

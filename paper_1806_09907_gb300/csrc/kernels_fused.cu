@@ -237,20 +237,22 @@ __device__ __forceinline__ void plane_rows(const float (&cb)[D][JZ][JY][JX], int
 
 template <int D, int JZ, int JY, int BX>
 __device__ __forceinline__ void plane_cols(const float *Rw, int jz, int qy, int tx,
-                                           const float (&wy)[4], float (&out)[D])
+                                           const float (&wy)[4], float2 &oxy, float &oz)
 {
+    float out[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-        float acc = 0.0f;
         if (jz < JZ) {
             const float *col = Rw + (i * JY + qy) * BX + tx;
-            acc = wy[0] * col[0];
+            float acc = wy[0] * col[0];
             acc = fmaf(wy[1], col[BX], acc);
             acc = fmaf(wy[2], col[2 * BX], acc);
             acc = fmaf(wy[3], col[3 * BX], acc);
+            out[i] = acc;
         }
-        out[i] = acc;
     }
+    oxy = make_float2(out[0], out[1]);
+    oz = out[2];
 }
 
 // Planes 0..NPL-1 of the thread's column partials qz -> x contraction -> y
@@ -476,7 +478,10 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     // sample bounds of axis_cell: y = x + u inside when -x <= u <= n - 1 - x
     const float lox = (float)(-x), hix = (float)(g.X - 1 - x);
     const float loy = (float)(-y), hiy = (float)(g.Y - 1 - y);
-    float cxy[4][D];  // xy-contracted control values of the four active planes
+    // xy-contracted control values of the four active planes: (x, y) packed
+    // for the f32x2 z expansion, z apart (3D)
+    float2 cxy2[4];
+    float cxyz[4];
     if constexpr (MODE != MODE_GW) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -484,7 +489,7 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
         __syncthreads();
 #pragma unroll
         for (int a = 0; a < 4; ++a)
-            plane_cols<D, JZ, JY, BX>(Rw + a * C::RPL, a, qyl, tx, wy, cxy[a]);
+            plane_cols<D, JZ, JY, BX>(Rw + a * C::RPL, a, qyl, tx, wy, cxy2[a], cxyz[a]);
     }
     float qz[4][CHS];  // column partial sums of the four active planes
 #pragma unroll
@@ -500,7 +505,6 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     float *const dstp = bpart + (int64_t)brick * C::NPART;
     const int cells_z = (D == 3) ? (g.Z + DELTA - 1) / DELTA : 1;
     const int nlayers = (D == 3) ? min(C::BCZ, cells_z - cz0) : 1;
-    constexpr int NCOR = (D == 3) ? 8 : 4;
     constexpr int VC = TMA ? 1 : C::VC;  // slices whose loads are in flight together
     int fail_layer = -1;
     for (int cz = 0; cz < C::BCZ; ++cz) {
@@ -536,9 +540,8 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
 #pragma unroll
                 for (int k = 0; k < CHS; ++k)
                     qz[a][k] = qz[a + 1][k];
-#pragma unroll
-                for (int i = 0; i < D; ++i)
-                    cxy[a][i] = cxy[a + 1][i];
+                cxy2[a] = cxy2[a + 1];
+                cxyz[a] = cxyz[a + 1];
             }
 #pragma unroll
             for (int k = 0; k < CHS; ++k)
@@ -565,7 +568,8 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
             __syncthreads();  // the row contractions of plane cz + 3 are written
         }
         if (MODE != MODE_GW && cz > 0)
-            plane_cols<D, JZ, JY, BX>(Rw + ((cz + 3) & 3) * C::RPL, cz + 3, qyl, tx, wy, cxy[3]);
+            plane_cols<D, JZ, JY, BX>(Rw + ((cz + 3) & 3) * C::RPL, cz + 3, qyl, tx, wy, cxy2[3],
+                                      cxyz[3]);
         if (!active)
             continue;
         if constexpr (MODE == MODE_GW) {
@@ -591,7 +595,9 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
 #pragma unroll
         for (int p0 = 0; p0 < DELTA; p0 += VC) {
             // issue every load of VC slices, then use them
-            float mcor[VC][NCOR], aux[VC], fx[VC], fy[VC], fz[VC];
+            // corners paired by z: mc[q] = (slice kz, slice kz + 1) at y x bits q
+            float2 mc[VC][4];
+            float aux[VC], fx[VC], fy[VC], fz[VC];
             bool inb[VC];
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
@@ -599,14 +605,20 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 if (pz >= DELTA)
                     break;
                 const int z = zl0 + pz;
-                float uu[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    float v = kW.w[pz][0] * cxy[0][i];
-                    v = fmaf(kW.w[pz][1], cxy[1][i], v);
-                    v = fmaf(kW.w[pz][2], cxy[2][i], v);
-                    v = fmaf(kW.w[pz][3], cxy[3][i], v);
-                    uu[i] = (D == 3) ? v : cxy[0][i];
+                float uu[3] = {cxy2[0].x, cxy2[0].y, 0.f};
+                if constexpr (D == 3) {
+                    // u = sum_a w[pz][a] (x, y, z)[a]: x and y as f32x2 pairs
+                    float2 v = __fmul2_rn(make_float2(kW.w[pz][0], kW.w[pz][0]), cxy2[0]);
+                    v = __ffma2_rn(make_float2(kW.w[pz][1], kW.w[pz][1]), cxy2[1], v);
+                    v = __ffma2_rn(make_float2(kW.w[pz][2], kW.w[pz][2]), cxy2[2], v);
+                    v = __ffma2_rn(make_float2(kW.w[pz][3], kW.w[pz][3]), cxy2[3], v);
+                    float w = kW.w[pz][0] * cxyz[0];
+                    w = fmaf(kW.w[pz][1], cxyz[1], w);
+                    w = fmaf(kW.w[pz][2], cxyz[2], w);
+                    w = fmaf(kW.w[pz][3], cxyz[3], w);
+                    uu[0] = v.x;
+                    uu[1] = v.y;
+                    uu[2] = w;
                 }
                 // cells are clamped into the volume even outside the mask, so
                 // every load is in bounds; the values outside are not used
@@ -634,29 +646,20 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                         const int o = (int)ry * T::TWX + (int)rx;
                         const float *p0s = ring + s0 * (T::SLOTB / 4) + o;
                         const float *p1s = ring + s1 * (T::SLOTB / 4) + o;
-                        mcor[j][0] = p0s[0];
-                        mcor[j][1] = p0s[1];
-                        mcor[j][2] = p0s[T::TWX];
-                        mcor[j][3] = p0s[T::TWX + 1];
-                        mcor[j][4] = p1s[0];
-                        mcor[j][5] = p1s[1];
-                        mcor[j][6] = p1s[T::TWX];
-                        mcor[j][7] = p1s[T::TWX + 1];
+                        mc[j][0] = make_float2(p0s[0], p1s[0]);
+                        mc[j][1] = make_float2(p0s[1], p1s[1]);
+                        mc[j][2] = make_float2(p0s[T::TWX], p1s[T::TWX]);
+                        mc[j][3] = make_float2(p0s[T::TWX + 1], p1s[T::TWX + 1]);
                     }
                 }
                 if (!staged) {
                     const float *mp = M + ((D == 3 ? kz * g.Y : 0) + ky) * g.X + kx;  // nv < 2^31
-                    mcor[j][0] = __ldg(mp);
-                    mcor[j][1] = __ldg(mp + 1);
-                    mcor[j][2] = __ldg(mp + g.X);
-                    mcor[j][3] = __ldg(mp + g.X + 1);
-                    if constexpr (D == 3) {
-                        const int sxy = g.X * g.Y;
-                        mcor[j][4] = __ldg(mp + sxy);
-                        mcor[j][5] = __ldg(mp + sxy + 1);
-                        mcor[j][6] = __ldg(mp + sxy + g.X);
-                        mcor[j][7] = __ldg(mp + sxy + g.X + 1);
-                    }
+                    const int sxy = (D == 3) ? g.X * g.Y : 0;
+                    mc[j][0] = make_float2(__ldg(mp), D == 3 ? __ldg(mp + sxy) : 0.0f);
+                    mc[j][1] = make_float2(__ldg(mp + 1), D == 3 ? __ldg(mp + sxy + 1) : 0.0f);
+                    mc[j][2] = make_float2(__ldg(mp + g.X), D == 3 ? __ldg(mp + sxy + g.X) : 0.0f);
+                    mc[j][3] = make_float2(__ldg(mp + g.X + 1),
+                                           D == 3 ? __ldg(mp + sxy + g.X + 1) : 0.0f);
                 }
                 aux[j] = 0.0f;
                 if constexpr (MODE == MODE_MSE || MODE == MODE_NCC) {
@@ -676,10 +679,12 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 if (z >= g.Z)
                     break;
                 Interp ip;
-                if constexpr (D == 3)
-                    ip = interp8(mcor[j], fx[j], fy[j], fz[j]);
-                else
-                    ip = interp4(mcor[j], fx[j], fy[j]);
+                if constexpr (D == 3) {
+                    ip = interp8_z2(mc[j], fx[j], fy[j], fz[j]);
+                } else {
+                    const float c4[4] = {mc[j][0].x, mc[j][1].x, mc[j][2].x, mc[j][3].x};
+                    ip = interp4(c4, fx[j], fy[j]);
+                }
                 const int v = (z * g.Y + y) * g.X + x;
                 if (MODE == MODE_FWD) {
                     W_out[v] = inb[j] ? ip.v : 0.0f;
