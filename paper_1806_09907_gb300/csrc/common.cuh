@@ -317,9 +317,11 @@ __device__ __forceinline__ bool al_mbar_wait(uint32_t bar, uint32_t parity)
     return al_mbar_try_wait(bar, parity) || al_mbar_wait_slow(bar, parity);
 }
 
-// Deterministic block reduction of K doubles per thread (fixed tree).
-// `scratch` holds at least K * (blockDim.x / 32) doubles. Result valid in
-// thread 0 (written back into v).
+// Deterministic block reduction of K doubles per thread (fixed tree):
+// shuffles within each warp, then warp 0 reduces the warps' sums the same
+// way (FP64 latency is long on this part, so no serial chain over the
+// warps). `scratch` holds at least K * (blockDim.x / 32) doubles (blockDim.x
+// <= 1024). Result valid in thread 0 (written back into v).
 template <int K>
 __device__ __forceinline__ void block_reduce_d(double (&v)[K], double *scratch)
 {
@@ -337,14 +339,54 @@ __device__ __forceinline__ void block_reduce_d(double (&v)[K], double *scratch)
         for (int k = 0; k < K; ++k)
             scratch[k * nwarp + warp] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nwarp; ++w)
-                s += scratch[k * nwarp + w];
-            v[k] = s;
+            double t = lane < nwarp ? scratch[k * nwarp + lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                t += __shfl_down_sync(0xffffffffu, t, off);
+            v[k] = t;
         }
+    }
+}
+
+// Block sum of K fp32 values per thread into doubles (valid in thread 0):
+// an fp32 shuffle tree within each warp (32 values of a few dozen terms each
+// keep their relative error near 1e-7), then warp 0 adds the warps' sums in
+// FP64 with a second tree. FP64 issues slowly on this part; this takes
+// 5 K FP64 adds per block instead of 5 K per warp. `scratch` holds at least
+// K * (blockDim.x / 32) doubles.
+template <int K>
+__device__ __forceinline__ void block_reduce_fd(float (&v)[K], double (&out)[K], double *scratch)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    }
+    __syncthreads();  // scratch may still be in use by a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            scratch[k * nwarp + warp] = (double)v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        out[k] = 0.0;
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nwarp ? scratch[k * nwarp + lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                t += __shfl_down_sync(0xffffffffu, t, off);
+            out[k] = t;
+        }
+    }
 }
 
 }  // namespace airgb

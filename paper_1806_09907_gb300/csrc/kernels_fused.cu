@@ -582,9 +582,15 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 for (int i = 0; i < D; ++i) {
                     const float vch = gv[pz] * gr[pz][i];
                     if (D == 3) {
-#pragma unroll
-                        for (int a = 0; a < 4; ++a)
-                            qz[a][i] = fmaf(kW.w[pz][a], vch, qz[a][i]);
+                        const float2 v2 = make_float2(vch, vch);
+                        const float2 lo = __ffma2_rn(make_float2(kW.w[pz][0], kW.w[pz][1]), v2,
+                                                     make_float2(qz[0][i], qz[1][i]));
+                        const float2 hi = __ffma2_rn(make_float2(kW.w[pz][2], kW.w[pz][3]), v2,
+                                                     make_float2(qz[2][i], qz[3][i]));
+                        qz[0][i] = lo.x;
+                        qz[1][i] = lo.y;
+                        qz[2][i] = hi.x;
+                        qz[3][i] = hi.y;
                     } else {
                         qz[0][i] += vch;
                     }
@@ -721,11 +727,19 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                         }
                     }
                     if (D == 3) {
+                        // qz[a][k] += w[pz][a] vch[k], planes paired (0, 1), (2, 3)
+                        const float2 w01 = make_float2(kW.w[pz][0], kW.w[pz][1]);
+                        const float2 w23 = make_float2(kW.w[pz][2], kW.w[pz][3]);
 #pragma unroll
-                        for (int a = 0; a < 4; ++a)
-#pragma unroll
-                            for (int k = 0; k < CHS; ++k)
-                                qz[a][k] = fmaf(kW.w[pz][a], vch[k], qz[a][k]);
+                        for (int k = 0; k < CHS; ++k) {
+                            const float2 v2 = make_float2(vch[k], vch[k]);
+                            const float2 lo = __ffma2_rn(w01, v2, make_float2(qz[0][k], qz[1][k]));
+                            const float2 hi = __ffma2_rn(w23, v2, make_float2(qz[2][k], qz[3][k]));
+                            qz[0][k] = lo.x;
+                            qz[1][k] = lo.y;
+                            qz[2][k] = hi.x;
+                            qz[3][k] = hi.y;
+                        }
                     } else {
 #pragma unroll
                         for (int k = 0; k < CHS; ++k)
@@ -773,10 +787,7 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     }
     if (C::NMOM > 0) {
         double mm[C::NMOM > 0 ? C::NMOM : 1];
-#pragma unroll
-        for (int k = 0; k < (C::NMOM > 0 ? C::NMOM : 1); ++k)
-            mm[k] = mom[k];
-        block_reduce_d<(C::NMOM > 0 ? C::NMOM : 1)>(mm, red);
+        block_reduce_fd<(C::NMOM > 0 ? C::NMOM : 1)>(mom, mm, red);
         if (tid == 0)
             for (int k = 0; k < C::NMOM; ++k)
                 mpart[(int64_t)brick * C::NMOM + k] = mm[k];
@@ -1014,6 +1025,29 @@ __device__ void sum_parts(const double *__restrict__ p, int nb, double (&t)[K], 
     block_reduce_d<K>(t, red);
 }
 
+// Sums of two partial arrays (K1 doubles per entry of p1, K2 of p2) in one
+// block reduction: t[0 .. K1-1] from p1, t[K1 ..] from p2.
+template <int K1, int K2, bool CG = false>
+__device__ void sum_parts2(const double *__restrict__ p1, int n1, const double *__restrict__ p2,
+                           int n2, double (&t)[K1 + K2], double *red)
+{
+#pragma unroll
+    for (int k = 0; k < K1 + K2; ++k)
+        t[k] = 0.0;
+    // unrolled so that a thread's loads are in flight together
+#pragma unroll 4
+    for (int b = threadIdx.x; b < n1; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < K1; ++k)
+            t[k] += load_part<CG>(p1 + (int64_t)b * K1 + k);
+#pragma unroll 4
+    for (int b = threadIdx.x; b < n2; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < K2; ++k)
+            t[K1 + k] += load_part<CG>(p2 + (int64_t)b * K2 + k);
+    block_reduce_d<K1 + K2>(t, red);
+}
+
 // Scalars of the objective from the fixed-order sums of the partials:
 // writes {J, S, R, n_mask} to value (when not NULL) and the coefficients of
 // the projected channels in dS/dc to the shared array k[3]. Every thread of
@@ -1027,29 +1061,21 @@ template <bool CG = false>
 __device__ void objective_scalars(int mode, int64_t nv, double lambda, double eps, const Parts &P,
                                   double *value, double *k, double *red)
 {
-    double r[1];
-    sum_parts<1, CG>(P.rpart, P.ngram, r, red);
-    const double R = r[0] / (double)nv;
-    double S = 0.0, n = 0.0;
-    if (mode == MODE_MSE) {
-        double t[2];
-        sum_parts<2, CG>(P.mpart, P.nbricks, t, red);
+    // the regulariser's tile shares and the similarity's partials, summed in
+    // one block reduction
+    double R = 0.0, S = 0.0, n = 0.0;
+    if (mode == MODE_NCC) {
+        double t[7];
+        sum_parts2<1, 6, CG>(P.rpart, P.ngram, P.mpart, P.nbricks, t, red);
         if (threadIdx.x == 0) {
+            R = t[0] / (double)nv;
             n = t[1];
-            S = n > 0.0 ? t[0] / n : 0.0;
-            k[0] = n > 0.0 ? 2.0 / n : 0.0;
-        }
-    } else if (mode == MODE_NCC) {
-        double t[6];
-        sum_parts<6, CG>(P.mpart, P.nbricks, t, red);
-        if (threadIdx.x == 0) {
-            n = t[0];
             k[0] = k[1] = k[2] = 0.0;
             if (n > 0.0) {
-                const double muf = t[1] / n, muw = t[2] / n;
-                const double cov = t[5] - n * muf * muw;
-                const double vf = t[3] - n * muf * muf;
-                const double vw = t[4] - n * muw * muw;
+                const double muf = t[2] / n, muw = t[3] / n;
+                const double cov = t[6] - n * muf * muw;
+                const double vf = t[4] - n * muf * muf;
+                const double vw = t[5] - n * muw * muw;
                 const double Dd = vf * vw + eps;
                 const double sD = sqrt(Dd);
                 S = 1.0 - cov / sD;
@@ -1059,13 +1085,23 @@ __device__ void objective_scalars(int mode, int64_t nv, double lambda, double ep
                 k[2] = -al * muf - be * muw;
             }
         }
-    } else {  // LCC
-        double t[2];
-        sum_parts<2, CG>(P.lpart, P.nlcc, t, red);
+    } else {
+        double t[3];
+        if (mode == MODE_MSE)
+            sum_parts2<1, 2, CG>(P.rpart, P.ngram, P.mpart, P.nbricks, t, red);
+        else
+            sum_parts2<1, 2, CG>(P.rpart, P.ngram, P.lpart, P.nlcc, t, red);
         if (threadIdx.x == 0) {
-            n = t[1];
-            S = n > 0.0 ? 1.0 - t[0] / n : 0.0;
-            k[0] = n > 0.0 ? 1.0 / n : 0.0;
+            R = t[0] / (double)nv;
+            n = t[2];
+            const double inv_n = n > 0.0 ? 1.0 / n : 0.0;  // the two divisions run side by side
+            if (mode == MODE_MSE) {
+                S = t[1] * inv_n;
+                k[0] = 2.0 * inv_n;
+            } else {  // LCC
+                S = n > 0.0 ? 1.0 - t[1] * inv_n : 0.0;
+                k[0] = inv_n;
+            }
         }
     }
     if (threadIdx.x == 0 && value) {
@@ -1077,13 +1113,17 @@ __device__ void objective_scalars(int mode, int64_t nv, double lambda, double ep
     __syncthreads();
 }
 
-// Value only (no gradient requested).
+// The scalars of the objective, once per evaluation (one block): {J, S, R,
+// n_mask} to value (when not NULL) and the channel coefficients to ks[3]
+// (when not NULL), for k_ctrl.
 __global__ void k_finalize(int mode, int64_t nv, double lambda, double eps, Parts P,
-                           double *__restrict__ value)
+                           double *__restrict__ value, double *__restrict__ ks)
 {
-    __shared__ double red[6 * 32];
+    __shared__ double red[7 * 32];  // objective_scalars: up to 7 sums per warp
     __shared__ double k[3];
     objective_scalars(mode, nv, lambda, eps, P, value, k, red);
+    if (ks && threadIdx.x < 3)
+        ks[threadIdx.x] = k[threadIdx.x];
 }
 
 // dJ/dc at control point e: the fixed-order sum of the partials of the (at
@@ -1132,6 +1172,47 @@ __device__ __forceinline__ void ctrl_sum(const Lattice &L, int gbx, int gby, int
         gr[i] = CG ? __ldcg(gR + (int64_t)i * total + e) : __ldg(gR + (int64_t)i * total + e);
 }
 
+// ctrl_sum for component i alone: the projected channels of i (i, and for
+// NCC D + i and 2D + i) and lambda * dR/dc_i.
+template <int D, int CH, int BCX, int BCY, int BCZ>
+__device__ __forceinline__ void ctrl_sum1(const Lattice &L, int gbx, int gby, int gbz,
+                                          const float *__restrict__ bpart,
+                                          const float *__restrict__ gR, int i, int64_t e,
+                                          float (&p)[CH / D], float &gr)
+{
+    constexpr int JX = BCX + 3, JY = BCY + 3, JZ = (D == 3) ? BCZ + 3 : 1;
+    constexpr int NPART = CH * JZ * JY * JX, NC = CH / D;
+    const int jx = (int)(e % L.nx);
+    const int64_t r = e / L.nx;
+    const int jy = (int)(r % L.ny), jz = (int)(r / L.ny);
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+        p[k] = 0.0f;
+    const int bz_hi = (D == 3) ? min(jz / BCZ, gbz - 1) : 0;
+    const int bz_lo = (D == 3) ? max(0, jz / BCZ - 1) : 0;
+    for (int bz = bz_lo; bz <= bz_hi; ++bz) {
+        const int lz = (D == 3) ? jz - bz * BCZ : 0;
+        if (lz >= JZ)
+            continue;
+        for (int by = max(0, jy / BCY - 1); by <= min(jy / BCY, gby - 1); ++by) {
+            const int ly = jy - by * BCY;
+            if (ly >= JY)
+                continue;
+            for (int bx = max(0, jx / BCX - 1); bx <= min(jx / BCX, gbx - 1); ++bx) {
+                const int lx = jx - bx * BCX;
+                if (lx >= JX)
+                    continue;
+                const int brick = (bz * gby + by) * gbx + bx;
+                const float *src = bpart + (int64_t)brick * NPART + (lz * JY + ly) * JX + lx;
+#pragma unroll
+                for (int k = 0; k < NC; ++k)
+                    p[k] += __ldg(src + (k * D + i) * (JZ * JY * JX));
+            }
+        }
+    }
+    gr = __ldg(gR + (int64_t)i * L.nc + e);
+}
+
 template <int D, int CH>
 __device__ __forceinline__ void ctrl_combine(const float (&p)[CH], const float (&gr)[D], float k0,
                                              float k1, float k2, float lam, float (&out)[D])
@@ -1158,38 +1239,30 @@ __device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, i
     ctrl_combine<D, CH>(p, gr, k0, k1, k2, lam, out);
 }
 
-// Per control point (one per thread): fixed-order sum of the partials of the
-// bricks that touch it, channel combination, plus lambda * dR/dc. Every
-// block also evaluates the scalars of the objective (the partial sums are
-// few); a thread issues its point's loads first, so their latency overlaps
-// that reduction. Block 0 writes {J, S, R, n_mask}.
+// Per control point and component (one per thread): fixed-order sum of the
+// partials of the bricks that touch it, channel combination with the scalars
+// ks (k_finalize), plus lambda * dR/dc.
 template <int D, int CH, int BCX, int BCY, int BCZ>
 __global__ void __launch_bounds__(256)
-    k_ctrl(Lattice L, int gbx, int gby, int gbz, int mode, int64_t nv, double lambda, double eps,
-           Parts P, const float *__restrict__ bpart, const float *__restrict__ gR,
-           float *__restrict__ gc, double *__restrict__ value)
+    k_ctrl(Lattice L, int gbx, int gby, int gbz, float lambda, const double *__restrict__ ks,
+           const float *__restrict__ bpart, const float *__restrict__ gR,
+           float *__restrict__ gc)
 {
-    __shared__ double red[6 * 8];
-    __shared__ double ks[3];
+    constexpr int NC = CH / D;
     const int64_t total = (int64_t)L.nc;
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    float p[CH], gr[D];
-    if (e < total)
-        ctrl_sum<D, CH, BCX, BCY, BCZ, false>(L, gbx, gby, gbz, bpart, gR, e, p, gr);
-    objective_scalars(mode, nv, lambda, eps, P, blockIdx.x == 0 ? value : nullptr, ks, red);
-    if (e >= total)
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int i = (int)(t / total);
+    if (i >= D)
         return;
-    const float k0 = (float)ks[0];
-    float k1 = 0.f, k2 = 0.f;
-    if (CH == 3 * D) {
-        k1 = (float)ks[1];
-        k2 = (float)ks[2];
-    }
-    float v[D];
-    ctrl_combine<D, CH>(p, gr, k0, k1, k2, (float)lambda, v);
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-        gc[(int64_t)i * total + e] = v[i];
+    const int64_t e = t - (int64_t)i * total;
+    float p[NC], gr;
+    ctrl_sum1<D, CH, BCX, BCY, BCZ>(L, gbx, gby, gbz, bpart, gR, i, e, p, gr);
+    float v;
+    if (NC == 3)
+        v = fmaf((float)ks[0], p[0], fmaf((float)ks[1], p[1 % NC], (float)ks[2] * p[2 % NC]));
+    else
+        v = (float)ks[0] * p[0];
+    gc[(int64_t)i * total + e] = fmaf(lambda, gr, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -1259,6 +1332,18 @@ struct GramBlocks {
     int gtx, gty, gtz, ngram;  // Gram tiles per axis (gtz = 1 in 2D), total over components
 };
 
+// The scalars of the objective computed by block 0 of a k_fused launch (the
+// bricks then start at block 1): the projection pass of LCC runs after the
+// statistics, so block 0 forms J and the channel coefficients beside the
+// bricks instead of in a launch of its own.
+struct ScalBlock {
+    int on, mode;
+    int64_t nv;
+    double lambda, eps;
+    Parts P;
+    double *value, *ks;
+};
+
 template <int D, int DELTA, int MODE>
 __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
                                   (FCfg<D, DELTA, MODE>::THREADS <= 512 && MODE != MODE_NCC) ? 2
@@ -1266,9 +1351,17 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
     k_fused(Grid g, Lattice L, const float *__restrict__ F, const float *__restrict__ M,
             const float *__restrict__ c, const float *__restrict__ gw_in,
             float *__restrict__ W_out, uint8_t *__restrict__ m_out, float *__restrict__ G_io,
-            float *__restrict__ bpart, double *__restrict__ mpart, GramBlocks gb)
+            float *__restrict__ bpart, double *__restrict__ mpart, GramBlocks gb, ScalBlock sb)
 {
-    const int b = blockIdx.x;
+    if (sb.on && blockIdx.x == 0) {
+        __shared__ double sred[7 * 32];
+        __shared__ double sk[3];
+        objective_scalars(sb.mode, sb.nv, sb.lambda, sb.eps, sb.P, sb.value, sk, sred);
+        if (threadIdx.x < 3)
+            sb.ks[threadIdx.x] = sk[threadIdx.x];
+        return;
+    }
+    const int b = blockIdx.x - sb.on;
     if (b < gb.nbricks) {
         const int bx = b % gb.gbx, by = (b / gb.gbx) % gb.gby, bz = b / (gb.gbx * gb.gby);
         fused_brick<D, DELTA, MODE>(g, L, F, M, c, gw_in, W_out, m_out, G_io, bpart, mpart, bx,
@@ -1345,7 +1438,8 @@ bool brick_tmaps(const Grid &g, const Lattice &L, const float *F, const float *M
 template <int D, int DELTA, int MODE>
 cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay, char *ws,
                              const float *F, const float *M, const float *c, const float *gw,
-                             float *Wo, uint8_t *mo, float *G, bool with_gram, cudaStream_t s)
+                             float *Wo, uint8_t *mo, float *G, bool with_gram, cudaStream_t s,
+                             const ScalBlock &sb = ScalBlock{})
 {
     using C = FCfg<D, DELTA, MODE>;
     GramBlocks gb{};
@@ -1391,9 +1485,9 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
         if (e != cudaSuccess)
             return e;
     }
-    k_fused<D, DELTA, MODE><<<lay.nbricks + gb.ngram, C::THREADS, dyn, s>>>(
+    k_fused<D, DELTA, MODE><<<sb.on + lay.nbricks + gb.ngram, C::THREADS, dyn, s>>>(
         g, L, F, M, c, gw, Wo, mo, G, (float *)(ws + lay.bpart), (double *)(ws + lay.mpart),
-        gb);
+        gb, sb);
     return cudaGetLastError();
 }
 
@@ -1436,31 +1530,38 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
             e = launch_lcc_grad(g, window, F, Wb, mb, coef, gb, s);
             if (e != cudaSuccess)
                 return e;
+            ScalBlock sb{1, 2, g.nv, lambda, eps,
+                         Parts{(const double *)(ws + lay.mpart), rpart,
+                               (const double *)(ws + lay.lpart), lay.nbricks, lay.ngram, lay.nlcc},
+                         value, (double *)(ws + lay.scal)};
             e = run_fused_kernel<D, DELTA, MODE_GW>(g, L, lay, ws, F, M, c, gb, nullptr, nullptr,
-                                                    Gb, false, s);
+                                                    Gb, false, s, sb);
         }
     }
     if (e != cudaSuccess)
         return e;
     Parts parts{(const double *)(ws + lay.mpart), rpart, (const double *)(ws + lay.lpart),
                 lay.nbricks, lay.ngram, lay.nlcc};
-    if (!gc) {
+    double *ks = (double *)(ws + lay.scal);  // channel coefficients for k_ctrl
+    if (!(kind == 2 && gc)) {  // LCC with gradient: block 0 of the projection pass did it
         ProfScope ps(s, "k_finalize");
-        k_finalize<<<1, 1024, 0, s>>>(mode, g.nv, lambda, eps, parts, value);
-        return cudaGetLastError();
+        k_finalize<<<1, 256, 0, s>>>(mode, g.nv, lambda, eps, parts, value, gc ? ks : nullptr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || !gc)
+            return e;
     }
     {
         const int th = 256;
-        const int64_t nb = ((int64_t)L.nc + th - 1) / th;  // one control point per thread
+        const int64_t nb = ((int64_t)D * L.nc + th - 1) / th;  // one (component, point) per thread
         const float *bp = (const float *)(ws + lay.bpart);
         ProfScope ps(s, "k_ctrl");
         constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
         if (kind == 1)
-            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(
-                L, lay.gbx, lay.gby, lay.gbz, mode, g.nv, lambda, eps, parts, bp, gR, gc, value);
+            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz,
+                                                                   (float)lambda, ks, bp, gR, gc);
         else
-            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(
-                L, lay.gbx, lay.gby, lay.gbz, mode, g.nv, lambda, eps, parts, bp, gR, gc, value);
+            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz,
+                                                               (float)lambda, ks, bp, gR, gc);
         e = cudaGetLastError();
     }
     return e;
@@ -1535,7 +1636,7 @@ __global__ void __launch_bounds__(BCfg<DELTA, T>::THREADS, BCfg<DELTA, T>::MINB)
             int *__restrict__ counters, BatchStep st)
 {
     __shared__ int s_item, s_ok;
-    __shared__ double red[6 * 32];
+    __shared__ double red[7 * 32];  // objective_scalars: up to 7 sums per warp
     __shared__ double ks[3];
     __shared__ float s_inv_bc[2];
     if (threadIdx.x == 0) {

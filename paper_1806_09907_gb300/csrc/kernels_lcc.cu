@@ -584,8 +584,9 @@ __global__ void __launch_bounds__(LccS<D, R>::THREADS, 2)
     if (ythr && nz > 0)
         lcc_yruns<D, R>(ty, g, sm + C::oX + ((nz - 1) & 1) * C::XBUF, ymask, yv, gxv, gyv0, n2,
                         inv_n, eps, pl, coef, rho_sum, cnt);
-    double acc[2] = {rho_sum, cnt};
-    block_reduce_d<2>(acc, red);
+    float accf[2] = {rho_sum, cnt};
+    double acc[2];
+    block_reduce_fd<2>(accf, acc, red);
     if (threadIdx.x == 0) {
         const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         part[2 * b] = acc[0];
