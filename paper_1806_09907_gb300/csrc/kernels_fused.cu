@@ -210,6 +210,38 @@ __device__ __forceinline__ void brick_issue(const BrickMaps &tm, uint32_t sbase,
         tma_load_3d(sbase + T::oF + (b & 1) * T::FSLOTB, tm.F, x0, y0, z0 + b * DELTA, bar);
 }
 
+// Staging of the projection pass (GW) by TMA: per layer one box of dS/dW
+// (BX x BY x DELTA) and one of the D planes of dM~/dy (a 4D box), two layers
+// buffered, on mbarriers 0 and 1 with bounded waits; then the one-plane flush
+// buffers.
+template <int DELTA>
+struct GCfg {
+    using C = FCfg<3, DELTA, MODE_GW>;
+    static constexpr int FSLOTB = C::BX * C::BY * DELTA * 4;  // one plane of a layer
+    static constexpr int LAYERB = 4 * FSLOTB;                  // dS/dW, then 3 planes
+    static constexpr int oU = 2 * LAYERB;
+    static constexpr int nU = (C::BY * C::BX * C::CHS + C::BY * C::BCX * 4 * C::CHS) * 4;
+    static constexpr int oBar = oU + round128(nU);
+    static constexpr int bytes = oBar + 2 * 8;
+    static_assert(FSLOTB % 128 == 0, "TMA destinations are 128-byte aligned");
+};
+
+template <int DELTA>
+__device__ __forceinline__ void gw_issue(const BrickMaps &tm, uint32_t sbase, int b, int x0, int y0,
+                                         int z0)
+{
+    using G = GCfg<DELTA>;
+    const uint32_t bar = sbase + G::oBar + 8 * (b & 1), dst = sbase + (b & 1) * G::LAYERB;
+    mbar_expect(bar, (uint32_t)G::LAYERB);
+    tma_load_3d(dst, tm.M, x0, y0, z0 + b * DELTA, bar);  // dS/dW
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst + G::FSLOTB),
+        "l"(reinterpret_cast<uint64_t>(tm.F)), "r"(x0), "r"(y0), "r"(z0 + b * DELTA), "r"(0),
+        "r"(bar)
+        : "memory");
+}
+
 // xy contraction of control plane jz for the voxel columns of a brick, in
 // two steps that share the x contraction among the DELTA columns of a cell
 // row:
@@ -371,9 +403,9 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
     using C = FCfg<D, DELTA, MODE, BCX_, BCY_>;
     using T = TCfg<DELTA, MODE == MODE_GW ? MODE_FWD : MODE>;
-    static_assert(!TMA || (D == 3 && MODE != MODE_GW && BCX_ == brick_bcx(DELTA) &&
-                           BCY_ == brick_bcy(DELTA)),
-                  "TMA staging: 3D single-problem bricks that gather");
+    using GS = GCfg<DELTA>;
+    static_assert(!TMA || (D == 3 && BCX_ == brick_bcx(DELTA) && BCY_ == brick_bcy(DELTA)),
+                  "TMA staging: 3D single-problem bricks");
     constexpr int JX = C::JX, JY = C::JY, JZ = C::JZ, CHS = C::CHS, BX = C::BX;
     constexpr WTab<DELTA> kW{};  // weights of the compile-time z phases
     __shared__ float cb[D][JZ][JY][JX];
@@ -384,8 +416,8 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     if constexpr (TMA)
         sm += (128u - (al_smem_u32(dsm) & 127u)) & 127u;
     const uint32_t sbase = al_smem_u32(sm);
-    float *P = TMA ? reinterpret_cast<float *>(sm + T::oU) : dsm;
-    float *Xc = TMA ? P + T::nP1 : dsm + C::nP;
+    float *P = TMA ? reinterpret_cast<float *>(sm + (MODE == MODE_GW ? GS::oU : T::oU)) : dsm;
+    float *Xc = TMA ? P + (MODE == MODE_GW ? C::BY * BX * CHS : T::nP1) : dsm + C::nP;
     float *Rw = TMA ? reinterpret_cast<float *>(sm + T::oU + T::oR) : dsm + C::nP + C::nX;
     const float *ring = reinterpret_cast<const float *>(sm + T::oRing);
     const float *Fs = reinterpret_cast<const float *>(sm + T::oF);
@@ -399,7 +431,21 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     if (tid < DELTA * 4)
         wt[tid / 4][tid % 4] = L.w[tid / 4][tid % 4];
     bool ok = true;
-    if constexpr (TMA) {
+    if constexpr (TMA && MODE == MODE_GW) {
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + GS::oBar)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbase + GS::oBar + 8)
+                         : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            gw_issue<DELTA>(tm, sbase, 0, x0, y0, z0);
+            if (C::BCZ > 1)
+                gw_issue<DELTA>(tm, sbase, 1, x0, y0, z0);
+        }
+    } else if constexpr (TMA) {
         if (tid == 0) {
 #pragma unroll
             for (int k = 0; k < 3; ++k)
@@ -514,7 +560,7 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
         // GW: the layer's loads are issued before the flush of the previous
         // plane, so they are in flight while the block contracts it
         float gv[MODE == MODE_GW ? DELTA : 1], gr[MODE == MODE_GW ? DELTA : 1][D];
-        if constexpr (MODE == MODE_GW) {
+        if constexpr (MODE == MODE_GW && !TMA) {
             if (active) {
                 // 32-bit voxel offsets (nv < 2^31), one per slice, shared by
                 // the D + 1 planes read
@@ -552,7 +598,17 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 plane_rows<D, JZ, JY, JX, BX, C::THREADS>(cb, cz + 3, qxl, wx,
                                                           Rw + ((cz + 3) & 3) * C::RPL);
         }
-        if constexpr (TMA) {
+        if constexpr (TMA && MODE == MODE_GW) {
+            ok = al_mbar_wait(sbase + GS::oBar + 8 * (cz & 1), (uint32_t)(cz >> 1) & 1u);
+            if (__syncthreads_or(!ok)) {
+                fail_layer = cz;
+                break;
+            }
+            if (tid == 0 && cz >= 1 && cz + 1 < C::BCZ) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                gw_issue<DELTA>(tm, sbase, cz + 1, x0, y0, z0);
+            }
+        } else if constexpr (TMA) {
             // this layer's copies; then every thread is past layer cz - 1, so
             // the slots it used take the next layer's copies
             ok = al_mbar_wait(sbase + T::oBar + 8 * (cz & 1), (uint32_t)(cz >> 1) & 1u);
@@ -574,10 +630,19 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
             continue;
         if constexpr (MODE == MODE_GW) {
             static_assert(C::VC >= 1, "the GW layer loads all DELTA slices at once");
+            const float *Gl = reinterpret_cast<const float *>(sm + (cz & 1) * GS::LAYERB) +
+                              ty * BX + tx;
 #pragma unroll
             for (int pz = 0; pz < DELTA; ++pz) {
                 if (zl0 + pz >= g.Z)
                     break;
+                if constexpr (TMA) {
+                    constexpr int PL = GS::FSLOTB / 4;
+                    gv[pz] = Gl[pz * (BX * C::BY)];
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+                        gr[pz][i] = Gl[(1 + i) * PL + pz * (BX * C::BY)];
+                }
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
                     const float vch = gv[pz] * gr[pz][i];
@@ -758,8 +823,9 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 atomicExch(&g_unit_error, kFusedTimeout);
                 // unconfirmed: batch fail_layer, and batch 1 when layer 0 failed
                 const int last = fail_layer == 0 ? min(1, C::BCZ - 1) : fail_layer;
+                const uint32_t bars = sbase + (MODE == MODE_GW ? GS::oBar : T::oBar);
                 for (int b = fail_layer; b <= last; ++b)
-                    al_mbar_wait(sbase + T::oBar + 8 * (b & 1), (uint32_t)(b >> 1) & 1u);
+                    al_mbar_wait(bars + 8 * (b & 1), (uint32_t)(b >> 1) & 1u);
             }
             return false;
         }
@@ -1389,9 +1455,17 @@ __global__ void __launch_bounds__(FCfg<3, DELTA, MODE>::THREADS,
                 const float *__restrict__ F, const float *__restrict__ M,
                 const float *__restrict__ c, float *__restrict__ W_out,
                 uint8_t *__restrict__ m_out, float *__restrict__ G_io, float *__restrict__ bpart,
-                double *__restrict__ mpart, GramBlocks gb)
+                double *__restrict__ mpart, GramBlocks gb, ScalBlock sb)
 {
-    const int b = blockIdx.x;
+    if (sb.on && blockIdx.x == 0) {
+        __shared__ double sred[7 * 32];
+        __shared__ double sk[3];
+        objective_scalars(sb.mode, sb.nv, sb.lambda, sb.eps, sb.P, sb.value, sk, sred);
+        if (threadIdx.x < 3)
+            sb.ks[threadIdx.x] = sk[threadIdx.x];
+        return;
+    }
+    const int b = blockIdx.x - sb.on;
     if (b < gb.nbricks) {
         const int bx = b % gb.gbx, by = (b / gb.gbx) % gb.gby, bz = b / (gb.gbx * gb.gby);
         fused_brick<3, DELTA, MODE, brick_bcx(DELTA), brick_bcy(DELTA), true>(
@@ -1460,6 +1534,32 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
                     : MODE == MODE_NCC ? "k_fused_ncc"
                     : MODE == MODE_FWD ? "k_fused_fwd"
                                        : "k_fused_gw");
+    if constexpr (D == 3 && MODE == MODE_GW) {
+        // dS/dW (3D box) and the D planes of dM~/dy (4D box) per layer
+        using GS = GCfg<DELTA>;
+        CUtensorMap mW, mG, mC;
+        memset(&mW, 0, sizeof(mW));
+        memset(&mG, 0, sizeof(mG));
+        memset(&mC, 0, sizeof(mC));
+        const uint64_t dims[4] = {(uint64_t)g.X, (uint64_t)g.Y, (uint64_t)g.Z, 3};
+        const uint64_t strides[3] = {(uint64_t)g.X * 4, (uint64_t)g.X * g.Y * 4,
+                                     (uint64_t)g.nv * 4};
+        const uint32_t box[4] = {(uint32_t)C::BX, (uint32_t)C::BY, (uint32_t)DELTA, 3u};
+        if (g.X % 4 == 0 && g.nv % 4 == 0 && g.X >= C::BX && g.Y >= C::BY && g.Z >= DELTA &&
+            encode_tmap_f32(&mW, 3, dims, strides, box, gw) &&
+            encode_tmap_f32(&mG, 4, dims, strides, box, G)) {
+            const size_t tdyn = (size_t)GS::bytes + 128;
+            cudaError_t e = cudaFuncSetAttribute(k_fused_tma<DELTA, MODE>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)tdyn);
+            if (e != cudaSuccess)
+                return e;
+            k_fused_tma<DELTA, MODE><<<sb.on + lay.nbricks, C::THREADS, tdyn, s>>>(
+                mW, mG, mC, int3{0, 0, 0}, g, L, F, M, c, Wo, mo, G, (float *)(ws + lay.bpart),
+                (double *)(ws + lay.mpart), gb, sb);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (D == 3 && MODE != MODE_GW) {
         CUtensorMap mM, mF, mC;
         int lbox = 0, lslot = 0, lplane = 0;
@@ -1471,9 +1571,9 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
                                                  (int)tdyn);
             if (e != cudaSuccess)
                 return e;
-            k_fused_tma<DELTA, MODE><<<lay.nbricks + gb.ngram, C::THREADS, tdyn, s>>>(
+            k_fused_tma<DELTA, MODE><<<sb.on + lay.nbricks + gb.ngram, C::THREADS, tdyn, s>>>(
                 mM, mF, mC, int3{lbox, lslot, lplane}, g, L, F, M, c, Wo, mo, G,
-                (float *)(ws + lay.bpart), (double *)(ws + lay.mpart), gb);
+                (float *)(ws + lay.bpart), (double *)(ws + lay.mpart), gb, sb);
             return cudaGetLastError();
         }
     }
