@@ -549,6 +549,19 @@ al_status al_get_device_error(al_stream stream);
  * drop_slice < -1. */
 al_status al_lcc_set_wait(int32_t drop_slice);
 
+/* Test of the fused objective's bounded waits (not part of the method). With
+ * drop_batch >= 0, the 3D brick kernels that stage their inputs by TMA (X a
+ * multiple of 4) do not issue copy batch `drop_batch` of each brick (batch b
+ * holds the moving-image slices and fixed-image layer that layer b of the
+ * brick adds, or the projection's planes of layer b). The wait for it runs
+ * out after about a second, the brick records AL_ERR_TIMEOUT, waits
+ * (bounded) for its other copies in flight and returns without writing its
+ * partial sums; the call's results are then not valid. -1 (the default)
+ * restores normal staging. Applies to launches issued after the call on the
+ * current device; blocking (a copy to device constant memory).
+ * AL_ERR_INVALID_ARG if drop_batch < -1. */
+al_status al_fused_set_wait(int32_t drop_batch);
+
 /* Instrumentation (not part of the method). When enabled, every kernel the
  * library launches is bracketed by two CUDA events recorded on the
  * launching stream. al_profile_collect synchronises on the recorded events,

@@ -49,7 +49,7 @@ EXPORTS = (
     "al_conv3d_backward_weight_workspace_bytes", "al_conv3d_backward_weight", "al_initnet_input",
     "al_initnet_upcat", "al_initnet_upcat_adjoint", "al_initnet_head_to_ctrl",
     "al_initnet_head_adjoint", "al_field_loss_workspace_bytes", "al_field_loss", "al_adam_flat",
-    "al_render_blobs", "al_lcc_set_wait",
+    "al_render_blobs", "al_lcc_set_wait", "al_fused_set_wait",
 )
 
 
@@ -121,6 +121,7 @@ def load():
         "al_objective_unfused_workspace_bytes": ([P(al_problem)], SZ),
         "al_get_device_error": ([VP], I32),
         "al_lcc_set_wait": ([I32], I32),
+        "al_fused_set_wait": ([I32], I32),
         "al_profile_enable": ([I32], I32),
         "al_profile_collect": ([ctypes.c_char_p, SZ, P(D), P(ctypes.c_int64), I32], I32),
         "al_profile_reset": ([], I32),
@@ -643,6 +644,12 @@ def al_lcc_set_wait(drop_slice=-1) -> None:
     """Test hook: the TMA-staged LCC gradient skips the load of this slice of
     every block, so its bounded wait runs out (AL_ERR_TIMEOUT); -1 restores."""
     _call("al_lcc_set_wait", int(drop_slice))
+
+
+def al_fused_set_wait(drop_batch=-1) -> None:
+    """Test hook: the TMA-staged 3D brick kernels skip this copy batch of every
+    brick, so its bounded wait runs out (AL_ERR_TIMEOUT); -1 restores."""
+    _call("al_fused_set_wait", int(drop_batch))
 
 
 def profile_enable(on: bool = True):

@@ -744,6 +744,13 @@ al_status al_lcc_set_wait(int32_t drop_slice)
     return lcc_set_drop_slice((int)drop_slice) == cudaSuccess ? AL_OK : AL_ERR_CUDA;
 }
 
+al_status al_fused_set_wait(int32_t drop_batch)
+{
+    if (drop_batch < -1)
+        return AL_ERR_INVALID_ARG;
+    return fused_set_drop_batch((int)drop_batch) == cudaSuccess ? AL_OK : AL_ERR_CUDA;
+}
+
 al_status al_get_device_error(al_stream stream)
 {
     if (cudaStreamSynchronize(S(stream)) != cudaSuccess)

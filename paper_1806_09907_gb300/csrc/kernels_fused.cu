@@ -165,6 +165,11 @@ void lattice_boxes(const Lattice &L, int *lbox, int *lslot, int *lplane)
 
 constexpr int kFusedTimeout = 6;  // AL_ERR_TIMEOUT
 
+// Test of the bounded waits of the TMA-staged bricks: the copy batch (layer
+// index within a brick) that is not issued, so the wait for it runs out;
+// -1 = none.
+__constant__ int c_fused_drop_batch = -1;
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             int z, uint32_t bar)
 {
@@ -198,6 +203,8 @@ __device__ __forceinline__ void brick_issue(const BrickMaps &tm, uint32_t sbase,
                                             int y0, int z0)
 {
     using T = TCfg<DELTA, MODE>;
+    if (b == c_fused_drop_batch)
+        return;
     const uint32_t bar = sbase + T::oBar + 8 * (b & 1);
     const int r0 = b == 0 ? 0 : T::NRES + (b - 1) * DELTA, r1 = T::NRES + b * DELTA;
     mbar_expect(bar, (uint32_t)((r1 - r0) * T::SLOTB + (T::NF > 0 ? T::FSLOTB : 0)));
@@ -231,6 +238,8 @@ __device__ __forceinline__ void gw_issue(const BrickMaps &tm, uint32_t sbase, in
                                          int z0)
 {
     using G = GCfg<DELTA>;
+    if (b == c_fused_drop_batch)
+        return;
     const uint32_t bar = sbase + G::oBar + 8 * (b & 1), dst = sbase + (b & 1) * G::LAYERB;
     mbar_expect(bar, (uint32_t)G::LAYERB);
     tma_load_3d(dst, tm.M, x0, y0, z0 + b * DELTA, bar);  // dS/dW
@@ -1952,5 +1961,10 @@ cudaError_t launch_batch(int delta, int tile, int blocks, const BatchProblem *pr
 }
 
 AL_UNIT_ERROR_READER(unit_error_fused)
+
+cudaError_t fused_set_drop_batch(int batch)
+{
+    return cudaMemcpyToSymbol(c_fused_drop_batch, &batch, sizeof(int));
+}
 
 }  // namespace airgb

@@ -207,6 +207,7 @@ int unit_error_conv(bool clear);
 int unit_error_lcc(bool clear);
 // Test hook of the LCC gradient's bounded waits (al_lcc_set_wait).
 cudaError_t lcc_set_drop_slice(int slice);
+cudaError_t fused_set_drop_batch(int batch);
 
 // Grids of the network's two coarsest levels: n3 (e3, the head) and n4 (e4),
 // (z, y, x); lat = spacing-8 lattice sizes (x, y, z).

@@ -307,6 +307,10 @@ def test_lcc_wait_hook_rejects_bad_slice(lib):
     assert lib.al_lcc_set_wait(-2) == 1
 
 
+def test_fused_wait_hook_rejects_bad_batch(lib):
+    assert lib.al_fused_set_wait(-2) == 1
+
+
 def test_batch_bind_tune_status_reject(lib):
     """Binding checks every device pointer (NULL 1, misaligned 3) and the
     workspace (8) on the host; tuning needs a bound workspace (8) and at

@@ -171,6 +171,27 @@ def test_lcc_tma_wait_timeout_is_reported_and_recoverable():
     assert rel_l2(host(gw), gr) <= G_TOL
 
 
+@pytest.mark.parametrize("sim,batch", [("mse", 1), ("lcc", 0)])
+def test_fused_tma_wait_timeout_is_reported_and_recoverable(sim, batch):
+    """A copy batch of the TMA-staged bricks that is never issued (the test
+    hook) makes their bounded wait run out: the call returns, AL_ERR_TIMEOUT
+    is reported, and the next evaluation on the same context matches the
+    oracle. Batch 1 is the second layer of the MSE brick's moving-image
+    slices; batch 0 the first layer of both LCC brick passes."""
+    shape = (30, 40, 48)  # X a multiple of 4: TMA-staged bricks (spacing 6, one brick in z)
+    F, M, c = blob_case(shape, 6, 1.2, 61)
+    pr = airgb.make_problem(shape, 6, sim, 0.1, 1e-5, 5)
+    airgb.al_get_device_error()
+    airgb.al_fused_set_wait(batch)
+    try:
+        airgb.al_objective_grad(pr, dev(F), dev(M), dev(c))
+        assert airgb.al_get_device_error() == 6  # AL_ERR_TIMEOUT
+    finally:
+        airgb.al_fused_set_wait(-1)
+    assert airgb.al_get_device_error() == 0
+    check_objective(F, M, c, 6, sim, window=5)
+
+
 # ----------------------------------------------------------------------- A4 --
 
 @pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (2, 2, 2)])
