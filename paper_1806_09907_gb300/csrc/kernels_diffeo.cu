@@ -156,6 +156,13 @@ __device__ __forceinline__ float fixed_scale(unsigned int maxbits)
 }
 
 // Local terms of one squaring's adjoint into h, the scatter into acc.
+// Consecutive lanes take consecutive voxels (all lanes run the same number of
+// iterations, so the warp shuffles see every lane). The scatter to the +x
+// corners of a sample is usually the scatter to the -x corners of the next
+// lane's sample (a smooth displacement keeps neighbours in neighbouring
+// cells): that lane adds it to its own contribution, as 64-bit integers, and
+// one atomic serves both. Integer addition is exact, so the result does not
+// change.
 template <int D>
 __global__ void __launch_bounds__(kDiffeoThreads)
     k_compose_adjoint(Grid g, const float *__restrict__ u, const float *__restrict__ gin,
@@ -163,16 +170,22 @@ __global__ void __launch_bounds__(kDiffeoThreads)
                       const unsigned int *__restrict__ maxbits)
 {
     const float S = fixed_scale(*maxbits);
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.nv;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((int64_t)g.X * g.Y));
-        const FieldSample s = field_sample<D>(g, x, y, z, u, v);
-        const int64_t base = ((int64_t)s.cell[2] * g.Y + s.cell[1]) * g.X + s.cell[0];
-        const int64_t sy = g.X, sz = (int64_t)g.X * g.Y;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < g.nv; v0 += stride) {
+        const int64_t v = v0 + threadIdx.x;
+        const bool valid = v < g.nv;
+        const int64_t vv = valid ? v : 0;
+        const int x = (int)(vv % g.X), y = (int)((vv / g.X) % g.Y),
+                  z = (int)(vv / ((int64_t)g.X * g.Y));
+        const FieldSample s = field_sample<D>(g, x, y, z, u, vv);
+        const int base = (s.cell[2] * g.Y + s.cell[1]) * g.X + s.cell[0];  // nv < 2^31
+        const int sy = g.X, sz = g.X * g.Y;
         float gv[D], loc[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            gv[i] = __ldg(gin + (int64_t)i * g.nv + v);
+            gv[i] = valid ? __ldg(gin + (int64_t)i * g.nv + vv) : 0.0f;
             loc[i] = gv[i];
         }
         // derivative of the interpolant of each component at the sample
@@ -205,28 +218,40 @@ __global__ void __launch_bounds__(kDiffeoThreads)
             if (D == 3 && s.in[2])
                 loc[D - 1] = fmaf(d2, gv[i], loc[D - 1]);
         }
+        if (valid) {
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-            h[(int64_t)i * g.nv + v] = loc[i];
-        // transposed interpolation: the sample's weights onto the corners
+            for (int i = 0; i < D; ++i)
+                h[(int64_t)i * g.nv + vv] = loc[i];
+        }
+        // transposed interpolation: the sample's weights onto the corners,
+        // the -x and +x corner of each (y, z) corner pair together
 #pragma unroll
         for (int cz = 0; cz < (D == 3 ? 2 : 1); ++cz)
 #pragma unroll
-            for (int cy = 0; cy < 2; ++cy)
+            for (int cy = 0; cy < 2; ++cy) {
+                const float wyz = (cy ? s.f[1] : 1.0f - s.f[1]) *
+                                  (D == 3 ? (cz ? s.f[2] : 1.0f - s.f[2]) : 1.0f);
+                const float w0 = (1.0f - s.f[0]) * wyz, w1 = s.f[0] * wyz;
+                const int n0 = valid ? base + cz * sz + cy * sy : -2, n1 = valid ? n0 + 1 : -4;
+                // the previous lane's +x node is this lane's -x node: take its value;
+                // the next lane's -x node is this lane's +x node: give this value
+                const int prev_n1 = __shfl_up_sync(FULL, n1, 1);
+                const int next_n0 = __shfl_down_sync(FULL, n0, 1);
+                const bool take = lane > 0 && prev_n1 == n0;
+                const bool give = lane < 31 && next_n0 == n1;
 #pragma unroll
-                for (int cx = 0; cx < 2; ++cx) {
-                    const float w = (cx ? s.f[0] : 1.0f - s.f[0]) * (cy ? s.f[1] : 1.0f - s.f[1]) *
-                                    (D == 3 ? (cz ? s.f[2] : 1.0f - s.f[2]) : 1.0f);
-                    if (w == 0.0f)
-                        continue;
-                    const int64_t node = base + cz * sz + cy * sy + cx;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        const long long q = __float2ll_rn(w * gv[i] * S);
-                        if (q != 0)
-                            atomicAdd(acc + (int64_t)i * g.nv + node, (unsigned long long)q);
-                    }
+                for (int i = 0; i < D; ++i) {
+                    long long q0 = valid ? __float2ll_rn(w0 * gv[i] * S) : 0ll;
+                    const long long q1 = valid ? __float2ll_rn(w1 * gv[i] * S) : 0ll;
+                    const long long qp = __shfl_up_sync(FULL, q1, 1);
+                    if (take)
+                        q0 += qp;
+                    if (q0 != 0)
+                        atomicAdd(acc + (int64_t)i * g.nv + n0, (unsigned long long)q0);
+                    if (!give && q1 != 0)
+                        atomicAdd(acc + (int64_t)i * g.nv + n1, (unsigned long long)q1);
                 }
+            }
     }
 }
 
