@@ -611,6 +611,7 @@ def learned_init_runs(dev, pairs, n_test):
         reports.append(learned_init.evaluate_pair(one, F[0].clone(), M[0].clone(),
                                                   ct[0].clone()))
     ok = [r for r in reports if r.iterations_to_plain >= 0]
+    okJ = [r for r in reports if r.iterations_to_plain_J >= 0]
 
     def mean(key, rs=reports):
         return float(np.mean([getattr(r, key) for r in rs])) if rs else None
@@ -636,6 +637,13 @@ def learned_init_runs(dev, pairs, n_test):
         "speedup": (float(np.mean([r.plain_ms for r in ok]) / np.mean([r.learned_ms for r in ok]))
                     if ok else None),
         "iterations_to_plain_best_mse": [r.iterations_to_best for r in reports],
+        "objective_J": {
+            "reached_plain_J": len(okJ),
+            "iterations_to_plain_J_mean": mean("iterations_to_plain_J", okJ),
+            "learned_ms_J_mean": mean("learned_ms_J", okJ),
+            "speedup_J": (float(np.mean([r.plain_ms for r in okJ]) /
+                                np.mean([r.learned_ms_J for r in okJ])) if okJ else None),
+            "plain_final_J": mean("plain_final_J"), "refined_final_J": mean("refined_final_J")},
         "mse": {"zero": mean("zero_mse"), "prediction": mean("init_mse"),
                 "plain_final": mean("plain_final_mse"), "plain_best": mean("plain_best_mse"),
                 "refined_final": mean("refined_final_mse")},

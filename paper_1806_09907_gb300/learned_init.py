@@ -309,6 +309,10 @@ class PairReport:
     field_rmse_pred: float    # rms |u_pred - u*|
     field_rmse_plain: float   # rms |u_plain - u*|
     field_rmse_refined: float  # rms |u_refined - u*|
+    plain_final_J: float      # J = MSE + lambda R after the plain optimiser's iterations
+    iterations_to_plain_J: int  # refinement iterations until J <= plain_final_J (-1: never)
+    learned_ms_J: float       # inference + those iterations, measured (device time)
+    refined_final_J: float    # J after as many refinement iterations as the plain run
 
 
 def _field_rmse(shape, c, c_true):
@@ -341,7 +345,8 @@ def _first(values, target):
 def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, lam=0.1):
     """Plain optimiser from zero for `iterations`, then the network's
     prediction refined by the same optimiser: iterations and device time
-    until it reaches the plain method's final MSE. The prediction is
+    until it reaches the plain method's final MSE, and until it reaches the
+    plain method's final J (the objective both runs minimise). The prediction is
     rejected (the refinement starts from zero, as the plain method) when its
     MSE is worse than at c = 0. net_single must have batch 1."""
     shape = tuple(F.shape)
@@ -363,15 +368,23 @@ def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, la
     refine = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
                                    iterations=iterations, lr=lr, ctrl=start_c)
     rv = refine.levels[0].values.cpu().numpy()
-    k = _first(rv[:, 1], target)
-    learned_ms = float("nan")
-    if k == 0:
-        learned_ms = infer_ms
-    elif k > 0:
+
+    def measured(k):
         # the measured run: exactly k refinement iterations after the inference
+        if k < 0:
+            return float("nan")
+        if k == 0:
+            return infer_ms
         again = registration.register(F, M, spacing=SPACING, sim="mse", lam=lam, factors=(1,),
                                       iterations=k, lr=lr, ctrl=start_c)
-        learned_ms = infer_ms + again.levels[0].ms
+        return infer_ms + again.levels[0].ms
+
+    k = _first(rv[:, 1], target)
+    learned_ms = measured(k)
+    # the same for the objective the optimiser minimises: J = MSE + lambda R
+    target_J = float(pv[-1, 0])
+    k_J = _first(rv[:, 0], target_J)
+    learned_ms_J = measured(k_J)
     return PairReport(
         plain_final_mse=target, plain_best_mse=best, plain_ms=plain.levels[0].ms,
         zero_mse=float(valz[1]), init_mse=float(val0[1]), init_J=float(val0[0]),
@@ -381,7 +394,9 @@ def evaluate_pair(net_single: InitNet, F, M, c_true, iterations=200, lr=0.01, la
         field_rmse_zero=_field_rmse(shape, zero, c_true),
         field_rmse_pred=_field_rmse(shape, c0, c_true),
         field_rmse_plain=_field_rmse(shape, plain.ctrl, c_true),
-        field_rmse_refined=_field_rmse(shape, refine.ctrl, c_true))
+        field_rmse_refined=_field_rmse(shape, refine.ctrl, c_true),
+        plain_final_J=target_J, iterations_to_plain_J=k_J, learned_ms_J=learned_ms_J,
+        refined_final_J=float(rv[-1, 0]))
 
 
 def _main():
