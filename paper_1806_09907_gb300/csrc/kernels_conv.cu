@@ -944,46 +944,61 @@ __global__ void k_pack_weights(const float *__restrict__ w, int cin, int cout, i
 // block of kReduceThreads per M row m = t cin + ci (m = 27 cin is the bias
 // row). Thread j adds the splits j / N, j / N + G, ... of column co = j % N
 // (G = kReduceThreads / N groups, coalesced reads of the N columns of a
-// split), in order and in double; the G group sums are then added in order
+// split), in order with compensated fp32 sums; the G group sums are then added in order
 // by one thread per column, so the result does not depend on timing.
 constexpr int kReduceThreads = 512;
+
+// Compensated (Kahan) fp32 accumulation: the sum keeps about the precision of
+// one rounding whatever the number of terms, with full-rate fp32 adds (FP64
+// issues slowly on this part).
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
 
 __global__ void __launch_bounds__(kReduceThreads)
     k_wgrad_reduce(const float *__restrict__ part, int splits, int mrows, int N, int cin,
                    int cout, float *__restrict__ gw, float *__restrict__ gb)
 {
-    __shared__ double red[kReduceThreads];
+    __shared__ float red[kReduceThreads];
     const int m = blockIdx.x;
     const int groups = kReduceThreads / N;
     const int co = threadIdx.x % N, grp = threadIdx.x / N;
-    double acc = 0.0;
+    Kahan acc;
     if (grp < groups) {
         const float *p = part + (size_t)m * N + co;
         const size_t step = (size_t)mrows * N;
         int sp = grp;
-        // four independent loads in flight per thread
+        // four independent loads in flight per thread, added in split order
         for (; sp + 3 * groups < splits; sp += 4 * groups) {
             const float a = p[(size_t)sp * step], b = p[(size_t)(sp + groups) * step],
                         c = p[(size_t)(sp + 2 * groups) * step],
                         d = p[(size_t)(sp + 3 * groups) * step];
-            acc += (double)a;
-            acc += (double)b;
-            acc += (double)c;
-            acc += (double)d;
+            acc.add(a);
+            acc.add(b);
+            acc.add(c);
+            acc.add(d);
         }
         for (; sp < splits; sp += groups)
-            acc += (double)p[(size_t)sp * step];
+            acc.add(p[(size_t)sp * step]);
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = acc.s - acc.c;
     __syncthreads();
     if (threadIdx.x < N && co < cout) {
-        double tot = 0.0;
+        Kahan tot;
         for (int gi = 0; gi < groups; ++gi)
-            tot += red[gi * N + co];
+            tot.add(red[gi * N + co]);
+        const float v = tot.s - tot.c;
         if (m < 27 * cin)
-            gw[(size_t)co * 27 * cin + m] = (float)tot;
+            gw[(size_t)co * 27 * cin + m] = v;
         else if (gb)
-            gb[co] = (float)tot;
+            gb[co] = v;
     }
 }
 

@@ -406,7 +406,8 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                                             float *__restrict__ W_out, uint8_t *__restrict__ m_out,
                                             float *__restrict__ G_io, float *__restrict__ bpart,
                                             double *__restrict__ mpart, int bx, int by, int bz,
-                                            int brick, BrickMaps tm = BrickMaps{})
+                                            int brick, BrickMaps tm = BrickMaps{},
+                                            int *__restrict__ icnt = nullptr)
 {
     // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
     // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
@@ -863,9 +864,12 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
     if (C::NMOM > 0) {
         double mm[C::NMOM > 0 ? C::NMOM : 1];
         block_reduce_fd<(C::NMOM > 0 ? C::NMOM : 1)>(mom, mm, red);
-        if (tid == 0)
+        if (tid == 0) {
             for (int k = 0; k < C::NMOM; ++k)
                 mpart[(int64_t)brick * C::NMOM + k] = mm[k];
+            if (MODE == MODE_MSE && icnt)  // the brick's masked voxels, for k_ctrl
+                icnt[brick] = (int)mm[1];
+        }
     }
     return true;
 }
@@ -1132,6 +1136,18 @@ struct Parts {
     int nbricks, ngram, nlcc;
 };
 
+// The scalars of the objective computed by block 0 of a k_fused launch (the
+// bricks then start at block 1): the projection pass of LCC runs after the
+// statistics, so block 0 forms J and the channel coefficients beside the
+// bricks instead of in a launch of its own.
+struct ScalBlock {
+    int on, mode;
+    int64_t nv;
+    double lambda, eps;
+    Parts P;
+    double *value, *ks;
+};
+
 template <bool CG = false>
 __device__ void objective_scalars(int mode, int64_t nv, double lambda, double eps, const Parts &P,
                                   double *value, double *k, double *red)
@@ -1317,32 +1333,66 @@ __device__ __forceinline__ void ctrl_point(const Lattice &L, int gbx, int gby, i
 // Per control point and component (one per thread): fixed-order sum of the
 // partials of the bricks that touch it, channel combination with the scalars
 // ks (k_finalize), plus lambda * dR/dc.
+// MSE (sb.on): block 0 forms J and the objective's scalars instead (the
+// points start at block 1), and the other blocks take k0 = 2 / n from the
+// bricks' integer mask counts (exact integer sums), so no separate launch
+// has to finish before them.
 template <int D, int CH, int BCX, int BCY, int BCZ>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_ctrl(Lattice L, int gbx, int gby, int gbz, float lambda, const double *__restrict__ ks,
            const float *__restrict__ bpart, const float *__restrict__ gR,
-           float *__restrict__ gc)
+           float *__restrict__ gc, ScalBlock sb, const int *__restrict__ icnt)
 {
     constexpr int NC = CH / D;
+    if (sb.on && blockIdx.x == 0) {
+        __shared__ double sred[7 * 32];
+        __shared__ double sk[3];
+        objective_scalars(sb.mode, sb.nv, sb.lambda, sb.eps, sb.P, sb.value, sk, sred);
+        return;
+    }
     const int64_t total = (int64_t)L.nc;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = (blockIdx.x - sb.on) * (int64_t)blockDim.x + threadIdx.x;
     const int i = (int)(t / total);
+    const int64_t e = t - (int64_t)i * total;
+    float p[NC], gr = 0.0f;
+    if (i < D)
+        ctrl_sum1<D, CH, BCX, BCY, BCZ>(L, gbx, gby, gbz, bpart, gR, i, e, p, gr);
+    float k0, k1 = 0.0f, k2 = 0.0f;
+    if (sb.on) {
+        __shared__ int scnt[8];
+        int n = 0;
+        for (int b = threadIdx.x; b < sb.P.nbricks; b += blockDim.x)
+            n += __ldg(icnt + b);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            n += __shfl_down_sync(0xffffffffu, n, off);
+        if ((threadIdx.x & 31) == 0)
+            scnt[threadIdx.x >> 5] = n;
+        __syncthreads();
+        n = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            n += scnt[w];
+        k0 = n > 0 ? 2.0f / (float)n : 0.0f;
+    } else {
+        k0 = (float)ks[0];
+        if (NC == 3) {
+            k1 = (float)ks[1];
+            k2 = (float)ks[2];
+        }
+    }
     if (i >= D)
         return;
-    const int64_t e = t - (int64_t)i * total;
-    float p[NC], gr;
-    ctrl_sum1<D, CH, BCX, BCY, BCZ>(L, gbx, gby, gbz, bpart, gR, i, e, p, gr);
     float v;
     if (NC == 3)
-        v = fmaf((float)ks[0], p[0], fmaf((float)ks[1], p[1 % NC], (float)ks[2] * p[2 % NC]));
+        v = fmaf(k0, p[0], fmaf(k1, p[1 % NC], k2 * p[2 % NC]));
     else
-        v = (float)ks[0] * p[0];
+        v = k0 * p[0];
     gc[(int64_t)i * total + e] = fmaf(lambda, gr, v);
 }
 
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t scal, rpart, gR, bpart, mpart, Wb, mb, gb, lpart, coef, Gb, total;
+    size_t scal, rpart, gR, bpart, mpart, icnt, Wb, mb, gb, lpart, coef, Gb, total;
     int nbricks, gbx, gby, gbz, ngram, nlcc;
 };
 
@@ -1376,6 +1426,8 @@ Layout make_layout(const Grid &g, const Lattice &L, int kind, int window)
     off += align256((size_t)o.nbricks * npart * 4);
     o.mpart = off;
     off += align256((size_t)o.nbricks * 6 * 8);
+    o.icnt = off;
+    off += align256((size_t)o.nbricks * 4);
     if (kind == 2) {
         o.Wb = off;
         off += align256((size_t)g.nv * 4);
@@ -1405,19 +1457,9 @@ struct GramBlocks {
     float gscale;
     int gbx, gby, nbricks;     // brick grid (x, y) and number of bricks
     int gtx, gty, gtz, ngram;  // Gram tiles per axis (gtz = 1 in 2D), total over components
+    int *icnt;                 // MSE: each brick's masked voxel count (or NULL)
 };
 
-// The scalars of the objective computed by block 0 of a k_fused launch (the
-// bricks then start at block 1): the projection pass of LCC runs after the
-// statistics, so block 0 forms J and the channel coefficients beside the
-// bricks instead of in a launch of its own.
-struct ScalBlock {
-    int on, mode;
-    int64_t nv;
-    double lambda, eps;
-    Parts P;
-    double *value, *ks;
-};
 
 template <int D, int DELTA, int MODE>
 __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
@@ -1440,7 +1482,7 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE>::THREADS,
     if (b < gb.nbricks) {
         const int bx = b % gb.gbx, by = (b / gb.gbx) % gb.gby, bz = b / (gb.gbx * gb.gby);
         fused_brick<D, DELTA, MODE>(g, L, F, M, c, gw_in, W_out, m_out, G_io, bpart, mpart, bx,
-                                    by, bz, b);
+                                    by, bz, b, BrickMaps{}, gb.icnt);
         return;
     }
     // tile index w = ((component * gtz + tz) * gty + ty) * gtx + tx, its R partial at rpart[w]
@@ -1479,7 +1521,7 @@ __global__ void __launch_bounds__(FCfg<3, DELTA, MODE>::THREADS,
         const int bx = b % gb.gbx, by = (b / gb.gbx) % gb.gby, bz = b / (gb.gbx * gb.gby);
         fused_brick<3, DELTA, MODE, brick_bcx(DELTA), brick_bcy(DELTA), true>(
             g, L, F, M, c, nullptr, W_out, m_out, G_io, bpart, mpart, bx, by, bz, b,
-            BrickMaps{&mapM, &mapF, &mapC, lb.x, lb.y, lb.z});
+            BrickMaps{&mapM, &mapF, &mapC, lb.x, lb.y, lb.z}, gb.icnt);
         return;
     }
     const int w = b - gb.nbricks;
@@ -1537,6 +1579,7 @@ cudaError_t run_fused_kernel(const Grid &g, const Lattice &L, const Layout &lay,
     gb.gty = (L.ny + T - 1) / T;
     gb.gtz = (D == 3) ? (L.nz + T - 1) / T : 1;
     gb.ngram = with_gram ? lay.ngram : 0;
+    gb.icnt = MODE == MODE_MSE ? (int *)(ws + lay.icnt) : nullptr;
     const size_t gsm = (size_t)((D == 3) ? kGram3Floats : kGram2Floats) * sizeof(float);
     const size_t dyn = (with_gram && gsm > C::dyn_smem) ? gsm : C::dyn_smem;
     ProfScope ps(s, MODE == MODE_MSE   ? "k_fused_mse"
@@ -1652,7 +1695,9 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     Parts parts{(const double *)(ws + lay.mpart), rpart, (const double *)(ws + lay.lpart),
                 lay.nbricks, lay.ngram, lay.nlcc};
     double *ks = (double *)(ws + lay.scal);  // channel coefficients for k_ctrl
-    if (!(kind == 2 && gc)) {  // LCC with gradient: block 0 of the projection pass did it
+    // MSE with gradient: block 0 of k_ctrl forms the scalars (selfk)
+    const bool selfk = kind == 0 && gc;
+    if (!(kind == 2 && gc) && !selfk) {  // LCC: block 0 of the projection pass did it
         ProfScope ps(s, "k_finalize");
         k_finalize<<<1, 256, 0, s>>>(mode, g.nv, lambda, eps, parts, value, gc ? ks : nullptr);
         e = cudaGetLastError();
@@ -1661,16 +1706,18 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
     }
     {
         const int th = 256;
-        const int64_t nb = ((int64_t)D * L.nc + th - 1) / th;  // one (component, point) per thread
+        const ScalBlock sb{selfk ? 1 : 0, mode, g.nv, lambda, eps, parts, value, nullptr};
+        const int64_t nb = sb.on + ((int64_t)D * L.nc + th - 1) / th;  // one (component, point) per thread
         const float *bp = (const float *)(ws + lay.bpart);
+        const int *icnt = (const int *)(ws + lay.icnt);
         ProfScope ps(s, "k_ctrl");
         constexpr int BCX = brick_bcx(DELTA), BCY = brick_bcy(DELTA), BCZ = brick_bcz(D);
         if (kind == 1)
-            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz,
-                                                                   (float)lambda, ks, bp, gR, gc);
+            k_ctrl<D, 3 * D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(
+                L, lay.gbx, lay.gby, lay.gbz, (float)lambda, ks, bp, gR, gc, sb, icnt);
         else
-            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(L, lay.gbx, lay.gby, lay.gbz,
-                                                               (float)lambda, ks, bp, gR, gc);
+            k_ctrl<D, D, BCX, BCY, BCZ><<<(int)nb, th, 0, s>>>(
+                L, lay.gbx, lay.gby, lay.gbz, (float)lambda, ks, bp, gR, gc, sb, icnt);
         e = cudaGetLastError();
     }
     return e;

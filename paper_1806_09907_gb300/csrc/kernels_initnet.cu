@@ -16,8 +16,8 @@
 //                    so the loss is exactly the mean squared difference of
 //                    the two displacement fields, computed on the lattice.
 //  * k_adam_flat     Adam (Sec. III-G) on a flat fp32 parameter array
-//  * k_render_blobs  training volumes: sums of isotropic Gaussian blobs (fast
-//                    exponential, terms beyond 6 sigma dropped: synthetic data)
+//  * k_render_blobs  training volumes: sums of isotropic Gaussian blobs (per-axis
+//                    factors, terms beyond 6 sigma dropped: synthetic data)
 //
 // All are memory- or latency-bound elementwise/gather kernels sized to the
 // data; none needs scratch beyond what its caller passes.
@@ -318,57 +318,76 @@ __global__ void k_tick(int64_t *step)
 // out[v][z][y][x] = sum_b a_b exp(-|x - mu_b|^2 / (2 sigma_b^2)) for the
 // blob table of volume v ([blob][mu_x, mu_y, mu_z, sigma, a]). A block owns
 // an 8 x 8 x 8 brick and first keeps the blobs that come within 6 sigma of
-// it: a dropped term is below a exp(-18) < 1.6e-8 a everywhere in the brick.
+// it (warp 0, in table order): a dropped term is below a exp(-18) < 1.6e-8 a
+// everywhere in the brick. A Gaussian separates into per-axis factors,
+//   a exp(-|p - mu|^2 / (2 sigma^2)) = ex(x) ey(y) (a ez(z)),
+// so each kept blob takes 24 exponentials per brick (8 per axis), and a
+// voxel's sum is three shared-memory reads and two multiplies per blob.
 constexpr int kBrick = 8;
 
 __global__ void __launch_bounds__(256) k_render_blobs(int D, int H, int W, int nblobs,
                                                       const float *__restrict__ table,
                                                       float *__restrict__ out)
 {
-    extern __shared__ float tb[];  // kept blobs: mu_x, mu_y, mu_z, -1/(2 sigma^2), a
+    extern __shared__ float fac[];  // kept blob k: ex[8], ey[8], a ez[8]
+    __shared__ int keep[1024];      // kept blob indices, in table order (n_blobs <= 1024)
     __shared__ int nkeep;
     const int vol = blockIdx.y;
     const int bx = (W + kBrick - 1) / kBrick, by = (H + kBrick - 1) / kBrick;
     const int brick = blockIdx.x;
     const int x0 = (brick % bx) * kBrick, y0 = ((brick / bx) % by) * kBrick,
               z0 = (brick / (bx * by)) * kBrick;
-    if (threadIdx.x == 0)
-        nkeep = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // in table order, so the sum below adds the kept blobs in a fixed order
-        for (int b = 0; b < nblobs; ++b) {
-            const float *e = table + ((int64_t)vol * nblobs + b) * 5;
-            const float mx = e[0], my = e[1], mz = e[2], sg = e[3];
-            // distance from the centre to the brick's box
-            const float dx = fmaxf(fmaxf((float)x0 - mx, mx - (float)(x0 + kBrick - 1)), 0.0f);
-            const float dy = fmaxf(fmaxf((float)y0 - my, my - (float)(y0 + kBrick - 1)), 0.0f);
-            const float dz = fmaxf(fmaxf((float)z0 - mz, mz - (float)(z0 + kBrick - 1)), 0.0f);
-            if (dx * dx + dy * dy + dz * dz <= 36.0f * sg * sg) {
-                float *k = tb + 5 * nkeep;
-                k[0] = mx;
-                k[1] = my;
-                k[2] = mz;
-                k[3] = -0.5f / (sg * sg);
-                k[4] = e[4];
-                ++nkeep;
+    const float *tv = table + (int64_t)vol * nblobs * 5;
+    if (threadIdx.x < 32) {
+        int base = 0;
+        for (int b0 = 0; b0 < nblobs; b0 += 32) {
+            const int b = b0 + threadIdx.x;
+            bool in = false;
+            if (b < nblobs) {
+                const float *e = tv + (int64_t)b * 5;
+                const float mx = e[0], my = e[1], mz = e[2], sg = e[3];
+                // distance from the centre to the brick's box
+                const float dx = fmaxf(fmaxf((float)x0 - mx, mx - (float)(x0 + kBrick - 1)), 0.0f);
+                const float dy = fmaxf(fmaxf((float)y0 - my, my - (float)(y0 + kBrick - 1)), 0.0f);
+                const float dz = fmaxf(fmaxf((float)z0 - mz, mz - (float)(z0 + kBrick - 1)), 0.0f);
+                in = dx * dx + dy * dy + dz * dz <= 36.0f * sg * sg;
             }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (in)
+                keep[base + __popc(m & ((1u << threadIdx.x) - 1u))] = b;
+            base += __popc(m);
         }
+        if (threadIdx.x == 0)
+            nkeep = base;
     }
     __syncthreads();
     const int n = nkeep;
+    // the per-axis factors of the kept blobs at the brick's 8 coordinates
+    for (int t = threadIdx.x; t < n * 24; t += blockDim.x) {
+        const int k = t / 24, r = t - k * 24, axis = r >> 3, o = r & 7;
+        const float *e = tv + (int64_t)keep[k] * 5;
+        const float c = (float)((axis == 0 ? x0 : axis == 1 ? y0 : z0) + o) - e[axis];
+        const float v = expf(-0.5f * c * c / (e[3] * e[3]));
+        fac[t] = axis == 2 ? e[4] * v : v;
+    }
+    __syncthreads();
+    // a thread takes the voxels lz and lz + 4 of one (x, y) column of the
+    // brick, sharing the x-y factor product (256 threads, 512 voxels)
     const int64_t nv = (int64_t)D * H * W;
-    for (int t = threadIdx.x; t < kBrick * kBrick * kBrick; t += blockDim.x) {
-        const int x = x0 + (t & 7), y = y0 + ((t >> 3) & 7), z = z0 + (t >> 6);
-        if (x >= W || y >= H || z >= D)
-            continue;
-        float acc = 0.0f;
-        for (int b = 0; b < n; ++b) {
-            const float dx = (float)x - tb[5 * b], dy = (float)y - tb[5 * b + 1],
-                        dz = (float)z - tb[5 * b + 2];
-            acc += tb[5 * b + 4] * __expf((dx * dx + dy * dy + dz * dz) * tb[5 * b + 3]);
-        }
-        out[(int64_t)vol * nv + ((int64_t)z * H + y) * W + x] = acc;
+    const int t = threadIdx.x & 255, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
+    const int x = x0 + lx, y = y0 + ly;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    for (int k = 0; k < n; ++k) {
+        const float *f = fac + 24 * k;
+        const float pxy = f[lx] * f[8 + ly];
+        acc0 = fmaf(pxy, f[16 + lz], acc0);
+        acc1 = fmaf(pxy, f[20 + lz], acc1);
+    }
+    if (threadIdx.x < 256 && x < W && y < H) {
+        if (z0 + lz < D)
+            out[(int64_t)vol * nv + ((int64_t)(z0 + lz) * H + y) * W + x] = acc0;
+        if (z0 + lz + 4 < D)
+            out[(int64_t)vol * nv + ((int64_t)(z0 + lz + 4) * H + y) * W + x] = acc1;
     }
 }
 
@@ -468,7 +487,14 @@ cudaError_t launch_render_blobs(int D, int H, int W, int count, int nblobs, cons
     const int bricks = ((W + kBrick - 1) / kBrick) * ((H + kBrick - 1) / kBrick) *
                        ((D + kBrick - 1) / kBrick);
     dim3 grid(bricks, count);
-    k_render_blobs<<<grid, 256, sizeof(float) * 5 * nblobs, s>>>(D, H, W, nblobs, table, out);
+    const size_t smem = sizeof(float) * 24 * (size_t)nblobs;  // up to 96 KB (1024 blobs)
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_render_blobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_render_blobs<<<grid, 256, smem, s>>>(D, H, W, nblobs, table, out);
     return cudaGetLastError();
 }
 
