@@ -68,15 +68,17 @@ struct FieldSample {
     bool in[3];
 };
 
+// (the field read is u * sc; sc is a power of two, so the product is exact)
 template <int D>
 __device__ __forceinline__ FieldSample field_sample(const Grid &g, int x, int y, int z,
-                                                    const float *__restrict__ u, int64_t v)
+                                                    const float *__restrict__ u, int64_t v,
+                                                    float sc = 1.0f)
 {
     FieldSample s;
-    s.in[0] = field_axis(x, __ldg(u + v), g.X, s.cell[0], s.f[0]);
-    s.in[1] = field_axis(y, __ldg(u + g.nv + v), g.Y, s.cell[1], s.f[1]);
+    s.in[0] = field_axis(x, __ldg(u + v) * sc, g.X, s.cell[0], s.f[0]);
+    s.in[1] = field_axis(y, __ldg(u + g.nv + v) * sc, g.Y, s.cell[1], s.f[1]);
     if (D == 3) {
-        s.in[2] = field_axis(z, __ldg(u + 2 * (int64_t)g.nv + v), g.Z, s.cell[2], s.f[2]);
+        s.in[2] = field_axis(z, __ldg(u + 2 * (int64_t)g.nv + v) * sc, g.Z, s.cell[2], s.f[2]);
     } else {
         s.cell[2] = 0;
         s.f[2] = 0.0f;
@@ -93,15 +95,20 @@ __global__ void __launch_bounds__(kDiffeoThreads)
         out[e] = in[e] * s;
 }
 
-// One squaring: out = u + u~(x + u).
-template <int D>
-__global__ void __launch_bounds__(kDiffeoThreads)
-    k_compose(Grid g, const float *__restrict__ u, float *__restrict__ out)
+// One squaring: out = u + u~(x + u), the field read as u * sc (sc = 2^-K on
+// the first squaring, which then reads v itself and also writes u_0 = v sc
+// to u0 when given; otherwise 1). Scaling by a power of two is exact, so
+// this equals scaling v in a pass of its own first.
+template <int D, bool SCALED>
+__global__ void __launch_bounds__(kDiffeoThreads, 8)
+    k_compose(Grid g, const float *__restrict__ u, float *__restrict__ out, float scale,
+              float *__restrict__ u0)
 {
+    const float sc = SCALED ? scale : 1.0f;  // a compile-time 1 on every squaring but the first
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.nv;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((int64_t)g.X * g.Y));
-        const FieldSample s = field_sample<D>(g, x, y, z, u, v);
+        const FieldSample s = field_sample<D>(g, x, y, z, u, v, sc);
         const int64_t base = ((int64_t)s.cell[2] * g.Y + s.cell[1]) * g.X + s.cell[0];
         const int64_t sx = 1, sy = g.X, sz = (int64_t)g.X * g.Y;
 #pragma unroll
@@ -109,20 +116,30 @@ __global__ void __launch_bounds__(kDiffeoThreads)
             const float *p = u + (int64_t)i * g.nv + base;
             float r;
             if (D == 3) {
-                const float c00 = (1.0f - s.f[0]) * __ldg(p) + s.f[0] * __ldg(p + sx);
-                const float c10 = (1.0f - s.f[0]) * __ldg(p + sy) + s.f[0] * __ldg(p + sy + sx);
-                const float c01 = (1.0f - s.f[0]) * __ldg(p + sz) + s.f[0] * __ldg(p + sz + sx);
-                const float c11 =
-                    (1.0f - s.f[0]) * __ldg(p + sz + sy) + s.f[0] * __ldg(p + sz + sy + sx);
+                const float c00 = (1.0f - s.f[0]) * (__ldg(p) * sc) + s.f[0] * (__ldg(p + sx) * sc);
+                const float c10 =
+                    (1.0f - s.f[0]) * (__ldg(p + sy) * sc) + s.f[0] * (__ldg(p + sy + sx) * sc);
+                const float c01 =
+                    (1.0f - s.f[0]) * (__ldg(p + sz) * sc) + s.f[0] * (__ldg(p + sz + sx) * sc);
+                const float c11 = (1.0f - s.f[0]) * (__ldg(p + sz + sy) * sc) +
+                                  s.f[0] * (__ldg(p + sz + sy + sx) * sc);
                 const float c0 = (1.0f - s.f[1]) * c00 + s.f[1] * c10;
                 const float c1 = (1.0f - s.f[1]) * c01 + s.f[1] * c11;
                 r = (1.0f - s.f[2]) * c0 + s.f[2] * c1;
             } else {
-                const float c0 = (1.0f - s.f[0]) * __ldg(p) + s.f[0] * __ldg(p + sx);
-                const float c1 = (1.0f - s.f[0]) * __ldg(p + sy) + s.f[0] * __ldg(p + sy + sx);
+                const float c0 = (1.0f - s.f[0]) * (__ldg(p) * sc) + s.f[0] * (__ldg(p + sx) * sc);
+                const float c1 =
+                    (1.0f - s.f[0]) * (__ldg(p + sy) * sc) + s.f[0] * (__ldg(p + sy + sx) * sc);
                 r = (1.0f - s.f[1]) * c0 + s.f[1] * c1;
             }
-            out[(int64_t)i * g.nv + v] = __ldg(u + (int64_t)i * g.nv + v) + r;
+            if constexpr (SCALED) {
+                const float own = __ldg(u + (int64_t)i * g.nv + v) * sc;
+                if (u0)
+                    u0[(int64_t)i * g.nv + v] = own;
+                out[(int64_t)i * g.nv + v] = own + r;
+            } else {
+                out[(int64_t)i * g.nv + v] = __ldg(u + (int64_t)i * g.nv + v) + r;
+            }
         }
     }
 }
@@ -255,19 +272,57 @@ __global__ void __launch_bounds__(kDiffeoThreads)
     }
 }
 
-// h += acc / 2^s; acc back to zero for the next step.
+// h += acc / 2^s; acc back to zero for the next step. With maxnext, also the
+// largest |h| (the next step's input) into *maxnext, as k_absmax does, so that
+// step needs no pass of its own for it.
+// With dest (the last step), (h + acc / 2^s) * dsc goes to dest instead, for
+// every entry (the exponential's final 2^-K).
 __global__ void __launch_bounds__(kDiffeoThreads)
     k_compose_finish(float *__restrict__ h, unsigned long long *__restrict__ acc, int64_t n,
-                     const unsigned int *__restrict__ maxbits)
+                     const unsigned int *__restrict__ maxbits, unsigned int *__restrict__ maxnext,
+                     float *__restrict__ dest, float dsc)
 {
     const float inv = 1.0f / fixed_scale(*maxbits);  // a power of two: exact
+    float m = 0.0f;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const long long q = (long long)acc[e];
-        if (q != 0) {
-            h[e] += __ll2float_rn(q) * inv;
-            acc[e] = 0ull;
+        float hv;
+        if (dest) {
+            hv = h[e];
+            if (q != 0) {
+                hv = hv + __ll2float_rn(q) * inv;
+                acc[e] = 0ull;
+            }
+            dest[e] = hv * dsc;
+            continue;
         }
+        if (q != 0) {
+            hv = h[e] + __ll2float_rn(q) * inv;
+            h[e] = hv;
+            acc[e] = 0ull;
+        } else if (maxnext) {
+            hv = h[e];
+        } else {
+            continue;
+        }
+        const float a = fabsf(hv);
+        m = a > m ? a : m;  // a NaN never wins
+    }
+    if (!maxnext)
+        return;
+    // one atomic per block (the grid is a few blocks per SM)
+    __shared__ float wm[kDiffeoThreads / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0)
+        wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kDiffeoThreads / 32; ++w)
+            m = fmaxf(m, wm[w]);
+        atomicMax(maxnext, __float_as_uint(m));
     }
 }
 
@@ -279,11 +334,29 @@ cudaError_t exp_run(const Grid &g, int K, const float *v, float *u, float *traj,
     const float sc = ldexpf(1.0f, -K);
     // u_0 -> traj[0] (or tmp); each squaring writes the next buffer
     ProfScope ps(s, "k_exp");
-    float *cur = traj ? traj : (K % 2 == 0 ? u : tmp);
-    if (K == 0)
-        cur = u;
-    k_scale<<<blocks_for(n), kDiffeoThreads, 0, s>>>(v, cur, sc, n);
-    cudaError_t e = cudaGetLastError();
+    if (K == 0) {
+        k_scale<<<blocks_for(n), kDiffeoThreads, 0, s>>>(v, u, sc, n);
+        return cudaGetLastError();
+    }
+    // the first squaring reads v scaled by 2^-K (and stores u_0 = v 2^-K in
+    // the trajectory); each squaring writes the next buffer. If v overlaps a
+    // buffer the squarings write, u_0 is formed in a pass of its own first.
+    auto overlaps = [&](const float *b, int64_t cnt) {
+        return b && v < b + cnt && b < v + n;
+    };
+    const float *cur = v;
+    float scale0 = sc;
+    cudaError_t e = cudaSuccess;
+    if (overlaps(u, n) || overlaps(tmp, n) || overlaps(traj, (int64_t)K * n)) {
+        float *u0 = traj ? traj : ((K - 1) % 2 == 0 ? tmp : u);
+        if (K == 1 && !traj)
+            u0 = tmp;
+        k_scale<<<blocks_for(n), kDiffeoThreads, 0, s>>>(v, u0, sc, n);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        cur = u0;
+        scale0 = 1.0f;
+    }
     for (int k = 0; k < K && e == cudaSuccess; ++k) {
         float *nxt;
         if (k == K - 1)
@@ -291,8 +364,13 @@ cudaError_t exp_run(const Grid &g, int K, const float *v, float *u, float *traj,
         else if (traj)
             nxt = traj + (int64_t)(k + 1) * n;
         else
-            nxt = (cur == tmp) ? u : tmp;
-        k_compose<D><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, cur, nxt);
+            nxt = ((K - 1 - k) % 2 == 0) ? u : tmp;
+        if (k == 0 && scale0 != 1.0f)
+            k_compose<D, true><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, cur, nxt, scale0,
+                                                                          traj);
+        else
+            k_compose<D, false><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, cur, nxt, 1.0f,
+                                                                           nullptr);
         e = cudaGetLastError();
         cur = nxt;
     }
@@ -312,19 +390,32 @@ cudaError_t exp_adjoint_run(const Grid &g, int K, const float *traj, const float
     cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)n * 8, s);
     const float *gin = gu;
     float *out = b0;
-    for (int k = K - 1; k >= 0 && e == cudaSuccess; --k) {
+    // mx[0], mx[1]: the largest |g| of a step's input; the first from a pass of
+    // its own, the others from the previous step's finish
+    if (e == cudaSuccess && K > 0) {
+        e = cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned int), s);
+        if (e == cudaSuccess) {
+            k_absmax<<<blocks_for(n) < 4 * device_sms() ? blocks_for(n) : 4 * device_sms(),
+                       kDiffeoThreads, 0, s>>>(gin, n, mx);
+            e = cudaGetLastError();
+        }
+    }
+    for (int k = K - 1, j = 0; k >= 0 && e == cudaSuccess; --k, j ^= 1) {
         const float *u = traj + (int64_t)k * n;
-        if ((e = cudaMemsetAsync(mx, 0, sizeof(unsigned int), s)) != cudaSuccess)
+        unsigned int *mcur = mx + j, *mnext = k > 0 ? mx + (j ^ 1) : nullptr;
+        k_compose_adjoint<D><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, u, gin, out, acc, mcur);
+        if (mnext && (e = cudaMemsetAsync(mnext, 0, sizeof(unsigned int), s)) != cudaSuccess)
             break;
-        k_absmax<<<blocks_for(n) < 4 * device_sms() ? blocks_for(n) : 4 * device_sms(),
-                   kDiffeoThreads, 0, s>>>(
-            gin, n, mx);
-        k_compose_adjoint<D><<<blocks_for(g.nv), kDiffeoThreads, 0, s>>>(g, u, gin, out, acc, mx);
-        k_compose_finish<<<blocks_for(n), kDiffeoThreads, 0, s>>>(out, acc, n, mx);
+        // the last step writes (its result) * 2^-K to gv directly
+        const int fb = blocks_for(n) < 4 * device_sms() ? blocks_for(n) : 4 * device_sms();
+        k_compose_finish<<<fb, kDiffeoThreads, 0, s>>>(out, acc, n, mcur, mnext,
+                                                       k == 0 ? gv : nullptr, ldexpf(1.0f, -K));
         e = cudaGetLastError();
         gin = out;
         out = (out == b0) ? b1 : b0;
     }
+    if (K > 0)
+        return e;
     if (e != cudaSuccess)
         return e;
     k_scale<<<blocks_for(n), kDiffeoThreads, 0, s>>>(gin, gv, ldexpf(1.0f, -K), n);
