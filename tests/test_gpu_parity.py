@@ -363,6 +363,19 @@ def check_objective(F, M, c, delta, sim, window=7, lam=0.1, fused=True):
     return val, g
 
 
+@pytest.mark.parametrize("sim", ["mse", "ncc", "lcc"])
+@pytest.mark.parametrize("delta", [4, 6, 8])
+def test_objective_tma_bricks(delta, sim):
+    """The TMA-staged 3D brick kernels (X a multiple of 4, the volume at least
+    one staged box wide) at every spacing and similarity against the oracle:
+    20 x 36 x 48 holds a ragged last brick along x at spacings 4 and 8, along
+    y at every spacing and along z, and displacements of a few voxels (c ~
+    N(0, 1.2^2)) keep some samples' cells outside the staged window (the
+    global-memory path)."""
+    F, M, c = blob_case((20, 36, 48), delta, 1.2, 70 + delta)
+    check_objective(F, M, c, delta, sim, window=5)
+
+
 @pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("sim", ["mse", "ncc", "lcc"])
 @pytest.mark.parametrize("shape,delta", SMALL)
