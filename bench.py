@@ -576,11 +576,12 @@ def learned_init_runs(dev, pairs, n_test):
     tr = learned_init.train(net, pairs=pairs, lr=1e-3, sigma=4.0, seed=0)
     # one training step's kernels (library event timing, a separate network)
     prof = learned_init.InitNet(shape, batch, dev, seed=7)
-    learned_init.train(prof, pairs=batch, seed=5)
+    learned_init.train(prof, pairs=batch, seed=5, graph=False)
     airgb.profile_reset()
     airgb.profile_enable(True)
     n_prof = 5
-    learned_init.train(prof, pairs=n_prof * batch, seed=5)
+    # eager, so every launch is timed (graph replays are not)
+    learned_init.train(prof, pairs=n_prof * batch, seed=5, graph=False)
     step_kernels = {k: {"us_per_step": 1000.0 * t / n_prof, "launches_per_step": n // n_prof}
                     for k, (t, n) in airgb.profile_collect().items()}
     airgb.profile_enable(False)

@@ -130,6 +130,16 @@ al_status al_bspline_init(al_bspline *bs, const al_grid *g, int32_t spacing);
  * (overwritten). */
 al_status al_displacement(const al_bspline *bs, const float *ctrl, float *disp, al_stream stream);
 
+/* A1 + A2 for `count` volumes at once, without materialising the field:
+ * warped[v] = moving[v] o (x + u_v), u_v = the displacement of ctrl[v] (as
+ * al_displacement), with the masked trilinear warp of al_warp; mask[v]
+ * written when mask is not NULL. moving, warped: count volumes of Z*Y*X
+ * floats; ctrl: count lattices of ndim * nz*ny*nx floats; mask: count * Z*Y*X
+ * bytes. The arithmetic is that of al_objective_grad's fused path. Spacings
+ * 4, 6 and 8 (AL_ERR_UNSUPPORTED otherwise); count 1 .. 65535. */
+al_status al_warp_ctrl(const al_bspline *bs, int32_t count, const float *moving,
+                       const float *ctrl, float *warped, uint8_t *mask, al_stream stream);
+
 /* A6. Adjoint of al_displacement (the transposed up-sampling):
  * grad_ctrl[i,j] = sum_x k(x_j, x) grad_disp[i](x), computed as a gather per
  * control point (fixed order, no atomics). grad_ctrl is overwritten.
@@ -569,7 +579,9 @@ al_status al_fused_set_wait(int32_t drop_batch);
  * max_kernels totals: total_ms[i], launches[i], and the kernel names as
  * newline-separated text in `names` (truncated to names_bytes). Returns the
  * number of distinct kernels seen. Host only; not thread-safe against
- * concurrent launches on other threads while enabled. */
+ * concurrent launches on other threads while enabled. Launches on a stream
+ * that is being captured into a CUDA graph are not timed (nor are their
+ * replays). */
 al_status al_profile_enable(int32_t on);
 int32_t al_profile_collect(char *names, size_t names_bytes, double *total_ms, int64_t *launches,
                            int32_t max_kernels);

@@ -49,7 +49,7 @@ EXPORTS = (
     "al_conv3d_backward_weight_workspace_bytes", "al_conv3d_backward_weight", "al_initnet_input",
     "al_initnet_upcat", "al_initnet_upcat_adjoint", "al_initnet_head_to_ctrl",
     "al_initnet_head_adjoint", "al_field_loss_workspace_bytes", "al_field_loss", "al_adam_flat",
-    "al_render_blobs", "al_lcc_set_wait", "al_fused_set_wait",
+    "al_render_blobs", "al_lcc_set_wait", "al_fused_set_wait", "al_warp_ctrl",
 )
 
 
@@ -106,6 +106,7 @@ def load():
         "al_status_string": ([I32], ctypes.c_char_p),
         "al_bspline_init": ([P(al_bspline), P(al_grid), I32], I32),
         "al_displacement": ([P(al_bspline), VP, VP, VP], I32),
+        "al_warp_ctrl": ([P(al_bspline), I32, VP, VP, VP, VP, VP], I32),
         "al_displacement_adjoint": ([P(al_bspline), VP, VP, VP, SZ, VP], I32),
         "al_displacement_adjoint_workspace_bytes": ([P(al_bspline)], SZ),
         "al_warp": ([P(al_grid), VP, VP, VP, VP, VP], I32),
@@ -290,6 +291,26 @@ def al_displacement(shape, spacing, ctrl, disp=None, stream=None):
     _f32(disp, (d,) + tuple(shape), "disp")
     _call("al_displacement", ctypes.byref(bs), _ptr(ctrl), _ptr(disp), _stream(stream))
     return disp
+
+
+def al_warp_ctrl(shape, spacing, moving, ctrl, warped=None, mask=None, stream=None):
+    """A1 + A2 for a batch: warped[v] = moving[v] o (x + B ctrl[v]) without
+    materialising the field. moving: (count, *shape), ctrl: (count, ndim,
+    *lattice); mask (optional, uint8, (count, *shape)) receives the mask."""
+    bs = bspline_init(shape, spacing)
+    d = _ndim_of(shape)
+    count = int(moving.shape[0])
+    _f32(moving, (count,) + tuple(shape), "moving")
+    _f32(ctrl, (count, d) + lattice_shape(shape, spacing), "ctrl")
+    if warped is None:
+        warped = torch.empty_like(moving)
+    _f32(warped, (count,) + tuple(shape), "warped")
+    if mask is not None and (mask.dtype != torch.uint8 or tuple(mask.shape) != (count,) + tuple(shape)
+                             or not mask.is_contiguous()):
+        raise ValueError(f"mask: expected uint8 {(count,) + tuple(shape)}")
+    _call("al_warp_ctrl", ctypes.byref(bs), count, _ptr(moving), _ptr(ctrl), _ptr(warped),
+          _ptr(mask), _stream(stream))
+    return warped
 
 
 def al_displacement_adjoint(shape, spacing, grad_disp, grad_ctrl=None, workspace=None,
@@ -724,18 +745,23 @@ def _act(t, shape, what, dtype=torch.bfloat16):
     return _ptr(t)
 
 
-def al_conv3d_pack(cv, weight, fwd=True, dgrad=True, stream=None):
-    """bf16 weight copies in the layer kernels' layout: (packed_fwd, packed_dgrad)."""
+def al_conv3d_pack(cv, weight, fwd=True, dgrad=True, stream=None, out=None):
+    """bf16 weight copies in the layer kernels' layout: (packed_fwd, packed_dgrad).
+    out: a previous result to write into (no allocation)."""
     _f32(weight, (cv.cout, 27, cv.cin), "weight")
     pf = pd = None
     if fwd:
-        pf = torch.empty(load().al_conv3d_packed_bytes(ctypes.byref(cv), 0), dtype=torch.uint8,
-                         device=weight.device)
+        nf = load().al_conv3d_packed_bytes(ctypes.byref(cv), 0)
+        pf = out[0] if out is not None and out[0] is not None else None
+        if pf is None or pf.numel() != nf:
+            pf = torch.empty(nf, dtype=torch.uint8, device=weight.device)
     if dgrad:
         n = load().al_conv3d_packed_bytes(ctypes.byref(cv), 1)
         if n == 0:
             raise ValueError("dgrad packing needs cin a multiple of 16")
-        pd = torch.empty(n, dtype=torch.uint8, device=weight.device)
+        pd = out[1] if out is not None and out[1] is not None else None
+        if pd is None or pd.numel() != n:
+            pd = torch.empty(n, dtype=torch.uint8, device=weight.device)
     _call("al_conv3d_pack", ctypes.byref(cv), _ptr(weight), _ptr(pf), _ptr(pd), _stream(stream))
     return pf, pd
 

@@ -217,6 +217,23 @@ al_status al_displacement(const al_bspline *bs, const float *ctrl, float *disp, 
     return launched(launch_displacement(g, L, ctrl, disp, S(stream)));
 }
 
+al_status al_warp_ctrl(const al_bspline *bs, int32_t count, const float *moving,
+                       const float *ctrl, float *warped, uint8_t *mask, al_stream stream)
+{
+    Grid g;
+    Lattice L;
+    al_status st = check_bspline(bs, &g, &L);
+    if (st != AL_OK)
+        return st;
+    if (count < 1 || count > 65535 || !moving || !ctrl || !warped)
+        return AL_ERR_INVALID_ARG;
+    if (L.delta != 4 && L.delta != 6 && L.delta != 8)
+        return AL_ERR_UNSUPPORTED;
+    if (!aligned16(moving) || !aligned16(ctrl) || !aligned16(warped) || (mask && !aligned16(mask)))
+        return AL_ERR_ALIGN;
+    return launched(launch_warp_ctrl(g, L, count, moving, ctrl, warped, mask, S(stream)));
+}
+
 size_t al_displacement_adjoint_workspace_bytes(const al_bspline *bs)
 {
     Grid g;

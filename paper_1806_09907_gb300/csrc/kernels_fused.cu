@@ -769,7 +769,8 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 const int v = (z * g.Y + y) * g.X + x;
                 if (MODE == MODE_FWD) {
                     W_out[v] = inb[j] ? ip.v : 0.0f;
-                    m_out[v] = inb[j] ? 1 : 0;
+                    if (m_out)
+                        m_out[v] = inb[j] ? 1 : 0;
                     if (G_io) {
                         G_io[v] = inb[j] ? ip.gx : 0.0f;
                         G_io[g.nv + v] = inb[j] ? ip.gy : 0.0f;
@@ -1724,6 +1725,42 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Warp of `count` volumes by the B-spline fields of their control lattices
+// (A1 + A2 fused, the forward brick with no gradient planes): W[v] =
+// M[v] o (x + B c[v]), mask[v] when given. blockIdx.y is the volume.
+template <int D, int DELTA>
+__global__ void __launch_bounds__(FCfg<D, DELTA, MODE_FWD>::THREADS,
+                                  FCfg<D, DELTA, MODE_FWD>::THREADS <= 512 ? 2 : 1)
+    k_warp_ctrl(Grid g, Lattice L, int gbx, int gby, const float *__restrict__ M,
+                const float *__restrict__ c, float *__restrict__ W, uint8_t *__restrict__ m)
+{
+    const int b = blockIdx.x;
+    const int64_t vol = blockIdx.y;
+    const int bx = b % gbx, by = (b / gbx) % gby, bz = b / (gbx * gby);
+    fused_brick<D, DELTA, MODE_FWD>(g, L, nullptr, M + vol * g.nv, c + vol * D * L.nc, nullptr,
+                                    W + vol * g.nv, m ? m + vol * g.nv : nullptr, nullptr,
+                                    nullptr, nullptr, bx, by, bz, b);
+}
+
+template <int D, int DELTA>
+cudaError_t warp_ctrl_run(const Grid &g, const Lattice &L, int count, const float *M,
+                          const float *c, float *W, uint8_t *m, cudaStream_t s)
+{
+    using C = FCfg<D, DELTA, MODE_FWD>;
+    const Layout lay = make_layout(g, L, 0, 3);
+    if (C::dyn_smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_warp_ctrl<D, DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::dyn_smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    ProfScope ps(s, "k_warp_ctrl");
+    k_warp_ctrl<D, DELTA><<<dim3(lay.nbricks, count), C::THREADS, C::dyn_smem, s>>>(
+        g, L, lay.gbx, lay.gby, M, c, W, m);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Batches: one persistent launch per iteration over many problems.
 //
 // The launch's blocks take work items from a device queue (one atomic
@@ -1952,6 +1989,25 @@ cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, 
         case 4: return run_all<2, 4>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
         case 6: return run_all<2, 6>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
         case 8: return run_all<2, 8>(g, L, kind, window, eps, lambda, F, M, c, value, gc, w, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_warp_ctrl(const Grid &g, const Lattice &L, int count, const float *M,
+                             const float *c, float *W, uint8_t *m, cudaStream_t s)
+{
+    if (g.ndim == 3) {
+        switch (L.delta) {
+        case 4: return warp_ctrl_run<3, 4>(g, L, count, M, c, W, m, s);
+        case 6: return warp_ctrl_run<3, 6>(g, L, count, M, c, W, m, s);
+        case 8: return warp_ctrl_run<3, 8>(g, L, count, M, c, W, m, s);
+        }
+    } else {
+        switch (L.delta) {
+        case 4: return warp_ctrl_run<2, 4>(g, L, count, M, c, W, m, s);
+        case 6: return warp_ctrl_run<2, 6>(g, L, count, M, c, W, m, s);
+        case 8: return warp_ctrl_run<2, 8>(g, L, count, M, c, W, m, s);
         }
     }
     return cudaErrorInvalidValue;

@@ -52,6 +52,13 @@ void prof_begin(cudaStream_t s, const char *name)
 {
     if (!g_on)
         return;
+    // a stream being captured into a CUDA graph records nothing: an event
+    // recorded there would become a graph node, not a timestamp
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     t_open = take_event();
     t_name = name;

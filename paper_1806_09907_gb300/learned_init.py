@@ -105,7 +105,8 @@ class InitNet:
     def pack(self, stream=None):
         """bf16 copies of the weights in the layer kernels' layout."""
         for k, cv in enumerate(self.convs):
-            self.packed[k] = airgb.al_conv3d_pack(cv, self.weight(k), True, k > 0, stream=stream)
+            self.packed[k] = airgb.al_conv3d_pack(cv, self.weight(k), True, k > 0, stream=stream,
+                                                  out=self.packed[k])
 
     # ---- forward / backward ----
     def forward(self, fixed, moving, out=None, stream=None):
@@ -215,12 +216,8 @@ class PairSource:
         self.M = torch.empty_like(self.F)
         self.ctrl = torch.empty((self.batch,) + self.lattice, dtype=torch.float32,
                                 device=self.device)
-        # one pair's coefficients: a batch slice is not 16-byte aligned in general
-        self.ctrl_one = torch.empty(self.lattice, dtype=torch.float32, device=self.device)
         self.table = torch.empty((self.batch, self.n_blobs, 5), dtype=torch.float32,
                                  device=self.device)
-        self.disp = torch.empty((3,) + self.shape, dtype=torch.float32, device=self.device)
-        self.mask = torch.empty(self.shape, dtype=torch.uint8, device=self.device)
         self.gen = torch.Generator(device=self.device)
         hi = [self.shape[2] - 1, self.shape[1] - 1, self.shape[0] - 1]
         lo_s, hi_s = self.sigma_range
@@ -237,11 +234,8 @@ class PairSource:
         torch.randn(self.ctrl.shape, generator=self.gen, device=self.device, out=self.ctrl)
         self.ctrl.mul_(self.sigma)
         airgb.al_render_blobs(self.shape, self.table, out=self.M, stream=stream)
-        for b in range(self.batch):
-            self.ctrl_one.copy_(self.ctrl[b])
-            airgb.al_displacement(self.shape, SPACING, self.ctrl_one, disp=self.disp,
-                                  stream=stream)
-            airgb.al_warp(self.M[b], self.disp, warped=self.F[b], mask=self.mask, stream=stream)
+        # F = M o (x + B c*), the whole batch in one launch
+        airgb.al_warp_ctrl(self.shape, SPACING, self.M, self.ctrl, warped=self.F, stream=stream)
         return self.F, self.M, self.ctrl
 
 
@@ -254,11 +248,15 @@ class TrainResult:
 
 
 def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigma=4.0, seed=0,
-          log_every=0, epochs=1, lr_final=None):
+          log_every=0, epochs=1, lr_final=None, graph=True):
     """Adam on the field loss over `pairs` method-generated pairs, net.batch
     per step, `epochs` passes over the same pairs. The step size decays from
     lr to lr_final along a half cosine when lr_final is given (else stays lr).
-    Returns the per-step losses and the wall time."""
+    With a constant step size (and graph=True) the network part of a step --
+    forward, field loss, backward, Adam, packing, all on fixed buffers -- is
+    captured once in a CUDA graph after the first (eager) step and replayed;
+    the pair generation stays eager, so it is issued while the previous
+    step's replay runs. Returns the per-step losses and the wall time."""
     dev = net.device
     src = PairSource(net.shape, net.batch, sigma, seed, dev)
     per_epoch = (int(pairs) + net.batch - 1) // net.batch
@@ -271,17 +269,33 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
     c = torch.empty_like(gc)
     lws = torch.empty(max(airgb.field_loss_workspace_bytes(net.batch), 256), dtype=torch.uint8,
                       device=dev)
+    loss_one = torch.empty(1, dtype=torch.float64, device=dev)
+    use_graph = graph and lr_final is None and steps > 1
+    step_graph = None
+
+    def net_step(F, M, ct, loss, lr_i):
+        net.forward(F, M, out=c)
+        airgb.al_field_loss(net.shape, c, ct, loss=loss, grad=gc, workspace=lws)
+        net.backward(gc)
+        airgb.al_adam_flat(net.params, net.grad, m, v, step, lr=lr_i, betas=betas, eps=eps)
+        net.pack()
+
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for i in range(steps):
         F, M, ct = src.make((i % per_epoch) * net.batch)
-        net.forward(F, M, out=c)
-        airgb.al_field_loss(net.shape, c, ct, loss=losses[i:i + 1], grad=gc, workspace=lws)
-        net.backward(gc)
-        lr_i = lr if lr_final is None else \
-            lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * i / max(steps - 1, 1)))
-        airgb.al_adam_flat(net.params, net.grad, m, v, step, lr=lr_i, betas=betas, eps=eps)
-        net.pack()
+        if step_graph is not None:
+            step_graph.replay()
+            losses[i:i + 1].copy_(loss_one)
+        else:
+            lr_i = lr if lr_final is None else \
+                lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * i / max(steps - 1, 1)))
+            net_step(F, M, ct, losses[i:i + 1], lr_i)
+            if use_graph:
+                # the buffers exist now (the eager step made them): capture
+                step_graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(step_graph, capture_error_mode="thread_local"):
+                    net_step(F, M, ct, loss_one, lr)
         if log_every and (i + 1) % log_every == 0:
             print(f"step {i + 1}/{steps} loss {float(losses[i]):.4f}", flush=True)
     torch.cuda.synchronize(dev)

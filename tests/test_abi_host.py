@@ -311,6 +311,19 @@ def test_fused_wait_hook_rejects_bad_batch(lib):
     assert lib.al_fused_set_wait(-2) == 1
 
 
+def test_warp_ctrl_rejects(lib):
+    """al_warp_ctrl: bad count or NULL pointers 1, a spacing without a fused
+    kernel 7 (unsupported), a misaligned pointer 3; nothing launches."""
+    from paper_1806_09907_gb300 import airgb
+    bs = airgb.bspline_init((20, 36, 48), 6)
+    a = ctypes.c_void_p(0x10000)
+    assert lib.al_warp_ctrl(ctypes.byref(bs), 0, a, a, a, None, None) == 1
+    assert lib.al_warp_ctrl(ctypes.byref(bs), 2, None, a, a, None, None) == 1
+    assert lib.al_warp_ctrl(ctypes.byref(bs), 2, a, a, ctypes.c_void_p(0x10004), None, None) == 3
+    bs5 = airgb.bspline_init((20, 36, 48), 5)
+    assert lib.al_warp_ctrl(ctypes.byref(bs5), 2, a, a, a, None, None) == 7
+
+
 def test_batch_bind_tune_status_reject(lib):
     """Binding checks every device pointer (NULL 1, misaligned 3) and the
     workspace (8) on the host; tuning needs a bound workspace (8) and at

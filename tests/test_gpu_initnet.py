@@ -382,6 +382,18 @@ def test_short_training_lowers_the_loss():
     assert airgb.al_get_device_error() == 0
 
 
+def test_graph_replayed_training_equals_eager():
+    """Training with the network part of each step replayed from a CUDA graph
+    gives the eager loop's losses and parameters bit for bit."""
+    runs = []
+    for graph in (False, True):
+        net = learned_init.InitNet((48, 48, 48), 2, DEV, seed=4)
+        res = learned_init.train(net, pairs=2 * 5, lr=1e-3, sigma=3.0, seed=9, graph=graph)
+        runs.append((res.losses, net.params.clone()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert torch.equal(runs[0][1], runs[1][1])
+
+
 @pytest.mark.parametrize("nb,dims,cin,cout,stride", [(1, (9, 10, 11), 112, 48, 1),
                                                      (1, (8, 8, 8), 48, 64, 2),
                                                      (1, (16, 16, 16), 32, 48, 2)])

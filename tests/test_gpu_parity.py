@@ -192,6 +192,39 @@ def test_fused_tma_wait_timeout_is_reported_and_recoverable(sim, batch):
     check_objective(F, M, c, 6, sim, window=5)
 
 
+@pytest.mark.parametrize("shape,delta", [((20, 36, 48), 6), ((17, 30, 41), 4), ((25, 26), 8)])
+def test_warp_ctrl_batch(shape, delta):
+    """al_warp_ctrl (the field never materialised, several volumes per call)
+    against the oracle's warp of each moving volume by its own B-spline
+    field: masks equal but for samples within the fp32 band of a face, W
+    within 1e-5 x range where both masks are set."""
+    nd = len(shape)
+    rng = np.random.default_rng(40 + delta)
+    Ms, cs = [], []
+    for k in range(3):
+        F, M, c = blob_case(shape, delta, 1.5, 80 + 7 * k)
+        Ms.append(M)
+        cs.append(c)
+    Mb, cb = np.stack(Ms), np.stack(cs)
+    mask = torch.empty(Mb.shape, dtype=torch.uint8, device="cuda")
+    W = host(airgb.al_warp_ctrl(shape, delta, dev(Mb), dev(cb), mask=mask))
+    mk = host(mask)
+    for k in range(3):
+        u = oracle.displacement(shape, delta, cs[k])
+        Wr, mr = oracle.warp(Ms[k], u)
+        ug = host(airgb.al_displacement(shape, delta, dev(cs[k])))
+        band = max(2 * float(np.abs(ug - u).max()), 1e-9)
+        near = np.zeros(shape, dtype=bool)
+        for a in range(nd):
+            n = shape[nd - 1 - a]
+            y = u[a] + np.arange(n).reshape([-1 if b == nd - 1 - a else 1 for b in range(nd)])
+            near |= (np.abs(y) < band) | (np.abs(y - (n - 1)) < band)
+        assert not np.any((mk[k] != mr) & ~near)
+        both = (mk[k] == 1) & (mr == 1)
+        assert float(np.abs(W[k] - Wr)[both].max()) <= W_TOL * float(Ms[k].max() - Ms[k].min())
+        assert np.all(W[k][mk[k] == 0] == 0.0)
+
+
 # ----------------------------------------------------------------------- A4 --
 
 @pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (2, 2, 2)])
