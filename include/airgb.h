@@ -533,6 +533,23 @@ al_status al_field_loss(const al_bspline *bs, int32_t batch, const float *ctrl,
 al_status al_adam_flat(const al_adam_params *p, int64_t n, int64_t *step, float *param,
                        const float *grad, float *m, float *v, al_stream stream);
 
+/* al_adam_flat that also refreshes the packed bf16 weights of up to 8
+ * convolution layers, so that a training step needs no al_conv3d_pack between
+ * its Adam update and the next forward pass. Layer j (layers[j]) owns
+ * param[weight_offset[j] .. + cout*27*cin) as its weight (cout x 27 x cin);
+ * the ranges lie inside [0, n) and do not overlap; parameters outside them
+ * (biases) take the plain update. packed_fwd[j] and packed_dgrad[j] (either
+ * NULL, not both) must hold an al_conv3d_pack result of the same layer: each
+ * updated weight is rounded to bf16 and written to its one place in each copy,
+ * the zero padding is left as that pack wrote it. The result equals
+ * al_adam_flat followed by al_conv3d_pack of every layer, bit for bit.
+ * Errors: AL_ERR_INVALID_ARG (pointers, parameters, ranges), the layer checks
+ * of al_conv3d_pack, AL_ERR_ALIGN (16-byte alignment of every buffer). */
+al_status al_adam_flat_pack(const al_adam_params *p, int64_t n, int64_t *step, float *param,
+                            const float *grad, float *m, float *v, int32_t n_layers,
+                            const al_conv3d *layers, const int64_t *weight_offset,
+                            void *const *packed_fwd, void *const *packed_dgrad, al_stream stream);
+
 /* Training volumes: out[v][z][y][x] = sum_b a_b exp(-|x - mu_b|^2/(2 sigma_b^2))
  * for `count` volumes of size (z, y, x), blob table[v][b] = {mu_x, mu_y,
  * mu_z, sigma, a} (fp32, n_blobs per volume; sigma > 0). Terms of blobs more

@@ -49,6 +49,7 @@ EXPORTS = (
     "al_conv3d_backward_weight_workspace_bytes", "al_conv3d_backward_weight", "al_initnet_input",
     "al_initnet_upcat", "al_initnet_upcat_adjoint", "al_initnet_head_to_ctrl",
     "al_initnet_head_adjoint", "al_field_loss_workspace_bytes", "al_field_loss", "al_adam_flat",
+    "al_adam_flat_pack",
     "al_render_blobs", "al_lcc_set_wait", "al_fused_set_wait", "al_warp_ctrl",
 )
 
@@ -169,6 +170,8 @@ def load():
         "al_field_loss_workspace_bytes": ([I32], SZ),
         "al_field_loss": ([P(al_bspline), I32, VP, VP, VP, VP, VP, SZ, VP], I32),
         "al_adam_flat": ([P(al_adam_params), ctypes.c_int64, VP, VP, VP, VP, VP, VP], I32),
+        "al_adam_flat_pack": ([P(al_adam_params), ctypes.c_int64, VP, VP, VP, VP, VP, I32,
+                               P(al_conv3d), P(ctypes.c_int64), P(VP), P(VP), VP], I32),
         "al_render_blobs": ([P(ctypes.c_int64), I32, I32, VP, VP, VP], I32),
     }
     for name, (args, res) in sig.items():
@@ -913,6 +916,22 @@ def al_adam_flat(param, grad, m, v, step, lr=1e-3, betas=(0.9, 0.999), eps=1e-8,
     p.lr, p.beta1, p.beta2, p.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
     _call("al_adam_flat", ctypes.byref(p), ctypes.c_int64(param.numel()), _ptr(step),
           _ptr(param), _ptr(grad), _ptr(m), _ptr(v), _stream(stream))
+
+
+def al_adam_flat_pack(param, grad, m, v, step, layers, lr=1e-3, betas=(0.9, 0.999), eps=1e-8,
+                      stream=None):
+    """al_adam_flat plus the refresh of packed weights: layers is a list of
+    (cv, weight_offset, packed_fwd, packed_dgrad), the packed tensors (either
+    None) holding an al_conv3d_pack result of that layer."""
+    p = al_adam_params()
+    p.lr, p.beta1, p.beta2, p.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
+    nl = len(layers)
+    cvs = (al_conv3d * max(nl, 1))(*[l[0] for l in layers])
+    offs = (ctypes.c_int64 * max(nl, 1))(*[int(l[1]) for l in layers])
+    pf = (ctypes.c_void_p * max(nl, 1))(*[_ptr(l[2]) for l in layers])
+    pd = (ctypes.c_void_p * max(nl, 1))(*[_ptr(l[3]) for l in layers])
+    _call("al_adam_flat_pack", ctypes.byref(p), ctypes.c_int64(param.numel()), _ptr(step),
+          _ptr(param), _ptr(grad), _ptr(m), _ptr(v), nl, cvs, offs, pf, pd, _stream(stream))
 
 
 def al_render_blobs(shape, table, out=None, stream=None):

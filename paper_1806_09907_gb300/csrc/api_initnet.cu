@@ -354,6 +354,53 @@ al_status al_adam_flat(const al_adam_params *p, int64_t n, int64_t *step, float 
     return ok_launch(launch_adam_flat(a, step, param, grad, m, v, St(stream)));
 }
 
+al_status al_adam_flat_pack(const al_adam_params *p, int64_t n, int64_t *step, float *param,
+                            const float *grad, float *m, float *v, int32_t n_layers,
+                            const al_conv3d *layers, const int64_t *weight_offset,
+                            void *const *packed_fwd, void *const *packed_dgrad, al_stream stream)
+{
+    if (!p || n < 1 || !step || !param || !grad || !m || !v)
+        return AL_ERR_INVALID_ARG;
+    if (!(p->lr > 0) || !(p->beta1 >= 0 && p->beta1 < 1) || !(p->beta2 >= 0 && p->beta2 < 1) ||
+        !(p->eps >= 0))
+        return AL_ERR_INVALID_ARG;
+    if (n_layers < 1 || n_layers > kMaxPackLayers || !layers || !weight_offset || !packed_fwd ||
+        !packed_dgrad)
+        return AL_ERR_INVALID_ARG;
+    if (!aligned16(param) || !aligned16(grad) || !aligned16(m) || !aligned16(v))
+        return AL_ERR_ALIGN;
+    AdamPackArgs a = {};
+    a.adam.beta1 = p->beta1;
+    a.adam.beta2 = p->beta2;
+    a.adam.lr = (float)p->lr;
+    a.adam.eps = (float)p->eps;
+    a.adam.n = n;
+    a.nl = n_layers;
+    int64_t lo[kMaxPackLayers], hi[kMaxPackLayers];
+    for (int j = 0; j < n_layers; ++j) {
+        ConvLayer l;
+        const al_status st = check_conv(&layers[j], &l);
+        if (st != AL_OK)
+            return st;
+        void *pf = packed_fwd[j], *pd = packed_dgrad[j];
+        if (!pf && !pd)
+            return AL_ERR_INVALID_ARG;
+        if (pd && (l.cin % 16 != 0 || l.cin > 128))
+            return AL_ERR_UNSUPPORTED;
+        if (!aligned16(pf) || !aligned16(pd))
+            return AL_ERR_ALIGN;
+        lo[j] = weight_offset[j];
+        hi[j] = lo[j] + (int64_t)l.cout * 27 * l.cin;
+        if (lo[j] < 0 || hi[j] > n)
+            return AL_ERR_INVALID_ARG;
+        for (int i = 0; i < j; ++i)
+            if (lo[j] < hi[i] && lo[i] < hi[j])
+                return AL_ERR_INVALID_ARG;  // weight ranges overlap
+        adam_pack_layer(l, lo[j], pf, pd, &a.L[j]);
+    }
+    return ok_launch(launch_adam_pack(a, step, param, grad, m, v, St(stream)));
+}
+
 al_status al_render_blobs(const int64_t *size, int32_t count, int32_t n_blobs, const float *table,
                           float *out, al_stream stream)
 {

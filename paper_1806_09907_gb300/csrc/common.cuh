@@ -389,4 +389,32 @@ __device__ __forceinline__ void block_reduce_fd(float (&v)[K], double (&out)[K],
     }
 }
 
+// Adam's bias-correction factor 1 / (1 - beta^t) at step t >= 1 (Kingma and
+// Ba), as float. beta^t is formed in FP64 by binary exponentiation (at most
+// 2 log2 t products) instead of a library pow: FP64 issues slowly on this
+// part, and one pow per block took most of a small Adam launch. The products'
+// FP64 roundings lie far below the final fp32 rounding.
+__device__ __forceinline__ float adam_inv_bias(double beta, long long t)
+{
+    double r = 1.0, b = beta;
+    for (; t > 0; t >>= 1) {
+        if (t & 1)
+            r *= b;
+        b *= b;
+    }
+    return (float)(1.0 / (1.0 - r));
+}
+
+// One Adam update of a flat parameter (Kingma and Ba): m <- b1 m + o1 g,
+// v <- b2 v + o2 g^2 (o = 1 - b), returns p - lr (m ib1) / (sqrt(v ib2) + eps)
+// with ib = 1 / (1 - b^t); m and v are updated in place.
+__device__ __forceinline__ float adam_flat_update(float p, float g, float &m, float &v, float b1,
+                                                  float o1, float b2, float o2, float lr,
+                                                  float eps, float ib1, float ib2)
+{
+    m = fmaf(b1, m, o1 * g);
+    v = fmaf(b2, v, o2 * g * g);
+    return p - lr * ((m * ib1) / (sqrtf(v * ib2) + eps));
+}
+
 }  // namespace airgb

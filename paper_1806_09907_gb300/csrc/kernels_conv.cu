@@ -940,6 +940,72 @@ __global__ void k_pack_weights(const float *__restrict__ w, int cin, int cout, i
     }
 }
 
+// Position of B[n][k] in a packed copy whose slices start at slice s0 and
+// hold N rows: slice s0 + k / 64, group of 8 rows n / 8, chunk of 8 K
+// elements (k % 64) / 8, row n % 8, element k % 8 (k_pack_weights' layout).
+__device__ __forceinline__ int64_t packed_pos(int n, int k, int N, int s0)
+{
+    const int s = s0 + k / kBK, kk = k % kBK;
+    return ((int64_t)s * N + (n / 8) * 8) * kBK + (kk / 8) * 64 + (n % 8) * 8 + (kk & 7);
+}
+
+// Adam on a network's flat parameters with k_adam_flat's update, writing each
+// updated weight of the listed layers, rounded to bf16, to where
+// k_pack_weights puts it: forward B[co][t cin + ci]; dgrad at stride 1
+// B[ci][t cout + co]; at stride 2 B[ci][ti cout + co] in the slices of the
+// tap's parity class (odd offsets on the axes of the class; ti the tap's index
+// within it, x fastest). Each weight has one place per copy, so only real
+// weights are written and the zero padding of the previous pack stays.
+__global__ void k_adam_pack(AdamPackArgs a, const int64_t *__restrict__ step,
+                            float *__restrict__ p, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v)
+{
+    __shared__ float s_ib[2];
+    if (threadIdx.x == 0) {
+        const long long t = (long long)*step + 1;
+        s_ib[0] = adam_inv_bias(a.adam.beta1, t);
+        s_ib[1] = adam_inv_bias(a.adam.beta2, t);
+    }
+    __syncthreads();
+    const float b1 = (float)a.adam.beta1, b2 = (float)a.adam.beta2;
+    const float o1 = (float)(1.0 - a.adam.beta1), o2 = (float)(1.0 - a.adam.beta2);
+    const float ib1 = s_ib[0], ib2 = s_ib[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.adam.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float mm = m[i], vv = v[i];
+        const float pn =
+            adam_flat_update(p[i], g[i], mm, vv, b1, o1, b2, o2, a.adam.lr, a.adam.eps, ib1, ib2);
+        p[i] = pn;
+        m[i] = mm;
+        v[i] = vv;
+        for (int j = 0; j < a.nl; ++j) {
+            const PackLayer &L = a.L[j];
+            const int64_t r = i - L.off;
+            const int K = 27 * L.cin;
+            if (r < 0 || r >= (int64_t)L.cout * K)
+                continue;
+            const int co = (int)(r / K), k = (int)(r - (int64_t)co * K);
+            const int t = k / L.cin, ci = k - t * L.cin;
+            const __nv_bfloat16 b = __float2bfloat16_rn(pn);
+            if (L.fwd)
+                static_cast<__nv_bfloat16 *>(L.fwd)[packed_pos(co, k, L.cout, 0)] = b;
+            if (L.dmode == 1) {
+                static_cast<__nv_bfloat16 *>(L.dgrad)[packed_pos(ci, t * L.cout + co, L.cin, 0)] =
+                    b;
+            } else if (L.dmode == 2) {
+                const int tz = t / 9, ty = (t / 3) % 3, tx = t % 3;
+                const int cz = tz != 1, cy = ty != 1, cx = tx != 1;
+                const int cls = (cz << 2) | (cy << 1) | cx;
+                const int ti = ((cz ? tz / 2 : 0) * (1 + cy) + (cy ? ty / 2 : 0)) * (1 + cx) +
+                               (cx ? tx / 2 : 0);
+                static_cast<__nv_bfloat16 *>(L.dgrad)[packed_pos(ci, ti * L.cout + co, L.cin,
+                                                                 L.cls0[cls])] = b;
+            }
+            break;
+        }
+    }
+}
+
 // g_w[co][t][ci] and g_b[co] from the wgrad partials [split][mrows][N]: one
 // block of kReduceThreads per M row m = t cin + ci (m = 27 cin is the bias
 // row). Thread j adds the splits j / N, j / N + G, ... of column co = j % N
@@ -1199,6 +1265,34 @@ cudaError_t launch_conv_pack(const ConvLayer &l, const float *w, void *fwd, void
             static_cast<__nv_bfloat16 *>(dgrad));
     }
     return cudaGetLastError();
+}
+
+void adam_pack_layer(const ConvLayer &l, int64_t off, void *fwd, void *dgrad, PackLayer *L)
+{
+    *L = PackLayer{};
+    L->off = off;
+    L->cin = l.cin;
+    L->cout = l.cout;
+    L->fwd = fwd;
+    L->dgrad = dgrad;
+    L->dmode = dgrad ? (l.stride == 1 ? 1 : 2) : 0;
+    if (L->dmode == 2) {
+        int u0[kMaxClasses + 1], ns[kMaxClasses];
+        dgrad_classes(l, u0, ns, L->cls0, nullptr);
+    }
+}
+
+cudaError_t launch_adam_pack(const AdamPackArgs &a, int64_t *step, float *p, const float *g,
+                             float *m, float *v, cudaStream_t s)
+{
+    {
+        ProfScope ps(s, "k_adam_pack");
+        k_adam_pack<<<blocks_for(a.adam.n, 256), 256, 0, s>>>(a, step, p, g, m, v);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    return launch_step_tick(step, s);
 }
 
 static ConvArgs base_args(const ConvLayer &l)

@@ -1833,8 +1833,8 @@ __global__ void __launch_bounds__(BCfg<DELTA, T>::THREADS, BCfg<DELTA, T>::MINB)
     __shared__ double ks[3];
     __shared__ float s_inv_bc[2];
     if (threadIdx.x == 0) {
-        s_inv_bc[0] = (float)(1.0 / (1.0 - pow(st.beta1, (double)st.t)));
-        s_inv_bc[1] = (float)(1.0 / (1.0 - pow(st.beta2, (double)st.t)));
+        s_inv_bc[0] = adam_inv_bias(st.beta1, (long long)st.t);
+        s_inv_bc[1] = adam_inv_bias(st.beta2, (long long)st.t);
     }
     for (;;) {
         __syncthreads();  // the previous item is done with shared memory

@@ -289,23 +289,22 @@ __global__ void k_adam_flat(AdamFlatArgs a, const int64_t *__restrict__ step,
                             float *__restrict__ p, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v)
 {
-    __shared__ float s_bc[2];
+    __shared__ float s_ib[2];
     if (threadIdx.x == 0) {
-        const double t = (double)(*step + 1);
-        s_bc[0] = (float)(1.0 / (1.0 - pow(a.beta1, t)));
-        s_bc[1] = (float)(1.0 / (1.0 - pow(a.beta2, t)));
+        const long long t = (long long)*step + 1;
+        s_ib[0] = adam_inv_bias(a.beta1, t);
+        s_ib[1] = adam_inv_bias(a.beta2, t);
     }
     __syncthreads();
     const float b1 = (float)a.beta1, b2 = (float)a.beta2;
     const float o1 = (float)(1.0 - a.beta1), o2 = (float)(1.0 - a.beta2);
+    const float ib1 = s_ib[0], ib2 = s_ib[1];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mm = fmaf(b1, m[i], o1 * gi);
-        const float vv = fmaf(b2, v[i], o2 * gi * gi);
+        float mm = m[i], vv = v[i];
+        p[i] = adam_flat_update(p[i], g[i], mm, vv, b1, o1, b2, o2, a.lr, a.eps, ib1, ib2);
         m[i] = mm;
         v[i] = vv;
-        p[i] -= a.lr * ((mm * s_bc[0]) / (sqrtf(vv * s_bc[1]) + a.eps));
     }
 }
 
@@ -475,6 +474,11 @@ cudaError_t launch_adam_flat(const AdamFlatArgs &a, int64_t *step, float *p, con
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
+    return launch_step_tick(step, s);
+}
+
+cudaError_t launch_step_tick(int64_t *step, cudaStream_t s)
+{
     ProfScope ps(s, "k_tick");
     k_tick<<<1, 32, 0, s>>>(step);
     return cudaGetLastError();

@@ -38,9 +38,9 @@ __global__ void __launch_bounds__(kOptThreads)
 {
     __shared__ float s_inv_bc[2];
     if (threadIdx.x == 0) {
-        const double t = (double)(*step + 1);
-        s_inv_bc[0] = (float)(1.0 / (1.0 - pow(a.beta1, t)));
-        s_inv_bc[1] = (float)(1.0 / (1.0 - pow(a.beta2, t)));
+        const long long t = (long long)*step + 1;
+        s_inv_bc[0] = adam_inv_bias(a.beta1, t);
+        s_inv_bc[1] = adam_inv_bias(a.beta2, t);
     }
     __syncthreads();
     const float inv_bc1 = s_inv_bc[0], inv_bc2 = s_inv_bc[1];

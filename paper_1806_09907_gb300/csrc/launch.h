@@ -245,6 +245,27 @@ struct AdamFlatArgs {
 };
 cudaError_t launch_adam_flat(const AdamFlatArgs &a, int64_t *step, float *p, const float *g,
                              float *m, float *v, cudaStream_t s);
+// *step += 1 (one thread), after the Adam launches that read it.
+cudaError_t launch_step_tick(int64_t *step, cudaStream_t s);
+// Adam on a network's flat parameters (k_adam_flat's update) that also
+// writes the updated weights of up to kMaxPackLayers layers into their packed
+// bf16 copies, as launch_conv_pack lays them out; then ticks *step.
+constexpr int kMaxPackLayers = 8;
+struct PackLayer {
+    int64_t off;         // first weight (cout x 27 x cin) in the flat array
+    int cin, cout;
+    int dmode;           // dgrad copy: 0 none, 1 stride 1, 2 stride 2 (parity classes)
+    int cls0[8];         // dmode 2: first packed slice of each parity class
+    void *fwd, *dgrad;   // packed copies (bf16; fwd nullable)
+};
+struct AdamPackArgs {
+    AdamFlatArgs adam;
+    int nl;
+    PackLayer L[kMaxPackLayers];
+};
+void adam_pack_layer(const ConvLayer &l, int64_t off, void *fwd, void *dgrad, PackLayer *L);
+cudaError_t launch_adam_pack(const AdamPackArgs &a, int64_t *step, float *p, const float *g,
+                             float *m, float *v, cudaStream_t s);
 cudaError_t launch_render_blobs(int D, int H, int W, int count, int nblobs, const float *table,
                                 float *out, cudaStream_t s);
 

@@ -108,6 +108,12 @@ class InitNet:
             self.packed[k] = airgb.al_conv3d_pack(cv, self.weight(k), True, k > 0, stream=stream,
                                                   out=self.packed[k])
 
+    def packed_layers(self):
+        """(cv, weight offset, packed_fwd, packed_dgrad) per layer, the list
+        al_adam_flat_pack refreshes."""
+        return [(cv, int(self.offsets[k]), self.packed[k][0], self.packed[k][1])
+                for k, cv in enumerate(self.convs)]
+
     # ---- forward / backward ----
     def forward(self, fixed, moving, out=None, stream=None):
         """fixed, moving: (batch, *shape) fp32 -> coefficients (batch, 3, nz, ny, nx)."""
@@ -253,7 +259,7 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
     per step, `epochs` passes over the same pairs. The step size decays from
     lr to lr_final along a half cosine when lr_final is given (else stays lr).
     With a constant step size (and graph=True) the network part of a step --
-    forward, field loss, backward, Adam, packing, all on fixed buffers -- is
+    forward, field loss, backward, Adam with the packing, all on fixed buffers -- is
     captured once in a CUDA graph after the first (eager) step and replayed;
     the pair generation stays eager, so it is issued while the previous
     step's replay runs. Returns the per-step losses and the wall time."""
@@ -271,14 +277,16 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
                       device=dev)
     loss_one = torch.empty(1, dtype=torch.float64, device=dev)
     use_graph = graph and lr_final is None and steps > 1
+    layers = net.packed_layers()
     step_graph = None
 
     def net_step(F, M, ct, loss, lr_i):
         net.forward(F, M, out=c)
         airgb.al_field_loss(net.shape, c, ct, loss=loss, grad=gc, workspace=lws)
         net.backward(gc)
-        airgb.al_adam_flat(net.params, net.grad, m, v, step, lr=lr_i, betas=betas, eps=eps)
-        net.pack()
+        # the Adam update also rewrites the packed bf16 weights of the layers
+        airgb.al_adam_flat_pack(net.params, net.grad, m, v, step, layers, lr=lr_i, betas=betas,
+                                eps=eps)
 
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -417,7 +425,7 @@ def _main():
     """Training steps of the network at a given batch and volume size, for
     timing and profiling: python -m paper_1806_09907_gb300.learned_init
     --batch 16 --size 128 --steps 3 runs 3 steps (pair generation, forward,
-    field loss, backward, Adam, packing) and prints the device time of each."""
+    field loss, backward, Adam with the packing) and prints the device time of each."""
     import argparse
 
     p = argparse.ArgumentParser()

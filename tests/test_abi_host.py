@@ -417,6 +417,38 @@ def test_conv_calls_reject_before_launching(lib):
     assert lib.al_conv3d_backward_weight(p, a, a, a, None, None, ws, None) == 8
 
 
+def test_adam_flat_pack_rejects(lib):
+    """Argument checks of the Adam update with the packing (nothing launches)."""
+    a = ctypes.c_void_p(0x10000)
+    mis = ctypes.c_void_p(0x10004)
+    p = airgb.al_adam_params()
+    p.lr, p.beta1, p.beta2, p.eps = 1e-3, 0.9, 0.999, 1e-8
+    c1, c2 = _conv(cin=16, cout=32), _conv(cin=32, cout=16, stride=1)
+    n1, n2 = 32 * 27 * 16, 16 * 27 * 32
+
+    def call(n, layers, offs, pf, pd, par=p, param=a):
+        k = max(len(layers), 1)
+        return lib.al_adam_flat_pack(ctypes.byref(par), n, a, param, a, a, a, len(layers),
+                                     (airgb.al_conv3d * k)(*layers), (ctypes.c_int64 * k)(*offs),
+                                     (ctypes.c_void_p * k)(*pf), (ctypes.c_void_p * k)(*pd), None)
+
+    n = n1 + n2 + 48
+    # a valid call would launch: only rejections are exercised here
+    assert call(n, [c1, c2], [0, n1 + 32], [a, a], [None, None], param=mis) == 3
+    assert call(n, [], [], [], []) == 1                                   # no layer
+    assert call(n, [c1] * 9, [0] * 9, [a] * 9, [a] * 9) == 1               # more than 8
+    assert call(n, [c1, c2], [0, n1], [None, a], [None, a]) == 1           # neither copy
+    assert call(n, [c1, c2], [0, n1 - 1], [a, a], [a, a]) == 1             # ranges overlap
+    assert call(n, [c1, c2], [0, n - n2 + 1], [a, a], [a, a]) == 1         # past n
+    assert call(n, [c1, c2], [-1, n1], [a, a], [a, a]) == 1                # negative offset
+    assert call(n, [c1, c2], [0, n1], [a, mis], [a, a]) == 3               # packed alignment
+    assert call(n, [_conv(cin=2), c2], [0, n1], [a, a], [a, a]) == 7       # no dgrad for cin 2
+    assert call(n, [_conv(cout=24), c2], [0, n1], [a, a], [a, a]) == 2     # layer checks
+    bad = airgb.al_adam_params()
+    bad.lr, bad.beta1, bad.beta2, bad.eps = 1e-3, 1.0, 0.999, 1e-8
+    assert call(n, [c1, c2], [0, n1], [a, a], [a, a], par=bad) == 1        # beta1 < 1
+
+
 def test_initnet_glue_checks(lib):
     a = ctypes.c_void_p(0x10000)
     n3 = (ctypes.c_int64 * 3)(16, 16, 16)

@@ -236,6 +236,34 @@ def test_adam_flat_parity():
     assert int(step) == 3
 
 
+def test_adam_flat_pack_equals_adam_then_pack():
+    """The Adam update that rewrites the packed weights leaves the parameters,
+    moments and every layer's packed copies (forward only, stride-2 and
+    stride-1 input adjoints) equal bit for bit to al_adam_flat followed by
+    al_conv3d_pack, padding included, step after step."""
+    net = learned_init.InitNet((40, 33, 45), 2, DEV, seed=3, head_scale=1.0)
+    n = net.params.numel()
+    ref = net.params.clone()
+    m1, v1, m2, v2 = (torch.zeros_like(ref) for _ in range(4))
+    s1, s2 = (torch.zeros(1, dtype=torch.int64, device=DEV) for _ in range(2))
+    gen = np.random.default_rng(4)
+    for _ in range(3):
+        grad = torch.from_numpy(gen.normal(0, 1e-2, n).astype(np.float32)).to(DEV)
+        airgb.al_adam_flat(ref, grad, m1, v1, s1, lr=1e-2)
+        want = [airgb.al_conv3d_pack(cv, net.weight(k, ref), True, k > 0)
+                for k, cv in enumerate(net.convs)]
+        airgb.al_adam_flat_pack(net.params, grad, m2, v2, s2, net.packed_layers(), lr=1e-2)
+        torch.cuda.synchronize()
+        assert torch.equal(net.params, ref) and torch.equal(m1, m2) and torch.equal(v1, v2)
+        for k in range(len(net.convs)):
+            for got, exp in zip(net.packed[k], want[k]):
+                assert (got is None) == (exp is None)
+                if got is not None:
+                    assert torch.equal(got, exp), k
+    assert int(s1) == int(s2) == 3
+    assert airgb.al_get_device_error() == 0
+
+
 def _small_net(nb=2, shape=(40, 33, 45), seed=9):
     net = learned_init.InitNet(shape, nb, DEV, seed=seed, head_scale=1.0)
     g = np.random.default_rng(seed)
