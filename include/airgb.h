@@ -484,6 +484,16 @@ al_status al_conv3d_backward_weight(const al_conv3d *cv, const void *input,
                                     const void *grad_output, float *grad_weight, float *grad_bias,
                                     void *workspace, size_t workspace_bytes, al_stream stream);
 
+/* The network input of `count` pairs made by the method, with the fixed
+ * image F = M o (x + B c) of each pair formed on the fly: x[b][v] = (F[b][v],
+ * M[b][v]) as two bf16 channels, equal bit for bit to al_warp_ctrl followed
+ * by al_initnet_input, without F in device memory. bs: a 3D grid with spacing
+ * 4, 6 or 8 (AL_ERR_UNSUPPORTED otherwise); moving: count volumes; ctrl:
+ * count lattices of 3 planes (voxel units); x: count x Z x Y x X x 2 bf16.
+ * count 1 .. 65535; every array 16-byte aligned. */
+al_status al_initnet_pair_input(const al_bspline *bs, int32_t count, const float *moving,
+                                const float *ctrl, void *x, al_stream stream);
+
 /* The network's input: x[b][v] = (F[b][v], M[b][v]) as two bf16 channels,
  * from fp32 volumes of `batch` x size[0] x size[1] x size[2] (z, y, x). */
 al_status al_initnet_input(int32_t batch, const int64_t *size, const float *fixed,
@@ -553,7 +563,8 @@ al_status al_adam_flat_pack(const al_adam_params *p, int64_t n, int64_t *step, f
 /* Training volumes: out[v][z][y][x] = sum_b a_b exp(-|x - mu_b|^2/(2 sigma_b^2))
  * for `count` volumes of size (z, y, x), blob table[v][b] = {mu_x, mu_y,
  * mu_z, sigma, a} (fp32, n_blobs per volume; sigma > 0). Terms of blobs more
- * than 6 sigma from a voxel's 8^3 brick are dropped (each below 1.6e-8 a). */
+ * than 6 sigma from a voxel's 8 x 8 x 32 box (x, y, z) are dropped (each below
+ * 1.6e-8 a). */
 al_status al_render_blobs(const int64_t *size, int32_t count, int32_t n_blobs, const float *table,
                           float *out, al_stream stream);
 

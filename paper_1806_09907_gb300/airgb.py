@@ -49,7 +49,7 @@ EXPORTS = (
     "al_conv3d_backward_weight_workspace_bytes", "al_conv3d_backward_weight", "al_initnet_input",
     "al_initnet_upcat", "al_initnet_upcat_adjoint", "al_initnet_head_to_ctrl",
     "al_initnet_head_adjoint", "al_field_loss_workspace_bytes", "al_field_loss", "al_adam_flat",
-    "al_adam_flat_pack",
+    "al_adam_flat_pack", "al_initnet_pair_input",
     "al_render_blobs", "al_lcc_set_wait", "al_fused_set_wait", "al_warp_ctrl",
 )
 
@@ -108,6 +108,7 @@ def load():
         "al_bspline_init": ([P(al_bspline), P(al_grid), I32], I32),
         "al_displacement": ([P(al_bspline), VP, VP, VP], I32),
         "al_warp_ctrl": ([P(al_bspline), I32, VP, VP, VP, VP, VP], I32),
+        "al_initnet_pair_input": ([P(al_bspline), I32, VP, VP, VP, VP], I32),
         "al_displacement_adjoint": ([P(al_bspline), VP, VP, VP, SZ, VP], I32),
         "al_displacement_adjoint_workspace_bytes": ([P(al_bspline)], SZ),
         "al_warp": ([P(al_grid), VP, VP, VP, VP, VP], I32),
@@ -848,6 +849,23 @@ def al_initnet_input(fixed, moving, out=None, stream=None):
         out = torch.empty(shape + (2,), dtype=torch.bfloat16, device=fixed.device)
     _call("al_initnet_input", int(shape[0]), _i64x3(shape[1:]), _ptr(fixed), _ptr(moving),
           _ptr(out), _stream(stream))
+    return out
+
+
+def al_initnet_pair_input(shape, spacing, moving, ctrl, out=None, stream=None):
+    """Network input (count, *shape, 2) bf16 of the pairs F = M o (x + B c):
+    moving (count, *shape) fp32, ctrl (count, 3, nz, ny, nx) fp32."""
+    bs = bspline_init(shape, spacing)
+    count = int(moving.shape[0])
+    _f32(moving, (count,) + tuple(shape), "moving")
+    _f32(ctrl, (count, 3) + lattice_shape(shape, spacing), "ctrl")
+    if out is None:
+        out = torch.empty((count,) + tuple(shape) + (2,), dtype=torch.bfloat16,
+                          device=moving.device)
+    if out.dtype != torch.bfloat16 or tuple(out.shape) != (count,) + tuple(shape) + (2,):
+        raise ValueError("out: expected bf16 (count, *shape, 2)")
+    _call("al_initnet_pair_input", ctypes.byref(bs), count, _ptr(moving), _ptr(ctrl), _ptr(out),
+          _stream(stream))
     return out
 
 

@@ -231,7 +231,24 @@ al_status al_warp_ctrl(const al_bspline *bs, int32_t count, const float *moving,
         return AL_ERR_UNSUPPORTED;
     if (!aligned16(moving) || !aligned16(ctrl) || !aligned16(warped) || (mask && !aligned16(mask)))
         return AL_ERR_ALIGN;
-    return launched(launch_warp_ctrl(g, L, count, moving, ctrl, warped, mask, S(stream)));
+    return launched(launch_warp_ctrl(g, L, count, moving, ctrl, warped, mask, nullptr, S(stream)));
+}
+
+al_status al_initnet_pair_input(const al_bspline *bs, int32_t count, const float *moving,
+                                const float *ctrl, void *x, al_stream stream)
+{
+    Grid g;
+    Lattice L;
+    al_status st = check_bspline(bs, &g, &L);
+    if (st != AL_OK)
+        return st;
+    if (count < 1 || count > 65535 || !moving || !ctrl || !x)
+        return AL_ERR_INVALID_ARG;
+    if (g.ndim != 3 || (L.delta != 4 && L.delta != 6 && L.delta != 8))
+        return AL_ERR_UNSUPPORTED;
+    if (!aligned16(moving) || !aligned16(ctrl) || !aligned16(x))
+        return AL_ERR_ALIGN;
+    return launched(launch_warp_ctrl(g, L, count, moving, ctrl, nullptr, nullptr, x, S(stream)));
 }
 
 size_t al_displacement_adjoint_workspace_bytes(const al_bspline *bs)

@@ -16,6 +16,7 @@
 // LCC needs W in a neighbourhood, so it runs as: k_fused<FWD> writes W, the
 // mask and dM~/dy, k_lcc_stats and k_lcc_grad turn W into dS/dW, and
 // k_fused<GW> projects dS/dW * dM~/dy onto the control points.
+#include <cuda_bf16.h>
 #include <string.h>
 
 #include "launch.h"
@@ -397,7 +398,7 @@ __device__ __forceinline__ void flush_planes(int lp0, const float (&qz)[4][FCfg<
 // give the same bits. Returns false if a copy did not land in time (the
 // brick's partials are then not written).
 template <int D, int DELTA, int MODE, int BCX_ = brick_bcx(DELTA), int BCY_ = brick_bcy(DELTA),
-          bool TMA = false>
+          bool TMA = false, bool PAIR = false>
 __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                                             const float *__restrict__ F,
                                             const float *__restrict__ M,
@@ -410,7 +411,9 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                                             int *__restrict__ icnt = nullptr)
 {
     // MODE_FWD writes W, the mask and (when G_io is given) dM~/dy as D planes;
-    // MODE_GW reads dS/dW and those planes back (no expansion, no gathers).
+    // with PAIR it writes only the bf16 pairs (W, M) of the network input,
+    // W_out then pointing at them. MODE_GW reads dS/dW and those planes back
+    // (no expansion, no gathers).
     using C = FCfg<D, DELTA, MODE, BCX_, BCY_>;
     using T = TCfg<DELTA, MODE == MODE_GW ? MODE_FWD : MODE>;
     using GS = GCfg<DELTA>;
@@ -768,14 +771,19 @@ __device__ __forceinline__ bool fused_brick(const Grid &g, const Lattice &L,
                 }
                 const int v = (z * g.Y + y) * g.X + x;
                 if (MODE == MODE_FWD) {
-                    W_out[v] = inb[j] ? ip.v : 0.0f;
-                    if (m_out)
-                        m_out[v] = inb[j] ? 1 : 0;
-                    if (G_io) {
-                        G_io[v] = inb[j] ? ip.gx : 0.0f;
-                        G_io[g.nv + v] = inb[j] ? ip.gy : 0.0f;
-                        if (D == 3)
-                            G_io[2 * g.nv + v] = inb[j] ? ip.gz : 0.0f;
+                    if constexpr (PAIR) {
+                        reinterpret_cast<__nv_bfloat162 *>(W_out)[v] =
+                            __floats2bfloat162_rn(inb[j] ? ip.v : 0.0f, __ldg(M + v));
+                    } else {
+                        W_out[v] = inb[j] ? ip.v : 0.0f;
+                        if (m_out)
+                            m_out[v] = inb[j] ? 1 : 0;
+                        if (G_io) {
+                            G_io[v] = inb[j] ? ip.gx : 0.0f;
+                            G_io[g.nv + v] = inb[j] ? ip.gy : 0.0f;
+                            if (D == 3)
+                                G_io[2 * g.nv + v] = inb[j] ? ip.gz : 0.0f;
+                        }
                     }
                 } else if (inb[j]) {
                     const float gr[3] = {ip.gx, ip.gy, ip.gz};
@@ -1727,8 +1735,10 @@ cudaError_t run_all(const Grid &g, const Lattice &L, int kind, int window, doubl
 // ---------------------------------------------------------------------------
 // Warp of `count` volumes by the B-spline fields of their control lattices
 // (A1 + A2 fused, the forward brick with no gradient planes): W[v] =
-// M[v] o (x + B c[v]), mask[v] when given. blockIdx.y is the volume.
-template <int D, int DELTA>
+// M[v] o (x + B c[v]), mask[v] when given. With PAIR, W points at bf16 pairs
+// (W[v], M[v]) instead (the network input of the pair F = W). blockIdx.y is
+// the volume.
+template <int D, int DELTA, bool PAIR>
 __global__ void __launch_bounds__(FCfg<D, DELTA, MODE_FWD>::THREADS,
                                   FCfg<D, DELTA, MODE_FWD>::THREADS <= 512 ? 2 : 1)
     k_warp_ctrl(Grid g, Lattice L, int gbx, int gby, const float *__restrict__ M,
@@ -1737,25 +1747,26 @@ __global__ void __launch_bounds__(FCfg<D, DELTA, MODE_FWD>::THREADS,
     const int b = blockIdx.x;
     const int64_t vol = blockIdx.y;
     const int bx = b % gbx, by = (b / gbx) % gby, bz = b / (gbx * gby);
-    fused_brick<D, DELTA, MODE_FWD>(g, L, nullptr, M + vol * g.nv, c + vol * D * L.nc, nullptr,
-                                    W + vol * g.nv, m ? m + vol * g.nv : nullptr, nullptr,
-                                    nullptr, nullptr, bx, by, bz, b);
+    fused_brick<D, DELTA, MODE_FWD, brick_bcx(DELTA), brick_bcy(DELTA), false, PAIR>(
+        g, L, nullptr, M + vol * g.nv, c + vol * D * L.nc, nullptr, W + vol * g.nv,
+        m ? m + vol * g.nv : nullptr, nullptr, nullptr, nullptr, bx, by, bz, b);
 }
 
-template <int D, int DELTA>
+template <int D, int DELTA, bool PAIR>
 cudaError_t warp_ctrl_run(const Grid &g, const Lattice &L, int count, const float *M,
                           const float *c, float *W, uint8_t *m, cudaStream_t s)
 {
     using C = FCfg<D, DELTA, MODE_FWD>;
     const Layout lay = make_layout(g, L, 0, 3);
     if (C::dyn_smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_warp_ctrl<D, DELTA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::dyn_smem);
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_warp_ctrl<D, DELTA, PAIR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::dyn_smem);
         if (e != cudaSuccess)
             return e;
     }
-    ProfScope ps(s, "k_warp_ctrl");
-    k_warp_ctrl<D, DELTA><<<dim3(lay.nbricks, count), C::THREADS, C::dyn_smem, s>>>(
+    ProfScope ps(s, PAIR ? "k_warp_ctrl_pair" : "k_warp_ctrl");
+    k_warp_ctrl<D, DELTA, PAIR><<<dim3(lay.nbricks, count), C::THREADS, C::dyn_smem, s>>>(
         g, L, lay.gbx, lay.gby, M, c, W, m);
     return cudaGetLastError();
 }
@@ -1995,19 +2006,28 @@ cudaError_t launch_fused(const Grid &g, const Lattice &L, int kind, int window, 
 }
 
 cudaError_t launch_warp_ctrl(const Grid &g, const Lattice &L, int count, const float *M,
-                             const float *c, float *W, uint8_t *m, cudaStream_t s)
+                             const float *c, float *W, uint8_t *m, void *pair, cudaStream_t s)
 {
-    if (g.ndim == 3) {
+    if (pair) {  // the network input: 3D only
+        float *P = static_cast<float *>(pair);
+        if (g.ndim != 3)
+            return cudaErrorInvalidValue;
         switch (L.delta) {
-        case 4: return warp_ctrl_run<3, 4>(g, L, count, M, c, W, m, s);
-        case 6: return warp_ctrl_run<3, 6>(g, L, count, M, c, W, m, s);
-        case 8: return warp_ctrl_run<3, 8>(g, L, count, M, c, W, m, s);
+        case 4: return warp_ctrl_run<3, 4, true>(g, L, count, M, c, P, nullptr, s);
+        case 6: return warp_ctrl_run<3, 6, true>(g, L, count, M, c, P, nullptr, s);
+        case 8: return warp_ctrl_run<3, 8, true>(g, L, count, M, c, P, nullptr, s);
+        }
+    } else if (g.ndim == 3) {
+        switch (L.delta) {
+        case 4: return warp_ctrl_run<3, 4, false>(g, L, count, M, c, W, m, s);
+        case 6: return warp_ctrl_run<3, 6, false>(g, L, count, M, c, W, m, s);
+        case 8: return warp_ctrl_run<3, 8, false>(g, L, count, M, c, W, m, s);
         }
     } else {
         switch (L.delta) {
-        case 4: return warp_ctrl_run<2, 4>(g, L, count, M, c, W, m, s);
-        case 6: return warp_ctrl_run<2, 6>(g, L, count, M, c, W, m, s);
-        case 8: return warp_ctrl_run<2, 8>(g, L, count, M, c, W, m, s);
+        case 4: return warp_ctrl_run<2, 4, false>(g, L, count, M, c, W, m, s);
+        case 6: return warp_ctrl_run<2, 6, false>(g, L, count, M, c, W, m, s);
+        case 8: return warp_ctrl_run<2, 8, false>(g, L, count, M, c, W, m, s);
         }
     }
     return cudaErrorInvalidValue;

@@ -194,16 +194,20 @@ __device__ __forceinline__ float kb3(float r)
 
 // One block per (pair, component). Shared: the three banded Gram matrices
 // (n x 7 each; fp32 sums of at most 4 delta terms), two float planes of the
-// lattice, reduction scratch.
-__global__ void __launch_bounds__(kT) k_field_loss(FieldLossArgs a, const float *__restrict__ c,
+// lattice, reduction scratch. With one block per SM at most (a batch of 16
+// has 48 blocks), 1024 threads give each SM enough warps to cover the
+// shared-memory latency of the three banded passes.
+constexpr int kFieldT = 1024;
+
+__global__ void __launch_bounds__(kFieldT) k_field_loss(FieldLossArgs a, const float *__restrict__ c,
                                                    const float *__restrict__ ct,
                                                    float *__restrict__ gc, double *__restrict__ part)
 {
     extern __shared__ double fsm[];
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int np = nx * ny * nz;
-    double *red = fsm;  // kT doubles
-    float *Gs = reinterpret_cast<float *>(fsm + kT);
+    double *red = fsm;  // kFieldT doubles
+    float *Gs = reinterpret_cast<float *>(fsm + kFieldT);
     float *G[3] = {Gs, Gs + 7 * nx, Gs + 7 * (nx + ny)};
     float *b0 = Gs + 7 * (nx + ny + nz);
     float *b1 = b0 + np;
@@ -316,26 +320,31 @@ __global__ void k_tick(int64_t *step)
 
 // out[v][z][y][x] = sum_b a_b exp(-|x - mu_b|^2 / (2 sigma_b^2)) for the
 // blob table of volume v ([blob][mu_x, mu_y, mu_z, sigma, a]). A block owns
-// an 8 x 8 x 8 brick and first keeps the blobs that come within 6 sigma of
-// it (warp 0, in table order): a dropped term is below a exp(-18) < 1.6e-8 a
-// everywhere in the brick. A Gaussian separates into per-axis factors,
+// an 8 x 8 x 32 box (x, y, z) and first keeps the blobs that come within 6
+// sigma of it (warp 0, in table order): a dropped term is below
+// a exp(-18) < 1.6e-8 a everywhere in the box. A Gaussian separates into
+// per-axis factors,
 //   a exp(-|p - mu|^2 / (2 sigma^2)) = ex(x) ey(y) (a ez(z)),
-// so each kept blob takes 24 exponentials per brick (8 per axis), and a
-// voxel's sum is three shared-memory reads and two multiplies per blob.
-constexpr int kBrick = 8;
+// so each kept blob takes 48 exponentials per box (8 + 8 + 32). A thread
+// owns 8 voxels of one (x, y) column: per blob one product ex ey, two
+// 16-byte shared-memory reads of the 8 z factors and 8 FMAs.
+constexpr int kBrick = 8;                        // x and y extent of a box
+constexpr int kBrickZ = 32;                      // z extent: 4 groups of 8 slices
+constexpr int kFac = 2 * kBrick + kBrickZ;       // factors per kept blob
 
 __global__ void __launch_bounds__(256) k_render_blobs(int D, int H, int W, int nblobs,
                                                       const float *__restrict__ table,
                                                       float *__restrict__ out)
 {
-    extern __shared__ float fac[];  // kept blob k: ex[8], ey[8], a ez[8]
-    __shared__ int keep[1024];      // kept blob indices, in table order (n_blobs <= 1024)
+    extern __shared__ float4 fac4[];  // kept blob k: ex[8], ey[8], a ez[32]
+    float *fac = reinterpret_cast<float *>(fac4);
+    __shared__ int keep[1024];        // kept blob indices, in table order (n_blobs <= 1024)
     __shared__ int nkeep;
     const int vol = blockIdx.y;
     const int bx = (W + kBrick - 1) / kBrick, by = (H + kBrick - 1) / kBrick;
     const int brick = blockIdx.x;
     const int x0 = (brick % bx) * kBrick, y0 = ((brick / bx) % by) * kBrick,
-              z0 = (brick / (bx * by)) * kBrick;
+              z0 = (brick / (bx * by)) * kBrickZ;
     const float *tv = table + (int64_t)vol * nblobs * 5;
     if (threadIdx.x < 32) {
         int base = 0;
@@ -345,10 +354,11 @@ __global__ void __launch_bounds__(256) k_render_blobs(int D, int H, int W, int n
             if (b < nblobs) {
                 const float *e = tv + (int64_t)b * 5;
                 const float mx = e[0], my = e[1], mz = e[2], sg = e[3];
-                // distance from the centre to the brick's box
+                // distance from the centre to the box
                 const float dx = fmaxf(fmaxf((float)x0 - mx, mx - (float)(x0 + kBrick - 1)), 0.0f);
                 const float dy = fmaxf(fmaxf((float)y0 - my, my - (float)(y0 + kBrick - 1)), 0.0f);
-                const float dz = fmaxf(fmaxf((float)z0 - mz, mz - (float)(z0 + kBrick - 1)), 0.0f);
+                const float dz =
+                    fmaxf(fmaxf((float)z0 - mz, mz - (float)(z0 + kBrickZ - 1)), 0.0f);
                 in = dx * dx + dy * dy + dz * dz <= 36.0f * sg * sg;
             }
             const unsigned m = __ballot_sync(0xffffffffu, in);
@@ -361,32 +371,46 @@ __global__ void __launch_bounds__(256) k_render_blobs(int D, int H, int W, int n
     }
     __syncthreads();
     const int n = nkeep;
-    // the per-axis factors of the kept blobs at the brick's 8 coordinates
-    for (int t = threadIdx.x; t < n * 24; t += blockDim.x) {
-        const int k = t / 24, r = t - k * 24, axis = r >> 3, o = r & 7;
+    // the per-axis factors of the kept blobs at the box's coordinates
+    for (int t = threadIdx.x; t < n * kFac; t += blockDim.x) {
+        const int k = t / kFac, r = t - k * kFac;
+        const int axis = r < kBrick ? 0 : r < 2 * kBrick ? 1 : 2;
+        const int o = r - axis * kBrick;
         const float *e = tv + (int64_t)keep[k] * 5;
         const float c = (float)((axis == 0 ? x0 : axis == 1 ? y0 : z0) + o) - e[axis];
         const float v = expf(-0.5f * c * c / (e[3] * e[3]));
         fac[t] = axis == 2 ? e[4] * v : v;
     }
     __syncthreads();
-    // a thread takes the voxels lz and lz + 4 of one (x, y) column of the
-    // brick, sharing the x-y factor product (256 threads, 512 voxels)
-    const int64_t nv = (int64_t)D * H * W;
-    const int t = threadIdx.x & 255, lx = t & 7, ly = (t >> 3) & 7, lz = t >> 6;
-    const int x = x0 + lx, y = y0 + ly;
-    float acc0 = 0.0f, acc1 = 0.0f;
+    // thread: column (lx, ly), slices 8 zg .. 8 zg + 7 of the box
+    const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, zg = t >> 6;
+    float acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        acc[i] = 0.0f;
     for (int k = 0; k < n; ++k) {
-        const float *f = fac + 24 * k;
-        const float pxy = f[lx] * f[8 + ly];
-        acc0 = fmaf(pxy, f[16 + lz], acc0);
-        acc1 = fmaf(pxy, f[20 + lz], acc1);
+        const float *f = fac + kFac * k;
+        const float pxy = f[lx] * f[kBrick + ly];
+        const float4 za = fac4[(kFac * k + 2 * kBrick + 8 * zg) / 4];
+        const float4 zb = fac4[(kFac * k + 2 * kBrick + 8 * zg) / 4 + 1];
+        acc[0] = fmaf(pxy, za.x, acc[0]);
+        acc[1] = fmaf(pxy, za.y, acc[1]);
+        acc[2] = fmaf(pxy, za.z, acc[2]);
+        acc[3] = fmaf(pxy, za.w, acc[3]);
+        acc[4] = fmaf(pxy, zb.x, acc[4]);
+        acc[5] = fmaf(pxy, zb.y, acc[5]);
+        acc[6] = fmaf(pxy, zb.z, acc[6]);
+        acc[7] = fmaf(pxy, zb.w, acc[7]);
     }
-    if (threadIdx.x < 256 && x < W && y < H) {
-        if (z0 + lz < D)
-            out[(int64_t)vol * nv + ((int64_t)(z0 + lz) * H + y) * W + x] = acc0;
-        if (z0 + lz + 4 < D)
-            out[(int64_t)vol * nv + ((int64_t)(z0 + lz + 4) * H + y) * W + x] = acc1;
+    const int64_t nv = (int64_t)D * H * W;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x < W && y < H) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int z = z0 + 8 * zg + i;
+            if (z < D)
+                out[(int64_t)vol * nv + ((int64_t)z * H + y) * W + x] = acc[i];
+        }
     }
 }
 
@@ -440,7 +464,7 @@ cudaError_t launch_head_adjoint(const NetGrid &g, int ch, const float *gc, void 
 size_t field_loss_smem(const FieldLossArgs &a)
 {
     const int np = a.n[0] * a.n[1] * a.n[2];
-    return sizeof(double) * kT + sizeof(float) * 7 * (a.n[0] + a.n[1] + a.n[2]) +
+    return sizeof(double) * kFieldT + sizeof(float) * 7 * (a.n[0] + a.n[1] + a.n[2]) +
            sizeof(float) * 2 * np;
 }
 
@@ -454,7 +478,7 @@ cudaError_t launch_field_loss(const FieldLossArgs &a, int nb, const float *c, co
         return e;
     {
         ProfScope ps(s, "k_field_loss");
-        k_field_loss<<<nb * 3, kT, sm, s>>>(a, c, ct, gc, part);
+        k_field_loss<<<nb * 3, kFieldT, sm, s>>>(a, c, ct, gc, part);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -489,9 +513,10 @@ cudaError_t launch_render_blobs(int D, int H, int W, int count, int nblobs, cons
 {
     ProfScope ps(s, "k_render_blobs");
     const int bricks = ((W + kBrick - 1) / kBrick) * ((H + kBrick - 1) / kBrick) *
-                       ((D + kBrick - 1) / kBrick);
+                       ((D + kBrickZ - 1) / kBrickZ);
     dim3 grid(bricks, count);
-    const size_t smem = sizeof(float) * 24 * (size_t)nblobs;  // up to 96 KB (1024 blobs)
+    // up to 192 KB (1024 blobs), beside the 4 KB keep list
+    const size_t smem = sizeof(float) * kFac * (size_t)nblobs;
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(
             k_render_blobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -208,8 +208,9 @@ int unit_error_lcc(bool clear);
 // Test hook of the LCC gradient's bounded waits (al_lcc_set_wait).
 cudaError_t lcc_set_drop_slice(int slice);
 cudaError_t fused_set_drop_batch(int batch);
+// pair (nullable, 3D only): write the bf16 pairs (W, M) there instead of W and m.
 cudaError_t launch_warp_ctrl(const Grid &g, const Lattice &L, int count, const float *M,
-                             const float *c, float *W, uint8_t *m, cudaStream_t s);
+                             const float *c, float *W, uint8_t *m, void *pair, cudaStream_t s);
 
 // Grids of the network's two coarsest levels: n3 (e3, the head) and n4 (e4),
 // (z, y, x); lat = spacing-8 lattice sizes (x, y, z).

@@ -117,9 +117,16 @@ class InitNet:
     # ---- forward / backward ----
     def forward(self, fixed, moving, out=None, stream=None):
         """fixed, moving: (batch, *shape) fp32 -> coefficients (batch, 3, nz, ny, nx)."""
+        self.acts["xin"] = airgb.al_initnet_input(fixed, moving, out=self.acts.get("xin"),
+                                                  stream=stream)
+        return self.forward_input(self.acts["xin"], out=out, stream=stream)
+
+    def forward_input(self, x, out=None, stream=None):
+        """The network on a prepared input x (batch, *shape, 2) bf16 (al_initnet_input's
+        or al_initnet_pair_input's); x must stay unchanged until backward."""
         A = self.acts
-        A["x"] = airgb.al_initnet_input(fixed, moving, out=A.get("x"), stream=stream)
-        a = A["x"]
+        A["x"] = x
+        a = x
         for k, name in enumerate(("e1", "e2", "e3", "e4")):
             a = airgb.al_conv3d_forward(self.convs[k], a, self.packed[k][0], self.bias(k),
                                         relu=True, out=A.get(name), workspace=self.fspaces[k],
@@ -202,7 +209,8 @@ class PairSource:
     """Training or test pairs made by the method: M = blob volume (60 blobs,
     centres uniform in the volume, sigma uniform in [3, 12] voxels, amplitudes
     uniform in [0, 1]), c* ~ N(0, sigma^2) voxels on the spacing-8 lattice,
-    F = M o (x + B c*) through al_displacement and al_warp. The random numbers
+    F = M o (x + B c*) through al_warp_ctrl (or, for training, only the
+    network input (F, M) through al_initnet_pair_input). The random numbers
     are drawn on the device by a counter-based generator (PyTorch's Philox)
     seeded with (seed, first pair), so a batch is fixed by its seed and index."""
 
@@ -232,17 +240,29 @@ class PairSource:
         self.offset = torch.tensor([0.0, 0.0, 0.0, lo_s, 0.0], dtype=torch.float32,
                                    device=self.device)
 
-    def make(self, first, stream=None):
-        """Pairs first .. first + batch - 1: (F, M, c*) on the device."""
+    def _draw(self, first, stream=None):
+        """M and c* of pairs first .. first + batch - 1."""
         self.gen.manual_seed(self.seed * 1_000_003 + int(first))
         torch.rand(self.table.shape, generator=self.gen, device=self.device, out=self.table)
         self.table.mul_(self.scale).add_(self.offset)
         torch.randn(self.ctrl.shape, generator=self.gen, device=self.device, out=self.ctrl)
         self.ctrl.mul_(self.sigma)
         airgb.al_render_blobs(self.shape, self.table, out=self.M, stream=stream)
+
+    def make(self, first, stream=None):
+        """Pairs first .. first + batch - 1: (F, M, c*) on the device."""
+        self._draw(first, stream)
         # F = M o (x + B c*), the whole batch in one launch
         airgb.al_warp_ctrl(self.shape, SPACING, self.M, self.ctrl, warped=self.F, stream=stream)
         return self.F, self.M, self.ctrl
+
+    def make_input(self, first, x, stream=None):
+        """The same pairs as make(first) as the network input only: x (batch,
+        *shape, 2) bf16 receives (F, M) as al_initnet_input(*make(first)[:2])
+        would write it, without F in device memory. Returns (x, c*)."""
+        self._draw(first, stream)
+        airgb.al_initnet_pair_input(self.shape, SPACING, self.M, self.ctrl, out=x, stream=stream)
+        return x, self.ctrl
 
 
 @dataclasses.dataclass
@@ -276,12 +296,13 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
     lws = torch.empty(max(airgb.field_loss_workspace_bytes(net.batch), 256), dtype=torch.uint8,
                       device=dev)
     loss_one = torch.empty(1, dtype=torch.float64, device=dev)
+    xin = torch.empty((net.batch,) + tuple(net.shape) + (2,), dtype=torch.bfloat16, device=dev)
     use_graph = graph and lr_final is None and steps > 1
     layers = net.packed_layers()
     step_graph = None
 
-    def net_step(F, M, ct, loss, lr_i):
-        net.forward(F, M, out=c)
+    def net_step(x, ct, loss, lr_i):
+        net.forward_input(x, out=c)
         airgb.al_field_loss(net.shape, c, ct, loss=loss, grad=gc, workspace=lws)
         net.backward(gc)
         # the Adam update also rewrites the packed bf16 weights of the layers
@@ -291,19 +312,19 @@ def train(net: InitNet, pairs=20000, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, sigm
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for i in range(steps):
-        F, M, ct = src.make((i % per_epoch) * net.batch)
+        x, ct = src.make_input((i % per_epoch) * net.batch, xin)
         if step_graph is not None:
             step_graph.replay()
             losses[i:i + 1].copy_(loss_one)
         else:
             lr_i = lr if lr_final is None else \
                 lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * i / max(steps - 1, 1)))
-            net_step(F, M, ct, losses[i:i + 1], lr_i)
+            net_step(x, ct, losses[i:i + 1], lr_i)
             if use_graph:
                 # the buffers exist now (the eager step made them): capture
                 step_graph = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(step_graph, capture_error_mode="thread_local"):
-                    net_step(F, M, ct, loss_one, lr)
+                    net_step(x, ct, loss_one, lr)
         if log_every and (i + 1) % log_every == 0:
             print(f"step {i + 1}/{steps} loss {float(losses[i]):.4f}", flush=True)
     torch.cuda.synchronize(dev)

@@ -324,6 +324,22 @@ def test_warp_ctrl_rejects(lib):
     assert lib.al_warp_ctrl(ctypes.byref(bs5), 2, a, a, a, None, None) == 7
 
 
+def test_initnet_pair_input_rejects(lib):
+    """al_initnet_pair_input: bad count or NULL pointers 1, a 2D grid or a
+    spacing without a fused kernel 7, a misaligned pointer 3; nothing launches."""
+    bs = airgb.bspline_init((20, 36, 48), 8)
+    a = ctypes.c_void_p(0x10000)
+    assert lib.al_initnet_pair_input(ctypes.byref(bs), 0, a, a, a, None) == 1
+    assert lib.al_initnet_pair_input(ctypes.byref(bs), 70000, a, a, a, None) == 1
+    assert lib.al_initnet_pair_input(ctypes.byref(bs), 2, a, a, None, None) == 1
+    assert lib.al_initnet_pair_input(ctypes.byref(bs), 2, a, a, ctypes.c_void_p(0x10004),
+                                     None) == 3
+    bs5 = airgb.bspline_init((20, 36, 48), 5)
+    assert lib.al_initnet_pair_input(ctypes.byref(bs5), 2, a, a, a, None) == 7
+    bs2 = airgb.bspline_init((36, 48), 8)
+    assert lib.al_initnet_pair_input(ctypes.byref(bs2), 2, a, a, a, None) == 7
+
+
 def test_batch_bind_tune_status_reject(lib):
     """Binding checks every device pointer (NULL 1, misaligned 3) and the
     workspace (8) on the host; tuning needs a bound workspace (8) and at

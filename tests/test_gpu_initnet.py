@@ -205,8 +205,10 @@ def test_field_loss_parity(shape):
     assert np.linalg.norm(gg - gref) <= 1e-5 * np.linalg.norm(gref)
 
 
-def test_render_blobs_parity():
-    shape = (21, 30, 17)
+@pytest.mark.parametrize("shape", [(21, 30, 17), (75, 19, 26)])
+def test_render_blobs_parity(shape):
+    """Boxes of 8 x 8 x 32 voxels, ragged in every axis, against the full sum
+    over every blob (culled terms are below 1.6e-8 of their amplitude)."""
     table = synth.blob_table(3, shape, 12, seed=5)
     out = _np(airgb.al_render_blobs(shape, torch.from_numpy(table).to(DEV)))
     for v in range(3):
@@ -400,6 +402,22 @@ def test_training_pairs_are_registered_by_their_coefficients():
         val, _ = airgb.al_objective_grad(pr, F[b], M[b], ct[b].clone())
         val0, _ = airgb.al_objective_grad(pr, F[b], M[b], torch.zeros_like(ct[b]))
         assert float(val[1]) <= 1e-8 and float(val0[1]) > 1e-4, (float(val[1]), float(val0[1]))
+
+
+def test_training_input_equals_the_pairs_input():
+    """The training step's input (al_initnet_pair_input, no F in device
+    memory) is the network input of the pairs make() returns, bit for bit,
+    with the same c*."""
+    src = learned_init.PairSource((48, 40, 56), 2, sigma=3.0, seed=3, device=DEV)
+    F, M, ct = src.make(2)
+    want_x = airgb.al_initnet_input(F, M)
+    want_c = ct.clone()
+    x = torch.empty_like(want_x)
+    got_x, got_c = src.make_input(2, x)
+    torch.cuda.synchronize()
+    assert got_x is x
+    assert torch.equal(x.view(torch.int16), want_x.view(torch.int16))
+    assert torch.equal(got_c, want_c)
 
 
 def test_short_training_lowers_the_loss():

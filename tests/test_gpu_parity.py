@@ -225,6 +225,24 @@ def test_warp_ctrl_batch(shape, delta):
         assert np.all(W[k][mk[k] == 0] == 0.0)
 
 
+@pytest.mark.parametrize("delta", [4, 6, 8])
+def test_initnet_pair_input_equals_warp_then_input(delta):
+    """The network input formed with the warp (no F in device memory) equals
+    al_warp_ctrl followed by al_initnet_input bit for bit, on a shape with
+    ragged bricks in every axis."""
+    shape = (21, 30, 37)
+    Ms, cs = [], []
+    for k in range(3):
+        _, M, c = blob_case(shape, delta, 2.0, 90 + 5 * k)
+        Ms.append(M)
+        cs.append(c)
+    Mb, cb = dev(np.stack(Ms)), dev(np.stack(cs))
+    want = airgb.al_initnet_input(airgb.al_warp_ctrl(shape, delta, Mb, cb), Mb)
+    got = airgb.al_initnet_pair_input(shape, delta, Mb, cb)
+    torch.cuda.synchronize()
+    assert torch.equal(got.view(torch.int16), want.view(torch.int16))
+
+
 # ----------------------------------------------------------------------- A4 --
 
 @pytest.mark.parametrize("shape", [(37, 45), (19, 23, 29), (2, 2, 2)])
