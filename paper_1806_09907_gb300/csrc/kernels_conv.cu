@@ -24,9 +24,10 @@
 // fp32 in tensor memory. A CTA of 4 warps owns a 128-row tile of D in TMEM
 // (tcgen05.alloc) and walks a stream of work items (one K slice of 64 of a
 // tile each, tile after tile, the CTA's tiles strided by the grid). The
-// threads gather the im2col operand of the item two slices ahead with
-// cp.async (16-byte copies, zero-filled at the faces) into a 3-slot
-// shared-memory ring; the weight operand of the forward and dgrad passes is
+// threads gather the im2col operand of the next item with cp.async
+// (16-byte copies, zero-filled at the faces) into a 2-slot shared-memory
+// ring (a 3-slot ring two items ahead fitted fewer CTAs per SM and was
+// slower: these gathers want resident warps more than depth); the weight operand of the forward and dgrad passes is
 // stored pre-tiled in the shared-memory layout, so each slice of it arrives
 // with one cp.async.bulk on an mbarrier. One thread issues tcgen05.mma
 // (kind::f16, bf16 x bf16 -> f32, M = 128, K = 16 per instruction) on
@@ -60,8 +61,8 @@ namespace {
 __device__ int g_conv_error = 0;
 
 constexpr int kThreads = 128;
-constexpr int kStages = 3;                    // shared-memory ring slots
-constexpr int kAhead = 2;                     // items gathered ahead of the MMA (< kStages)
+constexpr int kStages = 2;                    // shared-memory ring slots
+constexpr int kAhead = 1;                     // items gathered ahead of the MMA (< kStages)
 constexpr int kBK = 64;                       // K elements per ring slot
 constexpr int kATile = 128 * kBK * 2;         // bytes of one A slot (16 KB)
 // wgrad and split-K blocks aimed at (8 per SM of a 152-SM GB300). A constant,
