@@ -327,7 +327,7 @@ __global__ void k_tick(int64_t *step)
 //   a exp(-|p - mu|^2 / (2 sigma^2)) = ex(x) ey(y) (a ez(z)),
 // so each kept blob takes 48 exponentials per box (8 + 8 + 32). A thread
 // owns 8 voxels of one (x, y) column: per blob one product ex ey, two
-// 16-byte shared-memory reads of the 8 z factors and 8 FMAs.
+// 16-byte shared-memory reads of the 8 z factors and 4 packed f32x2 FMAs.
 constexpr int kBrick = 8;                        // x and y extent of a box
 constexpr int kBrickZ = 32;                      // z extent: 4 groups of 8 slices
 constexpr int kFac = 2 * kBrick + kBrickZ;       // factors per kept blob
@@ -382,25 +382,24 @@ __global__ void __launch_bounds__(256) k_render_blobs(int D, int H, int W, int n
         fac[t] = axis == 2 ? e[4] * v : v;
     }
     __syncthreads();
-    // thread: column (lx, ly), slices 8 zg .. 8 zg + 7 of the box
+    // thread: column (lx, ly), slices 8 zg .. 8 zg + 7 of the box; the 8
+    // sums as 4 pairs, each blob's 8 FMAs as 4 packed f32x2 FMAs (the same
+    // rounding per lane)
     const int t = threadIdx.x, lx = t & 7, ly = (t >> 3) & 7, zg = t >> 6;
-    float acc[8];
+    float2 acc[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-        acc[i] = 0.0f;
+    for (int i = 0; i < 4; ++i)
+        acc[i] = make_float2(0.0f, 0.0f);
     for (int k = 0; k < n; ++k) {
         const float *f = fac + kFac * k;
         const float pxy = f[lx] * f[kBrick + ly];
+        const float2 p2 = make_float2(pxy, pxy);
         const float4 za = fac4[(kFac * k + 2 * kBrick + 8 * zg) / 4];
         const float4 zb = fac4[(kFac * k + 2 * kBrick + 8 * zg) / 4 + 1];
-        acc[0] = fmaf(pxy, za.x, acc[0]);
-        acc[1] = fmaf(pxy, za.y, acc[1]);
-        acc[2] = fmaf(pxy, za.z, acc[2]);
-        acc[3] = fmaf(pxy, za.w, acc[3]);
-        acc[4] = fmaf(pxy, zb.x, acc[4]);
-        acc[5] = fmaf(pxy, zb.y, acc[5]);
-        acc[6] = fmaf(pxy, zb.z, acc[6]);
-        acc[7] = fmaf(pxy, zb.w, acc[7]);
+        acc[0] = __ffma2_rn(p2, make_float2(za.x, za.y), acc[0]);
+        acc[1] = __ffma2_rn(p2, make_float2(za.z, za.w), acc[1]);
+        acc[2] = __ffma2_rn(p2, make_float2(zb.x, zb.y), acc[2]);
+        acc[3] = __ffma2_rn(p2, make_float2(zb.z, zb.w), acc[3]);
     }
     const int64_t nv = (int64_t)D * H * W;
     const int x = x0 + lx, y = y0 + ly;
@@ -409,7 +408,8 @@ __global__ void __launch_bounds__(256) k_render_blobs(int D, int H, int W, int n
         for (int i = 0; i < 8; ++i) {
             const int z = z0 + 8 * zg + i;
             if (z < D)
-                out[(int64_t)vol * nv + ((int64_t)z * H + y) * W + x] = acc[i];
+                out[(int64_t)vol * nv + ((int64_t)z * H + y) * W + x] =
+                    (i & 1) ? acc[i >> 1].y : acc[i >> 1].x;
         }
     }
 }
