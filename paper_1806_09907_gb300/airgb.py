@@ -941,6 +941,16 @@ def al_adam_flat_pack(param, grad, m, v, step, layers, lr=1e-3, betas=(0.9, 0.99
     """al_adam_flat plus the refresh of packed weights: layers is a list of
     (cv, weight_offset, packed_fwd, packed_dgrad), the packed tensors (either
     None) holding an al_conv3d_pack result of that layer."""
+    n = param.numel()
+    for t, what in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
+        _f32(t, (n,), what)
+    for cv, _, f, d in layers:
+        # the kernel writes every slot of a real weight: the copies must be
+        # whole al_conv3d_pack results of this layer
+        for t, kind in ((f, 0), (d, 1)):
+            if t is not None and t.numel() * t.element_size() != \
+                    load().al_conv3d_packed_bytes(ctypes.byref(cv), kind):
+                raise ValueError("packed weights: expected an al_conv3d_pack result of the layer")
     p = al_adam_params()
     p.lr, p.beta1, p.beta2, p.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
     nl = len(layers)
@@ -948,7 +958,7 @@ def al_adam_flat_pack(param, grad, m, v, step, layers, lr=1e-3, betas=(0.9, 0.99
     offs = (ctypes.c_int64 * max(nl, 1))(*[int(l[1]) for l in layers])
     pf = (ctypes.c_void_p * max(nl, 1))(*[_ptr(l[2]) for l in layers])
     pd = (ctypes.c_void_p * max(nl, 1))(*[_ptr(l[3]) for l in layers])
-    _call("al_adam_flat_pack", ctypes.byref(p), ctypes.c_int64(param.numel()), _ptr(step),
+    _call("al_adam_flat_pack", ctypes.byref(p), ctypes.c_int64(n), _ptr(step),
           _ptr(param), _ptr(grad), _ptr(m), _ptr(v), nl, cvs, offs, pf, pd, _stream(stream))
 
 

@@ -264,6 +264,13 @@ def test_adam_flat_pack_equals_adam_then_pack():
                     assert torch.equal(got, exp), k
     assert int(s1) == int(s2) == 3
     assert airgb.al_get_device_error() == 0
+    # a packed copy that is not a whole pack result of its layer is refused
+    # before anything launches
+    bad = net.packed_layers()
+    bad[2] = (bad[2][0], bad[2][1], bad[2][2][:-64], bad[2][3])
+    with pytest.raises(ValueError):
+        airgb.al_adam_flat_pack(net.params, grad, m2, v2, s2, bad, lr=1e-2)
+    assert int(s2) == 3
 
 
 def _small_net(nb=2, shape=(40, 33, 45), seed=9):
