@@ -57,12 +57,12 @@ FLUSH_BYTES = 256 << 20
 #    transposed expansion (28): 31 flops;
 #  - the point-wise fused MSE / NCC kernels: read F and M (8 B); expansion,
 #    warp and its adjoint, transposed expansion, the similarity terms:
-#    150 / 160 flops (the survey's 120-180 for the MSE path).
+#    150 / 160 flops (120-180 by a per-step count for the MSE path).
 KERNEL_WORK = {  # name: (bytes per voxel, flops per voxel)
     "k_lcc_stats": (21.0, 118.0), "k_lcc_grad": (25.0, 58.0), "k_fused_fwd": (21.0, 83.0),
     "k_fused_gw": (16.0, 31.0), "k_fused_mse": (8.0, 150.0), "k_fused_ncc": (8.0, 160.0),
 }
-# Whole evaluation (the survey's grading formula): algorithmic bytes 8 B per
+# Whole evaluation (roofline of one objective evaluation): algorithmic bytes 8 B per
 # voxel (F and M read once) + 8 B per control coefficient (c in, dJ/dc out);
 # algorithmic flops per voxel: expansion and transposed expansion (2 x 28),
 # trilinear value and gradient (55), and the similarity: MSE 40 / NCC 50 /

@@ -73,7 +73,7 @@ typedef enum {
     AL_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
     AL_ERR_BOUNDS = 5,      /* a kernel saw an index out of range (checked builds) */
     AL_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
-    AL_ERR_UNSUPPORTED = 7, /* valid but not supported by this build */
+    AL_ERR_UNSUPPORTED = 7, /* valid but not supported by this library */
     AL_ERR_WORKSPACE = 8,   /* workspace missing or too small */
     AL_ERR_SCRATCH_LIMIT = 9 /* problem needs more than the built-in scratch of the
                                 allocation-free entry point */

@@ -179,7 +179,7 @@ const char *al_status_string(al_status s)
     case AL_ERR_CUDA: return "CUDA error";
     case AL_ERR_BOUNDS: return "kernel index out of range";
     case AL_ERR_TIMEOUT: return "device wait timed out";
-    case AL_ERR_UNSUPPORTED: return "not supported by this build";
+    case AL_ERR_UNSUPPORTED: return "not supported by this library";
     case AL_ERR_WORKSPACE: return "workspace missing or too small";
     case AL_ERR_SCRATCH_LIMIT: return "problem too large for the built-in scratch";
     }
